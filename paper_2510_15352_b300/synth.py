@@ -1,0 +1,110 @@
+"""Seeded synthetic inputs: Gaussian scenes and robot-mounted cameras.
+
+This module is shared by the tests, the benchmark and the CPU oracle's callers.
+It holds none of the rendering arithmetic: it only draws random scene
+attributes and builds camera poses. Everything is numpy ``default_rng`` with
+explicit seeds; the same call always returns the same arrays.
+
+The paper's own scenes (2,500 reconstructed splat scenes, Sec. 1 and Sec. 3.1)
+are not available, so these stand in for them, shaped like the paper's
+workload: thousands of robots, each with one camera at 640x480 (Sec. 1,
+Table 1), many robots per scene (4,096 environments over 128 scenes, Sec. 3.3).
+
+Scene layout (structure of arrays, float32 unless a half type is requested):
+  mean          (3, N)  world position, uniform in a 10 x 10 x 3 m box (z up)
+  log_scale     (3, N)  i.i.d. normal(-3, 0.5)
+  quat          (4, N)  (w, x, y, z) = normalised standard normal 4-vector
+  logit_opacity (N,)    standard normal
+  sh            (K, 3, N), K = (deg+1)^2, coefficient-major then channel:
+                DC uniform in [-sqrt(pi), sqrt(pi)] (the DC range whose
+                degree-0 colour is uniform in [0, 1]); higher coefficients
+                normal(0, 0.2)
+Camera: world->camera 4x4 viewmat (OpenCV axes: x right, y down, z forward)
+and intrinsics (fx, fy, cx, cy); pitch = roll = 0, yaw uniform in [0, 2 pi),
+position xy uniform in [1, 9]^2.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SCENE_BOX = (10.0, 10.0, 3.0)
+
+
+def make_scene(n: int, sh_degree: int, seed: int = 0) -> dict:
+    """One synthetic scene of ``n`` Gaussians with SH degree ``sh_degree``."""
+    rng = np.random.default_rng([seed, 0])
+    mean = rng.uniform(0.0, 1.0, size=(3, n)) * np.array(SCENE_BOX)[:, None]
+    log_scale = rng.normal(-3.0, 0.5, size=(3, n))
+    q = rng.normal(size=(4, n))
+    q /= np.linalg.norm(q, axis=0, keepdims=True)
+    logit = rng.normal(0.0, 1.0, size=n)
+    K = (sh_degree + 1) ** 2
+    sh = np.empty((K, 3, n))
+    sh[0] = rng.uniform(-math.sqrt(math.pi), math.sqrt(math.pi), size=(3, n))
+    if K > 1:
+        sh[1:] = rng.normal(0.0, 0.2, size=(K - 1, 3, n))
+    return {
+        "mean": mean.astype(np.float32),
+        "log_scale": log_scale.astype(np.float32),
+        "quat": q.astype(np.float32),
+        "logit_opacity": logit.astype(np.float32),
+        "sh": sh.astype(np.float32),
+        "sh_degree": int(sh_degree),
+    }
+
+
+def viewmat_from_pose(pos, yaw: float) -> np.ndarray:
+    """World->camera matrix of a level camera at ``pos`` looking along yaw.
+
+    Camera axes in world coordinates: forward (cos y, sin y, 0), right
+    (sin y, -cos y, 0), down (0, 0, -1); rows of R are (right, down, forward)
+    and t = -R pos.
+    """
+    f = np.array([math.cos(yaw), math.sin(yaw), 0.0])
+    r = np.array([math.sin(yaw), -math.cos(yaw), 0.0])
+    d = np.array([0.0, 0.0, -1.0])
+    R = np.stack([r, d, f])
+    V = np.eye(4)
+    V[:3, :3] = R
+    V[:3, 3] = -R @ np.asarray(pos, dtype=np.float64)
+    return V
+
+
+def make_cameras(n: int, W: int, H: int, focal: float, height=(0.5, 0.5),
+                 seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """``n`` robot cameras: viewmats (n,4,4) and intrinsics (n,4), float32.
+
+    height: (lo, hi) of the uniform camera height (lo == hi for a fixed one).
+    """
+    rng = np.random.default_rng([seed, 1])
+    yaw = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    xy = rng.uniform(1.0, 9.0, size=(n, 2))
+    h = rng.uniform(height[0], height[1], size=n) if height[1] > height[0] else \
+        np.full(n, float(height[0]))
+    vm = np.stack([viewmat_from_pose((xy[i, 0], xy[i, 1], h[i]), yaw[i]) for i in range(n)])
+    intr = np.tile(np.array([focal, focal, W / 2.0, H / 2.0]), (n, 1))
+    return vm.astype(np.float32), intr.astype(np.float32)
+
+
+# --------------------------------------------------------------- workloads
+# small: 1 scene of 20,000 Gaussians, SH degree 0, 8 cameras at 160x120,
+#        f = 120, camera height 0.5 m.
+# full:  1 scene of 1,000,000 Gaussians, SH degree 3, 1,024 cameras at
+#        640x480, f = 480, camera height uniform in [0.3, 1.2] m.
+
+WORKLOADS = {
+    "small_20k_8cam_160x120": dict(n=20_000, deg=0, cams=8, W=160, H=120, f=120.0,
+                                   height=(0.5, 0.5)),
+    "single_1m_sh3_1024cam_640x480": dict(n=1_000_000, deg=3, cams=1024, W=640, H=480,
+                                          f=480.0, height=(0.3, 1.2)),
+}
+
+
+def workload(name: str, seed: int = 0, n_cams: int | None = None):
+    """(scene, viewmats, intrinsics, W, H) of a named workload."""
+    w = WORKLOADS[name]
+    scene = make_scene(w["n"], w["deg"], seed)
+    vm, it = make_cameras(n_cams or w["cams"], w["W"], w["H"], w["f"], w["height"], seed)
+    return scene, vm, it, w["W"], w["H"]
