@@ -1,0 +1,285 @@
+"""Benchmark: 640x480 camera frames/s of batched 3DGS rendering on B300.
+
+Workload (default): one scene of 1,000,000 Gaussians (SH degree 3) and a
+1,024-camera batch at 640x480 (f = 480, robot cameras 0.3-1.2 m high); one
+step = one gs_render_batch call over the whole batch (projection + SH + cull,
+depth sort, tile binning, compositing of RGB and depth). Synthetic seeded
+inputs shaped like the paper's workload (thousands of robots at 640x480);
+the scene (236 MB) and the outputs (5 GB per step) are larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank renders its own
+1,024 cameras (weak scaling, no collective on the data path); value is the
+frames of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "640x480 camera frames/s, 4096-cam batch; upsampled vs plain at >=35 dB PSNR"
+UNIT = "frames/s"
+WORKLOAD = "single_1m_sh3_1024cam_640x480"
+# algorithmic FP32 operations of the compositing step per (pixel, Gaussian) pair,
+# counting an FMA as 2 and comparisons as 0:
+#   every evaluated pair: dx, dy (2), b'dy (1), c'dy^2 + log2(o) (3),
+#     a'dx + b'dy (2), (..)dx + (..) (2)                                   -> 10
+#   pairs with alpha >= alpha_min, additionally: min (1), 1 - alpha (1),
+#     T' = T(1-alpha) (1), w = alpha T (1), rgb + depth accumulation 4 FMA (8) -> 12
+#   the exp2 is a MUFU (SFU) op and is not counted here.
+F_EVAL, F_ALPHA = 10, 12
+# FP32 peak of one B300: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz max clock
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=8):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample
+    of the same workload (the first cameras of the batch)."""
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    orc = oracle.get()
+    t0 = time.perf_counter()
+    done = 0
+    while done < max_cams and (time.perf_counter() - t0) < budget_s:
+        orc.render(scene, vm[done], it[done], W, H)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{done} of {len(vm)} cameras (cameras 0..{done - 1}), full 640x480 "
+                      f"frames, {dt:.1f} s of CPU work"}
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    from paper_2510_15352_b300 import synth
+    scene, vm, it, W, H = synth.workload(WORKLOAD, seed=0)
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    orc = oracle.get()
+    for s in range(args.warmup):
+        orc.render(scene, vm[s % len(vm)], it[s % len(vm)], W, H)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        c = (args.warmup + s) % len(vm)
+        orc.render(scene, vm[c], it[c], W, H)
+    dt = time.perf_counter() - t0
+    fps = args.steps / dt
+    sample = (f"each step renders 1 of the {len(vm)} cameras (full 640x480 frame) of the "
+              f"workload, cameras {args.warmup}..{args.warmup + args.steps - 1}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "cameras": len(vm), "width": W,
+                                        "height": H, "gaussians": 1_000_000, "sh_degree": 3},
+        "cpu_baseline": {"value": fps, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_b300(args):
+    import numpy as np
+    import torch
+    rank, local, world = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2510_15352_b300 import gs, synth
+    scene, vm, it, W, H = synth.workload(WORKLOAD, seed=rank, n_cams=args.cams)
+    n = len(vm)
+    vm_d = torch.from_numpy(vm).cuda()
+    it_d = torch.from_numpy(it).cuda()
+    rgb = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
+    depth = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+
+    # algorithmic work of the compositing kernel on these inputs (counting run)
+    counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk)
+    sid_c = counter.add_scene(scene)
+    counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
+    torch.cuda.synchronize()
+    cst = counter.stats()
+    counter.close()
+    flops_per_step = F_EVAL * cst["pairs_evaluated"] + F_ALPHA * cst["pairs_alpha"]
+
+    R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk)
+    sid = R.add_scene(scene)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        R.render(sid, vm_d, it_d, W, H, rgb, depth, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ms_comp, n_chunks = 0.0, 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        st = R.stats()  # waits for this step's stage events
+        ms_comp += st["ms_composite"]
+        n_chunks += st["n_chunks"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    frames = n * world * args.steps
+    value = frames / (t_max / 1e3)
+    launches = 6 * n_chunks
+
+    # end to end: host cameras in, host frames out, through the host entry point
+    e2e = None
+    if args.e2e_steps > 0:
+        hvm = torch.from_numpy(vm).pin_memory()
+        hit = torch.from_numpy(it).pin_memory()
+        hrgb = torch.empty((n, H, W, 3), dtype=torch.float32).pin_memory()
+        hdep = torch.empty((n, H, W), dtype=torch.float32).pin_memory()
+        R.render_host(sid, hvm, hit, W, H, hrgb, hdep)  # warm the staging buffers
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            R.render_host(sid, hvm, hit, W, H, hrgb, hdep)
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": n * world * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(hvm.numel() * 4 + hit.numel() * 4),
+               "d2h_bytes_per_step": int(hrgb.numel() * 4 + hdep.numel() * 4)}
+
+    if rank == 0:
+        comp_ms_per_launch = ms_comp / max(n_chunks, 1)
+        achieved = flops_per_step / (ms_comp / args.steps / 1e3) / 1e12 if ms_comp else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cameras_per_gpu": n, "width": W, "height": H,
+                       "gaussians": 1_000_000, "sh_degree": 3, "chunk_cameras": args.chunk,
+                       "l2": "inputs larger than L2 (scene 236 MB; 5 GB of outputs per step)"},
+            "roofline": {
+                "kernel": "k_composite", "bound": "alu", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": None,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
+                "ms_per_launch": comp_ms_per_launch,
+                "launches_per_step": n_chunks / args.steps,
+                "composite_share_of_step": ms_comp / t_max,
+                "pairs_evaluated_per_step": cst["pairs_evaluated"],
+                "pairs_alpha_per_step": cst["pairs_alpha"],
+            },
+            "stats": {"survivors_per_step": cst["survivors"],
+                      "intersections_per_step": cst["intersections"]},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(scene, vm, it, W, H)
+        print(json.dumps(out), flush=True)
+    R.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
+    ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 1024)")
+    ap.add_argument("--chunk", type=int, default=256, help="cameras per internal chunk")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_b300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * gs.h -- C ABI of the B300-native batched 3D Gaussian Splatting renderer.
+ *
+ * The library renders, for a batch of cameras (one per simulated robot), every
+ * camera's view of its scene of 3D Gaussians and returns colour and expected
+ * depth. This is the renderer the paper drops into its vectorised simulator
+ * (Sec. 3.2 "3D Gaussian Splatting as a Drop-in Renderer"), with depth as a
+ * by-product of the same compositing pass (Sec. 3.3, Fig. 4), rendering many
+ * robots over many scenes on one GPU (Sec. 3.3: 4,096 environments over 128
+ * scenes at 640x480). The rasteriser itself is the 3DGS method the paper cites
+ * (Sec. 2.3): EWA projection with a 0.3 px dilation, SH colour, 3-sigma tile
+ * culling, 16x16 tiles, per-tile order by (depth, Gaussian index), front-to-back
+ * compositing with alpha = min(0.99, o exp(-d^T Sigma'^-1 d / 2)), alpha < 1/255
+ * skipped, and a pixel stops before its transmittance would fall below 1e-4.
+ *
+ * Conventions (all calls):
+ *  - Pointers are plain host or device addresses as stated per argument; no
+ *    framework types cross this boundary. `stream` is a cudaStream_t passed as
+ *    void* (NULL = the legacy default stream).
+ *  - Every call returns a gs_status; nothing throws. On failure the outputs of
+ *    that call are unspecified and gs_last_error() holds a one-line reason.
+ *  - A context belongs to one device and one host thread at a time.
+ *  - Cameras: `viewmats` are row-major 4x4 world->camera matrices (OpenCV axes:
+ *    x right, y down, z forward); `intrinsics` are (fx, fy, cx, cy) in pixels;
+ *    pixel (i, j) has its centre at (i + 0.5, j + 0.5).
+ *  - Outputs: rgb is [n][H][W][3] float32, depth [n][H][W] float32 (expected
+ *    depth sum_i w_i z_i of the camera-space depths, not normalised, 0 where
+ *    nothing is drawn), final_T [n][H][W] float32 (the transmittance left).
+ */
+#ifndef GS_B300_H
+#define GS_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* bad pointer, size, id or configuration */
+    GS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in gs_last_error) */
+    GS_ERR_OOM = 3,         /* device or pinned host allocation failed */
+    GS_ERR_CAPACITY = 4,    /* a request exceeds a fixed limit of the library */
+    GS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    GS_ERR_NOT_FOUND = 6    /* unknown scene id */
+} gs_status;
+
+typedef enum gs_dtype { GS_F32 = 0, GS_F16 = 1, GS_BF16 = 2 } gs_dtype;
+typedef enum gs_memory { GS_MEM_HOST = 0, GS_MEM_DEVICE = 1 } gs_memory;
+
+/* Rendering constants and resource limits. gs_config_default() fills the
+ * rasteriser's standard constants; the oracle uses the same values. */
+typedef struct gs_config {
+    float near_plane;      /* cull Gaussians whose camera-space z <= this (0.2) */
+    float dilation;        /* added to the 2D covariance diagonal, px^2 (0.3) */
+    float guard_band;      /* Jacobian clamp: x/z limited to guard*(W/2)/fx around the
+                              principal point (1.3) */
+    float sigma_cull;      /* footprint radius in standard deviations (3) */
+    float alpha_min;       /* a pair with alpha below this is skipped (1/255) */
+    float alpha_max;       /* alpha is clamped to this (0.99) */
+    float T_min;           /* a pixel stops before T would fall below this (1e-4) */
+    float background[3];   /* added as T * background to rgb (0, 0, 0) */
+    int32_t max_chunk_cameras; /* cameras rendered per internal chunk (256) */
+    int32_t camera_group;  /* cameras of one scene that share one Gaussian load in the
+                              projection kernel (32, at most 32) */
+    int32_t count_pairs;   /* 1: the compositing kernel also counts evaluated pairs
+                              (a slower variant of the kernel) */
+    int32_t time_stages;   /* 1: record CUDA events around every stage on the render
+                              stream; gs_get_stats reports the per-stage device time */
+    int32_t reserved[8];
+} gs_config;
+
+/* A scene: n Gaussians stored as structure of arrays.
+ * mean [3][n] (x row, y row, z row), log_scale [3][n], quat [4][n] (w, x, y, z;
+ * normalised by the renderer), logit_opacity [n], sh [K][3][n] with
+ * K = (sh_degree+1)^2 (coefficient-major, l-major with m = -l..l, then the
+ * channel, then the Gaussian; real SH basis with the Condon-Shortley phase).
+ * geometry_dtype applies to mean, log_scale and quat; appearance_dtype to
+ * logit_opacity and sh. memory says whether all five pointers are host or
+ * device addresses. */
+typedef struct gs_scene_desc {
+    int64_t n;
+    int32_t sh_degree;        /* 0..3 */
+    int32_t geometry_dtype;   /* gs_dtype */
+    int32_t appearance_dtype; /* gs_dtype */
+    int32_t memory;           /* gs_memory */
+    const void *mean;
+    const void *log_scale;
+    const void *quat;
+    const void *logit_opacity;
+    const void *sh;
+} gs_scene_desc;
+
+/* Counters of the last render call. */
+typedef struct gs_stats {
+    int64_t n_cameras;
+    int64_t survivors;       /* sum over cameras of Gaussians that survive culling */
+    int64_t intersections;   /* sum over cameras of (survivor, covered tile) pairs */
+    int64_t pairs_evaluated; /* (pixel, Gaussian) pairs whose alpha was computed before
+                                the pixel stopped; only with count_pairs */
+    int64_t pairs_alpha;     /* of those, pairs with alpha >= alpha_min; count_pairs */
+    int32_t n_chunks;
+    float ms_project;        /* per-stage device time summed over chunks, time_stages */
+    float ms_sort;
+    float ms_bin;
+    float ms_composite;
+    float ms_total;
+    int32_t reserved[4];
+} gs_stats;
+
+typedef struct gs_context gs_context;
+
+/* Library ABI version (changes when a struct layout or signature changes). */
+int32_t gs_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *gs_status_string(gs_status s);
+
+/* Fill *out with the default constants and limits. */
+gs_status gs_config_default(gs_config *out);
+
+/* Create a context on CUDA device `device` (cfg NULL = defaults). The context
+ * owns scene storage and the render workspace. *out is NULL on failure. */
+gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **out);
+
+/* Free a context and everything it owns (NULL is a no-op). Waits for its work. */
+void gs_context_destroy(gs_context *ctx);
+
+/* Last error message of this context (never NULL; "" after success). */
+const char *gs_last_error(gs_context *ctx);
+
+/* Copy a scene into the context (the caller keeps ownership of its arrays).
+ * The copy is done before the call returns. *scene_id stays valid until
+ * gs_scene_destroy. Errors: INVALID_ARG (n < 0, degree or dtype out of range,
+ * NULL pointer with n > 0), OOM, CUDA. */
+gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *desc, int32_t *scene_id);
+
+/* Release a scene's storage. Errors: NOT_FOUND. */
+gs_status gs_scene_destroy(gs_context *ctx, int32_t scene_id);
+
+/* Render n_cams cameras of size width x height.
+ *   scene_ids   HOST   [n_cams] scene of each camera (the library groups cameras
+ *                      by scene so one Gaussian load serves many cameras)
+ *   viewmats    DEVICE [n_cams][16] float32, row-major world->camera
+ *   intrinsics  DEVICE [n_cams][4]  float32 (fx, fy, cx, cy)
+ *   rgb         DEVICE [n_cams][height][width][3] float32, written
+ *   depth       DEVICE [n_cams][height][width] float32, written
+ *   final_T     DEVICE [n_cams][height][width] float32 or NULL
+ * Work is enqueued on `stream`; the call also synchronises that stream once
+ * per chunk of cameras (to size the workspace exactly), so when it returns
+ * GS_OK every chunk but the last has completed and the last is enqueued.
+ * Output buffers must not overlap the inputs. n_cams == 0 is a no-op.
+ * Errors: INVALID_ARG, NOT_FOUND, CAPACITY (more than 7000 tiles per camera),
+ * OOM, CUDA. */
+gs_status gs_render_batch(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                          const float *viewmats, const float *intrinsics, int32_t width,
+                          int32_t height, float *rgb, float *depth, float *final_T,
+                          void *stream);
+
+/* Same as gs_render_batch with every array in HOST memory: the call copies the
+ * cameras to the device, renders into context-owned device buffers and copies
+ * the outputs back (pinned host buffers make the copies asynchronous DMA).
+ * Returns after the outputs are in host memory. */
+gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                               const float *viewmats, const float *intrinsics, int32_t width,
+                               int32_t height, float *rgb, float *depth, float *final_T,
+                               void *stream);
+
+/* Counters (and stage times with time_stages) of the last render call. Waits for
+ * the last call's work when its counters or times are still on the device. */
+gs_status gs_get_stats(gs_context *ctx, gs_stats *out);
+
+/* ---------------------------------------------------------------------------
+ * Inspection entry points (used by the test suite). Each runs the hot-path
+ * kernels for ONE camera (viewmat / intrinsics in DEVICE memory) and copies an
+ * intermediate result to HOST buffers. They synchronise `stream`.
+ * ------------------------------------------------------------------------- */
+
+/* Projected records of the camera's surviving Gaussians, in Gaussian-index
+ * order. rec: HOST [cap][12] float32 = (u, v, z, opacity, A, B, C, r, red,
+ * green, blue, 0) with (A, B, C) the conic (inverse 2D covariance entries
+ * [[A, B], [B, C]]) and r the footprint radius in pixels; gidx: HOST [cap]
+ * Gaussian indices; rect: HOST [cap][4] tile rect (x0, x1, y0, y1, inclusive).
+ * *n_out receives the survivor count; CAPACITY if it exceeds cap (nothing is
+ * copied then). */
+gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewmat,
+                           const float *intrinsics, int32_t width, int32_t height, float *rec,
+                           int32_t *gidx, int32_t *rect, int64_t cap, int64_t *n_out,
+                           void *stream);
+
+/* Per-tile Gaussian lists of the camera in compositing order (depth, index).
+ * tile_off: HOST [ntiles+1] list offsets (ntiles = ceil(W/16) * ceil(H/16),
+ * tiles row-major); gidx: HOST [cap] Gaussian indices. *n_out receives the
+ * number of entries; CAPACITY if it exceeds cap (tile_off is still filled). */
+gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *viewmat,
+                              const float *intrinsics, int32_t width, int32_t height,
+                              int64_t *tile_off, int32_t *gidx, int64_t cap, int64_t *n_out,
+                              void *stream);
+
+/* The hot path's segmented sort on caller data: within each segment
+ * [seg_start[s], seg_start[s] + seg_count[s]) of keys/vals, a stable ascending
+ * sort of the uint32 keys, vals moved with their keys, in place.
+ * keys, vals: DEVICE [n] uint32; seg_start, seg_count: DEVICE [n_seg] int64,
+ * segments must not overlap and lie within [0, n). Scratch (2 n uint32) comes
+ * from the context's workspace. */
+gs_status gs_sort_segments(gs_context *ctx, uint32_t *keys, uint32_t *vals, int64_t n,
+                           const int64_t *seg_start, const int64_t *seg_count, int32_t n_seg,
+                           void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_B300_H */

@@ -1,0 +1,113 @@
+// gs_internal.cuh -- data layouts and launchers shared by the kernel files of
+// the batched 3DGS renderer (sm_103a). Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gsk {
+
+constexpr int TILE = 16;            // tile edge in pixels
+constexpr int MAX_GROUP = 32;       // cameras sharing one Gaussian load (<= warp size)
+constexpr int PROJ_THREADS = 256;   // Gaussians per projection block (8 mask words)
+constexpr int BIN_RANKS = 256;      // depth ranks per binning block
+constexpr int BIN_WORDS = BIN_RANKS / 32;
+constexpr int MAX_TILES = 7000;     // tiles per camera (binning smem: 32 B per tile)
+constexpr int COMP_THREADS = 128;   // compositing block: 16x16 tile, 2 pixels per thread
+constexpr int COMP_WORDS = 128;     // bitmap words read per compositing round
+constexpr int COMP_BATCH = 128;     // Gaussian records staged per compositing sub-batch
+constexpr int SORT_THREADS = 512;
+constexpr int SORT_IPT = 8;         // keys per thread per sort tile
+
+enum : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
+
+// Projection constants of a render call.
+struct ProjParams {
+    float near_plane, dilation, guard, sigma;
+};
+
+// Compositing constants of a render call.
+struct CompParams {
+    float log2_alpha_min;  // log2(alpha_min): alpha test done on log2(o e^power)
+    float alpha_max, T_min;
+    float bg[3];
+};
+
+// A scene resident in device memory (structure of arrays, see gs.h).
+struct SceneDev {
+    const void *mean, *log_scale, *quat, *logit, *sh;
+    long long n;
+    int deg, geo_dtype, app_dtype, pad;
+};
+
+// One camera of a chunk (a "slot"); offsets index the chunk's workspace arrays.
+struct CamInfo {
+    int user;        // index into viewmats / intrinsics / outputs
+    int scene;       // index into the scene table
+    int W, H;
+    int TX, TY;
+    int tile_off;    // first tile of this camera in the chunk's tile numbering
+    int count;       // surviving Gaussians (after the scan)
+    long long mask_off;  // first survival-mask word
+    long long seg_off;   // first survivor slot
+    long long bm_off;    // first tile-bitmap word
+    int nw;          // bitmap words per tile row = ceil(count / 32)
+    int pad;
+};
+
+// Cameras of one scene that share a projection block's Gaussian loads.
+struct Group {
+    int scene, slot0, ncam, pad;
+    long long n;
+};
+
+// A survivor's record in Gaussian-index order (64 B).
+//   a: u, v, z, opacity   b: A, B, C, r (conic + radius)   c: red, green, blue, 0
+//   d: x0 | x1 << 16, y0 | y1 << 16, Gaussian index, 0
+struct __align__(16) SlotRec {
+    float4 a, b, c;
+    uint4 d;
+};
+
+// A survivor's compositing record in depth-rank order (48 B), with the
+// constants folded so that  p = a'dx^2 + b'dx dy + c'dy^2 + log2(o)  is
+// log2(o e^power):
+//   a: u, v, a' = -log2(e)/2 A, b' = -log2(e) B
+//   b: c' = -log2(e)/2 C, log2(o), z, 0      c: red, green, blue, 0
+struct __align__(16) CRec {
+    float4 a, b, c;
+};
+
+// ---- launchers (each defined in its kernel file) ----
+
+cudaError_t launch_project_mask(const Group *groups, int n_groups, int max_blocks_x,
+                                const SceneDev *scenes, const CamInfo *cams,
+                                const float *viewmats, const float *intr, ProjParams P,
+                                uint32_t *masks, cudaStream_t s);
+
+cudaError_t launch_scan_masks(const CamInfo *cams, const SceneDev *scenes, int n_slots,
+                              const uint32_t *masks, uint32_t *woff, int *counts,
+                              cudaStream_t s);
+
+cudaError_t launch_project_write(const Group *groups, int n_groups, int max_blocks_x,
+                                 const SceneDev *scenes, const CamInfo *cams,
+                                 const float *viewmats, const float *intr, ProjParams P,
+                                 const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
+                                 uint32_t *keys, uint32_t *vals, cudaStream_t s);
+
+cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
+                                 uint32_t *tmp_vals, const long long *seg_start,
+                                 const long long *seg_count, int n_seg, cudaStream_t s);
+
+cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
+                       int max_tiles, const SlotRec *rec, const uint32_t *vals, CRec *crec,
+                       uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);
+
+cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
+                             int n_tiles, const CRec *crec, const uint32_t *bitmap,
+                             CompParams C, float *rgb, float *depth, float *final_T,
+                             unsigned long long *stats, bool collect, cudaStream_t s);
+
+}  // namespace gsk

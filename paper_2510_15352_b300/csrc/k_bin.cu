@@ -1,0 +1,89 @@
+// k_bin.cu -- tile binning of depth-sorted survivors: the stable counting sort
+// on the tile digit that completes the (camera, tile, depth, index) order of
+// the 3DGS renderer (Sec. 3.2 of the paper uses that renderer).
+//
+// Representation: for camera c with S_c survivors in depth-rank order, tile t
+// owns a bitmap row of ceil(S_c/32) words; bit r is set when the survivor of
+// rank r covers the tile. Reading a row's set bits in increasing order yields
+// exactly the tile's list in (depth, index) order, so no per-intersection key,
+// global scan or second sort is needed, and every word is written once.
+//
+// A block takes 256 consecutive ranks of one camera: it builds the 8 words of
+// that rank column for every tile of the camera in shared memory (32 B per
+// tile), then writes them out as 32-byte segments. The same pass copies each
+// survivor's record into rank order with the compositing constants folded in.
+#include "gs_internal.cuh"
+
+namespace gsk {
+
+namespace {
+
+constexpr float LOG2E = 1.4426950408889634f;
+
+__global__ void __launch_bounds__(BIN_RANKS)
+    k_bin(const CamInfo *__restrict__ cams, const int *__restrict__ blk_prefix, int n_slots,
+          const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
+          CRec *__restrict__ crec, uint32_t *__restrict__ bitmap,
+          unsigned long long *__restrict__ n_isect) {
+    extern __shared__ uint32_t sbm[];  // [tiles][BIN_WORDS]
+    int lo = 0, hi = n_slots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk_prefix[mid] <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const CamInfo ci = cams[lo];
+    const int r0 = ((int)blockIdx.x - blk_prefix[lo]) * BIN_RANKS;
+    const int tiles = ci.TX * ci.TY;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < tiles * BIN_WORDS; i += BIN_RANKS) sbm[i] = 0u;
+    __syncthreads();
+    const int r = r0 + tid;
+    unsigned long long area = 0;
+    if (r < ci.count) {
+        const uint32_t slot = vals[ci.seg_off + r];
+        const SlotRec R = rec[ci.seg_off + slot];
+        CRec C;
+        C.a = make_float4(R.a.x, R.a.y, -0.5f * LOG2E * R.b.x, -LOG2E * R.b.y);
+        C.b = make_float4(-0.5f * LOG2E * R.b.z, log2f(R.a.w), R.a.z, 0.0f);
+        C.c = R.c;
+        crec[ci.seg_off + r] = C;
+        const int x0 = (int)(R.d.x & 0xffffu), x1 = (int)(R.d.x >> 16);
+        const int y0 = (int)(R.d.y & 0xffffu), y1 = (int)(R.d.y >> 16);
+        const uint32_t bit = 1u << (tid & 31);
+        const int word = tid >> 5;
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx)
+                atomicOr(&sbm[(ty * ci.TX + tx) * BIN_WORDS + word], bit);
+        if (x1 >= x0 && y1 >= y0) area = (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
+    }
+    __syncthreads();
+    const int w0 = r0 >> 5;
+    const int nwb = min(BIN_WORDS, ci.nw - w0);
+    for (int i = tid; i < tiles * BIN_WORDS; i += BIN_RANKS) {
+        const int t = i / BIN_WORDS, k = i - t * BIN_WORDS;
+        if (k < nwb) bitmap[ci.bm_off + (long long)t * ci.nw + w0 + k] = sbm[i];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) area += __shfl_down_sync(0xffffffffu, area, d);
+    if ((tid & 31) == 0 && area) atomicAdd(n_isect, area);
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
+                       int max_tiles, const SlotRec *rec, const uint32_t *vals, CRec *crec,
+                       uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s) {
+    if (n_blocks == 0) return cudaSuccess;
+    const size_t smem = (size_t)max_tiles * BIN_WORDS * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_bin<<<n_blocks, BIN_RANKS, smem, s>>>(cams, blk_prefix, n_slots, rec, vals, crec, bitmap,
+                                            n_isect);
+    return cudaGetLastError();
+}
+
+}  // namespace gsk

@@ -1,0 +1,399 @@
+// k_project.cu -- projection, SH colour and culling of Gaussians for a batch of
+// cameras (the EWA splatting step of the 3DGS renderer the paper uses, Sec. 3.2).
+//
+// Layout of the work: a block holds 256 consecutive Gaussians of one scene and
+// loops over a group of up to 32 cameras of that scene, so each Gaussian's
+// attributes are read from HBM once per camera group instead of once per
+// camera. Attribute loads are structure-of-arrays: consecutive threads read
+// consecutive addresses of each attribute row.
+//
+// Two passes keep the survivor order deterministic (Gaussian-index order)
+// without a global sort key that carries the index:
+//   k_project_mask  -- survival bit per (camera, Gaussian), one warp ballot per
+//                      32 Gaussians -> a 32-bit mask word;
+//   k_scan_masks    -- per camera, exclusive prefix of the mask popcounts;
+//   k_project_write -- recomputes the projection for surviving pairs only,
+//                      evaluates SH colour and writes the record, the depth key
+//                      (float bits of z) and the slot at a stable position.
+// The decision chain is written with explicit fmaf / *_rn intrinsics so both
+// passes round identically.
+#include "gs_internal.cuh"
+
+namespace gsk {
+
+namespace {
+
+struct CamProj {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    float lxp, lxn, lyp, lyn;  // guard-band limits of x/z and y/z
+    float cpos[3];             // camera centre in world coordinates
+    float W, H;
+    int TX, TY;
+};
+
+struct GaussGeo {
+    float mx, my, mz;
+    float M[9];  // R(q) diag(exp(log_scale)), row-major
+};
+
+struct Proj {
+    float u, v, z, A, B, C, r;
+    int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ float ldv(const void *p, long long i, int dt) {
+    if (dt == DT_F32) return __ldg(reinterpret_cast<const float *>(p) + i);
+    if (dt == DT_F16) return __half2float(reinterpret_cast<const __half *>(p)[i]);
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i]);
+}
+
+__device__ void cam_setup(CamProj &c, const float *vm, const float *in, int W, int H,
+                          float guard) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c.R[3 * i + j] = vm[4 * i + j];
+        c.t[i] = vm[4 * i + 3];
+    }
+    c.fx = in[0];
+    c.fy = in[1];
+    c.cx = in[2];
+    c.cy = in[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        c.cpos[j] = -(c.R[j] * c.t[0] + c.R[3 + j] * c.t[1] + c.R[6 + j] * c.t[2]);
+    const float g = guard - 1.0f;
+    c.lxp = ((W - c.cx) + g * 0.5f * W) / c.fx;
+    c.lxn = (c.cx + g * 0.5f * W) / c.fx;
+    c.lyp = ((H - c.cy) + g * 0.5f * H) / c.fy;
+    c.lyn = (c.cy + g * 0.5f * H) / c.fy;
+    c.W = (float)W;
+    c.H = (float)H;
+    c.TX = (W + TILE - 1) / TILE;
+    c.TY = (H + TILE - 1) / TILE;
+}
+
+// Mean and M = R(q) S of Gaussian g (quaternion normalised here).
+__device__ __forceinline__ void load_geo(const SceneDev &s, long long g, GaussGeo &G) {
+    const long long n = s.n;
+    const int dt = s.geo_dtype;
+    G.mx = ldv(s.mean, g, dt);
+    G.my = ldv(s.mean, n + g, dt);
+    G.mz = ldv(s.mean, 2 * n + g, dt);
+    const float sx = expf(ldv(s.log_scale, g, dt));
+    const float sy = expf(ldv(s.log_scale, n + g, dt));
+    const float sz = expf(ldv(s.log_scale, 2 * n + g, dt));
+    float w = ldv(s.quat, g, dt), x = ldv(s.quat, n + g, dt);
+    float y = ldv(s.quat, 2 * n + g, dt), z = ldv(s.quat, 3 * n + g, dt);
+    const float qq = w * w + x * x + y * y + z * z;
+    if (qq > 0.0f) {
+        const float inv = 1.0f / sqrtf(qq);
+        w *= inv;
+        x *= inv;
+        y *= inv;
+        z *= inv;
+    } else {
+        w = 1.0f;
+        x = y = z = 0.0f;
+    }
+    G.M[0] = (1.0f - 2.0f * (y * y + z * z)) * sx;
+    G.M[1] = 2.0f * (x * y - w * z) * sy;
+    G.M[2] = 2.0f * (x * z + w * y) * sz;
+    G.M[3] = 2.0f * (x * y + w * z) * sx;
+    G.M[4] = (1.0f - 2.0f * (x * x + z * z)) * sy;
+    G.M[5] = 2.0f * (y * z - w * x) * sz;
+    G.M[6] = 2.0f * (x * z - w * y) * sx;
+    G.M[7] = 2.0f * (y * z + w * x) * sy;
+    G.M[8] = (1.0f - 2.0f * (x * x + y * y)) * sz;
+}
+
+// EWA projection of one Gaussian for one camera. Returns false when culled
+// (near plane, off image, non-finite). With G = J R_c M (2x3) the 2D covariance
+// is G G^T + dil I; its determinant is computed as |G0 x G1|^2 + dil tr + dil^2
+// (Cauchy-Binet), which has no cancellation, and lambda_max as
+// mid + sqrt(((a-c)/2)^2 + b^2), equal to the textbook mid + sqrt(mid^2 - det).
+__device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
+                                        const ProjParams &P, Proj &o) {
+    const float px = fmaf(c.R[0], G.mx, fmaf(c.R[1], G.my, fmaf(c.R[2], G.mz, c.t[0])));
+    const float py = fmaf(c.R[3], G.mx, fmaf(c.R[4], G.my, fmaf(c.R[5], G.mz, c.t[1])));
+    const float z = fmaf(c.R[6], G.mx, fmaf(c.R[7], G.my, fmaf(c.R[8], G.mz, c.t[2])));
+    o.z = z;
+    if (!(z > P.near_plane)) return false;
+    const float iz = __fdiv_rn(1.0f, z);
+    const float xz = __fmul_rn(px, iz), yz = __fmul_rn(py, iz);
+    const float xc = fminf(fmaxf(xz, -c.lxn), c.lxp);
+    const float yc = fminf(fmaxf(yz, -c.lyn), c.lyp);
+    const float j00 = __fmul_rn(c.fx, iz), j02 = -__fmul_rn(__fmul_rn(c.fx, xc), iz);
+    const float j11 = __fmul_rn(c.fy, iz), j12 = -__fmul_rn(__fmul_rn(c.fy, yc), iz);
+    float T0[3], T1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        T0[k] = fmaf(j00, c.R[k], __fmul_rn(j02, c.R[6 + k]));
+        T1[k] = fmaf(j11, c.R[3 + k], __fmul_rn(j12, c.R[6 + k]));
+    }
+    float g0[3], g1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g0[k] = fmaf(T0[0], G.M[k], fmaf(T0[1], G.M[3 + k], __fmul_rn(T0[2], G.M[6 + k])));
+        g1[k] = fmaf(T1[0], G.M[k], fmaf(T1[1], G.M[3 + k], __fmul_rn(T1[2], G.M[6 + k])));
+    }
+    const float s00 = fmaf(g0[0], g0[0], fmaf(g0[1], g0[1], __fmul_rn(g0[2], g0[2])));
+    const float s11 = fmaf(g1[0], g1[0], fmaf(g1[1], g1[1], __fmul_rn(g1[2], g1[2])));
+    const float s01 = fmaf(g0[0], g1[0], fmaf(g0[1], g1[1], __fmul_rn(g0[2], g1[2])));
+    const float dil = P.dilation;
+    const float a = __fadd_rn(s00, dil), cc = __fadd_rn(s11, dil), b = s01;
+    const float hd = __fmul_rn(0.5f, __fsub_rn(a, cc));
+    const float lmax = fmaf(0.5f, __fadd_rn(a, cc), __fsqrt_rn(fmaf(hd, hd, __fmul_rn(b, b))));
+    const float r = __fmul_rn(P.sigma, __fsqrt_rn(lmax));
+    const float u = fmaf(c.fx, xz, c.cx), v = fmaf(c.fy, yz, c.cy);
+    if (!(__fadd_rn(u, r) >= 0.0f) || !(__fsub_rn(u, r) < c.W) || !(__fadd_rn(v, r) >= 0.0f) ||
+        !(__fsub_rn(v, r) < c.H))
+        return false;
+    o.x0 = (int)fmaxf(floorf(__fmul_rn(__fsub_rn(u, r), 0.0625f)), 0.0f);
+    o.x1 = (int)fminf(floorf(__fmul_rn(__fadd_rn(u, r), 0.0625f)), (float)(c.TX - 1));
+    o.y0 = (int)fmaxf(floorf(__fmul_rn(__fsub_rn(v, r), 0.0625f)), 0.0f);
+    o.y1 = (int)fminf(floorf(__fmul_rn(__fadd_rn(v, r), 0.0625f)), (float)(c.TY - 1));
+    // conic: only the write pass uses it
+    const float e0 = fmaf(g0[1], g1[2], -__fmul_rn(g0[2], g1[1]));
+    const float e1 = fmaf(g0[2], g1[0], -__fmul_rn(g0[0], g1[2]));
+    const float e2 = fmaf(g0[0], g1[1], -__fmul_rn(g0[1], g1[0]));
+    const float det = fmaf(dil, __fadd_rn(__fadd_rn(s00, s11), dil),
+                           fmaf(e0, e0, fmaf(e1, e1, __fmul_rn(e2, e2))));
+    const float idet = __fdiv_rn(1.0f, det);
+    o.A = cc * idet;
+    o.B = -b * idet;
+    o.C = a * idet;
+    o.u = u;
+    o.v = v;
+    o.r = r;
+    return true;
+}
+
+// Real SH basis (Condon-Shortley phase), l-major with m = -l..l, constants
+// written as their closed forms sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the
+// factors of the Cartesian polynomials.
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *Y) {
+    Y[0] = 0.28209479177387814f;  // 1/(2 sqrt(pi))
+    if (deg >= 1) {
+        const float c1 = 0.4886025119029199f;  // sqrt(3/(4 pi))
+        Y[1] = -c1 * y;
+        Y[2] = c1 * z;
+        Y[3] = -c1 * x;
+    }
+    if (deg >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;           // sqrt(15/(4 pi))
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);  // sqrt(5/(16 pi))
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);       // sqrt(15/(16 pi))
+        if (deg >= 3) {
+            Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);   // sqrt(35/(32 pi))
+            Y[10] = 2.890611442640554f * x * y * z;              // sqrt(105/(4 pi))
+            Y[11] = -0.4570457994644658f * y * (5.0f * zz - 1.0f);  // sqrt(21/(32 pi))
+            Y[12] = 0.3731763325901154f * z * (5.0f * zz - 3.0f);   // sqrt(7/(16 pi))
+            Y[13] = -0.4570457994644658f * x * (5.0f * zz - 1.0f);
+            Y[14] = 1.445305721320277f * z * (xx - yy);          // sqrt(105/(16 pi))
+            Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+__device__ __forceinline__ void sh_colour(const SceneDev &s, long long g, const CamProj &c,
+                                          const GaussGeo &G, float rgb[3]) {
+    const int K = (s.deg + 1) * (s.deg + 1);
+    float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
+    const float dd = dx * dx + dy * dy + dz * dz;
+    if (dd > 0.0f) {
+        const float inv = 1.0f / sqrtf(dd);
+        dx *= inv;
+        dy *= inv;
+        dz *= inv;
+    } else {
+        dx = 0.0f;
+        dy = 0.0f;
+        dz = 1.0f;
+    }
+    float Y[16];
+    sh_basis(s.deg, dx, dy, dz, Y);
+    const long long n = s.n;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < K) acc = fmaf(ldv(s.sh, (3LL * k + ch) * n + g, s.app_dtype), Y[k], acc);
+        rgb[ch] = fmaxf(acc, 0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(PROJ_THREADS)
+    k_project_mask(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
+                   const CamInfo *__restrict__ cams, const float *__restrict__ vms,
+                   const float *__restrict__ intr, ProjParams P, uint32_t *__restrict__ masks) {
+    const Group gr = groups[blockIdx.y];
+    const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
+    if (g0 >= gr.n) return;
+    __shared__ CamProj cp[MAX_GROUP];
+    __shared__ long long moff[MAX_GROUP];
+    if ((int)threadIdx.x < gr.ncam) {
+        const CamInfo ci = cams[gr.slot0 + threadIdx.x];
+        cam_setup(cp[threadIdx.x], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H,
+                  P.guard);
+        moff[threadIdx.x] = ci.mask_off;
+    }
+    __syncthreads();
+    const SceneDev sc = scenes[gr.scene];
+    const long long g = g0 + threadIdx.x;
+    const bool valid = g < gr.n;
+    const int lane = threadIdx.x & 31;
+    const bool warp_live = (g - lane) < gr.n;
+    GaussGeo G;
+    if (valid) load_geo(sc, g, G);
+    for (int c = 0; c < gr.ncam; ++c) {
+        Proj pr;
+        const bool s = valid && project(cp[c], G, P, pr);
+        const unsigned b = __ballot_sync(0xffffffffu, s);
+        if (lane == 0 && warp_live) masks[moff[c] + (g >> 5)] = b;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_scan_masks(const CamInfo *__restrict__ cams, const SceneDev *__restrict__ scenes,
+                 const uint32_t *__restrict__ masks, uint32_t *__restrict__ woff,
+                 int *__restrict__ counts) {
+    const CamInfo ci = cams[blockIdx.x];
+    const long long nwords = (scenes[ci.scene].n + 31) >> 5;
+    const uint32_t *m = masks + ci.mask_off;
+    uint32_t *wo = woff + ci.mask_off;
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < nwords; base += 1024) {
+        const long long i = base + tid;
+        const uint32_t c = i < nwords ? __popc(m[i]) : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t v = wsum[lane];
+            uint32_t s = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, s, d);
+                if (lane >= d) s += t;
+            }
+            wsum[lane] = s - v;  // exclusive prefix of the warp sums
+        }
+        __syncthreads();
+        const uint32_t excl = carry + wsum[warp] + incl - c;
+        if (i < nwords) wo[i] = excl;
+        __syncthreads();
+        if (tid == 1023) carry = excl + c;
+        __syncthreads();
+    }
+    if (tid == 0) counts[blockIdx.x] = (int)carry;
+}
+
+__global__ void __launch_bounds__(PROJ_THREADS)
+    k_project_write(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
+                    const CamInfo *__restrict__ cams, const float *__restrict__ vms,
+                    const float *__restrict__ intr, ProjParams P,
+                    const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
+                    SlotRec *__restrict__ rec, uint32_t *__restrict__ keys,
+                    uint32_t *__restrict__ vals) {
+    const Group gr = groups[blockIdx.y];
+    const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
+    if (g0 >= gr.n) return;
+    __shared__ CamProj cp[MAX_GROUP];
+    __shared__ long long moff[MAX_GROUP], soff[MAX_GROUP];
+    if ((int)threadIdx.x < gr.ncam) {
+        const CamInfo ci = cams[gr.slot0 + threadIdx.x];
+        cam_setup(cp[threadIdx.x], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H,
+                  P.guard);
+        moff[threadIdx.x] = ci.mask_off;
+        soff[threadIdx.x] = ci.seg_off;
+    }
+    __syncthreads();
+    const SceneDev sc = scenes[gr.scene];
+    const long long g = g0 + threadIdx.x;
+    const bool valid = g < gr.n;
+    const int lane = threadIdx.x & 31;
+    const bool warp_live = (g - lane) < gr.n;
+    if (!warp_live) return;  // whole warp past the end: no mask words to read
+    GaussGeo G;
+    float opacity = 0.0f;
+    if (valid) {
+        load_geo(sc, g, G);
+        opacity = 1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype)));
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int c = 0; c < gr.ncam; ++c) {
+        const long long w = moff[c] + (g >> 5);
+        const uint32_t m = masks[w];
+        if (!((m >> lane) & 1u)) continue;
+        Proj pr;
+        if (!project(cp[c], G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
+            pr.x0 = 1;
+            pr.x1 = 0;
+            pr.y0 = 1;
+            pr.y1 = 0;
+            pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = 0.0f;
+        }
+        float rgb[3];
+        sh_colour(sc, g, cp[c], G, rgb);
+        const uint32_t slot = woff[w] + __popc(m & lt);
+        const long long at = soff[c] + slot;
+        SlotRec R;
+        R.a = make_float4(pr.u, pr.v, pr.z, opacity);
+        R.b = make_float4(pr.A, pr.B, pr.C, pr.r);
+        R.c = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+        R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
+                         (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)g, 0u);
+        rec[at] = R;
+        keys[at] = __float_as_uint(pr.z);
+        vals[at] = slot;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_project_mask(const Group *groups, int n_groups, int max_blocks_x,
+                                const SceneDev *scenes, const CamInfo *cams,
+                                const float *viewmats, const float *intr, ProjParams P,
+                                uint32_t *masks, cudaStream_t s) {
+    if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
+    dim3 grid(max_blocks_x, n_groups);
+    k_project_mask<<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, viewmats, intr, P, masks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_masks(const CamInfo *cams, const SceneDev *scenes, int n_slots,
+                              const uint32_t *masks, uint32_t *woff, int *counts,
+                              cudaStream_t s) {
+    if (n_slots == 0) return cudaSuccess;
+    k_scan_masks<<<n_slots, 1024, 0, s>>>(cams, scenes, masks, woff, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_write(const Group *groups, int n_groups, int max_blocks_x,
+                                 const SceneDev *scenes, const CamInfo *cams,
+                                 const float *viewmats, const float *intr, ProjParams P,
+                                 const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
+                                 uint32_t *keys, uint32_t *vals, cudaStream_t s) {
+    if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
+    dim3 grid(max_blocks_x, n_groups);
+    k_project_write<<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, viewmats, intr, P, masks,
+                                                  woff, rec, keys, vals);
+    return cudaGetLastError();
+}
+
+}  // namespace gsk

@@ -1,0 +1,360 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: integer work bit-exact (segmented sort; tile lists and survivor sets
+except decisions the oracle flags as within float32 rounding of a threshold);
+pixels within 2e-3 abs per rgb channel and 1e-3 relative depth (see
+``_parity``), on the small workload in full, on hand-built edge cases, and on
+sampled cameras of the full-size workload rendered in the benchmark's launch
+configuration.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+from _cases import identity_camera, logit, scene_from
+from _parity import BANDS, compare_camera
+
+import oracle as O
+from paper_2510_15352_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    return t
+
+
+@pytest.fixture(scope="module")
+def gsmod(torch):
+    from paper_2510_15352_b300 import gs
+    return gs
+
+
+@pytest.fixture(scope="module")
+def R(gsmod):
+    r = gsmod.Renderer(device=0)
+    yield r
+    r.close()
+
+
+def dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def render_np(torch, R, sid, vm, it, W, H):
+    rgb, depth, T = R.render(sid, dev(torch, vm), dev(torch, it), W, H, want_T=True)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy(), depth.cpu().numpy(), T.cpu().numpy()
+
+
+def assert_camera_parity(gpu_rgb, gpu_depth, gpu_T, ref, max_unresolved=0):
+    r = compare_camera(gpu_rgb, gpu_depth, gpu_T, ref)
+    assert len(r["unresolved"]) <= max_unresolved, r
+    return r
+
+
+# ------------------------------------------------------------------- sort
+
+@pytest.mark.parametrize("case", ["mixed", "ties", "big", "allbits"])
+def test_sort_segments_is_stable_argsort(torch, R, case):
+    rng = np.random.default_rng({"mixed": 0, "ties": 1, "big": 2, "allbits": 3}[case])
+    if case == "mixed":
+        lens = [0, 1, 2, 31, 32, 33, 4095, 4096, 4097, 10000, 0, 7]
+    elif case == "ties":
+        lens = [5000, 12345, 1]
+    elif case == "big":
+        lens = [300_000, 70_001]
+    else:
+        lens = [20_000, 3]
+    gaps = rng.integers(0, 5, size=len(lens))
+    starts, pos = [], 0
+    for L, g in zip(lens, gaps):
+        pos += int(g)
+        starts.append(pos)
+        pos += L
+    n = pos + 3
+    if case == "ties":
+        keys = rng.integers(0, 7, size=n).astype(np.uint32)
+    elif case == "allbits":
+        keys = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32)
+        keys[: 100] = np.uint32(0xFFFFFFFF)
+    else:
+        keys = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32)
+        keys[::3] = keys[0]
+    vals = np.arange(n, dtype=np.uint32) ^ np.uint32(0x5A5A5A5A)
+    want_k, want_v = keys.copy(), vals.copy()
+    for s, L in zip(starts, lens):
+        o = np.argsort(keys[s:s + L], kind="stable")
+        want_k[s:s + L] = keys[s:s + L][o]
+        want_v[s:s + L] = vals[s:s + L][o]
+    tk = torch.from_numpy(keys.view(np.int32)).cuda()
+    tv = torch.from_numpy(vals.view(np.int32)).cuda()
+    ss = torch.tensor(starts, dtype=torch.int64).cuda()
+    sc = torch.tensor(lens, dtype=torch.int64).cuda()
+    R.sort_segments(tk, tv, ss, sc)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(tk.cpu().numpy().view(np.uint32), want_k)
+    np.testing.assert_array_equal(tv.cpu().numpy().view(np.uint32), want_v)
+
+
+# --------------------------------------------------------------- records
+
+def small_workload():
+    return synth.workload("small_20k_8cam_160x120")
+
+
+def test_records_match_oracle(torch, R, orc):
+    scene, vm, it, W, H = small_workload()
+    sid = R.add_scene(scene)
+    try:
+        for c in range(len(vm)):
+            rec, gidx, rect = R.debug_project(sid, dev(torch, vm[c]), dev(torch, it[c]), W, H,
+                                              cap=scene["mean"].shape[1])
+            ref = orc.project(scene, vm[c], it[c], W, H, bands=BANDS)
+            assert np.all(np.diff(gidx) > 0), "survivors must come in Gaussian-index order"
+            amb = (ref["status"] & O.ST_AMBIG) != 0
+            inner_ok = ref["rect_inner"][:, 0] <= ref["rect_inner"][:, 1]
+            certain = ref["valid"] & ~amb & inner_ok
+            gpu_set = np.zeros(len(ref["valid"]), bool)
+            gpu_set[gidx] = True
+            # every certain survivor is found; every GPU survivor is possible
+            assert np.all(gpu_set[certain]), np.flatnonzero(certain & ~gpu_set)[:10]
+            possible = (ref["status"] & O.ST_PROJ) != 0
+            assert np.all(possible[gidx])
+            g = gidx
+            np.testing.assert_allclose(rec[:, 0], ref["u"][g], atol=1e-3, rtol=1e-5)
+            np.testing.assert_allclose(rec[:, 1], ref["v"][g], atol=1e-3, rtol=1e-5)
+            np.testing.assert_allclose(rec[:, 2], ref["z"][g], rtol=2e-6)
+            np.testing.assert_allclose(rec[:, 3], ref["o"][g], atol=1e-6)
+            scale = np.maximum(np.abs(ref["A"][g]), np.abs(ref["C"][g]))
+            for k, f in ((4, "A"), (5, "B"), (6, "C")):
+                assert np.all(np.abs(rec[:, k] - ref[f][g]) <= 1e-4 * scale), f
+            np.testing.assert_allclose(rec[:, 7], ref["r"][g], rtol=1e-4)
+            np.testing.assert_allclose(rec[:, 8:11], np.c_[ref["red"][g], ref["green"][g],
+                                                            ref["blue"][g]], atol=2e-5)
+            # rect: between the shrunk and the widened double-precision rects
+            ext, inn = ref["rect_ext"][g], ref["rect_inner"][g]
+            assert np.all(rect[:, 0] >= ext[:, 0]) and np.all(rect[:, 1] <= ext[:, 1])
+            assert np.all(rect[:, 2] >= ext[:, 2]) and np.all(rect[:, 3] <= ext[:, 3])
+            ok_in = inn[:, 0] <= inn[:, 1]
+            assert np.all(rect[ok_in, 0] <= inn[ok_in, 0]) and np.all(rect[ok_in, 1] >= inn[ok_in, 1])
+            exact = np.all(rect == ref["rect"][g], axis=1)
+            assert exact.mean() > 0.999
+    finally:
+        R.remove_scene(sid)
+
+
+# ------------------------------------------------------------ tile lists
+
+def check_tile_lists(off_g, gl, ref):
+    ntiles = len(off_g) - 1
+    mismatched_tiles = 0
+    for t in range(ntiles):
+        g = gl[off_g[t]:off_g[t + 1]].astype(np.int64)
+        og = ref["g"][ref["off"][t]:ref["off"][t + 1]]
+        of = ref["flags"][ref["off"][t]:ref["off"][t + 1]]
+        oz = ref["z"][ref["off"][t]:ref["off"][t + 1]]
+        member = (of & 1) != 0
+        amb = (of & 2) != 0
+        where = {int(x): k for k, x in enumerate(og)}
+        # every GPU entry may be a member; every certain member is present
+        assert all(int(x) in where for x in g), f"tile {t}: entry outside every possible rect"
+        gs_ = set(int(x) for x in g)
+        missing = [int(x) for x, m, a in zip(og, member, amb) if m and not a and int(x) not in gs_]
+        assert not missing, f"tile {t}: certain members missing {missing[:5]}"
+        # order: oracle positions increase except for swaps of depth-close entries
+        pos = np.array([where[int(x)] for x in g])
+        for k in range(1, len(pos)):
+            if pos[k] < pos[k - 1]:
+                a, b = pos[k], pos[k - 1]
+                assert abs(oz[a] - oz[b]) <= BANDS.z_abs + BANDS.z_rel * abs(oz[a]), \
+                    f"tile {t}: order differs beyond the depth band"
+        if not np.array_equal(g, og[member]):
+            mismatched_tiles += 1
+    return mismatched_tiles
+
+
+def test_tile_lists_match_oracle(torch, R, orc):
+    scene, vm, it, W, H = small_workload()
+    sid = R.add_scene(scene)
+    try:
+        total_mismatch = 0
+        for c in range(len(vm)):
+            off, gl = R.debug_tile_lists(sid, dev(torch, vm[c]), dev(torch, it[c]), W, H,
+                                         cap=4_000_000)
+            ref = orc.tile_lists(scene, vm[c], it[c], W, H, bands=BANDS)
+            total_mismatch += check_tile_lists(off, gl, ref)
+        # almost every tile list is bit-identical to the oracle's
+        assert total_mismatch <= 2, total_mismatch
+    finally:
+        R.remove_scene(sid)
+
+
+# ---------------------------------------------------------------- pixels
+
+def test_small_workload_pixels(torch, R, orc):
+    scene, vm, it, W, H = small_workload()
+    sid = R.add_scene(scene)
+    try:
+        rgb, depth, T = render_np(torch, R, sid, vm, it, W, H)
+        for c in range(len(vm)):
+            ref = orc.render(scene, vm[c], it[c], W, H, bands=BANDS)
+            assert_camera_parity(rgb[c], depth[c], T[c], ref)
+    finally:
+        R.remove_scene(sid)
+
+
+def _edge_scenes():
+    W, H = 64, 48
+    out = {}
+    out["single_closed_form"] = (scene_from([[0.1, -0.05, 2.0]], [math.log(0.05)] * 3,
+                                            [1, 0, 0, 0], logit(0.7), colours=(0.9, 0.4, 0.1)),
+                                 *identity_camera(W, H, 60.0), W, H)
+    out["near_plane"] = (scene_from([[0, 0, 0.19], [0.01, 0, 0.2001], [0, 0.01, 0.21]],
+                                    [math.log(0.02)] * 3, [1, 0, 0, 0], 2.0),
+                         *identity_camera(W, H, 60.0), W, H)
+    out["covers_all_tiles"] = (scene_from([[0, 0, 1.0], [0.2, 0.1, 3.0]], [math.log(0.6)] * 3,
+                                          [1, 0, 0, 0], [0.5, 1.0],
+                                          colours=[(1, 0, 0), (0, 1, 0)]),
+                               *identity_camera(160, 120, 120.0), 160, 120)
+    out["equal_depths"] = (scene_from([[0, 0, 2.0], [0.02, 0, 2.0], [0.0, 0.02, 2.0]],
+                                      [math.log(0.1)] * 3, [1, 0, 0, 0], [0.5, 0.8, 0.3],
+                                      colours=[(1, 0, 0), (0, 1, 0), (0, 0, 1)]),
+                           *identity_camera(W, H, 60.0), W, H)
+    out["alpha_at_threshold"] = (scene_from([[0, 0, 2.0]], [math.log(1.0)] * 3, [1, 0, 0, 0],
+                                            logit(1 / 255 * 1.05), colours=(1, 1, 1)),
+                                 *identity_camera(16, 16, 20.0), 16, 16)
+    out["termination"] = (scene_from([[0, 0, 1.0 + k] for k in range(6)], [math.log(2.0)] * 3,
+                                     [1, 0, 0, 0], logit(0.9999),
+                                     colours=[(1, 0, 0), (0, 1, 0), (0, 0, 1)] * 2),
+                          *identity_camera(32, 32, 20.0), 32, 32)
+    out["partial_tiles"] = (scene_from([[0.5, 0.3, 1.5], [-0.6, -0.3, 2.0]], [math.log(0.05)] * 3,
+                                       [1, 0, 0, 0], 1.0), *identity_camera(70, 37, 50.0), 70, 37)
+    out["zero_survivors"] = (scene_from([[0, 0, -3.0], [10.0, 0, 1.0]], [math.log(0.05)] * 3,
+                                        [1, 0, 0, 0], 0.0), *identity_camera(W, H, 60.0), W, H)
+    out["camera_inside"] = (scene_from([[0, 0, 0.05], [0, 0, 1.5]], [math.log(2.0), math.log(0.1)],
+                                       [1, 0, 0, 0], 3.0), *identity_camera(W, H, 60.0), W, H)
+    rng = np.random.default_rng(11)
+    n = 300
+    m = np.c_[rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(0.5, 4, n)]
+    out["dense_random_sh3"] = (scene_from(m, rng.normal(-2.5, 0.6, (n, 3)), rng.normal(size=(n, 4)),
+                                          rng.normal(0, 2, n), sh=rng.normal(0, 0.4, (16, 3, n)),
+                                          deg=3), *identity_camera(96, 80, 70.0), 96, 80)
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(_edge_scenes()))
+def test_edge_case_pixels(torch, R, orc, name):
+    scene, vm, it, W, H = _edge_scenes()[name]
+    sid = R.add_scene(scene)
+    try:
+        rgb, depth, T = render_np(torch, R, sid, vm[None], it[None], W, H)
+        ref = orc.render(scene, vm, it, W, H, bands=BANDS)
+        assert_camera_parity(rgb[0], depth[0], T[0], ref)
+        if name == "zero_survivors":
+            assert (rgb == 0).all() and (T == 1).all()
+    finally:
+        R.remove_scene(sid)
+
+
+def test_many_chunks_and_scenes(torch, gsmod, orc):
+    """Cameras of three scenes, interleaved, rendered in chunks of 3 cameras
+    with camera groups of 2: the output of camera i is camera i's view."""
+    r = gsmod.Renderer(device=0, max_chunk_cameras=3, camera_group=2)
+    try:
+        scenes = [synth.make_scene(3000, d, seed=20 + d) for d in (0, 1, 3)]
+        sids = [r.add_scene(s) for s in scenes]
+        W, H = 96, 64
+        vm, it = synth.make_cameras(8, W, H, 70.0, (0.3, 1.2), seed=5)
+        which = np.array([2, 0, 1, 0, 2, 2, 1, 0])
+        rgb, depth, T = r.render([sids[k] for k in which], dev(torch, vm), dev(torch, it), W, H,
+                                 want_T=True)
+        torch.cuda.synchronize()
+        rgb, depth, T = rgb.cpu().numpy(), depth.cpu().numpy(), T.cpu().numpy()
+        for c in range(8):
+            ref = orc.render(scenes[which[c]], vm[c], it[c], W, H, bands=BANDS)
+            assert_camera_parity(rgb[c], depth[c], T[c], ref)
+        assert r.stats()["n_chunks"] == 3
+    finally:
+        r.close()
+
+
+def test_pair_counts_match_oracle(torch, gsmod, orc):
+    """With statistics on, the evaluated-pair counts (the roofline's work
+    count) agree with the oracle's per-pixel walk lengths."""
+    r = gsmod.Renderer(device=0, count_pairs=1, time_stages=1)
+    try:
+        scene, vm, it, W, H = small_workload()
+        sid = r.add_scene(scene)
+        r.render(sid, dev(torch, vm[:4]), dev(torch, it[:4]), W, H)
+        torch.cuda.synchronize()
+        st = r.stats()
+        ev = al = 0
+        for c in range(4):
+            ref = orc.render(scene, vm[c], it[c], W, H)
+            ev += int(ref["n_eval"].sum())
+            al += int(ref["n_alpha"].sum())
+        assert abs(st["pairs_evaluated"] - ev) <= 1e-4 * ev + 50, (st, ev)
+        assert abs(st["pairs_alpha"] - al) <= 1e-4 * al + 50, (st, al)
+        assert st["ms_composite"] > 0
+    finally:
+        r.close()
+
+
+def test_host_entry_point_equals_device_entry_point(torch, R):
+    scene, vm, it, W, H = small_workload()
+    sid = R.add_scene(scene)
+    try:
+        rgb, depth, T = render_np(torch, R, sid, vm, it, W, H)
+        hr = torch.empty((len(vm), H, W, 3), dtype=torch.float32).pin_memory()
+        hd = torch.empty((len(vm), H, W), dtype=torch.float32).pin_memory()
+        hT = torch.empty((len(vm), H, W), dtype=torch.float32).pin_memory()
+        R.render_host(sid, torch.from_numpy(vm).contiguous(), torch.from_numpy(it).contiguous(),
+                      W, H, hr, hd, hT)
+        np.testing.assert_array_equal(hr.numpy(), rgb)
+        np.testing.assert_array_equal(hd.numpy(), depth)
+        np.testing.assert_array_equal(hT.numpy(), T)
+    finally:
+        R.remove_scene(sid)
+
+
+def test_errors_are_reported(torch, gsmod, R):
+    vm, it = identity_camera(32, 32, 30.0)
+    with pytest.raises(gsmod.GSError) as e:
+        R.render(12345, dev(torch, vm[None]), dev(torch, it[None]), 32, 32)
+    assert e.value.status == gsmod.GS_ERR_NOT_FOUND
+    sid = R.add_scene(scene_from([[0, 0, 1.0]], [math.log(0.1)] * 3, [1, 0, 0, 0], 0.0))
+    try:
+        with pytest.raises(gsmod.GSError) as e:
+            R.render(sid, dev(torch, vm[None]), dev(torch, it[None]), 4096, 4096)
+        assert e.value.status == gsmod.GS_ERR_CAPACITY
+    finally:
+        R.remove_scene(sid)
+    with pytest.raises(gsmod.GSError) as e:
+        R.remove_scene(sid)
+    assert e.value.status == gsmod.GS_ERR_NOT_FOUND
+
+
+# ------------------------------------------------------------- full size
+
+def test_full_size_workload_sampled_cameras(torch, R, orc):
+    """1M Gaussians (SH degree 3), 1,024 cameras at 640x480 in one call with
+    the default chunking (the benchmark's launch configuration); three
+    cameras across the batch are checked against the oracle pixel by pixel."""
+    scene, vm, it, W, H = synth.workload("single_1m_sh3_1024cam_640x480")
+    sid = R.add_scene(scene)
+    try:
+        rgb, depth, T = R.render(sid, dev(torch, vm), dev(torch, it), W, H, want_T=True)
+        torch.cuda.synchronize()
+        for c in (0, 517, 1023):
+            ref = orc.render(scene, vm[c], it[c], W, H, bands=BANDS)
+            r = compare_camera(rgb[c].cpu().numpy(), depth[c].cpu().numpy(), T[c].cpu().numpy(), ref)
+            assert len(r["unresolved"]) <= 1e-4 * r["pixels"], r
+    finally:
+        R.remove_scene(sid)
