@@ -130,7 +130,8 @@ def test_records_match_oracle(torch, R, orc):
             g = gidx
             np.testing.assert_allclose(rec[:, 0], ref["u"][g], atol=1e-3, rtol=1e-5)
             np.testing.assert_allclose(rec[:, 1], ref["v"][g], atol=1e-3, rtol=1e-5)
-            np.testing.assert_allclose(rec[:, 2], ref["z"][g], rtol=2e-6)
+            # z = R_c mu + t_c: terms of ~10 m cancel, so its float32 error is absolute
+            np.testing.assert_allclose(rec[:, 2], ref["z"][g], rtol=2e-6, atol=BANDS.z_abs / 2)
             np.testing.assert_allclose(rec[:, 3], ref["o"][g], atol=1e-6)
             scale = np.maximum(np.abs(ref["A"][g]), np.abs(ref["C"][g]))
             for k, f in ((4, "A"), (5, "B"), (6, "C")):
@@ -238,7 +239,8 @@ def _edge_scenes():
                                        [1, 0, 0, 0], 1.0), *identity_camera(70, 37, 50.0), 70, 37)
     out["zero_survivors"] = (scene_from([[0, 0, -3.0], [10.0, 0, 1.0]], [math.log(0.05)] * 3,
                                         [1, 0, 0, 0], 0.0), *identity_camera(W, H, 60.0), W, H)
-    out["camera_inside"] = (scene_from([[0, 0, 0.05], [0, 0, 1.5]], [math.log(2.0), math.log(0.1)],
+    out["camera_inside"] = (scene_from([[0, 0, 0.05], [0, 0, 1.5]],
+                                       [[math.log(2.0)] * 3, [math.log(0.1)] * 3],
                                        [1, 0, 0, 0], 3.0), *identity_camera(W, H, 60.0), W, H)
     rng = np.random.default_rng(11)
     n = 300
