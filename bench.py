@@ -187,12 +187,15 @@ def run_b300(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ms_comp, n_chunks = 0.0, 0
+    stage_ms = {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
     ev0.record(stream)
     for _ in range(args.steps):
         step()
         st = R.stats()  # waits for this step's stage events
         ms_comp += st["ms_composite"]
         n_chunks += st["n_chunks"]
+        for k in stage_ms:
+            stage_ms[k] += st["ms_" + k]
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -252,6 +255,7 @@ def run_b300(args):
                 "pairs_evaluated_per_step": cst["pairs_evaluated"],
                 "pairs_alpha_per_step": cst["pairs_alpha"],
             },
+            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "stats": {"survivors_per_step": cst["survivors"],
                       "intersections_per_step": cst["intersections"]},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
