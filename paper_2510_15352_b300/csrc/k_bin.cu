@@ -41,7 +41,9 @@ __global__ void __launch_bounds__(BIN_RANKS)
     for (int i = tid; i < tiles * BIN_WORDS; i += BIN_RANKS) sbm[i] = 0u;
     __syncthreads();
     const int r = r0 + tid;
-    unsigned long long area = 0;
+    const int lane = tid & 31, warp = tid >> 5;
+    int x0 = 0, y0 = 0, w = 0;
+    uint32_t a = 0;
     if (r < ci.count) {
         const uint32_t slot = vals[ci.seg_off + r];
         const SlotRec R = rec[ci.seg_off + slot];
@@ -50,15 +52,45 @@ __global__ void __launch_bounds__(BIN_RANKS)
         C.b = make_float4(-0.5f * LOG2E * R.b.z, log2f(R.a.w), R.a.z, 0.0f);
         C.c = R.c;
         crec[ci.seg_off + r] = C;
-        const int x0 = (int)(R.d.x & 0xffffu), x1 = (int)(R.d.x >> 16);
-        const int y0 = (int)(R.d.y & 0xffffu), y1 = (int)(R.d.y >> 16);
-        const uint32_t bit = 1u << (tid & 31);
-        const int word = tid >> 5;
-        for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx)
-                atomicOr(&sbm[(ty * ci.TX + tx) * BIN_WORDS + word], bit);
-        if (x1 >= x0 && y1 >= y0) area = (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
+        x0 = (int)(R.d.x & 0xffffu);
+        const int x1 = (int)(R.d.x >> 16);
+        y0 = (int)(R.d.y & 0xffffu);
+        const int y1 = (int)(R.d.y >> 16);
+        if (x1 >= x0 && y1 >= y0) {
+            w = x1 - x0 + 1;
+            a = (uint32_t)(w * (y1 - y0 + 1));
+        }
     }
+    // Load-balanced expansion of the warp's 32 rects into (rank, tile) pairs:
+    // pair e belongs to the first lane whose inclusive area prefix exceeds e.
+    uint32_t incl = a;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t b = 0; b < total; b += 32) {
+        const uint32_t e = b + lane;
+        int l = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const uint32_t v = __shfl_sync(0xffffffffu, incl, l + st - 1);
+            if (v <= e) l += st;
+        }
+        const uint32_t oi = __shfl_sync(0xffffffffu, incl, l);
+        const uint32_t oa = __shfl_sync(0xffffffffu, a, l);
+        const int ox = __shfl_sync(0xffffffffu, x0, l);
+        const int oy = __shfl_sync(0xffffffffu, y0, l);
+        const int ow = __shfl_sync(0xffffffffu, w, l);
+        if (e < total) {
+            const int local = (int)(e - (oi - oa));
+            const int dy = local / ow;
+            const int tx = ox + (local - dy * ow), ty = oy + dy;
+            atomicOr(&sbm[(ty * ci.TX + tx) * BIN_WORDS + warp], 1u << l);
+        }
+    }
+    unsigned long long area = (lane == 0) ? total : 0ull;
     __syncthreads();
     const int w0 = r0 >> 5;
     const int nwb = min(BIN_WORDS, ci.nw - w0);
@@ -66,9 +98,7 @@ __global__ void __launch_bounds__(BIN_RANKS)
         const int t = i / BIN_WORDS, k = i - t * BIN_WORDS;
         if (k < nwb) bitmap[ci.bm_off + (long long)t * ci.nw + w0 + k] = sbm[i];
     }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) area += __shfl_down_sync(0xffffffffu, area, d);
-    if ((tid & 31) == 0 && area) atomicAdd(n_isect, area);
+    if (area) atomicAdd(n_isect, area);
 }
 
 }  // namespace

@@ -28,13 +28,15 @@ struct CamProj {
     float fx, fy, cx, cy;
     float lxp, lxn, lyp, lyn;  // guard-band limits of x/z and y/z
     float cpos[3];             // camera centre in world coordinates
+    float kk;                  // bound of z^2 |J|_F^2 over the guard band
     float W, H;
     int TX, TY;
 };
 
 struct GaussGeo {
     float mx, my, mz;
-    float M[9];  // R(q) diag(exp(log_scale)), row-major
+    float M[9];   // R(q) diag(exp(log_scale)), row-major
+    float smax2;  // largest scale squared (largest eigenvalue of Sigma)
 };
 
 struct Proj {
@@ -68,6 +70,8 @@ __device__ void cam_setup(CamProj &c, const float *vm, const float *in, int W, i
     c.lxn = (c.cx + g * 0.5f * W) / c.fx;
     c.lyp = ((H - c.cy) + g * 0.5f * H) / c.fy;
     c.lyn = (c.cy + g * 0.5f * H) / c.fy;
+    const float lx = fmaxf(c.lxp, c.lxn), ly = fmaxf(c.lyp, c.lyn);
+    c.kk = c.fx * c.fx * (1.0f + lx * lx) + c.fy * c.fy * (1.0f + ly * ly);
     c.W = (float)W;
     c.H = (float)H;
     c.TX = (W + TILE - 1) / TILE;
@@ -84,6 +88,8 @@ __device__ __forceinline__ void load_geo(const SceneDev &s, long long g, GaussGe
     const float sx = expf(ldv(s.log_scale, g, dt));
     const float sy = expf(ldv(s.log_scale, n + g, dt));
     const float sz = expf(ldv(s.log_scale, 2 * n + g, dt));
+    const float sm = fmaxf(sx, fmaxf(sy, sz));
+    G.smax2 = sm * sm;
     float w = ldv(s.quat, g, dt), x = ldv(s.quat, n + g, dt);
     float y = ldv(s.quat, 2 * n + g, dt), z = ldv(s.quat, 3 * n + g, dt);
     const float qq = w * w + x * x + y * y + z * z;
@@ -122,6 +128,15 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     if (!(z > P.near_plane)) return false;
     const float iz = __fdiv_rn(1.0f, z);
     const float xz = __fmul_rn(px, iz), yz = __fmul_rn(py, iz);
+    const float u = fmaf(c.fx, xz, c.cx), v = fmaf(c.fy, yz, c.cy);
+    // Early cull with a bound of the radius: lambda_max(Sigma') <= |J|_F^2 s_max^2 + dil
+    // and |J|_F^2 <= kk / z^2 over the guard band; the 1.001 and +0.01 px margins keep
+    // rb above the float32 radius, so this culls only what the exact test culls.
+    {
+        const float rb = fmaf(1.001f * P.sigma,
+                              sqrtf(fmaf(c.kk * iz * iz, G.smax2, P.dilation)), 0.01f);
+        if (u + rb < 0.0f || u - rb >= c.W || v + rb < 0.0f || v - rb >= c.H) return false;
+    }
     const float xc = fminf(fmaxf(xz, -c.lxn), c.lxp);
     const float yc = fminf(fmaxf(yz, -c.lyn), c.lyp);
     const float j00 = __fmul_rn(c.fx, iz), j02 = -__fmul_rn(__fmul_rn(c.fx, xc), iz);
@@ -146,7 +161,6 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     const float hd = __fmul_rn(0.5f, __fsub_rn(a, cc));
     const float lmax = fmaf(0.5f, __fadd_rn(a, cc), __fsqrt_rn(fmaf(hd, hd, __fmul_rn(b, b))));
     const float r = __fmul_rn(P.sigma, __fsqrt_rn(lmax));
-    const float u = fmaf(c.fx, xz, c.cx), v = fmaf(c.fy, yz, c.cy);
     if (!(__fadd_rn(u, r) >= 0.0f) || !(__fsub_rn(u, r) < c.W) || !(__fadd_rn(v, r) >= 0.0f) ||
         !(__fsub_rn(v, r) < c.H))
         return false;
@@ -200,9 +214,11 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     }
 }
 
-__device__ __forceinline__ void sh_colour(const SceneDev &s, long long g, const CamProj &c,
-                                          const GaussGeo &G, float rgb[3]) {
-    const int K = (s.deg + 1) * (s.deg + 1);
+// Colour of one Gaussian seen from camera c. The block's SH coefficients are
+// staged in shared memory as shs[(3k + ch) * PROJ_THREADS + thread].
+__device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg, int tid,
+                                          const CamProj &c, const GaussGeo &G, float rgb[3]) {
+    const int K = (deg + 1) * (deg + 1);
     float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
     const float dd = dx * dx + dy * dy + dz * dz;
     if (dd > 0.0f) {
@@ -216,14 +232,13 @@ __device__ __forceinline__ void sh_colour(const SceneDev &s, long long g, const 
         dz = 1.0f;
     }
     float Y[16];
-    sh_basis(s.deg, dx, dy, dz, Y);
-    const long long n = s.n;
+    sh_basis(deg, dx, dy, dz, Y);
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.5f;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (k < K) acc = fmaf(ldv(s.sh, (3LL * k + ch) * n + g, s.app_dtype), Y[k], acc);
+            if (k < K) acc = fmaf(shs[(3 * k + ch) * PROJ_THREADS + tid], Y[k], acc);
         rgb[ch] = fmaxf(acc, 0.0f);
     }
 }
@@ -328,6 +343,12 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     const bool valid = g < gr.n;
     const int lane = threadIdx.x & 31;
     const bool warp_live = (g - lane) < gr.n;
+    // stage this block's SH coefficients: one coalesced row segment per (k, channel)
+    extern __shared__ float shs[];
+    const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
+    for (int k = 0; k < K3; ++k)
+        shs[k * PROJ_THREADS + threadIdx.x] = valid ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype) : 0.0f;
+    __syncthreads();
     if (!warp_live) return;  // whole warp past the end: no mask words to read
     GaussGeo G;
     float opacity = 0.0f;
@@ -349,7 +370,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
             pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = 0.0f;
         }
         float rgb[3];
-        sh_colour(sc, g, cp[c], G, rgb);
+        sh_colour(shs, sc.deg, threadIdx.x, cp[c], G, rgb);
         const uint32_t slot = woff[w] + __popc(m & lt);
         const long long at = soff[c] + slot;
         SlotRec R;
@@ -391,8 +412,12 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  uint32_t *keys, uint32_t *vals, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(max_blocks_x, n_groups);
-    k_project_write<<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, viewmats, intr, P, masks,
-                                                  woff, rec, keys, vals);
+    const int smem = 48 * PROJ_THREADS * (int)sizeof(float);  // SH of degree <= 3
+    cudaError_t e = cudaFuncSetAttribute(k_project_write,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, viewmats, intr, P,
+                                                     masks, woff, rec, keys, vals);
     return cudaGetLastError();
 }
 

@@ -85,14 +85,19 @@ __global__ void __launch_bounds__(SORT_THREADS)
             for (int j = 0; j < 8; ++j) wcnt[warp][lane * 8 + j] = 0;
             __syncwarp();
             uint32_t kr[SORT_IPT], vr[SORT_IPT], rk[SORT_IPT];
+            // all loads of the warp's sub-tile first, so they are in flight together
+#pragma unroll
+            for (int r = 0; r < SORT_IPT; ++r) {
+                const long long i = t0 + (long long)warp * (32 * SORT_IPT) + r * 32 + lane;
+                kr[r] = i < n ? sk[i] : 0u;
+                vr[r] = i < n ? sv[i] : 0u;
+            }
 #pragma unroll
             for (int r = 0; r < SORT_IPT; ++r) {
                 const long long i = t0 + (long long)warp * (32 * SORT_IPT) + r * 32 + lane;
                 const bool ok = i < n;
-                const uint32_t k = ok ? sk[i] : 0u;
+                const uint32_t k = kr[r];
                 const uint32_t d = (k >> shift) & 255u;
-                kr[r] = k;
-                vr[r] = ok ? sv[i] : 0u;
                 const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 256u + lane);
                 const uint32_t before = wcnt[warp][d & 255u];
                 rk[r] = ok ? before + __popc(peers & lt) : 0xffffffffu;
