@@ -29,14 +29,14 @@ sys.path.insert(0, ROOT)
 METRIC = "640x480 camera frames/s, 4096-cam batch; upsampled vs plain at >=35 dB PSNR"
 UNIT = "frames/s"
 WORKLOAD = "single_1m_sh3_1024cam_640x480"
-# algorithmic FP32 operations of the compositing step per (pixel, Gaussian) pair,
-# counting an FMA as 2 and comparisons as 0:
-#   every evaluated pair: dx, dy (2), b'dy (1), c'dy^2 + log2(o) (3),
-#     a'dx + b'dy (2), (..)dx + (..) (2)                                   -> 10
-#   pairs with alpha >= alpha_min, additionally: min (1), 1 - alpha (1),
-#     T' = T(1-alpha) (1), w = alpha T (1), rgb + depth accumulation 4 FMA (8) -> 12
-#   the exp2 is a MUFU (SFU) op and is not counted here.
-F_EVAL, F_ALPHA = 10, 12
+# Algorithmic FP32 work of the compositing step: the pairs (pixel, Gaussian)
+# that the method must blend -- alpha >= alpha_min before the pixel stops --
+# at 22 flops each (FMA = 2, comparisons 0): dx, dy (2), b'dy (1),
+# c'dy^2 + log2(o) (3), a'dx + b'dy (2), (..)dx + (..) (2), min (1), 1 - alpha (1),
+# T' = T(1-alpha) (1), w = alpha T (1), rgb + depth accumulation 4 FMA (8).
+# Pairs below alpha_min are not counted: how many of those a kernel evaluates
+# depends on its culling, not on the method. exp2 is an SFU op, not counted.
+F_PAIR = 22
 # FP32 peak of one B300: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz max clock
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
@@ -161,15 +161,17 @@ def run_b300(args):
     depth = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
 
     # algorithmic work of the compositing kernel on these inputs (counting run)
-    counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk)
+    counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk,
+                          pixels_per_thread=args.ppt)
     sid_c = counter.add_scene(scene)
     counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
     torch.cuda.synchronize()
     cst = counter.stats()
     counter.close()
-    flops_per_step = F_EVAL * cst["pairs_evaluated"] + F_ALPHA * cst["pairs_alpha"]
+    flops_per_step = F_PAIR * cst["pairs_alpha"]
 
-    R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk)
+    R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
+                    pixels_per_thread=args.ppt)
     sid = R.add_scene(scene)
     stream = torch.cuda.current_stream()
 
@@ -243,6 +245,7 @@ def run_b300(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cameras_per_gpu": n, "width": W, "height": H,
                        "gaussians": 1_000_000, "sh_degree": 3, "chunk_cameras": args.chunk,
+                       "pixels_per_thread": args.ppt,
                        "l2": "inputs larger than L2 (scene 236 MB; 5 GB of outputs per step)"},
             "roofline": {
                 "kernel": "k_composite", "bound": "alu", "achieved": achieved,
@@ -276,6 +279,7 @@ def main():
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
     ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 1024)")
     ap.add_argument("--chunk", type=int, default=256, help="cameras per internal chunk")
+    ap.add_argument("--ppt", type=int, default=4, help="compositing pixels per thread (2|4)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -304,13 +304,13 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, tiles,
                        (const SlotRec *)ctx->rec.p, (const uint32_t *)ctx->vals.p,
                        (CRec *)ctx->crec.p, (uint32_t *)ctx->bitmap.p,
-                       (unsigned long long *)ctx->stats.p + 2, a.st));
+                       (unsigned long long *)ctx->stats.p + 2, std::log(cfg.alpha_min), a.st));
         if (timing) CKC(cudaEventRecord(E[3], a.st));
         if (a.upto == UPTO_BIN) break;
         CKC(launch_composite((const CamInfo *)ctx->cams.p, (const int *)ctx->tilepre.p, m, m * tiles,
                              (const CRec *)ctx->crec.p, (const uint32_t *)ctx->bitmap.p, C, a.rgb,
                              a.depth, a.T, (unsigned long long *)ctx->stats.p,
-                             cfg.count_pairs != 0, a.st));
+                             cfg.count_pairs != 0, cfg.pixels_per_thread, a.st));
         if (timing) {
             CKC(cudaEventRecord(E[4], a.st));
             ctx->ev_used = chunk_id + 1;
@@ -378,6 +378,7 @@ gs_status gs_config_default(gs_config *out) {
     out->camera_group = 32;
     out->count_pairs = 0;
     out->time_stages = 0;
+    out->pixels_per_thread = 4;
     return GS_OK;
 }
 
@@ -392,7 +393,8 @@ gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **o
     if (!(c.near_plane > 0.0f) || !(c.dilation >= 0.0f) || !(c.sigma_cull > 0.0f) ||
         !(c.alpha_min > 0.0f) || !(c.alpha_max > 0.0f && c.alpha_max < 1.0f) ||
         !(c.T_min > 0.0f && c.T_min < 1.0f) || c.max_chunk_cameras < 1 || c.camera_group < 1 ||
-        c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f))
+        c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) ||
+        (c.pixels_per_thread != 2 && c.pixels_per_thread != 4))
         return GS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)

@@ -15,8 +15,6 @@ constexpr int PROJ_THREADS = 256;   // Gaussians per projection block (8 mask wo
 constexpr int BIN_RANKS = 256;      // depth ranks per binning block
 constexpr int BIN_WORDS = BIN_RANKS / 32;
 constexpr int MAX_TILES = 7000;     // tiles per camera (binning smem: 32 B per tile)
-constexpr int COMP_THREADS = 128;   // compositing block: 16x16 tile, 2 pixels per thread
-constexpr int COMP_WORDS = 128;     // bitmap words read per compositing round
 constexpr int COMP_BATCH = 128;     // Gaussian records staged per compositing sub-batch
 constexpr int SORT_THREADS = 512;
 constexpr int SORT_IPT = 8;         // keys per thread per sort tile
@@ -64,8 +62,8 @@ struct Group {
 };
 
 // A survivor's record in Gaussian-index order (64 B).
-//   a: u, v, z, opacity   b: A, B, C, r (conic + radius)   c: red, green, blue, 0
-//   d: x0 | x1 << 16, y0 | y1 << 16, Gaussian index, 0
+//   a: u, v, z, opacity   b: A, B, C, r (conic + radius)
+//   c: red, green, blue, Sigma'_00      d: x0 | x1 << 16, y0 | y1 << 16, index, Sigma'_11 bits
 struct __align__(16) SlotRec {
     float4 a, b, c;
     uint4 d;
@@ -74,8 +72,10 @@ struct __align__(16) SlotRec {
 // A survivor's compositing record in depth-rank order (48 B), with the
 // constants folded so that  p = a'dx^2 + b'dx dy + c'dy^2 + log2(o)  is
 // log2(o e^power):
-//   a: u, v, a' = -log2(e)/2 A, b' = -log2(e) B
-//   b: c' = -log2(e)/2 C, log2(o), z, 0      c: red, green, blue, 0
+//   a: u, v, hx, hy    (half extents of the box around the alpha >= alpha_min
+//                       ellipse, with a float32 margin; < 0 when o < alpha_min)
+//   b: a' = -log2(e)/2 A, b' = -log2(e) B, c' = -log2(e)/2 C, log2(o)
+//   c: red, green, blue, z
 struct __align__(16) CRec {
     float4 a, b, c;
 };
@@ -103,11 +103,14 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
 
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
                        int max_tiles, const SlotRec *rec, const uint32_t *vals, CRec *crec,
-                       uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);
+                       uint32_t *bitmap, unsigned long long *n_isect, float ln_alpha_min,
+                       cudaStream_t s);
 
+// pixels_per_thread: 2 (128-thread blocks) or 4 (64-thread blocks)
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
                              int n_tiles, const CRec *crec, const uint32_t *bitmap,
                              CompParams C, float *rgb, float *depth, float *final_T,
-                             unsigned long long *stats, bool collect, cudaStream_t s);
+                             unsigned long long *stats, bool collect, int pixels_per_thread,
+                             cudaStream_t s);
 
 }  // namespace gsk

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(BIN_RANKS)
     k_bin(const CamInfo *__restrict__ cams, const int *__restrict__ blk_prefix, int n_slots,
           const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
           CRec *__restrict__ crec, uint32_t *__restrict__ bitmap,
-          unsigned long long *__restrict__ n_isect) {
+          unsigned long long *__restrict__ n_isect, float ln_alpha_min) {
     extern __shared__ uint32_t sbm[];  // [tiles][BIN_WORDS]
     int lo = 0, hi = n_slots - 1;
     while (lo < hi) {
@@ -47,10 +47,20 @@ __global__ void __launch_bounds__(BIN_RANKS)
     if (r < ci.count) {
         const uint32_t slot = vals[ci.seg_off + r];
         const SlotRec R = rec[ci.seg_off + slot];
+        // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o / alpha_min):
+        // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so that float32
+        // rounding of the per-pixel test can never pass a pixel outside it
+        const float q = 2.0f * (logf(R.a.w) - ln_alpha_min);
+        float hx = -1e30f, hy = -1e30f;
+        if (q >= 0.0f) {
+            hx = fmaf(1.001f, sqrtf(q * R.c.w), 0.01f);
+            hy = fmaf(1.001f, sqrtf(q * __uint_as_float(R.d.w)), 0.01f);
+        }
         CRec C;
-        C.a = make_float4(R.a.x, R.a.y, -0.5f * LOG2E * R.b.x, -LOG2E * R.b.y);
-        C.b = make_float4(-0.5f * LOG2E * R.b.z, log2f(R.a.w), R.a.z, 0.0f);
-        C.c = R.c;
+        C.a = make_float4(R.a.x, R.a.y, hx, hy);
+        C.b = make_float4(-0.5f * LOG2E * R.b.x, -LOG2E * R.b.y, -0.5f * LOG2E * R.b.z,
+                          log2f(R.a.w));
+        C.c = make_float4(R.c.x, R.c.y, R.c.z, R.a.z);
         crec[ci.seg_off + r] = C;
         x0 = (int)(R.d.x & 0xffffu);
         const int x1 = (int)(R.d.x >> 16);
@@ -105,14 +115,15 @@ __global__ void __launch_bounds__(BIN_RANKS)
 
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
                        int max_tiles, const SlotRec *rec, const uint32_t *vals, CRec *crec,
-                       uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s) {
+                       uint32_t *bitmap, unsigned long long *n_isect, float ln_alpha_min,
+                       cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
     const size_t smem = (size_t)max_tiles * BIN_WORDS * sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_bin<<<n_blocks, BIN_RANKS, smem, s>>>(cams, blk_prefix, n_slots, rec, vals, crec, bitmap,
-                                            n_isect);
+                                            n_isect, ln_alpha_min);
     return cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ struct GaussGeo {
 
 struct Proj {
     float u, v, z, A, B, C, r;
+    float sa, sc;  // 2D covariance diagonal (with the dilation)
     int x0, x1, y0, y1;
 };
 
@@ -178,6 +179,8 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     o.A = cc * idet;
     o.B = -b * idet;
     o.C = a * idet;
+    o.sa = a;
+    o.sc = cc;
     o.u = u;
     o.v = v;
     o.r = r;
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
             pr.x1 = 0;
             pr.y0 = 1;
             pr.y1 = 0;
-            pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = 0.0f;
+            pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
         }
         float rgb[3];
         sh_colour(shs, sc.deg, threadIdx.x, cp[c], G, rgb);
@@ -376,9 +379,10 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         SlotRec R;
         R.a = make_float4(pr.u, pr.v, pr.z, opacity);
         R.b = make_float4(pr.A, pr.B, pr.C, pr.r);
-        R.c = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+        R.c = make_float4(rgb[0], rgb[1], rgb[2], pr.sa);
         R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
-                         (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)g, 0u);
+                         (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)g,
+                         __float_as_uint(pr.sc));
         rec[at] = R;
         keys[at] = __float_as_uint(pr.z);
         vals[at] = slot;

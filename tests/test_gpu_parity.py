@@ -199,16 +199,18 @@ def test_tile_lists_match_oracle(torch, R, orc):
 
 # ---------------------------------------------------------------- pixels
 
-def test_small_workload_pixels(torch, R, orc):
-    scene, vm, it, W, H = small_workload()
-    sid = R.add_scene(scene)
+@pytest.mark.parametrize("ppt", [2, 4])
+def test_small_workload_pixels(torch, gsmod, orc, ppt):
+    r = gsmod.Renderer(device=0, pixels_per_thread=ppt)
     try:
-        rgb, depth, T = render_np(torch, R, sid, vm, it, W, H)
+        scene, vm, it, W, H = small_workload()
+        sid = r.add_scene(scene)
+        rgb, depth, T = render_np(torch, r, sid, vm, it, W, H)
         for c in range(len(vm)):
             ref = orc.render(scene, vm[c], it[c], W, H, bands=BANDS)
             assert_camera_parity(rgb[c], depth[c], T[c], ref)
     finally:
-        R.remove_scene(sid)
+        r.close()
 
 
 def _edge_scenes():
