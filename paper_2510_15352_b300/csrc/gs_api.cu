@@ -51,7 +51,7 @@ struct gs_context {
     DevBuf d_scenes;
     // chunk workspace
     DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, crec, bitmap;
-    DevBuf cams, groups, blkpre, tilepre, segstart, segcount, stats;
+    DevBuf cams, groups, blkpre, tilepre, segstart, segcount, stats, sorttiles, sorthist;
     // host-API staging
     DevBuf h_vm, h_in, h_rgb, h_depth, h_T;
     PinBuf pin[2];
@@ -143,7 +143,7 @@ struct RenderArgs {
 struct Staging {
     CamInfo *cams;
     Group *groups;
-    int *blkpre, *tilepre, *counts;
+    int *blkpre, *tilepre, *counts, *sorttiles;
     long long *segstart, *segcount;
 };
 
@@ -170,7 +170,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     CKC(cudaMemsetAsync(ctx->stats.p, 0, 4 * sizeof(unsigned long long), a.st));
     const size_t stage_bytes =
         align_up((size_t)chunk_max * sizeof(CamInfo), 256) + align_up((size_t)chunk_max * sizeof(Group), 256) +
-        3 * align_up((size_t)(chunk_max + 1) * sizeof(int), 256) +
+        4 * align_up((size_t)(chunk_max + 1) * sizeof(int), 256) +
         2 * align_up((size_t)chunk_max * sizeof(long long), 256);
     for (int k = 0; k < 2; ++k) CKS(grow_pinned(ctx, ctx->pin[k], stage_bytes));
     CKS(grow(ctx, ctx->cams, (size_t)chunk_max * sizeof(CamInfo)));
@@ -180,6 +180,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     CKS(grow(ctx, ctx->segstart, (size_t)chunk_max * sizeof(long long)));
     CKS(grow(ctx, ctx->segcount, (size_t)chunk_max * sizeof(long long)));
     CKS(grow(ctx, ctx->counts, (size_t)chunk_max * sizeof(int)));
+    CKS(grow(ctx, ctx->sorttiles, (size_t)(chunk_max + 1) * sizeof(int)));
     const int n_chunks = (a.n + chunk_max - 1) / chunk_max;
     if (timing)
         while ((int)ctx->ev.size() < 5 * n_chunks) {
@@ -205,6 +206,8 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         S.tilepre = (int *)(base + off);
         off += align_up((size_t)(chunk_max + 1) * sizeof(int), 256);
         S.counts = (int *)(base + off);
+        off += align_up((size_t)(chunk_max + 1) * sizeof(int), 256);
+        S.sorttiles = (int *)(base + off);
         off += align_up((size_t)(chunk_max + 1) * sizeof(int), 256);
         S.segstart = (long long *)(base + off);
         off += align_up((size_t)chunk_max * sizeof(long long), 256);
@@ -258,7 +261,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
 
         // exact sizes of this chunk
         long long S_total = 0, bm_words = 0;
-        int blocks = 0;
+        int blocks = 0, sort_tiles = 0;
         for (int s = 0; s < m; ++s) {
             CamInfo &ci = S.cams[s];
             ci.count = S.counts[s];
@@ -272,7 +275,10 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             S.tilepre[s] = s * tiles;
             S.segstart[s] = ci.seg_off;
             S.segcount[s] = ci.count;
+            S.sorttiles[s] = sort_tiles;
+            sort_tiles += sort_tiles_for(ci.count);
         }
+        S.sorttiles[m] = sort_tiles;
         S.blkpre[m] = blocks;
         S.tilepre[m] = m * tiles;
         st.survivors += S_total;
@@ -284,11 +290,13 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         CKS(grow(ctx, ctx->tvals, Sx * 4));
         CKS(grow(ctx, ctx->crec, Sx * sizeof(CRec)));
         CKS(grow(ctx, ctx->bitmap, (size_t)std::max<long long>(bm_words, 1) * 4));
+        CKS(grow(ctx, ctx->sorthist, (size_t)std::max(sort_tiles, 1) * 256 * 4));
         CKC(cudaMemcpyAsync(ctx->cams.p, S.cams, m * sizeof(CamInfo), cudaMemcpyHostToDevice, a.st));
         CKC(cudaMemcpyAsync(ctx->blkpre.p, S.blkpre, (m + 1) * sizeof(int), cudaMemcpyHostToDevice, a.st));
         CKC(cudaMemcpyAsync(ctx->tilepre.p, S.tilepre, (m + 1) * sizeof(int), cudaMemcpyHostToDevice, a.st));
         CKC(cudaMemcpyAsync(ctx->segstart.p, S.segstart, m * sizeof(long long), cudaMemcpyHostToDevice, a.st));
         CKC(cudaMemcpyAsync(ctx->segcount.p, S.segcount, m * sizeof(long long), cudaMemcpyHostToDevice, a.st));
+        CKC(cudaMemcpyAsync(ctx->sorttiles.p, S.sorttiles, (m + 1) * sizeof(int), cudaMemcpyHostToDevice, a.st));
         CKC(launch_project_write((const Group *)ctx->groups.p, n_groups, max_bx,
                                  (const SceneDev *)ctx->d_scenes.p, (const CamInfo *)ctx->cams.p,
                                  a.vm, a.in, P, (const uint32_t *)ctx->masks.p,
@@ -299,7 +307,8 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         CKC(launch_sort_segments((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
                                  (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
                                  (const long long *)ctx->segstart.p,
-                                 (const long long *)ctx->segcount.p, m, a.st));
+                                 (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
+                                 m, sort_tiles, (uint32_t *)ctx->sorthist.p, a.st));
         if (timing) CKC(cudaEventRecord(E[2], a.st));
         CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, tiles,
                        (const SlotRec *)ctx->rec.p, (const uint32_t *)ctx->vals.p,
@@ -417,6 +426,7 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->crec,
                       &ctx->bitmap,   &ctx->cams,  &ctx->groups,  &ctx->blkpre,  &ctx->tilepre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
+                      &ctx->sorttiles, &ctx->sorthist,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -674,11 +684,32 @@ gs_status gs_sort_segments(gs_context *ctx, uint32_t *keys, uint32_t *vals, int6
         return fail(ctx, GS_ERR_INVALID_ARG, "NULL argument");
     ctx->err.clear();
     CKC(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    // the tile table is built on the host from the segment lengths
+    std::vector<int64_t> hs(n_seg), hc(n_seg);
+    CKC(cudaMemcpyAsync(hs.data(), seg_start, n_seg * 8, cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(hc.data(), seg_count, n_seg * 8, cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    std::vector<int> tiles(n_seg + 1);
+    int nt = 0;
+    for (int i = 0; i < n_seg; ++i) {
+        if (hc[i] < 0 || hs[i] < 0 || hs[i] + hc[i] > n)
+            return fail(ctx, GS_ERR_INVALID_ARG, "segment %d out of range", i);
+        tiles[i] = nt;
+        nt += sort_tiles_for(hc[i]);
+    }
+    tiles[n_seg] = nt;
     CKS(grow(ctx, ctx->tkeys, (size_t)std::max<int64_t>(n, 1) * 4));
     CKS(grow(ctx, ctx->tvals, (size_t)std::max<int64_t>(n, 1) * 4));
+    CKS(grow(ctx, ctx->sorttiles, tiles.size() * sizeof(int)));
+    CKS(grow(ctx, ctx->sorthist, (size_t)std::max(nt, 1) * 256 * 4));
+    CKC(cudaMemcpyAsync(ctx->sorttiles.p, tiles.data(), tiles.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, st));
     CKC(launch_sort_segments(keys, vals, (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
-                             (const long long *)seg_start, (const long long *)seg_count, n_seg,
-                             (cudaStream_t)stream));
+                             (const long long *)seg_start, (const long long *)seg_count,
+                             (const int *)ctx->sorttiles.p, n_seg, nt,
+                             (uint32_t *)ctx->sorthist.p, st));
+    CKC(cudaStreamSynchronize(st));  // the host tile table must outlive the copy
     return GS_OK;
 }
 

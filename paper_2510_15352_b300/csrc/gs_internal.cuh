@@ -16,8 +16,6 @@ constexpr int BIN_RANKS = 256;      // depth ranks per binning block
 constexpr int BIN_WORDS = BIN_RANKS / 32;
 constexpr int MAX_TILES = 7000;     // tiles per camera (binning smem: 32 B per tile)
 constexpr int COMP_BATCH = 128;     // Gaussian records staged per compositing sub-batch
-constexpr int SORT_THREADS = 512;
-constexpr int SORT_IPT = 8;         // keys per thread per sort tile
 
 enum : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 
@@ -97,9 +95,13 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
                                  uint32_t *keys, uint32_t *vals, cudaStream_t s);
 
+// Segmented sort: tile_start[n_seg + 1] is the prefix of sort_tiles_for(count)
+// over the segments; hist needs 256 uint32 per tile.
+int sort_tiles_for(long long count);
 cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
                                  uint32_t *tmp_vals, const long long *seg_start,
-                                 const long long *seg_count, int n_seg, cudaStream_t s);
+                                 const long long *seg_count, const int *tile_start, int n_seg,
+                                 int n_tiles, uint32_t *hist, cudaStream_t s);
 
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
                        int max_tiles, const SlotRec *rec, const uint32_t *vals, CRec *crec,

@@ -15,11 +15,12 @@
 //   p < log2(alpha_min): skip;  alpha = min(alpha_max, 2^p)
 //   T' = T (1 - alpha); T' < T_min: the pixel stops (this Gaussian not added)
 //   C += alpha T rgb, D += alpha T z, T = T'.
-// Instruction economy (the kernel is issue-bound): a warp skips a Gaussian
-// whose alpha >= alpha_min box misses the warp's pixel rows (uniform branch;
-// the box is widened past float32 rounding, so the skip never changes a
-// result), the blend runs only when some lane passes the alpha test (warp
-// vote), and a warp whose pixels have all stopped skips the batch. The block
+// Instruction economy (the kernel is issue-bound): when a record is staged,
+// the warps whose pixel rows meet the box of its alpha >= alpha_min region are
+// marked, and other warps skip it (uniform branch; the box is widened past
+// float32 rounding, so the skip never changes a result); the blend runs only
+// when some lane passes the alpha test (warp vote) and is branch-free: a
+// stopped pixel's alpha threshold becomes +inf, which freezes it. The block
 // stops reading its list once every pixel has stopped. No tensor cores: this
 // is not a dense contraction.
 #include "gs_internal.cuh"
@@ -44,6 +45,8 @@ __global__ void __launch_bounds__(256 / PPT)
     constexpr int CPR = 16 / PPT;    // threads per pixel row
     constexpr int RPW = 32 / CPR;    // pixel rows per warp
     constexpr int NWARP = NT / 32;
+    // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits),
+    // s2 = (red, green, blue, -)
     __shared__ float4 s0[COMP_BATCH], s1[COMP_BATCH], s2[COMP_BATCH];
     __shared__ uint32_t slist[NT * 32];
     __shared__ uint32_t wsum[NWARP];
@@ -62,29 +65,31 @@ __global__ void __launch_bounds__(256 / PPT)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int y = ty * TILE + tid / CPR;
     const float py = y + 0.5f;
-    float px[PPT], T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT];
-    bool done[PPT], in[PPT];
+    const float INF = __int_as_float(0x7f800000);
+    // Per pixel: T, colour, depth and its own alpha threshold; a pixel that has
+    // stopped (or lies outside the image) has threshold +inf, so it passes no
+    // further alpha test and its state stays frozen without a branch.
+    float px[PPT], T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT], thr[PPT];
+    bool in[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int x = tx * TILE + tid % CPR + k * CPR;
         px[k] = x + 0.5f;
         in[k] = x < ci.W && y < ci.H;
-        done[k] = !in[k];
+        thr[k] = in[k] ? P.log2_alpha_min : INF;
         T[k] = 1.0f;
         cr[k] = cg[k] = cb[k] = cd[k] = 0.0f;
     }
-    // pixel-centre box of this warp's rows
-    const float wx0 = tx * TILE + 0.5f, wx1 = tx * TILE + TILE - 0.5f;
-    const float wy0 = ty * TILE + warp * RPW + 0.5f, wy1 = wy0 + (RPW - 1);
+    const uint32_t warp_bit = 1u << warp;
     unsigned long long ev = 0, al = 0;
 
     const uint32_t *bm = bitmap + ci.bm_off + (long long)t * ci.nw;
     const CRec *recs = crec + ci.seg_off;
     for (int wb = 0; wb < ci.nw; wb += NT) {
-        bool mine_done = true;
+        bool live = false;
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) mine_done = mine_done && done[k];
-        if (!__syncthreads_or(!mine_done)) break;
+        for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
+        if (!__syncthreads_or(live)) break;
         const int w = wb + tid;
         uint32_t word = w < ci.nw ? bm[w] : 0u;
         const uint32_t c = __popc(word);
@@ -114,61 +119,69 @@ __global__ void __launch_bounds__(256 / PPT)
             const int nb = (int)min((uint32_t)COMP_BATCH, total - j0);
             for (int q = tid; q < nb; q += NT) {
                 const CRec R = recs[slist[j0 + q]];
-                s0[q] = R.a;
-                s1[q] = R.b;
+                // warps whose pixel rows meet the box of the alpha >= alpha_min region
+                const float x0 = tx * TILE + 0.5f, x1 = tx * TILE + TILE - 0.5f;
+                uint32_t m = 0;
+                if (R.a.x + R.a.z >= x0 && R.a.x - R.a.z <= x1) {
+#pragma unroll
+                    for (int k = 0; k < NWARP; ++k) {
+                        const float y0 = ty * TILE + k * RPW + 0.5f, y1 = y0 + (RPW - 1);
+                        if (R.a.y + R.a.w >= y0 && R.a.y - R.a.w <= y1) m |= 1u << k;
+                    }
+                }
+                s0[q] = make_float4(R.a.x, R.a.y, R.b.x, R.b.y);
+                s1[q] = make_float4(R.b.z, R.b.w, R.c.w, __uint_as_float(m));
                 s2[q] = R.c;
             }
             __syncthreads();
-            bool live = false;
+            live = false;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) live = live || !done[k];
+            for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
             if (__any_sync(0xffffffffu, live)) {
                 for (int j = 0; j < nb; ++j) {
-                    const float4 g0 = s0[j];  // u, v, hx, hy
+                    const float4 g1 = s1[j];  // c', log2 o, z, warp mask
                     if (STATS) {
 #pragma unroll
-                        for (int k = 0; k < PPT; ++k) ev += done[k] ? 0u : 1u;
+                        for (int k = 0; k < PPT; ++k) ev += thr[k] != INF ? 1u : 0u;
                     }
-                    if (g0.x + g0.z < wx0 || g0.x - g0.z > wx1 || g0.y + g0.w < wy0 ||
-                        g0.y - g0.w > wy1)
-                        continue;  // warp-uniform: no pixel of these rows can pass
-                    const float4 g1 = s1[j];  // a', b', c', log2 o
+                    if (!(__float_as_uint(g1.w) & warp_bit)) continue;  // warp-uniform
+                    const float4 g0 = s0[j];  // u, v, a', b'
                     const float dy = py - g0.y;
-                    const float base = fmaf(g1.z * dy, dy, g1.w);
-                    const float bdy = g1.y * dy;
+                    const float base = fmaf(g1.x * dy, dy, g1.y);
+                    const float bdy = g0.w * dy;
                     float p[PPT];
                     bool any = false;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
                         const float dx = px[k] - g0.x;
-                        p[k] = fmaf(fmaf(g1.x, dx, bdy), dx, base);
-                        any = any || (!done[k] && p[k] >= P.log2_alpha_min);
+                        p[k] = fmaf(fmaf(g0.z, dx, bdy), dx, base);
+                        any = any || p[k] >= thr[k];
                     }
                     if (!__any_sync(0xffffffffu, any)) continue;
-                    const float4 g2 = s2[j];  // red, green, blue, z
+                    const float4 g2 = s2[j];  // red, green, blue
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        if (done[k] || p[k] < P.log2_alpha_min) continue;
-                        if (STATS) al++;
+                        const bool pass = p[k] >= thr[k];
+                        if (STATS) al += pass ? 1u : 0u;
                         const float alpha = fminf(P.alpha_max, ex2_approx(p[k]));
-                        const float Tn = T[k] * (1.0f - alpha);
-                        if (Tn < P.T_min) {
-                            done[k] = true;
-                            continue;
-                        }
                         const float wgt = alpha * T[k];
-                        cr[k] = fmaf(wgt, g2.x, cr[k]);
-                        cg[k] = fmaf(wgt, g2.y, cg[k]);
-                        cb[k] = fmaf(wgt, g2.z, cb[k]);
-                        cd[k] = fmaf(wgt, g2.w, cd[k]);
-                        T[k] = Tn;
+                        const float Tn = T[k] - wgt;
+                        const bool acc = pass && Tn >= P.T_min;
+                        const bool stop = pass && !(Tn >= P.T_min);
+                        const float wa = acc ? wgt : 0.0f;
+                        cr[k] = fmaf(wa, g2.x, cr[k]);
+                        cg[k] = fmaf(wa, g2.y, cg[k]);
+                        cb[k] = fmaf(wa, g2.z, cb[k]);
+                        cd[k] = fmaf(wa, g1.z, cd[k]);
+                        T[k] = acc ? Tn : T[k];
+                        thr[k] = stop ? INF : thr[k];
                     }
                 }
             }
-            bool mine_done2 = true;
+            live = false;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) mine_done2 = mine_done2 && done[k];
-            if (!__syncthreads_or(!mine_done2)) goto finished;
+            for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
+            if (!__syncthreads_or(live)) goto finished;
         }
     }
 finished:

@@ -8,149 +8,177 @@
 // uses that renderer). The tile is the last, most significant digit of the
 // full key; the binning pass applies it as a stable counting sort.
 //
-// One block per segment, four 8-bit passes ping-ponging between the caller's
-// buffers and scratch. A pass whose digit is the same for every key of the
-// segment is skipped. Stability inside a pass: the block handles tiles of 4096
-// keys in order; warp w takes keys [w*256, w*256+256) of the tile in rounds of
-// 32, and a key's rank among equal digits before it is
-//   (equal digits in earlier warps of the tile) + (earlier rounds of its warp)
-//   + (lower lanes of its round, from __match_any_sync).
+// Four 8-bit passes, ping-ponging between the caller's buffers and scratch.
+// Every segment is cut into tiles of 2048 keys and each pass runs three
+// kernels over all tiles of all segments at once:
+//   k_sort_hist    -- digit histogram of every tile;
+//   k_sort_offsets -- per segment: where each (tile, digit) run starts
+//                     (digits in order, tiles in order within a digit);
+//   k_sort_scatter -- stable rank of each key among equal digits of its tile,
+//                     written at segment start + run start + rank.
+// Stable rank inside a tile: warp w takes keys [256 w, 256 w + 256) in rounds
+// of 32; a key's rank is (equal digits in earlier warps) + (equal digits in
+// earlier rounds of its warp) + (equal digits in lower lanes of its round,
+// from eight ballots over the digit bits).
 #include "gs_internal.cuh"
 
 namespace gsk {
 
 namespace {
 
-constexpr int NW = SORT_THREADS / 32;          // warps per block
-constexpr int TILE_KEYS = SORT_THREADS * SORT_IPT;
+constexpr int ST = 256;         // threads per sort block
+constexpr int SIPT = 8;         // keys per thread
+constexpr int TK = ST * SIPT;   // keys per tile
+constexpr int SNW = ST / 32;    // warps per block
 
-__global__ void __launch_bounds__(SORT_THREADS)
-    k_sort_segments(uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                    uint32_t *__restrict__ tkeys, uint32_t *__restrict__ tvals,
-                    const long long *__restrict__ seg_start, const long long *__restrict__ seg_count) {
-    const long long base = seg_start[blockIdx.x];
-    const long long n = seg_count[blockIdx.x];
-    if (n <= 1) return;
-    __shared__ uint32_t hist[4][256];
-    __shared__ uint32_t wcnt[NW][256];
-    __shared__ uint32_t dbase[256];
-    __shared__ uint32_t ttot[256];
+__device__ __forceinline__ int find_seg(const int *__restrict__ tile_start, int n_seg, int tile) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_start[mid] <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(ST)
+    k_sort_hist(const uint32_t *__restrict__ keys, const long long *__restrict__ seg_start,
+                const long long *__restrict__ seg_count, const int *__restrict__ tile_start,
+                int n_seg, int shift, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[256];
+    const int tile = blockIdx.x;
+    const int s = find_seg(tile_start, n_seg, tile);
+    const long long i0 = (long long)(tile - tile_start[s]) * TK;
+    const long long n = seg_count[s];
+    const uint32_t *k = keys + seg_start[s];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SIPT; ++r) {
+        const long long i = i0 + r * ST + threadIdx.x;
+        if (i < n) atomicAdd(&h[(k[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(long long)tile * 256 + threadIdx.x] = h[threadIdx.x];
+}
+
+// One block per segment; thread d owns digit d. In place: hist[tile][d]
+// becomes the offset (within the segment) of the run of digit d of that tile.
+__global__ void __launch_bounds__(256)
+    k_sort_offsets(const int *__restrict__ tile_start, uint32_t *__restrict__ hist) {
+    const int s = blockIdx.x, d = threadIdx.x, lane = d & 31, warp = d >> 5;
+    const int t0 = tile_start[s], t1 = tile_start[s + 1];
+    uint32_t run = 0;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = hist[(long long)t * 256 + d];
+        hist[(long long)t * 256 + d] = run;
+        run += c;
+    }
+    // exclusive scan of the digit totals
+    __shared__ uint32_t ws[8];
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) before += w < warp ? ws[w] : 0u;
+    const uint32_t base = before + incl - run;
+    for (int t = t0; t < t1; ++t) hist[(long long)t * 256 + d] += base;
+}
+
+__global__ void __launch_bounds__(ST)
+    k_sort_scatter(const uint32_t *__restrict__ sk, const uint32_t *__restrict__ sv,
+                   uint32_t *__restrict__ dk, uint32_t *__restrict__ dv,
+                   const long long *__restrict__ seg_start, const long long *__restrict__ seg_count,
+                   const int *__restrict__ tile_start, int n_seg, int shift,
+                   const uint32_t *__restrict__ offs) {
+    __shared__ uint32_t wcnt[SNW][256];
+    __shared__ uint32_t toff[256];
+    const int tile = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < 4 * 256; i += SORT_THREADS) (&hist[0][0])[i] = 0;
-    __syncthreads();
-    for (long long i = tid; i < n; i += SORT_THREADS) {
-        const uint32_t k = keys[base + i];
-        atomicAdd(&hist[0][k & 255u], 1u);
-        atomicAdd(&hist[1][(k >> 8) & 255u], 1u);
-        atomicAdd(&hist[2][(k >> 16) & 255u], 1u);
-        atomicAdd(&hist[3][k >> 24], 1u);
+    const int s = find_seg(tile_start, n_seg, tile);
+    const long long base = seg_start[s];
+    const long long i0 = (long long)(tile - tile_start[s]) * TK + (long long)warp * (32 * SIPT);
+    const long long n = seg_count[s];
+    toff[tid] = offs[(long long)tile * 256 + tid];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) wcnt[warp][lane * 8 + j] = 0;
+    uint32_t kr[SIPT], vr[SIPT], rk[SIPT];
+#pragma unroll
+    for (int r = 0; r < SIPT; ++r) {
+        const long long i = i0 + r * 32 + lane;
+        kr[r] = i < n ? sk[base + i] : 0u;
+        vr[r] = i < n ? sv[base + i] : 0u;
     }
-    __syncthreads();
-
-    uint32_t *sk = keys + base, *sv = vals + base;
-    uint32_t *dk = tkeys + base, *dv = tvals + base;
+    __syncwarp();
     const uint32_t lt = (1u << lane) - 1u;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 8 * pass;
-        // skip a pass whose digit is constant over the segment
-        __shared__ int trivial;
-        if (tid == 0) trivial = 0;
-        __syncthreads();
-        if (tid < 256 && (long long)hist[pass][tid] == n) trivial = 1;
-        __syncthreads();
-        const int skip = trivial;
-        __syncthreads();  // every thread has read the flag before it is reset
-        if (skip) continue;
-        // exclusive scan of the digit histogram (one warp, 8 digits per lane)
-        if (warp == 0) {
-            uint32_t loc[8], s = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                loc[j] = s;
-                s += hist[pass][lane * 8 + j];
-            }
-            uint32_t incl = s;
+    for (int r = 0; r < SIPT; ++r) {
+        const bool ok = i0 + r * 32 + lane < n;
+        const uint32_t d = (kr[r] >> shift) & 255u;
+        uint32_t peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += t;
-            }
-            const uint32_t ex = incl - s;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) dbase[lane * 8 + j] = ex + loc[j];
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
-        __syncthreads();
-        for (long long t0 = 0; t0 < n; t0 += TILE_KEYS) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) wcnt[warp][lane * 8 + j] = 0;
-            __syncwarp();
-            uint32_t kr[SORT_IPT], vr[SORT_IPT], rk[SORT_IPT];
-            // all loads of the warp's sub-tile first, so they are in flight together
-#pragma unroll
-            for (int r = 0; r < SORT_IPT; ++r) {
-                const long long i = t0 + (long long)warp * (32 * SORT_IPT) + r * 32 + lane;
-                kr[r] = i < n ? sk[i] : 0u;
-                vr[r] = i < n ? sv[i] : 0u;
-            }
-#pragma unroll
-            for (int r = 0; r < SORT_IPT; ++r) {
-                const long long i = t0 + (long long)warp * (32 * SORT_IPT) + r * 32 + lane;
-                const bool ok = i < n;
-                const uint32_t k = kr[r];
-                const uint32_t d = (k >> shift) & 255u;
-                const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 256u + lane);
-                const uint32_t before = wcnt[warp][d & 255u];
-                rk[r] = ok ? before + __popc(peers & lt) : 0xffffffffu;
-                __syncwarp();
-                if (ok && (__ffs(peers) - 1) == lane) wcnt[warp][d] = before + __popc(peers);
-                __syncwarp();
-            }
-            __syncthreads();
-            if (tid < 256) {
-                uint32_t run = 0;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const uint32_t c = wcnt[w][tid];
-                    wcnt[w][tid] = run;
-                    run += c;
-                }
-                ttot[tid] = run;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int r = 0; r < SORT_IPT; ++r) {
-                if (rk[r] != 0xffffffffu) {
-                    const uint32_t d = (kr[r] >> shift) & 255u;
-                    const uint32_t pos = dbase[d] + wcnt[warp][d] + rk[r];
-                    dk[pos] = kr[r];
-                    dv[pos] = vr[r];
-                }
-            }
-            __syncthreads();
-            if (tid < 256) dbase[tid] += ttot[tid];
-            __syncthreads();
-        }
-        uint32_t *t;
-        t = sk; sk = dk; dk = t;
-        t = sv; sv = dv; dv = t;
+        const uint32_t before = wcnt[warp][d];
+        rk[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (ok && (__ffs(peers) - 1) == lane) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
     }
-    // the sorted data must end in the caller's buffers
-    if (sk != keys + base) {
-        for (long long i = tid; i < n; i += SORT_THREADS) {
-            keys[base + i] = sk[i];
-            vals[base + i] = sv[i];
+    __syncthreads();
+    {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < SNW; ++w) {
+            const uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SIPT; ++r) {
+        if (i0 + r * 32 + lane < n) {
+            const uint32_t d = (kr[r] >> shift) & 255u;
+            const long long pos = base + toff[d] + wcnt[warp][d] + rk[r];
+            dk[pos] = kr[r];
+            dv[pos] = vr[r];
         }
     }
 }
 
 }  // namespace
 
+int sort_tiles_for(long long count) { return (int)((count + TK - 1) / TK); }
+
 cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
                                  uint32_t *tmp_vals, const long long *seg_start,
-                                 const long long *seg_count, int n_seg, cudaStream_t s) {
-    if (n_seg == 0) return cudaSuccess;
-    k_sort_segments<<<n_seg, SORT_THREADS, 0, s>>>(keys, vals, tmp_keys, tmp_vals, seg_start,
-                                                   seg_count);
+                                 const long long *seg_count, const int *tile_start, int n_seg,
+                                 int n_tiles, uint32_t *hist, cudaStream_t s) {
+    if (n_seg == 0 || n_tiles == 0) return cudaSuccess;
+    uint32_t *src_k = keys, *src_v = vals, *dst_k = tmp_keys, *dst_v = tmp_vals;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        k_sort_hist<<<n_tiles, ST, 0, s>>>(src_k, seg_start, seg_count, tile_start, n_seg, shift,
+                                           hist);
+        k_sort_offsets<<<n_seg, 256, 0, s>>>(tile_start, hist);
+        k_sort_scatter<<<n_tiles, ST, 0, s>>>(src_k, src_v, dst_k, dst_v, seg_start, seg_count,
+                                              tile_start, n_seg, shift, hist);
+        uint32_t *t;
+        t = src_k; src_k = dst_k; dst_k = t;
+        t = src_v; src_v = dst_v; dst_v = t;
+    }
+    // four passes: the sorted data is back in keys / vals
     return cudaGetLastError();
 }
 
