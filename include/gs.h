@@ -152,7 +152,7 @@ gs_status gs_scene_destroy(gs_context *ctx, int32_t scene_id);
  * per chunk of cameras (to size the workspace exactly), so when it returns
  * GS_OK every chunk but the last has completed and the last is enqueued.
  * Output buffers must not overlap the inputs. n_cams == 0 is a no-op.
- * Errors: INVALID_ARG, NOT_FOUND, CAPACITY (more than 7000 tiles per camera),
+ * Errors: INVALID_ARG, NOT_FOUND, CAPACITY (more than 65536 16x16 tiles per camera),
  * OOM, CUDA. */
 gs_status gs_render_batch(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
                           const float *viewmats, const float *intrinsics, int32_t width,

@@ -42,6 +42,12 @@ struct PinBuf {
 
 size_t dtype_size(int dt) { return dt == GS_F32 ? 4 : 2; }
 
+float __uint_as_float_host(uint32_t u) {
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 }  // namespace
 
 struct gs_context {
@@ -50,7 +56,7 @@ struct gs_context {
     std::vector<SceneSlot> scenes;
     DevBuf d_scenes;
     // chunk workspace
-    DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, crec, bitmap;
+    DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, bitmap;
     DevBuf cams, groups, blkpre, tilepre, segstart, segcount, stats, sorttiles, sorthist;
     // host-API staging
     DevBuf h_vm, h_in, h_rgb, h_depth, h_T;
@@ -151,6 +157,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     const gs_config &cfg = ctx->cfg;
     const int TX = (a.W + TILE - 1) / TILE, TY = (a.H + TILE - 1) / TILE;
     const int tiles = TX * TY;
+    const int nsup = ((TX + STILE - 1) / STILE) * ((TY + STILE - 1) / STILE);
     const int chunk_max = std::max(1, cfg.max_chunk_cameras);
     const int gmax = std::min(MAX_GROUP, std::max(1, cfg.camera_group));
     const ProjParams P{cfg.near_plane, cfg.dilation, cfg.guard_band, cfg.sigma_cull};
@@ -269,7 +276,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             ci.nw = (ci.count + 31) / 32;
             ci.bm_off = bm_words;
             S_total += ci.count;
-            bm_words += (long long)tiles * ci.nw;
+            bm_words += (long long)nsup * ci.nw;
             S.blkpre[s] = blocks;
             blocks += (ci.count + BIN_RANKS - 1) / BIN_RANKS;
             S.tilepre[s] = s * tiles;
@@ -288,7 +295,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         CKS(grow(ctx, ctx->vals, Sx * 4));
         CKS(grow(ctx, ctx->tkeys, Sx * 4));
         CKS(grow(ctx, ctx->tvals, Sx * 4));
-        CKS(grow(ctx, ctx->crec, Sx * sizeof(CRec)));
+        CKS(grow(ctx, ctx->rrect, Sx * sizeof(uint2)));
         CKS(grow(ctx, ctx->bitmap, (size_t)std::max<long long>(bm_words, 1) * 4));
         CKS(grow(ctx, ctx->sorthist, (size_t)std::max(sort_tiles, 1) * 256 * 4));
         CKC(cudaMemcpyAsync(ctx->cams.p, S.cams, m * sizeof(CamInfo), cudaMemcpyHostToDevice, a.st));
@@ -301,7 +308,8 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
                                  (const SceneDev *)ctx->d_scenes.p, (const CamInfo *)ctx->cams.p,
                                  a.vm, a.in, P, (const uint32_t *)ctx->masks.p,
                                  (const uint32_t *)ctx->woff.p, (SlotRec *)ctx->rec.p,
-                                 (uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p, a.st));
+                                 (uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
+                                 std::log(cfg.alpha_min), a.st));
         if (timing) CKC(cudaEventRecord(E[1], a.st));
         if (a.upto == UPTO_PROJECT) break;
         CKC(launch_sort_segments((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
@@ -310,14 +318,15 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
                                  (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
                                  m, sort_tiles, (uint32_t *)ctx->sorthist.p, a.st));
         if (timing) CKC(cudaEventRecord(E[2], a.st));
-        CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, tiles,
+        CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, nsup,
                        (const SlotRec *)ctx->rec.p, (const uint32_t *)ctx->vals.p,
-                       (CRec *)ctx->crec.p, (uint32_t *)ctx->bitmap.p,
-                       (unsigned long long *)ctx->stats.p + 2, std::log(cfg.alpha_min), a.st));
+                       (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p,
+                       (unsigned long long *)ctx->stats.p + 2, a.st));
         if (timing) CKC(cudaEventRecord(E[3], a.st));
         if (a.upto == UPTO_BIN) break;
         CKC(launch_composite((const CamInfo *)ctx->cams.p, (const int *)ctx->tilepre.p, m, m * tiles,
-                             (const CRec *)ctx->crec.p, (const uint32_t *)ctx->bitmap.p, C, a.rgb,
+                             (const SlotRec *)ctx->rec.p, (const uint32_t *)ctx->vals.p,
+                             (const uint2 *)ctx->rrect.p, (const uint32_t *)ctx->bitmap.p, C, a.rgb,
                              a.depth, a.T, (unsigned long long *)ctx->stats.p,
                              cfg.count_pairs != 0, cfg.pixels_per_thread, a.st));
         if (timing) {
@@ -423,7 +432,7 @@ void gs_context_destroy(gs_context *ctx) {
     for (auto &s : ctx->scenes)
         if (s.storage) cudaFree(s.storage);
     DevBuf *bufs[] = {&ctx->d_scenes, &ctx->masks, &ctx->woff,    &ctx->counts,  &ctx->rec,
-                      &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->crec,
+                      &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect,
                       &ctx->bitmap,   &ctx->cams,  &ctx->groups,  &ctx->blkpre,  &ctx->tilepre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
                       &ctx->sorttiles, &ctx->sorthist,
@@ -617,10 +626,22 @@ gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewm
     if (S > cap) return fail(ctx, GS_ERR_CAPACITY, "%lld survivors > cap %lld", S, (long long)cap);
     std::vector<SlotRec> h((size_t)S);
     if (S) CKC(cudaMemcpy(h.data(), ctx->rec.p, S * sizeof(SlotRec), cudaMemcpyDeviceToHost));
+    const float L2E = 1.4426950408889634f;
     for (long long i = 0; i < S; ++i) {
         const SlotRec &R = h[i];
-        const float v[12] = {R.a.x, R.a.y, R.a.z, R.a.w, R.b.x, R.b.y, R.b.z, R.b.w,
-                             R.c.x, R.c.y, R.c.z, 0.0f};
+        // undo the folding of the compositing constants (see SlotRec)
+        const float v[12] = {R.a.x,
+                             R.a.y,
+                             R.c.w,
+                             std::exp2(R.b.w),
+                             R.b.x / (-0.5f * L2E),
+                             R.b.y / (-L2E),
+                             R.b.z / (-0.5f * L2E),
+                             __uint_as_float_host(R.d.w),
+                             R.c.x,
+                             R.c.y,
+                             R.c.z,
+                             0.0f};
         memcpy(rec + 12 * i, v, sizeof(v));
         gidx[i] = (int32_t)R.d.z;
         rect[4 * i + 0] = (int32_t)(R.d.x & 0xffffu);
@@ -646,24 +667,36 @@ gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *vi
     CKS(render_impl(ctx, a));
     CKC(cudaStreamSynchronize(st));
     const long long S = ctx->last.survivors;
-    const int tiles = ((width + 15) / 16) * ((height + 15) / 16);
+    const int TX = (width + 15) / 16, TY = (height + 15) / 16, tiles = TX * TY;
+    const int SX = (TX + STILE - 1) / STILE, SY = (TY + STILE - 1) / STILE;
     const int nw = (int)((S + 31) / 32);
     std::vector<SlotRec> rec((size_t)S);
-    std::vector<uint32_t> vals((size_t)S), bm((size_t)tiles * nw);
+    std::vector<uint32_t> vals((size_t)S), bm((size_t)SX * SY * nw);
+    std::vector<uint2> rr((size_t)S);
     if (S) {
         CKC(cudaMemcpy(rec.data(), ctx->rec.p, S * sizeof(SlotRec), cudaMemcpyDeviceToHost));
         CKC(cudaMemcpy(vals.data(), ctx->vals.p, S * 4, cudaMemcpyDeviceToHost));
+        CKC(cudaMemcpy(rr.data(), ctx->rrect.p, S * sizeof(uint2), cudaMemcpyDeviceToHost));
         CKC(cudaMemcpy(bm.data(), ctx->bitmap.p, bm.size() * 4, cudaMemcpyDeviceToHost));
     }
+    // the compositing pass's reading of a tile's list: set bits of its
+    // super-tile's row in order, kept when the rank-ordered rect holds the tile
     long long k = 0;
     tile_off[0] = 0;
     for (int t = 0; t < tiles; ++t) {
+        const int tx = t % TX, ty = t / TX;
+        const uint32_t *row = bm.data() + (size_t)((ty / STILE) * SX + tx / STILE) * nw;
         for (int w = 0; w < nw; ++w) {
-            uint32_t word = bm[(size_t)t * nw + w];
+            uint32_t word = row[w];
             while (word) {
                 const int b = __builtin_ctz(word);
                 word &= word - 1u;
-                if (k < cap) gidx[k] = (int32_t)rec[vals[(size_t)w * 32 + b]].d.z;
+                const size_t r = (size_t)w * 32 + b;
+                const uint2 q = rr[r];
+                if (tx < (int)(q.x & 0xffffu) || tx > (int)(q.x >> 16) ||
+                    ty < (int)(q.y & 0xffffu) || ty > (int)(q.y >> 16))
+                    continue;
+                if (k < cap) gidx[k] = (int32_t)rec[vals[r]].d.z;
                 ++k;
             }
         }

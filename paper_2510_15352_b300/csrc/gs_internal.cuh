@@ -14,7 +14,7 @@ constexpr int MAX_GROUP = 32;       // cameras sharing one Gaussian load (<= war
 constexpr int PROJ_THREADS = 256;   // Gaussians per projection block (8 mask words)
 constexpr int BIN_RANKS = 256;      // depth ranks per binning block
 constexpr int BIN_WORDS = BIN_RANKS / 32;
-constexpr int MAX_TILES = 7000;     // tiles per camera (binning smem: 32 B per tile)
+constexpr int MAX_TILES = 65536;    // tiles per camera (binning smem: 2 B per tile)
 constexpr int COMP_BATCH = 128;     // Gaussian records staged per compositing sub-batch
 
 enum : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
@@ -48,8 +48,8 @@ struct CamInfo {
     int count;       // surviving Gaussians (after the scan)
     long long mask_off;  // first survival-mask word
     long long seg_off;   // first survivor slot
-    long long bm_off;    // first tile-bitmap word
-    int nw;          // bitmap words per tile row = ceil(count / 32)
+    long long bm_off;    // first super-tile bitmap word
+    int nw;          // bitmap words per super-tile row = ceil(count / 32)
     int pad;
 };
 
@@ -59,24 +59,22 @@ struct Group {
     long long n;
 };
 
-// A survivor's record in Gaussian-index order (64 B).
-//   a: u, v, z, opacity   b: A, B, C, r (conic + radius)
-//   c: red, green, blue, Sigma'_00      d: x0 | x1 << 16, y0 | y1 << 16, index, Sigma'_11 bits
+// A survivor's record (64 B), written by the projection pass in slot order
+// (Gaussian-index order within the camera), in the form the compositing pass
+// reads, with the constants folded so that p = a'dx^2 + b'dx dy + c'dy^2 + log2 o
+// is log2(o e^power):
+//   a: u, v, hx, hy      (hx, hy: half extents of the box around the region
+//                         alpha >= alpha_min, widened past float32 rounding;
+//                         negative when o < alpha_min)
+//   b: a' = -log2(e)/2 A, b' = -log2(e) B, c' = -log2(e)/2 C, log2(o)
+//   c: red, green, blue, z
+//   d: x0 | x1 << 16, y0 | y1 << 16 (tile rect), Gaussian index, radius (bits)
 struct __align__(16) SlotRec {
     float4 a, b, c;
     uint4 d;
 };
 
-// A survivor's compositing record in depth-rank order (48 B), with the
-// constants folded so that  p = a'dx^2 + b'dx dy + c'dy^2 + log2(o)  is
-// log2(o e^power):
-//   a: u, v, hx, hy    (half extents of the box around the alpha >= alpha_min
-//                       ellipse, with a float32 margin; < 0 when o < alpha_min)
-//   b: a' = -log2(e)/2 A, b' = -log2(e) B, c' = -log2(e)/2 C, log2(o)
-//   c: red, green, blue, z
-struct __align__(16) CRec {
-    float4 a, b, c;
-};
+constexpr int STILE = 4;  // tiles per super-tile edge (64 x 64 pixels)
 
 // ---- launchers (each defined in its kernel file) ----
 
@@ -93,7 +91,8 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
-                                 uint32_t *keys, uint32_t *vals, cudaStream_t s);
+                                 uint32_t *keys, uint32_t *vals, float ln_alpha_min,
+                                 cudaStream_t s);
 
 // Segmented sort: tile_start[n_seg + 1] is the prefix of sort_tiles_for(count)
 // over the segments; hist needs 256 uint32 per tile.
@@ -103,15 +102,17 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
                                  const long long *seg_count, const int *tile_start, int n_seg,
                                  int n_tiles, uint32_t *hist, cudaStream_t s);
 
+// Super-tile bitmaps (one row of ceil(count/32) words per 64x64-pixel
+// super-tile) and the rank-ordered tile rects.
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
-                       int max_tiles, const SlotRec *rec, const uint32_t *vals, CRec *crec,
-                       uint32_t *bitmap, unsigned long long *n_isect, float ln_alpha_min,
-                       cudaStream_t s);
+                       int n_super, const SlotRec *rec, const uint32_t *vals, uint2 *rrect,
+                       uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);
 
 // pixels_per_thread: 2 (128-thread blocks) or 4 (64-thread blocks)
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
-                             int n_tiles, const CRec *crec, const uint32_t *bitmap,
-                             CompParams C, float *rgb, float *depth, float *final_T,
+                             int n_tiles, const SlotRec *rec, const uint32_t *vals,
+                             const uint2 *rrect, const uint32_t *bitmap, CompParams C,
+                             float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
                              cudaStream_t s);
 

@@ -6,11 +6,13 @@
 // (columns c, c + 16/PPT, ...), so the per-Gaussian row terms (dy, c'dy^2 +
 // log2 o, b'dy) are shared by the thread's pixels. A warp covers 2*PPT rows.
 //
-// The tile's list is its bitmap row (bit r = the survivor of depth rank r
-// covers the tile). Each round reads one bitmap word per thread, turns the
-// set bits into a rank list in shared memory (block prefix of popcounts),
-// then stages the records of up to 128 ranks at a time in shared memory and
-// composites them. Per pixel and Gaussian:
+// The tile's list: each round reads one word per thread of its super-tile's
+// bitmap row (bit r = the survivor of depth rank r meets the 4x4-tile
+// super-tile), turns the set bits into candidate ranks in shared memory
+// (block prefix of popcounts), keeps the candidates whose exact tile rect
+// holds this tile (order-preserving ballot compaction), then stages up to 128
+// of their records at a time in shared memory and composites them. Per pixel
+// and Gaussian:
 //   p = a'dx^2 + b'dx dy + c'dy^2 + log2(o) = log2(o e^power)
 //   p < log2(alpha_min): skip;  alpha = min(alpha_max, 2^p)
 //   T' = T (1 - alpha); T' < T_min: the pixel stops (this Gaussian not added)
@@ -38,7 +40,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <int PPT, bool STATS>
 __global__ void __launch_bounds__(256 / PPT)
     k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
-                int n_slots, const CRec *__restrict__ crec, const uint32_t *__restrict__ bitmap,
+                int n_slots, const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
+                const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
                 CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
                 float *__restrict__ finalT, unsigned long long *__restrict__ stats) {
     constexpr int NT = 256 / PPT;    // threads per block
@@ -48,7 +51,8 @@ __global__ void __launch_bounds__(256 / PPT)
     // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits),
     // s2 = (red, green, blue, -)
     __shared__ float4 s0[COMP_BATCH], s1[COMP_BATCH], s2[COMP_BATCH];
-    __shared__ uint32_t slist[NT * 32];
+    __shared__ uint32_t cand[NT * 32];  // candidate ranks of one round, in order
+    __shared__ uint32_t kept[NT * 32];  // ranks of this tile's list, in order
     __shared__ uint32_t wsum[NWARP];
 
     int lo = 0, hi = n_slots - 1;
@@ -62,6 +66,7 @@ __global__ void __launch_bounds__(256 / PPT)
     const CamInfo ci = cams[lo];
     const int t = (int)blockIdx.x - tile_prefix[lo];
     const int tx = t % ci.TX, ty = t / ci.TX;
+    const int SX = (ci.TX + STILE - 1) / STILE;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int y = ty * TILE + tid / CPR;
     const float py = y + 0.5f;
@@ -83,16 +88,19 @@ __global__ void __launch_bounds__(256 / PPT)
     const uint32_t warp_bit = 1u << warp;
     unsigned long long ev = 0, al = 0;
 
-    const uint32_t *bm = bitmap + ci.bm_off + (long long)t * ci.nw;
-    const CRec *recs = crec + ci.seg_off;
+    const uint32_t *bm = bitmap + ci.bm_off + (long long)((ty / STILE) * SX + tx / STILE) * ci.nw;
+    const SlotRec *recs = rec + ci.seg_off;
+    const uint32_t *cv = vals + ci.seg_off;
+    const uint2 *crr = rrect + ci.seg_off;
     for (int wb = 0; wb < ci.nw; wb += NT) {
         bool live = false;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
         if (!__syncthreads_or(live)) break;
+        // 1. candidates: set bits of NT words of the super-tile row, in rank order
         const int w = wb + tid;
         uint32_t word = w < ci.nw ? bm[w] : 0u;
-        const uint32_t c = __popc(word);
+        uint32_t c = __popc(word);
         uint32_t incl = c;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -111,27 +119,56 @@ __global__ void __launch_bounds__(256 / PPT)
         uint32_t pos = before + incl - c;
         while (word) {
             const int bit = __ffs(word) - 1;
-            slist[pos++] = (uint32_t)w * 32u + (uint32_t)bit;
+            cand[pos++] = (uint32_t)w * 32u + (uint32_t)bit;
             word &= word - 1u;
         }
         __syncthreads();
-        for (uint32_t j0 = 0; j0 < total; j0 += COMP_BATCH) {
-            const int nb = (int)min((uint32_t)COMP_BATCH, total - j0);
+        // 2. keep the candidates whose rect holds this tile (order preserved)
+        uint32_t nkept = 0;
+        for (uint32_t q0 = 0; q0 < total; q0 += NT) {
+            const uint32_t q = q0 + tid;
+            bool keep = false;
+            uint32_t rk = 0;
+            if (q < total) {
+                rk = cand[q];
+                const uint2 rr = crr[rk];
+                keep = tx >= (int)(rr.x & 0xffffu) && tx <= (int)(rr.x >> 16) &&
+                       ty >= (int)(rr.y & 0xffffu) && ty <= (int)(rr.y >> 16);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) wsum[warp] = __popc(bal);
+            __syncthreads();
+            uint32_t wbefore = 0, wtotal = 0;
+#pragma unroll
+            for (int k = 0; k < NWARP; ++k) {
+                const uint32_t v = wsum[k];
+                wbefore += k < warp ? v : 0u;
+                wtotal += v;
+            }
+            if (keep) kept[nkept + wbefore + __popc(bal & ((1u << lane) - 1u))] = rk;
+            nkept += wtotal;
+            __syncthreads();
+        }
+        // 3. composite the kept records, COMP_BATCH at a time
+        for (uint32_t j0 = 0; j0 < nkept; j0 += COMP_BATCH) {
+            const int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
             for (int q = tid; q < nb; q += NT) {
-                const CRec R = recs[slist[j0 + q]];
+                const SlotRec &R = recs[cv[kept[j0 + q]]];
+                const float4 a = R.a;
                 // warps whose pixel rows meet the box of the alpha >= alpha_min region
                 const float x0 = tx * TILE + 0.5f, x1 = tx * TILE + TILE - 0.5f;
                 uint32_t m = 0;
-                if (R.a.x + R.a.z >= x0 && R.a.x - R.a.z <= x1) {
+                if (a.x + a.z >= x0 && a.x - a.z <= x1) {
 #pragma unroll
                     for (int k = 0; k < NWARP; ++k) {
                         const float y0 = ty * TILE + k * RPW + 0.5f, y1 = y0 + (RPW - 1);
-                        if (R.a.y + R.a.w >= y0 && R.a.y - R.a.w <= y1) m |= 1u << k;
+                        if (a.y + a.w >= y0 && a.y - a.w <= y1) m |= 1u << k;
                     }
                 }
-                s0[q] = make_float4(R.a.x, R.a.y, R.b.x, R.b.y);
-                s1[q] = make_float4(R.b.z, R.b.w, R.c.w, __uint_as_float(m));
-                s2[q] = R.c;
+                const float4 b = R.b, cc = R.c;
+                s0[q] = make_float4(a.x, a.y, b.x, b.y);
+                s1[q] = make_float4(b.z, b.w, cc.w, __uint_as_float(m));
+                s2[q] = cc;
             }
             __syncthreads();
             live = false;
@@ -211,31 +248,32 @@ finished:
 
 template <int PPT>
 cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots, int n_tiles,
-                       const CRec *crec, const uint32_t *bitmap, CompParams C, float *rgb,
-                       float *depth, float *final_T, unsigned long long *stats, bool collect,
-                       cudaStream_t s) {
+                       const SlotRec *rec, const uint32_t *vals, const uint2 *rrect,
+                       const uint32_t *bitmap, CompParams C, float *rgb, float *depth,
+                       float *final_T, unsigned long long *stats, bool collect, cudaStream_t s) {
     if (collect)
-        k_composite<PPT, true><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, crec,
-                                                             bitmap, C, rgb, depth, final_T, stats);
+        k_composite<PPT, true><<<n_tiles, 256 / PPT, 0, s>>>(
+            cams, tile_prefix, n_slots, rec, vals, rrect, bitmap, C, rgb, depth, final_T, stats);
     else
-        k_composite<PPT, false><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, crec,
-                                                              bitmap, C, rgb, depth, final_T, stats);
+        k_composite<PPT, false><<<n_tiles, 256 / PPT, 0, s>>>(
+            cams, tile_prefix, n_slots, rec, vals, rrect, bitmap, C, rgb, depth, final_T, stats);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
-                             int n_tiles, const CRec *crec, const uint32_t *bitmap,
-                             CompParams C, float *rgb, float *depth, float *final_T,
+                             int n_tiles, const SlotRec *rec, const uint32_t *vals,
+                             const uint2 *rrect, const uint32_t *bitmap, CompParams C,
+                             float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
                              cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
     if (pixels_per_thread == 4)
-        return launch_ppt<4>(cams, tile_prefix, n_slots, n_tiles, crec, bitmap, C, rgb, depth,
-                             final_T, stats, collect, s);
-    return launch_ppt<2>(cams, tile_prefix, n_slots, n_tiles, crec, bitmap, C, rgb, depth,
-                         final_T, stats, collect, s);
+        return launch_ppt<4>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
+                             rgb, depth, final_T, stats, collect, s);
+    return launch_ppt<2>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C, rgb,
+                         depth, final_T, stats, collect, s);
 }
 
 }  // namespace gsk

@@ -12,9 +12,12 @@
 //   k_project_mask  -- survival bit per (camera, Gaussian), one warp ballot per
 //                      32 Gaussians -> a 32-bit mask word;
 //   k_scan_masks    -- per camera, exclusive prefix of the mask popcounts;
-//   k_project_write -- recomputes the projection for surviving pairs only,
-//                      evaluates SH colour and writes the record, the depth key
-//                      (float bits of z) and the slot at a stable position.
+//   k_project_write -- stages the block's Gaussians (geometry and SH) in
+//                      shared memory, compacts the surviving (camera, Gaussian)
+//                      pairs into a dense item list, and for every item
+//                      recomputes the projection, evaluates the SH colour and
+//                      writes the record, the depth key (float bits of z) and
+//                      the slot at a stable position.
 // The decision chain is written with explicit fmaf / *_rn intrinsics so both
 // passes round identically.
 #include "gs_internal.cuh"
@@ -218,8 +221,8 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
 }
 
 // Colour of one Gaussian seen from camera c. The block's SH coefficients are
-// staged in shared memory as shs[(3k + ch) * PROJ_THREADS + thread].
-__device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg, int tid,
+// staged in shared memory as shs[(3k + ch) * PROJ_THREADS + local].
+__device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg, int local,
                                           const CamProj &c, const GaussGeo &G, float rgb[3]) {
     const int K = (deg + 1) * (deg + 1);
     float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
@@ -241,7 +244,7 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg
         float acc = 0.5f;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (k < K) acc = fmaf(shs[(3 * k + ch) * PROJ_THREADS + tid], Y[k], acc);
+            if (k < K) acc = fmaf(shs[(3 * k + ch) * PROJ_THREADS + local], Y[k], acc);
         rgb[ch] = fmaxf(acc, 0.0f);
     }
 }
@@ -321,71 +324,151 @@ __global__ void __launch_bounds__(1024)
     if (tid == 0) counts[blockIdx.x] = (int)carry;
 }
 
+constexpr int CAM_SUB = 8;  // cameras whose items are compacted at once
+constexpr float LOG2E = 1.4426950408889634f;
+
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project_write(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
                     const CamInfo *__restrict__ cams, const float *__restrict__ vms,
                     const float *__restrict__ intr, ProjParams P,
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
                     SlotRec *__restrict__ rec, uint32_t *__restrict__ keys,
-                    uint32_t *__restrict__ vals) {
+                    uint32_t *__restrict__ vals, float ln_alpha_min) {
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
     if (g0 >= gr.n) return;
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long moff[MAX_GROUP], soff[MAX_GROUP];
-    if ((int)threadIdx.x < gr.ncam) {
-        const CamInfo ci = cams[gr.slot0 + threadIdx.x];
-        cam_setup(cp[threadIdx.x], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H,
-                  P.guard);
-        moff[threadIdx.x] = ci.mask_off;
-        soff[threadIdx.x] = ci.seg_off;
+    __shared__ float sgeo[14][PROJ_THREADS];  // mean (3), M (9), smax2, opacity
+    __shared__ uint32_t smask[CAM_SUB * 8], swoff[CAM_SUB * 8], spos[CAM_SUB * 8];
+    __shared__ uint16_t items[CAM_SUB * PROJ_THREADS];
+    __shared__ uint32_t n_items;
+    extern __shared__ float shs[];  // SH: [(3k + ch)][PROJ_THREADS]
+    const int tid = threadIdx.x;
+    if (tid < gr.ncam) {
+        const CamInfo ci = cams[gr.slot0 + tid];
+        cam_setup(cp[tid], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H, P.guard);
+        moff[tid] = ci.mask_off;
+        soff[tid] = ci.seg_off;
     }
-    __syncthreads();
     const SceneDev sc = scenes[gr.scene];
-    const long long g = g0 + threadIdx.x;
-    const bool valid = g < gr.n;
-    const int lane = threadIdx.x & 31;
-    const bool warp_live = (g - lane) < gr.n;
-    // stage this block's SH coefficients: one coalesced row segment per (k, channel)
-    extern __shared__ float shs[];
-    const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
-    for (int k = 0; k < K3; ++k)
-        shs[k * PROJ_THREADS + threadIdx.x] = valid ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype) : 0.0f;
-    __syncthreads();
-    if (!warp_live) return;  // whole warp past the end: no mask words to read
-    GaussGeo G;
-    float opacity = 0.0f;
-    if (valid) {
-        load_geo(sc, g, G);
-        opacity = 1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype)));
-    }
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int c = 0; c < gr.ncam; ++c) {
-        const long long w = moff[c] + (g >> 5);
-        const uint32_t m = masks[w];
-        if (!((m >> lane) & 1u)) continue;
-        Proj pr;
-        if (!project(cp[c], G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
-            pr.x0 = 1;
-            pr.x1 = 0;
-            pr.y0 = 1;
-            pr.y1 = 0;
-            pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
+    {
+        const long long g = g0 + tid;
+        const bool valid = g < gr.n;
+        GaussGeo G;
+        float opacity = 0.0f;
+        if (valid) {
+            load_geo(sc, g, G);
+            opacity = 1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype)));
+        } else {
+            G.mx = G.my = G.mz = G.smax2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
         }
-        float rgb[3];
-        sh_colour(shs, sc.deg, threadIdx.x, cp[c], G, rgb);
-        const uint32_t slot = woff[w] + __popc(m & lt);
-        const long long at = soff[c] + slot;
-        SlotRec R;
-        R.a = make_float4(pr.u, pr.v, pr.z, opacity);
-        R.b = make_float4(pr.A, pr.B, pr.C, pr.r);
-        R.c = make_float4(rgb[0], rgb[1], rgb[2], pr.sa);
-        R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
-                         (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)g,
-                         __float_as_uint(pr.sc));
-        rec[at] = R;
-        keys[at] = __float_as_uint(pr.z);
-        vals[at] = slot;
+        sgeo[0][tid] = G.mx;
+        sgeo[1][tid] = G.my;
+        sgeo[2][tid] = G.mz;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sgeo[3 + k][tid] = G.M[k];
+        sgeo[12][tid] = G.smax2;
+        sgeo[13][tid] = opacity;
+        const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
+        for (int k = 0; k < K3; ++k)
+            shs[k * PROJ_THREADS + tid] =
+                valid ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype) : 0.0f;
+    }
+    __syncthreads();
+    // mask words of this block that exist (warps entirely past n have none)
+    const int nwords = (int)min(8LL, (gr.n - g0 + 31) >> 5);
+    for (int c0 = 0; c0 < gr.ncam; c0 += CAM_SUB) {
+        const int nc = min(CAM_SUB, gr.ncam - c0);
+        // (camera, word) entries: their masks, slot offsets and item positions
+        if (tid < 32) {
+            uint32_t cnt[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = tid * 2 + h, cl = e >> 3, w = e & 7;
+                uint32_t m = 0, wo = 0;
+                if (cl < nc && w < nwords) {
+                    const long long at = moff[c0 + cl] + (g0 >> 5) + w;
+                    m = masks[at];
+                    wo = woff[at];
+                }
+                smask[e] = m;
+                swoff[e] = wo;
+                cnt[h] = __popc(m);
+            }
+            const uint32_t pair = cnt[0] + cnt[1];
+            uint32_t incl = pair;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (tid >= d) incl += v;
+            }
+            const uint32_t ex = incl - pair;
+            spos[tid * 2] = ex;
+            spos[tid * 2 + 1] = ex + cnt[0];
+            if (tid == 31) n_items = incl;
+        }
+        __syncthreads();
+        if (tid < nc * 8) {
+            uint32_t m = smask[tid], pos = spos[tid];
+            const uint32_t hi = (uint32_t)(tid >> 3) << 8, lo = (uint32_t)(tid & 7) * 32u;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                items[pos++] = (uint16_t)(hi | (lo + b));
+                m &= m - 1u;
+            }
+        }
+        __syncthreads();
+        const int total = (int)n_items;
+        for (int i = tid; i < total; i += PROJ_THREADS) {
+            const int it = items[i];
+            const int cl = it >> 8, local = it & 255, w = local >> 5, bit = local & 31;
+            const int c = c0 + cl;
+            const int e = cl * 8 + w;
+            const uint32_t slot = swoff[e] + __popc(smask[e] & ((1u << bit) - 1u));
+            GaussGeo G;
+            G.mx = sgeo[0][local];
+            G.my = sgeo[1][local];
+            G.mz = sgeo[2][local];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) G.M[k] = sgeo[3 + k][local];
+            G.smax2 = sgeo[12][local];
+            const float opacity = sgeo[13][local];
+            Proj pr;
+            if (!project(cp[c], G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
+                pr.x0 = 1;
+                pr.x1 = 0;
+                pr.y0 = 1;
+                pr.y1 = 0;
+                pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
+            }
+            float rgb[3];
+            sh_colour(shs, sc.deg, local, cp[c], G, rgb);
+            // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o/alpha_min):
+            // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
+            // rounding of the per-pixel test can never pass a pixel outside it
+            const float q = 2.0f * (logf(opacity) - ln_alpha_min);
+            float hx = -1e30f, hy = -1e30f;
+            if (q >= 0.0f) {
+                hx = fmaf(1.001f, sqrtf(q * pr.sa), 0.01f);
+                hy = fmaf(1.001f, sqrtf(q * pr.sc), 0.01f);
+            }
+            const long long at = soff[c] + slot;
+            SlotRec R;
+            R.a = make_float4(pr.u, pr.v, hx, hy);
+            R.b = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C,
+                              log2f(opacity));
+            R.c = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
+            R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
+                             (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)(g0 + local),
+                             __float_as_uint(pr.r));
+            rec[at] = R;
+            keys[at] = __float_as_uint(pr.z);
+            vals[at] = slot;
+        }
+        __syncthreads();  // items / masks are rebuilt for the next cameras
     }
 }
 
@@ -413,7 +496,8 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
-                                 uint32_t *keys, uint32_t *vals, cudaStream_t s) {
+                                 uint32_t *keys, uint32_t *vals, float ln_alpha_min,
+                                 cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(max_blocks_x, n_groups);
     const int smem = 48 * PROJ_THREADS * (int)sizeof(float);  // SH of degree <= 3
@@ -421,7 +505,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, viewmats, intr, P,
-                                                     masks, woff, rec, keys, vals);
+                                                     masks, woff, rec, keys, vals, ln_alpha_min);
     return cudaGetLastError();
 }
 

@@ -336,7 +336,7 @@ def test_errors_are_reported(torch, gsmod, R):
     sid = R.add_scene(scene_from([[0, 0, 1.0]], [math.log(0.1)] * 3, [1, 0, 0, 0], 0.0))
     try:
         with pytest.raises(gsmod.GSError) as e:
-            R.render(sid, dev(torch, vm[None]), dev(torch, it[None]), 4096, 4096)
+            R.render(sid, dev(torch, vm[None]), dev(torch, it[None]), 4112, 4112)
         assert e.value.status == gsmod.GS_ERR_CAPACITY
     finally:
         R.remove_scene(sid)
