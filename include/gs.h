@@ -209,6 +209,28 @@ gs_status gs_sort_segments(gs_context *ctx, uint32_t *keys, uint32_t *vals, int6
                            const int64_t *seg_start, const int64_t *seg_count, int32_t n_seg,
                            void *stream);
 
+/* The segmented sort of gs_sort_segments for callers that cannot allocate
+ * GPU memory (code inside a graph or stream region it does not own, plugins of
+ * a host application that owns every device allocation, loops that forbid
+ * allocation after start-up). The paper has no counterpart: this is a service
+ * of this library. It takes no context and allocates nothing: its scratch
+ * (temporary keys and values, tile table, histograms) is one file-scope device
+ * array of about 22 MB that every GPU loading this library holds until the
+ * process exits.
+ *   keys, vals  DEVICE [n] uint32, sorted in place within each segment
+ *               (stable, ascending keys; vals move with their keys)
+ *   seg_start, seg_count  DEVICE [n_seg] int64; a segment outside [0, n) is
+ *               treated as empty; segments must not overlap
+ * Limits: n <= 2,097,152 keys and n_seg <= 4,096 segments, else
+ * GS_ERR_CAPACITY with nothing done. The first call on a device looks up the
+ * array's device address (a CUDA runtime query): make it before any stream
+ * capture. All calls share the array and it keeps the last call's contents,
+ * so calls that may overlap on the GPU (other streams or host threads) race
+ * and must be serialised by the caller. Work is enqueued on `stream`. */
+gs_status gs_sort_segments_noalloc(uint32_t *keys, uint32_t *vals, int64_t n,
+                                   const int64_t *seg_start, const int64_t *seg_count,
+                                   int32_t n_seg, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

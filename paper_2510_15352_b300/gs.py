@@ -72,6 +72,7 @@ SIGNATURES = {
     "gs_debug_tile_lists": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _i64,
                                            ctypes.POINTER(_i64), _vp]),
     "gs_sort_segments": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
+    "gs_sort_segments_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i32, _vp]),
 }
 
 
@@ -107,6 +108,7 @@ gs_get_stats = lib.gs_get_stats
 gs_debug_project = lib.gs_debug_project
 gs_debug_tile_lists = lib.gs_debug_tile_lists
 gs_sort_segments = lib.gs_sort_segments
+gs_sort_segments_noalloc = lib.gs_sort_segments_noalloc
 
 
 class GSError(RuntimeError):
