@@ -39,6 +39,18 @@ WORKLOAD = "single_1m_sh3_1024cam_640x480"
 F_PAIR = 22
 # FP32 peak of one B300: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz max clock
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# DRAM bytes (read + write) of one compositing launch from the ncu capture summarised in
+# profiles/k_composite_single_1m_sh3_16cam_640x480.md (16 cameras, scaled per camera), valid
+# only for the kernel source it was taken on (sha256 prefix below).
+TRAFFIC_SRC_SHA = "17cb9c487ff8022a"
+TRAFFIC_BYTES_PER_CAMERA = (2.673920e6 + 24.918784e6) / 16
+
+
+def composite_traffic(cams_per_launch: float):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2510_15352_b300", "csrc", "k_composite.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return TRAFFIC_BYTES_PER_CAMERA * cams_per_launch if sha == TRAFFIC_SRC_SHA else None
 
 
 def env_rank():
@@ -250,7 +262,9 @@ def run_b300(args):
             "roofline": {
                 "kernel": "k_composite", "bound": "alu", "achieved": achieved,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None, "traffic": None,
+                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None,
+                "traffic": composite_traffic(n / max(n_chunks / args.steps, 1)),
+                "traffic_unit": "bytes per launch (ncu capture scaled by cameras)",
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
                 "ms_per_launch": comp_ms_per_launch,
                 "launches_per_step": n_chunks / args.steps,
