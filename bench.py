@@ -274,6 +274,9 @@ def run_b300(args):
             },
             "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "stats": {"survivors_per_step": cst["survivors"],
+                      "composite_warp_iters": cst["warp_iters"],
+                      "composite_warp_iters_box": cst["warp_iters_box"],
+                      "composite_warp_iters_blend": cst["warp_iters_blend"],
                       "intersections_per_step": cst["intersections"]},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         }

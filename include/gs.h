@@ -107,7 +107,11 @@ typedef struct gs_stats {
     float ms_bin;
     float ms_composite;
     float ms_total;
-    int32_t reserved[4];
+    int32_t reserved0;
+    int64_t warp_iters;       /* compositing (warp, Gaussian) iterations of warps with live
+                                 pixels; only with count_pairs */
+    int64_t warp_iters_box;   /* of those, Gaussians whose alpha box meets the warp's rows */
+    int64_t warp_iters_blend; /* of those, Gaussians some lane of the warp blends */
 } gs_stats;
 
 typedef struct gs_context gs_context;

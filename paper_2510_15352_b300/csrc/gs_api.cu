@@ -173,8 +173,8 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
 
     gs_stats st{};
     st.n_cameras = a.n;
-    CKS(grow(ctx, ctx->stats, 4 * sizeof(unsigned long long)));
-    CKC(cudaMemsetAsync(ctx->stats.p, 0, 4 * sizeof(unsigned long long), a.st));
+    CKS(grow(ctx, ctx->stats, 8 * sizeof(unsigned long long)));
+    CKC(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), a.st));
     const size_t stage_bytes =
         align_up((size_t)chunk_max * sizeof(CamInfo), 256) + align_up((size_t)chunk_max * sizeof(Group), 256) +
         4 * align_up((size_t)(chunk_max + 1) * sizeof(int), 256) +
@@ -367,7 +367,7 @@ gs_status validate(gs_context *ctx, int n, const int32_t *scene_ids, const void 
 
 extern "C" {
 
-int32_t gs_abi_version(void) { return 1; }
+int32_t gs_abi_version(void) { return 2; }
 
 const char *gs_status_string(gs_status s) {
     switch (s) {
@@ -581,11 +581,14 @@ gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
     if (!ctx || !out) return GS_ERR_INVALID_ARG;
     if (ctx->stats_pending && ctx->stats.p) {
         CKC(cudaSetDevice(ctx->device));
-        unsigned long long h[4];
+        unsigned long long h[8];
         CKC(cudaMemcpy(h, ctx->stats.p, sizeof(h), cudaMemcpyDeviceToHost));
         ctx->last.pairs_evaluated = (int64_t)h[0];
         ctx->last.pairs_alpha = (int64_t)h[1];
         ctx->last.intersections = (int64_t)h[2];
+        ctx->last.warp_iters = (int64_t)h[3];
+        ctx->last.warp_iters_box = (int64_t)h[4];
+        ctx->last.warp_iters_blend = (int64_t)h[5];
         float ms[4] = {0, 0, 0, 0};
         for (int c = 0; c < ctx->ev_used; ++c) {
             cudaEvent_t *E = &ctx->ev[5 * c];

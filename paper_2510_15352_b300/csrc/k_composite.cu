@@ -51,8 +51,9 @@ __global__ void __launch_bounds__(256 / PPT)
     // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits),
     // s2 = (red, green, blue, -)
     __shared__ float4 s0[COMP_BATCH], s1[COMP_BATCH], s2[COMP_BATCH];
-    __shared__ uint32_t cand[NT * 32];  // candidate ranks of one round, in order
-    __shared__ uint32_t kept[NT * 32];  // ranks of this tile's list, in order
+    // candidate ranks of one round in order; compacted in place to the ranks of
+    // this tile's list (a kept candidate only moves to a lower index)
+    __shared__ uint32_t cand[NT * 32];
     __shared__ uint32_t wsum[NWARP];
 
     int lo = 0, hi = n_slots - 1;
@@ -74,19 +75,17 @@ __global__ void __launch_bounds__(256 / PPT)
     // Per pixel: T, colour, depth and its own alpha threshold; a pixel that has
     // stopped (or lies outside the image) has threshold +inf, so it passes no
     // further alpha test and its state stays frozen without a branch.
-    float px[PPT], T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT], thr[PPT];
-    bool in[PPT];
+    float T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT], thr[PPT];
+    const int x0 = tx * TILE + tid % CPR;  // pixel k of this thread is x0 + k * CPR
+    const float px0 = x0 + 0.5f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int x = tx * TILE + tid % CPR + k * CPR;
-        px[k] = x + 0.5f;
-        in[k] = x < ci.W && y < ci.H;
-        thr[k] = in[k] ? P.log2_alpha_min : INF;
+        thr[k] = (x0 + k * CPR < ci.W && y < ci.H) ? P.log2_alpha_min : INF;
         T[k] = 1.0f;
         cr[k] = cg[k] = cb[k] = cd[k] = 0.0f;
     }
     const uint32_t warp_bit = 1u << warp;
-    unsigned long long ev = 0, al = 0;
+    unsigned long long ev = 0, al = 0, wi = 0, wbox = 0, wbl = 0;
 
     const uint32_t *bm = bitmap + ci.bm_off + (long long)((ty / STILE) * SX + tx / STILE) * ci.nw;
     const SlotRec *recs = rec + ci.seg_off;
@@ -145,7 +144,7 @@ __global__ void __launch_bounds__(256 / PPT)
                 wbefore += k < warp ? v : 0u;
                 wtotal += v;
             }
-            if (keep) kept[nkept + wbefore + __popc(bal & ((1u << lane) - 1u))] = rk;
+            if (keep) cand[nkept + wbefore + __popc(bal & ((1u << lane) - 1u))] = rk;
             nkept += wtotal;
             __syncthreads();
         }
@@ -153,7 +152,7 @@ __global__ void __launch_bounds__(256 / PPT)
         for (uint32_t j0 = 0; j0 < nkept; j0 += COMP_BATCH) {
             const int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
             for (int q = tid; q < nb; q += NT) {
-                const SlotRec &R = recs[cv[kept[j0 + q]]];
+                const SlotRec &R = recs[cv[cand[j0 + q]]];
                 const float4 a = R.a;
                 // warps whose pixel rows meet the box of the alpha >= alpha_min region
                 const float x0 = tx * TILE + 0.5f, x1 = tx * TILE + TILE - 0.5f;
@@ -181,20 +180,24 @@ __global__ void __launch_bounds__(256 / PPT)
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) ev += thr[k] != INF ? 1u : 0u;
                     }
+                    if (STATS) wi++;
                     if (!(__float_as_uint(g1.w) & warp_bit)) continue;  // warp-uniform
+                    if (STATS) wbox++;
                     const float4 g0 = s0[j];  // u, v, a', b'
                     const float dy = py - g0.y;
                     const float base = fmaf(g1.x * dy, dy, g1.y);
                     const float bdy = g0.w * dy;
                     float p[PPT];
                     bool any = false;
+                    const float dx0 = px0 - g0.x;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float dx = px[k] - g0.x;
+                        const float dx = dx0 + (float)(k * CPR);
                         p[k] = fmaf(fmaf(g0.z, dx, bdy), dx, base);
                         any = any || p[k] >= thr[k];
                     }
                     if (!__any_sync(0xffffffffu, any)) continue;
+                    if (STATS) wbl++;
                     const float4 g2 = s2[j];  // red, green, blue
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
@@ -224,8 +227,8 @@ __global__ void __launch_bounds__(256 / PPT)
 finished:
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        if (!in[k]) continue;
-        const int x = tx * TILE + tid % CPR + k * CPR;
+        const int x = x0 + k * CPR;
+        if (x >= ci.W || y >= ci.H) continue;
         const long long pix = ((long long)ci.user * ci.H + y) * ci.W + x;
         rgb[3 * pix + 0] = fmaf(T[k], P.bg[0], cr[k]);
         rgb[3 * pix + 1] = fmaf(T[k], P.bg[1], cg[k]);
@@ -242,6 +245,9 @@ finished:
         if (lane == 0) {
             atomicAdd(&stats[0], ev);
             atomicAdd(&stats[1], al);
+            atomicAdd(&stats[3], wi);  // per warp: the same count on every lane
+            atomicAdd(&stats[4], wbox);
+            atomicAdd(&stats[5], wbl);
         }
     }
 }

@@ -15,7 +15,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgs_b300.so")
-ABI_VERSION = 1
+ABI_VERSION = 2
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, \
     GS_ERR_NOT_FOUND = range(7)
@@ -47,7 +47,9 @@ class gs_stats(ctypes.Structure):
                 ("pairs_alpha", ctypes.c_int64), ("n_chunks", ctypes.c_int32),
                 ("ms_project", ctypes.c_float), ("ms_sort", ctypes.c_float),
                 ("ms_bin", ctypes.c_float), ("ms_composite", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
+                ("ms_total", ctypes.c_float), ("reserved0", ctypes.c_int32),
+                ("warp_iters", ctypes.c_int64), ("warp_iters_box", ctypes.c_int64),
+                ("warp_iters_blend", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); the same set as include/gs.h declares
@@ -239,7 +241,7 @@ class Renderer:
     def stats(self) -> dict:
         s = gs_stats()
         self._check(gs_get_stats(self.ctx, ctypes.byref(s)))
-        return {k: getattr(s, k) for k, _ in gs_stats._fields_ if k != "reserved"}
+        return {k: getattr(s, k) for k, _ in gs_stats._fields_ if not k.startswith("reserved")}
 
     # ------------------------------------------------------------- inspection
     def debug_project(self, sid: int, viewmat, intr, W: int, H: int, cap: int):
