@@ -18,9 +18,11 @@
 //   T' = T (1 - alpha); T' < T_min: the pixel stops (this Gaussian not added)
 //   C += alpha T rgb, D += alpha T z, T = T'.
 // Instruction economy (the kernel is issue-bound): when a record is staged,
-// the warps whose pixel rows meet the box of its alpha >= alpha_min region are
-// marked, and other warps skip it (uniform branch; the box is widened past
-// float32 rounding, so the skip never changes a result); the blend runs only
+// the warps some pixel of which can pass its alpha test are marked (the box of
+// its alpha >= alpha_min region meets the warp's rows, and the largest value of
+// the quadratic over the rows' pixel-centre rectangle reaches the threshold);
+// other warps skip it (uniform branch; both tests have margins past float32
+// rounding, so the skip never changes a result); the blend runs only
 // when some lane passes the alpha test (warp vote) and is branch-free: a
 // stopped pixel's alpha threshold becomes +inf, which freezes it. The block
 // stops reading its list once every pixel has stopped. No tensor cores: this
@@ -35,6 +37,30 @@ __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Largest value over the rectangle [X0, X1] x [Y0, Y1] of the concave quadratic
+// p(x, y) = a dx^2 + b dx dy + c dy^2 + l (dx = x - u, dy = y - v; a, c < 0): the
+// centre value when (u, v) lies inside, else the best of the four edges, each a
+// 1-D concave quadratic whose vertex is clamped to the edge.
+__device__ __forceinline__ float max_p_rect(float u, float v, float a, float b, float c, float l,
+                                            float X0, float X1, float Y0, float Y1) {
+    if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return l;
+    const float ia = -0.5f / a, ic = -0.5f / c;
+    float best = -__int_as_float(0x7f800000);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = (e ? X1 : X0) - u;
+        const float dy = fminf(fmaxf(v + b * dx * ic, Y0), Y1) - v;
+        best = fmaxf(best, fmaf(fmaf(a, dx, b * dy), dx, fmaf(c * dy, dy, l)));
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dy = (e ? Y1 : Y0) - v;
+        const float dx = fminf(fmaxf(u + b * dy * ia, X0), X1) - u;
+        best = fmaxf(best, fmaf(fmaf(a, dx, b * dy), dx, fmaf(c * dy, dy, l)));
+    }
+    return best;
 }
 
 template <int PPT, bool STATS>
@@ -153,18 +179,29 @@ __global__ void __launch_bounds__(256 / PPT)
             const int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
             for (int q = tid; q < nb; q += NT) {
                 const SlotRec &R = recs[cv[cand[j0 + q]]];
-                const float4 a = R.a;
-                // warps whose pixel rows meet the box of the alpha >= alpha_min region
+                const float4 a = R.a, b = R.b, cc = R.c;
+                // warps some pixel of which can pass the alpha test: the box of the
+                // alpha >= alpha_min region meets the warp's rows and the largest p
+                // over the rows' pixel-centre rectangle reaches the threshold (with a
+                // margin past float32 rounding, so no passing pair is skipped)
                 const float x0 = tx * TILE + 0.5f, x1 = tx * TILE + TILE - 0.5f;
                 uint32_t m = 0;
                 if (a.x + a.z >= x0 && a.x - a.z <= x1) {
 #pragma unroll
                     for (int k = 0; k < NWARP; ++k) {
                         const float y0 = ty * TILE + k * RPW + 0.5f, y1 = y0 + (RPW - 1);
-                        if (a.y + a.w >= y0 && a.y - a.w <= y1) m |= 1u << k;
+                        if (!(a.y + a.w >= y0 && a.y - a.w <= y1)) continue;
+                        // float32 error of p grows with its terms' size: bound them
+                        const float DX = fmaxf(fabsf(x0 - a.x), fabsf(x1 - a.x));
+                        const float DY = fmaxf(fabsf(y0 - a.y), fabsf(y1 - a.y));
+                        const float terms = fmaf(fabsf(b.x), DX * DX,
+                                                 fmaf(fabsf(b.y), DX * DY, fabsf(b.z) * DY * DY));
+                        const float margin = fmaf(1e-6f, terms, 1e-3f);
+                        if (max_p_rect(a.x, a.y, b.x, b.y, b.z, b.w, x0, x1, y0, y1) >=
+                            P.log2_alpha_min - margin)
+                            m |= 1u << k;
                     }
                 }
-                const float4 b = R.b, cc = R.c;
                 s0[q] = make_float4(a.x, a.y, b.x, b.y);
                 s1[q] = make_float4(b.z, b.w, cc.w, __uint_as_float(m));
                 s2[q] = cc;
