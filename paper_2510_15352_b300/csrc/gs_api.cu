@@ -56,7 +56,7 @@ struct gs_context {
     std::vector<SceneSlot> scenes;
     DevBuf d_scenes;
     // chunk workspace
-    DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, bitmap;
+    DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, srect, bitmap;
     DevBuf cams, groups, blkpre, tilepre, segstart, segcount, stats, sorttiles, sorthist;
     // host-API staging
     DevBuf h_vm, h_in, h_rgb, h_depth, h_T;
@@ -296,6 +296,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         CKS(grow(ctx, ctx->tkeys, Sx * 4));
         CKS(grow(ctx, ctx->tvals, Sx * 4));
         CKS(grow(ctx, ctx->rrect, Sx * sizeof(uint2)));
+        CKS(grow(ctx, ctx->srect, Sx * sizeof(uint2)));
         CKS(grow(ctx, ctx->bitmap, (size_t)std::max<long long>(bm_words, 1) * 4));
         CKS(grow(ctx, ctx->sorthist, (size_t)std::max(sort_tiles, 1) * 256 * 4));
         CKC(cudaMemcpyAsync(ctx->cams.p, S.cams, m * sizeof(CamInfo), cudaMemcpyHostToDevice, a.st));
@@ -308,8 +309,8 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
                                  (const SceneDev *)ctx->d_scenes.p, (const CamInfo *)ctx->cams.p,
                                  a.vm, a.in, P, (const uint32_t *)ctx->masks.p,
                                  (const uint32_t *)ctx->woff.p, (SlotRec *)ctx->rec.p,
-                                 (uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
-                                 std::log(cfg.alpha_min), a.st));
+                                 (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p,
+                                 (uint32_t *)ctx->vals.p, std::log(cfg.alpha_min), a.st));
         if (timing) CKC(cudaEventRecord(E[1], a.st));
         if (a.upto == UPTO_PROJECT) break;
         CKC(launch_sort_segments((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
@@ -319,7 +320,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
                                  m, sort_tiles, (uint32_t *)ctx->sorthist.p, a.st));
         if (timing) CKC(cudaEventRecord(E[2], a.st));
         CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, nsup,
-                       (const SlotRec *)ctx->rec.p, (const uint32_t *)ctx->vals.p,
+                       (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->vals.p,
                        (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p,
                        (unsigned long long *)ctx->stats.p + 2, a.st));
         if (timing) CKC(cudaEventRecord(E[3], a.st));
@@ -432,7 +433,7 @@ void gs_context_destroy(gs_context *ctx) {
     for (auto &s : ctx->scenes)
         if (s.storage) cudaFree(s.storage);
     DevBuf *bufs[] = {&ctx->d_scenes, &ctx->masks, &ctx->woff,    &ctx->counts,  &ctx->rec,
-                      &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect,
+                      &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect, &ctx->srect,
                       &ctx->bitmap,   &ctx->cams,  &ctx->groups,  &ctx->blkpre,  &ctx->tilepre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
                       &ctx->sorttiles, &ctx->sorthist,

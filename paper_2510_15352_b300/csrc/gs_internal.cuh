@@ -91,8 +91,8 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
-                                 uint32_t *keys, uint32_t *vals, float ln_alpha_min,
-                                 cudaStream_t s);
+                                 uint2 *srect, uint32_t *keys, uint32_t *vals,
+                                 float ln_alpha_min, cudaStream_t s);
 
 // Segmented sort: tile_start[n_seg + 1] is the prefix of sort_tiles_for(count)
 // over the segments; hist needs 256 uint32 per tile.
@@ -105,7 +105,7 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
 // Super-tile bitmaps (one row of ceil(count/32) words per 64x64-pixel
 // super-tile) and the rank-ordered tile rects.
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
-                       int n_super, const SlotRec *rec, const uint32_t *vals, uint2 *rrect,
+                       int n_super, const uint2 *srect, const uint32_t *vals, uint2 *rrect,
                        uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);
 
 // pixels_per_thread: 2 (128-thread blocks) or 4 (64-thread blocks)

@@ -23,7 +23,7 @@ namespace {
 
 __global__ void __launch_bounds__(BIN_RANKS)
     k_bin(const CamInfo *__restrict__ cams, const int *__restrict__ blk_prefix, int n_slots,
-          const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
+          const uint2 *__restrict__ srect, const uint32_t *__restrict__ vals,
           uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
           unsigned long long *__restrict__ n_isect) {
     extern __shared__ uint32_t sbm[];  // [super-tiles][BIN_WORDS]
@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(BIN_RANKS)
     unsigned long long area = 0;
     if (r < ci.count) {
         const uint32_t slot = vals[ci.seg_off + r];
-        const uint4 d = rec[ci.seg_off + slot].d;
-        rrect[ci.seg_off + r] = make_uint2(d.x, d.y);
+        const uint2 d = srect[ci.seg_off + slot];
+        rrect[ci.seg_off + r] = d;
         const int x0 = (int)(d.x & 0xffffu), x1 = (int)(d.x >> 16);
         const int y0 = (int)(d.y & 0xffffu), y1 = (int)(d.y >> 16);
         if (x1 >= x0 && y1 >= y0) {
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(BIN_RANKS)
 }  // namespace
 
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
-                       int n_super, const SlotRec *rec, const uint32_t *vals, uint2 *rrect,
+                       int n_super, const uint2 *srect, const uint32_t *vals, uint2 *rrect,
                        uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
     const size_t smem = (size_t)n_super * BIN_WORDS * sizeof(uint32_t);
@@ -82,7 +82,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, 
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_bin<<<n_blocks, BIN_RANKS, smem, s>>>(cams, blk_prefix, n_slots, rec, vals, rrect, bitmap,
+    k_bin<<<n_blocks, BIN_RANKS, smem, s>>>(cams, blk_prefix, n_slots, srect, vals, rrect, bitmap,
                                             n_isect);
     return cudaGetLastError();
 }

@@ -26,7 +26,8 @@ namespace gsk {
 
 namespace {
 
-struct CamProj {
+// 28 words = 7 float4 (loaded as such from shared memory)
+struct __align__(16) CamProj {
     float R[9], t[3];
     float fx, fy, cx, cy;
     float lxp, lxn, lyp, lyn;  // guard-band limits of x/z and y/z
@@ -35,6 +36,16 @@ struct CamProj {
     float W, H;
     int TX, TY;
 };
+static_assert(sizeof(CamProj) == 7 * 16, "CamProj is seven float4");
+
+__device__ __forceinline__ CamProj load_cam(const CamProj &src) {
+    CamProj c;
+    const float4 *s4 = reinterpret_cast<const float4 *>(&src);
+    float4 *d4 = reinterpret_cast<float4 *>(&c);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) d4[k] = s4[k];
+    return c;
+}
 
 struct GaussGeo {
     float mx, my, mz;
@@ -47,6 +58,19 @@ struct Proj {
     float sa, sc;  // 2D covariance diagonal (with the dilation)
     int x0, x1, y0, y1;
 };
+
+// Hardware approximations (PTX rcp/sqrt .approx): a few ulp, far inside the
+// parity tolerances. Both projection passes run these same instructions.
+__device__ __forceinline__ float rcp_a(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_a(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 __device__ __forceinline__ float ldv(const void *p, long long i, int dt) {
     if (dt == DT_F32) return __ldg(reinterpret_cast<const float *>(p) + i);
@@ -130,15 +154,15 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     const float z = fmaf(c.R[6], G.mx, fmaf(c.R[7], G.my, fmaf(c.R[8], G.mz, c.t[2])));
     o.z = z;
     if (!(z > P.near_plane)) return false;
-    const float iz = __fdiv_rn(1.0f, z);
+    const float iz = rcp_a(z);
     const float xz = __fmul_rn(px, iz), yz = __fmul_rn(py, iz);
     const float u = fmaf(c.fx, xz, c.cx), v = fmaf(c.fy, yz, c.cy);
     // Early cull with a bound of the radius: lambda_max(Sigma') <= |J|_F^2 s_max^2 + dil
-    // and |J|_F^2 <= kk / z^2 over the guard band; the 1.001 and +0.01 px margins keep
+    // and |J|_F^2 <= kk / z^2 over the guard band; the 1.002 and +0.02 px margins keep
     // rb above the float32 radius, so this culls only what the exact test culls.
     {
-        const float rb = fmaf(1.001f * P.sigma,
-                              sqrtf(fmaf(c.kk * iz * iz, G.smax2, P.dilation)), 0.01f);
+        const float rb = fmaf(1.002f * P.sigma,
+                              sqrt_a(fmaf(c.kk * iz * iz, G.smax2, P.dilation)), 0.02f);
         if (u + rb < 0.0f || u - rb >= c.W || v + rb < 0.0f || v - rb >= c.H) return false;
     }
     const float xc = fminf(fmaxf(xz, -c.lxn), c.lxp);
@@ -163,8 +187,8 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     const float dil = P.dilation;
     const float a = __fadd_rn(s00, dil), cc = __fadd_rn(s11, dil), b = s01;
     const float hd = __fmul_rn(0.5f, __fsub_rn(a, cc));
-    const float lmax = fmaf(0.5f, __fadd_rn(a, cc), __fsqrt_rn(fmaf(hd, hd, __fmul_rn(b, b))));
-    const float r = __fmul_rn(P.sigma, __fsqrt_rn(lmax));
+    const float lmax = fmaf(0.5f, __fadd_rn(a, cc), sqrt_a(fmaf(hd, hd, __fmul_rn(b, b))));
+    const float r = __fmul_rn(P.sigma, sqrt_a(lmax));
     if (!(__fadd_rn(u, r) >= 0.0f) || !(__fsub_rn(u, r) < c.W) || !(__fadd_rn(v, r) >= 0.0f) ||
         !(__fsub_rn(v, r) < c.H))
         return false;
@@ -178,7 +202,7 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     const float e2 = fmaf(g0[0], g1[1], -__fmul_rn(g0[1], g1[0]));
     const float det = fmaf(dil, __fadd_rn(__fadd_rn(s00, s11), dil),
                            fmaf(e0, e0, fmaf(e1, e1, __fmul_rn(e2, e2))));
-    const float idet = __fdiv_rn(1.0f, det);
+    const float idet = rcp_a(det);
     o.A = cc * idet;
     o.B = -b * idet;
     o.C = a * idet;
@@ -274,7 +298,8 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     if (valid) load_geo(sc, g, G);
     for (int c = 0; c < gr.ncam; ++c) {
         Proj pr;
-        const bool s = valid && project(cp[c], G, P, pr);
+        const CamProj cam = load_cam(cp[c]);
+        const bool s = valid && project(cam, G, P, pr);
         const unsigned b = __ballot_sync(0xffffffffu, s);
         if (lane == 0 && warp_live) masks[moff[c] + (g >> 5)] = b;
     }
@@ -332,8 +357,9 @@ __global__ void __launch_bounds__(PROJ_THREADS)
                     const CamInfo *__restrict__ cams, const float *__restrict__ vms,
                     const float *__restrict__ intr, ProjParams P,
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
-                    SlotRec *__restrict__ rec, uint32_t *__restrict__ keys,
-                    uint32_t *__restrict__ vals, float ln_alpha_min) {
+                    SlotRec *__restrict__ rec, uint2 *__restrict__ srect,
+                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                    float ln_alpha_min) {
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
     if (g0 >= gr.n) return;
@@ -465,6 +491,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
                              (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)(g0 + local),
                              __float_as_uint(pr.r));
             rec[at] = R;
+            srect[at] = make_uint2(R.d.x, R.d.y);
             keys[at] = __float_as_uint(pr.z);
             vals[at] = slot;
         }
@@ -496,8 +523,8 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
-                                 uint32_t *keys, uint32_t *vals, float ln_alpha_min,
-                                 cudaStream_t s) {
+                                 uint2 *srect, uint32_t *keys, uint32_t *vals,
+                                 float ln_alpha_min, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(max_blocks_x, n_groups);
     const int smem = 48 * PROJ_THREADS * (int)sizeof(float);  // SH of degree <= 3
@@ -505,7 +532,8 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, viewmats, intr, P,
-                                                     masks, woff, rec, keys, vals, ln_alpha_min);
+                                                     masks, woff, rec, srect, keys, vals,
+                                                     ln_alpha_min);
     return cudaGetLastError();
 }
 

@@ -71,10 +71,16 @@ __global__ void __launch_bounds__(256)
     const int s = blockIdx.x, d = threadIdx.x, lane = d & 31, warp = d >> 5;
     const int t0 = tile_start[s], t1 = tile_start[s + 1];
     uint32_t run = 0;
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t c = hist[(long long)t * 256 + d];
-        hist[(long long)t * 256 + d] = run;
-        run += c;
+    // 16 independent loads in flight, then the running sum over them
+    for (int tb = t0; tb < t1; tb += 16) {
+        uint32_t c[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = tb + k < t1 ? hist[(long long)(tb + k) * 256 + d] : 0u;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (tb + k < t1) hist[(long long)(tb + k) * 256 + d] = run;
+            run += c[k];
+        }
     }
     // exclusive scan of the digit totals
     __shared__ uint32_t ws[8];
@@ -90,7 +96,14 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int w = 0; w < 8; ++w) before += w < warp ? ws[w] : 0u;
     const uint32_t base = before + incl - run;
-    for (int t = t0; t < t1; ++t) hist[(long long)t * 256 + d] += base;
+    for (int tb = t0; tb < t1; tb += 16) {
+        uint32_t c[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) c[k] = tb + k < t1 ? hist[(long long)(tb + k) * 256 + d] : 0u;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (tb + k < t1) hist[(long long)(tb + k) * 256 + d] = c[k] + base;
+    }
 }
 
 __global__ void __launch_bounds__(ST)
