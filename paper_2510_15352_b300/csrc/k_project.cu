@@ -245,7 +245,7 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
 }
 
 // Colour of one Gaussian seen from camera c. The block's SH coefficients are
-// staged in shared memory as shs[(3k + ch) * PROJ_THREADS + local].
+// staged in shared memory as shs[(3k + ch) * 128 + local].
 __device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg, int local,
                                           const CamProj &c, const GaussGeo &G, float rgb[3]) {
     const int K = (deg + 1) * (deg + 1);
@@ -268,7 +268,7 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg
         float acc = 0.5f;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (k < K) acc = fmaf(shs[(3 * k + ch) * PROJ_THREADS + local], Y[k], acc);
+            if (k < K) acc = fmaf(shs[(3 * k + ch) * 128 + local], Y[k], acc);
         rgb[ch] = fmaxf(acc, 0.0f);
     }
 }
@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(1024)
 }
 
 constexpr int CAM_SUB = 8;  // cameras whose items are compacted at once
+constexpr int WG = 128;     // Gaussians per write block (4 mask words per camera)
 constexpr float LOG2E = 1.4426950408889634f;
 
 __global__ void __launch_bounds__(PROJ_THREADS)
@@ -361,15 +362,15 @@ __global__ void __launch_bounds__(PROJ_THREADS)
                     uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                     float ln_alpha_min) {
     const Group gr = groups[blockIdx.y];
-    const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
+    const long long g0 = (long long)blockIdx.x * WG;
     if (g0 >= gr.n) return;
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long moff[MAX_GROUP], soff[MAX_GROUP];
-    __shared__ float sgeo[14][PROJ_THREADS];  // mean (3), M (9), smax2, opacity
-    __shared__ uint32_t smask[CAM_SUB * 8], swoff[CAM_SUB * 8], spos[CAM_SUB * 8];
-    __shared__ uint16_t items[CAM_SUB * PROJ_THREADS];
+    __shared__ float sgeo[14][WG];  // mean (3), M (9), smax2, opacity
+    __shared__ uint32_t smask[CAM_SUB * 4], swoff[CAM_SUB * 4], spos[CAM_SUB * 4];
+    __shared__ uint16_t items[CAM_SUB * WG];
     __shared__ uint32_t n_items;
-    extern __shared__ float shs[];  // SH: [(3k + ch)][PROJ_THREADS]
+    extern __shared__ float shs[];  // SH: [(3k + ch)][WG]
     const int tid = threadIdx.x;
     if (tid < gr.ncam) {
         const CamInfo ci = cams[gr.slot0 + tid];
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         soff[tid] = ci.seg_off;
     }
     const SceneDev sc = scenes[gr.scene];
-    {
+    if (tid < WG) {
         const long long g = g0 + tid;
         const bool valid = g < gr.n;
         GaussGeo G;
@@ -398,48 +399,47 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         for (int k = 0; k < 9; ++k) sgeo[3 + k][tid] = G.M[k];
         sgeo[12][tid] = G.smax2;
         sgeo[13][tid] = opacity;
+    }
+    {
+        // SH rows: one coalesced segment of WG values per (coefficient, channel)
         const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
-        for (int k = 0; k < K3; ++k)
-            shs[k * PROJ_THREADS + tid] =
-                valid ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype) : 0.0f;
+        for (int i = tid; i < K3 * WG; i += PROJ_THREADS) {
+            const int k = i / WG, j = i - k * WG;
+            const long long g = g0 + j;
+            shs[i] = g < gr.n ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype) : 0.0f;
+        }
     }
     __syncthreads();
     // mask words of this block that exist (warps entirely past n have none)
-    const int nwords = (int)min(8LL, (gr.n - g0 + 31) >> 5);
+    const int nwords = (int)min((long long)(WG / 32), (gr.n - g0 + 31) >> 5);
     for (int c0 = 0; c0 < gr.ncam; c0 += CAM_SUB) {
         const int nc = min(CAM_SUB, gr.ncam - c0);
         // (camera, word) entries: their masks, slot offsets and item positions
         if (tid < 32) {
-            uint32_t cnt[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int e = tid * 2 + h, cl = e >> 3, w = e & 7;
-                uint32_t m = 0, wo = 0;
-                if (cl < nc && w < nwords) {
-                    const long long at = moff[c0 + cl] + (g0 >> 5) + w;
-                    m = masks[at];
-                    wo = woff[at];
-                }
-                smask[e] = m;
-                swoff[e] = wo;
-                cnt[h] = __popc(m);
+            // entry e = (camera cl, word w), e = 4 cl + w, one per lane
+            const int e = tid, cl = e >> 2, w = e & 3;
+            uint32_t m = 0, wo = 0;
+            if (cl < nc && w < nwords) {
+                const long long at = moff[c0 + cl] + (g0 >> 5) + w;
+                m = masks[at];
+                wo = woff[at];
             }
-            const uint32_t pair = cnt[0] + cnt[1];
-            uint32_t incl = pair;
+            smask[e] = m;
+            swoff[e] = wo;
+            const uint32_t cnt = __popc(m);
+            uint32_t incl = cnt;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
                 if (tid >= d) incl += v;
             }
-            const uint32_t ex = incl - pair;
-            spos[tid * 2] = ex;
-            spos[tid * 2 + 1] = ex + cnt[0];
+            spos[e] = incl - cnt;
             if (tid == 31) n_items = incl;
         }
         __syncthreads();
-        if (tid < nc * 8) {
+        if (tid < nc * 4) {
             uint32_t m = smask[tid], pos = spos[tid];
-            const uint32_t hi = (uint32_t)(tid >> 3) << 8, lo = (uint32_t)(tid & 7) * 32u;
+            const uint32_t hi = (uint32_t)(tid >> 2) << 8, lo = (uint32_t)(tid & 3) * 32u;
             while (m) {
                 const int b = __ffs(m) - 1;
                 items[pos++] = (uint16_t)(hi | (lo + b));
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
             const int it = items[i];
             const int cl = it >> 8, local = it & 255, w = local >> 5, bit = local & 31;
             const int c = c0 + cl;
-            const int e = cl * 8 + w;
+            const int e = cl * 4 + w;
             const uint32_t slot = swoff[e] + __popc(smask[e] & ((1u << bit) - 1u));
             GaussGeo G;
             G.mx = sgeo[0][local];
@@ -526,8 +526,8 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  uint2 *srect, uint32_t *keys, uint32_t *vals,
                                  float ln_alpha_min, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
-    dim3 grid(max_blocks_x, n_groups);
-    const int smem = 48 * PROJ_THREADS * (int)sizeof(float);  // SH of degree <= 3
+    dim3 grid(2 * max_blocks_x, n_groups);  // 128 Gaussians per block
+    const int smem = 48 * WG * (int)sizeof(float);         // SH of degree <= 3
     cudaError_t e = cudaFuncSetAttribute(k_project_write,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
