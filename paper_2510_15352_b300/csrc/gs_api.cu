@@ -413,7 +413,7 @@ gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **o
         !(c.alpha_min > 0.0f) || !(c.alpha_max > 0.0f && c.alpha_max < 1.0f) ||
         !(c.T_min > 0.0f && c.T_min < 1.0f) || c.max_chunk_cameras < 1 || c.camera_group < 1 ||
         c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) ||
-        (c.pixels_per_thread != 2 && c.pixels_per_thread != 4))
+        (c.pixels_per_thread != 2 && c.pixels_per_thread != 4 && c.pixels_per_thread != 8))
         return GS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)

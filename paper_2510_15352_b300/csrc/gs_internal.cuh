@@ -108,7 +108,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, 
                        int n_super, const uint2 *srect, const uint32_t *vals, uint2 *rrect,
                        uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);
 
-// pixels_per_thread: 2 (128-thread blocks) or 4 (64-thread blocks)
+// pixels_per_thread: 2, 4 or 8 (blocks of 128, 64 or 32 threads)
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
                              int n_tiles, const SlotRec *rec, const uint32_t *vals,
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,

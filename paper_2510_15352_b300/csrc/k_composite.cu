@@ -312,6 +312,9 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
                              unsigned long long *stats, bool collect, int pixels_per_thread,
                              cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
+    if (pixels_per_thread == 8)
+        return launch_ppt<8>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
+                             rgb, depth, final_T, stats, collect, s);
     if (pixels_per_thread == 4)
         return launch_ppt<4>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
                              rgb, depth, final_T, stats, collect, s);

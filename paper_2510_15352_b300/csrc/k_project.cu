@@ -71,6 +71,16 @@ __device__ __forceinline__ float sqrt_a(float x) {
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float rsqrt_a(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_a(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 __device__ __forceinline__ float ldv(const void *p, long long i, int dt) {
     if (dt == DT_F32) return __ldg(reinterpret_cast<const float *>(p) + i);
@@ -252,7 +262,7 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg
     float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
     const float dd = dx * dx + dy * dy + dz * dz;
     if (dd > 0.0f) {
-        const float inv = 1.0f / sqrtf(dd);
+        const float inv = rsqrt_a(dd);
         dx *= inv;
         dy *= inv;
         dz *= inv;
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     if (g0 >= gr.n) return;
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long moff[MAX_GROUP], soff[MAX_GROUP];
-    __shared__ float sgeo[14][WG];  // mean (3), M (9), smax2, opacity
+    __shared__ float sgeo[14][WG];  // mean (3), M (9), smax2, log2(opacity)
     __shared__ uint32_t smask[CAM_SUB * 4], swoff[CAM_SUB * 4], spos[CAM_SUB * 4];
     __shared__ uint16_t items[CAM_SUB * WG];
     __shared__ uint32_t n_items;
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
         for (int k = 0; k < 9; ++k) sgeo[3 + k][tid] = G.M[k];
         sgeo[12][tid] = G.smax2;
-        sgeo[13][tid] = opacity;
+        sgeo[13][tid] = lg2_a(opacity);
     }
     {
         // SH rows: one coalesced segment of WG values per (coefficient, channel)
@@ -461,7 +471,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
             for (int k = 0; k < 9; ++k) G.M[k] = sgeo[3 + k][local];
             G.smax2 = sgeo[12][local];
-            const float opacity = sgeo[13][local];
+            const float log2o = sgeo[13][local];
             Proj pr;
             if (!project(cp[c], G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
                 pr.x0 = 1;
@@ -475,17 +485,16 @@ __global__ void __launch_bounds__(PROJ_THREADS)
             // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o/alpha_min):
             // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
             // rounding of the per-pixel test can never pass a pixel outside it
-            const float q = 2.0f * (logf(opacity) - ln_alpha_min);
+            const float q = 2.0f * fmaf(log2o, 0.6931471805599453f, -ln_alpha_min);
             float hx = -1e30f, hy = -1e30f;
             if (q >= 0.0f) {
-                hx = fmaf(1.001f, sqrtf(q * pr.sa), 0.01f);
-                hy = fmaf(1.001f, sqrtf(q * pr.sc), 0.01f);
+                hx = fmaf(1.002f, sqrt_a(q * pr.sa), 0.02f);
+                hy = fmaf(1.002f, sqrt_a(q * pr.sc), 0.02f);
             }
             const long long at = soff[c] + slot;
             SlotRec R;
             R.a = make_float4(pr.u, pr.v, hx, hy);
-            R.b = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C,
-                              log2f(opacity));
+            R.b = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C, log2o);
             R.c = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
             R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
                              (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)(g0 + local),
