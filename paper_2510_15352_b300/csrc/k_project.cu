@@ -12,9 +12,10 @@
 //   k_project_mask  -- survival bit per (camera, Gaussian), one warp ballot per
 //                      32 Gaussians -> a 32-bit mask word;
 //   k_scan_masks    -- per camera, exclusive prefix of the mask popcounts;
-//   k_project_write -- stages the block's Gaussians (geometry and SH) in
-//                      shared memory, compacts the surviving (camera, Gaussian)
-//                      pairs into a dense item list, and for every item
+//   k_project_write -- stages the block's 128 Gaussians (geometry and SH) and
+//                      the mask words of its cameras in shared memory, compacts
+//                      the surviving (camera, Gaussian) pairs into a dense item
+//                      list, and for every item
 //                      recomputes the projection, evaluates the SH colour and
 //                      writes the record, the depth key (float bits of z) and
 //                      the slot at a stable position.
@@ -359,11 +360,10 @@ __global__ void __launch_bounds__(1024)
     if (tid == 0) counts[blockIdx.x] = (int)carry;
 }
 
-constexpr int CAM_SUB = 8;  // cameras whose items are compacted at once
 constexpr int WG = 128;     // Gaussians per write block (4 mask words per camera)
 constexpr float LOG2E = 1.4426950408889634f;
 
-__global__ void __launch_bounds__(PROJ_THREADS)
+__global__ void __launch_bounds__(PROJ_THREADS, 4)
     k_project_write(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
                     const CamInfo *__restrict__ cams, const float *__restrict__ vms,
                     const float *__restrict__ intr, ProjParams P,
@@ -374,27 +374,28 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * WG;
     if (g0 >= gr.n) return;
+    constexpr int NE = MAX_GROUP * (WG / 32);  // (camera, mask word) entries
     __shared__ CamProj cp[MAX_GROUP];
-    __shared__ long long moff[MAX_GROUP], soff[MAX_GROUP];
+    __shared__ long long soff[MAX_GROUP];
     __shared__ float sgeo[14][WG];  // mean (3), M (9), smax2, log2(opacity)
-    __shared__ uint32_t smask[CAM_SUB * 4], swoff[CAM_SUB * 4], spos[CAM_SUB * 4];
-    __shared__ uint16_t items[CAM_SUB * WG];
-    __shared__ uint32_t n_items;
+    __shared__ uint32_t smask[NE], swoff[NE];
+    __shared__ uint16_t items[MAX_GROUP * WG];
+    __shared__ uint32_t wtot[NE / 32];
     extern __shared__ float shs[];  // SH: [(3k + ch)][WG]
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SceneDev sc = scenes[gr.scene];
+    const int nwords = (int)min((long long)(WG / 32), (gr.n - g0 + 31) >> 5);
+    // 1. stage: cameras, the block's Gaussians, their SH rows and all mask words
     if (tid < gr.ncam) {
         const CamInfo ci = cams[gr.slot0 + tid];
         cam_setup(cp[tid], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H, P.guard);
-        moff[tid] = ci.mask_off;
         soff[tid] = ci.seg_off;
     }
-    const SceneDev sc = scenes[gr.scene];
     if (tid < WG) {
         const long long g = g0 + tid;
-        const bool valid = g < gr.n;
         GaussGeo G;
         float opacity = 0.0f;
-        if (valid) {
+        if (g < gr.n) {
             load_geo(sc, g, G);
             opacity = 1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype)));
         } else {
@@ -409,6 +410,19 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         for (int k = 0; k < 9; ++k) sgeo[3 + k][tid] = G.M[k];
         sgeo[12][tid] = G.smax2;
         sgeo[13][tid] = lg2_a(opacity);
+    } else {
+        // entries e = 4 * camera + word
+        for (int e = tid - WG; e < NE; e += PROJ_THREADS - WG) {
+            const int cl = e >> 2, w = e & 3;
+            uint32_t m = 0, wo = 0;
+            if (cl < gr.ncam && w < nwords) {
+                const long long at = cams[gr.slot0 + cl].mask_off + (g0 >> 5) + w;
+                m = masks[at];
+                wo = woff[at];
+            }
+            smask[e] = m;
+            swoff[e] = wo;
+        }
     }
     {
         // SH rows: one coalesced segment of WG values per (coefficient, channel)
@@ -420,91 +434,82 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         }
     }
     __syncthreads();
-    // mask words of this block that exist (warps entirely past n have none)
-    const int nwords = (int)min((long long)(WG / 32), (gr.n - g0 + 31) >> 5);
-    for (int c0 = 0; c0 < gr.ncam; c0 += CAM_SUB) {
-        const int nc = min(CAM_SUB, gr.ncam - c0);
-        // (camera, word) entries: their masks, slot offsets and item positions
-        if (tid < 32) {
-            // entry e = (camera cl, word w), e = 4 cl + w, one per lane
-            const int e = tid, cl = e >> 2, w = e & 3;
-            uint32_t m = 0, wo = 0;
-            if (cl < nc && w < nwords) {
-                const long long at = moff[c0 + cl] + (g0 >> 5) + w;
-                m = masks[at];
-                wo = woff[at];
-            }
-            smask[e] = m;
-            swoff[e] = wo;
-            const uint32_t cnt = __popc(m);
-            uint32_t incl = cnt;
+    // 2. item positions: exclusive prefix of the entries' popcounts
+    uint32_t cnt = 0, incl = 0;
+    if (tid < NE) {
+        cnt = __popc(smask[tid]);
+        incl = cnt;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-                if (tid >= d) incl += v;
-            }
-            spos[e] = incl - cnt;
-            if (tid == 31) n_items = incl;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
         }
-        __syncthreads();
-        if (tid < nc * 4) {
-            uint32_t m = smask[tid], pos = spos[tid];
-            const uint32_t hi = (uint32_t)(tid >> 2) << 8, lo = (uint32_t)(tid & 3) * 32u;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                items[pos++] = (uint16_t)(hi | (lo + b));
-                m &= m - 1u;
-            }
-        }
-        __syncthreads();
-        const int total = (int)n_items;
-        for (int i = tid; i < total; i += PROJ_THREADS) {
-            const int it = items[i];
-            const int cl = it >> 8, local = it & 255, w = local >> 5, bit = local & 31;
-            const int c = c0 + cl;
-            const int e = cl * 4 + w;
-            const uint32_t slot = swoff[e] + __popc(smask[e] & ((1u << bit) - 1u));
-            GaussGeo G;
-            G.mx = sgeo[0][local];
-            G.my = sgeo[1][local];
-            G.mz = sgeo[2][local];
+        if (lane == 31) wtot[warp] = incl;
+    }
+    __syncthreads();
+    if (tid < NE) {
+        uint32_t before = 0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) G.M[k] = sgeo[3 + k][local];
-            G.smax2 = sgeo[12][local];
-            const float log2o = sgeo[13][local];
-            Proj pr;
-            if (!project(cp[c], G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
-                pr.x0 = 1;
-                pr.x1 = 0;
-                pr.y0 = 1;
-                pr.y1 = 0;
-                pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
-            }
-            float rgb[3];
-            sh_colour(shs, sc.deg, local, cp[c], G, rgb);
-            // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o/alpha_min):
-            // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
-            // rounding of the per-pixel test can never pass a pixel outside it
-            const float q = 2.0f * fmaf(log2o, 0.6931471805599453f, -ln_alpha_min);
-            float hx = -1e30f, hy = -1e30f;
-            if (q >= 0.0f) {
-                hx = fmaf(1.002f, sqrt_a(q * pr.sa), 0.02f);
-                hy = fmaf(1.002f, sqrt_a(q * pr.sc), 0.02f);
-            }
-            const long long at = soff[c] + slot;
-            SlotRec R;
-            R.a = make_float4(pr.u, pr.v, hx, hy);
-            R.b = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C, log2o);
-            R.c = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
-            R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
-                             (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)(g0 + local),
-                             __float_as_uint(pr.r));
-            rec[at] = R;
-            srect[at] = make_uint2(R.d.x, R.d.y);
-            keys[at] = __float_as_uint(pr.z);
-            vals[at] = slot;
+        for (int k = 0; k < NE / 32; ++k) before += k < warp ? wtot[k] : 0u;
+        uint32_t pos = before + incl - cnt;
+        uint32_t m = smask[tid];
+        const uint32_t hi = (uint32_t)(tid >> 2) << 7, lo = (uint32_t)(tid & 3) * 32u;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            items[pos++] = (uint16_t)(hi | (lo + b));
+            m &= m - 1u;
         }
-        __syncthreads();  // items / masks are rebuilt for the next cameras
+    }
+    __syncthreads();
+    uint32_t total = 0;
+#pragma unroll
+    for (int k = 0; k < NE / 32; ++k) total += wtot[k];
+    // 3. every surviving (camera, Gaussian) pair, densely
+    for (int i = tid; i < (int)total; i += PROJ_THREADS) {
+        const int it = items[i];
+        const int c = it >> 7, local = it & 127, w = local >> 5, bit = local & 31;
+        const int e = c * 4 + w;
+        const uint32_t slot = swoff[e] + __popc(smask[e] & ((1u << bit) - 1u));
+        GaussGeo G;
+        G.mx = sgeo[0][local];
+        G.my = sgeo[1][local];
+        G.mz = sgeo[2][local];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) G.M[k] = sgeo[3 + k][local];
+        G.smax2 = sgeo[12][local];
+        const float log2o = sgeo[13][local];
+        const CamProj cam = load_cam(cp[c]);
+        Proj pr;
+        if (!project(cam, G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
+            pr.x0 = 1;
+            pr.x1 = 0;
+            pr.y0 = 1;
+            pr.y1 = 0;
+            pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
+        }
+        float rgb[3];
+        sh_colour(shs, sc.deg, local, cam, G, rgb);
+        // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o/alpha_min):
+        // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
+        // rounding of the per-pixel test can never pass a pixel outside it
+        const float q = 2.0f * fmaf(log2o, 0.6931471805599453f, -ln_alpha_min);
+        float hx = -1e30f, hy = -1e30f;
+        if (q >= 0.0f) {
+            hx = fmaf(1.002f, sqrt_a(q * pr.sa), 0.02f);
+            hy = fmaf(1.002f, sqrt_a(q * pr.sc), 0.02f);
+        }
+        const long long at = soff[c] + slot;
+        SlotRec R;
+        R.a = make_float4(pr.u, pr.v, hx, hy);
+        R.b = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C, log2o);
+        R.c = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
+        R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
+                         (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)(g0 + local),
+                         __float_as_uint(pr.r));
+        rec[at] = R;
+        srect[at] = make_uint2(R.d.x, R.d.y);
+        keys[at] = __float_as_uint(pr.z);
+        vals[at] = slot;
     }
 }
 
