@@ -166,6 +166,8 @@ def run_b300(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2510_15352_b300 import gs, synth
     scene, vm, it, W, H = synth.workload(WORKLOAD, seed=rank, n_cams=args.cams)
+    if args.precision == "half":
+        scene = synth.to_half(scene)  # FP16 geometry, BF16 opacity + SH; FP32 math
     n = len(vm)
     vm_d = torch.from_numpy(vm).cuda()
     it_d = torch.from_numpy(it).cuda()
@@ -257,7 +259,7 @@ def run_b300(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cameras_per_gpu": n, "width": W, "height": H,
                        "gaussians": 1_000_000, "sh_degree": 3, "chunk_cameras": args.chunk,
-                       "pixels_per_thread": args.ppt,
+                       "pixels_per_thread": args.ppt, "storage": args.precision,
                        "l2": "inputs larger than L2 (scene 236 MB; 5 GB of outputs per step)"},
             "roofline": {
                 "kernel": "k_composite", "bound": "alu", "achieved": achieved,
@@ -296,7 +298,9 @@ def main():
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
     ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 1024)")
     ap.add_argument("--chunk", type=int, default=256, help="cameras per internal chunk")
-    ap.add_argument("--ppt", type=int, default=4, help="compositing pixels per thread (2|4)")
+    ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
+    ap.add_argument("--precision", choices=["f32", "half"], default="f32",
+                    help="scene attribute storage (half: FP16 geometry, BF16 appearance)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

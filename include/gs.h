@@ -68,7 +68,7 @@ typedef struct gs_config {
                               (a slower variant of the kernel) */
     int32_t time_stages;   /* 1: record CUDA events around every stage on the render
                               stream; gs_get_stats reports the per-stage device time */
-    int32_t pixels_per_thread; /* compositing layout: 2, 4 or 8 pixels per thread (4) */
+    int32_t pixels_per_thread; /* compositing layout: 2, 4 or 8 pixels per thread (8) */
     int32_t reserved[7];
 } gs_config;
 

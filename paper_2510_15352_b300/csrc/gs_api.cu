@@ -397,7 +397,7 @@ gs_status gs_config_default(gs_config *out) {
     out->camera_group = 32;
     out->count_pairs = 0;
     out->time_stages = 0;
-    out->pixels_per_thread = 4;
+    out->pixels_per_thread = 8;
     return GS_OK;
 }
 

@@ -108,3 +108,30 @@ def workload(name: str, seed: int = 0, n_cams: int | None = None):
     scene = make_scene(w["n"], w["deg"], seed)
     vm, it = make_cameras(n_cams or w["cams"], w["W"], w["H"], w["f"], w["height"], seed)
     return scene, vm, it, w["W"], w["H"]
+
+
+def to_half(scene: dict, geometry: str = "float16", appearance: str = "bfloat16") -> dict:
+    """Reduced-precision copy of a scene: mean, log_scale and quat stored as
+    ``geometry``, logit_opacity and sh as ``appearance`` ("float16" or
+    "bfloat16"; bfloat16 is held as its uint16 bit pattern, rounded to nearest
+    even). ``dequantised`` holds the exact float32 values the stored numbers
+    represent, which is what a renderer computes with."""
+    stored = {"sh_degree": scene["sh_degree"]}
+    deq = {"sh_degree": scene["sh_degree"]}
+    for keys, kind in ((("mean", "log_scale", "quat"), geometry),
+                       (("logit_opacity", "sh"), appearance)):
+        for k in keys:
+            a = np.ascontiguousarray(scene[k], dtype=np.float32)
+            if kind == "float16":
+                h = a.astype(np.float16)
+                stored[k] = h
+                deq[k] = h.astype(np.float32)
+            elif kind == "bfloat16":
+                u = a.view(np.uint32).astype(np.uint64)
+                bits = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+                stored[k] = bits
+                deq[k] = (bits.astype(np.uint32) << 16).view(np.float32)
+            else:
+                raise ValueError(kind)
+    stored["dequantised"] = deq
+    return stored

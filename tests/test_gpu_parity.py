@@ -199,7 +199,7 @@ def test_tile_lists_match_oracle(torch, R, orc):
 
 # ---------------------------------------------------------------- pixels
 
-@pytest.mark.parametrize("ppt", [2, 4])
+@pytest.mark.parametrize("ppt", [2, 4, 8])
 def test_small_workload_pixels(torch, gsmod, orc, ppt):
     r = gsmod.Renderer(device=0, pixels_per_thread=ppt)
     try:
