@@ -163,6 +163,19 @@ gs_status gs_render_batch(gs_context *ctx, int32_t n_cams, const int32_t *scene_
                           int32_t height, float *rgb, float *depth, float *final_T,
                           void *stream);
 
+/* gs_render_batch with a size per camera (a batch may mix resolutions).
+ *   widths, heights  HOST [n_cams] camera sizes (each as in gs_render_batch)
+ *   pixel_offsets    HOST [n_cams] index of camera i's first pixel in the packed
+ *                    outputs: camera i writes rgb[3 * (off_i + y * W_i + x) + ch],
+ *                    depth[off_i + y * W_i + x], final_T likewise; the images must
+ *                    not overlap
+ * Other arguments and errors as gs_render_batch. */
+gs_status gs_render_batch_v(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                            const float *viewmats, const float *intrinsics,
+                            const int32_t *widths, const int32_t *heights,
+                            const int64_t *pixel_offsets, float *rgb, float *depth,
+                            float *final_T, void *stream);
+
 /* Same as gs_render_batch with every array in HOST memory: the call copies the
  * cameras to the device, renders into context-owned device buffers and copies
  * the outputs back (pinned host buffers make the copies asynchronous DMA).

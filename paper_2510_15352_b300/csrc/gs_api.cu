@@ -139,10 +139,15 @@ struct RenderArgs {
     int n;
     const int32_t *scene_ids;  // host
     const float *vm, *in;      // device
-    int W, H;
+    int W, H;                  // every camera's size when Ws == NULL
+    const int32_t *Ws, *Hs;    // host per-camera sizes, or NULL
+    const int64_t *pix_off;    // host per-camera first output pixel, or NULL (i * W * H)
     float *rgb, *depth, *T;    // device
     cudaStream_t st;
     Stage upto;
+    int cam_w(int i) const { return Ws ? Ws[i] : W; }
+    int cam_h(int i) const { return Hs ? Hs[i] : H; }
+    long long cam_pix(int i) const { return pix_off ? pix_off[i] : (long long)i * W * H; }
 };
 
 // Pinned staging layout of one chunk.
@@ -155,9 +160,6 @@ struct Staging {
 
 gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     const gs_config &cfg = ctx->cfg;
-    const int TX = (a.W + TILE - 1) / TILE, TY = (a.H + TILE - 1) / TILE;
-    const int tiles = TX * TY;
-    const int nsup = ((TX + STILE - 1) / STILE) * ((TY + STILE - 1) / STILE);
     const int chunk_max = std::max(1, cfg.max_chunk_cameras);
     const int gmax = std::min(MAX_GROUP, std::max(1, cfg.camera_group));
     const ProjParams P{cfg.near_plane, cfg.dilation, cfg.guard_band, cfg.sigma_cull};
@@ -221,7 +223,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         S.segcount = (long long *)(base + off);
 
         long long mask_words = 0;
-        int n_groups = 0, max_bx = 0;
+        int n_groups = 0, max_bx = 0, tiles_total = 0, max_sup = 1;
         for (int s = 0; s < m; ++s) {
             const int user = order[c0 + s];
             const int sid = a.scene_ids[user];
@@ -230,11 +232,15 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             memset(&ci, 0, sizeof(ci));
             ci.user = user;
             ci.scene = sid;
-            ci.W = a.W;
-            ci.H = a.H;
-            ci.TX = TX;
-            ci.TY = TY;
-            ci.tile_off = s * tiles;
+            ci.W = a.cam_w(user);
+            ci.H = a.cam_h(user);
+            ci.TX = (ci.W + TILE - 1) / TILE;
+            ci.TY = (ci.H + TILE - 1) / TILE;
+            ci.pix_off = a.cam_pix(user);
+            ci.tile_off = tiles_total;
+            S.tilepre[s] = tiles_total;
+            tiles_total += ci.TX * ci.TY;
+            max_sup = std::max(max_sup, ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE));
             ci.mask_off = mask_words;
             mask_words += (sd.n + 31) / 32;
             const bool new_group = s == 0 || S.groups[n_groups - 1].scene != sid ||
@@ -276,10 +282,9 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             ci.nw = (ci.count + 31) / 32;
             ci.bm_off = bm_words;
             S_total += ci.count;
-            bm_words += (long long)nsup * ci.nw;
+            bm_words += (long long)((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE) * ci.nw;
             S.blkpre[s] = blocks;
             blocks += (ci.count + BIN_RANKS - 1) / BIN_RANKS;
-            S.tilepre[s] = s * tiles;
             S.segstart[s] = ci.seg_off;
             S.segcount[s] = ci.count;
             S.sorttiles[s] = sort_tiles;
@@ -287,7 +292,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         }
         S.sorttiles[m] = sort_tiles;
         S.blkpre[m] = blocks;
-        S.tilepre[m] = m * tiles;
+        S.tilepre[m] = tiles_total;
         st.survivors += S_total;
         const size_t Sx = (size_t)std::max<long long>(S_total, 1);
         CKS(grow(ctx, ctx->rec, Sx * sizeof(SlotRec)));
@@ -319,13 +324,13 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
                                  (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
                                  m, sort_tiles, (uint32_t *)ctx->sorthist.p, a.st));
         if (timing) CKC(cudaEventRecord(E[2], a.st));
-        CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, nsup,
+        CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, max_sup,
                        (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->vals.p,
                        (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p,
                        (unsigned long long *)ctx->stats.p + 2, a.st));
         if (timing) CKC(cudaEventRecord(E[3], a.st));
         if (a.upto == UPTO_BIN) break;
-        CKC(launch_composite((const CamInfo *)ctx->cams.p, (const int *)ctx->tilepre.p, m, m * tiles,
+        CKC(launch_composite((const CamInfo *)ctx->cams.p, (const int *)ctx->tilepre.p, m, tiles_total,
                              (const SlotRec *)ctx->rec.p, (const uint32_t *)ctx->vals.p,
                              (const uint2 *)ctx->rrect.p, (const uint32_t *)ctx->bitmap.p, C, a.rgb,
                              a.depth, a.T, (unsigned long long *)ctx->stats.p,
@@ -354,6 +359,7 @@ gs_status validate(gs_context *ctx, int n, const int32_t *scene_ids, const void 
     const long long tiles = (long long)((W + 15) / 16) * ((H + 15) / 16);
     if (tiles > MAX_TILES)
         return fail(ctx, GS_ERR_CAPACITY, "%lld tiles per camera > %d", tiles, MAX_TILES);
+    (void)tiles;
     for (int i = 0; i < n; ++i) {
         const int s = scene_ids[i];
         if (s < 0 || s >= (int)ctx->scenes.size() || !ctx->scenes[s].live)
@@ -537,8 +543,30 @@ gs_status gs_render_batch(gs_context *ctx, int32_t n_cams, const int32_t *scene_
     ctx->err.clear();
     if (n_cams == 0) return GS_OK;
     CKC(cudaSetDevice(ctx->device));
-    RenderArgs a{n_cams, scene_ids, viewmats, intrinsics, width, height,
-                 rgb,    depth,     final_T,  (cudaStream_t)stream, UPTO_ALL};
+    RenderArgs a{n_cams, scene_ids, viewmats, intrinsics, width, height, nullptr, nullptr,
+                 nullptr, rgb, depth, final_T, (cudaStream_t)stream, UPTO_ALL};
+    return render_impl(ctx, a);
+}
+
+gs_status gs_render_batch_v(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                            const float *viewmats, const float *intrinsics, const int32_t *widths,
+                            const int32_t *heights, const int64_t *pixel_offsets, float *rgb,
+                            float *depth, float *final_T, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (n_cams > 0 && (!widths || !heights || !pixel_offsets))
+        return fail(ctx, GS_ERR_INVALID_ARG, "NULL per-camera size or offset array");
+    for (int i = 0; i < n_cams; ++i) {
+        CKS(validate(ctx, 1, scene_ids + i, viewmats, intrinsics, widths[i], heights[i], rgb,
+                     depth, true));
+        if (pixel_offsets[i] < 0) return fail(ctx, GS_ERR_INVALID_ARG, "negative pixel offset");
+    }
+    CKS(validate(ctx, n_cams, scene_ids, viewmats, intrinsics, 1, 1, rgb, depth, true));
+    ctx->err.clear();
+    if (n_cams == 0) return GS_OK;
+    CKC(cudaSetDevice(ctx->device));
+    RenderArgs a{n_cams, scene_ids, viewmats, intrinsics, 0,
+                 0,      widths,    heights,  pixel_offsets, rgb,
+                 depth,  final_T,   (cudaStream_t)stream, UPTO_ALL};
     return render_impl(ctx, a);
 }
 
@@ -565,6 +593,9 @@ gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *s
                  (const float *)ctx->h_in.p,
                  width,
                  height,
+                 nullptr,
+                 nullptr,
+                 nullptr,
                  (float *)ctx->h_rgb.p,
                  (float *)ctx->h_depth.p,
                  final_T ? (float *)ctx->h_T.p : nullptr,
@@ -621,8 +652,8 @@ gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewm
     ctx->err.clear();
     CKC(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    RenderArgs a{1, &scene_id, viewmat, intrinsics, width, height, nullptr, nullptr, nullptr, st,
-                 UPTO_PROJECT};
+    RenderArgs a{1,       &scene_id, viewmat, intrinsics, width, height, nullptr, nullptr,
+                 nullptr, nullptr,   nullptr, nullptr,    st,    UPTO_PROJECT};
     CKS(render_impl(ctx, a));
     CKC(cudaStreamSynchronize(st));
     const long long S = ctx->last.survivors;
@@ -666,8 +697,8 @@ gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *vi
     ctx->err.clear();
     CKC(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    RenderArgs a{1, &scene_id, viewmat, intrinsics, width, height, nullptr, nullptr, nullptr, st,
-                 UPTO_BIN};
+    RenderArgs a{1,       &scene_id, viewmat, intrinsics, width, height, nullptr, nullptr,
+                 nullptr, nullptr,   nullptr, nullptr,    st,    UPTO_BIN};
     CKS(render_impl(ctx, a));
     CKC(cudaStreamSynchronize(st));
     const long long S = ctx->last.survivors;

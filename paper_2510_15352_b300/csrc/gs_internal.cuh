@@ -51,6 +51,7 @@ struct CamInfo {
     long long bm_off;    // first super-tile bitmap word
     int nw;          // bitmap words per super-tile row = ceil(count / 32)
     int pad;
+    long long pix_off;   // first pixel of this camera in the packed outputs
 };
 
 // Cameras of one scene that share a projection block's Gaussian loads.

@@ -266,7 +266,7 @@ finished:
     for (int k = 0; k < PPT; ++k) {
         const int x = x0 + k * CPR;
         if (x >= ci.W || y >= ci.H) continue;
-        const long long pix = ((long long)ci.user * ci.H + y) * ci.W + x;
+        const long long pix = ci.pix_off + (long long)y * ci.W + x;
         rgb[3 * pix + 0] = fmaf(T[k], P.bg[0], cr[k]);
         rgb[3 * pix + 1] = fmaf(T[k], P.bg[1], cg[k]);
         rgb[3 * pix + 2] = fmaf(T[k], P.bg[2], cb[k]);

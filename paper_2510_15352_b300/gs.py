@@ -68,6 +68,8 @@ SIGNATURES = {
                                        _vp]),
     "gs_render_batch_host": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp, _vp,
                                             _vp, _vp]),
+    "gs_render_batch_v": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         _vp]),
     "gs_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gs_stats)]),
     "gs_debug_project": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64,
                                         ctypes.POINTER(_i64), _vp]),
@@ -106,6 +108,7 @@ gs_scene_create = lib.gs_scene_create
 gs_scene_destroy = lib.gs_scene_destroy
 gs_render_batch = lib.gs_render_batch
 gs_render_batch_host = lib.gs_render_batch_host
+gs_render_batch_v = lib.gs_render_batch_v
 gs_get_stats = lib.gs_get_stats
 gs_debug_project = lib.gs_debug_project
 gs_debug_tile_lists = lib.gs_debug_tile_lists
@@ -227,6 +230,33 @@ class Renderer:
                                     W, H, rgb.data_ptr(), depth.data_ptr(), _ptr(final_T),
                                     _stream(stream)))
         return rgb, depth, final_T
+
+    def render_v(self, scene_ids, viewmats, intrinsics, widths, heights, rgb=None, depth=None,
+                 final_T=None, want_T: bool = False, stream=None):
+        """Render cameras of mixed sizes into packed outputs (camera i's pixels
+        start at offsets[i]). Returns (rgb [P, 3], depth [P], T or None, offsets)."""
+        import torch
+        n = int(viewmats.shape[0])
+        ids = np.ascontiguousarray(np.broadcast_to(np.asarray(scene_ids, dtype=np.int32), (n,)))
+        w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        h = np.ascontiguousarray(np.asarray(heights, dtype=np.int32))
+        sizes = w.astype(np.int64) * h
+        off = np.ascontiguousarray(np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64))
+        P = int(sizes.sum())
+        dev = viewmats.device
+        if rgb is None:
+            rgb = torch.empty((P, 3), dtype=torch.float32, device=dev)
+        if depth is None:
+            depth = torch.empty((P,), dtype=torch.float32, device=dev)
+        if final_T is None and want_T:
+            final_T = torch.empty((P,), dtype=torch.float32, device=dev)
+        vm = viewmats.contiguous()
+        it = intrinsics.contiguous()
+        self._check(gs_render_batch_v(self.ctx, n, ids.ctypes.data, vm.data_ptr(), it.data_ptr(),
+                                      w.ctypes.data, h.ctypes.data, off.ctypes.data,
+                                      rgb.data_ptr(), depth.data_ptr(), _ptr(final_T),
+                                      _stream(stream)))
+        return rgb, depth, final_T, off
 
     def render_host(self, scene_ids, viewmats, intrinsics, W: int, H: int, rgb, depth,
                     final_T=None, stream=None):

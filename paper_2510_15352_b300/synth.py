@@ -135,3 +135,34 @@ def to_half(scene: dict, geometry: str = "float16", appearance: str = "bfloat16"
                 raise ValueError(kind)
     stored["dequantised"] = deq
     return stored
+
+
+def make_batched(n_scenes: int = 32, n_cams: int = 4096, seed: int = 0,
+                 n_range=(200_000, 2_000_000), sh_degree: int = 3, zipf: float = 1.1,
+                 sizes=((320, 240, 240.0), (640, 480, 480.0)), height=(0.3, 1.2)):
+    """Many robots over many scenes of uneven size (the paper's 4,096
+    environments over 128 scenes, Sec. 3.3): scene sizes log-uniform in
+    ``n_range``; camera i's scene drawn with P(rank k) proportional to
+    k^-zipf over a random permutation of the scenes; camera i's resolution
+    and focal length alternate through ``sizes`` (W, H, f) by camera index.
+    Returns (scenes, scene_of_camera, viewmats, intrinsics, widths, heights)."""
+    rng = np.random.default_rng([seed, 2])
+    lo, hi = math.log(n_range[0]), math.log(n_range[1])
+    counts = np.rint(np.exp(rng.uniform(lo, hi, size=n_scenes))).astype(np.int64)
+    scenes = [make_scene(int(counts[s]), sh_degree, seed=1000 * seed + s + 1)
+              for s in range(n_scenes)]
+    perm = rng.permutation(n_scenes)
+    p = np.arange(1, n_scenes + 1, dtype=np.float64) ** -zipf
+    rank = rng.choice(n_scenes, size=n_cams, p=p / p.sum())
+    scene_of = perm[rank].astype(np.int32)
+    rng_c = np.random.default_rng([seed, 3])
+    yaw = rng_c.uniform(0.0, 2.0 * math.pi, size=n_cams)
+    xy = rng_c.uniform(1.0, 9.0, size=(n_cams, 2))
+    h = rng_c.uniform(height[0], height[1], size=n_cams)
+    vm = np.stack([viewmat_from_pose((xy[i, 0], xy[i, 1], h[i]), yaw[i]) for i in range(n_cams)])
+    which = np.arange(n_cams) % len(sizes)
+    W = np.array([sizes[k][0] for k in which], dtype=np.int32)
+    H = np.array([sizes[k][1] for k in which], dtype=np.int32)
+    f = np.array([sizes[k][2] for k in which])
+    intr = np.stack([f, f, W / 2.0, H / 2.0], axis=1)
+    return scenes, scene_of, vm.astype(np.float32), intr.astype(np.float32), W, H

@@ -289,6 +289,29 @@ def test_many_chunks_and_scenes(torch, gsmod, orc):
         r.close()
 
 
+def test_mixed_resolutions_uneven_scenes(torch, gsmod, orc):
+    """Batched uneven workload in miniature: six scenes of uneven size, cameras
+    assigned with a Zipf law and alternating between two resolutions, rendered
+    in one call into packed outputs; every camera checked against the oracle."""
+    scenes, which, vm, it, Ws, Hs = synth.make_batched(
+        n_scenes=6, n_cams=20, seed=3, n_range=(2_000, 20_000), sh_degree=1,
+        sizes=((96, 64, 70.0), (64, 48, 50.0)))
+    r = gsmod.Renderer(device=0, max_chunk_cameras=7, camera_group=3)
+    try:
+        sids = [r.add_scene(s) for s in scenes]
+        rgb, depth, T, off = r.render_v([sids[k] for k in which], dev(torch, vm), dev(torch, it),
+                                        Ws, Hs, want_T=True)
+        torch.cuda.synchronize()
+        rgb, depth, T = rgb.cpu().numpy(), depth.cpu().numpy(), T.cpu().numpy()
+        for c in range(len(vm)):
+            W, H, o = int(Ws[c]), int(Hs[c]), int(off[c])
+            ref = orc.render(scenes[which[c]], vm[c], it[c], W, H, bands=BANDS)
+            assert_camera_parity(rgb[o:o + W * H].reshape(H, W, 3), depth[o:o + W * H].reshape(H, W),
+                                 T[o:o + W * H].reshape(H, W), ref)
+    finally:
+        r.close()
+
+
 def test_pair_counts_match_oracle(torch, gsmod, orc):
     """With statistics on, the evaluated-pair counts (the roofline's work
     count) agree with the oracle's per-pixel walk lengths."""
