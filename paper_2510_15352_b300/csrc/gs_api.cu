@@ -57,7 +57,9 @@ struct gs_context {
     DevBuf d_scenes;
     // chunk workspace
     DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, srect, bitmap;
-    DevBuf cams, groups, blkpre, tilepre, segstart, segcount, stats, sorttiles, sorthist;
+    DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist;
+    long long cap_survivors = 0;  // survivors per chunk the workspace holds
+    int workspace_gen = 0;        // bumped when the survivor buffers are reallocated
     // host-API staging
     DevBuf h_vm, h_in, h_rgb, h_depth, h_T;
     PinBuf pin[2];
@@ -150,85 +152,50 @@ struct RenderArgs {
     long long cam_pix(int i) const { return pix_off ? pix_off[i] : (long long)i * W * H; }
 };
 
-// Pinned staging layout of one chunk.
-struct Staging {
-    CamInfo *cams;
-    Group *groups;
-    int *blkpre, *tilepre, *counts, *sorttiles;
-    long long *segstart, *segcount;
+// Static per-call tables (host side), built once per call and uploaded in one copy.
+struct ChunkPlan {
+    int c0, m;            // first camera (in scene order) and cameras of the chunk
+    int g0, n_groups;     // groups of the chunk in the group table
+    int max_bx;           // projection blocks (x) for the largest scene of the chunk
+    int tiles_total;      // 16x16 tiles of the chunk
+    int max_sup;          // largest super-tile count of a camera of the chunk
+    long long mask_words; // survival-mask words of the chunk
+    long long n_gauss;    // sum over cameras of their scene sizes
+    int sort_grid, bin_grid;
 };
 
-gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
+struct Plan {
+    std::vector<ChunkPlan> chunks;
+    std::vector<CamInfo> cams;       // static fields, all chunks (chunk k at chunks[k].c0)
+    std::vector<Group> groups;
+    std::vector<int> tilepre;        // per chunk m + 1 entries, at c0 + k
+    long long max_mask_words = 0, max_gauss = 0;
+    int max_m = 0, max_sup = 1;
+    size_t table_bytes = 0, off_groups = 0, off_tilepre = 0;
+};
+
+void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
     const gs_config &cfg = ctx->cfg;
     const int chunk_max = std::max(1, cfg.max_chunk_cameras);
     const int gmax = std::min(MAX_GROUP, std::max(1, cfg.camera_group));
-    const ProjParams P{cfg.near_plane, cfg.dilation, cfg.guard_band, cfg.sigma_cull};
-    const CompParams C{std::log2(cfg.alpha_min), cfg.alpha_max, cfg.T_min,
-                       {cfg.background[0], cfg.background[1], cfg.background[2]}};
-    const bool timing = cfg.time_stages != 0;
-
-    // cameras grouped by scene (stable), then chunked
     std::vector<int> order(a.n);
     for (int i = 0; i < a.n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return a.scene_ids[x] < a.scene_ids[y]; });
-
-    gs_stats st{};
-    st.n_cameras = a.n;
-    CKS(grow(ctx, ctx->stats, 8 * sizeof(unsigned long long)));
-    CKC(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), a.st));
-    const size_t stage_bytes =
-        align_up((size_t)chunk_max * sizeof(CamInfo), 256) + align_up((size_t)chunk_max * sizeof(Group), 256) +
-        4 * align_up((size_t)(chunk_max + 1) * sizeof(int), 256) +
-        2 * align_up((size_t)chunk_max * sizeof(long long), 256);
-    for (int k = 0; k < 2; ++k) CKS(grow_pinned(ctx, ctx->pin[k], stage_bytes));
-    CKS(grow(ctx, ctx->cams, (size_t)chunk_max * sizeof(CamInfo)));
-    CKS(grow(ctx, ctx->groups, (size_t)chunk_max * sizeof(Group)));
-    CKS(grow(ctx, ctx->blkpre, (size_t)(chunk_max + 1) * sizeof(int)));
-    CKS(grow(ctx, ctx->tilepre, (size_t)(chunk_max + 1) * sizeof(int)));
-    CKS(grow(ctx, ctx->segstart, (size_t)chunk_max * sizeof(long long)));
-    CKS(grow(ctx, ctx->segcount, (size_t)chunk_max * sizeof(long long)));
-    CKS(grow(ctx, ctx->counts, (size_t)chunk_max * sizeof(int)));
-    CKS(grow(ctx, ctx->sorttiles, (size_t)(chunk_max + 1) * sizeof(int)));
-    const int n_chunks = (a.n + chunk_max - 1) / chunk_max;
-    if (timing)
-        while ((int)ctx->ev.size() < 5 * n_chunks) {
-            cudaEvent_t e;
-            CKC(cudaEventCreate(&e));
-            ctx->ev.push_back(e);
-        }
-    ctx->ev_used = 0;
-
-    int chunk_id = 0;
-    for (int c0 = 0; c0 < a.n; c0 += chunk_max, ++chunk_id) {
-        const int m = std::min(chunk_max, a.n - c0);
-        // pinned staging for this chunk
-        char *base = (char *)ctx->pin[chunk_id & 1].p;
-        Staging S;
-        size_t off = 0;
-        S.cams = (CamInfo *)(base + off);
-        off += align_up((size_t)chunk_max * sizeof(CamInfo), 256);
-        S.groups = (Group *)(base + off);
-        off += align_up((size_t)chunk_max * sizeof(Group), 256);
-        S.blkpre = (int *)(base + off);
-        off += align_up((size_t)(chunk_max + 1) * sizeof(int), 256);
-        S.tilepre = (int *)(base + off);
-        off += align_up((size_t)(chunk_max + 1) * sizeof(int), 256);
-        S.counts = (int *)(base + off);
-        off += align_up((size_t)(chunk_max + 1) * sizeof(int), 256);
-        S.sorttiles = (int *)(base + off);
-        off += align_up((size_t)(chunk_max + 1) * sizeof(int), 256);
-        S.segstart = (long long *)(base + off);
-        off += align_up((size_t)chunk_max * sizeof(long long), 256);
-        S.segcount = (long long *)(base + off);
-
-        long long mask_words = 0;
-        int n_groups = 0, max_bx = 0, tiles_total = 0, max_sup = 1;
-        for (int s = 0; s < m; ++s) {
+    P.cams.resize(a.n);
+    P.tilepre.resize(a.n + (a.n + chunk_max - 1) / chunk_max + 1);
+    int tp = 0;
+    for (int c0 = 0; c0 < a.n; c0 += chunk_max) {
+        ChunkPlan ch{};
+        ch.c0 = c0;
+        ch.m = std::min(chunk_max, a.n - c0);
+        ch.g0 = (int)P.groups.size();
+        long long sort_up = 0, bin_up = 0;
+        for (int s = 0; s < ch.m; ++s) {
             const int user = order[c0 + s];
             const int sid = a.scene_ids[user];
             const SceneDev &sd = ctx->scenes[sid].dev;
-            CamInfo &ci = S.cams[s];
+            CamInfo &ci = P.cams[c0 + s];
             memset(&ci, 0, sizeof(ci));
             ci.user = user;
             ci.scene = sid;
@@ -237,111 +204,179 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             ci.TX = (ci.W + TILE - 1) / TILE;
             ci.TY = (ci.H + TILE - 1) / TILE;
             ci.pix_off = a.cam_pix(user);
-            ci.tile_off = tiles_total;
-            S.tilepre[s] = tiles_total;
-            tiles_total += ci.TX * ci.TY;
-            max_sup = std::max(max_sup, ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE));
-            ci.mask_off = mask_words;
-            mask_words += (sd.n + 31) / 32;
-            const bool new_group = s == 0 || S.groups[n_groups - 1].scene != sid ||
-                                   S.groups[n_groups - 1].ncam == gmax;
+            ci.tile_off = ch.tiles_total;
+            P.tilepre[tp + s] = ch.tiles_total;
+            ch.tiles_total += ci.TX * ci.TY;
+            ch.max_sup = std::max(ch.max_sup,
+                                  ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE));
+            ci.mask_off = ch.mask_words;
+            ch.mask_words += (sd.n + 31) / 32;
+            ch.n_gauss += sd.n;
+            sort_up += (sd.n + SORT_TILE_KEYS - 1) / SORT_TILE_KEYS;
+            bin_up += (sd.n + BIN_RANKS - 1) / BIN_RANKS;
+            const bool new_group = ch.n_groups == 0 || P.groups.back().scene != sid ||
+                                   P.groups.back().ncam == gmax;
             if (new_group) {
-                Group &g = S.groups[n_groups++];
+                Group g{};
                 g.scene = sid;
                 g.slot0 = s;
-                g.ncam = 0;
-                g.pad = 0;
                 g.n = sd.n;
-                max_bx = std::max<long long>(max_bx, (sd.n + PROJ_THREADS - 1) / PROJ_THREADS);
+                P.groups.push_back(g);
+                ch.n_groups++;
+                ch.max_bx = std::max<long long>(ch.max_bx, (sd.n + PROJ_THREADS - 1) / PROJ_THREADS);
             }
-            S.groups[n_groups - 1].ncam++;
+            P.groups.back().ncam++;
         }
-        CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(mask_words, 1) * 4));
-        CKS(grow(ctx, ctx->woff, (size_t)std::max<long long>(mask_words, 1) * 4));
-        CKC(cudaMemcpyAsync(ctx->cams.p, S.cams, m * sizeof(CamInfo), cudaMemcpyHostToDevice, a.st));
-        CKC(cudaMemcpyAsync(ctx->groups.p, S.groups, n_groups * sizeof(Group),
-                            cudaMemcpyHostToDevice, a.st));
-        cudaEvent_t *E = timing ? &ctx->ev[5 * chunk_id] : nullptr;
-        if (timing) CKC(cudaEventRecord(E[0], a.st));
-        CKC(launch_project_mask((const Group *)ctx->groups.p, n_groups, max_bx,
-                                (const SceneDev *)ctx->d_scenes.p, (const CamInfo *)ctx->cams.p,
-                                a.vm, a.in, P, (uint32_t *)ctx->masks.p, a.st));
-        CKC(launch_scan_masks((const CamInfo *)ctx->cams.p, (const SceneDev *)ctx->d_scenes.p, m,
-                              (const uint32_t *)ctx->masks.p, (uint32_t *)ctx->woff.p,
-                              (int *)ctx->counts.p, a.st));
-        CKC(cudaMemcpyAsync(S.counts, ctx->counts.p, m * sizeof(int), cudaMemcpyDeviceToHost, a.st));
-        CKC(cudaStreamSynchronize(a.st));
+        P.tilepre[tp + ch.m] = ch.tiles_total;
+        tp += ch.m + 1;
+        ch.sort_grid = (int)std::max<long long>(1, std::min<long long>(sort_up, 4 * 1184));
+        ch.bin_grid = (int)std::max<long long>(1, std::min<long long>(bin_up, 4 * 1184));
+        P.max_mask_words = std::max(P.max_mask_words, ch.mask_words);
+        P.max_gauss = std::max(P.max_gauss, ch.n_gauss);
+        P.max_m = std::max(P.max_m, ch.m);
+        P.max_sup = std::max(P.max_sup, ch.max_sup);
+        P.chunks.push_back(ch);
+    }
+    P.off_groups = align_up(P.cams.size() * sizeof(CamInfo), 256);
+    P.off_tilepre = P.off_groups + align_up(std::max<size_t>(P.groups.size(), 1) * sizeof(Group), 256);
+    P.table_bytes = P.off_tilepre + align_up(P.tilepre.size() * sizeof(int), 256);
+}
 
-        // exact sizes of this chunk
-        long long S_total = 0, bm_words = 0;
-        int blocks = 0, sort_tiles = 0;
-        for (int s = 0; s < m; ++s) {
-            CamInfo &ci = S.cams[s];
-            ci.count = S.counts[s];
-            ci.seg_off = S_total;
-            ci.nw = (ci.count + 31) / 32;
-            ci.bm_off = bm_words;
-            S_total += ci.count;
-            bm_words += (long long)((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE) * ci.nw;
-            S.blkpre[s] = blocks;
-            blocks += (ci.count + BIN_RANKS - 1) / BIN_RANKS;
-            S.segstart[s] = ci.seg_off;
-            S.segcount[s] = ci.count;
-            S.sorttiles[s] = sort_tiles;
-            sort_tiles += sort_tiles_for(ci.count);
-        }
-        S.sorttiles[m] = sort_tiles;
-        S.blkpre[m] = blocks;
-        S.tilepre[m] = tiles_total;
-        st.survivors += S_total;
-        const size_t Sx = (size_t)std::max<long long>(S_total, 1);
-        CKS(grow(ctx, ctx->rec, Sx * sizeof(SlotRec)));
-        CKS(grow(ctx, ctx->keys, Sx * 4));
-        CKS(grow(ctx, ctx->vals, Sx * 4));
-        CKS(grow(ctx, ctx->tkeys, Sx * 4));
-        CKS(grow(ctx, ctx->tvals, Sx * 4));
-        CKS(grow(ctx, ctx->rrect, Sx * sizeof(uint2)));
-        CKS(grow(ctx, ctx->srect, Sx * sizeof(uint2)));
-        CKS(grow(ctx, ctx->bitmap, (size_t)std::max<long long>(bm_words, 1) * 4));
-        CKS(grow(ctx, ctx->sorthist, (size_t)std::max(sort_tiles, 1) * 256 * 4));
-        CKC(cudaMemcpyAsync(ctx->cams.p, S.cams, m * sizeof(CamInfo), cudaMemcpyHostToDevice, a.st));
-        CKC(cudaMemcpyAsync(ctx->blkpre.p, S.blkpre, (m + 1) * sizeof(int), cudaMemcpyHostToDevice, a.st));
-        CKC(cudaMemcpyAsync(ctx->tilepre.p, S.tilepre, (m + 1) * sizeof(int), cudaMemcpyHostToDevice, a.st));
-        CKC(cudaMemcpyAsync(ctx->segstart.p, S.segstart, m * sizeof(long long), cudaMemcpyHostToDevice, a.st));
-        CKC(cudaMemcpyAsync(ctx->segcount.p, S.segcount, m * sizeof(long long), cudaMemcpyHostToDevice, a.st));
-        CKC(cudaMemcpyAsync(ctx->sorttiles.p, S.sorttiles, (m + 1) * sizeof(int), cudaMemcpyHostToDevice, a.st));
-        CKC(launch_project_write((const Group *)ctx->groups.p, n_groups, max_bx,
-                                 (const SceneDev *)ctx->d_scenes.p, (const CamInfo *)ctx->cams.p,
-                                 a.vm, a.in, P, (const uint32_t *)ctx->masks.p,
+// Workspace for a chunk of up to max_m cameras and cap_S survivors.
+gs_status size_workspace(gs_context *ctx, const Plan &P) {
+    const long long S = std::max<long long>(ctx->cap_survivors, 1);
+    const size_t Sx = (size_t)S;
+    const int m = std::max(P.max_m, 1);
+    const bool changed = (ctx->rec.cap < Sx * sizeof(SlotRec));
+    CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
+    CKS(grow(ctx, ctx->woff, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
+    CKS(grow(ctx, ctx->counts, (size_t)m * sizeof(int)));
+    CKS(grow(ctx, ctx->rec, Sx * sizeof(SlotRec)));
+    CKS(grow(ctx, ctx->srect, Sx * sizeof(uint2)));
+    CKS(grow(ctx, ctx->rrect, Sx * sizeof(uint2)));
+    CKS(grow(ctx, ctx->keys, Sx * 4));
+    CKS(grow(ctx, ctx->vals, Sx * 4));
+    CKS(grow(ctx, ctx->tkeys, Sx * 4));
+    CKS(grow(ctx, ctx->tvals, Sx * 4));
+    // bounds implied by S: bitmap words <= max_sup * (S/32 + m), sort tiles <= S/2048 + m
+    CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
+    CKS(grow(ctx, ctx->sorthist, (Sx / SORT_TILE_KEYS + m + 1) * 256 * 4));
+    CKS(grow(ctx, ctx->blkpre, (size_t)(m + 1) * sizeof(int)));
+    CKS(grow(ctx, ctx->sorttiles, (size_t)(m + 1) * sizeof(int)));
+    CKS(grow(ctx, ctx->segstart, (size_t)m * sizeof(long long)));
+    CKS(grow(ctx, ctx->segcount, (size_t)m * sizeof(long long)));
+    CKS(grow(ctx, ctx->stats, 8 * sizeof(unsigned long long)));
+    CKS(grow(ctx, ctx->status, 4 * sizeof(long long)));
+    if (changed) ctx->workspace_gen++;
+    return GS_OK;
+}
+
+// Enqueue the whole render on `st` (no host synchronisation). `tab` holds the
+// uploaded static tables of P. With events != NULL, 5 events per chunk are
+// recorded around the stages.
+gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, char *tab,
+                         cudaStream_t st, cudaEvent_t *events) {
+    const gs_config &cfg = ctx->cfg;
+    const ProjParams PP{cfg.near_plane, cfg.dilation, cfg.guard_band, cfg.sigma_cull};
+    const CompParams C{std::log2(cfg.alpha_min), cfg.alpha_max, cfg.T_min,
+                       {cfg.background[0], cfg.background[1], cfg.background[2]}};
+    CamInfo *cams_all = (CamInfo *)tab;
+    Group *groups_all = (Group *)(tab + P.off_groups);
+    int *tilepre_all = (int *)(tab + P.off_tilepre);
+    int *status = (int *)ctx->status.p;
+    long long *need = (long long *)ctx->status.p + 1;
+    unsigned long long *stats = (unsigned long long *)ctx->stats.p;
+    int tp = 0;
+    for (size_t k = 0; k < P.chunks.size(); ++k) {
+        const ChunkPlan &ch = P.chunks[k];
+        CamInfo *cams = cams_all + ch.c0;
+        const Group *groups = groups_all + ch.g0;
+        const int *tilepre = tilepre_all + tp;
+        tp += ch.m + 1;
+        cudaEvent_t *E = events ? events + 5 * k : nullptr;
+        if (E) CKC(cudaEventRecord(E[0], st));
+        CKC(launch_project_mask(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
+                                cams, a.vm, a.in, PP, (uint32_t *)ctx->masks.p, st));
+        CKC(launch_scan_masks(cams, (const SceneDev *)ctx->d_scenes.p, ch.m,
+                              (const uint32_t *)ctx->masks.p, (uint32_t *)ctx->woff.p,
+                              (int *)ctx->counts.p, st));
+        CKC(launch_plan(cams, (const int *)ctx->counts.p, ch.m, ctx->cap_survivors,
+                        (int *)ctx->blkpre.p, (int *)ctx->sorttiles.p, (long long *)ctx->segstart.p,
+                        (long long *)ctx->segcount.p, status, need, stats + 6, st));
+        CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
+                                 cams, a.vm, a.in, PP, (const uint32_t *)ctx->masks.p,
                                  (const uint32_t *)ctx->woff.p, (SlotRec *)ctx->rec.p,
                                  (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p,
-                                 (uint32_t *)ctx->vals.p, std::log(cfg.alpha_min), a.st));
-        if (timing) CKC(cudaEventRecord(E[1], a.st));
+                                 (uint32_t *)ctx->vals.p, std::log(cfg.alpha_min), status, st));
+        if (E) CKC(cudaEventRecord(E[1], st));
         if (a.upto == UPTO_PROJECT) break;
         CKC(launch_sort_segments((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
                                  (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
                                  (const long long *)ctx->segstart.p,
                                  (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
-                                 m, sort_tiles, (uint32_t *)ctx->sorthist.p, a.st));
-        if (timing) CKC(cudaEventRecord(E[2], a.st));
-        CKC(launch_bin((const CamInfo *)ctx->cams.p, (const int *)ctx->blkpre.p, m, blocks, max_sup,
+                                 ch.m, ch.sort_grid, (uint32_t *)ctx->sorthist.p, st,
+                                 (const int *)ctx->sorttiles.p + ch.m));
+        if (E) CKC(cudaEventRecord(E[2], st));
+        CKC(launch_bin(cams, (const int *)ctx->blkpre.p, ch.m, ch.bin_grid, ch.max_sup,
                        (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->vals.p,
-                       (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p,
-                       (unsigned long long *)ctx->stats.p + 2, a.st));
-        if (timing) CKC(cudaEventRecord(E[3], a.st));
+                       (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
+        if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;
-        CKC(launch_composite((const CamInfo *)ctx->cams.p, (const int *)ctx->tilepre.p, m, tiles_total,
-                             (const SlotRec *)ctx->rec.p, (const uint32_t *)ctx->vals.p,
-                             (const uint2 *)ctx->rrect.p, (const uint32_t *)ctx->bitmap.p, C, a.rgb,
-                             a.depth, a.T, (unsigned long long *)ctx->stats.p,
-                             cfg.count_pairs != 0, cfg.pixels_per_thread, a.st));
-        if (timing) {
-            CKC(cudaEventRecord(E[4], a.st));
-            ctx->ev_used = chunk_id + 1;
-        }
+        CKC(launch_composite(cams, tilepre, ch.m, ch.tiles_total, (const SlotRec *)ctx->rec.p,
+                             (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->rrect.p,
+                             (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
+                             cfg.count_pairs != 0, cfg.pixels_per_thread, st));
+        if (E) CKC(cudaEventRecord(E[4], st));
     }
-    st.n_chunks = chunk_id;
-    ctx->last = st;
+    return GS_OK;
+}
+
+gs_status upload_tables(gs_context *ctx, const Plan &P, DevBuf &dst, cudaStream_t st) {
+    CKS(grow_pinned(ctx, ctx->pin[0], P.table_bytes));
+    CKS(grow(ctx, dst, P.table_bytes));
+    char *h = (char *)ctx->pin[0].p;
+    memcpy(h, P.cams.data(), P.cams.size() * sizeof(CamInfo));
+    if (!P.groups.empty()) memcpy(h + P.off_groups, P.groups.data(), P.groups.size() * sizeof(Group));
+    memcpy(h + P.off_tilepre, P.tilepre.data(), P.tilepre.size() * sizeof(int));
+    CKC(cudaMemcpyAsync(dst.p, h, P.table_bytes, cudaMemcpyHostToDevice, st));
+    return GS_OK;
+}
+
+gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
+    Plan P;
+    build_plan(ctx, a, P);
+    if (ctx->cap_survivors <= 0)  // first guess: a third of the Gaussians seen by a chunk
+        ctx->cap_survivors = std::max<long long>(1 << 20, P.max_gauss / 3);
+    const bool timing = ctx->cfg.time_stages != 0;
+    if (timing)
+        while (ctx->ev.size() < 5 * P.chunks.size()) {
+            cudaEvent_t e;
+            CKC(cudaEventCreate(&e));
+            ctx->ev.push_back(e);
+        }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        CKS(size_workspace(ctx, P));
+        CKS(upload_tables(ctx, P, ctx->tables, a.st));
+        CKC(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), a.st));
+        CKC(cudaMemsetAsync(ctx->status.p, 0, 4 * sizeof(long long), a.st));
+        CKS(enqueue_render(ctx, a, P, (char *)ctx->tables.p, a.st, timing ? ctx->ev.data() : nullptr));
+        long long *hs = (long long *)ctx->pin[1].p;
+        CKS(grow_pinned(ctx, ctx->pin[1], 64));
+        hs = (long long *)ctx->pin[1].p;
+        CKC(cudaMemcpyAsync(hs, ctx->status.p, 2 * sizeof(long long), cudaMemcpyDeviceToHost, a.st));
+        CKC(cudaStreamSynchronize(a.st));
+        const int st = (int)(hs[0] & 0xffffffff);
+        if (!st) break;
+        if (attempt == 1)
+            return fail(ctx, GS_ERR_CAPACITY, "workspace overflow after resizing (%lld survivors)",
+                        hs[1]);
+        ctx->cap_survivors = hs[1] + hs[1] / 8 + 1024;  // exact need plus headroom; render again
+    }
+    gs_stats stt{};
+    stt.n_cameras = a.n;
+    stt.n_chunks = (int)P.chunks.size();
+    ctx->last = stt;
+    ctx->ev_used = timing ? (int)P.chunks.size() : 0;
     ctx->stats_pending = true;
     return GS_OK;
 }
@@ -440,7 +475,7 @@ void gs_context_destroy(gs_context *ctx) {
         if (s.storage) cudaFree(s.storage);
     DevBuf *bufs[] = {&ctx->d_scenes, &ctx->masks, &ctx->woff,    &ctx->counts,  &ctx->rec,
                       &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect, &ctx->srect,
-                      &ctx->bitmap,   &ctx->cams,  &ctx->groups,  &ctx->blkpre,  &ctx->tilepre,
+                      &ctx->bitmap,   &ctx->tables, &ctx->status, &ctx->blkpre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
                       &ctx->sorttiles, &ctx->sorthist,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
@@ -621,6 +656,7 @@ gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
         ctx->last.warp_iters = (int64_t)h[3];
         ctx->last.warp_iters_box = (int64_t)h[4];
         ctx->last.warp_iters_blend = (int64_t)h[5];
+        ctx->last.survivors = (int64_t)h[6];
         float ms[4] = {0, 0, 0, 0};
         for (int c = 0; c < ctx->ev_used; ++c) {
             cudaEvent_t *E = &ctx->ev[5 * c];
@@ -656,6 +692,8 @@ gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewm
                  nullptr, nullptr,   nullptr, nullptr,    st,    UPTO_PROJECT};
     CKS(render_impl(ctx, a));
     CKC(cudaStreamSynchronize(st));
+    gs_stats tmp;
+    CKS(gs_get_stats(ctx, &tmp));
     const long long S = ctx->last.survivors;
     *n_out = S;
     if (S > cap) return fail(ctx, GS_ERR_CAPACITY, "%lld survivors > cap %lld", S, (long long)cap);
@@ -701,6 +739,8 @@ gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *vi
                  nullptr, nullptr,   nullptr, nullptr,    st,    UPTO_BIN};
     CKS(render_impl(ctx, a));
     CKC(cudaStreamSynchronize(st));
+    gs_stats tmp;
+    CKS(gs_get_stats(ctx, &tmp));
     const long long S = ctx->last.survivors;
     const int TX = (width + 15) / 16, TY = (height + 15) / 16, tiles = TX * TY;
     const int SX = (TX + STILE - 1) / STILE, SY = (TY + STILE - 1) / STILE;

@@ -76,6 +76,8 @@ struct __align__(16) SlotRec {
 };
 
 constexpr int STILE = 4;  // tiles per super-tile edge (64 x 64 pixels)
+constexpr int SORT_TILE_KEYS = 2048;  // keys per sort tile
+constexpr int GS_STATUS_CAPACITY = 1; // device status word: a chunk exceeded the workspace
 
 // ---- launchers (each defined in its kernel file) ----
 
@@ -93,18 +95,28 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
                                  uint2 *srect, uint32_t *keys, uint32_t *vals,
-                                 float ln_alpha_min, cudaStream_t s);
+                                 float ln_alpha_min, const int *status, cudaStream_t s);
 
 // Segmented sort: tile_start[n_seg + 1] is the prefix of sort_tiles_for(count)
-// over the segments; hist needs 256 uint32 per tile.
+// over the segments; hist needs 256 uint32 per tile. n_tiles blocks are
+// launched; with n_tiles_dev != NULL the kernels loop over the device total
+// *n_tiles_dev (grid-stride), else over n_tiles.
 int sort_tiles_for(long long count);
 cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
                                  uint32_t *tmp_vals, const long long *seg_start,
                                  const long long *seg_count, const int *tile_start, int n_seg,
-                                 int n_tiles, uint32_t *hist, cudaStream_t s);
+                                 int n_tiles, uint32_t *hist, cudaStream_t s,
+                                 const int *n_tiles_dev = nullptr);
+
+// Device-side sizing of a chunk (see k_plan.cu).
+cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, long long cap_survivors,
+                        int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
+                        int *status, long long *need, unsigned long long *survivors,
+                        cudaStream_t s);
 
 // Super-tile bitmaps (one row of ceil(count/32) words per 64x64-pixel
 // super-tile) and the rank-ordered tile rects.
+// n_blocks blocks are launched; they loop over the device total blk_prefix[n_slots].
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
                        int n_super, const uint2 *srect, const uint32_t *vals, uint2 *rrect,
                        uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);

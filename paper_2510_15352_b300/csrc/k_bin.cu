@@ -27,16 +27,18 @@ __global__ void __launch_bounds__(BIN_RANKS)
           uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
           unsigned long long *__restrict__ n_isect) {
     extern __shared__ uint32_t sbm[];  // [super-tiles][BIN_WORDS]
+    const int nblk = blk_prefix[n_slots];
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     int lo = 0, hi = n_slots - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (blk_prefix[mid] <= (int)blockIdx.x)
+        if (blk_prefix[mid] <= blk)
             lo = mid;
         else
             hi = mid - 1;
     }
     const CamInfo ci = cams[lo];
-    const int r0 = ((int)blockIdx.x - blk_prefix[lo]) * BIN_RANKS;
+    const int r0 = (blk - blk_prefix[lo]) * BIN_RANKS;
     const int SX = (ci.TX + STILE - 1) / STILE, SY = (ci.TY + STILE - 1) / STILE;
     const int nsup = SX * SY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -68,6 +70,8 @@ __global__ void __launch_bounds__(BIN_RANKS)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) area += __shfl_down_sync(0xffffffffu, area, o);
     if (lane == 0 && area) atomicAdd(n_isect, area);
+    __syncthreads();  // sbm is cleared for the next block of ranks
+    }
 }
 
 }  // namespace

@@ -1,0 +1,125 @@
+// k_plan.cu -- device-side sizing of one chunk, so that a render needs no host
+// round trip between its kernels (and can be captured in a CUDA graph).
+//
+// From the per-camera survivor counts it writes each camera's survivor slot
+// offset, bitmap words and offsets, the prefix tables of the binning blocks and
+// of the sort tiles, and the segment table of the sort. When the chunk's
+// survivors exceed the workspace, it records the size needed, raises the status
+// word and plans an empty chunk (every count 0), so the later kernels do
+// nothing and the host can grow the workspace and render again.
+#include "gs_internal.cuh"
+
+namespace gsk {
+
+namespace {
+
+constexpr int PT = 1024;
+
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T &total, T *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    T before = 0;
+    total = 0;
+    for (int w = 0; w < PT / 32; ++w) {
+        const T x = wsum[w];
+        before += w < warp ? x : (T)0;
+        total += x;
+    }
+    __syncthreads();
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(PT)
+    k_plan(CamInfo *__restrict__ cams, const int *__restrict__ counts, int m,
+           long long cap_survivors, int *__restrict__ blkpre, int *__restrict__ sorttiles,
+           long long *__restrict__ segstart, long long *__restrict__ segcount,
+           int *__restrict__ status, long long *__restrict__ need,
+           unsigned long long *__restrict__ survivors) {
+    __shared__ long long ws64[PT / 32];
+    __shared__ int ws32[PT / 32];
+    __shared__ long long carry_s, carry_bm;
+    __shared__ int carry_bb, carry_st, overflow;
+    const int tid = threadIdx.x;
+    // 1. is the chunk's survivor total within the workspace?
+    long long part = 0;
+    for (int i = tid; i < m; i += PT) part += counts[i];
+    long long tot;
+    block_excl_scan<long long>(part, tot, ws64);
+    if (tid == 0) {
+        overflow = tot > cap_survivors;
+        if (overflow) {
+            *status = GS_STATUS_CAPACITY;
+            atomicMax((unsigned long long *)need, (unsigned long long)tot);
+        } else {
+            atomicAdd(survivors, (unsigned long long)tot);
+        }
+        carry_s = carry_bm = 0;
+        carry_bb = carry_st = 0;
+    }
+    __syncthreads();
+    // 2. offsets (all zero-sized when the chunk does not fit)
+    for (int b = 0; b < m; b += PT) {
+        const int i = b + tid;
+        long long c = 0, bmw = 0;
+        int bb = 0, st = 0, nw = 0;
+        if (i < m && !overflow) {
+            const CamInfo ci = cams[i];
+            c = counts[i];
+            nw = (int)((c + 31) / 32);
+            const int nsup = ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE);
+            bmw = (long long)nsup * nw;
+            bb = (int)((c + BIN_RANKS - 1) / BIN_RANKS);
+            st = (int)((c + SORT_TILE_KEYS - 1) / SORT_TILE_KEYS);
+        }
+        long long t_s, t_bm;
+        int t_bb, t_st;
+        const long long off_s = block_excl_scan<long long>(c, t_s, ws64) + carry_s;
+        const long long off_bm = block_excl_scan<long long>(bmw, t_bm, ws64) + carry_bm;
+        const int off_bb = block_excl_scan<int>(bb, t_bb, ws32) + carry_bb;
+        const int off_st = block_excl_scan<int>(st, t_st, ws32) + carry_st;
+        if (i < m) {
+            cams[i].count = (int)c;
+            cams[i].seg_off = off_s;
+            cams[i].nw = nw;
+            cams[i].bm_off = off_bm;
+            blkpre[i] = off_bb;
+            sorttiles[i] = off_st;
+            segstart[i] = off_s;
+            segcount[i] = c;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            carry_s += t_s;
+            carry_bm += t_bm;
+            carry_bb += t_bb;
+            carry_st += t_st;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        blkpre[m] = carry_bb;
+        sorttiles[m] = carry_st;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, long long cap_survivors,
+                        int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
+                        int *status, long long *need, unsigned long long *survivors,
+                        cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    k_plan<<<1, PT, 0, s>>>(cams, counts, m, cap_survivors, blkpre, sorttiles, segstart, segcount,
+                            status, need, survivors);
+    return cudaGetLastError();
+}
+
+}  // namespace gsk

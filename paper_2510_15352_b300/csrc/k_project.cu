@@ -370,10 +370,11 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
                     SlotRec *__restrict__ rec, uint2 *__restrict__ srect,
                     uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                    float ln_alpha_min) {
+                    float ln_alpha_min, const int *__restrict__ status) {
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * WG;
     if (g0 >= gr.n) return;
+    if (status && *status) return;  // the chunk was planned empty: workspace too small
     constexpr int NE = MAX_GROUP * (WG / 32);  // (camera, mask word) entries
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long soff[MAX_GROUP];
@@ -538,7 +539,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
                                  uint2 *srect, uint32_t *keys, uint32_t *vals,
-                                 float ln_alpha_min, cudaStream_t s) {
+                                 float ln_alpha_min, const int *status, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(2 * max_blocks_x, n_groups);  // 128 Gaussians per block
     const int smem = 48 * WG * (int)sizeof(float);         // SH of degree <= 3
@@ -547,7 +548,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
     if (e != cudaSuccess) return e;
     k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, viewmats, intr, P,
                                                      masks, woff, rec, srect, keys, vals,
-                                                     ln_alpha_min);
+                                                     ln_alpha_min, status);
     return cudaGetLastError();
 }
 

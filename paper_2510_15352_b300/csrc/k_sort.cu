@@ -46,9 +46,11 @@ __device__ __forceinline__ int find_seg(const int *__restrict__ tile_start, int 
 __global__ void __launch_bounds__(ST)
     k_sort_hist(const uint32_t *__restrict__ keys, const long long *__restrict__ seg_start,
                 const long long *__restrict__ seg_count, const int *__restrict__ tile_start,
-                int n_seg, int shift, uint32_t *__restrict__ hist) {
+                int n_seg, int shift, uint32_t *__restrict__ hist, const int *__restrict__ nt_dev,
+                int nt_host) {
     __shared__ uint32_t h[256];
-    const int tile = blockIdx.x;
+    const int nt = nt_dev ? *nt_dev : nt_host;
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
     const int s = find_seg(tile_start, n_seg, tile);
     const long long i0 = (long long)(tile - tile_start[s]) * TK;
     const long long n = seg_count[s];
@@ -62,6 +64,8 @@ __global__ void __launch_bounds__(ST)
     }
     __syncthreads();
     hist[(long long)tile * 256 + threadIdx.x] = h[threadIdx.x];
+    __syncthreads();  // h is cleared for the next tile of this block
+    }
 }
 
 // One block per segment; thread d owns digit d. In place: hist[tile][d]
@@ -111,11 +115,12 @@ __global__ void __launch_bounds__(ST)
                    uint32_t *__restrict__ dk, uint32_t *__restrict__ dv,
                    const long long *__restrict__ seg_start, const long long *__restrict__ seg_count,
                    const int *__restrict__ tile_start, int n_seg, int shift,
-                   const uint32_t *__restrict__ offs) {
+                   const uint32_t *__restrict__ offs, const int *__restrict__ nt_dev, int nt_host) {
     __shared__ uint32_t wcnt[SNW][256];
     __shared__ uint32_t toff[256];
-    const int tile = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nt = nt_dev ? *nt_dev : nt_host;
+    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
     const int s = find_seg(tile_start, n_seg, tile);
     const long long base = seg_start[s];
     const long long i0 = (long long)(tile - tile_start[s]) * TK + (long long)warp * (32 * SIPT);
@@ -168,6 +173,8 @@ __global__ void __launch_bounds__(ST)
             dv[pos] = vr[r];
         }
     }
+    __syncthreads();  // toff / wcnt are rebuilt for the next tile of this block
+    }
 }
 
 }  // namespace
@@ -177,16 +184,17 @@ int sort_tiles_for(long long count) { return (int)((count + TK - 1) / TK); }
 cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
                                  uint32_t *tmp_vals, const long long *seg_start,
                                  const long long *seg_count, const int *tile_start, int n_seg,
-                                 int n_tiles, uint32_t *hist, cudaStream_t s) {
+                                 int n_tiles, uint32_t *hist, cudaStream_t s,
+                                 const int *n_tiles_dev) {
     if (n_seg == 0 || n_tiles == 0) return cudaSuccess;
     uint32_t *src_k = keys, *src_v = vals, *dst_k = tmp_keys, *dst_v = tmp_vals;
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         k_sort_hist<<<n_tiles, ST, 0, s>>>(src_k, seg_start, seg_count, tile_start, n_seg, shift,
-                                           hist);
+                                           hist, n_tiles_dev, n_tiles);
         k_sort_offsets<<<n_seg, 256, 0, s>>>(tile_start, hist);
         k_sort_scatter<<<n_tiles, ST, 0, s>>>(src_k, src_v, dst_k, dst_v, seg_start, seg_count,
-                                              tile_start, n_seg, shift, hist);
+                                              tile_start, n_seg, shift, hist, n_tiles_dev, n_tiles);
         uint32_t *t;
         t = src_k; src_k = dst_k; dst_k = t;
         t = src_v; src_v = dst_v; dst_v = t;
