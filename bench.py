@@ -180,12 +180,20 @@ def run_b300_batched(args):
     torch.cuda.synchronize()
     cst = counter.stats()
     counter.close()
-    R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
-                    pixels_per_thread=args.ppt)
+    R = gs.Renderer(device=local, time_stages=0 if args.graph else 1,
+                    max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt)
     ids = np.array([R.add_scene(s) for s in scenes], dtype=np.int32)[which]
     stream = torch.cuda.current_stream()
+    graph = R.graph(ids, vm_d, it_d, Ws, Hs, rgb, depth) if args.graph else None
+
+    def step():
+        if graph is not None:
+            graph.launch(stream)
+        else:
+            R.render_v(ids, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
+
     for _ in range(args.warmup):
-        R.render_v(ids, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
+        step()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -194,14 +202,28 @@ def run_b300_batched(args):
     ms_comp, stage_ms = 0.0, {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
     ev0.record(stream)
     for _ in range(args.steps):
-        R.render_v(ids, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
-        st = R.stats()
-        for k in stage_ms:
-            stage_ms[k] += st["ms_" + k]
+        step()
+        if graph is None:
+            st = R.stats()
+            for k in stage_ms:
+                stage_ms[k] += st["ms_" + k]
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
+    if graph is not None:
+        graph.check(stream)
+        # stage times from one eager render of the same batch (events inside a
+        # graph replay are not read back)
+        R2 = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
+                         pixels_per_thread=args.ppt)
+        ids2 = np.array([R2.add_scene(s) for s in scenes], dtype=np.int32)[which]
+        for _ in range(2):
+            R2.render_v(ids2, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
+        st = R2.stats()
+        stage_ms = {k: st["ms_" + k] * args.steps for k in stage_ms}
+        R2.close()
+        graph.close()
     eq_frames = P / (640 * 480)
     achieved = F_PAIR * cst["pairs_alpha"] / (stage_ms["composite"] / args.steps / 1e3) / 1e12
     out = {
@@ -213,7 +235,8 @@ def run_b300_batched(args):
                    "scenes": len(scenes), "gaussians": int(sum(s["mean"].shape[1] for s in scenes)),
                    "cameras_640x480": int((Ws == 640).sum()), "cameras_320x240": int((Ws == 320).sum()),
                    "frames_640x480_equivalent": eq_frames, "chunk_cameras": args.chunk,
-                   "pixels_per_thread": args.ppt, "storage": args.precision},
+                   "pixels_per_thread": args.ppt, "storage": args.precision,
+                   "cuda_graph": bool(args.graph)},
         "roofline": {"kernel": "k_composite", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
@@ -375,6 +398,8 @@ def main():
     ap.add_argument("--precision", choices=["f32", "half"], default="f32",
                     help="scene attribute storage (half: FP16 geometry, BF16 appearance)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--graph", action="store_true",
+                    help="time replays of one captured CUDA graph (batched workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -115,6 +115,7 @@ typedef struct gs_stats {
 } gs_stats;
 
 typedef struct gs_context gs_context;
+typedef struct gs_graph gs_graph;
 
 /* Library ABI version (changes when a struct layout or signature changes). */
 int32_t gs_abi_version(void);
@@ -175,6 +176,34 @@ gs_status gs_render_batch_v(gs_context *ctx, int32_t n_cams, const int32_t *scen
                             const int32_t *widths, const int32_t *heights,
                             const int64_t *pixel_offsets, float *rgb, float *depth,
                             float *final_T, void *stream);
+
+/* Record the render of a fixed batch of cameras (arguments as gs_render_batch_v,
+ * no stream) into a CUDA graph. The call renders the batch once (which sizes the
+ * workspace; the graph keeps 1.25x headroom over the survivors it saw), then
+ * captures the whole kernel sequence -- projection, sort, binning, compositing
+ * for every chunk, with no host round trip inside -- into one graph. Later
+ * launches read the cameras from and write the images to the same device
+ * addresses: update viewmats / intrinsics in place between launches. A graph
+ * uses its context's workspace: renders on that context (eager or other
+ * graphs) must not overlap its launches, and an eager render that has to grow
+ * the workspace invalidates it (gs_graph_launch then returns INVALID_ARG). */
+gs_status gs_graph_create(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                          const float *viewmats, const float *intrinsics,
+                          const int32_t *widths, const int32_t *heights,
+                          const int64_t *pixel_offsets, float *rgb, float *depth,
+                          float *final_T, gs_graph **out);
+
+/* Enqueue one replay of the graph on `stream` (no host synchronisation). */
+gs_status gs_graph_launch(gs_graph *g, void *stream);
+
+/* Wait for `stream` and report whether the last replay fitted the workspace:
+ * GS_ERR_CAPACITY when cameras moved so that a chunk had more survivors than
+ * the workspace holds (that chunk's images are left as background); render
+ * eagerly once and create the graph again. */
+gs_status gs_graph_check(gs_graph *g, void *stream);
+
+/* Free the graph (NULL is a no-op). */
+void gs_graph_destroy(gs_graph *g);
 
 /* Same as gs_render_batch with every array in HOST memory: the call copies the
  * cameras to the device, renders into context-owned device buffers and copies

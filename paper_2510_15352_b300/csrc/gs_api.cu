@@ -59,6 +59,7 @@ struct gs_context {
     DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, srect, bitmap;
     DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist;
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
+    long long last_chunk_survivors = 0;  // largest chunk of the last render
     int workspace_gen = 0;        // bumped when the survivor buffers are reallocated
     // host-API staging
     DevBuf h_vm, h_in, h_rgb, h_depth, h_T;
@@ -68,6 +69,14 @@ struct gs_context {
     std::string err;
     std::vector<cudaEvent_t> ev;  // time_stages: 5 events per chunk of the last call
     int ev_used = 0;              // chunks whose events the last call recorded
+};
+
+struct gs_graph {
+    gs_context *ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    DevBuf tables;  // this graph's copy of the static per-camera tables
+    int gen = 0;    // the context's workspace generation at capture
 };
 
 namespace {
@@ -229,8 +238,8 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
         }
         P.tilepre[tp + ch.m] = ch.tiles_total;
         tp += ch.m + 1;
-        ch.sort_grid = (int)std::max<long long>(1, std::min<long long>(sort_up, 4 * 1184));
-        ch.bin_grid = (int)std::max<long long>(1, std::min<long long>(bin_up, 4 * 1184));
+        ch.sort_grid = (int)std::max<long long>(1, std::min<long long>(sort_up, 32 * 1184));
+        ch.bin_grid = (int)std::max<long long>(1, std::min<long long>(bin_up, 32 * 1184));
         P.max_mask_words = std::max(P.max_mask_words, ch.mask_words);
         P.max_gauss = std::max(P.max_gauss, ch.n_gauss);
         P.max_m = std::max(P.max_m, ch.m);
@@ -372,6 +381,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
                         hs[1]);
         ctx->cap_survivors = hs[1] + hs[1] / 8 + 1024;  // exact need plus headroom; render again
     }
+    ctx->last_chunk_survivors = ((long long *)ctx->pin[1].p)[1];
     gs_stats stt{};
     stt.n_cameras = a.n;
     stt.n_chunks = (int)P.chunks.size();
@@ -603,6 +613,105 @@ gs_status gs_render_batch_v(gs_context *ctx, int32_t n_cams, const int32_t *scen
                  0,      widths,    heights,  pixel_offsets, rgb,
                  depth,  final_T,   (cudaStream_t)stream, UPTO_ALL};
     return render_impl(ctx, a);
+}
+
+gs_status gs_graph_create(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                          const float *viewmats, const float *intrinsics, const int32_t *widths,
+                          const int32_t *heights, const int64_t *pixel_offsets, float *rgb,
+                          float *depth, float *final_T, gs_graph **out) {
+    if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_cams < 1) return fail(ctx, GS_ERR_INVALID_ARG, "a graph needs at least one camera");
+    // size everything with one eager render of the same cameras
+    CKS(gs_render_batch_v(ctx, n_cams, scene_ids, viewmats, intrinsics, widths, heights,
+                          pixel_offsets, rgb, depth, final_T, nullptr));
+    CKC(cudaDeviceSynchronize());
+    RenderArgs a{n_cams, scene_ids, viewmats, intrinsics, 0,
+                 0,      widths,    heights,  pixel_offsets, rgb,
+                 depth,  final_T,   nullptr,  UPTO_ALL};
+    Plan P;
+    build_plan(ctx, a, P);
+    // headroom for cameras that move between launches: 1.25x the largest chunk seen
+    const long long want = ctx->last_chunk_survivors + ctx->last_chunk_survivors / 4 + 4096;
+    if (want > ctx->cap_survivors) ctx->cap_survivors = want;
+    CKS(size_workspace(ctx, P));
+    gs_graph *g = new gs_graph();
+    g->ctx = ctx;
+    cudaStream_t cs = nullptr;
+    gs_status rc = GS_OK;
+    do {
+        if (upload_tables(ctx, P, g->tables, nullptr) != GS_OK) { rc = GS_ERR_CUDA; break; }
+        if (cudaDeviceSynchronize() != cudaSuccess) { rc = GS_ERR_CUDA; break; }
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = GS_ERR_CUDA;
+            break;
+        }
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = GS_ERR_CUDA;
+            break;
+        }
+        RenderArgs ac = a;
+        ac.st = cs;
+        gs_status e1 = GS_OK;
+        if (cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), cs) != cudaSuccess ||
+            cudaMemsetAsync(ctx->status.p, 0, 4 * sizeof(long long), cs) != cudaSuccess)
+            e1 = GS_ERR_CUDA;
+        if (e1 == GS_OK) e1 = enqueue_render(ctx, ac, P, (char *)g->tables.p, cs, nullptr);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+        if (e1 != GS_OK || e2 != cudaSuccess) {
+            rc = e1 != GS_OK ? e1 : GS_ERR_CUDA;
+            if (e2 != cudaSuccess) fail(ctx, rc, "graph capture: %s", cudaGetErrorString(e2));
+            break;
+        }
+        const cudaError_t e3 = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (e3 != cudaSuccess) {
+            rc = fail(ctx, GS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
+            break;
+        }
+    } while (0);
+    if (cs) cudaStreamDestroy(cs);
+    if (rc != GS_OK) {
+        gs_graph_destroy(g);
+        return rc;
+    }
+    g->gen = ctx->workspace_gen;
+    ctx->stats_pending = false;
+    *out = g;
+    return GS_OK;
+}
+
+gs_status gs_graph_launch(gs_graph *g, void *stream) {
+    if (!g || !g->exec) return GS_ERR_INVALID_ARG;
+    gs_context *ctx = g->ctx;
+    if (g->gen != ctx->workspace_gen)
+        return fail(ctx, GS_ERR_INVALID_ARG,
+                    "the context's workspace was reallocated after capture: create the graph again");
+    CKC(cudaSetDevice(ctx->device));
+    CKC(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return GS_OK;
+}
+
+gs_status gs_graph_check(gs_graph *g, void *stream) {
+    if (!g) return GS_ERR_INVALID_ARG;
+    gs_context *ctx = g->ctx;
+    CKC(cudaSetDevice(ctx->device));
+    CKC(cudaStreamSynchronize((cudaStream_t)stream));
+    long long h[2];
+    CKC(cudaMemcpy(h, ctx->status.p, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[0] & 0xffffffff)
+        return fail(ctx, GS_ERR_CAPACITY,
+                    "a graph launch exceeded the workspace (%lld survivors in a chunk): "
+                    "render eagerly once and create the graph again", h[1]);
+    return GS_OK;
+}
+
+void gs_graph_destroy(gs_graph *g) {
+    if (!g) return;
+    if (g->ctx) cudaSetDevice(g->ctx->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->tables.p) cudaFree(g->tables.p);
+    delete g;
 }
 
 gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,

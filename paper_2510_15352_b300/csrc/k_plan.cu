@@ -55,12 +55,11 @@ __global__ void __launch_bounds__(PT)
     block_excl_scan<long long>(part, tot, ws64);
     if (tid == 0) {
         overflow = tot > cap_survivors;
-        if (overflow) {
+        atomicMax((unsigned long long *)need, (unsigned long long)tot);  // largest chunk
+        if (overflow)
             *status = GS_STATUS_CAPACITY;
-            atomicMax((unsigned long long *)need, (unsigned long long)tot);
-        } else {
+        else
             atomicAdd(survivors, (unsigned long long)tot);
-        }
         carry_s = carry_bm = 0;
         carry_bb = carry_st = 0;
     }

@@ -70,6 +70,11 @@ SIGNATURES = {
                                             _vp, _vp]),
     "gs_render_batch_v": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                          _vp]),
+    "gs_graph_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                       ctypes.POINTER(_vp)]),
+    "gs_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "gs_graph_check": (ctypes.c_int, [_vp, _vp]),
+    "gs_graph_destroy": (None, [_vp]),
     "gs_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gs_stats)]),
     "gs_debug_project": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64,
                                         ctypes.POINTER(_i64), _vp]),
@@ -109,6 +114,10 @@ gs_scene_destroy = lib.gs_scene_destroy
 gs_render_batch = lib.gs_render_batch
 gs_render_batch_host = lib.gs_render_batch_host
 gs_render_batch_v = lib.gs_render_batch_v
+gs_graph_create = lib.gs_graph_create
+gs_graph_launch = lib.gs_graph_launch
+gs_graph_check = lib.gs_graph_check
+gs_graph_destroy = lib.gs_graph_destroy
 gs_get_stats = lib.gs_get_stats
 gs_debug_project = lib.gs_debug_project
 gs_debug_tile_lists = lib.gs_debug_tile_lists
@@ -258,6 +267,22 @@ class Renderer:
                                       _stream(stream)))
         return rgb, depth, final_T, off
 
+    def graph(self, scene_ids, viewmats, intrinsics, widths, heights, rgb, depth, final_T=None):
+        """Capture the render of these cameras into a CUDA graph (outputs packed as
+        in render_v, which must be preallocated). Returns a Graph."""
+        n = int(viewmats.shape[0])
+        ids = np.ascontiguousarray(np.broadcast_to(np.asarray(scene_ids, dtype=np.int32), (n,)))
+        w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        h = np.ascontiguousarray(np.asarray(heights, dtype=np.int32))
+        sizes = w.astype(np.int64) * h
+        off = np.ascontiguousarray(np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64))
+        g = ctypes.c_void_p()
+        self._check(gs_graph_create(self.ctx, n, ids.ctypes.data, viewmats.data_ptr(),
+                                    intrinsics.data_ptr(), w.ctypes.data, h.ctypes.data,
+                                    off.ctypes.data, rgb.data_ptr(), depth.data_ptr(),
+                                    _ptr(final_T), ctypes.byref(g)))
+        return Graph(self, g, off)
+
     def render_host(self, scene_ids, viewmats, intrinsics, W: int, H: int, rgb, depth,
                     final_T=None, stream=None):
         """Render with every array in host memory (pinned tensors copy fastest)."""
@@ -300,3 +325,30 @@ class Renderer:
         self._check(gs_sort_segments(self.ctx, keys.data_ptr(), vals.data_ptr(), keys.numel(),
                                      seg_start.data_ptr(), seg_count.data_ptr(),
                                      int(seg_start.numel()), _stream(stream)))
+
+
+class Graph:
+    """A captured render: launch() replays it on a stream; check() waits and
+    reports a workspace overflow of the last replay."""
+
+    def __init__(self, renderer: Renderer, handle, offsets):
+        self.r = renderer
+        self.h = handle
+        self.offsets = offsets
+
+    def launch(self, stream=None):
+        self.r._check(gs_graph_launch(self.h, _stream(stream)))
+
+    def check(self, stream=None):
+        self.r._check(gs_graph_check(self.h, _stream(stream)))
+
+    def close(self):
+        if self.h:
+            gs_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
