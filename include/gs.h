@@ -69,7 +69,11 @@ typedef struct gs_config {
     int32_t time_stages;   /* 1: record CUDA events around every stage on the render
                               stream; gs_get_stats reports the per-stage device time */
     int32_t pixels_per_thread; /* compositing layout: 2, 4 or 8 pixels per thread (8) */
-    int32_t reserved[7];
+    int32_t reserved0;
+    int64_t workspace_survivors; /* surviving (camera, Gaussian) pairs per chunk the
+                                    workspace starts with (0: a third of the Gaussians a
+                                    chunk sees); it grows when a render needs more */
+    int32_t reserved[4];
 } gs_config;
 
 /* A scene: n Gaussians stored as structure of arrays.

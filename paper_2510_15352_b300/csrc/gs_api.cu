@@ -354,8 +354,10 @@ gs_status upload_tables(gs_context *ctx, const Plan &P, DevBuf &dst, cudaStream_
 gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     Plan P;
     build_plan(ctx, a, P);
-    if (ctx->cap_survivors <= 0)  // first guess: a third of the Gaussians seen by a chunk
-        ctx->cap_survivors = std::max<long long>(1 << 20, P.max_gauss / 3);
+    if (ctx->cap_survivors <= 0)  // configured, else a third of the Gaussians a chunk sees
+        ctx->cap_survivors = ctx->cfg.workspace_survivors > 0
+                                 ? ctx->cfg.workspace_survivors
+                                 : std::max<long long>(1 << 20, P.max_gauss / 3);
     const bool timing = ctx->cfg.time_stages != 0;
     if (timing)
         while (ctx->ev.size() < 5 * P.chunks.size()) {
@@ -419,7 +421,7 @@ gs_status validate(gs_context *ctx, int n, const int32_t *scene_ids, const void 
 
 extern "C" {
 
-int32_t gs_abi_version(void) { return 2; }
+int32_t gs_abi_version(void) { return 3; }
 
 const char *gs_status_string(gs_status s) {
     switch (s) {
@@ -463,7 +465,7 @@ gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **o
     if (!(c.near_plane > 0.0f) || !(c.dilation >= 0.0f) || !(c.sigma_cull > 0.0f) ||
         !(c.alpha_min > 0.0f) || !(c.alpha_max > 0.0f && c.alpha_max < 1.0f) ||
         !(c.T_min > 0.0f && c.T_min < 1.0f) || c.max_chunk_cameras < 1 || c.camera_group < 1 ||
-        c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) ||
+        c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) || c.workspace_survivors < 0 ||
         (c.pixels_per_thread != 2 && c.pixels_per_thread != 4 && c.pixels_per_thread != 8))
         return GS_ERR_INVALID_ARG;
     int ndev = 0;

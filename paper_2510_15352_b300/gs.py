@@ -15,7 +15,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgs_b300.so")
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, \
     GS_ERR_NOT_FOUND = range(7)
@@ -30,7 +30,8 @@ class gs_config(ctypes.Structure):
                 ("T_min", ctypes.c_float), ("background", ctypes.c_float * 3),
                 ("max_chunk_cameras", ctypes.c_int32), ("camera_group", ctypes.c_int32),
                 ("count_pairs", ctypes.c_int32), ("time_stages", ctypes.c_int32),
-                ("pixels_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("pixels_per_thread", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("workspace_survivors", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4)]
 
 
 class gs_scene_desc(ctypes.Structure):

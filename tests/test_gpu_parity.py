@@ -351,6 +351,21 @@ def test_host_entry_point_equals_device_entry_point(torch, R):
         R.remove_scene(sid)
 
 
+def test_workspace_overflow_is_retried(torch, gsmod, orc):
+    """A workspace far too small for the batch: the first pass overflows, the
+    call grows it to the exact need and renders again, with the same result."""
+    scene, vm, it, W, H = small_workload()
+    r = gsmod.Renderer(device=0, workspace_survivors=10)
+    try:
+        sid = r.add_scene(scene)
+        rgb, depth, T = render_np(torch, r, sid, vm, it, W, H)
+        for c in (0, 7):
+            ref = orc.render(scene, vm[c], it[c], W, H, bands=BANDS)
+            assert_camera_parity(rgb[c], depth[c], T[c], ref)
+    finally:
+        r.close()
+
+
 def test_errors_are_reported(torch, gsmod, R):
     vm, it = identity_camera(32, 32, 30.0)
     with pytest.raises(gsmod.GSError) as e:
