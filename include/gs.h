@@ -181,6 +181,21 @@ gs_status gs_render_batch_v(gs_context *ctx, int32_t n_cams, const int32_t *scen
                             const int64_t *pixel_offsets, float *rgb, float *depth,
                             float *final_T, void *stream);
 
+/* Motion blur as the paper simulates it (Sec. 3.3, Fig. 9): `samples` frames
+ * whose camera centres are moved along the camera's velocity, by
+ * velocity * shutter * (j/(samples-1) - 1/2) for frame j (orientation kept),
+ * rendered and blended with equal weights 1/samples into one image per camera
+ * (rgb, depth and final_T alike). samples = 1 is a plain render.
+ *   velocities  DEVICE [n_cams][3] float32, world-frame camera velocity (m/s)
+ *   shutter     exposure time in seconds (>= 0); samples in 1..64
+ * Other arguments and errors as gs_render_batch (outputs must not alias the
+ * inputs; the frames are accumulated in rgb / depth / final_T). */
+gs_status gs_render_motion_blur(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                                const float *viewmats, const float *intrinsics,
+                                const float *velocities, float shutter, int32_t samples,
+                                int32_t width, int32_t height, float *rgb, float *depth,
+                                float *final_T, void *stream);
+
 /* Record the render of a fixed batch of cameras (arguments as gs_render_batch_v,
  * no stream) into a CUDA graph. The call renders the batch once (which sizes the
  * workspace; the graph keeps 1.25x headroom over the survivors it saw), then
@@ -202,8 +217,8 @@ gs_status gs_graph_launch(gs_graph *g, void *stream);
 
 /* Wait for `stream` and report whether the last replay fitted the workspace:
  * GS_ERR_CAPACITY when cameras moved so that a chunk had more survivors than
- * the workspace holds (that chunk's images are left as background); render
- * eagerly once and create the graph again. */
+ * the workspace holds (that chunk's images are not written); render eagerly
+ * once and create the graph again. */
 gs_status gs_graph_check(gs_graph *g, void *stream);
 
 /* Free the graph (NULL is a no-op). */

@@ -233,6 +233,47 @@ class Oracle:
                 "n_alpha": n_alpha, "leaf_pix": lp[:tot], "leaf_val": lv[:tot]}
 
 
+def blur_poses(viewmat, velocity, shutter: float, samples: int) -> list:
+    """Motion-blur sub-frame poses (Sec. 3.3, Fig. 9: frames offset along the
+    camera's velocity, then blended): frame j moves the camera centre by
+    velocity * shutter * (j/(samples-1) - 1/2), orientation kept, so the
+    world->camera translation becomes t - R d. Double precision."""
+    V = _f64(viewmat).reshape(4, 4)
+    R, t = V[:3, :3], V[:3, 3]
+    v = _f64(velocity).reshape(3)
+    out = []
+    for j in range(samples):
+        frac = j / (samples - 1) - 0.5 if samples > 1 else 0.0
+        W = V.copy()
+        W[:3, 3] = t - R @ (v * shutter * frac)
+        out.append(W)
+    return out
+
+
+def render_motion_blur(orc: "Oracle", scene, viewmat, intr, velocity, shutter: float,
+                       samples: int, W: int, H: int, params=None, bands=None) -> dict:
+    """Equal-weight blend of the sub-frame renders (rgb, depth and T). For each
+    pixel, `allow` bounds how far a float32 renderer may drift from the blend
+    through near-threshold decisions: the mean over sub-frames of the largest
+    gap between that sub-frame's alternative results and its primary one."""
+    acc = None
+    for V in blur_poses(viewmat, velocity, shutter, samples):
+        r = orc.render(scene, V, intr, W, H, params, bands)
+        gap = np.zeros((H, W))
+        if len(r["leaf_pix"]):
+            prim = np.concatenate([r["rgb"].reshape(-1, 3), r["depth"].reshape(-1, 1),
+                                   r["T"].reshape(-1, 1)], axis=1)
+            d = np.abs(r["leaf_val"] - prim[r["leaf_pix"]]).max(axis=1)
+            np.maximum.at(gap.reshape(-1), r["leaf_pix"], d)
+        part = {"rgb": r["rgb"], "depth": r["depth"], "T": r["T"], "allow": gap}
+        if acc is None:
+            acc = {k: v / samples for k, v in part.items()}
+        else:
+            for k in acc:
+                acc[k] = acc[k] + part[k] / samples
+    return acc
+
+
 _default = None
 
 

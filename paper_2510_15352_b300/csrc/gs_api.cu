@@ -63,6 +63,7 @@ struct gs_context {
     int workspace_gen = 0;        // bumped when the survivor buffers are reallocated
     // host-API staging
     DevBuf h_vm, h_in, h_rgb, h_depth, h_T;
+    DevBuf blur_vm;  // motion-blur sub-frame poses
     PinBuf pin[2];
     gs_stats last{};
     bool stats_pending = false;
@@ -77,6 +78,7 @@ struct gs_graph {
     cudaGraphExec_t exec = nullptr;
     DevBuf tables;  // this graph's copy of the static per-camera tables
     int gen = 0;    // the context's workspace generation at capture
+    int n_chunks = 0;
 };
 
 namespace {
@@ -156,6 +158,8 @@ struct RenderArgs {
     float *rgb, *depth, *T;    // device
     cudaStream_t st;
     Stage upto;
+    float out_w = 1.0f;        // outputs = out_w * value (+ existing outputs if accumulate)
+    int accumulate = 0;
     int cam_w(int i) const { return Ws ? Ws[i] : W; }
     int cam_h(int i) const { return Hs ? Hs[i] : H; }
     long long cam_pix(int i) const { return pix_off ? pix_off[i] : (long long)i * W * H; }
@@ -275,7 +279,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->segstart, (size_t)m * sizeof(long long)));
     CKS(grow(ctx, ctx->segcount, (size_t)m * sizeof(long long)));
     CKS(grow(ctx, ctx->stats, 8 * sizeof(unsigned long long)));
-    CKS(grow(ctx, ctx->status, 4 * sizeof(long long)));
+    CKS(grow(ctx, ctx->status, (P.chunks.size() + 2) * sizeof(long long)));
     if (changed) ctx->workspace_gen++;
     return GS_OK;
 }
@@ -284,16 +288,21 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
 // uploaded static tables of P. With events != NULL, 5 events per chunk are
 // recorded around the stages.
 gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, char *tab,
-                         cudaStream_t st, cudaEvent_t *events) {
+                         cudaStream_t st, cudaEvent_t *events,
+                         const std::vector<char> *only = nullptr) {
     const gs_config &cfg = ctx->cfg;
     const ProjParams PP{cfg.near_plane, cfg.dilation, cfg.guard_band, cfg.sigma_cull};
-    const CompParams C{std::log2(cfg.alpha_min), cfg.alpha_max, cfg.T_min,
-                       {cfg.background[0], cfg.background[1], cfg.background[2]}};
+    const CompParams C{std::log2(cfg.alpha_min),
+                       cfg.alpha_max,
+                       cfg.T_min,
+                       {cfg.background[0], cfg.background[1], cfg.background[2]},
+                       a.out_w,
+                       a.accumulate};
     CamInfo *cams_all = (CamInfo *)tab;
     Group *groups_all = (Group *)(tab + P.off_groups);
     int *tilepre_all = (int *)(tab + P.off_tilepre);
-    int *status = (int *)ctx->status.p;
-    long long *need = (long long *)ctx->status.p + 1;
+    long long *need = (long long *)ctx->status.p;               // [0]: largest chunk
+    int *status_all = (int *)((long long *)ctx->status.p + 1);  // [k]: chunk k overflowed
     unsigned long long *stats = (unsigned long long *)ctx->stats.p;
     int tp = 0;
     for (size_t k = 0; k < P.chunks.size(); ++k) {
@@ -301,7 +310,9 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CamInfo *cams = cams_all + ch.c0;
         const Group *groups = groups_all + ch.g0;
         const int *tilepre = tilepre_all + tp;
+        int *status = status_all + k;
         tp += ch.m + 1;
+        if (only && !(*only)[k]) continue;
         cudaEvent_t *E = events ? events + 5 * k : nullptr;
         if (E) CKC(cudaEventRecord(E[0], st));
         CKC(launch_project_mask(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
@@ -334,7 +345,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(launch_composite(cams, tilepre, ch.m, ch.tiles_total, (const SlotRec *)ctx->rec.p,
                              (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->rrect.p,
                              (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
-                             cfg.count_pairs != 0, cfg.pixels_per_thread, st));
+                             cfg.count_pairs != 0, cfg.pixels_per_thread, status, st));
         if (E) CKC(cudaEventRecord(E[4], st));
     }
     return GS_OK;
@@ -365,25 +376,35 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             CKC(cudaEventCreate(&e));
             ctx->ev.push_back(e);
         }
+    const size_t status_bytes = sizeof(long long) + P.chunks.size() * sizeof(int);
+    std::vector<char> redo;
     for (int attempt = 0; attempt < 2; ++attempt) {
         CKS(size_workspace(ctx, P));
         CKS(upload_tables(ctx, P, ctx->tables, a.st));
-        CKC(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), a.st));
-        CKC(cudaMemsetAsync(ctx->status.p, 0, 4 * sizeof(long long), a.st));
-        CKS(enqueue_render(ctx, a, P, (char *)ctx->tables.p, a.st, timing ? ctx->ev.data() : nullptr));
-        long long *hs = (long long *)ctx->pin[1].p;
-        CKS(grow_pinned(ctx, ctx->pin[1], 64));
-        hs = (long long *)ctx->pin[1].p;
-        CKC(cudaMemcpyAsync(hs, ctx->status.p, 2 * sizeof(long long), cudaMemcpyDeviceToHost, a.st));
+        if (attempt == 0) CKC(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), a.st));
+        CKC(cudaMemsetAsync(ctx->status.p, 0, status_bytes, a.st));
+        // the second pass renders only the chunks that overflowed (the others are
+        // final, and may have been accumulated into the outputs)
+        CKS(enqueue_render(ctx, a, P, (char *)ctx->tables.p, a.st,
+                           timing && attempt == 0 ? ctx->ev.data() : nullptr,
+                           attempt ? &redo : nullptr));
+        CKS(grow_pinned(ctx, ctx->pin[1], status_bytes + 64));
+        char *hs = (char *)ctx->pin[1].p;
+        CKC(cudaMemcpyAsync(hs, ctx->status.p, status_bytes, cudaMemcpyDeviceToHost, a.st));
         CKC(cudaStreamSynchronize(a.st));
-        const int st = (int)(hs[0] & 0xffffffff);
-        if (!st) break;
+        const long long need = *(long long *)hs;
+        const int *st = (const int *)(hs + sizeof(long long));
+        ctx->last_chunk_survivors = std::max(attempt ? ctx->last_chunk_survivors : 0LL, need);
+        redo.assign(P.chunks.size(), 0);
+        bool any = false;
+        for (size_t k = 0; k < P.chunks.size(); ++k)
+            if (st[k]) redo[k] = 1, any = true;
+        if (!any) break;
         if (attempt == 1)
             return fail(ctx, GS_ERR_CAPACITY, "workspace overflow after resizing (%lld survivors)",
-                        hs[1]);
-        ctx->cap_survivors = hs[1] + hs[1] / 8 + 1024;  // exact need plus headroom; render again
+                        need);
+        ctx->cap_survivors = need + need / 8 + 1024;  // exact need plus headroom; render again
     }
-    ctx->last_chunk_survivors = ((long long *)ctx->pin[1].p)[1];
     gs_stats stt{};
     stt.n_cameras = a.n;
     stt.n_chunks = (int)P.chunks.size();
@@ -489,7 +510,7 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect, &ctx->srect,
                       &ctx->bitmap,   &ctx->tables, &ctx->status, &ctx->blkpre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
-                      &ctx->sorttiles, &ctx->sorthist,
+                      &ctx->sorttiles, &ctx->sorthist, &ctx->blur_vm,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -617,6 +638,34 @@ gs_status gs_render_batch_v(gs_context *ctx, int32_t n_cams, const int32_t *scen
     return render_impl(ctx, a);
 }
 
+gs_status gs_render_motion_blur(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
+                                const float *viewmats, const float *intrinsics,
+                                const float *velocities, float shutter, int32_t samples,
+                                int32_t width, int32_t height, float *rgb, float *depth,
+                                float *final_T, void *stream) {
+    CKS(validate(ctx, n_cams, scene_ids, viewmats, intrinsics, width, height, rgb, depth, true));
+    if (samples < 1 || samples > 64)
+        return fail(ctx, GS_ERR_INVALID_ARG, "samples %d not in 1..64", samples);
+    if (!(shutter >= 0.0f)) return fail(ctx, GS_ERR_INVALID_ARG, "negative shutter time");
+    if (n_cams > 0 && !velocities) return fail(ctx, GS_ERR_INVALID_ARG, "NULL velocities");
+    ctx->err.clear();
+    if (n_cams == 0) return GS_OK;
+    CKC(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(grow(ctx, ctx->blur_vm, (size_t)n_cams * samples * 16 * sizeof(float)));
+    CKC(launch_blur_poses(viewmats, velocities, n_cams, samples, shutter, (float *)ctx->blur_vm.p,
+                          st));
+    for (int j = 0; j < samples; ++j) {
+        RenderArgs a{n_cams,  scene_ids, (const float *)ctx->blur_vm.p + (size_t)j * n_cams * 16,
+                     intrinsics, width, height, nullptr, nullptr, nullptr, rgb, depth, final_T, st,
+                     UPTO_ALL};
+        a.out_w = 1.0f / (float)samples;
+        a.accumulate = j > 0;
+        CKS(render_impl(ctx, a));
+    }
+    return GS_OK;
+}
+
 gs_status gs_graph_create(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
                           const float *viewmats, const float *intrinsics, const int32_t *widths,
                           const int32_t *heights, const int64_t *pixel_offsets, float *rgb,
@@ -656,7 +705,8 @@ gs_status gs_graph_create(gs_context *ctx, int32_t n_cams, const int32_t *scene_
         ac.st = cs;
         gs_status e1 = GS_OK;
         if (cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), cs) != cudaSuccess ||
-            cudaMemsetAsync(ctx->status.p, 0, 4 * sizeof(long long), cs) != cudaSuccess)
+            cudaMemsetAsync(ctx->status.p, 0, sizeof(long long) + P.chunks.size() * sizeof(int),
+                            cs) != cudaSuccess)
             e1 = GS_ERR_CUDA;
         if (e1 == GS_OK) e1 = enqueue_render(ctx, ac, P, (char *)g->tables.p, cs, nullptr);
         const cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
@@ -677,6 +727,7 @@ gs_status gs_graph_create(gs_context *ctx, int32_t n_cams, const int32_t *scene_
         return rc;
     }
     g->gen = ctx->workspace_gen;
+    g->n_chunks = (int)P.chunks.size();
     ctx->stats_pending = false;
     *out = g;
     return GS_OK;
@@ -698,12 +749,15 @@ gs_status gs_graph_check(gs_graph *g, void *stream) {
     gs_context *ctx = g->ctx;
     CKC(cudaSetDevice(ctx->device));
     CKC(cudaStreamSynchronize((cudaStream_t)stream));
-    long long h[2];
-    CKC(cudaMemcpy(h, ctx->status.p, sizeof(h), cudaMemcpyDeviceToHost));
-    if (h[0] & 0xffffffff)
-        return fail(ctx, GS_ERR_CAPACITY,
-                    "a graph launch exceeded the workspace (%lld survivors in a chunk): "
-                    "render eagerly once and create the graph again", h[1]);
+    std::vector<char> h(sizeof(long long) + g->n_chunks * sizeof(int));
+    CKC(cudaMemcpy(h.data(), ctx->status.p, h.size(), cudaMemcpyDeviceToHost));
+    const int *st = (const int *)(h.data() + sizeof(long long));
+    for (int k = 0; k < g->n_chunks; ++k)
+        if (st[k])
+            return fail(ctx, GS_ERR_CAPACITY,
+                        "a graph launch exceeded the workspace (%lld survivors in a chunk): "
+                        "render eagerly once and create the graph again",
+                        *(const long long *)h.data());
     return GS_OK;
 }
 

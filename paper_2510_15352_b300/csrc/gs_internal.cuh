@@ -29,6 +29,8 @@ struct CompParams {
     float log2_alpha_min;  // log2(alpha_min): alpha test done on log2(o e^power)
     float alpha_max, T_min;
     float bg[3];
+    float out_w;           // outputs are out_w * value ...
+    int accumulate;        // ... added to the existing outputs when non-zero
 };
 
 // A scene resident in device memory (structure of arrays, see gs.h).
@@ -108,6 +110,10 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
                                  int n_tiles, uint32_t *hist, cudaStream_t s,
                                  const int *n_tiles_dev = nullptr);
 
+// Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
+cudaError_t launch_blur_poses(const float *vm, const float *vel, int n, int k, float shutter,
+                              float *out, cudaStream_t s);
+
 // Device-side sizing of a chunk (see k_plan.cu).
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, long long cap_survivors,
                         int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
@@ -127,6 +133,6 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
-                             cudaStream_t s);
+                             const int *status, cudaStream_t s);
 
 }  // namespace gsk

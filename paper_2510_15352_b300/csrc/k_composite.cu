@@ -69,7 +69,9 @@ __global__ void __launch_bounds__(256 / PPT)
                 int n_slots, const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
                 const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
                 CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
-                float *__restrict__ finalT, unsigned long long *__restrict__ stats) {
+                float *__restrict__ finalT, unsigned long long *__restrict__ stats,
+                const int *__restrict__ status) {
+    if (status && *status) return;  // the chunk did not fit the workspace: nothing written
     constexpr int NT = 256 / PPT;    // threads per block
     constexpr int CPR = 16 / PPT;    // threads per pixel row
     constexpr int RPW = 32 / CPR;    // pixel rows per warp
@@ -267,11 +269,23 @@ finished:
         const int x = x0 + k * CPR;
         if (x >= ci.W || y >= ci.H) continue;
         const long long pix = ci.pix_off + (long long)y * ci.W + x;
-        rgb[3 * pix + 0] = fmaf(T[k], P.bg[0], cr[k]);
-        rgb[3 * pix + 1] = fmaf(T[k], P.bg[1], cg[k]);
-        rgb[3 * pix + 2] = fmaf(T[k], P.bg[2], cb[k]);
-        depth[pix] = cd[k];
-        if (finalT) finalT[pix] = T[k];
+        float o[5] = {fmaf(T[k], P.bg[0], cr[k]), fmaf(T[k], P.bg[1], cg[k]),
+                      fmaf(T[k], P.bg[2], cb[k]), cd[k], T[k]};
+        if (P.accumulate) {  // one sub-frame of a blended image (motion blur)
+            o[0] = fmaf(P.out_w, o[0], rgb[3 * pix + 0]);
+            o[1] = fmaf(P.out_w, o[1], rgb[3 * pix + 1]);
+            o[2] = fmaf(P.out_w, o[2], rgb[3 * pix + 2]);
+            o[3] = fmaf(P.out_w, o[3], depth[pix]);
+            if (finalT) o[4] = fmaf(P.out_w, o[4], finalT[pix]);
+        } else if (P.out_w != 1.0f) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) o[q] *= P.out_w;
+        }
+        rgb[3 * pix + 0] = o[0];
+        rgb[3 * pix + 1] = o[1];
+        rgb[3 * pix + 2] = o[2];
+        depth[pix] = o[3];
+        if (finalT) finalT[pix] = o[4];
     }
     if (STATS) {
 #pragma unroll
@@ -293,13 +307,16 @@ template <int PPT>
 cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots, int n_tiles,
                        const SlotRec *rec, const uint32_t *vals, const uint2 *rrect,
                        const uint32_t *bitmap, CompParams C, float *rgb, float *depth,
-                       float *final_T, unsigned long long *stats, bool collect, cudaStream_t s) {
+                       float *final_T, unsigned long long *stats, bool collect,
+                       const int *status, cudaStream_t s) {
     if (collect)
-        k_composite<PPT, true><<<n_tiles, 256 / PPT, 0, s>>>(
-            cams, tile_prefix, n_slots, rec, vals, rrect, bitmap, C, rgb, depth, final_T, stats);
+        k_composite<PPT, true><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+                                                             rrect, bitmap, C, rgb, depth, final_T,
+                                                             stats, status);
     else
-        k_composite<PPT, false><<<n_tiles, 256 / PPT, 0, s>>>(
-            cams, tile_prefix, n_slots, rec, vals, rrect, bitmap, C, rgb, depth, final_T, stats);
+        k_composite<PPT, false><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+                                                              rrect, bitmap, C, rgb, depth, final_T,
+                                                              stats, status);
     return cudaGetLastError();
 }
 
@@ -310,16 +327,16 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
-                             cudaStream_t s) {
+                             const int *status, cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
     if (pixels_per_thread == 8)
         return launch_ppt<8>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
-                             rgb, depth, final_T, stats, collect, s);
+                             rgb, depth, final_T, stats, collect, status, s);
     if (pixels_per_thread == 4)
         return launch_ppt<4>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
-                             rgb, depth, final_T, stats, collect, s);
+                             rgb, depth, final_T, stats, collect, status, s);
     return launch_ppt<2>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C, rgb,
-                         depth, final_T, stats, collect, s);
+                         depth, final_T, stats, collect, status, s);
 }
 
 }  // namespace gsk

@@ -71,6 +71,8 @@ SIGNATURES = {
                                             _vp, _vp]),
     "gs_render_batch_v": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                          _vp]),
+    "gs_render_motion_blur": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_float,
+                                             _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "gs_graph_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                        ctypes.POINTER(_vp)]),
     "gs_graph_launch": (ctypes.c_int, [_vp, _vp]),
@@ -115,6 +117,7 @@ gs_scene_destroy = lib.gs_scene_destroy
 gs_render_batch = lib.gs_render_batch
 gs_render_batch_host = lib.gs_render_batch_host
 gs_render_batch_v = lib.gs_render_batch_v
+gs_render_motion_blur = lib.gs_render_motion_blur
 gs_graph_create = lib.gs_graph_create
 gs_graph_launch = lib.gs_graph_launch
 gs_graph_check = lib.gs_graph_check
@@ -283,6 +286,23 @@ class Renderer:
                                     off.ctypes.data, rgb.data_ptr(), depth.data_ptr(),
                                     _ptr(final_T), ctypes.byref(g)))
         return Graph(self, g, off)
+
+    def render_motion_blur(self, scene_ids, viewmats, intrinsics, velocities, shutter: float,
+                           samples: int, W: int, H: int, want_T: bool = False, stream=None):
+        """Motion-blurred render (device tensors in and out). Returns (rgb, depth, T)."""
+        import torch
+        n = int(viewmats.shape[0])
+        ids = np.ascontiguousarray(np.broadcast_to(np.asarray(scene_ids, dtype=np.int32), (n,)))
+        dev = viewmats.device
+        rgb = torch.empty((n, H, W, 3), dtype=torch.float32, device=dev)
+        depth = torch.empty((n, H, W), dtype=torch.float32, device=dev)
+        T = torch.empty((n, H, W), dtype=torch.float32, device=dev) if want_T else None
+        vm, it, vel = viewmats.contiguous(), intrinsics.contiguous(), velocities.contiguous()
+        self._check(gs_render_motion_blur(self.ctx, n, ids.ctypes.data, vm.data_ptr(),
+                                          it.data_ptr(), vel.data_ptr(), float(shutter),
+                                          int(samples), W, H, rgb.data_ptr(), depth.data_ptr(),
+                                          _ptr(T), _stream(stream)))
+        return rgb, depth, T
 
     def render_host(self, scene_ids, viewmats, intrinsics, W: int, H: int, rgb, depth,
                     final_T=None, stream=None):
