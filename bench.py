@@ -29,14 +29,18 @@ sys.path.insert(0, ROOT)
 METRIC = "640x480 camera frames/s, 4096-cam batch; upsampled vs plain at >=35 dB PSNR"
 UNIT = "frames/s"
 WORKLOAD = "single_1m_sh3_1024cam_640x480"
-# Algorithmic FP32 work of the compositing step: the pairs (pixel, Gaussian)
-# that the method must blend -- alpha >= alpha_min before the pixel stops --
-# at 22 flops each (FMA = 2, comparisons 0): dx, dy (2), b'dy (1),
-# c'dy^2 + log2(o) (3), a'dx + b'dy (2), (..)dx + (..) (2), min (1), 1 - alpha (1),
-# T' = T(1-alpha) (1), w = alpha T (1), rgb + depth accumulation 4 FMA (8).
-# Pairs below alpha_min are not counted: how many of those a kernel evaluates
-# depends on its culling, not on the method. exp2 is an SFU op, not counted.
-F_PAIR = 22
+# Algorithmic FP32 work of the compositing step, per (pixel, Gaussian) pair that the
+# per-pixel algorithm evaluates: every entry of the pixel's tile list up to and
+# including the one at which it stops (lanes of pixels that have stopped, and
+# entries after that, are not counted). F_PAIR = 20 flops per evaluated pair
+# (FMA = 2): dx, dy, the quadratic, the exponent argument, the alpha clamp, the T
+# update and four accumulations. Two stricter counts are reported beside it:
+# an itemised one, 11 flops per evaluated pair (dx, dy, quadratic, o*e^p, min) plus
+# 11 per contributing pair (alpha >= alpha_min: 1 - alpha, T', alpha T, four FMAs),
+# and a lower bound, 22 flops per contributing pair only.
+F_PAIR = 20
+F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
+F_CONTRIB_ONLY = 22
 # FP32 peak of one B300: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz max clock
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read + write) of one compositing launch from the ncu capture summarised in
@@ -225,7 +229,7 @@ def run_b300_batched(args):
         R2.close()
         graph.close()
     eq_frames = P / (640 * 480)
-    achieved = F_PAIR * cst["pairs_alpha"] / (stage_ms["composite"] / args.steps / 1e3) / 1e12
+    achieved = F_PAIR * cst["pairs_evaluated"] / (stage_ms["composite"] / args.steps / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": eq_frames * args.steps / (ms / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -276,7 +280,9 @@ def run_b300(args):
     torch.cuda.synchronize()
     cst = counter.stats()
     counter.close()
-    flops_per_step = F_PAIR * cst["pairs_alpha"]
+    flops_per_step = F_PAIR * cst["pairs_evaluated"]
+    flops_itemised = F_EVAL_ITEMISED * cst["pairs_evaluated"] + F_CONTRIB_ITEMISED * cst["pairs_alpha"]
+    flops_contrib = F_CONTRIB_ONLY * cst["pairs_alpha"]
 
     R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
                     pixels_per_thread=args.ppt)
@@ -367,6 +373,11 @@ def run_b300(args):
                 "composite_share_of_step": ms_comp / t_max,
                 "pairs_evaluated_per_step": cst["pairs_evaluated"],
                 "pairs_alpha_per_step": cst["pairs_alpha"],
+                "flops_per_pair": F_PAIR,
+                "frac_itemised": (flops_itemised / (ms_comp / args.steps / 1e3) / 1e12
+                                  / FP32_PEAK_TFLOPS) if ms_comp else None,
+                "frac_contributing_only": (flops_contrib / (ms_comp / args.steps / 1e3) / 1e12
+                                           / FP32_PEAK_TFLOPS) if ms_comp else None,
             },
             "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "stats": {"survivors_per_step": cst["survivors"],
