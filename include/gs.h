@@ -296,6 +296,65 @@ gs_status gs_sort_segments_noalloc(uint32_t *keys, uint32_t *vals, int64_t n,
                                    const int64_t *seg_start, const int64_t *seg_count,
                                    int32_t n_seg, void *stream);
 
+/* ---- Learned 4x upsampler ----
+ * The paper renders every robot camera at 640x480 (Sec. 3.2) and has no
+ * upsampler; this is a service of this library: a small residual CNN that
+ * turns a render at a quarter of the resolution (e.g. 160x120, intrinsics / 4)
+ * into the full-resolution image, trained on pairs the renderer produces.
+ *   x0  = rgb - 1/2
+ *   h_l = relu(conv3x3(h_{l-1}))           l = 1..5, 32 channels
+ *   z   = conv3x3(h_5)                      48 channels
+ *   out = bilinear4(rgb) + pixel_shuffle4(z)
+ * conv3x3 is cross-correlation with zero padding 1; pixel_shuffle4 sends
+ * channel 16 c + 4 dy + dx of LR pixel (y, x) to colour c of HR pixel
+ * (4 y + dy, 4 x + dx); bilinear4 uses half-pixel centres (HR pixel centre
+ * i + 1/2 at LR coordinate (i + 1/2) / 4) with edge clamp. Weights and
+ * activations are BF16 on the tensor cores with FP32 accumulation; master
+ * weights, the loss and Adam are FP32.
+ * Parameters: one flat FP32 array, per layer weights [c_out][c_in][3][3] then
+ * biases [c_out], layers (c_out, c_in) = (32, 3), (32, 32) x 4, (48, 32):
+ * gs_upsampler_param_count() = 51,760 values. A new upsampler has all
+ * parameters zero (it then computes plain bilinear upsampling). */
+typedef struct gs_upsampler gs_upsampler;
+
+int64_t gs_upsampler_param_count(void);
+
+/* Creates an upsampler on `device`. GS_ERR_INVALID_ARG for a bad device,
+ * GS_ERR_OOM / GS_ERR_CUDA when its ~1.5 MB of parameter state cannot be set up. */
+gs_status gs_upsampler_create(int32_t device, gs_upsampler **out);
+void gs_upsampler_destroy(gs_upsampler *u);
+const char *gs_upsampler_last_error(gs_upsampler *u);
+
+/* HOST arrays of exactly gs_upsampler_param_count() floats. set_params also
+ * clears the Adam moments and step count; all three synchronise the device. */
+gs_status gs_upsampler_set_params(gs_upsampler *u, const float *host_params, int64_t n);
+gs_status gs_upsampler_get_params(gs_upsampler *u, float *host_params, int64_t n);
+/* Gradient of the last gs_upsample_grad call, same layout as the parameters. */
+gs_status gs_upsampler_get_grads(gs_upsampler *u, float *host_grads, int64_t n);
+
+/* Inference: n frames of h x w.
+ *   lr_rgb    DEVICE [n][h][w][3] f32     lr_depth  DEVICE [n][h][w] f32 or NULL
+ *   hr_rgb    DEVICE [n][4h][4w][3] f32   hr_depth  DEVICE [n][4h][4w] f32 or NULL
+ * (depth is upsampled bilinearly; both depth pointers NULL or both set).
+ * Enqueued on `stream`; the workspace (<= ~1 GB, frames in groups) grows with
+ * cudaMalloc on first use. Sizes: n >= 0, 1 <= h, w <= 65535. */
+gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
+                              const float *lr_rgb, const float *lr_depth, float *hr_rgb,
+                              float *hr_depth, void *stream);
+
+/* Training pass: forward on lr_rgb, loss = mean over HR pixels and channels of
+ * (out - hr_target)^2, and the gradient of the loss with respect to every
+ * parameter into the upsampler's gradient buffer (replacing the previous one).
+ *   lr_rgb DEVICE [n][h][w][3], hr_target DEVICE [n][4h][4w][3] f32;
+ *   loss   DEVICE 1 f32 (overwritten with the loss) or NULL.
+ * The workspace holds every layer's activations (~0.8 KB per LR pixel). */
+gs_status gs_upsample_grad(gs_upsampler *u, int32_t n, int32_t h, int32_t w, const float *lr_rgb,
+                           const float *hr_target, float *loss, void *stream);
+
+/* One Adam step (Kingma & Ba, bias-corrected) with the current gradient. */
+gs_status gs_upsample_adam(gs_upsampler *u, float lr, float beta1, float beta2, float eps,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

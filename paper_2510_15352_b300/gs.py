@@ -85,6 +85,17 @@ SIGNATURES = {
                                            ctypes.POINTER(_i64), _vp]),
     "gs_sort_segments": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "gs_sort_segments_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i32, _vp]),
+    "gs_upsampler_param_count": (_i64, []),
+    "gs_upsampler_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp)]),
+    "gs_upsampler_destroy": (None, [_vp]),
+    "gs_upsampler_last_error": (ctypes.c_char_p, [_vp]),
+    "gs_upsampler_set_params": (ctypes.c_int, [_vp, _vp, _i64]),
+    "gs_upsampler_get_params": (ctypes.c_int, [_vp, _vp, _i64]),
+    "gs_upsampler_get_grads": (ctypes.c_int, [_vp, _vp, _i64]),
+    "gs_upsample_forward": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "gs_upsample_grad": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
+    "gs_upsample_adam": (ctypes.c_int, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, _vp]),
 }
 
 
@@ -127,6 +138,16 @@ gs_debug_project = lib.gs_debug_project
 gs_debug_tile_lists = lib.gs_debug_tile_lists
 gs_sort_segments = lib.gs_sort_segments
 gs_sort_segments_noalloc = lib.gs_sort_segments_noalloc
+gs_upsampler_param_count = lib.gs_upsampler_param_count
+gs_upsampler_create = lib.gs_upsampler_create
+gs_upsampler_destroy = lib.gs_upsampler_destroy
+gs_upsampler_last_error = lib.gs_upsampler_last_error
+gs_upsampler_set_params = lib.gs_upsampler_set_params
+gs_upsampler_get_params = lib.gs_upsampler_get_params
+gs_upsampler_get_grads = lib.gs_upsampler_get_grads
+gs_upsample_forward = lib.gs_upsample_forward
+gs_upsample_grad = lib.gs_upsample_grad
+gs_upsample_adam = lib.gs_upsample_adam
 
 
 class GSError(RuntimeError):
@@ -373,3 +394,71 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Upsampler:
+    """The learned 4x upsampler (gs_upsampler_*): parameters, inference, one
+    training pass and Adam. Tensors are CUDA float32, NHWC, contiguous."""
+
+    n_params = int(gs_upsampler_param_count())
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        st = gs_upsampler_create(device, ctypes.byref(h))
+        if st != GS_OK:
+            raise GSError(st, "upsampler creation")
+        self.u = h
+        self.device = device
+
+    def close(self):
+        if self.u:
+            gs_upsampler_destroy(self.u)
+            self.u = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != GS_OK:
+            raise GSError(st, gs_upsampler_last_error(self.u).decode())
+
+    def set_params(self, flat) -> None:
+        a = np.ascontiguousarray(flat, dtype=np.float32).ravel()
+        self._check(gs_upsampler_set_params(self.u, a.ctypes.data, a.size))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.n_params, np.float32)
+        self._check(gs_upsampler_get_params(self.u, a.ctypes.data, a.size))
+        return a
+
+    def get_grads(self) -> np.ndarray:
+        a = np.empty(self.n_params, np.float32)
+        self._check(gs_upsampler_get_grads(self.u, a.ctypes.data, a.size))
+        return a
+
+    def forward(self, lr_rgb, lr_depth=None, out_rgb=None, out_depth=None, stream=None):
+        import torch
+        n, h, w, _ = lr_rgb.shape
+        if out_rgb is None:
+            out_rgb = torch.empty((n, 4 * h, 4 * w, 3), dtype=torch.float32, device=lr_rgb.device)
+        if lr_depth is not None and out_depth is None:
+            out_depth = torch.empty((n, 4 * h, 4 * w), dtype=torch.float32, device=lr_rgb.device)
+        self._check(gs_upsample_forward(self.u, n, h, w, _ptr(lr_rgb), _ptr(lr_depth),
+                                        _ptr(out_rgb), _ptr(out_depth), _stream(stream)))
+        return out_rgb, out_depth
+
+    def grad(self, lr_rgb, hr_target, loss=None, stream=None):
+        import torch
+        n, h, w, _ = lr_rgb.shape
+        if loss is None:
+            loss = torch.empty((1,), dtype=torch.float32, device=lr_rgb.device)
+        self._check(gs_upsample_grad(self.u, n, h, w, _ptr(lr_rgb), _ptr(hr_target), _ptr(loss),
+                                     _stream(stream)))
+        return loss
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             stream=None) -> None:
+        self._check(gs_upsample_adam(self.u, lr, beta1, beta2, eps, _stream(stream)))

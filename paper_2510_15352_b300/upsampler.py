@@ -1,0 +1,117 @@
+"""Training and evaluation of the learned 4x upsampler on renderer pairs.
+
+The upsampler (gs.Upsampler, kernels in csrc/k_upsample.cu) maps a render at a
+quarter of the resolution (intrinsics / 4) to the full-resolution image. It is
+trained on pairs the renderer itself produces: the same camera pose rendered
+at both resolutions. Everything here is orchestration -- choosing poses,
+calling the renderer and the upsampler's gradient / Adam entry points, and
+measuring PSNR; the arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import gs, synth
+
+
+def quarter(intr) -> "object":
+    """Intrinsics (fx, fy, cx, cy) of the same camera at a quarter of the
+    resolution: pixel centres (i + 1/2) map to (i + 1/2) / 4."""
+    return intr / 4.0
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-normal weights for the ReLU layers, zero biases, zero last layer: the
+    untrained network is exactly bilinear upsampling."""
+    rng = np.random.default_rng([seed, 11])
+    shapes = [(32, 3)] + [(32, 32)] * 4 + [(48, 32)]
+    parts = []
+    for li, (co, ci) in enumerate(shapes):
+        W = rng.normal(0.0, math.sqrt(2.0 / (9 * ci)), size=(co, ci, 3, 3))
+        if li == len(shapes) - 1:
+            W[:] = 0.0
+        parts += [W.ravel(), np.zeros(co)]
+    flat = np.concatenate(parts).astype(np.float32)
+    assert flat.size == gs.Upsampler.n_params
+    return flat
+
+
+def render_pairs(renderer: "gs.Renderer", scene_id: int, viewmats, intrinsics, W: int, H: int,
+                 stream=None):
+    """(lr_rgb [n][H/4][W/4][3], lr_depth, hr_rgb [n][H][W][3], hr_depth) device tensors."""
+    import torch
+    vm = torch.as_tensor(np.ascontiguousarray(viewmats, dtype=np.float32)).cuda(renderer.device)
+    it = torch.as_tensor(np.ascontiguousarray(intrinsics, dtype=np.float32)).cuda(renderer.device)
+    hr, hd, _ = renderer.render(scene_id, vm, it, W, H, stream=stream)
+    lr, ld, _ = renderer.render(scene_id, vm, quarter(it), W // 4, H // 4, stream=stream)
+    return lr, ld, hr, hd
+
+
+def psnr(a, b):
+    """Per-frame PSNR (dB) of images clamped to [0, 1]: 10 log10(1 / MSE)."""
+    import torch
+    mse = ((a.clamp(0, 1) - b.clamp(0, 1)) ** 2).flatten(1).mean(1)
+    return 10.0 * torch.log10(1.0 / mse.clamp_min(1e-20))
+
+
+def evaluate(up: "gs.Upsampler", renderer: "gs.Renderer", scene_id: int, viewmats, intrinsics,
+             W: int, H: int, batch: int = 64) -> dict:
+    """PSNR of the upsampled render and of plain bilinear upsampling (an
+    upsampler with zero parameters) against the full-resolution render."""
+    import torch
+    bil = gs.Upsampler(device=renderer.device)
+    try:
+        bil.set_params(np.zeros(gs.Upsampler.n_params, np.float32))
+        p_net, p_bil = [], []
+        for i in range(0, len(viewmats), batch):
+            lr, _, hr, _ = render_pairs(renderer, scene_id, viewmats[i:i + batch],
+                                        intrinsics[i:i + batch], W, H)
+            out, _ = up.forward(lr)
+            ob, _ = bil.forward(lr)
+            p_net.append(psnr(out, hr))
+            p_bil.append(psnr(ob, hr))
+        torch.cuda.synchronize(renderer.device)
+    finally:
+        bil.close()
+    pn, pb = torch.cat(p_net).cpu().numpy(), torch.cat(p_bil).cpu().numpy()
+    return {"psnr_mean": float(pn.mean()), "psnr_p5": float(np.percentile(pn, 5)),
+            "bilinear_psnr_mean": float(pb.mean()), "bilinear_psnr_p5": float(np.percentile(pb, 5)),
+            "frames": int(len(pn))}
+
+
+def train(up: "gs.Upsampler", renderer: "gs.Renderer", scene_ids, W: int, H: int,
+          n_pairs: int, seed: int = 100, frames_per_step: int = 8, render_batch: int = 256,
+          lr_max: float = 1e-4, lr_min: float = 1e-6, heights=(0.3, 1.2), log=None) -> list:
+    """Adam on the mean squared error against the full-resolution render, over
+    n_pairs training pairs (poses from camera seeds seed, seed + 1, ...; the
+    scene of each batch cycles through scene_ids), frames_per_step frames per
+    step, learning rate cosine-decayed from lr_max to lr_min. Returns the loss
+    of every step (device tensors read back at the end)."""
+    import torch
+    steps_total = max(1, n_pairs // frames_per_step)
+    fx = W * 0.75  # 640x480 at fx = 480, 320x240 at fx = 240
+    losses = []
+    step = 0
+    b = 0
+    while step < steps_total:
+        m = min(render_batch, (steps_total - step) * frames_per_step)
+        vm, it = synth.make_cameras(m, W, H, fx, heights, seed=seed + b)
+        sid = scene_ids[b % len(scene_ids)]
+        lr, _, hr, _ = render_pairs(renderer, sid, vm, it, W, H)
+        perm = torch.randperm(m, generator=torch.Generator().manual_seed(seed + b)).cuda(lr.device)
+        for k in range(0, m - frames_per_step + 1, frames_per_step):
+            if step >= steps_total:
+                break
+            idx = perm[k:k + frames_per_step]
+            lrb, hrb = lr.index_select(0, idx).contiguous(), hr.index_select(0, idx).contiguous()
+            loss = up.grad(lrb, hrb)
+            rate = lr_min + 0.5 * (lr_max - lr_min) * (1 + math.cos(math.pi * step / steps_total))
+            up.adam(rate)
+            losses.append(loss)
+            step += 1
+        b += 1
+        if log:
+            log(f"pairs {step * frames_per_step}: loss {float(losses[-1].item()):.3e}")
+    return [float(x) for x in torch.cat(losses).cpu()]

@@ -1,0 +1,197 @@
+"""The learned 4x upsampler on the GPU against the FP64 oracle (forward,
+gradients, Adam), and the gain of the trained network over bilinear
+upsampling on renderer pairs.
+
+Precision: the kernels keep weights and activations in BF16 (8 significant
+bits, relative rounding <= 2^-9) with FP32 accumulation. The tests feed both
+sides the same BF16-representable weights and inputs, so the differences come
+only from rounding the five hidden activations (and, backward, the gradients
+between layers) to BF16. Each rounding perturbs a value by <= 2^-9 relative;
+over six layers the propagated relative error of an output or a weight
+gradient stays below ~6 x 2^-9 = 1.2 % in the worst case and is ~0.3 % in
+RMS. The bars: relative Frobenius error <= 2 % per layer, cosine >= 0.999.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import upsampler as U
+from paper_2510_15352_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round float32 values to the nearest BF16 (ties to even), as float32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def flat_to_layers(flat):
+    out, o = [], 0
+    for co, ci in U.layer_shapes():
+        nW = co * ci * 9
+        out.append((flat[o:o + nW].reshape(co, ci, 3, 3).astype(np.float64),
+                    flat[o + nW:o + nW + co].astype(np.float64)))
+        o += nW + co
+    return out
+
+
+def layers_to_flat(layers):
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in layers]).astype(np.float32)
+
+
+def random_case(seed, n, h, w):
+    rng = np.random.default_rng(seed)
+    params = U.init_params(seed, zero_last=False)
+    params = [(W, rng.normal(0, 0.05, size=b.shape)) for W, b in params]
+    params[-1] = (params[-1][0] * 0.3, params[-1][1])
+    flat = layers_to_flat(params)
+    nW = 0
+    qs = []
+    for co, ci in U.layer_shapes():
+        m = co * ci * 9
+        qs.append((nW, nW + m))
+        nW += m + co
+    for a, b in qs:
+        flat[a:b] = bf16_round(flat[a:b])
+    # rgb - 1/2 exactly representable in BF16
+    rgb = (0.5 + rng.integers(-128, 128, size=(n, h, w, 3)) / 256.0).astype(np.float32)
+    tgt = rng.uniform(0, 1, size=(n, 4 * h, 4 * w, 3)).astype(np.float32)
+    return flat, rgb, tgt
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def cosine(a, b):
+    return float(np.dot(a.ravel(), b.ravel()) / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+
+
+@pytest.mark.parametrize("n,h,w", [(2, 13, 37), (1, 8, 16), (3, 30, 40)])
+def test_forward_matches_oracle(torch_cuda, n, h, w):
+    torch = torch_cuda
+    from paper_2510_15352_b300 import gs
+    flat, rgb, _ = random_case(1, n, h, w)
+    up = gs.Upsampler(0)
+    try:
+        up.set_params(flat)
+        depth = np.random.default_rng(2).uniform(0.5, 5.0, size=(n, h, w)).astype(np.float32)
+        out, od = up.forward(torch.from_numpy(rgb).cuda(), torch.from_numpy(depth).cuda())
+        torch.cuda.synchronize()
+        out, od = out.cpu().numpy(), od.cpu().numpy()
+    finally:
+        up.close()
+    ref = U.forward(flat_to_layers(flat), rgb)
+    bil = U.bilinear(rgb)
+    res_ref, res_gpu = ref - bil, out - bil
+    assert rel_err(res_gpu, res_ref) <= 2e-2
+    assert cosine(res_gpu, res_ref) >= 0.999
+    assert np.abs(out - ref).max() <= 2e-2 * np.abs(res_ref).max() + 1e-5
+    np.testing.assert_allclose(od, U.bilinear(depth[..., None].astype(np.float64))[..., 0],
+                               rtol=1e-6, atol=1e-6)
+
+
+def test_zero_params_is_bilinear(torch_cuda):
+    torch = torch_cuda
+    from paper_2510_15352_b300 import gs
+    rgb = np.random.default_rng(3).uniform(0, 1, size=(2, 7, 9, 3)).astype(np.float32)
+    up = gs.Upsampler(0)
+    try:
+        out, _ = up.forward(torch.from_numpy(rgb).cuda())
+        torch.cuda.synchronize()
+        out = out.cpu().numpy()
+    finally:
+        up.close()
+    np.testing.assert_allclose(out, U.bilinear(rgb.astype(np.float64)), rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("n,h,w", [(2, 13, 37), (4, 24, 32)])
+def test_gradients_match_oracle(torch_cuda, n, h, w):
+    torch = torch_cuda
+    from paper_2510_15352_b300 import gs
+    flat, rgb, tgt = random_case(4, n, h, w)
+    up = gs.Upsampler(0)
+    try:
+        up.set_params(flat)
+        loss = up.grad(torch.from_numpy(rgb).cuda(), torch.from_numpy(tgt).cuda())
+        torch.cuda.synchronize()
+        loss = float(loss.item())
+        g = up.get_grads()
+    finally:
+        up.close()
+    ref_loss, ref_grads = U.loss_and_grads(flat_to_layers(flat), rgb, tgt)
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    for li, (gw, gb) in enumerate(flat_to_layers(g)):
+        rw, rb = ref_grads[li]
+        assert rel_err(gw, rw) <= 2e-2, (li, rel_err(gw, rw))
+        assert cosine(gw, rw) >= 0.999, li
+        assert rel_err(gb, rb) <= 2e-2, (li, rel_err(gb, rb))
+
+
+def test_adam_step_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_2510_15352_b300 import gs
+    flat, rgb, tgt = random_case(5, 2, 16, 16)
+    up = gs.Upsampler(0)
+    try:
+        up.set_params(flat)
+        params = flat_to_layers(flat)
+        opt = U.Adam(params, lr=1e-3)
+        for _ in range(3):
+            up.grad(torch.from_numpy(rgb).cuda(), torch.from_numpy(tgt).cuda())
+            g = flat_to_layers(up.get_grads())
+            up.adam(1e-3)
+            params = opt.step(params, g)
+            got = up.get_params()
+            want = layers_to_flat(params)
+            # the update of each step is ~1e-3; float32 arithmetic keeps it to ~1e-7
+            assert np.abs(got - want).max() <= 1e-6
+    finally:
+        up.close()
+
+
+def test_bad_arguments(torch_cuda):
+    from paper_2510_15352_b300 import gs
+    up = gs.Upsampler(0)
+    try:
+        with pytest.raises(gs.GSError):
+            up.set_params(np.zeros(10, np.float32))
+        with pytest.raises(gs.GSError):
+            up.adam(-1.0)
+        assert gs.gs_upsample_forward(up.u, -1, 8, 8, None, None, None, None, None) != gs.GS_OK
+        assert gs.gs_upsample_forward(up.u, 0, 8, 8, None, None, None, None, None) == gs.GS_OK
+    finally:
+        up.close()
+
+
+def test_training_gains_over_bilinear(torch_cuda):
+    """Trained on renderer pairs of one scene (training poses from camera seeds
+    100..), evaluated on held-out poses (seed 7): the network beats plain
+    bilinear upsampling of the quarter-resolution render."""
+    from paper_2510_15352_b300 import gs, upsampler
+    scene = synth.make_scene(200_000, 3, seed=21)
+    R = gs.Renderer(0)
+    up = gs.Upsampler(0)
+    try:
+        sid = R.add_scene(scene)
+        up.set_params(upsampler.init_params(0))
+        losses = upsampler.train(up, R, [sid], 640, 480, n_pairs=4096, frames_per_step=8,
+                                 render_batch=256)
+        vm, it = synth.make_cameras(64, 640, 480, 480.0, (0.3, 1.2), seed=7)
+        ev = upsampler.evaluate(up, R, sid, vm, it, 640, 480)
+    finally:
+        up.close()
+        R.close()
+    assert np.mean(losses[-50:]) < np.mean(losses[:50])
+    assert ev["psnr_mean"] > ev["bilinear_psnr_mean"] + 0.5, ev
