@@ -301,10 +301,13 @@ gs_status gs_sort_segments_noalloc(uint32_t *keys, uint32_t *vals, int64_t n,
  * upsampler; this is a service of this library: a small residual CNN that
  * turns a render at a quarter of the resolution (e.g. 160x120, intrinsics / 4)
  * into the full-resolution image, trained on pairs the renderer produces.
- *   x0  = rgb - 1/2
+ *   x0  = [rgb - 1/2, S (rgb - box3(rgb))]   6 channels, S = 32
  *   h_l = relu(conv3x3(h_{l-1}))           l = 1..5, 32 channels
  *   z   = conv3x3(h_5)                      48 channels
- *   out = bilinear4(rgb) + pixel_shuffle4(z)
+ *   out = bilinear4(rgb) + pixel_shuffle4(z) / S
+ * box3 is the 3x3 mean (indices clamped); the detail channels and the 1/S
+ * scale keep the small differences between a render and its bilinear
+ * upsampling well above BF16's relative precision.
  * conv3x3 is cross-correlation with zero padding 1; pixel_shuffle4 sends
  * channel 16 c + 4 dy + dx of LR pixel (y, x) to colour c of HR pixel
  * (4 y + dy, 4 x + dx); bilinear4 uses half-pixel centres (HR pixel centre
@@ -312,8 +315,8 @@ gs_status gs_sort_segments_noalloc(uint32_t *keys, uint32_t *vals, int64_t n,
  * activations are BF16 on the tensor cores with FP32 accumulation; master
  * weights, the loss and Adam are FP32.
  * Parameters: one flat FP32 array, per layer weights [c_out][c_in][3][3] then
- * biases [c_out], layers (c_out, c_in) = (32, 3), (32, 32) x 4, (48, 32):
- * gs_upsampler_param_count() = 51,760 values. A new upsampler has all
+ * biases [c_out], layers (c_out, c_in) = (32, 6), (32, 32) x 4, (48, 32):
+ * gs_upsampler_param_count() = 52,624 values. A new upsampler has all
  * parameters zero (it then computes plain bilinear upsampling). */
 typedef struct gs_upsampler gs_upsampler;
 

@@ -8,10 +8,16 @@ The paper (Sec. 3.2) renders every robot camera at 640x480; the upsampler turns
 a 160x120 render of the same pose into 640x480. The network is a plain residual
 CNN, written here from the textbook definitions (numpy, float64, NHWC images):
 
-    x0  = rgb_lr - 0.5                               (3 channels, centred)
+    x0  = [rgb_lr - 1/2, S (rgb_lr - box3(rgb_lr))]  (6 channels)
     h_l = relu(conv3x3(h_{l-1}; W_l, b_l))           l = 1..5, 32 channels
     z6  = conv3x3(h_5; W_6, b_6)                     48 = 3 * 4 * 4 channels
-    out = bilinear4(rgb_lr) + pixel_shuffle4(z6)     (3 channels at 4x)
+    out = bilinear4(rgb_lr) + pixel_shuffle4(z6) / S  (3 channels at 4x)
+
+with S = 32. The detail channels and the 1/S output scale keep the small
+differences the network reads and writes (renders of dense scenes differ from
+their bilinear upsampling by ~1e-3) far above the relative precision of BF16
+storage (2^-9 of the value stored); in float64 they are only a change of units.
+box3: mean of the 3x3 neighbourhood, indices clamped to the image.
 
 conv3x3: cross-correlation with zero padding 1, weights [c_out][c_in][3][3]
     y[i, j, o] = b[o] + sum_{c, u, v} W[o, c, u, v] x[i + u - 1, j + v - 1, c]
@@ -35,9 +41,11 @@ import numpy as np
 C_MID = 32
 N_LAYERS = 6
 SCALE = 4
+C_IN = 6
+DETAIL_SCALE = 32.0
 
 
-def layer_shapes(c_in: int = 3, c_mid: int = C_MID, scale: int = SCALE):
+def layer_shapes(c_in: int = C_IN, c_mid: int = C_MID, scale: int = SCALE):
     """(c_out, c_in) of the six 3x3 convolutions."""
     c_out_last = 3 * scale * scale
     return [(c_mid, c_in)] + [(c_mid, c_mid)] * (N_LAYERS - 2) + [(c_out_last, c_mid)]
@@ -48,7 +56,7 @@ def init_params(seed: int, c_mid: int = C_MID, zero_last: bool = True) -> list:
     as plain bilinear upsampling."""
     rng = np.random.default_rng([seed, 7])
     params = []
-    for li, (co, ci) in enumerate(layer_shapes(3, c_mid)):
+    for li, (co, ci) in enumerate(layer_shapes(C_IN, c_mid)):
         std = np.sqrt(2.0 / (9 * ci))
         W = rng.normal(0.0, std, size=(co, ci, 3, 3))
         if zero_last and li == N_LAYERS - 1:
@@ -115,17 +123,35 @@ def bilinear(x: np.ndarray, r: int = SCALE) -> np.ndarray:
     return top[:, :, x0] * (1 - fx)[None, None, :, None] + top[:, :, x1] * fx[None, None, :, None]
 
 
-def forward(params: list, rgb: np.ndarray, keep: bool = False):
-    """rgb [n][h][w][3] -> out [n][4h][4w][3]; with keep, also the layer inputs
-    and pre-activations needed by backward."""
+def box3(x: np.ndarray) -> np.ndarray:
+    """Mean of the 3x3 neighbourhood of every pixel, indices clamped."""
+    _, h, w, _ = x.shape
+    acc = np.zeros_like(x, dtype=np.float64)
+    for du in (-1, 0, 1):
+        rows = np.clip(np.arange(h) + du, 0, h - 1)
+        for dv in (-1, 0, 1):
+            cols = np.clip(np.arange(w) + dv, 0, w - 1)
+            acc += x[:, rows][:, :, cols]
+    return acc / 9.0
+
+
+def network_input(rgb: np.ndarray) -> np.ndarray:
+    """x0 = [rgb - 1/2, S (rgb - box3(rgb))]."""
     x = np.asarray(rgb, np.float64)
-    h = x - 0.5
+    return np.concatenate([x - 0.5, DETAIL_SCALE * (x - box3(x))], axis=-1)
+
+
+def forward(params: list, rgb: np.ndarray, keep: bool = False):
+    """rgb [n][h][w][3] -> out [n][4h][4w][3]; with keep, also every layer's
+    input and the last layer's output, as backward needs them."""
+    x = np.asarray(rgb, np.float64)
+    h = network_input(x)
     acts = [h]
     for li, (W, b) in enumerate(params):
         z = conv3x3(h, W, b)
         h = np.maximum(z, 0.0) if li < N_LAYERS - 1 else z
         acts.append(h)
-    out = bilinear(x) + pixel_shuffle(acts[-1])
+    out = bilinear(x) + pixel_shuffle(acts[-1]) / DETAIL_SCALE
     return (out, acts) if keep else out
 
 
@@ -134,7 +160,7 @@ def loss_and_grads(params: list, rgb: np.ndarray, target: np.ndarray):
     out, acts = forward(params, rgb, keep=True)
     diff = out - np.asarray(target, np.float64)
     loss = float(np.mean(diff * diff))
-    d = pixel_unshuffle(2.0 * diff / diff.size)
+    d = pixel_unshuffle(2.0 * diff / diff.size) / DETAIL_SCALE
     grads = [None] * N_LAYERS
     for li in range(N_LAYERS - 1, -1, -1):
         W, _ = params[li]

@@ -2,8 +2,8 @@
 // Adam), on the kernels of k_upsample.cu.
 //
 // Parameters are one flat FP32 array, layer by layer: weights [c_out][c_in][3][3]
-// then biases [c_out], for the layers (c_out, c_in) = (32, 3), 4 x (32, 32),
-// (48, 32) -- 51,760 values. The library keeps them as FP32 masters plus BF16
+// then biases [c_out], for the layers (c_out, c_in) = (32, 6), 4 x (32, 32),
+// (48, 32) -- 52,624 values. The library keeps them as FP32 masters plus BF16
 // copies in the layouts the convolution kernels read.
 #include <algorithm>
 #include <cmath>
@@ -14,7 +14,8 @@
 #include "gs_internal.cuh"
 
 namespace gsk {
-cudaError_t up_prep_input(const float *rgb, long long n_pix, __nv_bfloat16 *x0, cudaStream_t s);
+cudaError_t up_prep_input(const float *rgb, int n, int h, int w, __nv_bfloat16 *x0,
+                          cudaStream_t s);
 cudaError_t up_conv_forward(int layer, const __nv_bfloat16 *x, int n, int h, int w,
                             const __nv_bfloat16 *wt, const float *bias, void *out,
                             cudaStream_t s);
@@ -41,7 +42,7 @@ namespace {
 using bf16 = __nv_bfloat16;
 constexpr int NL = 6;
 constexpr int L_CO[NL] = {32, 32, 32, 32, 32, 48};
-constexpr int L_CI[NL] = {3, 32, 32, 32, 32, 32};
+constexpr int L_CI[NL] = {6, 32, 32, 32, 32, 32};
 constexpr int L_CIP[NL] = {16, 32, 32, 32, 32, 32};  // input channels as stored (padded)
 
 constexpr long long layer_size(int l) { return (long long)L_CO[l] * L_CI[l] * 9 + L_CO[l]; }
@@ -50,7 +51,7 @@ long long layer_off(int l) {
     for (int i = 0; i < l; ++i) o += layer_size(i);
     return o;
 }
-constexpr long long N_PARAMS = 896 + 4 * 9248 + 13872;
+constexpr long long N_PARAMS = 1760 + 4 * 9248 + 13872;
 
 // Inference works on frames in groups whose activations fit this budget.
 constexpr size_t INFER_BYTES = size_t(1) << 30;
@@ -229,8 +230,9 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
     for (int f0 = 0; f0 < n; f0 += group) {
         const int m = std::min(group, n - f0);
         const float *rgb = lr_rgb + (size_t)f0 * px * 3;
-        e = gsk::up_prep_input(rgb, (long long)m * px, x0, s);
-        if (e == cudaSuccess) e = gsk::up_conv_forward(0, x0, m, h, w, u->wf[0], u->params + layer_off(0) + 32 * 3 * 9, a, s);
+        e = gsk::up_prep_input(rgb, m, h, w, x0, s);
+        if (e == cudaSuccess)
+            e = gsk::up_conv_forward(0, x0, m, h, w, u->wf[0], u->params + layer_off(0) + 32 * 6 * 9, a, s);
         for (int l = 1; l < 5 && e == cudaSuccess; ++l) {
             e = gsk::up_conv_forward(l, a, m, h, w, u->wf[l],
                                      u->params + layer_off(l) + (long long)L_CO[l] * L_CI[l] * 9, b, s);
@@ -275,7 +277,7 @@ gs_status gs_upsample_grad(gs_upsampler *u, int32_t n, int32_t h, int32_t w, con
     float *lacc = loss ? loss : (float *)p;
     e = cudaMemsetAsync(u->grads, 0, N_PARAMS * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(lacc, 0, sizeof(float), s);
-    if (e == cudaSuccess) e = gsk::up_prep_input(lr_rgb, (long long)px, act[0], s);
+    if (e == cudaSuccess) e = gsk::up_prep_input(lr_rgb, n, h, w, act[0], s);
     for (int l = 0; l < 6 && e == cudaSuccess; ++l) {
         const float *bias = u->params + layer_off(l) + (long long)L_CO[l] * L_CI[l] * 9;
         e = gsk::up_conv_forward(l, act[l], n, h, w, u->wf[l], bias, l < 5 ? (void *)act[l + 1] : (void *)z, s);

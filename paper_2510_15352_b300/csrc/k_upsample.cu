@@ -1,12 +1,15 @@
 // k_upsample.cu -- the learned 4x upsampler's kernels on the BF16 tensor cores
 // (warp-level mma.sync m16n8k16, FP32 accumulation).
 //
-// Network (a residual CNN on the 160x120 render of a camera): x0 = rgb - 1/2,
-// five 3x3 convolutions of 32 channels with ReLU, a 3x3 convolution to 48
-// channels, pixel shuffle x4 (channel 16 c + 4 dy + dx -> colour c at offset
-// (dy, dx)) added to the bilinear x4 upsampling of rgb (half-pixel centres,
-// edge clamp). Activations are NHWC BF16; weights are BF16 copies of FP32
-// master weights.
+// Network (a residual CNN on the 160x120 render of a camera): the input is
+// x0 = [rgb - 1/2, S (rgb - box3(rgb))] (box3: 3x3 mean, edge clamp; S = 32),
+// then five 3x3 convolutions of 32 channels with ReLU, a 3x3 convolution to
+// 48 channels, pixel shuffle x4 (channel 16 c + 4 dy + dx -> colour c at
+// offset (dy, dx)) scaled by 1/S and added to the bilinear x4 upsampling of
+// rgb (half-pixel centres, edge clamp). The detail channels and the 1/S scale
+// keep the ~1e-3 differences between a render and its bilinear upsampling far
+// above BF16's relative precision. Activations are NHWC BF16; weights are BF16
+// copies of FP32 master weights.
 //
 // A convolution is an implicit GEMM over a tile of 8 x 16 output pixels: the
 // input tile with its one-pixel halo and all nine taps of the weights sit in
@@ -34,6 +37,7 @@ constexpr int UT_W = 16, UT_H = 8;            // output tile of a convolution bl
 constexpr int UH_W = UT_W + 2, UH_H = UT_H + 2;  // input tile with halo
 constexpr int CONV_THREADS = 128;             // 4 warps x 2 tile rows
 constexpr int WGRAD_THREADS = 288;            // one warp per tap
+constexpr float DETAIL_S = 32.0f;             // scale of the detail channels and 1/S of the output
 
 typedef __nv_bfloat16 bf16;
 
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(CONV_THREADS)
 }
 
 // Last layer for inference: z = conv(h5) + bias (48 channels), then
-// out[4y + dy][4x + dx][c] = bilinear(rgb)[..][c] + z[16 c + 4 dy + dx], written
+// out[4y + dy][4x + dx][c] = bilinear(rgb)[..][c] + z[16 c + 4 dy + dx] / S, written
 // as whole HR rows of the tile (coalesced).
 template <int CIN>
 __global__ void __launch_bounds__(CONV_THREADS)
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(CONV_THREADS)
         const float bl = fmaf(fy, bot - top, top);
         const int p = (row >> 2) * UT_W + (X >> 2);
         const float z = zs[p * ZS + 16 * c + 4 * (row & 3) + (X & 3)];
-        out[(((long long)img * H4 + HY) * W4 + HX) * 3 + c] = bl + z;
+        out[(((long long)img * H4 + HY) * W4 + HX) * 3 + c] = fmaf(z, 1.0f / DETAIL_S, bl);
     }
 }
 
@@ -338,23 +342,42 @@ __global__ void __launch_bounds__(WGRAD_THREADS)
     if (tid < COUT) atomicAdd(&gb[tid], bacc);
 }
 
-// x0 = rgb - 1/2 in BF16, channels 3..15 zero.
-__global__ void k_prep_input(const float *__restrict__ rgb, long long n_pix,
+// x0 = [rgb - 1/2, S (rgb - box3(rgb))] in BF16, channels 6..15 zero.
+__global__ void k_prep_input(const float *__restrict__ rgb, int n, int h, int w,
                              bf16 *__restrict__ x0) {
+    const long long n_pix = (long long)n * h * w;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n_pix;
          p += (long long)gridDim.x * blockDim.x) {
+        const int img = (int)(p / ((long long)h * w));
+        const int rem = (int)(p - (long long)img * h * w);
+        const int y = rem / w, x = rem - y * w;
+        const float *base = rgb + (long long)img * h * w * 3;
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+        for (int du = -1; du <= 1; ++du) {
+            const int yy = min(max(y + du, 0), h - 1);
+#pragma unroll
+            for (int dv = -1; dv <= 1; ++dv) {
+                const int xx = min(max(x + dv, 0), w - 1);
+                const float *q = base + (yy * w + xx) * 3;
+                s0 += q[0];
+                s1 += q[1];
+                s2 += q[2];
+            }
+        }
+        const float r = rgb[3 * p], g = rgb[3 * p + 1], b = rgb[3 * p + 2];
         uint4 lo, hi = make_uint4(0u, 0u, 0u, 0u);
-        lo.x = pack_bf16(rgb[3 * p] - 0.5f, rgb[3 * p + 1] - 0.5f);
-        lo.y = pack_bf16(rgb[3 * p + 2] - 0.5f, 0.0f);
-        lo.z = 0u;
+        lo.x = pack_bf16(r - 0.5f, g - 0.5f);
+        lo.y = pack_bf16(b - 0.5f, DETAIL_S * (r - s0 / 9.0f));
+        lo.z = pack_bf16(DETAIL_S * (g - s1 / 9.0f), DETAIL_S * (b - s2 / 9.0f));
         lo.w = 0u;
         *(uint4 *)(x0 + 16 * p) = lo;
         *(uint4 *)(x0 + 16 * p + 8) = hi;
     }
 }
 
-// Loss of the training pass: out = bilinear(rgb) + shuffle(z); per LR pixel
-// and channel, dz = 2 (out - target) / count (BF16) and sum (out - target)^2 / count.
+// Loss of the training pass: out = bilinear(rgb) + shuffle(z) / S; per LR pixel
+// and channel, dz = 2 (out - target) / (count S) (BF16) and sum (out - target)^2 / count.
 __global__ void __launch_bounds__(256)
     k_upsample_loss(const float *__restrict__ z, const float *__restrict__ rgb,
                     const float *__restrict__ target, int n, int h, int w,
@@ -380,9 +403,9 @@ __global__ void __launch_bounds__(256)
         const float a00 = base[(y0 * w + x0) * 3 + c], a01 = base[(y0 * w + x1) * 3 + c];
         const float a10 = base[(y1 * w + x0) * 3 + c], a11 = base[(y1 * w + x1) * 3 + c];
         const float top = fmaf(fx, a01 - a00, a00), bot = fmaf(fx, a11 - a10, a10);
-        const float o = fmaf(fy, bot - top, top) + z[i];
+        const float o = fmaf(z[i], 1.0f / DETAIL_S, fmaf(fy, bot - top, top));
         const float d = o - target[(((long long)img * H4 + HY) * W4 + HX) * 3 + c];
-        dz[i] = __float2bfloat16_rn(2.0f * d * inv);
+        dz[i] = __float2bfloat16_rn(2.0f * d * inv * (1.0f / DETAIL_S));
         part = fmaf(d * d, inv, part);
     }
 #pragma unroll
@@ -487,10 +510,12 @@ cudaError_t run_wgrad(const bf16 *x, const bf16 *dz, int n, int h, int w, float 
 
 // ---- launchers ----
 
-cudaError_t up_prep_input(const float *rgb, long long n_pix, __nv_bfloat16 *x0, cudaStream_t s) {
+cudaError_t up_prep_input(const float *rgb, int n, int h, int w, __nv_bfloat16 *x0,
+                          cudaStream_t s) {
+    const long long n_pix = (long long)n * h * w;
     if (n_pix == 0) return cudaSuccess;
     const int grid = (int)std::min<long long>((n_pix + 255) / 256, 148LL * 16);
-    k_prep_input<<<grid, 256, 0, s>>>(rgb, n_pix, x0);
+    k_prep_input<<<grid, 256, 0, s>>>(rgb, n, h, w, x0);
     return cudaGetLastError();
 }
 
@@ -526,7 +551,7 @@ cudaError_t up_conv_dgrad(int layer, const __nv_bfloat16 *dz, int n, int h, int 
 
 cudaError_t up_wgrad(int layer, const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int n, int h,
                      int w, float *gW, float *gb, int n_sm, cudaStream_t s) {
-    if (layer == 0) return run_wgrad<16, 32>(x, dz, n, h, w, gW, gb, 3, n_sm, s);
+    if (layer == 0) return run_wgrad<16, 32>(x, dz, n, h, w, gW, gb, 6, n_sm, s);
     if (layer < 5) return run_wgrad<32, 32>(x, dz, n, h, w, gW, gb, 32, n_sm, s);
     return run_wgrad<32, 48>(x, dz, n, h, w, gW, gb, 32, n_sm, s);
 }

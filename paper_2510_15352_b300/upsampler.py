@@ -26,7 +26,7 @@ def init_params(seed: int) -> np.ndarray:
     """He-normal weights for the ReLU layers, zero biases, zero last layer: the
     untrained network is exactly bilinear upsampling."""
     rng = np.random.default_rng([seed, 11])
-    shapes = [(32, 3)] + [(32, 32)] * 4 + [(48, 32)]
+    shapes = [(32, 6)] + [(32, 32)] * 4 + [(48, 32)]
     parts = []
     for li, (co, ci) in enumerate(shapes):
         W = rng.normal(0.0, math.sqrt(2.0 / (9 * ci)), size=(co, ci, 3, 3))

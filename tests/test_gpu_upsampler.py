@@ -3,13 +3,18 @@ gradients, Adam), and the gain of the trained network over bilinear
 upsampling on renderer pairs.
 
 Precision: the kernels keep weights and activations in BF16 (8 significant
-bits, relative rounding <= 2^-9) with FP32 accumulation. The tests feed both
-sides the same BF16-representable weights and inputs, so the differences come
-only from rounding the five hidden activations (and, backward, the gradients
-between layers) to BF16. Each rounding perturbs a value by <= 2^-9 relative;
-over six layers the propagated relative error of an output or a weight
-gradient stays below ~6 x 2^-9 = 1.2 % in the worst case and is ~0.3 % in
-RMS. The bars: relative Frobenius error <= 2 % per layer, cosine >= 0.999.
+bits) with FP32 accumulation. The tests feed both sides the same
+BF16-representable weights and inputs, so the differences come from rounding
+the hidden activations and the back-propagated gradients to BF16 (relative
+2^-9 each). Two references:
+  * the exact FP64 oracle: a weight gradient several layers down sums many
+    terms of both signs, so the storage roundings show up relatively larger
+    there (emulated on these cases: up to ~5 % for layer 1, <= 2.4 % above);
+    bar 8 %, cosine >= 0.995;
+  * the oracle's own functions with the same BF16 storage points emulated in
+    the test (activations after ReLU and the gradients between layers rounded
+    to BF16): only FP32-vs-FP64 accumulation and rare one-ulp rounding flips
+    remain; bar 3e-3.
 """
 from __future__ import annotations
 
@@ -57,7 +62,7 @@ def random_case(seed, n, h, w):
         nW += m + co
     for a, b in qs:
         flat[a:b] = bf16_round(flat[a:b])
-    # rgb - 1/2 exactly representable in BF16
+    # rgb - 1/2 exactly representable in BF16 (the detail channels are rounded)
     rgb = (0.5 + rng.integers(-128, 128, size=(n, h, w, 3)) / 256.0).astype(np.float32)
     tgt = rng.uniform(0, 1, size=(n, 4 * h, 4 * w, 3)).astype(np.float32)
     return flat, rgb, tgt
@@ -68,6 +73,34 @@ def torch_cuda():
     import torch
     assert torch.cuda.is_available()
     return torch
+
+
+def emulate_bf16_storage(params, rgb, tgt):
+    """Loss, gradients and output of the oracle with the kernels' BF16 storage
+    points: the network input, the ReLU outputs and the gradients between layers rounded to
+    BF16, the last layer's output to float32."""
+    def bf(a):
+        return bf16_round(np.asarray(a, np.float32)).astype(np.float64)
+    x = rgb.astype(np.float64)
+    h = bf(U.network_input(x))
+    acts = [h]
+    for li, (W, b) in enumerate(params):
+        z = U.conv3x3(h, W, b)
+        if li < U.N_LAYERS - 1:
+            h = bf(np.maximum(z, 0.0))
+            acts.append(h)
+        else:
+            z6 = z.astype(np.float32).astype(np.float64)
+    out = U.bilinear(x) + U.pixel_shuffle(z6) / U.DETAIL_SCALE
+    diff = out - tgt
+    d = bf(U.pixel_unshuffle(2.0 * diff / diff.size) / U.DETAIL_SCALE)
+    grads = [None] * U.N_LAYERS
+    for li in range(U.N_LAYERS - 1, -1, -1):
+        dx, dW, db = U.conv3x3_backward(acts[li], params[li][0], d)
+        grads[li] = (dW, db)
+        if li > 0:
+            d = bf(dx * (acts[li] > 0.0))
+    return float(np.mean(diff * diff)), grads, out
 
 
 def rel_err(a, b):
@@ -92,12 +125,15 @@ def test_forward_matches_oracle(torch_cuda, n, h, w):
         out, od = out.cpu().numpy(), od.cpu().numpy()
     finally:
         up.close()
-    ref = U.forward(flat_to_layers(flat), rgb)
+    params = flat_to_layers(flat)
+    ref = U.forward(params, rgb)
     bil = U.bilinear(rgb)
     res_ref, res_gpu = ref - bil, out - bil
     assert rel_err(res_gpu, res_ref) <= 2e-2
     assert cosine(res_gpu, res_ref) >= 0.999
     assert np.abs(out - ref).max() <= 2e-2 * np.abs(res_ref).max() + 1e-5
+    emu = emulate_bf16_storage(params, rgb, np.zeros((n, 4 * h, 4 * w, 3)))[2]
+    assert rel_err(res_gpu, emu - bil) <= 3e-3
     np.testing.assert_allclose(od, U.bilinear(depth[..., None].astype(np.float64))[..., 0],
                                rtol=1e-6, atol=1e-6)
 
@@ -130,13 +166,18 @@ def test_gradients_match_oracle(torch_cuda, n, h, w):
         g = up.get_grads()
     finally:
         up.close()
-    ref_loss, ref_grads = U.loss_and_grads(flat_to_layers(flat), rgb, tgt)
+    params = flat_to_layers(flat)
+    ref_loss, ref_grads = U.loss_and_grads(params, rgb, tgt)
+    _, emu_grads, _ = emulate_bf16_storage(params, rgb, tgt)
     assert loss == pytest.approx(ref_loss, rel=1e-3)
+    errs = []
     for li, (gw, gb) in enumerate(flat_to_layers(g)):
-        rw, rb = ref_grads[li]
-        assert rel_err(gw, rw) <= 2e-2, (li, rel_err(gw, rw))
-        assert cosine(gw, rw) >= 0.999, li
-        assert rel_err(gb, rb) <= 2e-2, (li, rel_err(gb, rb))
+        (rw, rb), (ew, eb) = ref_grads[li], emu_grads[li]
+        errs.append((li, rel_err(gw, rw), cosine(gw, rw), rel_err(gb, rb), rel_err(gw, ew),
+                     rel_err(gb, eb)))
+    for li, ew_exact, cos, eb_exact, ew_emu, eb_emu in errs:
+        assert ew_exact <= 8e-2 and eb_exact <= 8e-2 and cos >= 0.995, errs
+        assert ew_emu <= 3e-3 and eb_emu <= 3e-3, errs
 
 
 def test_adam_step_matches_oracle(torch_cuda):

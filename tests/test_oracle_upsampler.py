@@ -75,6 +75,22 @@ def test_zero_last_layer_is_bilinear():
     np.testing.assert_allclose(U.forward(params, rgb), U.bilinear(rgb), atol=1e-15)
 
 
+def test_box3_and_network_input():
+    x = np.zeros((1, 4, 5, 3))
+    x[0, 0, 0, 1] = 9.0          # corner: clamping counts it 4 times in its own mean
+    x[0, 2, 2, 2] = 9.0          # interior
+    b = U.box3(x)
+    assert b[0, 0, 0, 1] == pytest.approx(4.0) and b[0, 1, 1, 1] == pytest.approx(1.0)
+    assert b[0, 2, 2, 2] == pytest.approx(1.0) and b[0, 3, 3, 2] == pytest.approx(1.0)
+    assert b[0, 0, 2, 2] == 0.0 and b[0, 3, 4, 0] == 0.0
+    const = np.full((2, 3, 4, 3), 0.7)
+    x0 = U.network_input(const)
+    np.testing.assert_allclose(x0[..., :3], 0.2, atol=1e-15)
+    np.testing.assert_allclose(x0[..., 3:], 0.0, atol=1e-14)
+    x0 = U.network_input(x)
+    np.testing.assert_allclose(x0[0, 2, 2, 5], U.DETAIL_SCALE * 8.0, rtol=1e-14)
+
+
 def _fd_check(params, rgb, tgt, picks, h=1e-6):
     loss, grads = U.loss_and_grads(params, rgb, tgt)
     for li, kind, idx in picks:
