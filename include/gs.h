@@ -345,6 +345,17 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
                               const float *lr_rgb, const float *lr_depth, float *hr_rgb,
                               float *hr_depth, void *stream);
 
+/* Kernels of gs_upsample_forward: the 5th-generation tensor cores (tcgen05.mma
+ * with tensor-memory accumulators; the default) or warp-level mma.sync. Both
+ * compute the same network with BF16 operands and FP32 accumulation. */
+enum { GS_UPSAMPLE_TCGEN05 = 0, GS_UPSAMPLE_MMA_SYNC = 1 };
+gs_status gs_upsampler_set_backend(gs_upsampler *u, int32_t backend);
+
+/* Waits for `stream` and reports whether a tensor-core convolution enqueued
+ * on it gave up waiting for its MMAs (GS_ERR_TIMEOUT; that call's outputs are
+ * incomplete). Clears the flag. */
+gs_status gs_upsample_check(gs_upsampler *u, void *stream);
+
 /* Training pass: forward on lr_rgb, loss = mean over HR pixels and channels of
  * (out - hr_target)^2, and the gradient of the loss with respect to every
  * parameter into the upsampler's gradient buffer (replacing the previous one).

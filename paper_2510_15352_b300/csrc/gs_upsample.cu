@@ -32,9 +32,12 @@ cudaError_t up_loss(const float *z, const float *rgb, const float *target, int n
 cudaError_t up_bilinear1(const float *src, int n, int h, int w, float *dst, cudaStream_t s);
 cudaError_t up_adam(float *p, float *m, float *v, const float *g, int co, int ci, int cin_pad,
                     float lr, float b1, float b2, float eps, float c1, float c2,
-                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, cudaStream_t s);
+                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s);
 cudaError_t up_weights_bf16(const float *p, int co, int ci, int cin_pad, __nv_bfloat16 *wf,
-                            __nv_bfloat16 *wd, cudaStream_t s);
+                            __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s);
+cudaError_t up_conv_tc(int layer, const __nv_bfloat16 *x, int n, int h, int w,
+                       const __nv_bfloat16 *wt, const float *bias, void *out, const float *rgb,
+                       int *status, int n_sm, cudaStream_t s);
 }  // namespace gsk
 
 namespace {
@@ -66,8 +69,10 @@ struct Buf {
 struct gs_upsampler {
     int device = 0, n_sm = 148;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *wf[NL] = {}, *wd[NL] = {};
+    bf16 *wf[NL] = {}, *wd[NL] = {}, *wt[NL] = {};
     bf16 *wblock = nullptr;
+    int *status = nullptr;  // device: set when a tensor-core kernel timed out
+    int backend = GS_UPSAMPLE_TCGEN05;
     long long steps = 0;
     Buf work;
     std::string err;
@@ -111,7 +116,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 cudaError_t refresh_bf16(gs_upsampler *u, cudaStream_t s) {
     for (int l = 0; l < NL; ++l) {
         cudaError_t e = gsk::up_weights_bf16(u->params + layer_off(l), L_CO[l], L_CI[l], L_CIP[l],
-                                             u->wf[l], l > 0 ? u->wd[l] : nullptr, s);
+                                             u->wf[l], l > 0 ? u->wd[l] : nullptr, u->wt[l], s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -135,7 +140,8 @@ gs_status gs_upsampler_create(int32_t device, gs_upsampler **out) {
     cudaDeviceGetAttribute(&u->n_sm, cudaDevAttrMultiProcessorCount, device);
     size_t wbytes = 0;
     for (int l = 0; l < NL; ++l)
-        wbytes += 2 * align256((size_t)9 * L_CO[l] * std::max(L_CIP[l], L_CI[l]) * sizeof(bf16));
+        wbytes += 3 * align256((size_t)9 * L_CO[l] * std::max(L_CIP[l], L_CI[l]) * sizeof(bf16));
+    wbytes += 256;  // status word
     cudaError_t e = cudaMalloc(&u->params, 4 * N_PARAMS * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&u->wblock, wbytes);
     if (e != cudaSuccess) {
@@ -153,8 +159,10 @@ gs_status gs_upsampler_create(int32_t device, gs_upsampler **out) {
         const size_t sz = align256((size_t)9 * L_CO[l] * std::max(L_CIP[l], L_CI[l]) * sizeof(bf16));
         u->wf[l] = (bf16 *)w;
         u->wd[l] = (bf16 *)(w + sz);
-        w += 2 * sz;
+        u->wt[l] = (bf16 *)(w + 2 * sz);
+        w += 3 * sz;
     }
+    u->status = (int *)w;
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(u->params);
@@ -227,24 +235,51 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
     bf16 *x0 = (bf16 *)base;
     bf16 *a = (bf16 *)(base + align256(px * 16 * 2) * group);
     bf16 *b = (bf16 *)((char *)a + align256(px * 32 * 2) * group);
+    const bool tc = u->backend == GS_UPSAMPLE_TCGEN05;
     for (int f0 = 0; f0 < n; f0 += group) {
         const int m = std::min(group, n - f0);
         const float *rgb = lr_rgb + (size_t)f0 * px * 3;
+        float *hr = hr_rgb + (size_t)f0 * px * 48;
         e = gsk::up_prep_input(rgb, m, h, w, x0, s);
-        if (e == cudaSuccess)
-            e = gsk::up_conv_forward(0, x0, m, h, w, u->wf[0], u->params + layer_off(0) + 32 * 6 * 9, a, s);
-        for (int l = 1; l < 5 && e == cudaSuccess; ++l) {
-            e = gsk::up_conv_forward(l, a, m, h, w, u->wf[l],
-                                     u->params + layer_off(l) + (long long)L_CO[l] * L_CI[l] * 9, b, s);
-            std::swap(a, b);
+        const bf16 *in = x0;
+        for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+            const float *bias = u->params + layer_off(l) + (long long)L_CO[l] * L_CI[l] * 9;
+            bf16 *dst = (in == a) ? b : a;
+            if (tc)
+                e = gsk::up_conv_tc(l, in, m, h, w, u->wt[l], bias, l < NL - 1 ? (void *)dst : (void *)hr,
+                                    rgb, u->status, u->n_sm, s);
+            else if (l < NL - 1)
+                e = gsk::up_conv_forward(l, in, m, h, w, u->wf[l], bias, dst, s);
+            else
+                e = gsk::up_conv_upsample(in, m, h, w, u->wf[l], bias, rgb, hr, s);
+            in = dst;
         }
-        if (e == cudaSuccess)
-            e = gsk::up_conv_upsample(a, m, h, w, u->wf[5], u->params + layer_off(5) + 48 * 32 * 9, rgb,
-                                      hr_rgb + (size_t)f0 * px * 48, s);
         if (e == cudaSuccess && lr_depth)
             e = gsk::up_bilinear1(lr_depth + (size_t)f0 * px, m, h, w, hr_depth + (size_t)f0 * px * 16, s);
         if (e != cudaSuccess) return cuda_fail(u, e, "upsample_forward");
-        // a and b were swapped an even number of times: restore for the next group
+    }
+    return GS_OK;
+}
+
+gs_status gs_upsampler_set_backend(gs_upsampler *u, int32_t backend) {
+    if (!u || (backend != GS_UPSAMPLE_TCGEN05 && backend != GS_UPSAMPLE_MMA_SYNC))
+        return fail(u, GS_ERR_INVALID_ARG, "set_backend: unknown backend");
+    u->backend = backend;
+    return GS_OK;
+}
+
+gs_status gs_upsample_check(gs_upsampler *u, void *stream) {
+    if (!u) return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(u->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, u->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(u, e, "upsample_check");
+    if (st) {
+        cudaMemsetAsync(u->status, 0, sizeof(int), s);
+        cudaStreamSynchronize(s);
+        return fail(u, GS_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
     }
     return GS_OK;
 }
@@ -312,7 +347,7 @@ gs_status gs_upsample_adam(gs_upsampler *u, float lr, float beta1, float beta2, 
         const long long o = layer_off(l);
         cudaError_t e = gsk::up_adam(u->params + o, u->m + o, u->v + o, u->grads + o, L_CO[l], L_CI[l],
                                      L_CIP[l], lr, beta1, beta2, eps, c1, c2, u->wf[l],
-                                     l > 0 ? u->wd[l] : nullptr, s);
+                                     l > 0 ? u->wd[l] : nullptr, u->wt[l], s);
         if (e != cudaSuccess) return cuda_fail(u, e, "upsample_adam");
     }
     return GS_OK;

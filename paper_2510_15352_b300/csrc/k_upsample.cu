@@ -434,13 +434,24 @@ __global__ void k_bilinear1(const float *__restrict__ src, int n, int h, int w,
     }
 }
 
+// Writes one weight, as BF16, into the three layouts the kernels read:
+// wf[tap][co][cin_pad] (warp-level MMA, forward), wd[8 - tap][ci][co] (backward
+// data pass) and wt[tap][cin_pad / 8][co][8] (tcgen05 K-major B operand).
+__device__ __forceinline__ void store_weight(float val, int i, int co, int ci, int cin_pad,
+                                             bf16 *wf, bf16 *wd, bf16 *wt) {
+    const int o = i / (ci * 9), rem = i - o * ci * 9, c = rem / 9, tap = rem - 9 * c;
+    const bf16 b = __float2bfloat16_rn(val);
+    wf[((long long)tap * co + o) * cin_pad + c] = b;
+    if (wd) wd[((long long)(8 - tap) * ci + c) * co + o] = b;
+    if (wt) wt[(((long long)tap * (cin_pad / 8) + c / 8) * co + o) * 8 + (c & 7)] = b;
+}
+
 // Adam on one layer's FP32 master weights [co][ci][3][3] and biases [co]
-// (flat: weights then biases), refreshing the BF16 copies: forward
-// wf[tap][co][cin_pad] and backward-data wd[8 - tap][ci][co].
+// (flat: weights then biases), refreshing the BF16 copies.
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                        const float *__restrict__ g, int co, int ci, int cin_pad, float lr,
                        float b1, float b2, float eps, float c1, float c2, bf16 *__restrict__ wf,
-                       bf16 *__restrict__ wd) {
+                       bf16 *__restrict__ wd, bf16 *__restrict__ wt) {
     const int nW = co * ci * 9, total = nW + co;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -450,25 +461,17 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
         v[i] = vi;
         const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         p[i] = pi;
-        if (i < nW) {
-            const int o = i / (ci * 9), rem = i - o * ci * 9, c = rem / 9, tap = rem - 9 * c;
-            const bf16 b = __float2bfloat16_rn(pi);
-            wf[((long long)tap * co + o) * cin_pad + c] = b;
-            if (wd) wd[((long long)(8 - tap) * ci + c) * co + o] = b;
-        }
+        if (i < nW) store_weight(pi, i, co, ci, cin_pad, wf, wd, wt);
     }
 }
 
 // BF16 copies of one layer's weights without an update (after a parameter upload).
 __global__ void k_weights_bf16(const float *__restrict__ p, int co, int ci, int cin_pad,
-                               bf16 *__restrict__ wf, bf16 *__restrict__ wd) {
+                               bf16 *__restrict__ wf, bf16 *__restrict__ wd,
+                               bf16 *__restrict__ wt) {
     const int nW = co * ci * 9;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nW; i += gridDim.x * blockDim.x) {
-        const int o = i / (ci * 9), rem = i - o * ci * 9, c = rem / 9, tap = rem - 9 * c;
-        const bf16 b = __float2bfloat16_rn(p[i]);
-        wf[((long long)tap * co + o) * cin_pad + c] = b;
-        if (wd) wd[((long long)(8 - tap) * ci + c) * co + o] = b;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nW; i += gridDim.x * blockDim.x)
+        store_weight(p[i], i, co, ci, cin_pad, wf, wd, wt);
 }
 
 template <int CIN, int COUT>
@@ -575,17 +578,17 @@ cudaError_t up_bilinear1(const float *src, int n, int h, int w, float *dst, cuda
 
 cudaError_t up_adam(float *p, float *m, float *v, const float *g, int co, int ci, int cin_pad,
                     float lr, float b1, float b2, float eps, float c1, float c2,
-                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, cudaStream_t s) {
+                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s) {
     const int total = co * ci * 9 + co;
     k_adam<<<(total + 255) / 256, 256, 0, s>>>(p, m, v, g, co, ci, cin_pad, lr, b1, b2, eps, c1,
-                                                c2, wf, wd);
+                                                c2, wf, wd, wt);
     return cudaGetLastError();
 }
 
 cudaError_t up_weights_bf16(const float *p, int co, int ci, int cin_pad, __nv_bfloat16 *wf,
-                            __nv_bfloat16 *wd, cudaStream_t s) {
+                            __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s) {
     const int nW = co * ci * 9;
-    k_weights_bf16<<<(nW + 255) / 256, 256, 0, s>>>(p, co, ci, cin_pad, wf, wd);
+    k_weights_bf16<<<(nW + 255) / 256, 256, 0, s>>>(p, co, ci, cin_pad, wf, wd, wt);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,8 @@ SIGNATURES = {
     "gs_upsample_grad": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp]),
     "gs_upsample_adam": (ctypes.c_int, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, _vp]),
+    "gs_upsampler_set_backend": (ctypes.c_int, [_vp, _i32]),
+    "gs_upsample_check": (ctypes.c_int, [_vp, _vp]),
 }
 
 
@@ -148,6 +150,9 @@ gs_upsampler_get_grads = lib.gs_upsampler_get_grads
 gs_upsample_forward = lib.gs_upsample_forward
 gs_upsample_grad = lib.gs_upsample_grad
 gs_upsample_adam = lib.gs_upsample_adam
+gs_upsampler_set_backend = lib.gs_upsampler_set_backend
+gs_upsample_check = lib.gs_upsample_check
+GS_UPSAMPLE_TCGEN05, GS_UPSAMPLE_MMA_SYNC = 0, 1
 
 
 class GSError(RuntimeError):
@@ -462,3 +467,12 @@ class Upsampler:
     def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
              stream=None) -> None:
         self._check(gs_upsample_adam(self.u, lr, beta1, beta2, eps, _stream(stream)))
+
+    def set_backend(self, backend: str) -> None:
+        """"tcgen05" (default) or "mma_sync": the kernels of forward()."""
+        code = {"tcgen05": GS_UPSAMPLE_TCGEN05, "mma_sync": GS_UPSAMPLE_MMA_SYNC}[backend]
+        self._check(gs_upsampler_set_backend(self.u, code))
+
+    def check(self, stream=None) -> None:
+        """Synchronise and raise if a tensor-core kernel timed out."""
+        self._check(gs_upsample_check(self.u, _stream(stream)))
