@@ -342,16 +342,13 @@ __global__ void __launch_bounds__(WGRAD_THREADS)
     if (tid < COUT) atomicAdd(&gb[tid], bacc);
 }
 
-// x0 = [rgb - 1/2, S (rgb - box3(rgb))] in BF16, channels 6..15 zero.
-__global__ void k_prep_input(const float *__restrict__ rgb, int n, int h, int w,
-                             bf16 *__restrict__ x0) {
-    const long long n_pix = (long long)n * h * w;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n_pix;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int img = (int)(p / ((long long)h * w));
-        const int rem = (int)(p - (long long)img * h * w);
-        const int y = rem / w, x = rem - y * w;
-        const float *base = rgb + (long long)img * h * w * 3;
+// x0 = [rgb - 1/2, S (rgb - box3(rgb))] in BF16, channels 6..15 zero. One
+// block row per image row (blockIdx.x = img * h + y).
+__global__ void k_prep_input(const float *__restrict__ rgb, int h, int w, bf16 *__restrict__ x0) {
+    const int y = blockIdx.x % h;
+    const long long rowp = (long long)blockIdx.x * w;  // first pixel of this row
+    const float *row_img = rgb + (rowp - (long long)y * w) * 3;  // first pixel of the image
+    for (int x = threadIdx.x; x < w; x += blockDim.x) {
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
 #pragma unroll
         for (int du = -1; du <= 1; ++du) {
@@ -359,12 +356,13 @@ __global__ void k_prep_input(const float *__restrict__ rgb, int n, int h, int w,
 #pragma unroll
             for (int dv = -1; dv <= 1; ++dv) {
                 const int xx = min(max(x + dv, 0), w - 1);
-                const float *q = base + (yy * w + xx) * 3;
+                const float *q = row_img + ((long long)yy * w + xx) * 3;
                 s0 += q[0];
                 s1 += q[1];
                 s2 += q[2];
             }
         }
+        const long long p = rowp + x;
         const float r = rgb[3 * p], g = rgb[3 * p + 1], b = rgb[3 * p + 2];
         uint4 lo, hi = make_uint4(0u, 0u, 0u, 0u);
         lo.x = pack_bf16(r - 0.5f, g - 0.5f);
@@ -414,23 +412,22 @@ __global__ void __launch_bounds__(256)
 }
 
 // Bilinear x4 of a single-channel image (the depth of the upsampled path).
-__global__ void k_bilinear1(const float *__restrict__ src, int n, int h, int w,
-                            float *__restrict__ dst) {
+// One block per HR row (blockIdx.x = img * 4h + HY).
+__global__ void k_bilinear1(const float *__restrict__ src, int h, int w, float *__restrict__ dst) {
     const int H4 = 4 * h, W4 = 4 * w;
-    const long long total = (long long)n * H4 * W4;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int img = (int)(i / ((long long)H4 * W4));
-        const int rem = (int)(i - (long long)img * H4 * W4);
-        const int HY = rem / W4, HX = rem - HY * W4;
-        int y0, y1, x0, x1;
-        float fy, fx;
-        bl_src(HY, h, y0, y1, fy);
+    const int img = blockIdx.x / H4, HY = blockIdx.x - img * H4;
+    int y0, y1;
+    float fy;
+    bl_src(HY, h, y0, y1, fy);
+    const float *b = src + (long long)img * h * w;
+    float *o = dst + (long long)blockIdx.x * W4;
+    for (int HX = threadIdx.x; HX < W4; HX += blockDim.x) {
+        int x0, x1;
+        float fx;
         bl_src(HX, w, x0, x1, fx);
-        const float *b = src + (long long)img * h * w;
         const float top = fmaf(fx, b[y0 * w + x1] - b[y0 * w + x0], b[y0 * w + x0]);
         const float bot = fmaf(fx, b[y1 * w + x1] - b[y1 * w + x0], b[y1 * w + x0]);
-        dst[i] = fmaf(fy, bot - top, top);
+        o[HX] = fmaf(fy, bot - top, top);
     }
 }
 
@@ -515,10 +512,8 @@ cudaError_t run_wgrad(const bf16 *x, const bf16 *dz, int n, int h, int w, float 
 
 cudaError_t up_prep_input(const float *rgb, int n, int h, int w, __nv_bfloat16 *x0,
                           cudaStream_t s) {
-    const long long n_pix = (long long)n * h * w;
-    if (n_pix == 0) return cudaSuccess;
-    const int grid = (int)std::min<long long>((n_pix + 255) / 256, 148LL * 16);
-    k_prep_input<<<grid, 256, 0, s>>>(rgb, n, h, w, x0);
+    if ((long long)n * h == 0) return cudaSuccess;
+    k_prep_input<<<n * h, std::min(256, (w + 31) / 32 * 32), 0, s>>>(rgb, h, w, x0);
     return cudaGetLastError();
 }
 
@@ -569,10 +564,8 @@ cudaError_t up_loss(const float *z, const float *rgb, const float *target, int n
 }
 
 cudaError_t up_bilinear1(const float *src, int n, int h, int w, float *dst, cudaStream_t s) {
-    const long long total = (long long)n * 16 * h * w;
-    if (total == 0) return cudaSuccess;
-    const int grid = (int)std::min<long long>((total + 255) / 256, 148LL * 16);
-    k_bilinear1<<<grid, 256, 0, s>>>(src, n, h, w, dst);
+    if ((long long)n * h == 0) return cudaSuccess;
+    k_bilinear1<<<n * 4 * h, std::min(256, (4 * w + 31) / 32 * 32), 0, s>>>(src, h, w, dst);
     return cudaGetLastError();
 }
 

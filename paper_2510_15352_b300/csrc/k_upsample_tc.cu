@@ -16,11 +16,15 @@
 // Weights are staged once per block as [tap][c8][c_out][8] (K-major B).
 //
 // Blocks are persistent: weights and the tensor-memory accumulator (2 M-tiles
-// x N columns) are set up once, then each block walks its tiles: load the input
-// tile, one thread issues 9 taps x CIN/16 x 2 MMAs and commits them to an
-// mbarrier, every warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) and writes
-// the epilogue. Every mbarrier wait is bounded; on time-out the block records
-// the error in the status word and leaves, releasing its tensor memory.
+// x N columns) are set up once, then each block walks its tiles: one thread
+// issues 9 taps x CIN/16 x 2 MMAs on the staged tile and commits them to an
+// mbarrier, the block starts the asynchronous copy of its next tile into the
+// other buffer, and every warp reads its 32 TMEM lanes (tcgen05.ld 32x32b) and
+// writes the epilogue. The last layer's epilogue turns each LR pixel's 48
+// outputs into its 4 x 4 block of HR pixels (pixel shuffle plus bilinear
+// upsampling from the pixel's 3 x 3 LR neighbourhood). Every mbarrier wait is
+// bounded; on time-out the block records the error in the status word and
+// leaves, releasing its tensor memory.
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -154,25 +158,172 @@ __host__ __device__ constexpr int tmem_stride() {
     return COUT <= 32 ? 32 : 64;
 }
 template <int COUT>
-__host__ __device__ constexpr int tmem_cols() {
-    return TC_MT * tmem_stride<COUT>() <= 64 ? 64 : 128;
+__host__ __device__ constexpr int tmem_cols() {  // two accumulators (double buffer)
+    return 2 * TC_MT * tmem_stride<COUT>() <= 128 ? 128 : 256;
 }
 
 enum : int { TC_EPI_RELU = 0, TC_EPI_UPSAMPLE = 1 };
 
+// Shared memory of a block: two input-tile buffers (the next tile is fetched
+// while the current one is multiplied), the weights, for the upsampling layer
+// three LR-colour tiles (fetched with the input, read one tile later by the
+// epilogue), the biases, two mbarriers and the TMEM address slot.
 template <int CIN, int COUT, int EPI>
 struct TcSmem {
     static constexpr size_t in_bytes = (size_t)(CIN / 8) * TC_PIN * 16;
     static constexpr size_t w_bytes = (size_t)9 * CIN * COUT * 2;
-    static constexpr size_t z_bytes = EPI == TC_EPI_UPSAMPLE ? (size_t)TC_TH * TC_TW * (COUT + 1) * 4 : 0;
     static constexpr size_t l_bytes = EPI == TC_EPI_UPSAMPLE ? (size_t)(TC_TH + 2) * TC_PW * 3 * 4 : 0;
-    static constexpr size_t off_w = in_bytes;
-    static constexpr size_t off_z = off_w + w_bytes;
-    static constexpr size_t off_l = off_z + z_bytes;
-    static constexpr size_t off_bias = off_l + l_bytes;
+    static constexpr size_t off_w = 2 * in_bytes;
+    static constexpr size_t off_l = off_w + w_bytes;
+    static constexpr size_t off_bias = off_l + 3 * l_bytes;
     static constexpr size_t off_bar = off_bias + COUT * 4;
-    static constexpr size_t total = off_bar + 16;
+    static constexpr size_t total = off_bar + 32;
 };
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool fill) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                 "r"(fill ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+struct TileXY {
+    int img, by, bx;
+};
+
+__device__ __forceinline__ TileXY tile_xy(long long tile, int tx, int ty) {
+    TileXY t;
+    t.img = (int)(tile / ((long long)tx * ty));
+    const int rem = (int)(tile - (long long)t.img * tx * ty);
+    t.by = (rem / tx) * TC_TH;
+    t.bx = (rem % tx) * TC_TW;
+    return t;
+}
+
+// Issues the asynchronous copies of one tile's input (and LR colours).
+template <int CIN, int EPI>
+__device__ __forceinline__ void fetch_tile(const bf16 *__restrict__ x, const float *__restrict__ rgb,
+                                           int h, int w, TileXY t, unsigned char *xs, float *ls) {
+    constexpr int C8 = CIN / 8;
+    for (int i = threadIdx.x; i < TC_PIN * C8; i += TC_THREADS) {
+        const int c8 = i / TC_PIN, pos = i - c8 * TC_PIN;
+        const int yy = t.by - 1 + pos / TC_PW, xx = t.bx - 1 + pos % TC_PW;
+        const bool in = pos < TC_ROWS_IN * TC_PW && yy >= 0 && yy < h && xx >= 0 && xx < w;
+        const bf16 *src = in ? x + (((long long)t.img * h + yy) * w + xx) * CIN + c8 * 8 : x;
+        cp_async16(smem_u32(xs + (size_t)i * 16), src, in);
+    }
+    if (EPI == TC_EPI_UPSAMPLE) {
+        for (int i = threadIdx.x; i < (TC_TH + 2) * TC_PW * 3; i += TC_THREADS) {
+            const int q = i / 3, c = i - 3 * q;
+            const int yy = min(max(t.by - 1 + q / TC_PW, 0), h - 1);
+            const int xx = min(max(t.bx - 1 + q % TC_PW, 0), w - 1);
+            cp_async4(smem_u32(ls + i), rgb + (((long long)t.img * h + yy) * w + xx) * 3 + c);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Bilinear x4 weights along one axis for sub-pixel d of LR index i (n pixels):
+// neighbour offsets (-1, 0 or +1 from i) and the weight of the second one.
+__device__ __forceinline__ void bl_axis(int i, int d, int n, int &o0, int &o1, float &f) {
+    int a, b;
+    float t;
+    bl_src(4 * i + d, n, a, b, t);
+    o0 = a - i;
+    o1 = b - i;
+    f = t;
+}
+
+// Epilogue of one tile from accumulator columns dcol (warp w: TMEM lanes 32 w..).
+template <int COUT, int EPI>
+__device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t dcol, TileXY t, int h, int w,
+                                              const float *bs, const float *ls, void *out) {
+    constexpr int CST = tmem_stride<COUT>();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int m = 0; m < TC_MT; ++m) {
+        const int p = m * 128 + warp * 32 + lane;
+        const int row = p / TC_PW, col = p - row * TC_PW;
+        const int yy = t.by + row, xx = t.bx + col;
+        const bool valid = row < TC_TH && col < TC_TW && yy < h && xx < w;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + dcol + (uint32_t)(m * CST);
+        if (EPI == TC_EPI_RELU) {
+            float v[32];
+            tmem_ld32(taddr, v);
+            if (valid) {
+                uint4 *dst = (uint4 *)((bf16 *)out + (((long long)t.img * h + yy) * w + xx) * COUT);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 o;
+                    o.x = pack2(fmaxf(v[8 * q + 0] + bs[8 * q + 0], 0.f), fmaxf(v[8 * q + 1] + bs[8 * q + 1], 0.f));
+                    o.y = pack2(fmaxf(v[8 * q + 2] + bs[8 * q + 2], 0.f), fmaxf(v[8 * q + 3] + bs[8 * q + 3], 0.f));
+                    o.z = pack2(fmaxf(v[8 * q + 4] + bs[8 * q + 4], 0.f), fmaxf(v[8 * q + 5] + bs[8 * q + 5], 0.f));
+                    o.w = pack2(fmaxf(v[8 * q + 6] + bs[8 * q + 6], 0.f), fmaxf(v[8 * q + 7] + bs[8 * q + 7], 0.f));
+                    dst[q] = o;
+                }
+            }
+        } else {
+            // this thread's LR pixel -> its 4 x 4 HR block, all three colours:
+            // out = bilinear4(rgb) + z[16 c + 4 dy + dx] / S
+            float v[32], v2[16];
+            tmem_ld32(taddr, v);
+            tmem_ld16(taddr + 32, v2);
+            if (valid) {
+                float z[48];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) z[c] = v[c] + bs[c];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) z[32 + c] = v2[c] + bs[32 + c];
+                float nb[3][3][3];  // LR colours at (row + a - 1, col + b - 1)
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) nb[a][b][c] = ls[((row + a) * TC_PW + col + b) * 3 + c];
+                int xo0[4], xo1[4];
+                float fx[4];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) bl_axis(xx, d, w, xo0[d], xo1[d], fx[d]);
+                const int W4 = 4 * w;
+#pragma unroll
+                for (int dy = 0; dy < 4; ++dy) {
+                    int yo0, yo1;
+                    float fy;
+                    bl_axis(yy, dy, h, yo0, yo1, fy);
+                    float o[12];
+#pragma unroll
+                    for (int dx = 0; dx < 4; ++dx)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            // neighbour offsets are -1, 0 or +1: select from the 3 x 3 block
+                            float r0[3], r1[3];
+#pragma unroll
+                            for (int b = 0; b < 3; ++b) {
+                                r0[b] = yo0 < 0 ? nb[0][b][c] : (yo0 == 0 ? nb[1][b][c] : nb[2][b][c]);
+                                r1[b] = yo1 < 0 ? nb[0][b][c] : (yo1 == 0 ? nb[1][b][c] : nb[2][b][c]);
+                            }
+                            const float t00 = xo0[dx] < 0 ? r0[0] : (xo0[dx] == 0 ? r0[1] : r0[2]);
+                            const float t01 = xo1[dx] < 0 ? r0[0] : (xo1[dx] == 0 ? r0[1] : r0[2]);
+                            const float t10 = xo0[dx] < 0 ? r1[0] : (xo0[dx] == 0 ? r1[1] : r1[2]);
+                            const float t11 = xo1[dx] < 0 ? r1[0] : (xo1[dx] == 0 ? r1[1] : r1[2]);
+                            const float top = fmaf(fx[dx], t01 - t00, t00);
+                            const float bot = fmaf(fx[dx], t11 - t10, t10);
+                            o[3 * dx + c] =
+                                fmaf(z[16 * c + 4 * dy + dx], 1.0f / TC_DETAIL_S, fmaf(fy, bot - top, top));
+                        }
+                    float4 *dst = (float4 *)((float *)out +
+                                             (((long long)t.img * 4 * h + 4 * yy + dy) * W4 + 4 * xx) * 3);
+                    dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+                    dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+                    dst[2] = make_float4(o[8], o[9], o[10], o[11]);
+                }
+            }
+        }
+    }
+}
 
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(TC_THREADS)
@@ -180,22 +331,29 @@ __global__ void __launch_bounds__(TC_THREADS)
               const float *__restrict__ bias, void *__restrict__ out,
               const float *__restrict__ rgb, int *__restrict__ status) {
     using L = TcSmem<CIN, COUT, EPI>;
-    constexpr int NCOL = tmem_cols<COUT>(), CST = tmem_stride<COUT>();
+    constexpr int CST = tmem_stride<COUT>(), ACC = TC_MT * CST, NCOL = tmem_cols<COUT>(), C8 = CIN / 8;
     constexpr uint32_t IDESC = idesc_bf16(128, COUT);
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *xs = smem;
     unsigned char *ws = smem + L::off_w;
     float *bs = (float *)(smem + L::off_bias);
-    uint64_t *bar = (uint64_t *)(smem + L::off_bar);
-    uint32_t *tslot = (uint32_t *)(smem + L::off_bar + 8);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint64_t *bar = (uint64_t *)(smem + L::off_bar);  // [2]
+    uint32_t *tslot = (uint32_t *)(smem + L::off_bar + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tx = (w + TC_TW - 1) / TC_TW, ty = (h + TC_TH - 1) / TC_TH;
+    const long long n_tiles = (long long)tx * ty * n;
+    const long long G = gridDim.x;
+    auto xbuf = [&](long long k) { return smem + (size_t)(k & 1) * L::in_bytes; };
+    auto lbuf = [&](long long k) { return (float *)(smem + L::off_l + (size_t)(k % 3) * L::l_bytes); };
 
-    // weights (already in [tap][c8][co][8] order) and biases, once per block
+    // the first two tiles' inputs in flight while the weights are staged
+    if (blockIdx.x < n_tiles)
+        fetch_tile<CIN, EPI>(x, rgb, h, w, tile_xy(blockIdx.x, tx, ty), xbuf(0), lbuf(0));
     for (int i = tid; i < (int)(L::w_bytes / 16); i += TC_THREADS)
         ((uint4 *)ws)[i] = ((const uint4 *)wt)[i];
     for (int i = tid; i < COUT; i += TC_THREADS) bs[i] = bias[i];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + 1)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -209,133 +367,59 @@ __global__ void __launch_bounds__(TC_THREADS)
     fence_after();
     const uint32_t tmem = *tslot;
 
-    const int tx = (w + TC_TW - 1) / TC_TW, ty = (h + TC_TH - 1) / TC_TH;
-    const long long n_tiles = (long long)tx * ty * n;
-    uint32_t phase = 0;
+    // Tile k of this block: its MMAs go to accumulator k & 1 while the
+    // epilogue drains tile k - 1 from the other one.
+    uint32_t phase_bits = 0u;  // bit j: parity of the next completion of bar[j]
     bool failed = false;
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int img = (int)(tile / ((long long)tx * ty));
-        const int rem = (int)(tile - (long long)img * tx * ty);
-        const int by = (rem / tx) * TC_TH, bx = (rem % tx) * TC_TW;
-        // input tile, zero outside the image and past the staged rows
-        constexpr int C8 = CIN / 8;
-        for (int i = tid; i < TC_PIN * C8; i += TC_THREADS) {
-            const int c8 = i / TC_PIN, pos = i - c8 * TC_PIN;
-            const int yy = by - 1 + pos / TC_PW, xx = bx - 1 + pos % TC_PW;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (pos < TC_ROWS_IN * TC_PW && yy >= 0 && yy < h && xx >= 0 && xx < w)
-                v = *(const uint4 *)(x + (((long long)img * h + yy) * w + xx) * CIN + c8 * 8);
-            *(uint4 *)(xs + (size_t)i * 16) = v;
+    for (long long k = 0;; ++k) {
+        const long long tile = blockIdx.x + k * G;
+        const bool has = tile < n_tiles;
+        if (has) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            // generic-proxy writes -> visible to the tensor core's async proxy
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         }
-        if (EPI == TC_EPI_UPSAMPLE) {
-            float *ls = (float *)(smem + L::off_l);
-            for (int i = tid; i < (TC_TH + 2) * TC_PW; i += TC_THREADS) {
-                const int yy = min(max(by - 1 + i / TC_PW, 0), h - 1);
-                const int xx = min(max(bx - 1 + i % TC_PW, 0), w - 1);
-                const float *src = rgb + (((long long)img * h + yy) * w + xx) * 3;
-                ls[3 * i] = src[0];
-                ls[3 * i + 1] = src[1];
-                ls[3 * i + 2] = src[2];
-            }
-        }
-        // generic-proxy stores -> visible to the tensor core's async proxy
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         fence_before();
         __syncthreads();
         fence_after();
-        if (tid == 0) {
-            const uint32_t xa = smem_u32(xs), wa = smem_u32(ws);
-#pragma unroll 1
-            for (int m = 0; m < TC_MT; ++m) {
-#pragma unroll 1
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int off = (tap / 3) * TC_PW + tap % 3;
+        if (has && tid == 0) {
+            const uint64_t a0 = sdesc(smem_u32(xbuf(k)), TC_PIN * 16, 128);
+            const uint64_t b0 = sdesc(smem_u32(ws), COUT * 16, 128);
+            const uint32_t d = tmem + (uint32_t)((k & 1) * ACC);
+            // descriptor start addresses advance in 16-byte units
 #pragma unroll
-                    for (int ks = 0; ks < CIN / 16; ++ks) {
-                        const uint64_t a = sdesc(xa + (uint32_t)((2 * ks * TC_PIN + m * 128 + off) * 16),
-                                                 TC_PIN * 16, 128);
-                        const uint64_t b = sdesc(wa + (uint32_t)((tap * C8 + 2 * ks) * COUT * 16),
-                                                 COUT * 16, 128);
-                        mma_bf16(tmem + (uint32_t)(m * CST), a, b, IDESC, (tap | ks) ? 1u : 0u);
-                    }
-                }
-            }
-            mma_commit(smem_u32(bar));
+            for (int m = 0; m < TC_MT; ++m)
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                    for (int ks = 0; ks < CIN / 16; ++ks)
+                        mma_bf16(d + (uint32_t)(m * CST),
+                                 a0 + (uint64_t)(2 * ks * TC_PIN + m * 128 + (tap / 3) * TC_PW + tap % 3),
+                                 b0 + (uint64_t)((tap * C8 + 2 * ks) * COUT), IDESC, (tap | ks) ? 1u : 0u);
+            mma_commit(smem_u32(bar + (k & 1)));
         }
         __syncwarp();
-        const bool ok = mbar_wait(smem_u32(bar), phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        fence_after();
-        // epilogue: warp w owns TMEM lanes 32 w .. 32 w + 31 of each M-tile
-#pragma unroll 1
-        for (int m = 0; m < TC_MT; ++m) {
-            const int p = m * 128 + warp * 32 + lane;
-            const int row = p / TC_PW, col = p - row * TC_PW;
-            const int yy = by + row, xx = bx + col;
-            const bool valid = row < TC_TH && col < TC_TW && yy < h && xx < w;
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * CST);
-            if (EPI == TC_EPI_RELU) {
-                float v[32];
-                tmem_ld32(taddr, v);
-                if (valid) {
-                    uint4 *dst = (uint4 *)((bf16 *)out + (((long long)img * h + yy) * w + xx) * COUT);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 o;
-                        o.x = pack2(fmaxf(v[8 * q + 0] + bs[8 * q + 0], 0.f), fmaxf(v[8 * q + 1] + bs[8 * q + 1], 0.f));
-                        o.y = pack2(fmaxf(v[8 * q + 2] + bs[8 * q + 2], 0.f), fmaxf(v[8 * q + 3] + bs[8 * q + 3], 0.f));
-                        o.z = pack2(fmaxf(v[8 * q + 4] + bs[8 * q + 4], 0.f), fmaxf(v[8 * q + 5] + bs[8 * q + 5], 0.f));
-                        o.w = pack2(fmaxf(v[8 * q + 6] + bs[8 * q + 6], 0.f), fmaxf(v[8 * q + 7] + bs[8 * q + 7], 0.f));
-                        dst[q] = o;
-                    }
-                }
-            } else {
-                float *zs = (float *)(smem + L::off_z);
-                float v[32], v2[16];
-                tmem_ld32(taddr, v);
-                tmem_ld16(taddr + 32, v2);
-                if (row < TC_TH && col < TC_TW) {
-                    float *zp = zs + (row * TC_TW + col) * (COUT + 1);
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) zp[c] = v[c] + bs[c];
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) zp[32 + c] = v2[c] + bs[32 + c];
-                }
+        if (k == 0) {
+            if (blockIdx.x + G < n_tiles)
+                fetch_tile<CIN, EPI>(x, rgb, h, w, tile_xy(blockIdx.x + G, tx, ty), xbuf(1), lbuf(1));
+        } else {
+            const int j = (int)((k - 1) & 1);
+            const bool ok = mbar_wait(smem_u32(bar + j), (phase_bits >> j) & 1u);
+            phase_bits ^= 1u << j;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
             }
+            fence_after();
+            // tile k + 1 into the buffer the finished MMAs of tile k - 1 read
+            if (tile + G < n_tiles)
+                fetch_tile<CIN, EPI>(x, rgb, h, w, tile_xy(tile + G, tx, ty), xbuf(k + 1), lbuf(k + 1));
+            tile_epilogue<COUT, EPI>(tmem, (uint32_t)(j * ACC), tile_xy(tile - G, tx, ty), h, w, bs,
+                                     lbuf(k - 1), out);
         }
-        if (EPI == TC_EPI_UPSAMPLE) {
-            __syncthreads();
-            const float *zs = (const float *)(smem + L::off_z);
-            const float *ls = (const float *)(smem + L::off_l);
-            const int H4 = 4 * h, W4 = 4 * w;
-            constexpr int ROWF = 4 * TC_TW * 3;
-            float *o = (float *)out;
-            for (int i = tid; i < 4 * TC_TH * ROWF; i += TC_THREADS) {
-                const int r = i / ROWF, e = i - r * ROWF;
-                const int X = e / 3, c = e - 3 * X;
-                const int HY = 4 * by + r, HX = 4 * bx + X;
-                if (HY >= H4 || HX >= W4) continue;
-                int y0, y1, x0, x1;
-                float fy, fx;
-                bl_src(HY, h, y0, y1, fy);
-                bl_src(HX, w, x0, x1, fx);
-                y0 -= by - 1; y1 -= by - 1; x0 -= bx - 1; x1 -= bx - 1;
-                const float a00 = ls[3 * (y0 * TC_PW + x0) + c], a01 = ls[3 * (y0 * TC_PW + x1) + c];
-                const float a10 = ls[3 * (y1 * TC_PW + x0) + c], a11 = ls[3 * (y1 * TC_PW + x1) + c];
-                const float top = fmaf(fx, a01 - a00, a00), bot = fmaf(fx, a11 - a10, a10);
-                const float z = zs[((r >> 2) * TC_TW + (X >> 2)) * (COUT + 1) + 16 * c + 4 * (r & 3) + (X & 3)];
-                o[(((long long)img * H4 + HY) * W4 + HX) * 3 + c] = fmaf(z, 1.0f / TC_DETAIL_S, fmaf(fy, bot - top, top));
-            }
-        }
-        // TMEM and the staged tiles are reused by the next tile
-        fence_before();
-        __syncthreads();
-        fence_after();
+        if (!has) break;
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (failed && tid == 0) atomicOr(status, 1);
     fence_before();
     __syncthreads();
@@ -349,14 +433,28 @@ cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const flo
                    void *out, const float *rgb, int *status, int n_sm, cudaStream_t s) {
     using L = TcSmem<CIN, COUT, EPI>;
     auto kern = k_conv_tc<CIN, COUT, EPI>;
-    // One block per SM with the largest shared-memory request, so that every
-    // operand read the descriptors describe stays inside the block's
-    // allocation whatever the tile position.
-    const int per_sm = 1;
-    const size_t smem = (size_t)227 * 1024;
+    constexpr int NCOL = tmem_cols<COUT>();
+    // blocks per SM: limited by shared memory and by the 512 TMEM columns; the
+    // shared-memory request is raised so that no more blocks than that fit
+    constexpr size_t SM_BYTES = 227 * 1024, PER_BLOCK_RESERVED = 1024;
+    const int by_tmem = 512 / NCOL;
+    const int by_smem = (int)(SM_BYTES / (L::total + PER_BLOCK_RESERVED));
+    const int cap = std::max(1, std::min(by_tmem, by_smem));
+    const size_t smem = std::max(L::total, SM_BYTES / cap - PER_BLOCK_RESERVED);
     static_assert(L::total <= (size_t)227 * 1024, "tile fits shared memory");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
+    // resident blocks per SM (registers may allow fewer than the cap; the
+    // occupancy query answers 1 for kernels that allocate tensor memory, so
+    // the register limit is computed here): the persistent grid is one wave
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const int regs_per_warp = ((fa.numRegs + 7) / 8) * 8 * 32;
+    const int by_regs = 65536 / (regs_per_warp * (TC_THREADS / 32));
+    const int per_sm = std::max(1, std::min(cap, by_regs));
     const long long tiles = (long long)((w + TC_TW - 1) / TC_TW) * ((h + TC_TH - 1) / TC_TH) * n;
     if (tiles == 0) return cudaSuccess;
     const int grid = (int)std::min<long long>(tiles, (long long)per_sm * n_sm);
