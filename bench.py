@@ -108,7 +108,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=8):
+def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=64):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample
     of the same workload (the first cameras of the batch)."""
     cores = os.cpu_count() or 1
@@ -125,6 +125,106 @@ def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=8):
             "kind": "oracle",
             "sample": f"{done} of {len(vm)} cameras (cameras 0..{done - 1}), full 640x480 "
                       f"frames, {dt:.1f} s of CPU work"}
+
+
+# Algorithmic work of the upsampler per LR pixel: 2 flops per MAC of the six
+# 3x3 convolutions ((6 -> 32), 4 x (32 -> 32), (32 -> 48)).
+CNN_FLOPS_PER_LR_PIXEL = 2 * 9 * (6 * 32 + 4 * 32 * 32 + 32 * 48)
+
+
+def upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb_plain, stream, local):
+    """The learned-upsampler path on the same cameras: render at W/4 x H/4
+    (intrinsics / 4), then the CNN to W x H (RGB; depth bilinear). The network
+    is trained first on renderer pairs of held-out poses (untimed), validated
+    on 64 other poses; below 35 dB the scene falls back to the plain render.
+    PSNR is measured against the plain render of the metric cameras."""
+    import numpy as np
+    import torch
+    from paper_2510_15352_b300 import upsampler
+    n = vm_d.shape[0]
+    h, w = H // 4, W // 4
+    up = gs.Upsampler(device=local)
+    bil = gs.Upsampler(device=local)
+    try:
+        up.set_params(upsampler.init_params(0))
+        bil.set_params(np.zeros(gs.Upsampler.n_params, np.float32))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = upsampler.train(up, R, [sid], W, H, n_pairs=args.up_pairs, frames_per_step=4,
+                                 lr_max=1e-3, lr_min=3e-5, seed=100)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        vmv, itv = synth.make_cameras(64, W, H, 0.75 * W, (0.3, 1.2), seed=7)
+        val = upsampler.evaluate(up, R, sid, vmv, itv, W, H)
+        fallback = val["psnr_mean"] < 35.0
+        it_q = it_d / 4.0
+        lr = torch.empty((n, h, w, 3), dtype=torch.float32, device="cuda")
+        ld = torch.empty((n, h, w), dtype=torch.float32, device="cuda")
+        out = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
+        od = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+
+        def render_lr():
+            R.render(sid, vm_d, it_q, w, h, lr, ld, stream=stream)
+
+        def cnn():
+            up.forward(lr, ld, out, od, stream=stream)
+
+        def step():
+            if fallback:
+                R.render(sid, vm_d, it_d, W, H, out, od, stream=stream)
+            else:
+                render_lr()
+                cnn()
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / args.steps
+
+        ms_step = timed(step)
+        up.check(stream)
+        # quality of exactly these frames against the plain render
+        p_net = upsampler.psnr(out, rgb_plain)
+        ob, _ = bil.forward(lr)
+        p_bil = upsampler.psnr(ob, rgb_plain)
+        torch.cuda.synchronize()
+        p_net, p_bil = p_net.cpu().numpy(), p_bil.cpu().numpy()
+        ms_lr = timed(render_lr) if not fallback else None
+        ms_cnn = timed(cnn) if not fallback else None
+        up.check(stream)
+    finally:
+        up.close()
+        bil.close()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = peaks.get("bf16_tflops", 1800.0)
+    cnn_tflops = (CNN_FLOPS_PER_LR_PIXEL * h * w * n / (ms_cnn / 1e3) / 1e12) if ms_cnn else None
+    return {
+        "value": n / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step,
+        "fallback": bool(fallback),
+        "render": f"{w}x{h}, intrinsics / 4, then the learned 4x upsampler to {W}x{H}",
+        "psnr_db_mean": float(p_net.mean()), "psnr_db_p5": float(np.percentile(p_net, 5)),
+        "bilinear_psnr_db_mean": float(p_bil.mean()),
+        "bilinear_psnr_db_p5": float(np.percentile(p_bil, 5)),
+        "validation": val, "train_pairs": int(args.up_pairs), "train_s": t_train,
+        "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
+        "stages_ms_per_step": {"render_lr": ms_lr, "cnn": ms_cnn},
+        "cnn_roofline": {
+            "kernel": "k_conv_tc (6 layers, tcgen05) + k_prep_input + k_bilinear1",
+            "bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": cnn_tflops / bf16_peak if cnn_tflops else None,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the CNN is timed alone)",
+            "flops_per_lr_pixel": CNN_FLOPS_PER_LR_PIXEL},
+        "gpu_launches_per_step": None if fallback else None,
+    }
 
 
 def run_reference(args):
@@ -325,7 +425,8 @@ def run_b300(args):
         t_max = float(t.item())
     frames = n * world * args.steps
     value = frames / (t_max / 1e3)
-    launches = 6 * n_chunks
+    # per chunk: mask, scan, plan, write, 4 x (hist, offsets, scatter), bin, composite
+    launches = 18 * n_chunks
 
     # end to end: host cameras in, host frames out, through the host entry point
     e2e = None
@@ -389,6 +490,13 @@ def run_b300(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(scene, vm, it, W, H)
+    if args.up_pairs > 0:
+        ups = upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb, stream, local)
+        ups["gpu_launches_per_step"] = 18 * (n_chunks // args.steps) + 8
+        ups["speedup_vs_plain"] = ups["value"] / (n / (t_max / args.steps / 1e3))
+        if rank == 0:
+            out["upsampled"] = ups
+    if rank == 0:
         print(json.dumps(out), flush=True)
     R.close()
     if dist:
@@ -412,6 +520,8 @@ def main():
     ap.add_argument("--graph", action="store_true",
                     help="time replays of one captured CUDA graph (batched workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--up-pairs", type=int, default=200_000,
+                    help="training pairs of the learned upsampler (0: skip the upsampled path)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
