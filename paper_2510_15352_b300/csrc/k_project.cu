@@ -426,12 +426,25 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
         }
     }
     {
-        // SH rows: one coalesced segment of WG values per (coefficient, channel)
+        // SH rows: one coalesced segment of WG values per (coefficient, channel);
+        // eight loads in flight per thread before the shared-memory stores
         const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
-        for (int i = tid; i < K3 * WG; i += PROJ_THREADS) {
-            const int k = i / WG, j = i - k * WG;
-            const long long g = g0 + j;
-            shs[i] = g < gr.n ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype) : 0.0f;
+        constexpr int BATCH = 8;
+        for (int i0 = tid; i0 < K3 * WG; i0 += BATCH * PROJ_THREADS) {
+            float v[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                const int i = i0 + u * PROJ_THREADS;
+                const int k = i / WG, j = i - k * WG;
+                const long long g = g0 + j;
+                v[u] = (i < K3 * WG && g < gr.n) ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype)
+                                                 : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                const int i = i0 + u * PROJ_THREADS;
+                if (i < K3 * WG) shs[i] = v[u];
+            }
         }
     }
     __syncthreads();

@@ -14,8 +14,10 @@
 //   k_sort_hist    -- digit histogram of every tile;
 //   k_sort_offsets -- per segment: where each (tile, digit) run starts
 //                     (digits in order, tiles in order within a digit);
-//   k_sort_scatter -- stable rank of each key among equal digits of its tile,
-//                     written at segment start + run start + rank.
+//   k_sort_scatter -- stable rank of each key among equal digits of its tile;
+//                     the tile is put in sorted order in shared memory, then
+//                     written out run by run (coalesced) at segment start +
+//                     run start + rank.
 // Stable rank inside a tile: warp w takes keys [256 w, 256 w + 256) in rounds
 // of 32; a key's rank is (equal digits in earlier warps) + (equal digits in
 // earlier rounds of its warp) + (equal digits in lower lanes of its round,
@@ -117,14 +119,19 @@ __global__ void __launch_bounds__(ST)
                    const int *__restrict__ tile_start, int n_seg, int shift,
                    const uint32_t *__restrict__ offs, const int *__restrict__ nt_dev, int nt_host) {
     __shared__ uint32_t wcnt[SNW][256];
-    __shared__ uint32_t toff[256];
+    __shared__ uint32_t toff[256];   // where the tile's run of each digit starts in the segment
+    __shared__ uint32_t tdig[256];   // where each digit starts in the tile's sorted order
+    __shared__ uint32_t dsum[SNW];
+    __shared__ uint32_t skey[TK], sval[TK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = nt_dev ? *nt_dev : nt_host;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
     const int s = find_seg(tile_start, n_seg, tile);
     const long long base = seg_start[s];
-    const long long i0 = (long long)(tile - tile_start[s]) * TK + (long long)warp * (32 * SIPT);
+    const long long t0 = (long long)(tile - tile_start[s]) * TK;
+    const long long i0 = t0 + (long long)warp * (32 * SIPT);
     const long long n = seg_count[s];
+    const int nk = (int)min((long long)TK, n - t0);  // keys in this tile
     toff[tid] = offs[(long long)tile * 256 + tid];
 #pragma unroll
     for (int j = 0; j < 8; ++j) wcnt[warp][lane * 8 + j] = 0;
@@ -154,26 +161,51 @@ __global__ void __launch_bounds__(ST)
         __syncwarp();
     }
     __syncthreads();
-    {
-        uint32_t run = 0;
+    // per digit (thread tid owns digit tid): exclusive prefix over warps, and
+    // the digit's total for the tile
+    uint32_t run = 0;
 #pragma unroll
-        for (int w = 0; w < SNW; ++w) {
-            const uint32_t c = wcnt[w][tid];
-            wcnt[w][tid] = run;
-            run += c;
-        }
+    for (int w = 0; w < SNW; ++w) {
+        const uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = run;
+        run += c;
     }
+    // exclusive prefix of the digit totals over digits: where each digit's
+    // keys start in the tile's sorted order
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) dsum[warp] = incl;
     __syncthreads();
+    uint32_t before = 0;
+#pragma unroll
+    for (int w = 0; w < SNW; ++w) before += w < warp ? dsum[w] : 0u;
+    tdig[tid] = before + incl - run;
+    __syncthreads();
+    // the tile in sorted order in shared memory ...
 #pragma unroll
     for (int r = 0; r < SIPT; ++r) {
         if (i0 + r * 32 + lane < n) {
             const uint32_t d = (kr[r] >> shift) & 255u;
-            const long long pos = base + toff[d] + wcnt[warp][d] + rk[r];
-            dk[pos] = kr[r];
-            dv[pos] = vr[r];
+            const uint32_t pos = tdig[d] + wcnt[warp][d] + rk[r];
+            skey[pos] = kr[r];
+            sval[pos] = vr[r];
         }
     }
-    __syncthreads();  // toff / wcnt are rebuilt for the next tile of this block
+    __syncthreads();
+    // ... then written out in that order: consecutive threads write
+    // consecutive addresses within each digit's run
+    for (int p = tid; p < nk; p += ST) {
+        const uint32_t key = skey[p];
+        const uint32_t d = (key >> shift) & 255u;
+        const long long at = base + toff[d] + (p - tdig[d]);
+        dk[at] = key;
+        dv[at] = sval[p];
+    }
+    __syncthreads();  // shared arrays are rebuilt for the next tile of this block
     }
 }
 
