@@ -240,20 +240,24 @@ __global__ void __launch_bounds__(256 / PPT)
                     const float4 g2 = s2[j];  // red, green, blue
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
+                        // alpha is 0 for a pair that fails the test (and for a
+                        // stopped pixel, whose threshold is +inf); then
+                        // T - alpha T >= T_min holds (T >= T_min for every pixel),
+                        // so "keep" is false exactly when a passing pair would
+                        // take T below T_min: that pair is not added and the
+                        // pixel stops
                         const bool pass = p[k] >= thr[k];
                         if (STATS) al += pass ? 1u : 0u;
-                        const float alpha = fminf(P.alpha_max, ex2_approx(p[k]));
+                        const float alpha = pass ? fminf(P.alpha_max, ex2_approx(p[k])) : 0.0f;
                         const float wgt = alpha * T[k];
-                        const float Tn = T[k] - wgt;
-                        const bool acc = pass && Tn >= P.T_min;
-                        const bool stop = pass && !(Tn >= P.T_min);
-                        const float wa = acc ? wgt : 0.0f;
+                        const bool keep = T[k] - wgt >= P.T_min;
+                        const float wa = keep ? wgt : 0.0f;
                         cr[k] = fmaf(wa, g2.x, cr[k]);
                         cg[k] = fmaf(wa, g2.y, cg[k]);
                         cb[k] = fmaf(wa, g2.z, cb[k]);
                         cd[k] = fmaf(wa, g1.z, cd[k]);
-                        T[k] = acc ? Tn : T[k];
-                        thr[k] = stop ? INF : thr[k];
+                        T[k] -= wa;
+                        thr[k] = keep ? thr[k] : INF;
                     }
                 }
             }
