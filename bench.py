@@ -278,14 +278,14 @@ def run_b300_batched(args):
     rgb = torch.empty((P, 3), dtype=torch.float32, device="cuda")
     depth = torch.empty((P,), dtype=torch.float32, device="cuda")
     counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk,
-                          pixels_per_thread=args.ppt)
+                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
     ids_c = np.array([counter.add_scene(s) for s in scenes], dtype=np.int32)[which]
     counter.render_v(ids_c, vm_d, it_d, Ws, Hs, rgb, depth)
     torch.cuda.synchronize()
     cst = counter.stats()
     counter.close()
     R = gs.Renderer(device=local, time_stages=0 if args.graph else 1,
-                    max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt)
+                    max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
     ids = np.array([R.add_scene(s) for s in scenes], dtype=np.int32)[which]
     stream = torch.cuda.current_stream()
     graph = R.graph(ids, vm_d, it_d, Ws, Hs, rgb, depth) if args.graph else None
@@ -320,7 +320,7 @@ def run_b300_batched(args):
         # stage times from one eager render of the same batch (events inside a
         # graph replay are not read back)
         R2 = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
-                         pixels_per_thread=args.ppt)
+                         pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
         ids2 = np.array([R2.add_scene(s) for s in scenes], dtype=np.int32)[which]
         for _ in range(2):
             R2.render_v(ids2, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
@@ -339,7 +339,8 @@ def run_b300_batched(args):
                    "scenes": len(scenes), "gaussians": int(sum(s["mean"].shape[1] for s in scenes)),
                    "cameras_640x480": int((Ws == 640).sum()), "cameras_320x240": int((Ws == 320).sum()),
                    "frames_640x480_equivalent": eq_frames, "chunk_cameras": args.chunk,
-                   "pixels_per_thread": args.ppt, "storage": args.precision,
+                   "pixels_per_thread": args.ppt, "tiles_per_block": args.tpb,
+                       "storage": args.precision,
                    "cuda_graph": bool(args.graph)},
         "roofline": {"kernel": "k_composite", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -374,7 +375,7 @@ def run_b300(args):
 
     # algorithmic work of the compositing kernel on these inputs (counting run)
     counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk,
-                          pixels_per_thread=args.ppt)
+                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
     sid_c = counter.add_scene(scene)
     counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
     torch.cuda.synchronize()
@@ -385,7 +386,7 @@ def run_b300(args):
     flops_contrib = F_CONTRIB_ONLY * cst["pairs_alpha"]
 
     R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
-                    pixels_per_thread=args.ppt)
+                    pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
     sid = R.add_scene(scene)
     stream = torch.cuda.current_stream()
 
@@ -460,7 +461,8 @@ def run_b300(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cameras_per_gpu": n, "width": W, "height": H,
                        "gaussians": 1_000_000, "sh_degree": 3, "chunk_cameras": args.chunk,
-                       "pixels_per_thread": args.ppt, "storage": args.precision,
+                       "pixels_per_thread": args.ppt, "tiles_per_block": args.tpb,
+                       "storage": args.precision,
                        "l2": "inputs larger than L2 (scene 236 MB; 5 GB of outputs per step)"},
             "roofline": {
                 "kernel": "k_composite", "bound": "alu", "achieved": achieved,
@@ -514,6 +516,8 @@ def main():
                     choices=[WORKLOAD, "batched_32scene_4096cam_mixed"])
     ap.add_argument("--chunk", type=int, default=256, help="cameras per internal chunk")
     ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
+    ap.add_argument("--tpb", type=int, default=1,
+                    help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
     ap.add_argument("--precision", choices=["f32", "half"], default="f32",
                     help="scene attribute storage (half: FP16 geometry, BF16 appearance)")
     ap.add_argument("--e2e-steps", type=int, default=2)

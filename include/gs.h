@@ -69,7 +69,10 @@ typedef struct gs_config {
     int32_t time_stages;   /* 1: record CUDA events around every stage on the render
                               stream; gs_get_stats reports the per-stage device time */
     int32_t pixels_per_thread; /* compositing layout: 2, 4 or 8 pixels per thread (8) */
-    int32_t reserved0;
+    int32_t tiles_per_block;   /* compositing blocks: 1 = one block per 16x16 tile, 4 = one
+                                  block per 2x2 quad of tiles sharing the list scan and the
+                                  record staging (1; quads only with 8 pixels per thread,
+                                  other layouts use one tile per block) */
     int64_t workspace_survivors; /* surviving (camera, Gaussian) pairs per chunk the
                                     workspace starts with (0: a third of the Gaussians a
                                     chunk sees); it grows when a render needs more */

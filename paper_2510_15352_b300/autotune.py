@@ -5,6 +5,8 @@ stream, after a warm-up render) over:
   pixels_per_thread   2, 4 or 8 -- the compositing layout: each warp of a tile
                       block covers 4x16, 8x16 or 16x16 pixels (the shape of the
                       pixel region over which Gaussians are culled and blended);
+  tiles_per_block     1 or 4 -- with 8 pixels per thread, one tile per block or a
+                      2x2 quad of tiles sharing the list scan and record staging;
   camera_group        cameras of one scene that share one Gaussian load in the
                       projection kernels (Gaussian batch per projection block);
   max_chunk_cameras   cameras per chunk of the render pipeline,
@@ -23,6 +25,7 @@ import numpy as np
 
 DEFAULT_SPACE = {
     "pixels_per_thread": (2, 4, 8),
+    "tiles_per_block": (1, 4),
     "camera_group": (16, 32),
     "max_chunk_cameras": (128, 256, 512),
 }
@@ -63,10 +66,15 @@ def store_cache(entry_key: str, entry: dict, path: str = DEFAULT_CACHE) -> None:
 
 
 def candidates(space: dict | None = None):
+    """Every combination of the space, except quads with fewer than 8 pixels per
+    thread (the library runs those as one tile per block: a duplicate)."""
     space = space or DEFAULT_SPACE
     keys = sorted(space)
     for vals in itertools.product(*(space[k] for k in keys)):
-        yield dict(zip(keys, vals))
+        c = dict(zip(keys, vals))
+        if c.get("tiles_per_block", 1) == 4 and c.get("pixels_per_thread", 8) != 8:
+            continue
+        yield c
 
 
 def tune(scenes, scene_of_camera, viewmats, intrinsics, widths, heights, device: int = 0,

@@ -170,7 +170,7 @@ struct ChunkPlan {
     int c0, m;            // first camera (in scene order) and cameras of the chunk
     int g0, n_groups;     // groups of the chunk in the group table
     int max_bx;           // projection blocks (x) for the largest scene of the chunk
-    int tiles_total;      // 16x16 tiles of the chunk
+    int tiles_total;      // compositing blocks of the chunk (tiles or 2x2 quads)
     int max_sup;          // largest super-tile count of a camera of the chunk
     long long mask_words; // survival-mask words of the chunk
     long long n_gauss;    // sum over cameras of their scene sizes
@@ -219,7 +219,9 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
             ci.pix_off = a.cam_pix(user);
             ci.tile_off = ch.tiles_total;
             P.tilepre[tp + s] = ch.tiles_total;
-            ch.tiles_total += ci.TX * ci.TY;
+            // compositing blocks of this camera: tiles, or 2 x 2 quads of tiles
+            ch.tiles_total += cfg.tiles_per_block == 4 ? ((ci.TX + 1) / 2) * ((ci.TY + 1) / 2)
+                                                       : ci.TX * ci.TY;
             ch.max_sup = std::max(ch.max_sup,
                                   ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE));
             ci.mask_off = ch.mask_words;
@@ -345,7 +347,8 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(launch_composite(cams, tilepre, ch.m, ch.tiles_total, (const SlotRec *)ctx->rec.p,
                              (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->rrect.p,
                              (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
-                             cfg.count_pairs != 0, cfg.pixels_per_thread, status, st));
+                             cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,
+                             status, st));
         if (E) CKC(cudaEventRecord(E[4], st));
     }
     return GS_OK;
@@ -472,6 +475,7 @@ gs_status gs_config_default(gs_config *out) {
     out->count_pairs = 0;
     out->time_stages = 0;
     out->pixels_per_thread = 8;
+    out->tiles_per_block = 1;
     return GS_OK;
 }
 
@@ -487,8 +491,10 @@ gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **o
         !(c.alpha_min > 0.0f) || !(c.alpha_max > 0.0f && c.alpha_max < 1.0f) ||
         !(c.T_min > 0.0f && c.T_min < 1.0f) || c.max_chunk_cameras < 1 || c.camera_group < 1 ||
         c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) || c.workspace_survivors < 0 ||
-        (c.pixels_per_thread != 2 && c.pixels_per_thread != 4 && c.pixels_per_thread != 8))
+        (c.pixels_per_thread != 2 && c.pixels_per_thread != 4 && c.pixels_per_thread != 8) ||
+        (c.tiles_per_block != 1 && c.tiles_per_block != 4))
         return GS_ERR_INVALID_ARG;
+    if (c.pixels_per_thread != 8) c.tiles_per_block = 1;  // quads use 8 pixels per thread
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return GS_ERR_INVALID_ARG;

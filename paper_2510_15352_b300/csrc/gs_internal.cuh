@@ -127,12 +127,15 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, 
                        int n_super, const uint2 *srect, const uint32_t *vals, uint2 *rrect,
                        uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);
 
-// pixels_per_thread: 2, 4 or 8 (blocks of 128, 64 or 32 threads)
+// tiles_per_block 1: one block per tile, pixels_per_thread 2, 4 or 8 (blocks of
+// 128, 64 or 32 threads); tiles_per_block 4: one block of 4 warps per 2 x 2 quad
+// of tiles (8 pixels per thread). tile_prefix / n_tiles count the blocks: tiles
+// or quads per camera.
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
                              int n_tiles, const SlotRec *rec, const uint32_t *vals,
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
-                             const int *status, cudaStream_t s);
+                             int tiles_per_block, const int *status, cudaStream_t s);
 
 }  // namespace gsk

@@ -307,6 +307,250 @@ finished:
     }
 }
 
+// The same compositing with a 2 x 2 quad of tiles per block: warp w owns tile
+// (2 qx + (w & 1), 2 qy + (w >> 1)) with 8 pixels per thread (16 rows x 2
+// threads, pixels x0, x0 + 2, ...). The quad lies inside one super-tile, so
+// the four warps share one scan of its bitmap row, one rect filter (the rect
+// meets the quad) and one staging of every record: per record, bits 4-7 mark
+// the warps whose tile lies in the record's rect (the record is in that
+// tile's list) and bits 0-3 those of them some pixel of which can reach
+// alpha >= alpha_min (the box test and the exact maximum of the quadratic over
+// the tile's pixel-centre rectangle, with the float32 margin).
+// A warp blends only the records whose bit it has, so each tile still sees
+// exactly its own list, in order.
+template <bool STATS>
+__global__ void __launch_bounds__(128)
+    k_composite_quad(const CamInfo *__restrict__ cams, const int *__restrict__ quad_prefix,
+                     int n_slots, const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
+                     const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
+                     CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
+                     float *__restrict__ finalT, unsigned long long *__restrict__ stats,
+                     const int *__restrict__ status) {
+    if (status && *status) return;  // the chunk did not fit the workspace: nothing written
+    constexpr int PPT = 8, NT = 128, CPR = 2, NWARP = 4;
+    __shared__ float4 s0[COMP_BATCH], s1[COMP_BATCH], s2[COMP_BATCH];
+    __shared__ uint32_t cand[NT * 32];
+    __shared__ uint32_t wsum[NWARP];
+
+    int lo = 0, hi = n_slots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (quad_prefix[mid] <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const CamInfo ci = cams[lo];
+    const int QX = (ci.TX + 1) >> 1;
+    const int qi = (int)blockIdx.x - quad_prefix[lo];
+    const int qx = qi % QX, qy = qi / QX;
+    const int SX = (ci.TX + STILE - 1) / STILE;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = 2 * qx + (warp & 1), ty = 2 * qy + (warp >> 1);  // this warp's tile
+    const int y = ty * TILE + (lane >> 1);
+    const float py = y + 0.5f;
+    const float INF = __int_as_float(0x7f800000);
+    float T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT], thr[PPT];
+    const int x0 = tx * TILE + (lane & 1);
+    const float px0 = x0 + 0.5f;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        thr[k] = (x0 + k * CPR < ci.W && y < ci.H) ? P.log2_alpha_min : INF;
+        T[k] = 1.0f;
+        cr[k] = cg[k] = cb[k] = cd[k] = 0.0f;
+    }
+    const uint32_t warp_bit = 1u << warp;
+    unsigned long long ev = 0, al = 0, wi = 0, wbox = 0, wbl = 0;
+
+    const uint32_t *bm = bitmap + ci.bm_off + (long long)((2 * qy / STILE) * SX + 2 * qx / STILE) * ci.nw;
+    const SlotRec *recs = rec + ci.seg_off;
+    const uint32_t *cv = vals + ci.seg_off;
+    const uint2 *crr = rrect + ci.seg_off;
+    const int qx0 = 2 * qx, qx1 = 2 * qx + 1, qy0 = 2 * qy, qy1 = 2 * qy + 1;
+    for (int wb = 0; wb < ci.nw; wb += NT) {
+        bool live = false;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
+        if (!__syncthreads_or(live)) break;
+        // 1. candidates: set bits of NT words of the super-tile row, in rank order
+        const int w = wb + tid;
+        uint32_t word = w < ci.nw ? bm[w] : 0u;
+        uint32_t c = __popc(word);
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < NWARP; ++k) {
+            const uint32_t v = wsum[k];
+            before += k < warp ? v : 0u;
+            total += v;
+        }
+        uint32_t pos = before + incl - c;
+        while (word) {
+            const int bit = __ffs(word) - 1;
+            cand[pos++] = (uint32_t)w * 32u + (uint32_t)bit;
+            word &= word - 1u;
+        }
+        __syncthreads();
+        // 2. keep the candidates whose rect meets the quad (order preserved)
+        uint32_t nkept = 0;
+        for (uint32_t q0 = 0; q0 < total; q0 += NT) {
+            const uint32_t q = q0 + tid;
+            bool keep = false;
+            uint32_t rk = 0;
+            if (q < total) {
+                rk = cand[q];
+                const uint2 rr = crr[rk];
+                keep = qx1 >= (int)(rr.x & 0xffffu) && qx0 <= (int)(rr.x >> 16) &&
+                       qy1 >= (int)(rr.y & 0xffffu) && qy0 <= (int)(rr.y >> 16);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) wsum[warp] = __popc(bal);
+            __syncthreads();
+            uint32_t wbefore = 0, wtotal = 0;
+#pragma unroll
+            for (int k = 0; k < NWARP; ++k) {
+                const uint32_t v = wsum[k];
+                wbefore += k < warp ? v : 0u;
+                wtotal += v;
+            }
+            if (keep) cand[nkept + wbefore + __popc(bal & ((1u << lane) - 1u))] = rk;
+            nkept += wtotal;
+            __syncthreads();
+        }
+        // 3. composite the kept records, COMP_BATCH at a time
+        for (uint32_t j0 = 0; j0 < nkept; j0 += COMP_BATCH) {
+            const int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
+            for (int q = tid; q < nb; q += NT) {
+                const SlotRec &R = recs[cv[cand[j0 + q]]];
+                const float4 a = R.a, b = R.b, cc = R.c;
+                const uint4 d = R.d;
+                const int rx0 = (int)(d.x & 0xffffu), rx1 = (int)(d.x >> 16);
+                const int ry0 = (int)(d.y & 0xffffu), ry1 = (int)(d.y >> 16);
+                uint32_t m = 0;
+#pragma unroll
+                for (int k = 0; k < NWARP; ++k) {
+                    const int ktx = 2 * qx + (k & 1), kty = 2 * qy + (k >> 1);
+                    if (ktx < rx0 || ktx > rx1 || kty < ry0 || kty > ry1) continue;
+                    m |= 16u << k;  // in this warp's tile list
+                    const float X0 = ktx * TILE + 0.5f, X1 = ktx * TILE + TILE - 0.5f;
+                    const float Y0 = kty * TILE + 0.5f, Y1 = kty * TILE + TILE - 0.5f;
+                    if (!(a.x + a.z >= X0 && a.x - a.z <= X1 && a.y + a.w >= Y0 && a.y - a.w <= Y1))
+                        continue;
+                    const float DX = fmaxf(fabsf(X0 - a.x), fabsf(X1 - a.x));
+                    const float DY = fmaxf(fabsf(Y0 - a.y), fabsf(Y1 - a.y));
+                    const float terms =
+                        fmaf(fabsf(b.x), DX * DX, fmaf(fabsf(b.y), DX * DY, fabsf(b.z) * DY * DY));
+                    const float margin = fmaf(1e-6f, terms, 1e-3f);
+                    if (max_p_rect(a.x, a.y, b.x, b.y, b.z, b.w, X0, X1, Y0, Y1) >=
+                        P.log2_alpha_min - margin)
+                        m |= 1u << k;
+                }
+                s0[q] = make_float4(a.x, a.y, b.x, b.y);
+                s1[q] = make_float4(b.z, b.w, cc.w, __uint_as_float(m));
+                s2[q] = cc;
+            }
+            __syncthreads();
+            live = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
+            if (__any_sync(0xffffffffu, live)) {
+                for (int j = 0; j < nb; ++j) {
+                    const float4 g1 = s1[j];  // c', log2 o, z, warp masks
+                    // pairs of this tile's list only (bit 4 + warp: the record's
+                    // rect holds the warp's tile)
+                    if (STATS && (__float_as_uint(g1.w) & (16u << warp))) {
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) ev += thr[k] != INF ? 1u : 0u;
+                    }
+                    if (STATS) wi++;
+                    if (!(__float_as_uint(g1.w) & warp_bit)) continue;  // warp-uniform
+                    if (STATS) wbox++;
+                    const float4 g0 = s0[j];  // u, v, a', b'
+                    const float dy = py - g0.y;
+                    const float base = fmaf(g1.x * dy, dy, g1.y);
+                    const float bdy = g0.w * dy;
+                    float p[PPT];
+                    bool any = false;
+                    const float dx0 = px0 - g0.x;
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const float dx = dx0 + (float)(k * CPR);
+                        p[k] = fmaf(fmaf(g0.z, dx, bdy), dx, base);
+                        any = any || p[k] >= thr[k];
+                    }
+                    if (!__any_sync(0xffffffffu, any)) continue;
+                    if (STATS) wbl++;
+                    const float4 g2 = s2[j];  // red, green, blue
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const bool pass = p[k] >= thr[k];
+                        if (STATS) al += pass ? 1u : 0u;
+                        const float alpha = pass ? fminf(P.alpha_max, ex2_approx(p[k])) : 0.0f;
+                        const float wgt = alpha * T[k];
+                        const bool keep = T[k] - wgt >= P.T_min;
+                        const float wa = keep ? wgt : 0.0f;
+                        cr[k] = fmaf(wa, g2.x, cr[k]);
+                        cg[k] = fmaf(wa, g2.y, cg[k]);
+                        cb[k] = fmaf(wa, g2.z, cb[k]);
+                        cd[k] = fmaf(wa, g1.z, cd[k]);
+                        T[k] -= wa;
+                        thr[k] = keep ? thr[k] : INF;
+                    }
+                }
+            }
+            live = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
+            if (!__syncthreads_or(live)) goto finished;
+        }
+    }
+finished:
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int x = x0 + k * CPR;
+        if (x >= ci.W || y >= ci.H) continue;
+        const long long pix = ci.pix_off + (long long)y * ci.W + x;
+        float o[5] = {fmaf(T[k], P.bg[0], cr[k]), fmaf(T[k], P.bg[1], cg[k]),
+                      fmaf(T[k], P.bg[2], cb[k]), cd[k], T[k]};
+        if (P.accumulate) {  // one sub-frame of a blended image (motion blur)
+            o[0] = fmaf(P.out_w, o[0], rgb[3 * pix + 0]);
+            o[1] = fmaf(P.out_w, o[1], rgb[3 * pix + 1]);
+            o[2] = fmaf(P.out_w, o[2], rgb[3 * pix + 2]);
+            o[3] = fmaf(P.out_w, o[3], depth[pix]);
+            if (finalT) o[4] = fmaf(P.out_w, o[4], finalT[pix]);
+        } else if (P.out_w != 1.0f) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) o[q] *= P.out_w;
+        }
+        rgb[3 * pix + 0] = o[0];
+        rgb[3 * pix + 1] = o[1];
+        rgb[3 * pix + 2] = o[2];
+        depth[pix] = o[3];
+        if (finalT) finalT[pix] = o[4];
+    }
+    if (STATS) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            ev += __shfl_down_sync(0xffffffffu, ev, d);
+            al += __shfl_down_sync(0xffffffffu, al, d);
+        }
+        if (lane == 0) {
+            atomicAdd(&stats[0], ev);
+            atomicAdd(&stats[1], al);
+            atomicAdd(&stats[3], wi);
+            atomicAdd(&stats[4], wbox);
+            atomicAdd(&stats[5], wbl);
+        }
+    }
+}
+
 template <int PPT>
 cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots, int n_tiles,
                        const SlotRec *rec, const uint32_t *vals, const uint2 *rrect,
@@ -331,8 +575,19 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
-                             const int *status, cudaStream_t s) {
+                             int tiles_per_block, const int *status, cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
+    if (tiles_per_block == 4) {
+        if (collect)
+            k_composite_quad<true><<<n_tiles, 128, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+                                                            rrect, bitmap, C, rgb, depth, final_T,
+                                                            stats, status);
+        else
+            k_composite_quad<false><<<n_tiles, 128, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+                                                             rrect, bitmap, C, rgb, depth, final_T,
+                                                             stats, status);
+        return cudaGetLastError();
+    }
     if (pixels_per_thread == 8)
         return launch_ppt<8>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
                              rgb, depth, final_T, stats, collect, status, s);

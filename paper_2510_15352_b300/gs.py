@@ -30,7 +30,7 @@ class gs_config(ctypes.Structure):
                 ("T_min", ctypes.c_float), ("background", ctypes.c_float * 3),
                 ("max_chunk_cameras", ctypes.c_int32), ("camera_group", ctypes.c_int32),
                 ("count_pairs", ctypes.c_int32), ("time_stages", ctypes.c_int32),
-                ("pixels_per_thread", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("pixels_per_thread", ctypes.c_int32), ("tiles_per_block", ctypes.c_int32),
                 ("workspace_survivors", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4)]
 
 

@@ -10,8 +10,9 @@ from paper_2510_15352_b300 import autotune, synth
 
 def test_candidates_cover_the_space():
     c = list(autotune.candidates())
-    assert len(c) == 3 * 2 * 3
+    assert len(c) == 4 * 2 * 3  # layouts (2,1) (4,1) (8,1) (8,4) x groups x chunks
     assert {x["pixels_per_thread"] for x in c} == {2, 4, 8}
+    assert {(x["pixels_per_thread"], x["tiles_per_block"]) for x in c} == {(2, 1), (4, 1), (8, 1), (8, 4)}
 
 
 def test_signature_depends_on_the_batch_not_on_order():

@@ -199,9 +199,9 @@ def test_tile_lists_match_oracle(torch, R, orc):
 
 # ---------------------------------------------------------------- pixels
 
-@pytest.mark.parametrize("ppt", [2, 4, 8])
-def test_small_workload_pixels(torch, gsmod, orc, ppt):
-    r = gsmod.Renderer(device=0, pixels_per_thread=ppt)
+@pytest.mark.parametrize("ppt,tpb", [(2, 1), (4, 1), (8, 1), (8, 4)])
+def test_small_workload_pixels(torch, gsmod, orc, ppt, tpb):
+    r = gsmod.Renderer(device=0, pixels_per_thread=ppt, tiles_per_block=tpb)
     try:
         scene, vm, it, W, H = small_workload()
         sid = r.add_scene(scene)
