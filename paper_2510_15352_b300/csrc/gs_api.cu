@@ -492,9 +492,10 @@ gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **o
         !(c.T_min > 0.0f && c.T_min < 1.0f) || c.max_chunk_cameras < 1 || c.camera_group < 1 ||
         c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) || c.workspace_survivors < 0 ||
         (c.pixels_per_thread != 2 && c.pixels_per_thread != 4 && c.pixels_per_thread != 8) ||
-        (c.tiles_per_block != 1 && c.tiles_per_block != 4))
+        (c.tiles_per_block != 0 && c.tiles_per_block != 1 && c.tiles_per_block != 4))
         return GS_ERR_INVALID_ARG;
-    if (c.pixels_per_thread != 8) c.tiles_per_block = 1;  // quads use 8 pixels per thread
+    // 0 (a zero-initialised config) means 1; quads use 8 pixels per thread
+    if (c.tiles_per_block == 0 || c.pixels_per_thread != 8) c.tiles_per_block = 1;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return GS_ERR_INVALID_ARG;
