@@ -158,24 +158,33 @@ __device__ __forceinline__ void load_geo(const SceneDev &s, long long g, GaussGe
 // is G G^T + dil I; its determinant is computed as |G0 x G1|^2 + dil tr + dil^2
 // (Cauchy-Binet), which has no cancellation, and lambda_max as
 // mid + sqrt(((a-c)/2)^2 + b^2), equal to the textbook mid + sqrt(mid^2 - det).
-__device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
-                                        const ProjParams &P, Proj &o) {
+// The cheap first part of project(): near plane and the cull with a bound of
+// the radius. lambda_max(Sigma') <= |J|_F^2 s_max^2 + dil and |J|_F^2 <= kk / z^2
+// over the guard band; the 1.002 and +0.02 px margins keep rb above the float32
+// radius, so this culls only what the exact test culls. project() calls it, so
+// a pair it rejects is exactly a pair project() rejects here.
+__device__ __forceinline__ bool prefilter(const CamProj &c, const GaussGeo &G, const ProjParams &P,
+                                          float &z, float &iz, float &xz, float &yz, float &u,
+                                          float &v) {
     const float px = fmaf(c.R[0], G.mx, fmaf(c.R[1], G.my, fmaf(c.R[2], G.mz, c.t[0])));
     const float py = fmaf(c.R[3], G.mx, fmaf(c.R[4], G.my, fmaf(c.R[5], G.mz, c.t[1])));
-    const float z = fmaf(c.R[6], G.mx, fmaf(c.R[7], G.my, fmaf(c.R[8], G.mz, c.t[2])));
-    o.z = z;
+    z = fmaf(c.R[6], G.mx, fmaf(c.R[7], G.my, fmaf(c.R[8], G.mz, c.t[2])));
     if (!(z > P.near_plane)) return false;
-    const float iz = rcp_a(z);
-    const float xz = __fmul_rn(px, iz), yz = __fmul_rn(py, iz);
-    const float u = fmaf(c.fx, xz, c.cx), v = fmaf(c.fy, yz, c.cy);
-    // Early cull with a bound of the radius: lambda_max(Sigma') <= |J|_F^2 s_max^2 + dil
-    // and |J|_F^2 <= kk / z^2 over the guard band; the 1.002 and +0.02 px margins keep
-    // rb above the float32 radius, so this culls only what the exact test culls.
-    {
-        const float rb = fmaf(1.002f * P.sigma,
-                              sqrt_a(fmaf(c.kk * iz * iz, G.smax2, P.dilation)), 0.02f);
-        if (u + rb < 0.0f || u - rb >= c.W || v + rb < 0.0f || v - rb >= c.H) return false;
-    }
+    iz = rcp_a(z);
+    xz = __fmul_rn(px, iz);
+    yz = __fmul_rn(py, iz);
+    u = fmaf(c.fx, xz, c.cx);
+    v = fmaf(c.fy, yz, c.cy);
+    const float rb = fmaf(1.002f * P.sigma, sqrt_a(fmaf(c.kk * iz * iz, G.smax2, P.dilation)), 0.02f);
+    return !(u + rb < 0.0f || u - rb >= c.W || v + rb < 0.0f || v - rb >= c.H);
+}
+
+__device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
+                                        const ProjParams &P, Proj &o) {
+    float z, iz, xz, yz, u, v;
+    const bool pre = prefilter(c, G, P, z, iz, xz, yz, u, v);
+    o.z = z;
+    if (!pre) return false;
     const float xc = fminf(fmaxf(xz, -c.lxn), c.lxp);
     const float yc = fminf(fmaxf(yz, -c.lyn), c.lyp);
     const float j00 = __fmul_rn(c.fx, iz), j02 = -__fmul_rn(__fmul_rn(c.fx, xc), iz);
@@ -284,6 +293,15 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg
     }
 }
 
+// Mask pass in two phases so that the long exact test runs on full warps:
+// per camera, every lane applies the cheap prefilter to its own Gaussian and
+// the warp appends the passing (camera, Gaussian) pairs to a queue in shared
+// memory; whenever 32 pairs are queued, each lane takes one and runs the exact
+// test (project()); the results are OR-ed into the warp's mask word of that
+// camera. Pairs the prefilter rejects are exactly those project() rejects
+// there, so the words equal one ballot of project() per camera.
+constexpr int MQ = 64;  // queue entries per warp: < 32 left + < 32 appended
+
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project_mask(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
                    const CamInfo *__restrict__ cams, const float *__restrict__ vms,
@@ -291,29 +309,81 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
     if (g0 >= gr.n) return;
+    constexpr int NW = PROJ_THREADS / 32;
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long moff[MAX_GROUP];
-    if ((int)threadIdx.x < gr.ncam) {
-        const CamInfo ci = cams[gr.slot0 + threadIdx.x];
-        cam_setup(cp[threadIdx.x], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H,
-                  P.guard);
-        moff[threadIdx.x] = ci.mask_off;
+    __shared__ float sgeo[13][PROJ_THREADS];          // mean (3), M (9), smax2
+    __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane
+    __shared__ uint32_t smask[NW][MAX_GROUP];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < gr.ncam) {
+        const CamInfo ci = cams[gr.slot0 + tid];
+        cam_setup(cp[tid], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H, P.guard);
+        moff[tid] = ci.mask_off;
     }
-    __syncthreads();
+    smask[warp][lane] = 0u;
     const SceneDev sc = scenes[gr.scene];
-    const long long g = g0 + threadIdx.x;
+    const long long g = g0 + tid;
     const bool valid = g < gr.n;
-    const int lane = threadIdx.x & 31;
-    const bool warp_live = (g - lane) < gr.n;
     GaussGeo G;
-    if (valid) load_geo(sc, g, G);
-    for (int c = 0; c < gr.ncam; ++c) {
-        Proj pr;
-        const CamProj cam = load_cam(cp[c]);
-        const bool s = valid && project(cam, G, P, pr);
-        const unsigned b = __ballot_sync(0xffffffffu, s);
-        if (lane == 0 && warp_live) masks[moff[c] + (g >> 5)] = b;
+    if (valid) {
+        load_geo(sc, g, G);
+    } else {
+        G.mx = G.my = G.mz = G.smax2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
     }
+    sgeo[0][tid] = G.mx;
+    sgeo[1][tid] = G.my;
+    sgeo[2][tid] = G.mz;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sgeo[3 + k][tid] = G.M[k];
+    sgeo[12][tid] = G.smax2;
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    int nq = 0;  // queued pairs of this warp (warp-uniform)
+    // the exact test on queue entries [0, cnt) (cnt <= 32), results OR-ed into smask
+    auto drain = [&](int cnt) {
+        bool surv = false;
+        int cam = 0;
+        if (lane < cnt) {
+            const int e = queue[warp][lane];
+            cam = e >> 5;
+            const int gl = warp * 32 + (e & 31);
+            GaussGeo H;
+            H.mx = sgeo[0][gl];
+            H.my = sgeo[1][gl];
+            H.mz = sgeo[2][gl];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) H.M[k] = sgeo[3 + k][gl];
+            H.smax2 = sgeo[12][gl];
+            Proj pr;
+            surv = project(load_cam(cp[cam]), H, P, pr);
+            if (surv) atomicOr(&smask[warp][cam], 1u << (e & 31));
+        }
+        __syncwarp();
+        // move the entries past the drained ones to the front
+        const int rest = nq - cnt;
+        const uint16_t keep = lane < rest ? queue[warp][cnt + lane] : (uint16_t)0;
+        __syncwarp();
+        if (lane < rest) queue[warp][lane] = keep;
+        __syncwarp();
+        nq = rest;
+    };
+    for (int c = 0; c < gr.ncam; ++c) {
+        const CamProj cam = load_cam(cp[c]);
+        float z, iz, xz, yz, u, v;
+        const bool cand = valid && prefilter(cam, G, P, z, iz, xz, yz, u, v);
+        const uint32_t b = __ballot_sync(0xffffffffu, cand);
+        if (cand) queue[warp][nq + __popc(b & lt)] = (uint16_t)((c << 5) | lane);
+        nq += __popc(b);
+        __syncwarp();
+        if (nq >= 32) drain(32);
+    }
+    if (nq > 0) drain(nq);
+    __syncwarp();
+    const bool warp_live = (g0 + warp * 32) < gr.n;
+    if (lane < gr.ncam && warp_live) masks[moff[lane] + (g0 >> 5) + warp] = smask[warp][lane];
 }
 
 __global__ void __launch_bounds__(1024)
