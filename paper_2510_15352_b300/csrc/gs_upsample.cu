@@ -37,7 +37,8 @@ cudaError_t up_weights_bf16(const float *p, int co, int ci, int cin_pad, __nv_bf
                             __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s);
 cudaError_t up_conv_tc(int layer, const __nv_bfloat16 *x, int n, int h, int w,
                        const __nv_bfloat16 *wt, const float *bias, void *out, const float *rgb,
-                       int *status, int n_sm, cudaStream_t s);
+                       const float *lr_depth, float *hr_depth, int *status, int n_sm,
+                       cudaStream_t s);
 }  // namespace gsk
 
 namespace {
@@ -245,16 +246,19 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
         for (int l = 0; l < NL && e == cudaSuccess; ++l) {
             const float *bias = u->params + layer_off(l) + (long long)L_CO[l] * L_CI[l] * 9;
             bf16 *dst = (in == a) ? b : a;
+            const float *ldep = lr_depth ? lr_depth + (size_t)f0 * px : nullptr;
+            float *hdep = hr_depth ? hr_depth + (size_t)f0 * px * 16 : nullptr;
             if (tc)
                 e = gsk::up_conv_tc(l, in, m, h, w, u->wt[l], bias, l < NL - 1 ? (void *)dst : (void *)hr,
-                                    rgb, u->status, u->n_sm, s);
+                                    rgb, ldep, hdep, u->status, u->n_sm, s);
             else if (l < NL - 1)
                 e = gsk::up_conv_forward(l, in, m, h, w, u->wf[l], bias, dst, s);
             else
                 e = gsk::up_conv_upsample(in, m, h, w, u->wf[l], bias, rgb, hr, s);
             in = dst;
         }
-        if (e == cudaSuccess && lr_depth)
+        // the tensor-core path writes the depth in its last layer
+        if (e == cudaSuccess && lr_depth && !tc)
             e = gsk::up_bilinear1(lr_depth + (size_t)f0 * px, m, h, w, hr_depth + (size_t)f0 * px * 16, s);
         if (e != cudaSuccess) return cuda_fail(u, e, "upsample_forward");
     }

@@ -172,7 +172,8 @@ template <int CIN, int COUT, int EPI>
 struct TcSmem {
     static constexpr size_t in_bytes = (size_t)(CIN / 8) * TC_PIN * 16;
     static constexpr size_t w_bytes = (size_t)9 * CIN * COUT * 2;
-    static constexpr size_t l_bytes = EPI == TC_EPI_UPSAMPLE ? (size_t)(TC_TH + 2) * TC_PW * 3 * 4 : 0;
+    // LR tile with halo, 4 floats per pixel: red, green, blue, depth
+    static constexpr size_t l_bytes = EPI == TC_EPI_UPSAMPLE ? (size_t)(TC_TH + 2) * TC_PW * 4 * 4 : 0;
     static constexpr size_t off_w = 2 * in_bytes;
     static constexpr size_t off_l = off_w + w_bytes;
     static constexpr size_t off_bias = off_l + 3 * l_bytes;
@@ -202,10 +203,12 @@ __device__ __forceinline__ TileXY tile_xy(long long tile, int tx, int ty) {
     return t;
 }
 
-// Issues the asynchronous copies of one tile's input (and LR colours).
+// Issues the asynchronous copies of one tile's input (and for the upsampling
+// layer its LR colours and depth, edge-clamped).
 template <int CIN, int EPI>
 __device__ __forceinline__ void fetch_tile(const bf16 *__restrict__ x, const float *__restrict__ rgb,
-                                           int h, int w, TileXY t, unsigned char *xs, float *ls) {
+                                           const float *__restrict__ dep, int h, int w, TileXY t,
+                                           unsigned char *xs, float *ls) {
     constexpr int C8 = CIN / 8;
     for (int i = threadIdx.x; i < TC_PIN * C8; i += TC_THREADS) {
         const int c8 = i / TC_PIN, pos = i - c8 * TC_PIN;
@@ -215,11 +218,14 @@ __device__ __forceinline__ void fetch_tile(const bf16 *__restrict__ x, const flo
         cp_async16(smem_u32(xs + (size_t)i * 16), src, in);
     }
     if (EPI == TC_EPI_UPSAMPLE) {
-        for (int i = threadIdx.x; i < (TC_TH + 2) * TC_PW * 3; i += TC_THREADS) {
-            const int q = i / 3, c = i - 3 * q;
+        const int nc = dep ? 4 : 3;
+        for (int i = threadIdx.x; i < (TC_TH + 2) * TC_PW * 4; i += TC_THREADS) {
+            const int q = i >> 2, c = i & 3;
+            if (c >= nc) continue;
             const int yy = min(max(t.by - 1 + q / TC_PW, 0), h - 1);
             const int xx = min(max(t.bx - 1 + q % TC_PW, 0), w - 1);
-            cp_async4(smem_u32(ls + i), rgb + (((long long)t.img * h + yy) * w + xx) * 3 + c);
+            const long long pix = ((long long)t.img * h + yy) * w + xx;
+            cp_async4(smem_u32(ls + i), c < 3 ? rgb + pix * 3 + c : dep + pix);
         }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -239,7 +245,8 @@ __device__ __forceinline__ void bl_axis(int i, int d, int n, int &o0, int &o1, f
 // Epilogue of one tile from accumulator columns dcol (warp w: TMEM lanes 32 w..).
 template <int COUT, int EPI>
 __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t dcol, TileXY t, int h, int w,
-                                              const float *bs, const float *ls, void *out) {
+                                              const float *bs, const float *ls, void *out,
+                                              float *hd) {
     constexpr int CST = tmem_stride<COUT>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 1
@@ -265,60 +272,82 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t dcol, Tile
                 }
             }
         } else {
-            // this thread's LR pixel -> its 4 x 4 HR block, all three colours:
-            // out = bilinear4(rgb) + z[16 c + 4 dy + dx] / S
+            // this thread's LR pixel -> its 4 x 4 HR block: colour c is
+            // bilinear4(rgb) + z[16 c + 4 dy + dx] / S, depth is bilinear4(depth).
+            // The bilinear sample of HR sub-pixel (dy, dx) mixes the pixel's 3 x 3
+            // LR neighbourhood with weights wy[dy][a] wx[dx][b] (two of three
+            // non-zero per axis; edge clamping only moves weight between them).
             float v[32], v2[16];
             tmem_ld32(taddr, v);
             tmem_ld16(taddr + 32, v2);
             if (valid) {
-                float z[48];
+                float wy[4][3], wx[4][3];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) z[c] = v[c] + bs[c];
+                for (int d = 0; d < 4; ++d) {
+                    int o0, o1;
+                    float f;
+                    bl_axis(yy, d, h, o0, o1, f);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) z[32 + c] = v2[c] + bs[32 + c];
-                float nb[3][3][3];  // LR colours at (row + a - 1, col + b - 1)
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
+                    for (int a = 0; a < 3; ++a)
+                        wy[d][a] = (o0 == a - 1 ? 1.0f - f : 0.0f) + (o1 == a - 1 ? f : 0.0f);
+                    bl_axis(xx, d, w, o0, o1, f);
 #pragma unroll
                     for (int b = 0; b < 3; ++b)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) nb[a][b][c] = ls[((row + a) * TC_PW + col + b) * 3 + c];
-                int xo0[4], xo1[4];
-                float fx[4];
-#pragma unroll
-                for (int d = 0; d < 4; ++d) bl_axis(xx, d, w, xo0[d], xo1[d], fx[d]);
+                        wx[d][b] = (o0 == b - 1 ? 1.0f - f : 0.0f) + (o1 == b - 1 ? f : 0.0f);
+                }
                 const int W4 = 4 * w;
+                float *orow = (float *)out + (((long long)t.img * 4 * h + 4 * yy) * W4 + 4 * xx) * 3;
+                float o[4][12];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float nb[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) nb[a][b] = ls[((row + a) * TC_PW + col + b) * 4 + c];
+#pragma unroll
+                    for (int dy = 0; dy < 4; ++dy) {
+                        float rb[3];
+#pragma unroll
+                        for (int b = 0; b < 3; ++b)
+                            rb[b] = fmaf(wy[dy][0], nb[0][b], fmaf(wy[dy][1], nb[1][b], wy[dy][2] * nb[2][b]));
+#pragma unroll
+                        for (int dx = 0; dx < 4; ++dx) {
+                            const float zc = (16 * c + 4 * dy + dx) < 32 ? v[16 * c + 4 * dy + dx]
+                                                                         : v2[16 * c + 4 * dy + dx - 32];
+                            const float zb = zc + bs[16 * c + 4 * dy + dx];
+                            o[dy][3 * dx + c] =
+                                fmaf(zb, 1.0f / TC_DETAIL_S,
+                                     fmaf(wx[dx][0], rb[0], fmaf(wx[dx][1], rb[1], wx[dx][2] * rb[2])));
+                        }
+                    }
+                }
 #pragma unroll
                 for (int dy = 0; dy < 4; ++dy) {
-                    int yo0, yo1;
-                    float fy;
-                    bl_axis(yy, dy, h, yo0, yo1, fy);
-                    float o[12];
+                    float4 *dst = (float4 *)(orow + (long long)dy * W4 * 3);
+                    dst[0] = make_float4(o[dy][0], o[dy][1], o[dy][2], o[dy][3]);
+                    dst[1] = make_float4(o[dy][4], o[dy][5], o[dy][6], o[dy][7]);
+                    dst[2] = make_float4(o[dy][8], o[dy][9], o[dy][10], o[dy][11]);
+                }
+                if (hd) {
+                    float nb[3][3];
 #pragma unroll
-                    for (int dx = 0; dx < 4; ++dx)
+                    for (int a = 0; a < 3; ++a)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            // neighbour offsets are -1, 0 or +1: select from the 3 x 3 block
-                            float r0[3], r1[3];
+                        for (int b = 0; b < 3; ++b) nb[a][b] = ls[((row + a) * TC_PW + col + b) * 4 + 3];
+                    float *drow = hd + ((long long)t.img * 4 * h + 4 * yy) * W4 + 4 * xx;
 #pragma unroll
-                            for (int b = 0; b < 3; ++b) {
-                                r0[b] = yo0 < 0 ? nb[0][b][c] : (yo0 == 0 ? nb[1][b][c] : nb[2][b][c]);
-                                r1[b] = yo1 < 0 ? nb[0][b][c] : (yo1 == 0 ? nb[1][b][c] : nb[2][b][c]);
-                            }
-                            const float t00 = xo0[dx] < 0 ? r0[0] : (xo0[dx] == 0 ? r0[1] : r0[2]);
-                            const float t01 = xo1[dx] < 0 ? r0[0] : (xo1[dx] == 0 ? r0[1] : r0[2]);
-                            const float t10 = xo0[dx] < 0 ? r1[0] : (xo0[dx] == 0 ? r1[1] : r1[2]);
-                            const float t11 = xo1[dx] < 0 ? r1[0] : (xo1[dx] == 0 ? r1[1] : r1[2]);
-                            const float top = fmaf(fx[dx], t01 - t00, t00);
-                            const float bot = fmaf(fx[dx], t11 - t10, t10);
-                            o[3 * dx + c] =
-                                fmaf(z[16 * c + 4 * dy + dx], 1.0f / TC_DETAIL_S, fmaf(fy, bot - top, top));
-                        }
-                    float4 *dst = (float4 *)((float *)out +
-                                             (((long long)t.img * 4 * h + 4 * yy + dy) * W4 + 4 * xx) * 3);
-                    dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-                    dst[1] = make_float4(o[4], o[5], o[6], o[7]);
-                    dst[2] = make_float4(o[8], o[9], o[10], o[11]);
+                    for (int dy = 0; dy < 4; ++dy) {
+                        float rb[3];
+#pragma unroll
+                        for (int b = 0; b < 3; ++b)
+                            rb[b] = fmaf(wy[dy][0], nb[0][b], fmaf(wy[dy][1], nb[1][b], wy[dy][2] * nb[2][b]));
+                        float q[4];
+#pragma unroll
+                        for (int dx = 0; dx < 4; ++dx)
+                            q[dx] = fmaf(wx[dx][0], rb[0], fmaf(wx[dx][1], rb[1], wx[dx][2] * rb[2]));
+                        *(float4 *)(drow + (long long)dy * W4) = make_float4(q[0], q[1], q[2], q[3]);
+                    }
                 }
             }
         }
@@ -329,7 +358,8 @@ template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(TC_THREADS)
     k_conv_tc(const bf16 *__restrict__ x, int n, int h, int w, const bf16 *__restrict__ wt,
               const float *__restrict__ bias, void *__restrict__ out,
-              const float *__restrict__ rgb, int *__restrict__ status) {
+              const float *__restrict__ rgb, const float *__restrict__ lr_depth,
+              float *__restrict__ hr_depth, int *__restrict__ status) {
     using L = TcSmem<CIN, COUT, EPI>;
     constexpr int CST = tmem_stride<COUT>(), ACC = TC_MT * CST, NCOL = tmem_cols<COUT>(), C8 = CIN / 8;
     constexpr uint32_t IDESC = idesc_bf16(128, COUT);
@@ -347,7 +377,7 @@ __global__ void __launch_bounds__(TC_THREADS)
 
     // the first two tiles' inputs in flight while the weights are staged
     if (blockIdx.x < n_tiles)
-        fetch_tile<CIN, EPI>(x, rgb, h, w, tile_xy(blockIdx.x, tx, ty), xbuf(0), lbuf(0));
+        fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x, tx, ty), xbuf(0), lbuf(0));
     for (int i = tid; i < (int)(L::w_bytes / 16); i += TC_THREADS)
         ((uint4 *)ws)[i] = ((const uint4 *)wt)[i];
     for (int i = tid; i < COUT; i += TC_THREADS) bs[i] = bias[i];
@@ -401,7 +431,7 @@ __global__ void __launch_bounds__(TC_THREADS)
         __syncwarp();
         if (k == 0) {
             if (blockIdx.x + G < n_tiles)
-                fetch_tile<CIN, EPI>(x, rgb, h, w, tile_xy(blockIdx.x + G, tx, ty), xbuf(1), lbuf(1));
+                fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x + G, tx, ty), xbuf(1), lbuf(1));
         } else {
             const int j = (int)((k - 1) & 1);
             const bool ok = mbar_wait(smem_u32(bar + j), (phase_bits >> j) & 1u);
@@ -413,9 +443,9 @@ __global__ void __launch_bounds__(TC_THREADS)
             fence_after();
             // tile k + 1 into the buffer the finished MMAs of tile k - 1 read
             if (tile + G < n_tiles)
-                fetch_tile<CIN, EPI>(x, rgb, h, w, tile_xy(tile + G, tx, ty), xbuf(k + 1), lbuf(k + 1));
+                fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(tile + G, tx, ty), xbuf(k + 1), lbuf(k + 1));
             tile_epilogue<COUT, EPI>(tmem, (uint32_t)(j * ACC), tile_xy(tile - G, tx, ty), h, w, bs,
-                                     lbuf(k - 1), out);
+                                     lbuf(k - 1), out, hr_depth);
         }
         if (!has) break;
     }
@@ -430,7 +460,8 @@ __global__ void __launch_bounds__(TC_THREADS)
 
 template <int CIN, int COUT, int EPI>
 cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const float *bias,
-                   void *out, const float *rgb, int *status, int n_sm, cudaStream_t s) {
+                   void *out, const float *rgb, const float *lr_depth, float *hr_depth,
+                   int *status, int n_sm, cudaStream_t s) {
     using L = TcSmem<CIN, COUT, EPI>;
     auto kern = k_conv_tc<CIN, COUT, EPI>;
     constexpr int NCOL = tmem_cols<COUT>();
@@ -458,7 +489,7 @@ cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const flo
     const long long tiles = (long long)((w + TC_TW - 1) / TC_TW) * ((h + TC_TH - 1) / TC_TH) * n;
     if (tiles == 0) return cudaSuccess;
     const int grid = (int)std::min<long long>(tiles, (long long)per_sm * n_sm);
-    kern<<<grid, TC_THREADS, smem, s>>>(x, n, h, w, wt, bias, out, rgb, status);
+    kern<<<grid, TC_THREADS, smem, s>>>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth, status);
     return cudaGetLastError();
 }
 
@@ -466,15 +497,20 @@ cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const flo
 
 // Forward convolution of layer `layer` on the tensor cores. Layers 0-4 write
 // relu(conv + bias) as BF16 NHWC; layer 5 writes the upsampled image
-// bilinear4(rgb) + shuffle4(conv + bias) / S (FP32, [n][4h][4w][3]).
+// bilinear4(rgb) + shuffle4(conv + bias) / S (FP32, [n][4h][4w][3]) and, when
+// lr_depth is given, bilinear4(depth) into hr_depth ([n][4h][4w]).
 cudaError_t up_conv_tc(int layer, const __nv_bfloat16 *x, int n, int h, int w,
                        const __nv_bfloat16 *wt, const float *bias, void *out, const float *rgb,
-                       int *status, int n_sm, cudaStream_t s) {
+                       const float *lr_depth, float *hr_depth, int *status, int n_sm,
+                       cudaStream_t s) {
     if (layer == 0)
-        return run_tc<16, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, status, n_sm, s);
+        return run_tc<16, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, nullptr, nullptr,
+                                           status, n_sm, s);
     if (layer < 5)
-        return run_tc<32, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, status, n_sm, s);
-    return run_tc<32, 48, TC_EPI_UPSAMPLE>(x, n, h, w, wt, bias, out, rgb, status, n_sm, s);
+        return run_tc<32, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, nullptr, nullptr,
+                                           status, n_sm, s);
+    return run_tc<32, 48, TC_EPI_UPSAMPLE>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth,
+                                           status, n_sm, s);
 }
 
 }  // namespace gsk
