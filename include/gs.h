@@ -348,9 +348,11 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
                               const float *lr_rgb, const float *lr_depth, float *hr_rgb,
                               float *hr_depth, void *stream);
 
-/* Kernels of gs_upsample_forward: the 5th-generation tensor cores (tcgen05.mma
- * with tensor-memory accumulators; the default) or warp-level mma.sync. Both
- * compute the same network with BF16 operands and FP32 accumulation. */
+/* Kernels of gs_upsample_forward and of the forward and backward-data passes of
+ * gs_upsample_grad: the 5th-generation tensor cores (tcgen05.mma with
+ * tensor-memory accumulators; the default) or warp-level mma.sync. Both compute
+ * the same network with BF16 operands and FP32 accumulation; the weight
+ * gradient always runs on mma.sync. */
 enum { GS_UPSAMPLE_TCGEN05 = 0, GS_UPSAMPLE_MMA_SYNC = 1 };
 gs_status gs_upsampler_set_backend(gs_upsampler *u, int32_t backend);
 

@@ -32,9 +32,17 @@ cudaError_t up_loss(const float *z, const float *rgb, const float *target, int n
 cudaError_t up_bilinear1(const float *src, int n, int h, int w, float *dst, cudaStream_t s);
 cudaError_t up_adam(float *p, float *m, float *v, const float *g, int co, int ci, int cin_pad,
                     float lr, float b1, float b2, float eps, float c1, float c2,
-                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s);
+                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wt, __nv_bfloat16 *wdt,
+                    cudaStream_t s);
 cudaError_t up_weights_bf16(const float *p, int co, int ci, int cin_pad, __nv_bfloat16 *wf,
-                            __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s);
+                            __nv_bfloat16 *wd, __nv_bfloat16 *wt, __nv_bfloat16 *wdt,
+                            cudaStream_t s);
+cudaError_t up_conv_tc_linear(const __nv_bfloat16 *x, int n, int h, int w,
+                              const __nv_bfloat16 *wt, const float *bias, float *z, int *status,
+                              int n_sm, cudaStream_t s);
+cudaError_t up_dgrad_tc(int layer, const __nv_bfloat16 *dz, int n, int h, int w,
+                        const __nv_bfloat16 *wdt, const __nv_bfloat16 *act, __nv_bfloat16 *dx,
+                        int *status, int n_sm, cudaStream_t s);
 cudaError_t up_conv_tc(int layer, const __nv_bfloat16 *x, int n, int h, int w,
                        const __nv_bfloat16 *wt, const float *bias, void *out, const float *rgb,
                        const float *lr_depth, float *hr_depth, int *status, int n_sm,
@@ -70,7 +78,7 @@ struct Buf {
 struct gs_upsampler {
     int device = 0, n_sm = 148;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *wf[NL] = {}, *wd[NL] = {}, *wt[NL] = {};
+    bf16 *wf[NL] = {}, *wd[NL] = {}, *wt[NL] = {}, *wdt[NL] = {};
     bf16 *wblock = nullptr;
     int *status = nullptr;  // device: set when a tensor-core kernel timed out
     int backend = GS_UPSAMPLE_TCGEN05;
@@ -117,7 +125,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 cudaError_t refresh_bf16(gs_upsampler *u, cudaStream_t s) {
     for (int l = 0; l < NL; ++l) {
         cudaError_t e = gsk::up_weights_bf16(u->params + layer_off(l), L_CO[l], L_CI[l], L_CIP[l],
-                                             u->wf[l], l > 0 ? u->wd[l] : nullptr, u->wt[l], s);
+                                             u->wf[l], l > 0 ? u->wd[l] : nullptr, u->wt[l],
+                                             l > 0 ? u->wdt[l] : nullptr, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -141,7 +150,7 @@ gs_status gs_upsampler_create(int32_t device, gs_upsampler **out) {
     cudaDeviceGetAttribute(&u->n_sm, cudaDevAttrMultiProcessorCount, device);
     size_t wbytes = 0;
     for (int l = 0; l < NL; ++l)
-        wbytes += 3 * align256((size_t)9 * L_CO[l] * std::max(L_CIP[l], L_CI[l]) * sizeof(bf16));
+        wbytes += 4 * align256((size_t)9 * L_CO[l] * std::max(L_CIP[l], L_CI[l]) * sizeof(bf16));
     wbytes += 256;  // status word
     cudaError_t e = cudaMalloc(&u->params, 4 * N_PARAMS * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&u->wblock, wbytes);
@@ -161,7 +170,8 @@ gs_status gs_upsampler_create(int32_t device, gs_upsampler **out) {
         u->wf[l] = (bf16 *)w;
         u->wd[l] = (bf16 *)(w + sz);
         u->wt[l] = (bf16 *)(w + 2 * sz);
-        w += 3 * sz;
+        u->wdt[l] = (bf16 *)(w + 3 * sz);
+        w += 4 * sz;
     }
     u->status = (int *)w;
     e = cudaDeviceSynchronize();
@@ -317,9 +327,17 @@ gs_status gs_upsample_grad(gs_upsampler *u, int32_t n, int32_t h, int32_t w, con
     e = cudaMemsetAsync(u->grads, 0, N_PARAMS * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(lacc, 0, sizeof(float), s);
     if (e == cudaSuccess) e = gsk::up_prep_input(lr_rgb, n, h, w, act[0], s);
+    const bool tc = u->backend == GS_UPSAMPLE_TCGEN05;
     for (int l = 0; l < 6 && e == cudaSuccess; ++l) {
         const float *bias = u->params + layer_off(l) + (long long)L_CO[l] * L_CI[l] * 9;
-        e = gsk::up_conv_forward(l, act[l], n, h, w, u->wf[l], bias, l < 5 ? (void *)act[l + 1] : (void *)z, s);
+        if (tc && l < 5)
+            e = gsk::up_conv_tc(l, act[l], n, h, w, u->wt[l], bias, act[l + 1], nullptr, nullptr,
+                                nullptr, u->status, u->n_sm, s);
+        else if (tc)
+            e = gsk::up_conv_tc_linear(act[l], n, h, w, u->wt[l], bias, z, u->status, u->n_sm, s);
+        else
+            e = gsk::up_conv_forward(l, act[l], n, h, w, u->wf[l], bias,
+                                     l < 5 ? (void *)act[l + 1] : (void *)z, s);
     }
     if (e == cudaSuccess) e = gsk::up_loss(z, lr_rgb, hr_target, n, h, w, dz6, lacc, s);
     const bf16 *dz = dz6;
@@ -329,7 +347,8 @@ gs_status gs_upsample_grad(gs_upsampler *u, int32_t n, int32_t h, int32_t w, con
         e = gsk::up_wgrad(l, act[l], dz, n, h, w, gW, gb, u->n_sm, s);
         if (e == cudaSuccess && l > 0) {
             bf16 *dst = (dz == dzA) ? dzB : dzA;
-            e = gsk::up_conv_dgrad(l, dz, n, h, w, u->wd[l], act[l], dst, s);
+            e = tc ? gsk::up_dgrad_tc(l, dz, n, h, w, u->wdt[l], act[l], dst, u->status, u->n_sm, s)
+                   : gsk::up_conv_dgrad(l, dz, n, h, w, u->wd[l], act[l], dst, s);
             dz = dst;
         }
     }
@@ -351,7 +370,8 @@ gs_status gs_upsample_adam(gs_upsampler *u, float lr, float beta1, float beta2, 
         const long long o = layer_off(l);
         cudaError_t e = gsk::up_adam(u->params + o, u->m + o, u->v + o, u->grads + o, L_CO[l], L_CI[l],
                                      L_CIP[l], lr, beta1, beta2, eps, c1, c2, u->wf[l],
-                                     l > 0 ? u->wd[l] : nullptr, u->wt[l], s);
+                                     l > 0 ? u->wd[l] : nullptr, u->wt[l],
+                                     l > 0 ? u->wdt[l] : nullptr, s);
         if (e != cudaSuccess) return cuda_fail(u, e, "upsample_adam");
     }
     return GS_OK;

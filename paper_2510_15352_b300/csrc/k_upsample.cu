@@ -431,16 +431,18 @@ __global__ void k_bilinear1(const float *__restrict__ src, int h, int w, float *
     }
 }
 
-// Writes one weight, as BF16, into the three layouts the kernels read:
-// wf[tap][co][cin_pad] (warp-level MMA, forward), wd[8 - tap][ci][co] (backward
-// data pass) and wt[tap][cin_pad / 8][co][8] (tcgen05 K-major B operand).
+// Writes one weight, as BF16, into the four layouts the kernels read:
+// wf[tap][co][cin_pad] (warp-level MMA, forward), wd[8 - tap][ci][co] (warp-level
+// MMA, backward data pass), wt[tap][cin_pad / 8][co][8] (tcgen05 K-major B
+// operand, forward) and wdt[8 - tap][co / 8][ci][8] (tcgen05, backward data).
 __device__ __forceinline__ void store_weight(float val, int i, int co, int ci, int cin_pad,
-                                             bf16 *wf, bf16 *wd, bf16 *wt) {
+                                             bf16 *wf, bf16 *wd, bf16 *wt, bf16 *wdt) {
     const int o = i / (ci * 9), rem = i - o * ci * 9, c = rem / 9, tap = rem - 9 * c;
     const bf16 b = __float2bfloat16_rn(val);
     wf[((long long)tap * co + o) * cin_pad + c] = b;
     if (wd) wd[((long long)(8 - tap) * ci + c) * co + o] = b;
     if (wt) wt[(((long long)tap * (cin_pad / 8) + c / 8) * co + o) * 8 + (c & 7)] = b;
+    if (wdt) wdt[(((long long)(8 - tap) * (co / 8) + o / 8) * ci + c) * 8 + (o & 7)] = b;
 }
 
 // Adam on one layer's FP32 master weights [co][ci][3][3] and biases [co]
@@ -448,7 +450,7 @@ __device__ __forceinline__ void store_weight(float val, int i, int co, int ci, i
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
                        const float *__restrict__ g, int co, int ci, int cin_pad, float lr,
                        float b1, float b2, float eps, float c1, float c2, bf16 *__restrict__ wf,
-                       bf16 *__restrict__ wd, bf16 *__restrict__ wt) {
+                       bf16 *__restrict__ wd, bf16 *__restrict__ wt, bf16 *__restrict__ wdt) {
     const int nW = co * ci * 9, total = nW + co;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -458,17 +460,17 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
         v[i] = vi;
         const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         p[i] = pi;
-        if (i < nW) store_weight(pi, i, co, ci, cin_pad, wf, wd, wt);
+        if (i < nW) store_weight(pi, i, co, ci, cin_pad, wf, wd, wt, wdt);
     }
 }
 
 // BF16 copies of one layer's weights without an update (after a parameter upload).
 __global__ void k_weights_bf16(const float *__restrict__ p, int co, int ci, int cin_pad,
                                bf16 *__restrict__ wf, bf16 *__restrict__ wd,
-                               bf16 *__restrict__ wt) {
+                               bf16 *__restrict__ wt, bf16 *__restrict__ wdt) {
     const int nW = co * ci * 9;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nW; i += gridDim.x * blockDim.x)
-        store_weight(p[i], i, co, ci, cin_pad, wf, wd, wt);
+        store_weight(p[i], i, co, ci, cin_pad, wf, wd, wt, wdt);
 }
 
 template <int CIN, int COUT>
@@ -571,17 +573,19 @@ cudaError_t up_bilinear1(const float *src, int n, int h, int w, float *dst, cuda
 
 cudaError_t up_adam(float *p, float *m, float *v, const float *g, int co, int ci, int cin_pad,
                     float lr, float b1, float b2, float eps, float c1, float c2,
-                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s) {
+                    __nv_bfloat16 *wf, __nv_bfloat16 *wd, __nv_bfloat16 *wt, __nv_bfloat16 *wdt,
+                    cudaStream_t s) {
     const int total = co * ci * 9 + co;
     k_adam<<<(total + 255) / 256, 256, 0, s>>>(p, m, v, g, co, ci, cin_pad, lr, b1, b2, eps, c1,
-                                                c2, wf, wd, wt);
+                                                c2, wf, wd, wt, wdt);
     return cudaGetLastError();
 }
 
 cudaError_t up_weights_bf16(const float *p, int co, int ci, int cin_pad, __nv_bfloat16 *wf,
-                            __nv_bfloat16 *wd, __nv_bfloat16 *wt, cudaStream_t s) {
+                            __nv_bfloat16 *wd, __nv_bfloat16 *wt, __nv_bfloat16 *wdt,
+                            cudaStream_t s) {
     const int nW = co * ci * 9;
-    k_weights_bf16<<<(nW + 255) / 256, 256, 0, s>>>(p, co, ci, cin_pad, wf, wd, wt);
+    k_weights_bf16<<<(nW + 255) / 256, 256, 0, s>>>(p, co, ci, cin_pad, wf, wd, wt, wdt);
     return cudaGetLastError();
 }
 

@@ -162,7 +162,11 @@ __host__ __device__ constexpr int tmem_cols() {  // two accumulators (double buf
     return 2 * TC_MT * tmem_stride<COUT>() <= 128 ? 128 : 256;
 }
 
-enum : int { TC_EPI_RELU = 0, TC_EPI_UPSAMPLE = 1 };
+// Epilogues: RELU  out bf16 = relu(acc + bias)            (hidden layers)
+//            UPSAMPLE  out f32 HR image (+ depth)           (last layer, inference)
+//            LINEAR    out f32 = acc + bias, 48 channels    (last layer, training)
+//            GATE      out bf16 = acc * (gate > 0)          (backward data pass)
+enum : int { TC_EPI_RELU = 0, TC_EPI_UPSAMPLE = 1, TC_EPI_LINEAR = 2, TC_EPI_GATE = 3 };
 
 // Shared memory of a block: two input-tile buffers (the next tile is fetched
 // while the current one is multiplied), the weights, for the upsampling layer
@@ -246,7 +250,7 @@ __device__ __forceinline__ void bl_axis(int i, int d, int n, int &o0, int &o1, f
 template <int COUT, int EPI>
 __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t dcol, TileXY t, int h, int w,
                                               const float *bs, const float *ls, void *out,
-                                              float *hd) {
+                                              float *hd, const bf16 *__restrict__ gate) {
     constexpr int CST = tmem_stride<COUT>();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 1
@@ -256,7 +260,44 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t dcol, Tile
         const int yy = t.by + row, xx = t.bx + col;
         const bool valid = row < TC_TH && col < TC_TW && yy < h && xx < w;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + dcol + (uint32_t)(m * CST);
-        if (EPI == TC_EPI_RELU) {
+        if (EPI == TC_EPI_LINEAR) {
+            float v[32], v2[16];
+            tmem_ld32(taddr, v);
+            tmem_ld16(taddr + 32, v2);
+            if (valid) {
+                float4 *dst = (float4 *)((float *)out + (((long long)t.img * h + yy) * w + xx) * COUT);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    dst[q] = make_float4(v[4 * q] + bs[4 * q], v[4 * q + 1] + bs[4 * q + 1],
+                                         v[4 * q + 2] + bs[4 * q + 2], v[4 * q + 3] + bs[4 * q + 3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    dst[8 + q] = make_float4(v2[4 * q] + bs[32 + 4 * q], v2[4 * q + 1] + bs[33 + 4 * q],
+                                             v2[4 * q + 2] + bs[34 + 4 * q], v2[4 * q + 3] + bs[35 + 4 * q]);
+            }
+        } else if (EPI == TC_EPI_GATE) {
+            float v[32];
+            tmem_ld32(taddr, v);
+            if (valid) {
+                const long long pix = ((long long)t.img * h + yy) * w + xx;
+                const uint4 *g4 = (const uint4 *)(gate + pix * COUT);
+                uint4 *dst = (uint4 *)((bf16 *)out + pix * COUT);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 gq = g4[q];
+                    const uint32_t gw[4] = {gq.x, gq.y, gq.z, gq.w};
+                    uint32_t ow[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const __nv_bfloat162 gg = *(const __nv_bfloat162 *)&gw[r];
+                        const float a = __bfloat162float(gg.x) > 0.0f ? v[8 * q + 2 * r] : 0.0f;
+                        const float b = __bfloat162float(gg.y) > 0.0f ? v[8 * q + 2 * r + 1] : 0.0f;
+                        ow[r] = pack2(a, b);
+                    }
+                    dst[q] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+                }
+            }
+        } else if (EPI == TC_EPI_RELU) {
             float v[32];
             tmem_ld32(taddr, v);
             if (valid) {
@@ -359,7 +400,8 @@ __global__ void __launch_bounds__(TC_THREADS)
     k_conv_tc(const bf16 *__restrict__ x, int n, int h, int w, const bf16 *__restrict__ wt,
               const float *__restrict__ bias, void *__restrict__ out,
               const float *__restrict__ rgb, const float *__restrict__ lr_depth,
-              float *__restrict__ hr_depth, int *__restrict__ status) {
+              float *__restrict__ hr_depth, const bf16 *__restrict__ gate,
+              int *__restrict__ status) {
     using L = TcSmem<CIN, COUT, EPI>;
     constexpr int CST = tmem_stride<COUT>(), ACC = TC_MT * CST, NCOL = tmem_cols<COUT>(), C8 = CIN / 8;
     constexpr uint32_t IDESC = idesc_bf16(128, COUT);
@@ -380,7 +422,7 @@ __global__ void __launch_bounds__(TC_THREADS)
         fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x, tx, ty), xbuf(0), lbuf(0));
     for (int i = tid; i < (int)(L::w_bytes / 16); i += TC_THREADS)
         ((uint4 *)ws)[i] = ((const uint4 *)wt)[i];
-    for (int i = tid; i < COUT; i += TC_THREADS) bs[i] = bias[i];
+    for (int i = tid; i < COUT; i += TC_THREADS) bs[i] = bias ? bias[i] : 0.0f;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + 1)));
@@ -445,7 +487,7 @@ __global__ void __launch_bounds__(TC_THREADS)
             if (tile + G < n_tiles)
                 fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(tile + G, tx, ty), xbuf(k + 1), lbuf(k + 1));
             tile_epilogue<COUT, EPI>(tmem, (uint32_t)(j * ACC), tile_xy(tile - G, tx, ty), h, w, bs,
-                                     lbuf(k - 1), out, hr_depth);
+                                     lbuf(k - 1), out, hr_depth, gate);
         }
         if (!has) break;
     }
@@ -461,7 +503,7 @@ __global__ void __launch_bounds__(TC_THREADS)
 template <int CIN, int COUT, int EPI>
 cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const float *bias,
                    void *out, const float *rgb, const float *lr_depth, float *hr_depth,
-                   int *status, int n_sm, cudaStream_t s) {
+                   const bf16 *gate, int *status, int n_sm, cudaStream_t s) {
     using L = TcSmem<CIN, COUT, EPI>;
     auto kern = k_conv_tc<CIN, COUT, EPI>;
     constexpr int NCOL = tmem_cols<COUT>();
@@ -489,7 +531,8 @@ cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const flo
     const long long tiles = (long long)((w + TC_TW - 1) / TC_TW) * ((h + TC_TH - 1) / TC_TH) * n;
     if (tiles == 0) return cudaSuccess;
     const int grid = (int)std::min<long long>(tiles, (long long)per_sm * n_sm);
-    kern<<<grid, TC_THREADS, smem, s>>>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth, status);
+    kern<<<grid, TC_THREADS, smem, s>>>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth, gate,
+                                        status);
     return cudaGetLastError();
 }
 
@@ -505,12 +548,32 @@ cudaError_t up_conv_tc(int layer, const __nv_bfloat16 *x, int n, int h, int w,
                        cudaStream_t s) {
     if (layer == 0)
         return run_tc<16, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, nullptr, nullptr,
-                                           status, n_sm, s);
+                                           nullptr, status, n_sm, s);
     if (layer < 5)
         return run_tc<32, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, nullptr, nullptr,
-                                           status, n_sm, s);
+                                           nullptr, status, n_sm, s);
     return run_tc<32, 48, TC_EPI_UPSAMPLE>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth,
-                                           status, n_sm, s);
+                                           nullptr, status, n_sm, s);
+}
+
+// Training: the last layer's raw output z = conv + bias (FP32 [n][h][w][48]).
+cudaError_t up_conv_tc_linear(const __nv_bfloat16 *x, int n, int h, int w,
+                              const __nv_bfloat16 *wt, const float *bias, float *z, int *status,
+                              int n_sm, cudaStream_t s) {
+    return run_tc<32, 48, TC_EPI_LINEAR>(x, n, h, w, wt, bias, z, nullptr, nullptr, nullptr,
+                                         nullptr, status, n_sm, s);
+}
+
+// Backward data pass of layer `layer` (1..5): dx = conv(dz, flipped transposed
+// weights) * (act > 0), BF16 [n][h][w][32].
+cudaError_t up_dgrad_tc(int layer, const __nv_bfloat16 *dz, int n, int h, int w,
+                        const __nv_bfloat16 *wdt, const __nv_bfloat16 *act, __nv_bfloat16 *dx,
+                        int *status, int n_sm, cudaStream_t s) {
+    if (layer == 5)
+        return run_tc<48, 32, TC_EPI_GATE>(dz, n, h, w, wdt, nullptr, dx, nullptr, nullptr, nullptr,
+                                           act, status, n_sm, s);
+    return run_tc<32, 32, TC_EPI_GATE>(dz, n, h, w, wdt, nullptr, dx, nullptr, nullptr, nullptr, act,
+                                       status, n_sm, s);
 }
 
 }  // namespace gsk

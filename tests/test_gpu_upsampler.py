@@ -178,16 +178,18 @@ def test_zero_params_is_bilinear(torch_cuda):
     np.testing.assert_allclose(out, U.bilinear(rgb.astype(np.float64)), rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("backend", ["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("n,h,w", [(2, 13, 37), (4, 24, 32)])
-def test_gradients_match_oracle(torch_cuda, n, h, w):
+def test_gradients_match_oracle(torch_cuda, n, h, w, backend):
     torch = torch_cuda
     from paper_2510_15352_b300 import gs
     flat, rgb, tgt = random_case(4, n, h, w)
     up = gs.Upsampler(0)
     try:
+        up.set_backend(backend)
         up.set_params(flat)
         loss = up.grad(torch.from_numpy(rgb).cuda(), torch.from_numpy(tgt).cuda())
-        torch.cuda.synchronize()
+        up.check()
         loss = float(loss.item())
         g = up.get_grads()
     finally:
