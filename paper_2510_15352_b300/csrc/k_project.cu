@@ -21,6 +21,8 @@
 //                      the slot at a stable position.
 // The decision chain is written with explicit fmaf / *_rn intrinsics so both
 // passes round identically.
+#include <type_traits>
+
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -117,20 +119,30 @@ __device__ void cam_setup(CamProj &c, const float *vm, const float *in, int W, i
     c.TY = (H + TILE - 1) / TILE;
 }
 
-// Mean and M = R(q) S of Gaussian g (quaternion normalised here).
-__device__ __forceinline__ void load_geo(const SceneDev &s, long long g, GaussGeo &G) {
+template <typename T>
+__device__ __forceinline__ float ldt(const void *p, long long i) {
+    if constexpr (sizeof(T) == 4)
+        return __ldg(reinterpret_cast<const float *>(p) + i);
+    else if constexpr (std::is_same<T, __half>::value)
+        return __half2float(__ldg(reinterpret_cast<const __half *>(p) + i));
+    else
+        return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(p) + i));
+}
+
+// Mean and M = R(q) S of Gaussian g (quaternion normalised here), attributes of type T.
+template <typename T>
+__device__ __forceinline__ void load_geo_t(const SceneDev &s, long long g, GaussGeo &G) {
     const long long n = s.n;
-    const int dt = s.geo_dtype;
-    G.mx = ldv(s.mean, g, dt);
-    G.my = ldv(s.mean, n + g, dt);
-    G.mz = ldv(s.mean, 2 * n + g, dt);
-    const float sx = expf(ldv(s.log_scale, g, dt));
-    const float sy = expf(ldv(s.log_scale, n + g, dt));
-    const float sz = expf(ldv(s.log_scale, 2 * n + g, dt));
+    G.mx = ldt<T>(s.mean, g);
+    G.my = ldt<T>(s.mean, n + g);
+    G.mz = ldt<T>(s.mean, 2 * n + g);
+    const float sx = expf(ldt<T>(s.log_scale, g));
+    const float sy = expf(ldt<T>(s.log_scale, n + g));
+    const float sz = expf(ldt<T>(s.log_scale, 2 * n + g));
     const float sm = fmaxf(sx, fmaxf(sy, sz));
     G.smax2 = sm * sm;
-    float w = ldv(s.quat, g, dt), x = ldv(s.quat, n + g, dt);
-    float y = ldv(s.quat, 2 * n + g, dt), z = ldv(s.quat, 3 * n + g, dt);
+    float w = ldt<T>(s.quat, g), x = ldt<T>(s.quat, n + g);
+    float y = ldt<T>(s.quat, 2 * n + g), z = ldt<T>(s.quat, 3 * n + g);
     const float qq = w * w + x * x + y * y + z * z;
     if (qq > 0.0f) {
         const float inv = 1.0f / sqrtf(qq);
@@ -153,11 +165,16 @@ __device__ __forceinline__ void load_geo(const SceneDev &s, long long g, GaussGe
     G.M[8] = (1.0f - 2.0f * (x * x + y * y)) * sz;
 }
 
-// EWA projection of one Gaussian for one camera. Returns false when culled
-// (near plane, off image, non-finite). With G = J R_c M (2x3) the 2D covariance
-// is G G^T + dil I; its determinant is computed as |G0 x G1|^2 + dil tr + dil^2
-// (Cauchy-Binet), which has no cancellation, and lambda_max as
-// mid + sqrt(((a-c)/2)^2 + b^2), equal to the textbook mid + sqrt(mid^2 - det).
+// The storage type is uniform per scene: one branch, then loads of a fixed type.
+__device__ __forceinline__ void load_geo(const SceneDev &s, long long g, GaussGeo &G) {
+    if (s.geo_dtype == DT_F32)
+        load_geo_t<float>(s, g, G);
+    else if (s.geo_dtype == DT_F16)
+        load_geo_t<__half>(s, g, G);
+    else
+        load_geo_t<__nv_bfloat16>(s, g, G);
+}
+
 // The cheap first part of project(): near plane and the cull with a bound of
 // the radius. lambda_max(Sigma') <= |J|_F^2 s_max^2 + dil and |J|_F^2 <= kk / z^2
 // over the guard band; the 1.002 and +0.02 px margins keep rb above the float32
@@ -499,23 +516,31 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
         // SH rows: one coalesced segment of WG values per (coefficient, channel);
         // eight loads in flight per thread before the shared-memory stores
         const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
-        constexpr int BATCH = 8;
-        for (int i0 = tid; i0 < K3 * WG; i0 += BATCH * PROJ_THREADS) {
-            float v[BATCH];
+        auto stage = [&](auto tag) {
+            using T = decltype(tag);
+            constexpr int BATCH = 8;
+            for (int i0 = tid; i0 < K3 * WG; i0 += BATCH * PROJ_THREADS) {
+                float v[BATCH];
 #pragma unroll
-            for (int u = 0; u < BATCH; ++u) {
-                const int i = i0 + u * PROJ_THREADS;
-                const int k = i / WG, j = i - k * WG;
-                const long long g = g0 + j;
-                v[u] = (i < K3 * WG && g < gr.n) ? ldv(sc.sh, (long long)k * sc.n + g, sc.app_dtype)
-                                                 : 0.0f;
-            }
+                for (int u = 0; u < BATCH; ++u) {
+                    const int i = i0 + u * PROJ_THREADS;
+                    const int k = i / WG, j = i - k * WG;
+                    const long long g = g0 + j;
+                    v[u] = (i < K3 * WG && g < gr.n) ? ldt<T>(sc.sh, (long long)k * sc.n + g) : 0.0f;
+                }
 #pragma unroll
-            for (int u = 0; u < BATCH; ++u) {
-                const int i = i0 + u * PROJ_THREADS;
-                if (i < K3 * WG) shs[i] = v[u];
+                for (int u = 0; u < BATCH; ++u) {
+                    const int i = i0 + u * PROJ_THREADS;
+                    if (i < K3 * WG) shs[i] = v[u];
+                }
             }
-        }
+        };
+        if (sc.app_dtype == DT_F32)
+            stage(float{});
+        else if (sc.app_dtype == DT_F16)
+            stage(__half{});
+        else
+            stage(__nv_bfloat16{});
     }
     __syncthreads();
     // 2. item positions: exclusive prefix of the entries' popcounts
