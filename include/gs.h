@@ -361,6 +361,15 @@ gs_status gs_upsampler_set_backend(gs_upsampler *u, int32_t backend);
  * incomplete). Clears the flag. */
 gs_status gs_upsample_check(gs_upsampler *u, void *stream);
 
+/* Test hook for the failure path of the tensor-core kernels (no counterpart in
+ * the paper): enqueues one hidden-layer convolution on a small internal input
+ * whose first MMA completion per block is deliberately never signalled, with
+ * waits that give up after 4,096 polls. Every block then records the time-out,
+ * waits for its own MMAs and frees its tensor memory; the next
+ * gs_upsample_check returns GS_ERR_TIMEOUT and the upsampler stays usable. No
+ * GPU fault is involved. */
+gs_status gs_upsample_timeout_probe(gs_upsampler *u, void *stream);
+
 /* Training pass: forward on lr_rgb, loss = mean over HR pixels and channels of
  * (out - hr_target)^2, and the gradient of the loss with respect to every
  * parameter into the upsampler's gradient buffer (replacing the previous one).

@@ -40,6 +40,9 @@ cudaError_t up_weights_bf16(const float *p, int co, int ci, int cin_pad, __nv_bf
 cudaError_t up_conv_tc_linear(const __nv_bfloat16 *x, int n, int h, int w,
                               const __nv_bfloat16 *wt, const float *bias, float *z, int *status,
                               int n_sm, cudaStream_t s);
+cudaError_t up_conv_tc_timeout_probe(const __nv_bfloat16 *x, int n, int h, int w,
+                                     const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out,
+                                     int *status, int n_sm, long long spin_limit, cudaStream_t s);
 cudaError_t up_dgrad_tc(int layer, const __nv_bfloat16 *dz, int n, int h, int w,
                         const __nv_bfloat16 *wdt, const __nv_bfloat16 *act, __nv_bfloat16 *dx,
                         int *status, int n_sm, cudaStream_t s);
@@ -280,6 +283,23 @@ gs_status gs_upsampler_set_backend(gs_upsampler *u, int32_t backend) {
         return fail(u, GS_ERR_INVALID_ARG, "set_backend: unknown backend");
     u->backend = backend;
     return GS_OK;
+}
+
+gs_status gs_upsample_timeout_probe(gs_upsampler *u, void *stream) {
+    if (!u) return GS_ERR_INVALID_ARG;
+    DeviceGuard dg(u->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = 4, h = 28, w = 32;  // 16 tiles: several blocks
+    const size_t bytes = 2 * align256((size_t)n * h * w * 32 * sizeof(bf16));
+    cudaError_t e = grow(u->work, bytes);
+    if (e != cudaSuccess) return cuda_fail(u, e, "timeout_probe: workspace");
+    bf16 *x = (bf16 *)u->work.p;
+    bf16 *y = (bf16 *)((char *)u->work.p + bytes / 2);
+    e = cudaMemsetAsync(x, 0, bytes / 2, s);
+    if (e == cudaSuccess)
+        e = gsk::up_conv_tc_timeout_probe(x, n, h, w, u->wt[1], u->params + layer_off(1) + 32 * 32 * 9,
+                                          y, u->status, u->n_sm, 1 << 12, s);
+    return e == cudaSuccess ? GS_OK : cuda_fail(u, e, "timeout_probe");
 }
 
 gs_status gs_upsample_check(gs_upsampler *u, void *stream) {

@@ -42,7 +42,7 @@ constexpr int TC_PIN = 312;                 // staged positions: >= 17 * 18 = 30
 constexpr int TC_THREADS = 128;
 constexpr int TC_MT = 2;                    // M-tiles of 128 positions per tile
 constexpr float TC_DETAIL_S = 32.0f;
-constexpr long long TC_SPIN_LIMIT = 1LL << 22;
+constexpr long long TC_SPIN_LIMIT = 1LL << 22;  // mbarrier polls before a wait gives up
 
 static_assert(TC_MT * 128 >= TC_TH * TC_PW, "the M-tiles cover every output row");
 static_assert(TC_MT * 128 - 1 + 2 * TC_PW + 2 < TC_PIN, "taps stay inside the staged rows");
@@ -91,8 +91,8 @@ __device__ __forceinline__ void fence_after() {
 }
 
 // Bounded wait for phase `parity` of an mbarrier; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long i = 0; i < TC_SPIN_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -401,15 +401,16 @@ __global__ void __launch_bounds__(TC_THREADS)
               const float *__restrict__ bias, void *__restrict__ out,
               const float *__restrict__ rgb, const float *__restrict__ lr_depth,
               float *__restrict__ hr_depth, const bf16 *__restrict__ gate,
-              int *__restrict__ status) {
+              int *__restrict__ status, long long spin_limit, int no_commit_first) {
     using L = TcSmem<CIN, COUT, EPI>;
     constexpr int CST = tmem_stride<COUT>(), ACC = TC_MT * CST, NCOL = tmem_cols<COUT>(), C8 = CIN / 8;
     constexpr uint32_t IDESC = idesc_bf16(128, COUT);
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *ws = smem + L::off_w;
     float *bs = (float *)(smem + L::off_bias);
-    uint64_t *bar = (uint64_t *)(smem + L::off_bar);  // [2]
-    uint32_t *tslot = (uint32_t *)(smem + L::off_bar + 16);
+    // bar[0], bar[1]: MMAs of even / odd tiles done; bar[2]: drain on failure
+    uint64_t *bar = (uint64_t *)(smem + L::off_bar);
+    uint32_t *tslot = (uint32_t *)(smem + L::off_bar + 24);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int tx = (w + TC_TW - 1) / TC_TW, ty = (h + TC_TH - 1) / TC_TH;
     const long long n_tiles = (long long)tx * ty * n;
@@ -426,6 +427,7 @@ __global__ void __launch_bounds__(TC_THREADS)
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + 1)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar + 2)));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -468,7 +470,9 @@ __global__ void __launch_bounds__(TC_THREADS)
                         mma_bf16(d + (uint32_t)(m * CST),
                                  a0 + (uint64_t)(2 * ks * TC_PIN + m * 128 + (tap / 3) * TC_PW + tap % 3),
                                  b0 + (uint64_t)((tap * C8 + 2 * ks) * COUT), IDESC, (tap | ks) ? 1u : 0u);
-            mma_commit(smem_u32(bar + (k & 1)));
+            // (test hook: the first tile's completion is never signalled, so
+            // the wait for it gives up and the failure path runs)
+            if (!(no_commit_first && k == 0)) mma_commit(smem_u32(bar + (k & 1)));
         }
         __syncwarp();
         if (k == 0) {
@@ -476,7 +480,7 @@ __global__ void __launch_bounds__(TC_THREADS)
                 fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x + G, tx, ty), xbuf(1), lbuf(1));
         } else {
             const int j = (int)((k - 1) & 1);
-            const bool ok = mbar_wait(smem_u32(bar + j), (phase_bits >> j) & 1u);
+            const bool ok = mbar_wait(smem_u32(bar + j), (phase_bits >> j) & 1u, spin_limit);
             phase_bits ^= 1u << j;
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -492,7 +496,16 @@ __global__ void __launch_bounds__(TC_THREADS)
         if (!has) break;
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (failed && tid == 0) atomicOr(status, 1);
+    if (failed) {
+        // MMAs may still be in flight: one more commit tracks every MMA this
+        // block issued; wait for it (bounded) before the accumulators are freed
+        if (tid == 0) {
+            atomicOr(status, 1);
+            mma_commit(smem_u32(bar + 2));
+        }
+        __syncwarp();
+        mbar_wait(smem_u32(bar + 2), 0u, TC_SPIN_LIMIT);
+    }
     fence_before();
     __syncthreads();
     fence_after();
@@ -503,7 +516,8 @@ __global__ void __launch_bounds__(TC_THREADS)
 template <int CIN, int COUT, int EPI>
 cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const float *bias,
                    void *out, const float *rgb, const float *lr_depth, float *hr_depth,
-                   const bf16 *gate, int *status, int n_sm, cudaStream_t s) {
+                   const bf16 *gate, int *status, int n_sm, cudaStream_t s,
+                   long long spin_limit = TC_SPIN_LIMIT, int no_commit_first = 0) {
     using L = TcSmem<CIN, COUT, EPI>;
     auto kern = k_conv_tc<CIN, COUT, EPI>;
     constexpr int NCOL = tmem_cols<COUT>();
@@ -532,7 +546,7 @@ cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const flo
     if (tiles == 0) return cudaSuccess;
     const int grid = (int)std::min<long long>(tiles, (long long)per_sm * n_sm);
     kern<<<grid, TC_THREADS, smem, s>>>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth, gate,
-                                        status);
+                                        status, spin_limit, no_commit_first);
     return cudaGetLastError();
 }
 
@@ -574,6 +588,17 @@ cudaError_t up_dgrad_tc(int layer, const __nv_bfloat16 *dz, int n, int h, int w,
                                            act, status, n_sm, s);
     return run_tc<32, 32, TC_EPI_GATE>(dz, n, h, w, wdt, nullptr, dx, nullptr, nullptr, nullptr, act,
                                        status, n_sm, s);
+}
+
+// Test hook for the failure path: one hidden-layer convolution whose first
+// tile's MMA completion is never signalled and whose waits give up after
+// `spin_limit` polls; every block then sets the status word, waits for its MMAs
+// and frees its tensor memory.
+cudaError_t up_conv_tc_timeout_probe(const __nv_bfloat16 *x, int n, int h, int w,
+                                     const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out,
+                                     int *status, int n_sm, long long spin_limit, cudaStream_t s) {
+    return run_tc<32, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, nullptr, nullptr,
+                                       nullptr, status, n_sm, s, spin_limit, 1);
 }
 
 }  // namespace gsk

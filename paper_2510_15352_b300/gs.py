@@ -98,6 +98,7 @@ SIGNATURES = {
                                         ctypes.c_float, _vp]),
     "gs_upsampler_set_backend": (ctypes.c_int, [_vp, _i32]),
     "gs_upsample_check": (ctypes.c_int, [_vp, _vp]),
+    "gs_upsample_timeout_probe": (ctypes.c_int, [_vp, _vp]),
 }
 
 
@@ -152,6 +153,7 @@ gs_upsample_grad = lib.gs_upsample_grad
 gs_upsample_adam = lib.gs_upsample_adam
 gs_upsampler_set_backend = lib.gs_upsampler_set_backend
 gs_upsample_check = lib.gs_upsample_check
+gs_upsample_timeout_probe = lib.gs_upsample_timeout_probe
 GS_UPSAMPLE_TCGEN05, GS_UPSAMPLE_MMA_SYNC = 0, 1
 
 

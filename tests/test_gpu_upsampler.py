@@ -230,6 +230,31 @@ def test_adam_step_matches_oracle(torch_cuda):
         up.close()
 
 
+def test_timeout_is_reported_and_recovered(torch_cuda):
+    """A tensor-core convolution whose MMA completion is never signalled gives
+    up after its bounded wait, reports GS_ERR_TIMEOUT, and the upsampler keeps
+    working (no fault, no hang)."""
+    torch = torch_cuda
+    from paper_2510_15352_b300 import gs
+    flat, rgb, _ = random_case(7, 1, 20, 24)
+    up = gs.Upsampler(0)
+    try:
+        up.set_params(flat)
+        up.check()  # clean
+        assert gs.gs_upsample_timeout_probe(up.u, None) == gs.GS_OK
+        with pytest.raises(gs.GSError) as err:
+            up.check()
+        assert err.value.status == gs.GS_ERR_TIMEOUT
+        up.check()  # the flag was cleared
+        out, _ = up.forward(torch.from_numpy(rgb).cuda())
+        up.check()
+        ref = U.forward(flat_to_layers(flat), rgb)
+        bil = U.bilinear(rgb)
+        assert rel_err(out.cpu().numpy() - bil, ref - bil) <= 2e-2
+    finally:
+        up.close()
+
+
 def test_bad_arguments(torch_cuda):
     from paper_2510_15352_b300 import gs
     up = gs.Upsampler(0)
