@@ -278,14 +278,16 @@ def run_b300_batched(args):
     rgb = torch.empty((P, 3), dtype=torch.float32, device="cuda")
     depth = torch.empty((P,), dtype=torch.float32, device="cuda")
     counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk,
-                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
+                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
+                          camera_group=args.group)
     ids_c = np.array([counter.add_scene(s) for s in scenes], dtype=np.int32)[which]
     counter.render_v(ids_c, vm_d, it_d, Ws, Hs, rgb, depth)
     torch.cuda.synchronize()
     cst = counter.stats()
     counter.close()
     R = gs.Renderer(device=local, time_stages=0 if args.graph else 1,
-                    max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
+                    max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
+                          camera_group=args.group)
     ids = np.array([R.add_scene(s) for s in scenes], dtype=np.int32)[which]
     stream = torch.cuda.current_stream()
     graph = R.graph(ids, vm_d, it_d, Ws, Hs, rgb, depth) if args.graph else None
@@ -320,7 +322,8 @@ def run_b300_batched(args):
         # stage times from one eager render of the same batch (events inside a
         # graph replay are not read back)
         R2 = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
-                         pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
+                         pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
+                          camera_group=args.group)
         ids2 = np.array([R2.add_scene(s) for s in scenes], dtype=np.int32)[which]
         for _ in range(2):
             R2.render_v(ids2, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
@@ -375,7 +378,8 @@ def run_b300(args):
 
     # algorithmic work of the compositing kernel on these inputs (counting run)
     counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk,
-                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
+                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
+                          camera_group=args.group)
     sid_c = counter.add_scene(scene)
     counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
     torch.cuda.synchronize()
@@ -386,7 +390,8 @@ def run_b300(args):
     flops_contrib = F_CONTRIB_ONLY * cst["pairs_alpha"]
 
     R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
-                    pixels_per_thread=args.ppt, tiles_per_block=args.tpb)
+                    pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
+                          camera_group=args.group)
     sid = R.add_scene(scene)
     stream = torch.cuda.current_stream()
 
@@ -516,6 +521,8 @@ def main():
                     choices=[WORKLOAD, "batched_32scene_4096cam_mixed"])
     ap.add_argument("--chunk", type=int, default=256, help="cameras per internal chunk")
     ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
+    ap.add_argument("--group", type=int, default=64,
+                    help="cameras sharing one Gaussian load in the projection (<= 64)")
     ap.add_argument("--tpb", type=int, default=1,
                     help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
     ap.add_argument("--precision", choices=["f32", "half"], default="f32",

@@ -26,7 +26,7 @@ import numpy as np
 DEFAULT_SPACE = {
     "pixels_per_thread": (2, 4, 8),
     "tiles_per_block": (1, 4),
-    "camera_group": (16, 32),
+    "camera_group": (32, 64),
     "max_chunk_cameras": (128, 256, 512),
 }
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")

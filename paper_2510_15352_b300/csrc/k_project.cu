@@ -2,7 +2,7 @@
 // cameras (the EWA splatting step of the 3DGS renderer the paper uses, Sec. 3.2).
 //
 // Layout of the work: a block holds 256 consecutive Gaussians of one scene and
-// loops over a group of up to 32 cameras of that scene, so each Gaussian's
+// loops over a group of up to 64 cameras of that scene, so each Gaussian's
 // attributes are read from HBM once per camera group instead of once per
 // camera. Attribute loads are structure-of-arrays: consecutive threads read
 // consecutive addresses of each attribute row.
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long moff[MAX_GROUP];
     __shared__ float sgeo[13][PROJ_THREADS];          // mean (3), M (9), smax2
-    __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane
+    __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane (camera < 64)
     __shared__ uint32_t smask[NW][MAX_GROUP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < gr.ncam) {
@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         moff[tid] = ci.mask_off;
     }
     smask[warp][lane] = 0u;
+    smask[warp][lane + 32] = 0u;
     const SceneDev sc = scenes[gr.scene];
     const long long g = g0 + tid;
     const bool valid = g < gr.n;
@@ -400,7 +401,9 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     if (nq > 0) drain(nq);
     __syncwarp();
     const bool warp_live = (g0 + warp * 32) < gr.n;
-    if (lane < gr.ncam && warp_live) masks[moff[lane] + (g0 >> 5) + warp] = smask[warp][lane];
+#pragma unroll
+    for (int c = lane; c < MAX_GROUP; c += 32)
+        if (c < gr.ncam && warp_live) masks[moff[c] + (g0 >> 5) + warp] = smask[warp][c];
 }
 
 __global__ void __launch_bounds__(1024)
