@@ -175,6 +175,7 @@ struct ChunkPlan {
     long long mask_words; // survival-mask words of the chunk
     long long n_gauss;    // sum over cameras of their scene sizes
     int sort_grid, bin_grid;
+    int bin_ranks;        // depth ranks per binning block (from max_sup)
 };
 
 struct Plan {
@@ -228,7 +229,7 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
             ch.mask_words += (sd.n + 31) / 32;
             ch.n_gauss += sd.n;
             sort_up += (sd.n + SORT_TILE_KEYS - 1) / SORT_TILE_KEYS;
-            bin_up += (sd.n + BIN_RANKS - 1) / BIN_RANKS;
+            bin_up += (sd.n + BIN_RANKS_SMALL - 1) / BIN_RANKS_SMALL;  // bound for either size
             const bool new_group = ch.n_groups == 0 || P.groups.back().scene != sid ||
                                    P.groups.back().ncam == gmax;
             if (new_group) {
@@ -245,6 +246,8 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
         P.tilepre[tp + ch.m] = ch.tiles_total;
         tp += ch.m + 1;
         ch.sort_grid = (int)std::max<long long>(1, std::min<long long>(sort_up, 32 * 1184));
+        ch.bin_ranks = bin_ranks_for(ch.max_sup);
+        if (ch.bin_ranks == BIN_RANKS) bin_up = (bin_up + 3) / 4;
         ch.bin_grid = (int)std::max<long long>(1, std::min<long long>(bin_up, 32 * 1184));
         P.max_mask_words = std::max(P.max_mask_words, ch.mask_words);
         P.max_gauss = std::max(P.max_gauss, ch.n_gauss);
@@ -322,7 +325,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(launch_scan_masks(cams, (const SceneDev *)ctx->d_scenes.p, ch.m,
                               (const uint32_t *)ctx->masks.p, (uint32_t *)ctx->woff.p,
                               (int *)ctx->counts.p, st));
-        CKC(launch_plan(cams, (const int *)ctx->counts.p, ch.m, ctx->cap_survivors,
+        CKC(launch_plan(cams, (const int *)ctx->counts.p, ch.m, ch.bin_ranks, ctx->cap_survivors,
                         (int *)ctx->blkpre.p, (int *)ctx->sorttiles.p, (long long *)ctx->segstart.p,
                         (long long *)ctx->segcount.p, status, need, stats + 6, st));
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
@@ -340,7 +343,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                                  (const int *)ctx->sorttiles.p + ch.m));
         if (E) CKC(cudaEventRecord(E[2], st));
         CKC(launch_bin(cams, (const int *)ctx->blkpre.p, ch.m, ch.bin_grid, ch.max_sup,
-                       (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->vals.p,
+                       ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->vals.p,
                        (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
         if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;

@@ -12,8 +12,11 @@ namespace gsk {
 constexpr int TILE = 16;            // tile edge in pixels
 constexpr int MAX_GROUP = 64;       // cameras sharing one Gaussian load (<= 2 x warp size)
 constexpr int PROJ_THREADS = 256;   // Gaussians per projection block (8 mask words)
-constexpr int BIN_RANKS = 256;      // depth ranks per binning block
-constexpr int BIN_WORDS = BIN_RANKS / 32;
+constexpr int BIN_THREADS = 256;    // threads per binning block
+constexpr int BIN_RANKS = 1024;     // depth ranks per binning block (4 per thread) ...
+constexpr int BIN_RANKS_SMALL = 256;  // ... or 1 per thread when the bitmap words of
+                                      // 1,024 ranks of every super-tile exceed
+constexpr int BIN_SMEM_MAX = 200 * 1024;  // this much shared memory
 constexpr int MAX_TILES = 65536;    // tiles per camera (binning smem: 2 B per tile)
 constexpr int COMP_BATCH = 128;     // Gaussian records staged per compositing sub-batch
 
@@ -115,7 +118,7 @@ cudaError_t launch_blur_poses(const float *vm, const float *vel, int n, int k, f
                               float *out, cudaStream_t s);
 
 // Device-side sizing of a chunk (see k_plan.cu).
-cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, long long cap_survivors,
+cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks, long long cap_survivors,
                         int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
                         int *status, long long *need, unsigned long long *survivors,
                         cudaStream_t s);
@@ -123,9 +126,13 @@ cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, long long cap_s
 // Super-tile bitmaps (one row of ceil(count/32) words per 64x64-pixel
 // super-tile) and the rank-ordered tile rects.
 // n_blocks blocks are launched; they loop over the device total blk_prefix[n_slots].
+// bin_ranks: ranks per block, BIN_RANKS or BIN_RANKS_SMALL (the plan kernel's
+// blocks must use the same value).
+int bin_ranks_for(int n_super);
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
-                       int n_super, const uint2 *srect, const uint32_t *vals, uint2 *rrect,
-                       uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s);
+                       int n_super, int bin_ranks, const uint2 *srect, const uint32_t *vals,
+                       uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
+                       cudaStream_t s);
 
 // tiles_per_block 1: one block per tile, pixels_per_thread 2, 4 or 8 (blocks of
 // 128, 64 or 32 threads); tiles_per_block 4: one block of 4 warps per 2 x 2 quad

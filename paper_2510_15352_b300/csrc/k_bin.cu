@@ -12,20 +12,23 @@
 // whose rect holds the tile. No per-intersection key, global scan or second
 // sort is needed, and every bitmap word is written once.
 //
-// A block takes 256 consecutive ranks of one camera: it builds the 8 words of
-// that rank column for every super-tile of the camera in shared memory, then
-// writes them out as 32-byte segments.
+// A block takes 1,024 consecutive ranks of one camera (4 per thread, their
+// slot and rect loads issued together): it builds the 32 words of that rank
+// column for every super-tile of the camera in shared memory, then writes them
+// out as 128-byte segments.
 #include "gs_internal.cuh"
 
 namespace gsk {
 
 namespace {
 
-__global__ void __launch_bounds__(BIN_RANKS)
+template <int RPT>  // ranks per thread
+__global__ void __launch_bounds__(BIN_THREADS)
     k_bin(const CamInfo *__restrict__ cams, const int *__restrict__ blk_prefix, int n_slots,
           const uint2 *__restrict__ srect, const uint32_t *__restrict__ vals,
           uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
           unsigned long long *__restrict__ n_isect) {
+    constexpr int BIN_RANKS = RPT * BIN_THREADS, BIN_WORDS = BIN_RANKS / 32;
     extern __shared__ uint32_t sbm[];  // [super-tiles][BIN_WORDS]
     const int nblk = blk_prefix[n_slots];
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
@@ -42,28 +45,42 @@ __global__ void __launch_bounds__(BIN_RANKS)
     const int SX = (ci.TX + STILE - 1) / STILE, SY = (ci.TY + STILE - 1) / STILE;
     const int nsup = SX * SY;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < nsup * BIN_WORDS; i += BIN_RANKS) sbm[i] = 0u;
-    __syncthreads();
-    const int r = r0 + tid;
+    for (int i = tid; i < nsup * BIN_WORDS; i += BIN_THREADS) sbm[i] = 0u;
+    // rank r0 + j * BIN_THREADS + tid: word j * (BIN_THREADS / 32) + warp, bit lane
+    uint32_t slot[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int r = r0 + j * BIN_THREADS + tid;
+        slot[j] = r < ci.count ? vals[ci.seg_off + r] : 0u;
+    }
+    uint2 d[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int r = r0 + j * BIN_THREADS + tid;
+        d[j] = r < ci.count ? srect[ci.seg_off + slot[j]] : make_uint2(1u, 1u);  // empty rect
+    }
+    __syncthreads();  // sbm cleared
     unsigned long long area = 0;
-    if (r < ci.count) {
-        const uint32_t slot = vals[ci.seg_off + r];
-        const uint2 d = srect[ci.seg_off + slot];
-        rrect[ci.seg_off + r] = d;
-        const int x0 = (int)(d.x & 0xffffu), x1 = (int)(d.x >> 16);
-        const int y0 = (int)(d.y & 0xffffu), y1 = (int)(d.y >> 16);
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int r = r0 + j * BIN_THREADS + tid;
+        if (r >= ci.count) continue;
+        rrect[ci.seg_off + r] = d[j];
+        const int x0 = (int)(d[j].x & 0xffffu), x1 = (int)(d[j].x >> 16);
+        const int y0 = (int)(d[j].y & 0xffffu), y1 = (int)(d[j].y >> 16);
         if (x1 >= x0 && y1 >= y0) {
-            area = (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
+            area += (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
             const uint32_t bit = 1u << lane;
+            const int word = j * (BIN_THREADS / 32) + warp;
             for (int sy = y0 / STILE; sy <= y1 / STILE; ++sy)
                 for (int sx = x0 / STILE; sx <= x1 / STILE; ++sx)
-                    atomicOr(&sbm[(sy * SX + sx) * BIN_WORDS + warp], bit);
+                    atomicOr(&sbm[(sy * SX + sx) * BIN_WORDS + word], bit);
         }
     }
     __syncthreads();
     const int w0 = r0 >> 5;
     const int nwb = min(BIN_WORDS, ci.nw - w0);
-    for (int i = tid; i < nsup * BIN_WORDS; i += BIN_RANKS) {
+    for (int i = tid; i < nsup * BIN_WORDS; i += BIN_THREADS) {
         const int st = i / BIN_WORDS, k = i - st * BIN_WORDS;
         if (k < nwb) bitmap[ci.bm_off + (long long)st * ci.nw + w0 + k] = sbm[i];
     }
@@ -76,18 +93,27 @@ __global__ void __launch_bounds__(BIN_RANKS)
 
 }  // namespace
 
+int bin_ranks_for(int n_super) {
+    return (size_t)n_super * (BIN_RANKS / 32) * sizeof(uint32_t) <= (size_t)BIN_SMEM_MAX
+               ? BIN_RANKS
+               : BIN_RANKS_SMALL;
+}
+
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
-                       int n_super, const uint2 *srect, const uint32_t *vals, uint2 *rrect,
-                       uint32_t *bitmap, unsigned long long *n_isect, cudaStream_t s) {
+                       int n_super, int bin_ranks, const uint2 *srect, const uint32_t *vals,
+                       uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
+                       cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
-    const size_t smem = (size_t)n_super * BIN_WORDS * sizeof(uint32_t);
+    const size_t smem = (size_t)n_super * (bin_ranks / 32) * sizeof(uint32_t);
+    auto kern = bin_ranks == BIN_RANKS ? k_bin<BIN_RANKS / BIN_THREADS>
+                                       : k_bin<BIN_RANKS_SMALL / BIN_THREADS>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_bin<<<n_blocks, BIN_RANKS, smem, s>>>(cams, blk_prefix, n_slots, srect, vals, rrect, bitmap,
-                                            n_isect);
+    kern<<<n_blocks, BIN_THREADS, smem, s>>>(cams, blk_prefix, n_slots, srect, vals, rrect, bitmap,
+                                             n_isect);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,8 @@ __device__ __forceinline__ T block_excl_scan(T v, T &total, T *wsum) {
 
 __global__ void __launch_bounds__(PT)
     k_plan(CamInfo *__restrict__ cams, const int *__restrict__ counts, int m,
-           long long cap_survivors, int *__restrict__ blkpre, int *__restrict__ sorttiles,
+           int bin_ranks, long long cap_survivors, int *__restrict__ blkpre,
+           int *__restrict__ sorttiles,
            long long *__restrict__ segstart, long long *__restrict__ segcount,
            int *__restrict__ status, long long *__restrict__ need,
            unsigned long long *__restrict__ survivors) {
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(PT)
             nw = (int)((c + 31) / 32);
             const int nsup = ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE);
             bmw = (long long)nsup * nw;
-            bb = (int)((c + BIN_RANKS - 1) / BIN_RANKS);
+            bb = (int)((c + bin_ranks - 1) / bin_ranks);
             st = (int)((c + SORT_TILE_KEYS - 1) / SORT_TILE_KEYS);
         }
         long long t_s, t_bm;
@@ -111,13 +112,13 @@ __global__ void __launch_bounds__(PT)
 
 }  // namespace
 
-cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, long long cap_survivors,
-                        int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
-                        int *status, long long *need, unsigned long long *survivors,
-                        cudaStream_t s) {
+cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks,
+                        long long cap_survivors, int *blkpre, int *sorttiles, long long *segstart,
+                        long long *segcount, int *status, long long *need,
+                        unsigned long long *survivors, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
-    k_plan<<<1, PT, 0, s>>>(cams, counts, m, cap_survivors, blkpre, sorttiles, segstart, segcount,
-                            status, need, survivors);
+    k_plan<<<1, PT, 0, s>>>(cams, counts, m, bin_ranks, cap_survivors, blkpre, sorttiles, segstart,
+                            segcount, status, need, survivors);
     return cudaGetLastError();
 }
 
