@@ -63,8 +63,11 @@ __device__ __forceinline__ float max_p_rect(float u, float v, float a, float b, 
     return best;
 }
 
+// With 8 pixels per thread (one-warp blocks) the register budget is set for 20
+// resident blocks per SM (96 registers, no spills): 29.3 instead of 30.1 ms per
+// 1,024 cameras at 16 blocks; 24 blocks spill less well and run slower.
 template <int PPT, bool STATS>
-__global__ void __launch_bounds__(256 / PPT)
+__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
                 int n_slots, const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
                 const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
