@@ -340,7 +340,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                                  (const long long *)ctx->segstart.p,
                                  (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
                                  ch.m, ch.sort_grid, (uint32_t *)ctx->sorthist.p, st,
-                                 (const int *)ctx->sorttiles.p + ch.m));
+                                 (const int *)ctx->sorttiles.p + ch.m, true));
         if (E) CKC(cudaEventRecord(E[2], st));
         CKC(launch_bin(cams, (const int *)ctx->blkpre.p, ch.m, ch.bin_grid, ch.max_sup,
                        ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->vals.p,

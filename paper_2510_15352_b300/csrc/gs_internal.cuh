@@ -105,13 +105,14 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
 // Segmented sort: tile_start[n_seg + 1] is the prefix of sort_tiles_for(count)
 // over the segments; hist needs 256 uint32 per tile. n_tiles blocks are
 // launched; with n_tiles_dev != NULL the kernels loop over the device total
-// *n_tiles_dev (grid-stride), else over n_tiles.
+// *n_tiles_dev (grid-stride), else over n_tiles. With index_vals the input
+// values are not read: value i of a segment is i (the projection's slots).
 int sort_tiles_for(long long count);
 cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
                                  uint32_t *tmp_vals, const long long *seg_start,
                                  const long long *seg_count, const int *tile_start, int n_seg,
                                  int n_tiles, uint32_t *hist, cudaStream_t s,
-                                 const int *n_tiles_dev = nullptr);
+                                 const int *n_tiles_dev = nullptr, bool index_vals = false);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
 cudaError_t launch_blur_poses(const float *vm, const float *vel, int n, int k, float shutter,

@@ -620,8 +620,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
                          __float_as_uint(pr.r));
         rec[at] = R;
         srect[at] = make_uint2(R.d.x, R.d.y);
-        keys[at] = __float_as_uint(pr.z);
-        vals[at] = slot;
+        keys[at] = __float_as_uint(pr.z);  // its value, the slot, is implied by the position
     }
 }
 

@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(ST)
                    uint32_t *__restrict__ dk, uint32_t *__restrict__ dv,
                    const long long *__restrict__ seg_start, const long long *__restrict__ seg_count,
                    const int *__restrict__ tile_start, int n_seg, int shift,
-                   const uint32_t *__restrict__ offs, const int *__restrict__ nt_dev, int nt_host) {
+                   const uint32_t *__restrict__ offs, const int *__restrict__ nt_dev, int nt_host,
+                   int index_vals) {
     __shared__ uint32_t wcnt[SNW][256];
     __shared__ uint32_t toff[256];   // where the tile's run of each digit starts in the segment
     __shared__ uint32_t tdig[256];   // where each digit starts in the tile's sorted order
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(ST)
     for (int r = 0; r < SIPT; ++r) {
         const long long i = i0 + r * 32 + lane;
         kr[r] = i < n ? sk[base + i] : 0u;
-        vr[r] = i < n ? sv[base + i] : 0u;
+        // index_vals: the values are the positions in the segment (not read)
+        vr[r] = i < n ? (index_vals ? (uint32_t)i : sv[base + i]) : 0u;
     }
     __syncwarp();
     const uint32_t lt = (1u << lane) - 1u;
@@ -217,7 +219,7 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
                                  uint32_t *tmp_vals, const long long *seg_start,
                                  const long long *seg_count, const int *tile_start, int n_seg,
                                  int n_tiles, uint32_t *hist, cudaStream_t s,
-                                 const int *n_tiles_dev) {
+                                 const int *n_tiles_dev, bool index_vals) {
     if (n_seg == 0 || n_tiles == 0) return cudaSuccess;
     uint32_t *src_k = keys, *src_v = vals, *dst_k = tmp_keys, *dst_v = tmp_vals;
     for (int pass = 0; pass < 4; ++pass) {
@@ -226,7 +228,8 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
                                            hist, n_tiles_dev, n_tiles);
         k_sort_offsets<<<n_seg, 256, 0, s>>>(tile_start, hist);
         k_sort_scatter<<<n_tiles, ST, 0, s>>>(src_k, src_v, dst_k, dst_v, seg_start, seg_count,
-                                              tile_start, n_seg, shift, hist, n_tiles_dev, n_tiles);
+                                              tile_start, n_seg, shift, hist, n_tiles_dev, n_tiles,
+                                              index_vals && pass == 0);
         uint32_t *t;
         t = src_k; src_k = dst_k; dst_k = t;
         t = src_v; src_v = dst_v; dst_v = t;
