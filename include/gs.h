@@ -228,8 +228,9 @@ gs_status gs_graph_check(gs_graph *g, void *stream);
 void gs_graph_destroy(gs_graph *g);
 
 /* Same as gs_render_batch with every array in HOST memory: the call copies the
- * cameras to the device, renders into context-owned device buffers and copies
- * the outputs back (pinned host buffers make the copies asynchronous DMA).
+ * cameras to the device, renders into context-owned device buffers in parts of
+ * max_chunk_cameras cameras and copies each part back on a second stream while
+ * the next part renders (pinned host buffers make the copies asynchronous DMA).
  * Returns after the outputs are in host memory. */
 gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
                                const float *viewmats, const float *intrinsics, int32_t width,

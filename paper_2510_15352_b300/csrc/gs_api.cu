@@ -69,6 +69,8 @@ struct gs_context {
     bool stats_pending = false;
     std::string err;
     std::vector<cudaEvent_t> ev;  // time_stages: 5 events per chunk of the last call
+    cudaStream_t copy_stream = nullptr;       // host entry point: device-to-host copies
+    std::vector<cudaEvent_t> part_done;       // host entry point: one event per part
     int ev_used = 0;              // chunks whose events the last call recorded
 };
 
@@ -527,6 +529,8 @@ void gs_context_destroy(gs_context *ctx) {
     for (auto &p : ctx->pin)
         if (p.p) cudaFreeHost(p.p);
     for (auto &e : ctx->ev) cudaEventDestroy(e);
+    for (auto &e : ctx->part_done) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     delete ctx;
 }
 
@@ -797,24 +801,52 @@ gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *s
     if (final_T) CKS(grow(ctx, ctx->h_T, px * 4));
     CKC(cudaMemcpyAsync(ctx->h_vm.p, viewmats, (size_t)n_cams * 16 * 4, cudaMemcpyHostToDevice, st));
     CKC(cudaMemcpyAsync(ctx->h_in.p, intrinsics, (size_t)n_cams * 4 * 4, cudaMemcpyHostToDevice, st));
-    RenderArgs a{n_cams,
-                 scene_ids,
-                 (const float *)ctx->h_vm.p,
-                 (const float *)ctx->h_in.p,
-                 width,
-                 height,
-                 nullptr,
-                 nullptr,
-                 nullptr,
-                 (float *)ctx->h_rgb.p,
-                 (float *)ctx->h_depth.p,
-                 final_T ? (float *)ctx->h_T.p : nullptr,
-                 st,
-                 UPTO_ALL};
-    CKS(render_impl(ctx, a));
-    CKC(cudaMemcpyAsync(rgb, ctx->h_rgb.p, px * 3 * 4, cudaMemcpyDeviceToHost, st));
-    CKC(cudaMemcpyAsync(depth, ctx->h_depth.p, px * 4, cudaMemcpyDeviceToHost, st));
-    if (final_T) CKC(cudaMemcpyAsync(final_T, ctx->h_T.p, px * 4, cudaMemcpyDeviceToHost, st));
+    // The batch is rendered in parts of one chunk each; the copies of part k
+    // back to the host run on a second stream while part k + 1 renders.
+    if (!ctx->copy_stream)
+        CKC(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    const int part = std::max(1, ctx->cfg.max_chunk_cameras);
+    const int n_parts = (n_cams + part - 1) / part;
+    while ((int)ctx->part_done.size() < n_parts) {
+        cudaEvent_t e;
+        CKC(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->part_done.push_back(e);
+    }
+    const size_t fpx = (size_t)width * height;  // pixels per frame
+    for (int k = 0; k < n_parts; ++k) {
+        const int c0 = k * part, m = std::min(part, n_cams - c0);
+        const size_t p0 = (size_t)c0 * fpx, pm = (size_t)m * fpx;
+        RenderArgs a{m,
+                     scene_ids + c0,
+                     (const float *)ctx->h_vm.p + 16LL * c0,
+                     (const float *)ctx->h_in.p + 4LL * c0,
+                     width,
+                     height,
+                     nullptr,
+                     nullptr,
+                     nullptr,
+                     (float *)ctx->h_rgb.p + 3 * p0,
+                     (float *)ctx->h_depth.p + p0,
+                     final_T ? (float *)ctx->h_T.p + p0 : nullptr,
+                     st,
+                     UPTO_ALL};
+        gs_status rs = render_impl(ctx, a);
+        if (rs != GS_OK) {
+            cudaStreamSynchronize(ctx->copy_stream);
+            return rs;
+        }
+        CKC(cudaEventRecord(ctx->part_done[k], st));
+        cudaStream_t cs = ctx->copy_stream;
+        CKC(cudaStreamWaitEvent(cs, ctx->part_done[k], 0));
+        CKC(cudaMemcpyAsync(rgb + 3 * p0, (float *)ctx->h_rgb.p + 3 * p0, pm * 3 * 4,
+                            cudaMemcpyDeviceToHost, cs));
+        CKC(cudaMemcpyAsync(depth + p0, (float *)ctx->h_depth.p + p0, pm * 4, cudaMemcpyDeviceToHost,
+                            cs));
+        if (final_T)
+            CKC(cudaMemcpyAsync(final_T + p0, (float *)ctx->h_T.p + p0, pm * 4,
+                                cudaMemcpyDeviceToHost, cs));
+    }
+    CKC(cudaStreamSynchronize(ctx->copy_stream));
     CKC(cudaStreamSynchronize(st));
     return GS_OK;
 }

@@ -351,6 +351,27 @@ def test_host_entry_point_equals_device_entry_point(torch, R):
         R.remove_scene(sid)
 
 
+def test_host_entry_point_in_parts(torch, gsmod):
+    """The host entry point renders a batch in parts of one chunk (3 cameras
+    here) and copies each part back while the next renders: same images as
+    one device call."""
+    scene, vm, it, W, H = small_workload()
+    r = gsmod.Renderer(device=0, max_chunk_cameras=3)
+    try:
+        sid = r.add_scene(scene)
+        rgb, depth, T = render_np(torch, r, sid, vm, it, W, H)
+        hr = torch.empty((len(vm), H, W, 3), dtype=torch.float32).pin_memory()
+        hd = torch.empty((len(vm), H, W), dtype=torch.float32).pin_memory()
+        hT = torch.empty((len(vm), H, W), dtype=torch.float32).pin_memory()
+        r.render_host(sid, torch.from_numpy(vm).contiguous(), torch.from_numpy(it).contiguous(),
+                      W, H, hr, hd, hT)
+        np.testing.assert_array_equal(hr.numpy(), rgb)
+        np.testing.assert_array_equal(hd.numpy(), depth)
+        np.testing.assert_array_equal(hT.numpy(), T)
+    finally:
+        r.close()
+
+
 def test_workspace_overflow_is_retried(torch, gsmod, orc):
     """A workspace far too small for the batch: the first pass overflows, the
     call grows it to the exact need and renders again, with the same result."""
