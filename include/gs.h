@@ -384,6 +384,21 @@ gs_status gs_upsample_grad(gs_upsampler *u, int32_t n, int32_t h, int32_t w, con
 gs_status gs_upsample_adam(gs_upsampler *u, float lr, float beta1, float beta2, float eps,
                            void *stream);
 
+/* The upsampled render path in one call: renders every camera at a quarter of
+ * the resolution (width / 4 x height / 4 with intrinsics / 4) and runs the
+ * upsampler to width x height, RGB from the network and depth bilinear. The
+ * batch is processed in parts of max_chunk_cameras cameras; the upsampler runs
+ * part k on a stream of its own while part k + 1 renders. Arguments as
+ * gs_render_batch (full-resolution intrinsics, outputs [n][height][width]...),
+ * width and height multiples of 4; `up` must live on the context's device.
+ * The work is ordered on `stream`: when it completes, the outputs are written.
+ * The paper renders at full resolution; this path is a service of the library
+ * (gs_upsampler_*) for callers that accept the upsampler's error. */
+gs_status gs_render_batch_upsampled(gs_context *ctx, gs_upsampler *up, int32_t n_cams,
+                                    const int32_t *scene_ids, const float *viewmats,
+                                    const float *intrinsics, int32_t width, int32_t height,
+                                    float *rgb, float *depth, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,10 @@ struct gs_context {
     std::string err;
     std::vector<cudaEvent_t> ev;  // time_stages: 5 events per chunk of the last call
     cudaStream_t copy_stream = nullptr;       // host entry point: device-to-host copies
-    std::vector<cudaEvent_t> part_done;       // host entry point: one event per part
+    std::vector<cudaEvent_t> part_done;       // host / upsampled entry points: one event per part
+    cudaStream_t up_stream = nullptr;         // upsampled entry point: the upsampler's stream
+    cudaEvent_t up_done = nullptr;
+    DevBuf lr_in, lr_rgb, lr_depth;           // upsampled entry point: quarter-resolution frames
     int ev_used = 0;              // chunks whose events the last call recorded
 };
 
@@ -531,6 +534,10 @@ void gs_context_destroy(gs_context *ctx) {
     for (auto &e : ctx->ev) cudaEventDestroy(e);
     for (auto &e : ctx->part_done) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+    if (ctx->up_done) cudaEventDestroy(ctx->up_done);
+    for (DevBuf *b : {&ctx->lr_in, &ctx->lr_rgb, &ctx->lr_depth})
+        if (b->p) cudaFree(b->p);
     delete ctx;
 }
 
@@ -848,6 +855,57 @@ gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *s
     }
     CKC(cudaStreamSynchronize(ctx->copy_stream));
     CKC(cudaStreamSynchronize(st));
+    return GS_OK;
+}
+
+gs_status gs_render_batch_upsampled(gs_context *ctx, gs_upsampler *up, int32_t n_cams,
+                                    const int32_t *scene_ids, const float *viewmats,
+                                    const float *intrinsics, int32_t width, int32_t height,
+                                    float *rgb, float *depth, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    if (!up) return fail(ctx, GS_ERR_INVALID_ARG, "NULL upsampler");
+    if (width % 4 || height % 4)
+        return fail(ctx, GS_ERR_INVALID_ARG, "width and height must be multiples of 4");
+    CKS(validate(ctx, n_cams, scene_ids, viewmats, intrinsics, width, height, rgb, depth, true));
+    ctx->err.clear();
+    if (n_cams == 0) return GS_OK;
+    CKC(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int w = width / 4, h = height / 4;
+    const size_t lpx = (size_t)w * h;
+    CKS(grow(ctx, ctx->lr_in, (size_t)n_cams * 4 * sizeof(float)));
+    CKS(grow(ctx, ctx->lr_rgb, (size_t)n_cams * lpx * 3 * sizeof(float)));
+    CKS(grow(ctx, ctx->lr_depth, (size_t)n_cams * lpx * sizeof(float)));
+    if (!ctx->up_stream) CKC(cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking));
+    if (!ctx->up_done) CKC(cudaEventCreateWithFlags(&ctx->up_done, cudaEventDisableTiming));
+    CKC(gsk::launch_scale_intrinsics(intrinsics, n_cams, 4.0f, (float *)ctx->lr_in.p, st));
+    // Parts of one chunk: the upsampler works on part k on its own stream while
+    // part k + 1 renders.
+    const int part = std::max(1, ctx->cfg.max_chunk_cameras);
+    const int n_parts = (n_cams + part - 1) / part;
+    while ((int)ctx->part_done.size() < n_parts) {
+        cudaEvent_t e;
+        CKC(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->part_done.push_back(e);
+    }
+    CKC(cudaEventRecord(ctx->up_done, ctx->up_stream));
+    CKC(cudaStreamWaitEvent(st, ctx->up_done, 0));  // earlier upsampling of these buffers done
+    for (int k = 0; k < n_parts; ++k) {
+        const int c0 = k * part, m = std::min(part, n_cams - c0);
+        float *lr = (float *)ctx->lr_rgb.p + (size_t)c0 * lpx * 3;
+        float *ld = (float *)ctx->lr_depth.p + (size_t)c0 * lpx;
+        RenderArgs a{m,  scene_ids + c0, viewmats + 16LL * c0, (const float *)ctx->lr_in.p + 4LL * c0,
+                     w,  h,  nullptr, nullptr, nullptr, lr, ld, nullptr, st, UPTO_ALL};
+        CKS(render_impl(ctx, a));
+        CKC(cudaEventRecord(ctx->part_done[k], st));
+        CKC(cudaStreamWaitEvent(ctx->up_stream, ctx->part_done[k], 0));
+        const gs_status us = gs_upsample_forward(up, m, h, w, lr, ld, rgb + (size_t)c0 * lpx * 48,
+                                                 depth + (size_t)c0 * lpx * 16, ctx->up_stream);
+        if (us != GS_OK) return fail(ctx, us, "upsampler: %s", gs_upsampler_last_error(up));
+    }
+    // the caller's stream continues after the last upsampling
+    CKC(cudaEventRecord(ctx->up_done, ctx->up_stream));
+    CKC(cudaStreamWaitEvent(st, ctx->up_done, 0));
     return GS_OK;
 }
 

@@ -115,6 +115,9 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
                                  const int *n_tiles_dev = nullptr, bool index_vals = false);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
+// Intrinsics scaled by 1/f (see k_blur.cu).
+cudaError_t launch_scale_intrinsics(const float *in, int n, float f, float *out, cudaStream_t s);
+
 cudaError_t launch_blur_poses(const float *vm, const float *vel, int n, int k, float shutter,
                               float *out, cudaStream_t s);
 

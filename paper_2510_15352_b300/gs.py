@@ -99,6 +99,8 @@ SIGNATURES = {
     "gs_upsampler_set_backend": (ctypes.c_int, [_vp, _i32]),
     "gs_upsample_check": (ctypes.c_int, [_vp, _vp]),
     "gs_upsample_timeout_probe": (ctypes.c_int, [_vp, _vp]),
+    "gs_render_batch_upsampled": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp,
+                                                 _vp, _vp]),
 }
 
 
@@ -154,6 +156,7 @@ gs_upsample_adam = lib.gs_upsample_adam
 gs_upsampler_set_backend = lib.gs_upsampler_set_backend
 gs_upsample_check = lib.gs_upsample_check
 gs_upsample_timeout_probe = lib.gs_upsample_timeout_probe
+gs_render_batch_upsampled = lib.gs_render_batch_upsampled
 GS_UPSAMPLE_TCGEN05, GS_UPSAMPLE_MMA_SYNC = 0, 1
 
 
@@ -271,6 +274,25 @@ class Renderer:
                                     W, H, rgb.data_ptr(), depth.data_ptr(), _ptr(final_T),
                                     _stream(stream)))
         return rgb, depth, final_T
+
+    def render_upsampled(self, upsampler: "Upsampler", scene_ids, viewmats, intrinsics, W: int,
+                         H: int, rgb=None, depth=None, stream=None):
+        """The upsampled path (gs_render_batch_upsampled): render at W/4 x H/4,
+        upsample to W x H with `upsampler`. Returns (rgb, depth)."""
+        import torch
+        n = int(viewmats.shape[0])
+        ids = np.ascontiguousarray(np.broadcast_to(np.asarray(scene_ids, dtype=np.int32), (n,)))
+        dev = viewmats.device
+        if rgb is None:
+            rgb = torch.empty((n, H, W, 3), dtype=torch.float32, device=dev)
+        if depth is None:
+            depth = torch.empty((n, H, W), dtype=torch.float32, device=dev)
+        vm = viewmats.contiguous()
+        it = intrinsics.contiguous()
+        self._check(gs_render_batch_upsampled(self.ctx, upsampler.u, n, ids.ctypes.data,
+                                              vm.data_ptr(), it.data_ptr(), W, H, rgb.data_ptr(),
+                                              depth.data_ptr(), _stream(stream)))
+        return rgb, depth
 
     def render_v(self, scene_ids, viewmats, intrinsics, widths, heights, rgb=None, depth=None,
                  final_T=None, want_T: bool = False, stream=None):

@@ -255,6 +255,33 @@ def test_timeout_is_reported_and_recovered(torch_cuda):
         up.close()
 
 
+def test_render_upsampled_equals_the_two_steps(torch_cuda):
+    """gs_render_batch_upsampled (parts of 3 cameras, upsampler on its own
+    stream) gives the same images as rendering at a quarter of the resolution
+    and calling the upsampler."""
+    torch = torch_cuda
+    from paper_2510_15352_b300 import gs, upsampler
+    scene = synth.make_scene(20_000, 3, seed=13)
+    vm, it = synth.make_cameras(8, 160, 120, 120.0, (0.3, 1.2), seed=13)
+    rng = np.random.default_rng(3)
+    R = gs.Renderer(0, max_chunk_cameras=3)
+    up = gs.Upsampler(0)
+    try:
+        up.set_params(upsampler.init_params(0) + rng.normal(0, 0.01, gs.Upsampler.n_params).astype(np.float32))
+        sid = R.add_scene(scene)
+        vm_d, it_d = torch.from_numpy(vm).cuda(), torch.from_numpy(it).cuda()
+        a_rgb, a_d = R.render_upsampled(up, sid, vm_d, it_d, 160, 120)
+        lr, ld, _ = R.render(sid, vm_d, it_d / 4.0, 40, 30)
+        b_rgb, b_d = up.forward(lr, ld)
+        up.check()
+        assert torch.equal(a_rgb, b_rgb) and torch.equal(a_d, b_d)
+        with pytest.raises(gs.GSError):
+            R.render_upsampled(up, sid, vm_d, it_d, 162, 120)  # not a multiple of 4
+    finally:
+        up.close()
+        R.close()
+
+
 def test_bad_arguments(torch_cuda):
     from paper_2510_15352_b300 import gs
     up = gs.Upsampler(0)
