@@ -57,6 +57,34 @@ def composite_traffic(cams_per_launch: float):
     return TRAFFIC_BYTES_PER_CAMERA * cams_per_launch if sha == TRAFFIC_SRC_SHA else None
 
 
+def step_roofline(scene, n_cams: int, W: int, H: int, cst: dict, ms_step: float) -> dict:
+    """The whole step against the roofline of the method as the survey states it:
+    max(algorithmic bytes / HBM peak, FP32 flops / FP32 peak). Bytes: the scene
+    once, a 48-byte record written and read per survivor, a 12-byte
+    intersection entry written and read per (survivor, tile) pair, 16 bytes of
+    output per pixel. Flops: 20 per (camera, Gaussian) cull test, 150 + 6 K per
+    survivor (projection and SH, K = (deg + 1)^2), 20 per evaluated pixel pair.
+    This design never materialises the intersection list (tiles read bitmap
+    rows instead), so its DRAM traffic is below that byte count."""
+    import numpy as np
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6400.0) * 1e9
+    N = scene["mean"].shape[-1]
+    K = (int(scene["sh_degree"]) + 1) ** 2
+    scene_bytes = sum(int(np.asarray(scene[k]).nbytes) for k in ("mean", "log_scale", "quat",
+                                                                    "logit", "sh"))
+    S, I, E = cst["survivors"], cst["intersections"], cst["pairs_evaluated"]
+    px = n_cams * W * H
+    nbytes = scene_bytes + 2 * 48 * S + 2 * 12 * I + 16 * px
+    flops = 20 * N * n_cams + (150 + 6 * K) * S + F_PAIR * E
+    t_b = nbytes / hbm * 1e3
+    t_f = flops / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    return {"bytes": nbytes, "flops": flops, "ms_bytes": t_b, "ms_flops": t_f,
+            "ms_roofline": max(t_b, t_f), "ms_measured": ms_step,
+            "frac": max(t_b, t_f) / ms_step}
+
+
 def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
     """The largest value of x over all ranks (x itself without a process group)."""
     if dist is None:
@@ -506,6 +534,7 @@ def run_b300(args):
                 "frac_contributing_only": (flops_contrib / (ms_comp / args.steps / 1e3) / 1e12
                                            / FP32_PEAK_TFLOPS) if ms_comp else None,
             },
+            "step_roofline": step_roofline(scene, n, W, H, cst, t_max / args.steps),
             "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "stats": {"survivors_per_step": cst["survivors"],
                       "composite_warp_iters": cst["warp_iters"],
