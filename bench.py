@@ -73,7 +73,7 @@ def step_roofline(scene, n_cams: int, W: int, H: int, cst: dict, ms_step: float)
     N = scene["mean"].shape[-1]
     K = (int(scene["sh_degree"]) + 1) ** 2
     scene_bytes = sum(int(np.asarray(scene[k]).nbytes) for k in ("mean", "log_scale", "quat",
-                                                                    "logit", "sh"))
+                                                                    "logit_opacity", "sh"))
     S, I, E = cst["survivors"], cst["intersections"], cst["pairs_evaluated"]
     px = n_cams * W * H
     nbytes = scene_bytes + 2 * 48 * S + 2 * 12 * I + 16 * px
