@@ -58,6 +58,7 @@ struct gs_context {
     // chunk workspace
     DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, srect, bitmap;
     DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist;
+    DevBuf wide;  // per chunk: some depth key needs the sort's fourth pass
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
     int workspace_gen = 0;        // bumped when the survivor buffers are reallocated
@@ -283,7 +284,8 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->tvals, Sx * 4));
     // bounds implied by S: bitmap words <= max_sup * (S/32 + m), sort tiles <= S/2048 + m
     CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
-    CKS(grow(ctx, ctx->sorthist, (Sx / SORT_TILE_KEYS + m + 1) * 256 * 4));
+    CKS(grow(ctx, ctx->sorthist, (Sx / SORT_TILE_KEYS + m + 1) * 512 * 4));
+    CKS(grow(ctx, ctx->wide, (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->blkpre, (size_t)(m + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->sorttiles, (size_t)(m + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->segstart, (size_t)m * sizeof(long long)));
@@ -333,27 +335,31 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(launch_plan(cams, (const int *)ctx->counts.p, ch.m, ch.bin_ranks, ctx->cap_survivors,
                         (int *)ctx->blkpre.p, (int *)ctx->sorttiles.p, (long long *)ctx->segstart.p,
                         (long long *)ctx->segcount.p, status, need, stats + 6, st));
+        int *wide = (int *)ctx->wide.p + k;
+        CKC(cudaMemsetAsync(wide, 0, sizeof(int), st));
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
                                  cams, a.vm, a.in, PP, (const uint32_t *)ctx->masks.p,
                                  (const uint32_t *)ctx->woff.p, (SlotRec *)ctx->rec.p,
-                                 (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p,
-                                 (uint32_t *)ctx->vals.p, std::log(cfg.alpha_min), status, st));
+                                 (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p, wide,
+                                 std::log(cfg.alpha_min), status, st));
         if (E) CKC(cudaEventRecord(E[1], st));
         if (a.upto == UPTO_PROJECT) break;
-        CKC(launch_sort_segments((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
-                                 (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
-                                 (const long long *)ctx->segstart.p,
-                                 (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
-                                 ch.m, ch.sort_grid, (uint32_t *)ctx->sorthist.p, st,
-                                 (const int *)ctx->sorttiles.p + ch.m, true));
+        CKC(launch_sort_depth((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
+                              (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
+                              (long long)std::min<long long>(ctx->cap_survivors,
+                                                             (long long)(ctx->keys.cap / 4)),
+                              (const long long *)ctx->segstart.p,
+                              (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
+                              ch.m, ch.sort_grid, (uint32_t *)ctx->sorthist.p, wide, st,
+                              (const int *)ctx->sorttiles.p + ch.m));
         if (E) CKC(cudaEventRecord(E[2], st));
         CKC(launch_bin(cams, (const int *)ctx->blkpre.p, ch.m, ch.bin_grid, ch.max_sup,
-                       ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->vals.p,
+                       ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->tvals.p,
                        (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
         if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;
         CKC(launch_composite(cams, tilepre, ch.m, ch.tiles_total, (const SlotRec *)ctx->rec.p,
-                             (const uint32_t *)ctx->vals.p, (const uint2 *)ctx->rrect.p,
+                             (const uint32_t *)ctx->tvals.p, (const uint2 *)ctx->rrect.p,
                              (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
                              cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,
                              status, st));
@@ -525,7 +531,7 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect, &ctx->srect,
                       &ctx->bitmap,   &ctx->tables, &ctx->status, &ctx->blkpre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
-                      &ctx->sorttiles, &ctx->sorthist, &ctx->blur_vm,
+                      &ctx->sorttiles, &ctx->sorthist, &ctx->blur_vm, &ctx->wide,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -1015,7 +1021,7 @@ gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *vi
     std::vector<uint2> rr((size_t)S);
     if (S) {
         CKC(cudaMemcpy(rec.data(), ctx->rec.p, S * sizeof(SlotRec), cudaMemcpyDeviceToHost));
-        CKC(cudaMemcpy(vals.data(), ctx->vals.p, S * 4, cudaMemcpyDeviceToHost));
+        CKC(cudaMemcpy(vals.data(), ctx->tvals.p, S * 4, cudaMemcpyDeviceToHost));
         CKC(cudaMemcpy(rr.data(), ctx->rrect.p, S * sizeof(uint2), cudaMemcpyDeviceToHost));
         CKC(cudaMemcpy(bm.data(), ctx->bitmap.p, bm.size() * 4, cudaMemcpyDeviceToHost));
     }

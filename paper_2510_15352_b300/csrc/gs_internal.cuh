@@ -99,7 +99,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
-                                 uint2 *srect, uint32_t *keys, uint32_t *vals,
+                                 uint2 *srect, uint32_t *keys, int *wide,
                                  float ln_alpha_min, const int *status, cudaStream_t s);
 
 // Segmented sort: tile_start[n_seg + 1] is the prefix of sort_tiles_for(count)
@@ -113,6 +113,15 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
                                  const long long *seg_count, const int *tile_start, int n_seg,
                                  int n_tiles, uint32_t *hist, cudaStream_t s,
                                  const int *n_tiles_dev = nullptr, bool index_vals = false);
+
+// The render's depth sort: keys are z bits minus the near plane's bits; three
+// passes (9, 9, 8 bits) and, when *wide, a fourth pass and a copy. The sorted
+// keys and values end in tmp_keys / tmp_vals. hist needs 512 uint32 per tile.
+cudaError_t launch_sort_depth(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
+                              uint32_t *tmp_vals, long long n_keys, const long long *seg_start,
+                              const long long *seg_count, const int *tile_start, int n_seg,
+                              int n_tiles, uint32_t *hist, const int *wide, cudaStream_t s,
+                              const int *n_tiles_dev);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
 // Intrinsics scaled by 1/f (see k_blur.cu).

@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
                     const float *__restrict__ intr, ProjParams P,
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
                     SlotRec *__restrict__ rec, uint2 *__restrict__ srect,
-                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                    uint32_t *__restrict__ keys, int *__restrict__ wide,
                     float ln_alpha_min, const int *__restrict__ status) {
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * WG;
@@ -620,7 +620,12 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
                          __float_as_uint(pr.r));
         rec[at] = R;
         srect[at] = make_uint2(R.d.x, R.d.y);
-        keys[at] = __float_as_uint(pr.z);  // its value, the slot, is implied by the position
+        // depth key: float bits of z minus those of the near plane (z > near, so
+        // non-negative and in the same order); its value, the slot, is implied
+        // by the position. Keys of 2^26 or more need the depth sort's 4th pass.
+        const uint32_t kz = __float_as_uint(pr.z) - __float_as_uint(P.near_plane);
+        keys[at] = kz;
+        if (kz >= (1u << 26)) atomicOr(wide, 1);
     }
 }
 
@@ -648,7 +653,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
-                                 uint2 *srect, uint32_t *keys, uint32_t *vals,
+                                 uint2 *srect, uint32_t *keys, int *wide,
                                  float ln_alpha_min, const int *status, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(2 * max_blocks_x, n_groups);  // 128 Gaussians per block
@@ -657,7 +662,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, viewmats, intr, P,
-                                                     masks, woff, rec, srect, keys, vals,
+                                                     masks, woff, rec, srect, keys, wide,
                                                      ln_alpha_min, status);
     return cudaGetLastError();
 }

@@ -8,7 +8,13 @@
 // uses that renderer). The tile is the last, most significant digit of the
 // full key; the binning pass applies it as a stable counting sort.
 //
-// Four 8-bit passes, ping-ponging between the caller's buffers and scratch.
+// The generic sort (gs_sort_segments) makes four 8-bit passes, ping-ponging
+// between the caller's buffers and scratch. The render's depth sort takes keys
+// already offset by the near plane's bits (z > near, so key - bits(near) is
+// non-negative and keeps the order) and makes three passes of 9, 9 and 8 bits,
+// enough for every z below 2^26 ulps above the near plane (z < 51 m for a 0.2 m
+// near plane); a fourth 6-bit pass and a copy run only when the projection
+// flagged a wider key.
 // Every segment is cut into tiles of 2048 keys and each pass runs three
 // kernels over all tiles of all segments at once:
 //   k_sort_hist    -- digit histogram of every tile;
@@ -22,6 +28,8 @@
 // of 32; a key's rank is (equal digits in earlier warps) + (equal digits in
 // earlier rounds of its warp) + (equal digits in lower lanes of its round,
 // from eight ballots over the digit bits).
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -45,52 +53,62 @@ __device__ __forceinline__ int find_seg(const int *__restrict__ tile_start, int 
     return lo;
 }
 
+// Digit histogram of every tile: BITS-bit digit at `shift`. With a skip flag
+// that is zero, the pass does nothing (an optional pass of the depth sort).
+template <int BITS>
 __global__ void __launch_bounds__(ST)
     k_sort_hist(const uint32_t *__restrict__ keys, const long long *__restrict__ seg_start,
                 const long long *__restrict__ seg_count, const int *__restrict__ tile_start,
                 int n_seg, int shift, uint32_t *__restrict__ hist, const int *__restrict__ nt_dev,
-                int nt_host) {
-    __shared__ uint32_t h[256];
+                int nt_host, const int *__restrict__ run) {
+    constexpr int ND = 1 << BITS;
+    __shared__ uint32_t h[ND];
+    if (run && !*run) return;
     const int nt = nt_dev ? *nt_dev : nt_host;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
     const int s = find_seg(tile_start, n_seg, tile);
     const long long i0 = (long long)(tile - tile_start[s]) * TK;
     const long long n = seg_count[s];
     const uint32_t *k = keys + seg_start[s];
-    h[threadIdx.x] = 0;
+    for (int d = threadIdx.x; d < ND; d += ST) h[d] = 0;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < SIPT; ++r) {
         const long long i = i0 + r * ST + threadIdx.x;
-        if (i < n) atomicAdd(&h[(k[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&h[(k[i] >> shift) & (ND - 1)], 1u);
     }
     __syncthreads();
-    hist[(long long)tile * 256 + threadIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < ND; d += ST) hist[(long long)tile * ND + d] = h[d];
     __syncthreads();  // h is cleared for the next tile of this block
     }
 }
 
-// One block per segment; thread d owns digit d. In place: hist[tile][d]
-// becomes the offset (within the segment) of the run of digit d of that tile.
-__global__ void __launch_bounds__(256)
-    k_sort_offsets(const int *__restrict__ tile_start, uint32_t *__restrict__ hist) {
+// One block of ND threads per segment; thread d owns digit d. In place:
+// hist[tile][d] becomes the offset (within the segment) of the run of digit d
+// of that tile.
+template <int BITS>
+__global__ void __launch_bounds__(1 << BITS)
+    k_sort_offsets(const int *__restrict__ tile_start, uint32_t *__restrict__ hist,
+                   const int *__restrict__ run) {
+    constexpr int ND = 1 << BITS, NWD = ND / 32;
+    if (run && !*run) return;
     const int s = blockIdx.x, d = threadIdx.x, lane = d & 31, warp = d >> 5;
     const int t0 = tile_start[s], t1 = tile_start[s + 1];
-    uint32_t run = 0;
+    uint32_t run_d = 0;
     // 16 independent loads in flight, then the running sum over them
     for (int tb = t0; tb < t1; tb += 16) {
         uint32_t c[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) c[k] = tb + k < t1 ? hist[(long long)(tb + k) * 256 + d] : 0u;
+        for (int k = 0; k < 16; ++k) c[k] = tb + k < t1 ? hist[(long long)(tb + k) * ND + d] : 0u;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            if (tb + k < t1) hist[(long long)(tb + k) * 256 + d] = run;
-            run += c[k];
+            if (tb + k < t1) hist[(long long)(tb + k) * ND + d] = run_d;
+            run_d += c[k];
         }
     }
     // exclusive scan of the digit totals
-    __shared__ uint32_t ws[8];
-    uint32_t incl = run;
+    __shared__ uint32_t ws[NWD];
+    uint32_t incl = run_d;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -100,30 +118,34 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     uint32_t before = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) before += w < warp ? ws[w] : 0u;
-    const uint32_t base = before + incl - run;
+    for (int w = 0; w < NWD; ++w) before += w < warp ? ws[w] : 0u;
+    const uint32_t base = before + incl - run_d;
     for (int tb = t0; tb < t1; tb += 16) {
         uint32_t c[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) c[k] = tb + k < t1 ? hist[(long long)(tb + k) * 256 + d] : 0u;
+        for (int k = 0; k < 16; ++k) c[k] = tb + k < t1 ? hist[(long long)(tb + k) * ND + d] : 0u;
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-            if (tb + k < t1) hist[(long long)(tb + k) * 256 + d] = c[k] + base;
+            if (tb + k < t1) hist[(long long)(tb + k) * ND + d] = c[k] + base;
     }
 }
 
+template <int BITS>
 __global__ void __launch_bounds__(ST)
     k_sort_scatter(const uint32_t *__restrict__ sk, const uint32_t *__restrict__ sv,
                    uint32_t *__restrict__ dk, uint32_t *__restrict__ dv,
                    const long long *__restrict__ seg_start, const long long *__restrict__ seg_count,
                    const int *__restrict__ tile_start, int n_seg, int shift,
                    const uint32_t *__restrict__ offs, const int *__restrict__ nt_dev, int nt_host,
-                   int index_vals) {
-    __shared__ uint32_t wcnt[SNW][256];
-    __shared__ uint32_t toff[256];   // where the tile's run of each digit starts in the segment
-    __shared__ uint32_t tdig[256];   // where each digit starts in the tile's sorted order
+                   int index_vals, const int *__restrict__ run) {
+    constexpr int ND = 1 << BITS, DPT = ND / ST;  // digits per thread (1 or 2)
+    static_assert(ND % ST == 0, "digits are a multiple of the block size");
+    __shared__ uint32_t wcnt[SNW][ND];
+    __shared__ uint32_t toff[ND];   // where the tile's run of each digit starts in the segment
+    __shared__ uint32_t tdig[ND];   // where each digit starts in the tile's sorted order
     __shared__ uint32_t dsum[SNW];
     __shared__ uint32_t skey[TK], sval[TK];
+    if (run && !*run) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = nt_dev ? *nt_dev : nt_host;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
@@ -133,9 +155,9 @@ __global__ void __launch_bounds__(ST)
     const long long i0 = t0 + (long long)warp * (32 * SIPT);
     const long long n = seg_count[s];
     const int nk = (int)min((long long)TK, n - t0);  // keys in this tile
-    toff[tid] = offs[(long long)tile * 256 + tid];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) wcnt[warp][lane * 8 + j] = 0;
+    for (int q = 0; q < DPT; ++q) toff[q * ST + tid] = offs[(long long)tile * ND + q * ST + tid];
+    for (int j = lane; j < ND; j += 32) wcnt[warp][j] = 0;
     uint32_t kr[SIPT], vr[SIPT], rk[SIPT];
 #pragma unroll
     for (int r = 0; r < SIPT; ++r) {
@@ -149,10 +171,10 @@ __global__ void __launch_bounds__(ST)
 #pragma unroll
     for (int r = 0; r < SIPT; ++r) {
         const bool ok = i0 + r * 32 + lane < n;
-        const uint32_t d = (kr[r] >> shift) & 255u;
+        const uint32_t d = (kr[r] >> shift) & (ND - 1);
         uint32_t peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
+        for (int b = 0; b < BITS; ++b) {
             const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
@@ -163,35 +185,48 @@ __global__ void __launch_bounds__(ST)
         __syncwarp();
     }
     __syncthreads();
-    // per digit (thread tid owns digit tid): exclusive prefix over warps, and
-    // the digit's total for the tile
-    uint32_t run = 0;
+    // per digit (thread tid owns digits tid and tid + ST): exclusive prefix over
+    // warps, and the digit's total for the tile
+    uint32_t tot[DPT];
 #pragma unroll
-    for (int w = 0; w < SNW; ++w) {
-        const uint32_t c = wcnt[w][tid];
-        wcnt[w][tid] = run;
-        run += c;
+    for (int q = 0; q < DPT; ++q) {
+        uint32_t run_d = 0;
+#pragma unroll
+        for (int w = 0; w < SNW; ++w) {
+            const uint32_t c = wcnt[w][q * ST + tid];
+            wcnt[w][q * ST + tid] = run_d;
+            run_d += c;
+        }
+        tot[q] = run_d;
     }
-    // exclusive prefix of the digit totals over digits: where each digit's
-    // keys start in the tile's sorted order
-    uint32_t incl = run;
+    // exclusive prefix of the digit totals over digits: where each digit's keys
+    // start in the tile's sorted order (digits q * ST + tid, in order of q then tid)
+    uint32_t carry = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+    for (int q = 0; q < DPT; ++q) {
+        uint32_t incl = tot[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) dsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0, all = 0;
+#pragma unroll
+        for (int w = 0; w < SNW; ++w) {
+            before += w < warp ? dsum[w] : 0u;
+            all += dsum[w];
+        }
+        tdig[q * ST + tid] = carry + before + incl - tot[q];
+        carry += all;
+        __syncthreads();
     }
-    if (lane == 31) dsum[warp] = incl;
-    __syncthreads();
-    uint32_t before = 0;
-#pragma unroll
-    for (int w = 0; w < SNW; ++w) before += w < warp ? dsum[w] : 0u;
-    tdig[tid] = before + incl - run;
-    __syncthreads();
     // the tile in sorted order in shared memory ...
 #pragma unroll
     for (int r = 0; r < SIPT; ++r) {
         if (i0 + r * 32 + lane < n) {
-            const uint32_t d = (kr[r] >> shift) & 255u;
+            const uint32_t d = (kr[r] >> shift) & (ND - 1);
             const uint32_t pos = tdig[d] + wcnt[warp][d] + rk[r];
             skey[pos] = kr[r];
             sval[pos] = vr[r];
@@ -202,13 +237,38 @@ __global__ void __launch_bounds__(ST)
     // consecutive addresses within each digit's run
     for (int p = tid; p < nk; p += ST) {
         const uint32_t key = skey[p];
-        const uint32_t d = (key >> shift) & 255u;
+        const uint32_t d = (key >> shift) & (ND - 1);
         const long long at = base + toff[d] + (p - tdig[d]);
         dk[at] = key;
         dv[at] = sval[p];
     }
     __syncthreads();  // shared arrays are rebuilt for the next tile of this block
     }
+}
+
+// Copy of the values (and keys) of every segment, src -> dst, when *run.
+__global__ void k_sort_copy(const uint32_t *__restrict__ sk, const uint32_t *__restrict__ sv,
+                            uint32_t *__restrict__ dk, uint32_t *__restrict__ dv, long long n,
+                            const int *__restrict__ run) {
+    if (!*run) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        dk[i] = sk[i];
+        dv[i] = sv[i];
+    }
+}
+
+template <int BITS>
+void sort_pass(const uint32_t *sk, const uint32_t *sv, uint32_t *dk, uint32_t *dv,
+               const long long *seg_start, const long long *seg_count, const int *tile_start,
+               int n_seg, int n_tiles, int shift, uint32_t *hist, cudaStream_t s,
+               const int *n_tiles_dev, bool index_vals, const int *run) {
+    k_sort_hist<BITS><<<n_tiles, ST, 0, s>>>(sk, seg_start, seg_count, tile_start, n_seg, shift,
+                                             hist, n_tiles_dev, n_tiles, run);
+    k_sort_offsets<BITS><<<n_seg, 1 << BITS, 0, s>>>(tile_start, hist, run);
+    k_sort_scatter<BITS><<<n_tiles, ST, 0, s>>>(sk, sv, dk, dv, seg_start, seg_count, tile_start,
+                                                n_seg, shift, hist, n_tiles_dev, n_tiles,
+                                                index_vals, run);
 }
 
 }  // namespace
@@ -223,18 +283,37 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
     if (n_seg == 0 || n_tiles == 0) return cudaSuccess;
     uint32_t *src_k = keys, *src_v = vals, *dst_k = tmp_keys, *dst_v = tmp_vals;
     for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 8 * pass;
-        k_sort_hist<<<n_tiles, ST, 0, s>>>(src_k, seg_start, seg_count, tile_start, n_seg, shift,
-                                           hist, n_tiles_dev, n_tiles);
-        k_sort_offsets<<<n_seg, 256, 0, s>>>(tile_start, hist);
-        k_sort_scatter<<<n_tiles, ST, 0, s>>>(src_k, src_v, dst_k, dst_v, seg_start, seg_count,
-                                              tile_start, n_seg, shift, hist, n_tiles_dev, n_tiles,
-                                              index_vals && pass == 0);
+        sort_pass<8>(src_k, src_v, dst_k, dst_v, seg_start, seg_count, tile_start, n_seg, n_tiles,
+                     8 * pass, hist, s, n_tiles_dev, index_vals && pass == 0, nullptr);
         uint32_t *t;
         t = src_k; src_k = dst_k; dst_k = t;
         t = src_v; src_v = dst_v; dst_v = t;
     }
     // four passes: the sorted data is back in keys / vals
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_depth(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
+                              uint32_t *tmp_vals, long long n_keys, const long long *seg_start,
+                              const long long *seg_count, const int *tile_start, int n_seg,
+                              int n_tiles, uint32_t *hist, const int *wide, cudaStream_t s,
+                              const int *n_tiles_dev) {
+    if (n_seg == 0 || n_tiles == 0) return cudaSuccess;
+    // bits 0-8, 9-17, 18-25: keys -> tmp -> keys -> tmp
+    sort_pass<9>(keys, vals, tmp_keys, tmp_vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
+                 0, hist, s, n_tiles_dev, true, nullptr);
+    sort_pass<9>(tmp_keys, tmp_vals, keys, vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
+                 9, hist, s, n_tiles_dev, false, nullptr);
+    sort_pass<8>(keys, vals, tmp_keys, tmp_vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
+                 18, hist, s, n_tiles_dev, false, nullptr);
+    // bits 26-31 only when some key needs them (*wide): tmp -> keys, then back
+    sort_pass<8>(tmp_keys, tmp_vals, keys, vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
+                 26, hist, s, n_tiles_dev, false, wide);
+    if (n_keys > 0) {
+        const int grid = (int)std::min<long long>((n_keys + 255) / 256, 148LL * 8);
+        k_sort_copy<<<grid, 256, 0, s>>>(keys, vals, tmp_keys, tmp_vals, n_keys, wide);
+    }
+    // the sorted data is in tmp_keys / tmp_vals
     return cudaGetLastError();
 }
 

@@ -351,6 +351,31 @@ def test_host_entry_point_equals_device_entry_point(torch, R):
         R.remove_scene(sid)
 
 
+def test_far_depths_take_the_fourth_sort_pass(torch, R, orc):
+    """Depths from 0.5 m to 400 m: keys (z bits minus the near plane's) above
+    2^26 switch on the depth sort's 4th pass; pixels and tile lists still match
+    the oracle."""
+    rng = np.random.default_rng(17)
+    n = 600
+    z = np.exp(rng.uniform(np.log(0.5), np.log(400.0), n))
+    xy = rng.uniform(-0.4, 0.4, size=(n, 2)) * z[:, None]
+    means = np.column_stack([xy, z])
+    log_s = np.log(0.02 * z)[:, None] + rng.normal(0, 0.3, size=(n, 3))
+    q = rng.normal(size=(n, 4))
+    scene = scene_from(means, log_s, q, rng.normal(0, 1, n), colours=rng.uniform(0, 1, (n, 3)))
+    vm, it = identity_camera(64, 48, 60.0)
+    sid = R.add_scene(scene)
+    try:
+        rgb, depth, T = render_np(torch, R, sid, vm[None], it[None], 64, 48)
+        ref = orc.render(scene, vm, it, 64, 48, bands=BANDS)
+        assert_camera_parity(rgb[0], depth[0], T[0], ref)
+        assert float(np.max(np.where(T[0] < 1, depth[0], 0))) > 0.0
+        off_g, gl = R.debug_tile_lists(sid, dev(torch, vm), dev(torch, it), 64, 48, cap=1_000_000)
+        assert check_tile_lists(off_g, gl, orc.tile_lists(scene, vm, it, 64, 48, bands=BANDS)) <= 1
+    finally:
+        R.remove_scene(sid)
+
+
 def test_host_entry_point_in_parts(torch, gsmod):
     """The host entry point renders a batch in parts of one chunk (3 cameras
     here) and copies each part back while the next renders: same images as
