@@ -581,7 +581,7 @@ def main():
     ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 1024)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched_32scene_4096cam_mixed"])
-    ap.add_argument("--chunk", type=int, default=256, help="cameras per internal chunk")
+    ap.add_argument("--chunk", type=int, default=512, help="cameras per internal chunk")
     ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
     ap.add_argument("--group", type=int, default=64,
                     help="cameras sharing one Gaussian load in the projection (<= 64)")

@@ -61,7 +61,7 @@ typedef struct gs_config {
     float alpha_max;       /* alpha is clamped to this (0.99) */
     float T_min;           /* a pixel stops before T would fall below this (1e-4) */
     float background[3];   /* added as T * background to rgb (0, 0, 0) */
-    int32_t max_chunk_cameras; /* cameras rendered per internal chunk (256) */
+    int32_t max_chunk_cameras; /* cameras rendered per internal chunk (512) */
     int32_t camera_group;  /* cameras of one scene that share one Gaussian load in the
                               projection kernels (64, at most 64) */
     int32_t count_pairs;   /* 1: the compositing kernel also counts evaluated pairs
@@ -229,8 +229,8 @@ void gs_graph_destroy(gs_graph *g);
 
 /* Same as gs_render_batch with every array in HOST memory: the call copies the
  * cameras to the device, renders into context-owned device buffers in parts of
- * max_chunk_cameras cameras and copies each part back on a second stream while
- * the next part renders (pinned host buffers make the copies asynchronous DMA).
+ * at most min(max_chunk_cameras, 128) cameras and copies each part back on a
+ * second stream while the next part renders (pinned host buffers make the copies asynchronous DMA).
  * Returns after the outputs are in host memory. */
 gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *scene_ids,
                                const float *viewmats, const float *intrinsics, int32_t width,

@@ -484,7 +484,7 @@ gs_status gs_config_default(gs_config *out) {
     out->alpha_min = 1.0f / 255.0f;
     out->alpha_max = 0.99f;
     out->T_min = 1e-4f;
-    out->max_chunk_cameras = 256;
+    out->max_chunk_cameras = 512;
     out->camera_group = 64;
     out->count_pairs = 0;
     out->time_stages = 0;
@@ -814,11 +814,12 @@ gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *s
     if (final_T) CKS(grow(ctx, ctx->h_T, px * 4));
     CKC(cudaMemcpyAsync(ctx->h_vm.p, viewmats, (size_t)n_cams * 16 * 4, cudaMemcpyHostToDevice, st));
     CKC(cudaMemcpyAsync(ctx->h_in.p, intrinsics, (size_t)n_cams * 4 * 4, cudaMemcpyHostToDevice, st));
-    // The batch is rendered in parts of one chunk each; the copies of part k
-    // back to the host run on a second stream while part k + 1 renders.
+    // The batch is rendered in parts (at most one chunk, at most 128 cameras);
+    // the copies of part k back to the host run on a second stream while part
+    // k + 1 renders, so only the last part's copy is not hidden.
     if (!ctx->copy_stream)
         CKC(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-    const int part = std::max(1, ctx->cfg.max_chunk_cameras);
+    const int part = std::max(1, std::min(ctx->cfg.max_chunk_cameras, 128));
     const int n_parts = (n_cams + part - 1) / part;
     while ((int)ctx->part_done.size() < n_parts) {
         cudaEvent_t e;
