@@ -39,6 +39,7 @@ WORKLOAD = "single_1m_sh3_1024cam_640x480"
 # 11 per contributing pair (alpha >= alpha_min: 1 - alpha, T', alpha T, four FMAs),
 # and a lower bound, 22 flops per contributing pair only.
 F_PAIR = 20
+LAUNCHES_PER_CHUNK = 19
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
 # FP32 peak of one B300: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz max clock
@@ -174,6 +175,22 @@ def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=64):
 # Algorithmic work of the upsampler per LR pixel: 2 flops per MAC of the six
 # 3x3 convolutions ((6 -> 32), 4 x (32 -> 32), (32 -> 48)).
 CNN_FLOPS_PER_LR_PIXEL = 2 * 9 * (6 * 32 + 4 * 32 * 32 + 32 * 48)
+
+
+def upsampled_launches(n_cams, chunk, w, h):
+    """Kernel launches of one gs_render_batch_upsampled call: the intrinsics
+    scaling, then per part of at most `chunk` cameras one render chunk and the
+    upsampler (input preparation + 6 convolutions per frame group of at most
+    1 GiB of activations)."""
+    def a256(b):
+        return (b + 255) // 256 * 256
+    per_frame = a256(w * h * 16 * 2) + 2 * a256(w * h * 32 * 2)
+    total = 1
+    for c0 in range(0, n_cams, chunk):
+        m = min(chunk, n_cams - c0)
+        group = max(1, min(m, (1 << 30) // per_frame))
+        total += LAUNCHES_PER_CHUNK + 7 * -(-m // group)
+    return total
 
 
 def upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb_plain, stream, local):
@@ -496,8 +513,10 @@ def run_b300(args):
     clk = clocks.stop()
     t_max = max_over_ranks(ms, dist)
     value = whole_job_rate(n * args.steps, world, t_max / 1e3)
-    # per chunk: mask, scan, plan, write, 4 x (hist, offsets, scatter), bin, composite
-    launches = 18 * n_chunks
+    # per chunk: mask, scan, plan, write, 4 x (hist, offsets, scatter) + copy (the
+    # fourth pass and the copy launch always and exit at once unless a depth key
+    # needs them), bin, composite
+    launches = LAUNCHES_PER_CHUNK * n_chunks
 
     # end to end: host cameras in, host frames out, through the host entry point
     e2e = None
@@ -561,7 +580,7 @@ def run_b300(args):
             out["cpu_baseline"] = cpu_baseline(scene, vm, it, W, H)
     if args.up_pairs > 0:
         ups = upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb, stream, local)
-        ups["gpu_launches_per_step"] = 18 * (n_chunks // args.steps) + 8
+        ups["gpu_launches_per_step"] = upsampled_launches(n, args.chunk, W // 4, H // 4)
         ups["speedup_vs_plain"] = ups["value"] / (n / (t_max / args.steps / 1e3))
         if rank == 0:
             out["upsampled"] = ups
