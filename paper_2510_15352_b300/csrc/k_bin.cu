@@ -15,7 +15,10 @@
 // A block takes 1,024 consecutive ranks of one camera (4 per thread, their
 // slot and rect loads issued together): it builds the 32 words of that rank
 // column for every super-tile of the camera in shared memory, then writes them
-// out as 128-byte segments.
+// out as 128-byte segments. In shared memory the words are word-major with an
+// odd row pitch (P >= number of super-tiles): the lanes of a warp set bits of
+// one word in the super-tiles their rects meet, which then fall in different
+// banks, and the write-out reads 32 words of one super-tile from 32 banks.
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -29,7 +32,7 @@ __global__ void __launch_bounds__(BIN_THREADS)
           uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
           unsigned long long *__restrict__ n_isect) {
     constexpr int BIN_RANKS = RPT * BIN_THREADS, BIN_WORDS = BIN_RANKS / 32;
-    extern __shared__ uint32_t sbm[];  // [super-tiles][BIN_WORDS]
+    extern __shared__ uint32_t sbm[];  // [BIN_WORDS][P]
     const int nblk = blk_prefix[n_slots];
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     int lo = 0, hi = n_slots - 1;
@@ -44,8 +47,9 @@ __global__ void __launch_bounds__(BIN_THREADS)
     const int r0 = (blk - blk_prefix[lo]) * BIN_RANKS;
     const int SX = (ci.TX + STILE - 1) / STILE, SY = (ci.TY + STILE - 1) / STILE;
     const int nsup = SX * SY;
+    const int P = nsup | 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < nsup * BIN_WORDS; i += BIN_THREADS) sbm[i] = 0u;
+    for (int i = tid; i < P * BIN_WORDS; i += BIN_THREADS) sbm[i] = 0u;
     // rank r0 + j * BIN_THREADS + tid: word j * (BIN_THREADS / 32) + warp, bit lane
     uint32_t slot[RPT];
 #pragma unroll
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(BIN_THREADS)
             const int word = j * (BIN_THREADS / 32) + warp;
             for (int sy = y0 / STILE; sy <= y1 / STILE; ++sy)
                 for (int sx = x0 / STILE; sx <= x1 / STILE; ++sx)
-                    atomicOr(&sbm[(sy * SX + sx) * BIN_WORDS + word], bit);
+                    atomicOr(&sbm[word * P + sy * SX + sx], bit);
         }
     }
     __syncthreads();
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(BIN_THREADS)
     const int nwb = min(BIN_WORDS, ci.nw - w0);
     for (int i = tid; i < nsup * BIN_WORDS; i += BIN_THREADS) {
         const int st = i / BIN_WORDS, k = i - st * BIN_WORDS;
-        if (k < nwb) bitmap[ci.bm_off + (long long)st * ci.nw + w0 + k] = sbm[i];
+        if (k < nwb) bitmap[ci.bm_off + (long long)st * ci.nw + w0 + k] = sbm[k * P + st];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) area += __shfl_down_sync(0xffffffffu, area, o);
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(BIN_THREADS)
 }  // namespace
 
 int bin_ranks_for(int n_super) {
-    return (size_t)n_super * (BIN_RANKS / 32) * sizeof(uint32_t) <= (size_t)BIN_SMEM_MAX
+    return (size_t)(n_super | 1) * (BIN_RANKS / 32) * sizeof(uint32_t) <= (size_t)BIN_SMEM_MAX
                ? BIN_RANKS
                : BIN_RANKS_SMALL;
 }
@@ -104,7 +108,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, 
                        uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
                        cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
-    const size_t smem = (size_t)n_super * (bin_ranks / 32) * sizeof(uint32_t);
+    const size_t smem = (size_t)(n_super | 1) * (bin_ranks / 32) * sizeof(uint32_t);
     auto kern = bin_ranks == BIN_RANKS ? k_bin<BIN_RANKS / BIN_THREADS>
                                        : k_bin<BIN_RANKS_SMALL / BIN_THREADS>;
     if (smem > 48 * 1024) {

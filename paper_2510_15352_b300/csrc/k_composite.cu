@@ -42,11 +42,18 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // Largest value over the rectangle [X0, X1] x [Y0, Y1] of the concave quadratic
 // p(x, y) = a dx^2 + b dx dy + c dy^2 + l (dx = x - u, dy = y - v; a, c < 0): the
 // centre value when (u, v) lies inside, else the best of the four edges, each a
-// 1-D concave quadratic whose vertex is clamped to the edge.
+// 1-D concave quadratic whose vertex is clamped to the edge. The vertices come
+// from approximate reciprocals: p at a point a few ulp from a vertex differs
+// from the vertex value in second order only, far inside the skip margin.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float max_p_rect(float u, float v, float a, float b, float c, float l,
                                             float X0, float X1, float Y0, float Y1) {
     if (u >= X0 && u <= X1 && v >= Y0 && v <= Y1) return l;
-    const float ia = -0.5f / a, ic = -0.5f / c;
+    const float ia = -0.5f * rcp_approx(a), ic = -0.5f * rcp_approx(c);
     float best = -__int_as_float(0x7f800000);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -226,16 +233,20 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                     if (!(__float_as_uint(g1.w) & warp_bit)) continue;  // warp-uniform
                     if (STATS) wbox++;
                     const float4 g0 = s0[j];  // u, v, a', b'
+                    // the thread's pixels k = 0..PPT-1 lie at dx = dx0 + k CPR, so
+                    // p_k = a'dx^2 + b'dy dx + c'dy^2 + log2 o = P0 + k (D + k E)
                     const float dy = py - g0.y;
-                    const float base = fmaf(g1.x * dy, dy, g1.y);
+                    const float dx0 = px0 - g0.x;
                     const float bdy = g0.w * dy;
+                    const float t0 = fmaf(g0.z, dx0, bdy);
+                    const float P0 = fmaf(t0, dx0, fmaf(g1.x * dy, dy, g1.y));
+                    const float D = (float)CPR * fmaf(g0.z, dx0, t0);
+                    const float E = (float)(CPR * CPR) * g0.z;
                     float p[PPT];
                     bool any = false;
-                    const float dx0 = px0 - g0.x;
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
-                        const float dx = dx0 + (float)(k * CPR);
-                        p[k] = fmaf(fmaf(g0.z, dx, bdy), dx, base);
+                        p[k] = k == 0 ? P0 : fmaf((float)k, fmaf((float)k, E, D), P0);
                         any = any || p[k] >= thr[k];
                     }
                     if (!__any_sync(0xffffffffu, any)) continue;

@@ -282,8 +282,11 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
 }
 
 // Colour of one Gaussian seen from camera c. The block's SH coefficients are
-// staged in shared memory as shs[(3k + ch) * 128 + local].
-__device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg, int local,
+// staged in shared memory as float4 rows: shq[r * WG + local] holds the
+// coefficients of flat index 4r .. 4r + 3 (flat index 3k + ch; zero past 3K),
+// so one 16-byte load brings four of them.
+template <int WGN>
+__device__ __forceinline__ void sh_colour(const float4 *__restrict__ shq, int deg, int local,
                                           const CamProj &c, const GaussGeo &G, float rgb[3]) {
     const int K = (deg + 1) * (deg + 1);
     float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
@@ -299,15 +302,51 @@ __device__ __forceinline__ void sh_colour(const float *__restrict__ shs, int deg
         dz = 1.0f;
     }
     float Y[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Y[k] = 0.0f;
     sh_basis(deg, dx, dy, dz, Y);
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    const int nq = (3 * K + 3) / 4;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        float acc = 0.5f;
+    for (int r = 0; r < 12; ++r) {
+        if (r < nq) {
+            const float4 q = shq[r * WGN + local];
+            const float v[4] = {q.x, q.y, q.z, q.w};
+            // per channel the terms still add in order of k
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < K) acc = fmaf(shs[(3 * k + ch) * 128 + local], Y[k], acc);
-        rgb[ch] = fmaxf(acc, 0.0f);
+            for (int j = 0; j < 4; ++j) acc[(4 * r + j) % 3] = fmaf(v[j], Y[(4 * r + j) / 3], acc[(4 * r + j) % 3]);
+        }
     }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.0f);
+}
+
+// A Gaussian's geometry staged in shared memory as four float4 rows (row r of
+// Gaussian i at rows[r][i]): (mean, smax2), M[0..3], M[4..7], (M[8], extra).
+template <int N>
+__device__ __forceinline__ void store_geo(float4 (*rows)[N], int i, const GaussGeo &G, float extra) {
+    rows[0][i] = make_float4(G.mx, G.my, G.mz, G.smax2);
+    rows[1][i] = make_float4(G.M[0], G.M[1], G.M[2], G.M[3]);
+    rows[2][i] = make_float4(G.M[4], G.M[5], G.M[6], G.M[7]);
+    rows[3][i] = make_float4(G.M[8], extra, 0.0f, 0.0f);
+}
+template <int N>
+__device__ __forceinline__ float load_staged_geo(const float4 (*rows)[N], int i, GaussGeo &G) {
+    const float4 a = rows[0][i], b = rows[1][i], c = rows[2][i], d = rows[3][i];
+    G.mx = a.x;
+    G.my = a.y;
+    G.mz = a.z;
+    G.smax2 = a.w;
+    G.M[0] = b.x;
+    G.M[1] = b.y;
+    G.M[2] = b.z;
+    G.M[3] = b.w;
+    G.M[4] = c.x;
+    G.M[5] = c.y;
+    G.M[6] = c.z;
+    G.M[7] = c.w;
+    G.M[8] = d.x;
+    return d.y;
 }
 
 // Mask pass in two phases so that the long exact test runs on full warps:
@@ -329,7 +368,8 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     constexpr int NW = PROJ_THREADS / 32;
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long moff[MAX_GROUP];
-    __shared__ float sgeo[13][PROJ_THREADS];          // mean (3), M (9), smax2
+    // per Gaussian, as float4 rows: (mean, smax2), M[0..3], M[4..7], (M[8], -)
+    __shared__ float4 sgeo[4][PROJ_THREADS];
     __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane (camera < 64)
     __shared__ uint32_t smask[NW][MAX_GROUP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -351,12 +391,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
         for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
     }
-    sgeo[0][tid] = G.mx;
-    sgeo[1][tid] = G.my;
-    sgeo[2][tid] = G.mz;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sgeo[3 + k][tid] = G.M[k];
-    sgeo[12][tid] = G.smax2;
+    store_geo(sgeo, tid, G, 0.0f);
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
     int nq = 0;  // queued pairs of this warp (warp-uniform)
@@ -369,12 +404,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
             cam = e >> 5;
             const int gl = warp * 32 + (e & 31);
             GaussGeo H;
-            H.mx = sgeo[0][gl];
-            H.my = sgeo[1][gl];
-            H.mz = sgeo[2][gl];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) H.M[k] = sgeo[3 + k][gl];
-            H.smax2 = sgeo[12][gl];
+            load_staged_geo(sgeo, gl, H);
             Proj pr;
             surv = project(load_cam(cp[cam]), H, P, pr);
             if (surv) atomicOr(&smask[warp][cam], 1u << (e & 31));
@@ -468,19 +498,32 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
     constexpr int NE = MAX_GROUP * (WG / 32);  // (camera, mask word) entries
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long soff[MAX_GROUP];
-    __shared__ float sgeo[14][WG];  // mean (3), M (9), smax2, log2(opacity)
+    __shared__ float4 sgeo[4][WG];  // geometry rows (store_geo), extra = log2(opacity)
     __shared__ uint32_t smask[NE], swoff[NE];
     __shared__ uint16_t items[MAX_GROUP * WG];
     __shared__ uint32_t wtot[NE / 32];
-    extern __shared__ float shs[];  // SH: [(3k + ch)][WG]
+    extern __shared__ float4 shq[];  // SH: float4 rows [flat index / 4][WG] (sh_colour)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SceneDev sc = scenes[gr.scene];
     const int nwords = (int)min((long long)(WG / 32), (gr.n - g0 + 31) >> 5);
-    // 1. stage: cameras, the block's Gaussians, their SH rows and all mask words
-    if (tid < gr.ncam) {
-        const CamInfo ci = cams[gr.slot0 + tid];
-        cam_setup(cp[tid], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H, P.guard);
-        soff[tid] = ci.seg_off;
+    // 1. stage: cameras, the block's Gaussians, their SH rows and all mask
+    // words, in two rounds of global loads. Round 1: the CamInfo of this
+    // thread's (camera, mask word) entry and (threads < WG) its Gaussian's
+    // attributes. Round 2, issued together: its share of the SH rows, the mask
+    // word and its offset, and (one thread per camera) the view matrix and
+    // intrinsics.
+    static_assert(NE == PROJ_THREADS, "one (camera, mask word) entry per thread");
+    const int cl = tid >> 2, wq = tid & 3;
+    const bool cam_ok = cl < gr.ncam;
+    long long c_moff = 0, c_soff = 0;
+    int c_user = 0, c_W = 0, c_H = 0;
+    if (cam_ok) {
+        const CamInfo *ci = cams + gr.slot0 + cl;
+        c_moff = ci->mask_off;
+        c_soff = ci->seg_off;
+        c_user = ci->user;
+        c_W = ci->W;
+        c_H = ci->H;
     }
     if (tid < WG) {
         const long long g = g0 + tid;
@@ -494,56 +537,54 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
 #pragma unroll
             for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
         }
-        sgeo[0][tid] = G.mx;
-        sgeo[1][tid] = G.my;
-        sgeo[2][tid] = G.mz;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) sgeo[3 + k][tid] = G.M[k];
-        sgeo[12][tid] = G.smax2;
-        sgeo[13][tid] = lg2_a(opacity);
-    } else {
-        // entries e = 4 * camera + word
-        for (int e = tid - WG; e < NE; e += PROJ_THREADS - WG) {
-            const int cl = e >> 2, w = e & 3;
-            uint32_t m = 0, wo = 0;
-            if (cl < gr.ncam && w < nwords) {
-                const long long at = cams[gr.slot0 + cl].mask_off + (g0 >> 5) + w;
-                m = masks[at];
-                wo = woff[at];
-            }
-            smask[e] = m;
-            swoff[e] = wo;
-        }
+        store_geo(sgeo, tid, G, lg2_a(opacity));
     }
-    {
-        // SH rows: one coalesced segment of WG values per (coefficient, channel);
-        // eight loads in flight per thread before the shared-memory stores
-        const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
-        auto stage = [&](auto tag) {
-            using T = decltype(tag);
-            constexpr int BATCH = 8;
-            for (int i0 = tid; i0 < K3 * WG; i0 += BATCH * PROJ_THREADS) {
-                float v[BATCH];
+    // SH: thread t stages Gaussian t % WG in float4 rows t / WG, t / WG + 2, ...
+    // (four coefficient rows each; loads coalesced over consecutive Gaussians)
+    constexpr int RSTEP = PROJ_THREADS / WG, SH_Q = 12 / RSTEP;  // float4 rows per thread
+    const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
+    const int nq = (K3 + 3) / 4;
+    const int sl = tid % WG;
+    float4 shv[SH_Q];
+    auto sh_load = [&](auto tag) {
+        using T = decltype(tag);
+        const long long g = g0 + sl;
 #pragma unroll
-                for (int u = 0; u < BATCH; ++u) {
-                    const int i = i0 + u * PROJ_THREADS;
-                    const int k = i / WG, j = i - k * WG;
-                    const long long g = g0 + j;
-                    v[u] = (i < K3 * WG && g < gr.n) ? ldt<T>(sc.sh, (long long)k * sc.n + g) : 0.0f;
-                }
+        for (int u = 0; u < SH_Q; ++u) {
+            const int r = tid / WG + RSTEP * u;
+            float v[4];
 #pragma unroll
-                for (int u = 0; u < BATCH; ++u) {
-                    const int i = i0 + u * PROJ_THREADS;
-                    if (i < K3 * WG) shs[i] = v[u];
-                }
+            for (int j = 0; j < 4; ++j) {
+                const int i = 4 * r + j;
+                v[j] = (i < K3 && g < gr.n) ? ldt<T>(sc.sh, (long long)i * sc.n + g) : 0.0f;
             }
-        };
-        if (sc.app_dtype == DT_F32)
-            stage(float{});
-        else if (sc.app_dtype == DT_F16)
-            stage(__half{});
-        else
-            stage(__nv_bfloat16{});
+            shv[u] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    };
+    if (sc.app_dtype == DT_F32)
+        sh_load(float{});
+    else if (sc.app_dtype == DT_F16)
+        sh_load(__half{});
+    else
+        sh_load(__nv_bfloat16{});
+    {
+        uint32_t m = 0, wo = 0;
+        if (cam_ok && wq < nwords) {
+            const long long at = c_moff + (g0 >> 5) + wq;
+            m = masks[at];
+            wo = woff[at];
+        }
+        if (cam_ok && wq == 0) {
+            cam_setup(cp[cl], vms + 16LL * c_user, intr + 4LL * c_user, c_W, c_H, P.guard);
+            soff[cl] = c_soff;
+        }
+        smask[tid] = m;
+        swoff[tid] = wo;
+    }
+#pragma unroll
+    for (int u = 0; u < SH_Q; ++u) {
+        const int r = tid / WG + RSTEP * u;
+        if (r < nq) shq[r * WG + sl] = shv[u];
     }
     __syncthreads();
     // 2. item positions: exclusive prefix of the entries' popcounts
@@ -583,13 +624,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
         const int e = c * 4 + w;
         const uint32_t slot = swoff[e] + __popc(smask[e] & ((1u << bit) - 1u));
         GaussGeo G;
-        G.mx = sgeo[0][local];
-        G.my = sgeo[1][local];
-        G.mz = sgeo[2][local];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) G.M[k] = sgeo[3 + k][local];
-        G.smax2 = sgeo[12][local];
-        const float log2o = sgeo[13][local];
+        const float log2o = load_staged_geo(sgeo, local, G);
         const CamProj cam = load_cam(cp[c]);
         Proj pr;
         if (!project(cam, G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
@@ -600,7 +635,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
             pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
         }
         float rgb[3];
-        sh_colour(shs, sc.deg, local, cam, G, rgb);
+        sh_colour<WG>(shq, sc.deg, local, cam, G, rgb);
         // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o/alpha_min):
         // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
         // rounding of the per-pixel test can never pass a pixel outside it
@@ -657,7 +692,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  float ln_alpha_min, const int *status, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(2 * max_blocks_x, n_groups);  // 128 Gaussians per block
-    const int smem = 48 * WG * (int)sizeof(float);         // SH of degree <= 3
+    const int smem = 12 * WG * (int)sizeof(float4);        // SH of degree <= 3
     cudaError_t e = cudaFuncSetAttribute(k_project_write,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
