@@ -271,11 +271,11 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     const long long S = std::max<long long>(ctx->cap_survivors, 1);
     const size_t Sx = (size_t)S;
     const int m = std::max(P.max_m, 1);
-    const bool changed = (ctx->rec.cap < Sx * sizeof(SlotRec));
+    const bool changed = (ctx->rec.cap < rec_bytes(S));
     CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->woff, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->counts, (size_t)m * sizeof(int)));
-    CKS(grow(ctx, ctx->rec, Sx * sizeof(SlotRec)));
+    CKS(grow(ctx, ctx->rec, rec_bytes(S)));
     CKS(grow(ctx, ctx->srect, Sx * sizeof(uint2)));
     CKS(grow(ctx, ctx->rrect, Sx * sizeof(uint2)));
     CKS(grow(ctx, ctx->keys, Sx * 4));
@@ -316,6 +316,9 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
     long long *need = (long long *)ctx->status.p;               // [0]: largest chunk
     int *status_all = (int *)((long long *)ctx->status.p + 1);  // [k]: chunk k overflowed
     unsigned long long *stats = (unsigned long long *)ctx->stats.p;
+    // records: the render writes fields a, b, c; the debug stages also d
+    float4 *recs = (float4 *)ctx->rec.p;
+    const int with_d = a.upto != UPTO_ALL;
     int tp = 0;
     for (size_t k = 0; k < P.chunks.size(); ++k) {
         const ChunkPlan &ch = P.chunks[k];
@@ -339,7 +342,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(cudaMemsetAsync(wide, 0, sizeof(int), st));
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
                                  cams, a.vm, a.in, PP, (const uint32_t *)ctx->masks.p,
-                                 (const uint32_t *)ctx->woff.p, (SlotRec *)ctx->rec.p,
+                                 (const uint32_t *)ctx->woff.p, recs, with_d,
                                  (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p, wide,
                                  std::log(cfg.alpha_min), status, st));
         if (E) CKC(cudaEventRecord(E[1], st));
@@ -358,7 +361,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                        (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
         if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;
-        CKC(launch_composite(cams, tilepre, ch.m, ch.tiles_total, (const SlotRec *)ctx->rec.p,
+        CKC(launch_composite(cams, tilepre, ch.m, ch.tiles_total, recs,
                              (const uint32_t *)ctx->tvals.p, (const uint2 *)ctx->rrect.p,
                              (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
                              cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,
@@ -950,6 +953,19 @@ gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
     return GS_OK;
 }
 
+// The first S records of the last render (all four fields) to the host.
+static gs_status copy_records(gs_context *ctx, long long S, std::vector<SlotRec> &out) {
+    if (S == 0) return GS_OK;
+    std::vector<float4> raw(rec_bytes(S) / sizeof(float4));
+    CKC(cudaMemcpy(raw.data(), ctx->rec.p, rec_bytes(S), cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < S; ++i) {
+        uint4 d;
+        memcpy(&d, &raw[rec_d(i)], sizeof(d));
+        out[i] = SlotRec{raw[rec_a(i)], raw[rec_b(i)], raw[rec_c(i)], d};
+    }
+    return GS_OK;
+}
+
 gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewmat,
                            const float *intrinsics, int32_t width, int32_t height, float *rec,
                            int32_t *gidx, int32_t *rect, int64_t cap, int64_t *n_out,
@@ -970,7 +986,7 @@ gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewm
     *n_out = S;
     if (S > cap) return fail(ctx, GS_ERR_CAPACITY, "%lld survivors > cap %lld", S, (long long)cap);
     std::vector<SlotRec> h((size_t)S);
-    if (S) CKC(cudaMemcpy(h.data(), ctx->rec.p, S * sizeof(SlotRec), cudaMemcpyDeviceToHost));
+    CKS(copy_records(ctx, S, h));
     const float L2E = 1.4426950408889634f;
     for (long long i = 0; i < S; ++i) {
         const SlotRec &R = h[i];
@@ -1021,7 +1037,7 @@ gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *vi
     std::vector<uint32_t> vals((size_t)S), bm((size_t)SX * SY * nw);
     std::vector<uint2> rr((size_t)S);
     if (S) {
-        CKC(cudaMemcpy(rec.data(), ctx->rec.p, S * sizeof(SlotRec), cudaMemcpyDeviceToHost));
+        CKS(copy_records(ctx, S, rec));
         CKC(cudaMemcpy(vals.data(), ctx->tvals.p, S * 4, cudaMemcpyDeviceToHost));
         CKC(cudaMemcpy(rr.data(), ctx->rrect.p, S * sizeof(uint2), cudaMemcpyDeviceToHost));
         CKC(cudaMemcpy(bm.data(), ctx->bitmap.p, bm.size() * 4, cudaMemcpyDeviceToHost));

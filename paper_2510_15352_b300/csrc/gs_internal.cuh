@@ -65,7 +65,7 @@ struct Group {
     long long n;
 };
 
-// A survivor's record (64 B), written by the projection pass in slot order
+// A survivor's record, written by the projection pass in slot order
 // (Gaussian-index order within the camera), in the form the compositing pass
 // reads, with the constants folded so that p = a'dx^2 + b'dx dy + c'dy^2 + log2 o
 // is log2(o e^power):
@@ -75,10 +75,24 @@ struct Group {
 //   b: a' = -log2(e)/2 A, b' = -log2(e) B, c' = -log2(e)/2 C, log2(o)
 //   c: red, green, blue, z
 //   d: x0 | x1 << 16, y0 | y1 << 16 (tile rect), Gaussian index, radius (bits)
+// Layout in memory: blocks of 32 slots (2 KB), each holding the (a, b) pairs of
+// its 32 slots, then their c, then their d. A warp writing consecutive slots
+// writes each field as one contiguous run (coalesced stores), and a reader
+// finds a and b of a slot in one 32-byte sector. (Plain 64-byte records in
+// slot order made the projection's strided stores the bottleneck of its L1
+// traffic; one array per field made the compositing pass touch three lines
+// per record.) The render writes a, b and c only (the rect also goes to its own
+// array); d is written for the debug entry points.
 struct __align__(16) SlotRec {
     float4 a, b, c;
     uint4 d;
 };
+// float4 index of field a, b, c, d of slot s
+__host__ __device__ inline long long rec_a(long long s) { return 4 * (s & ~31LL) + 2 * (s & 31); }
+__host__ __device__ inline long long rec_b(long long s) { return rec_a(s) + 1; }
+__host__ __device__ inline long long rec_c(long long s) { return 4 * (s & ~31LL) + 64 + (s & 31); }
+__host__ __device__ inline long long rec_d(long long s) { return 4 * (s & ~31LL) + 96 + (s & 31); }
+inline size_t rec_bytes(long long slots) { return (size_t)((slots + 31) / 32) * 32 * sizeof(SlotRec); }
 
 constexpr int STILE = 4;  // tiles per super-tile edge (64 x 64 pixels)
 constexpr int SORT_TILE_KEYS = 2048;  // keys per sort tile
@@ -98,7 +112,7 @@ cudaError_t launch_scan_masks(const CamInfo *cams, const SceneDev *scenes, int n
 cudaError_t launch_project_write(const Group *groups, int n_groups, int max_blocks_x,
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
-                                 const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
+                                 const uint32_t *masks, const uint32_t *woff, float4 *rec, int rec_d,
                                  uint2 *srect, uint32_t *keys, int *wide,
                                  float ln_alpha_min, const int *status, cudaStream_t s);
 
@@ -152,7 +166,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, 
 // of tiles (8 pixels per thread). tile_prefix / n_tiles count the blocks: tiles
 // or quads per camera.
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
-                             int n_tiles, const SlotRec *rec, const uint32_t *vals,
+                             int n_tiles, const float4 *rec, const uint32_t *vals,
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,

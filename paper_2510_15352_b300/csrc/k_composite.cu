@@ -76,7 +76,7 @@ __device__ __forceinline__ float max_p_rect(float u, float v, float a, float b, 
 template <int PPT, bool STATS>
 __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
-                int n_slots, const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
+                int n_slots, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                 const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
                 CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
                 float *__restrict__ finalT, unsigned long long *__restrict__ stats,
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     unsigned long long ev = 0, al = 0, wi = 0, wbox = 0, wbl = 0;
 
     const uint32_t *bm = bitmap + ci.bm_off + (long long)((ty / STILE) * SX + tx / STILE) * ci.nw;
-    const SlotRec *recs = rec + ci.seg_off;
+    const long long rec0 = ci.seg_off;
     const uint32_t *cv = vals + ci.seg_off;
     const uint2 *crr = rrect + ci.seg_off;
     for (int wb = 0; wb < ci.nw; wb += NT) {
@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
         for (uint32_t j0 = 0; j0 < nkept; j0 += COMP_BATCH) {
             const int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
             for (int q = tid; q < nb; q += NT) {
-                const SlotRec &R = recs[cv[cand[j0 + q]]];
-                const float4 a = R.a, b = R.b, cc = R.c;
+                const long long sl = rec0 + cv[cand[j0 + q]];
+                const float4 a = rec[rec_a(sl)], b = rec[rec_b(sl)], cc = rec[rec_c(sl)];
                 // warps some pixel of which can pass the alpha test: the box of the
                 // alpha >= alpha_min region meets the warp's rows and the largest p
                 // over the rows' pixel-centre rectangle reaches the threshold (with a
@@ -335,7 +335,7 @@ finished:
 template <bool STATS>
 __global__ void __launch_bounds__(128)
     k_composite_quad(const CamInfo *__restrict__ cams, const int *__restrict__ quad_prefix,
-                     int n_slots, const SlotRec *__restrict__ rec, const uint32_t *__restrict__ vals,
+                     int n_slots, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                      const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
                      CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
                      float *__restrict__ finalT, unsigned long long *__restrict__ stats,
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(128)
     unsigned long long ev = 0, al = 0, wi = 0, wbox = 0, wbl = 0;
 
     const uint32_t *bm = bitmap + ci.bm_off + (long long)((2 * qy / STILE) * SX + 2 * qx / STILE) * ci.nw;
-    const SlotRec *recs = rec + ci.seg_off;
+    const long long rec0 = ci.seg_off;
     const uint32_t *cv = vals + ci.seg_off;
     const uint2 *crr = rrect + ci.seg_off;
     const int qx0 = 2 * qx, qx1 = 2 * qx + 1, qy0 = 2 * qy, qy1 = 2 * qy + 1;
@@ -442,9 +442,10 @@ __global__ void __launch_bounds__(128)
         for (uint32_t j0 = 0; j0 < nkept; j0 += COMP_BATCH) {
             const int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
             for (int q = tid; q < nb; q += NT) {
-                const SlotRec &R = recs[cv[cand[j0 + q]]];
-                const float4 a = R.a, b = R.b, cc = R.c;
-                const uint4 d = R.d;
+                const uint32_t rk = cand[j0 + q];
+                const long long sl = rec0 + cv[rk];
+                const float4 a = rec[rec_a(sl)], b = rec[rec_b(sl)], cc = rec[rec_c(sl)];
+                const uint2 d = crr[rk];  // the record's tile rect (rank order)
                 const int rx0 = (int)(d.x & 0xffffu), rx1 = (int)(d.x >> 16);
                 const int ry0 = (int)(d.y & 0xffffu), ry1 = (int)(d.y >> 16);
                 uint32_t m = 0;
@@ -567,7 +568,7 @@ finished:
 
 template <int PPT>
 cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots, int n_tiles,
-                       const SlotRec *rec, const uint32_t *vals, const uint2 *rrect,
+                       const float4 *rec, const uint32_t *vals, const uint2 *rrect,
                        const uint32_t *bitmap, CompParams C, float *rgb, float *depth,
                        float *final_T, unsigned long long *stats, bool collect,
                        const int *status, cudaStream_t s) {
@@ -585,7 +586,7 @@ cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots,
 }  // namespace
 
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
-                             int n_tiles, const SlotRec *rec, const uint32_t *vals,
+                             int n_tiles, const float4 *rec, const uint32_t *vals,
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,

@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
                     const CamInfo *__restrict__ cams, const float *__restrict__ vms,
                     const float *__restrict__ intr, ProjParams P,
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
-                    SlotRec *__restrict__ rec, uint2 *__restrict__ srect,
+                    float4 *__restrict__ rec, int with_d, uint2 *__restrict__ srect,
                     uint32_t *__restrict__ keys, int *__restrict__ wide,
                     float ln_alpha_min, const int *__restrict__ status) {
     const Group gr = groups[blockIdx.y];
@@ -646,15 +646,15 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
             hy = fmaf(1.002f, sqrt_a(q * pr.sc), 0.02f);
         }
         const long long at = soff[c] + slot;
-        SlotRec R;
-        R.a = make_float4(pr.u, pr.v, hx, hy);
-        R.b = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C, log2o);
-        R.c = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
-        R.d = make_uint4((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
-                         (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16), (uint32_t)(g0 + local),
-                         __float_as_uint(pr.r));
-        rec[at] = R;
-        srect[at] = make_uint2(R.d.x, R.d.y);
+        const uint2 rect = make_uint2((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
+                                      (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16));
+        rec[rec_a(at)] = make_float4(pr.u, pr.v, hx, hy);
+        rec[rec_b(at)] = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C, log2o);
+        rec[rec_c(at)] = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
+        if (with_d)
+            reinterpret_cast<uint4 *>(rec)[rec_d(at)] =
+                make_uint4(rect.x, rect.y, (uint32_t)(g0 + local), __float_as_uint(pr.r));
+        srect[at] = rect;
         // depth key: float bits of z minus those of the near plane (z > near, so
         // non-negative and in the same order); its value, the slot, is implied
         // by the position. Keys of 2^26 or more need the depth sort's 4th pass.
@@ -687,7 +687,7 @@ cudaError_t launch_scan_masks(const CamInfo *cams, const SceneDev *scenes, int n
 cudaError_t launch_project_write(const Group *groups, int n_groups, int max_blocks_x,
                                  const SceneDev *scenes, const CamInfo *cams,
                                  const float *viewmats, const float *intr, ProjParams P,
-                                 const uint32_t *masks, const uint32_t *woff, SlotRec *rec,
+                                 const uint32_t *masks, const uint32_t *woff, float4 *rec, int with_d,
                                  uint2 *srect, uint32_t *keys, int *wide,
                                  float ln_alpha_min, const int *status, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
@@ -697,7 +697,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, viewmats, intr, P,
-                                                     masks, woff, rec, srect, keys, wide,
+                                                     masks, woff, rec, with_d, srect, keys, wide,
                                                      ln_alpha_min, status);
     return cudaGetLastError();
 }
