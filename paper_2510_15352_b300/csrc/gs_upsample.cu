@@ -50,6 +50,12 @@ cudaError_t up_conv_tc(int layer, const __nv_bfloat16 *x, int n, int h, int w,
                        const __nv_bfloat16 *wt, const float *bias, void *out, const float *rgb,
                        const float *lr_depth, float *hr_depth, int *status, int n_sm,
                        cudaStream_t s);
+cudaError_t up_conv_tc_planar(int layer, const __nv_bfloat16 *x, int n, int h, int w,
+                              const __nv_bfloat16 *wt, const float *bias, void *out,
+                              const float *rgb, const float *lr_depth, float *hr_depth,
+                              int *status, int n_sm, cudaStream_t s);
+cudaError_t up_prep_input_plane(const float *rgb, int n, int h, int w, __nv_bfloat16 *x0,
+                                cudaStream_t s);
 }  // namespace gsk
 
 namespace {
@@ -254,7 +260,8 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
         const int m = std::min(group, n - f0);
         const float *rgb = lr_rgb + (size_t)f0 * px * 3;
         float *hr = hr_rgb + (size_t)f0 * px * 48;
-        e = gsk::up_prep_input(rgb, m, h, w, x0, s);
+        // tensor cores: planar activations (one stored input plane); mma.sync: NHWC
+        e = tc ? gsk::up_prep_input_plane(rgb, m, h, w, x0, s) : gsk::up_prep_input(rgb, m, h, w, x0, s);
         const bf16 *in = x0;
         for (int l = 0; l < NL && e == cudaSuccess; ++l) {
             const float *bias = u->params + layer_off(l) + (long long)L_CO[l] * L_CI[l] * 9;
@@ -262,8 +269,9 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
             const float *ldep = lr_depth ? lr_depth + (size_t)f0 * px : nullptr;
             float *hdep = hr_depth ? hr_depth + (size_t)f0 * px * 16 : nullptr;
             if (tc)
-                e = gsk::up_conv_tc(l, in, m, h, w, u->wt[l], bias, l < NL - 1 ? (void *)dst : (void *)hr,
-                                    rgb, ldep, hdep, u->status, u->n_sm, s);
+                e = gsk::up_conv_tc_planar(l, in, m, h, w, u->wt[l], bias,
+                                           l < NL - 1 ? (void *)dst : (void *)hr, rgb, ldep, hdep,
+                                           u->status, u->n_sm, s);
             else if (l < NL - 1)
                 e = gsk::up_conv_forward(l, in, m, h, w, u->wf[l], bias, dst, s);
             else

@@ -374,6 +374,38 @@ __global__ void k_prep_input(const float *__restrict__ rgb, int h, int w, bf16 *
     }
 }
 
+// The same input for the tensor-core inference path, as one plane of the 8
+// stored channels ([n][h][w][8]; channels 8-15 of the padded input are zero
+// and are not stored: that kernel keeps them zero in shared memory).
+__global__ void k_prep_input_plane(const float *__restrict__ rgb, int h, int w, bf16 *__restrict__ x0) {
+    const int y = blockIdx.x % h;
+    const long long rowp = (long long)blockIdx.x * w;
+    const float *row_img = rgb + (rowp - (long long)y * w) * 3;
+    for (int x = threadIdx.x; x < w; x += blockDim.x) {
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+        for (int du = -1; du <= 1; ++du) {
+            const int yy = min(max(y + du, 0), h - 1);
+#pragma unroll
+            for (int dv = -1; dv <= 1; ++dv) {
+                const int xx = min(max(x + dv, 0), w - 1);
+                const float *q = row_img + ((long long)yy * w + xx) * 3;
+                s0 += q[0];
+                s1 += q[1];
+                s2 += q[2];
+            }
+        }
+        const long long p = rowp + x;
+        const float r = rgb[3 * p], g = rgb[3 * p + 1], b = rgb[3 * p + 2];
+        uint4 lo;
+        lo.x = pack_bf16(r - 0.5f, g - 0.5f);
+        lo.y = pack_bf16(b - 0.5f, DETAIL_S * (r - s0 / 9.0f));
+        lo.z = pack_bf16(DETAIL_S * (g - s1 / 9.0f), DETAIL_S * (b - s2 / 9.0f));
+        lo.w = 0u;
+        *(uint4 *)(x0 + 8 * p) = lo;
+    }
+}
+
 // Loss of the training pass: out = bilinear(rgb) + shuffle(z) / S; per LR pixel
 // and channel, dz = 2 (out - target) / (count S) (BF16) and sum (out - target)^2 / count.
 __global__ void __launch_bounds__(256)
@@ -516,6 +548,13 @@ cudaError_t up_prep_input(const float *rgb, int n, int h, int w, __nv_bfloat16 *
                           cudaStream_t s) {
     if ((long long)n * h == 0) return cudaSuccess;
     k_prep_input<<<n * h, std::min(256, (w + 31) / 32 * 32), 0, s>>>(rgb, h, w, x0);
+    return cudaGetLastError();
+}
+
+cudaError_t up_prep_input_plane(const float *rgb, int n, int h, int w, __nv_bfloat16 *x0,
+                                cudaStream_t s) {
+    if ((long long)n * h == 0) return cudaSuccess;
+    k_prep_input_plane<<<n * h, std::min(256, (w + 31) / 32 * 32), 0, s>>>(rgb, h, w, x0);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,10 @@
 // upsampling from the pixel's 3 x 3 LR neighbourhood). Every mbarrier wait is
 // bounded; on time-out the block records the error in the status word and
 // leaves, releasing its tensor memory.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
+
 #include <algorithm>
+#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -166,7 +169,11 @@ __host__ __device__ constexpr int tmem_cols() {  // two accumulators (double buf
 //            UPSAMPLE  out f32 HR image (+ depth)           (last layer, inference)
 //            LINEAR    out f32 = acc + bias, 48 channels    (last layer, training)
 //            GATE      out bf16 = acc * (gate > 0)          (backward data pass)
-enum : int { TC_EPI_RELU = 0, TC_EPI_UPSAMPLE = 1, TC_EPI_LINEAR = 2, TC_EPI_GATE = 3 };
+//            RELU_P    out bf16 = relu(acc + bias), planar   (hidden layers, inference)
+// Planar activations: [n][C / 8][h][w][8] -- one plane per 8 channels, so a
+// tile's plane is a 2-D box of 16-byte pixels for the tensor-memory-access
+// (TMA) unit, and a warp's stores of one plane are contiguous runs.
+enum : int { TC_EPI_RELU = 0, TC_EPI_UPSAMPLE = 1, TC_EPI_LINEAR = 2, TC_EPI_GATE = 3, TC_EPI_RELU_P = 4 };
 
 // Shared memory of a block: two input-tile buffers (the next tile is fetched
 // while the current one is multiplied), the weights, for the upsampling layer
@@ -209,7 +216,7 @@ __device__ __forceinline__ TileXY tile_xy(long long tile, int tx, int ty) {
 
 // Issues the asynchronous copies of one tile's input (and for the upsampling
 // layer its LR colours and depth, edge-clamped).
-template <int CIN, int EPI>
+template <int CIN, int EPI, bool PLANAR>
 __device__ __forceinline__ void fetch_tile(const bf16 *__restrict__ x, const float *__restrict__ rgb,
                                            const float *__restrict__ dep, int h, int w, TileXY t,
                                            unsigned char *xs, float *ls) {
@@ -218,7 +225,9 @@ __device__ __forceinline__ void fetch_tile(const bf16 *__restrict__ x, const flo
         const int c8 = i / TC_PIN, pos = i - c8 * TC_PIN;
         const int yy = t.by - 1 + pos / TC_PW, xx = t.bx - 1 + pos % TC_PW;
         const bool in = pos < TC_ROWS_IN * TC_PW && yy >= 0 && yy < h && xx >= 0 && xx < w;
-        const bf16 *src = in ? x + (((long long)t.img * h + yy) * w + xx) * CIN + c8 * 8 : x;
+        const bf16 *src = !in ? x
+                          : PLANAR ? x + ((((long long)t.img * C8 + c8) * h + yy) * w + xx) * 8
+                                   : x + (((long long)t.img * h + yy) * w + xx) * CIN + c8 * 8;
         cp_async16(smem_u32(xs + (size_t)i * 16), src, in);
     }
     if (EPI == TC_EPI_UPSAMPLE) {
@@ -295,6 +304,21 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t dcol, Tile
                         ow[r] = pack2(a, b);
                     }
                     dst[q] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+                }
+            }
+        } else if (EPI == TC_EPI_RELU_P) {
+            float v[32];
+            tmem_ld32(taddr, v);
+            if (valid) {
+                bf16 *o = (bf16 *)out;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 r;
+                    r.x = pack2(fmaxf(v[8 * q + 0] + bs[8 * q + 0], 0.f), fmaxf(v[8 * q + 1] + bs[8 * q + 1], 0.f));
+                    r.y = pack2(fmaxf(v[8 * q + 2] + bs[8 * q + 2], 0.f), fmaxf(v[8 * q + 3] + bs[8 * q + 3], 0.f));
+                    r.z = pack2(fmaxf(v[8 * q + 4] + bs[8 * q + 4], 0.f), fmaxf(v[8 * q + 5] + bs[8 * q + 5], 0.f));
+                    r.w = pack2(fmaxf(v[8 * q + 6] + bs[8 * q + 6], 0.f), fmaxf(v[8 * q + 7] + bs[8 * q + 7], 0.f));
+                    *(uint4 *)(o + ((((long long)t.img * 4 + q) * h + yy) * w + xx) * 8) = r;
                 }
             }
         } else if (EPI == TC_EPI_RELU) {
@@ -395,7 +419,7 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tmem, uint32_t dcol, Tile
     }
 }
 
-template <int CIN, int COUT, int EPI>
+template <int CIN, int COUT, int EPI, bool PLANAR = false>
 __global__ void __launch_bounds__(TC_THREADS)
     k_conv_tc(const bf16 *__restrict__ x, int n, int h, int w, const bf16 *__restrict__ wt,
               const float *__restrict__ bias, void *__restrict__ out,
@@ -420,7 +444,7 @@ __global__ void __launch_bounds__(TC_THREADS)
 
     // the first two tiles' inputs in flight while the weights are staged
     if (blockIdx.x < n_tiles)
-        fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x, tx, ty), xbuf(0), lbuf(0));
+        fetch_tile<CIN, EPI, PLANAR>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x, tx, ty), xbuf(0), lbuf(0));
     for (int i = tid; i < (int)(L::w_bytes / 16); i += TC_THREADS)
         ((uint4 *)ws)[i] = ((const uint4 *)wt)[i];
     for (int i = tid; i < COUT; i += TC_THREADS) bs[i] = bias ? bias[i] : 0.0f;
@@ -477,7 +501,7 @@ __global__ void __launch_bounds__(TC_THREADS)
         __syncwarp();
         if (k == 0) {
             if (blockIdx.x + G < n_tiles)
-                fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x + G, tx, ty), xbuf(1), lbuf(1));
+                fetch_tile<CIN, EPI, PLANAR>(x, rgb, lr_depth, h, w, tile_xy(blockIdx.x + G, tx, ty), xbuf(1), lbuf(1));
         } else {
             const int j = (int)((k - 1) & 1);
             const bool ok = mbar_wait(smem_u32(bar + j), (phase_bits >> j) & 1u, spin_limit);
@@ -489,7 +513,7 @@ __global__ void __launch_bounds__(TC_THREADS)
             fence_after();
             // tile k + 1 into the buffer the finished MMAs of tile k - 1 read
             if (tile + G < n_tiles)
-                fetch_tile<CIN, EPI>(x, rgb, lr_depth, h, w, tile_xy(tile + G, tx, ty), xbuf(k + 1), lbuf(k + 1));
+                fetch_tile<CIN, EPI, PLANAR>(x, rgb, lr_depth, h, w, tile_xy(tile + G, tx, ty), xbuf(k + 1), lbuf(k + 1));
             tile_epilogue<COUT, EPI>(tmem, (uint32_t)(j * ACC), tile_xy(tile - G, tx, ty), h, w, bs,
                                      lbuf(k - 1), out, hr_depth, gate);
         }
@@ -513,13 +537,290 @@ __global__ void __launch_bounds__(TC_THREADS)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL));
 }
 
-template <int CIN, int COUT, int EPI>
+// ---- hidden layers: warp-specialised TMA + tcgen05 pipeline ----
+//
+// Persistent blocks (WS_BPS per SM) walk their tiles (blockIdx.x, + gridDim.x,
+// ...) with three roles that meet only at mbarriers:
+//   warp 4, one lane  -- TMA producer: per tile, one 4-D tensor load per plane
+//                        of the planar input (box 8 ch x 18 x 17 at (x - 1,
+//                        y - 1); the halo outside the image is the zero fill)
+//                        into stage i % WS_NS, signalled on full[stage]. The
+//                        first layer's input has one stored plane (6 real
+//                        channels); its second plane stays zero in shared memory;
+//   warp 5, one lane  -- MMA issuer: waits for full[stage] and for the
+//                        accumulator set i % WS_NA to be drained, issues the
+//                        9 taps x CIN/16 x 2 M-tiles MMAs, commits to
+//                        empty[stage] (the stage may be refilled) and to
+//                        accf[set];
+//   warps 0-3         -- epilogue: wait for accf[set], read TMEM lanes
+//                        32 w .. 32 w + 31, write relu(acc + bias) as BF16
+//                        planes, arrive on acce[set].
+// WS_BPS x WS_NS input tiles are in flight per SM, and two blocks' MMA streams
+// keep the tensor pipe busy: with N = 32 output channels an MMA is short, and
+// one issuer alone left gaps (1,024 frames at 160x120: 7.1 ms for the network
+// with one block of 8 stages per SM, 5.1 ms with two blocks of 3 stages; three
+// blocks of 2 stages 5.1 ms). Every wait is bounded
+// and also gives up once another role has failed; then the block records the
+// error in the status word, waits for its own loads and MMAs and frees its
+// tensor memory.
+constexpr int WS_THREADS = 192;
+constexpr int WS_NS = 3;   // input stages
+constexpr int WS_NA = 4;   // accumulator sets (2 M-tiles x 32 columns each)
+constexpr int WS_BPS = 2;  // resident blocks per SM
+constexpr int WS_COLS = WS_NA * 64 <= 128 ? 128 : 256;
+static_assert(WS_NA * 64 <= WS_COLS && WS_BPS * WS_COLS <= 512, "accumulators fit tensor memory");
+
+template <int CIN>
+struct WsSmem {
+    static constexpr size_t stage_bytes = (size_t)(CIN / 8) * TC_PIN * 16;
+    static constexpr size_t w_bytes = (size_t)9 * CIN * 32 * 2;
+    static constexpr size_t off_w = WS_NS * stage_bytes;
+    static constexpr size_t off_bias = off_w + w_bytes;
+    static constexpr size_t off_bar = off_bias + 32 * 4;
+    // full[WS_NS], empty[WS_NS], accf[WS_NA], acce[WS_NA], drain
+    static constexpr int n_bar = 2 * WS_NS + 2 * WS_NA + 1;
+    static constexpr size_t off_misc = off_bar + (size_t)n_bar * 8;  // TMEM slot, abort flag
+    static constexpr size_t total = off_misc + 16;
+};
+
+// Bounded wait that also gives up when *abort is set.
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, long long limit,
+                                        const volatile int *abort) {
+    for (long long i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 31) == 31 && *abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void ws_fail(volatile int *abort, int *status) {
+    *abort = 1;
+    atomicOr(status, 1);
+}
+
+template <int CIN>
+__global__ void __launch_bounds__(WS_THREADS)
+    k_conv_ws(const __grid_constant__ CUtensorMap xmap, int n, int h, int w,
+              const bf16 *__restrict__ wt, const float *__restrict__ bias, bf16 *__restrict__ out,
+              int *__restrict__ status, long long spin_limit, int no_commit_first) {
+    using L = WsSmem<CIN>;
+    constexpr int C8 = CIN / 8;
+    constexpr int CL = CIN == 16 ? 1 : C8;  // planes stored in memory (and loaded) per image
+    constexpr uint32_t IDESC = idesc_bf16(128, 32);
+    constexpr uint32_t STAGE_TX = (uint32_t)CL * 8 * TC_PW * TC_ROWS_IN * 2;  // bytes per tile
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *ws = smem + L::off_w;
+    float *bs = (float *)(smem + L::off_bias);
+    uint64_t *bar = (uint64_t *)(smem + L::off_bar);
+    uint64_t *full = bar, *empty = bar + WS_NS, *accf = bar + 2 * WS_NS, *acce = accf + WS_NA;
+    uint64_t *drain = acce + WS_NA;
+    uint32_t *tslot = (uint32_t *)(smem + L::off_misc);
+    volatile int *abort = (volatile int *)(smem + L::off_misc + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx = (w + TC_TW - 1) / TC_TW, ty = (h + TC_TH - 1) / TC_TH;
+    const long long n_tiles = (long long)tx * ty * n;
+    const long long G = gridDim.x;
+    auto stage = [&](long long i) { return smem + (size_t)(i % WS_NS) * L::stage_bytes; };
+
+    for (int i = tid; i < (int)(L::w_bytes / 16); i += WS_THREADS)
+        ((uint4 *)ws)[i] = ((const uint4 *)wt)[i];
+    for (int i = tid; i < 32; i += WS_THREADS) bs[i] = bias ? bias[i] : 0.0f;
+    // planes that are not loaded (the first layer's channels 8-15) are zero
+    for (int st = 0; st < WS_NS; ++st)
+        for (int i = tid; i < (C8 - CL) * TC_PIN; i += WS_THREADS)
+            ((uint4 *)(smem + (size_t)st * L::stage_bytes + (size_t)CL * TC_PIN * 16))[i] =
+                make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int b = 0; b < L::n_bar; ++b) {
+            const uint32_t cnt = (b >= 2 * WS_NS + WS_NA && b < 2 * WS_NS + 2 * WS_NA) ? 4u : 1u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + b)), "r"(cnt));
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(WS_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    // the weights were written by the generic proxy; the MMAs read them through
+    // the async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        // ---- TMA producer
+        long long issued = 0;
+        if (lane == 0) {
+            for (long long i = 0;; ++i) {
+                const long long tile = blockIdx.x + i * G;
+                if (tile >= n_tiles) break;
+                const int s = (int)(i % WS_NS);
+                if (i >= WS_NS &&
+                    !ws_wait(smem_u32(empty + s), (uint32_t)((i / WS_NS - 1) & 1), spin_limit, abort)) {
+                    ws_fail(abort, status);
+                    break;
+                }
+                const TileXY t = tile_xy(tile, tx, ty);
+                const uint32_t fb = smem_u32(full + s);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb),
+                             "r"(STAGE_TX)
+                             : "memory");
+#pragma unroll
+                for (int c8 = 0; c8 < CL; ++c8)
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(
+                            smem_u32(stage(i) + (size_t)c8 * TC_PIN * 16)),
+                        "l"((uint64_t)&xmap), "r"(0), "r"(t.bx - 1), "r"(t.by - 1), "r"(t.img * CL + c8),
+                        "r"(fb)
+                        : "memory");
+                issued = i + 1;
+            }
+            // every load this block started has landed before the block leaves
+            // (after a failure some were never consumed)
+            for (long long i = issued > WS_NS ? issued - WS_NS : 0; i < issued; ++i)
+                mbar_wait(smem_u32(full + i % WS_NS), (uint32_t)((i / WS_NS) & 1), TC_SPIN_LIMIT);
+        }
+    } else if (warp == 5) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint64_t b0 = sdesc(smem_u32(ws), 32 * 16, 128);
+            long long done = 0;  // tiles whose MMAs were issued and committed
+            for (long long i = 0;; ++i) {
+                const long long tile = blockIdx.x + i * G;
+                if (tile >= n_tiles) break;
+                const int s = (int)(i % WS_NS), a = (int)(i % WS_NA);
+                if (!ws_wait(smem_u32(full + s), (uint32_t)((i / WS_NS) & 1), spin_limit, abort) ||
+                    (i >= WS_NA &&
+                     !ws_wait(smem_u32(acce + a), (uint32_t)((i / WS_NA - 1) & 1), spin_limit, abort))) {
+                    ws_fail(abort, status);
+                    break;
+                }
+                fence_after();
+                const uint64_t a0 = sdesc(smem_u32(stage(i)), TC_PIN * 16, 128);
+                const uint32_t d = tmem + (uint32_t)(a * 2 * 32);
+#pragma unroll
+                for (int m = 0; m < TC_MT; ++m)
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                        for (int ks = 0; ks < CIN / 16; ++ks)
+                            mma_bf16(d + (uint32_t)(m * 32),
+                                     a0 + (uint64_t)(2 * ks * TC_PIN + m * 128 + (tap / 3) * TC_PW + tap % 3),
+                                     b0 + (uint64_t)((tap * C8 + 2 * ks) * 32), IDESC, (tap | ks) ? 1u : 0u);
+                mma_commit(smem_u32(empty + s));
+                // (test hook: the first tile's completion is never signalled, so
+                // the epilogue's wait for it gives up and the failure path runs)
+                if (!(no_commit_first && i == 0)) mma_commit(smem_u32(accf + a));
+                done = i + 1;
+            }
+            // Before the block leaves: every MMA has completed (one more commit
+            // tracks all of them) and every commit has arrived on its barrier
+            // (after a failure some were never waited for).
+            mma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0u, TC_SPIN_LIMIT);
+            for (long long i = done > WS_NS ? done - WS_NS : 0; i < done; ++i)
+                mbar_wait(smem_u32(empty + i % WS_NS), (uint32_t)((i / WS_NS) & 1), TC_SPIN_LIMIT);
+            for (long long i = done > WS_NA ? done - WS_NA : 0; i < done; ++i)
+                if (!(no_commit_first && i == 0))
+                    mbar_wait(smem_u32(accf + i % WS_NA), (uint32_t)((i / WS_NA) & 1), TC_SPIN_LIMIT);
+        }
+    } else {
+        // ---- epilogue (warps 0-3)
+        for (long long i = 0;; ++i) {
+            const long long tile = blockIdx.x + i * G;
+            if (tile >= n_tiles) break;
+            const int a = (int)(i % WS_NA);
+            const bool ok = ws_wait(smem_u32(accf + a), (uint32_t)((i / WS_NA) & 1), spin_limit, abort);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) ws_fail(abort, status);
+                break;
+            }
+            fence_after();
+            tile_epilogue<32, TC_EPI_RELU_P>(tmem, (uint32_t)(a * 2 * 32), tile_xy(tile, tx, ty), h, w, bs,
+                                             nullptr, out, nullptr, nullptr);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + a)) : "memory");
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 5)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(WS_COLS));
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+template <int CIN>
+cudaError_t run_ws(const bf16 *x, int n, int h, int w, const bf16 *wt, const float *bias, bf16 *out,
+                   int *status, int n_sm, cudaStream_t s, long long spin_limit = TC_SPIN_LIMIT,
+                   int no_commit_first = 0) {
+    using L = WsSmem<CIN>;
+    static_assert(WS_BPS * (L::total + 1024) <= (size_t)228 * 1024, "stages fit shared memory");
+    const long long tiles = (long long)((w + TC_TW - 1) / TC_TW) * ((h + TC_TH - 1) / TC_TH) * n;
+    if (tiles == 0) return cudaSuccess;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // x: planar [n][CL][h][w][8] BF16 (CL = 1 for the first layer's stored plane),
+    // a 4-D tensor (8, w, h, n CL); dims innermost first, strides in bytes of dims 1..3
+    constexpr int CL = CIN == 16 ? 1 : CIN / 8;
+    alignas(64) CUtensorMap map;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n * CL};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)w * 16, (cuuint64_t)h * w * 16};
+    const cuuint32_t box[4] = {8, (cuuint32_t)TC_PW, (cuuint32_t)TC_ROWS_IN, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)x, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    auto kern = k_conv_ws<CIN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<long long>(tiles, (long long)WS_BPS * n_sm);
+    kern<<<grid, WS_THREADS, L::total, s>>>(map, n, h, w, wt, bias, out, status, spin_limit,
+                                            no_commit_first);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int EPI, bool PLANAR = false>
 cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const float *bias,
                    void *out, const float *rgb, const float *lr_depth, float *hr_depth,
                    const bf16 *gate, int *status, int n_sm, cudaStream_t s,
                    long long spin_limit = TC_SPIN_LIMIT, int no_commit_first = 0) {
     using L = TcSmem<CIN, COUT, EPI>;
-    auto kern = k_conv_tc<CIN, COUT, EPI>;
+    auto kern = k_conv_tc<CIN, COUT, EPI, PLANAR>;
     constexpr int NCOL = tmem_cols<COUT>();
     // blocks per SM: limited by shared memory and by the 512 TMEM columns; the
     // shared-memory request is raised so that no more blocks than that fit
@@ -570,6 +871,20 @@ cudaError_t up_conv_tc(int layer, const __nv_bfloat16 *x, int n, int h, int w,
                                            nullptr, status, n_sm, s);
 }
 
+// Inference on planar activations: layer 0 reads the one stored input plane
+// ([n][h][w][8]), layers 0-4 write relu(conv + bias) as planar BF16
+// ([n][4][h][w][8]) through the warp-specialised TMA kernel, layer 5 reads the
+// planes and writes the upsampled image and depth as up_conv_tc does.
+cudaError_t up_conv_tc_planar(int layer, const __nv_bfloat16 *x, int n, int h, int w,
+                              const __nv_bfloat16 *wt, const float *bias, void *out,
+                              const float *rgb, const float *lr_depth, float *hr_depth,
+                              int *status, int n_sm, cudaStream_t s) {
+    if (layer == 0) return run_ws<16>(x, n, h, w, wt, bias, (bf16 *)out, status, n_sm, s);
+    if (layer < 5) return run_ws<32>(x, n, h, w, wt, bias, (bf16 *)out, status, n_sm, s);
+    return run_tc<32, 48, TC_EPI_UPSAMPLE, true>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth,
+                                                 nullptr, status, n_sm, s);
+}
+
 // Training: the last layer's raw output z = conv + bias (FP32 [n][h][w][48]).
 cudaError_t up_conv_tc_linear(const __nv_bfloat16 *x, int n, int h, int w,
                               const __nv_bfloat16 *wt, const float *bias, float *z, int *status,
@@ -597,8 +912,7 @@ cudaError_t up_dgrad_tc(int layer, const __nv_bfloat16 *dz, int n, int h, int w,
 cudaError_t up_conv_tc_timeout_probe(const __nv_bfloat16 *x, int n, int h, int w,
                                      const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out,
                                      int *status, int n_sm, long long spin_limit, cudaStream_t s) {
-    return run_tc<32, 32, TC_EPI_RELU>(x, n, h, w, wt, bias, out, nullptr, nullptr, nullptr,
-                                       nullptr, status, n_sm, s, spin_limit, 1);
+    return run_ws<32>(x, n, h, w, wt, bias, out, status, n_sm, s, spin_limit, 1);
 }
 
 }  // namespace gsk
