@@ -280,7 +280,7 @@ def upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb_plain, stream, 
         "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
         "stages_ms_per_step": {"render_lr": ms_lr, "cnn": ms_cnn},
         "cnn_roofline": {
-            "kernel": "k_conv_tc (6 layers, tcgen05) + k_prep_input + k_bilinear1",
+            "kernel": "k_conv_ws (layers 1-5, TMA + tcgen05) + k_conv_tc (layer 6, tcgen05) + k_prep_input_plane",
             "bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
             "frac": cnn_tflops / bf16_peak if cnn_tflops else None,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the CNN is timed alone)",
