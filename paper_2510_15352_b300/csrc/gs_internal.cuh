@@ -131,11 +131,18 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
 // The render's depth sort: keys are z bits minus the near plane's bits; three
 // passes (9, 9, 8 bits) and, when *wide, a fourth pass and a copy. The sorted
 // keys and values end in tmp_keys / tmp_vals. hist needs 512 uint32 per tile.
+// One sort tile of a segmented sort: the segment's first key, the tile's
+// first key within the segment and its key count (a direct lookup for the sort
+// kernels, whose blocks would otherwise search the segment table first).
+struct SortTile {
+    long long seg_base;
+    int t0, nk;
+};
 cudaError_t launch_sort_depth(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
                               uint32_t *tmp_vals, long long n_keys, const long long *seg_start,
                               const long long *seg_count, const int *tile_start, int n_seg,
                               int n_tiles, uint32_t *hist, const int *wide, cudaStream_t s,
-                              const int *n_tiles_dev);
+                              const int *n_tiles_dev, const SortTile *tiles);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
 // Intrinsics scaled by 1/f (see k_blur.cu).
@@ -147,8 +154,8 @@ cudaError_t launch_blur_poses(const float *vm, const float *vel, int n, int k, f
 // Device-side sizing of a chunk (see k_plan.cu).
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks, long long cap_survivors,
                         int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
-                        int *status, long long *need, unsigned long long *survivors,
-                        cudaStream_t s);
+                        SortTile *stiles, int *status, long long *need,
+                        unsigned long long *survivors, cudaStream_t s);
 
 // Super-tile bitmaps (one row of ceil(count/32) words per 64x64-pixel
 // super-tile) and the rank-ordered tile rects.

@@ -3,7 +3,8 @@
 //
 // From the per-camera survivor counts it writes each camera's survivor slot
 // offset, bitmap words and offsets, the prefix tables of the binning blocks and
-// of the sort tiles, and the segment table of the sort. When the chunk's
+// of the sort tiles, the segment table of the sort and one SortTile entry per
+// sort tile. When the chunk's
 // survivors exceed the workspace, it records the size needed, raises the status
 // word and plans an empty chunk (every count 0), so the later kernels do
 // nothing and the host can grow the workspace and render again.
@@ -42,11 +43,13 @@ __global__ void __launch_bounds__(PT)
            int bin_ranks, long long cap_survivors, int *__restrict__ blkpre,
            int *__restrict__ sorttiles,
            long long *__restrict__ segstart, long long *__restrict__ segcount,
-           int *__restrict__ status, long long *__restrict__ need,
+           SortTile *__restrict__ stiles, int *__restrict__ status, long long *__restrict__ need,
            unsigned long long *__restrict__ survivors) {
     __shared__ long long ws64[PT / 32];
     __shared__ int ws32[PT / 32];
     __shared__ long long carry_s, carry_bm;
+    __shared__ long long b_off[PT], b_cnt[PT];  // per segment of a batch: first survivor, count
+    __shared__ int b_st[PT];                    // and first sort tile within the batch
     __shared__ int carry_bb, carry_st, overflow;
     const int tid = threadIdx.x;
     // 1. is the chunk's survivor total within the workspace?
@@ -95,6 +98,26 @@ __global__ void __launch_bounds__(PT)
             segstart[i] = off_s;
             segcount[i] = c;
         }
+        // the SortTile entries of this batch's segments, one tile per thread
+        // (consecutive threads write consecutive entries); a tile's segment is
+        // found by a search over the batch's tile offsets in shared memory
+        b_off[tid] = off_s;
+        b_cnt[tid] = c;
+        b_st[tid] = off_st - carry_st;  // tiles of this batch before segment i
+        __syncthreads();
+        for (int g = tid; g < t_st; g += PT) {
+            int lo = 0, hi = min(PT, m - b) - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (b_st[mid] <= g)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const int t0 = (g - b_st[lo]) * SORT_TILE_KEYS;
+            stiles[carry_st + g] = SortTile{b_off[lo], t0,
+                                            (int)min((long long)SORT_TILE_KEYS, b_cnt[lo] - t0)};
+        }
         __syncthreads();
         if (tid == 0) {
             carry_s += t_s;
@@ -114,11 +137,11 @@ __global__ void __launch_bounds__(PT)
 
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks,
                         long long cap_survivors, int *blkpre, int *sorttiles, long long *segstart,
-                        long long *segcount, int *status, long long *need,
+                        long long *segcount, SortTile *stiles, int *status, long long *need,
                         unsigned long long *survivors, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     k_plan<<<1, PT, 0, s>>>(cams, counts, m, bin_ranks, cap_survivors, blkpre, sorttiles, segstart,
-                            segcount, status, need, survivors);
+                            segcount, stiles, status, need, survivors);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,18 @@ __device__ __forceinline__ int find_seg(const int *__restrict__ tile_start, int 
     return lo;
 }
 
+// Where tile `tile` lies: from the SortTile table when there is one (one
+// load), else by searching the segment table.
+__device__ __forceinline__ SortTile tile_of(const SortTile *__restrict__ tab,
+                                            const long long *__restrict__ seg_start,
+                                            const long long *__restrict__ seg_count,
+                                            const int *__restrict__ tile_start, int n_seg, int tile) {
+    if (tab) return tab[tile];
+    const int s = find_seg(tile_start, n_seg, tile);
+    const int t0 = (tile - tile_start[s]) * TK;
+    return SortTile{seg_start[s], t0, (int)min((long long)TK, seg_count[s] - t0)};
+}
+
 // Digit histogram of every tile: BITS-bit digit at `shift`. With a skip flag
 // that is zero, the pass does nothing (an optional pass of the depth sort).
 template <int BITS>
@@ -60,23 +72,25 @@ __global__ void __launch_bounds__(ST)
     k_sort_hist(const uint32_t *__restrict__ keys, const long long *__restrict__ seg_start,
                 const long long *__restrict__ seg_count, const int *__restrict__ tile_start,
                 int n_seg, int shift, uint32_t *__restrict__ hist, const int *__restrict__ nt_dev,
-                int nt_host, const int *__restrict__ run) {
+                int nt_host, const int *__restrict__ run, const SortTile *__restrict__ tab) {
     constexpr int ND = 1 << BITS;
     __shared__ uint32_t h[ND];
     if (run && !*run) return;
     const int nt = nt_dev ? *nt_dev : nt_host;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const int s = find_seg(tile_start, n_seg, tile);
-    const long long i0 = (long long)(tile - tile_start[s]) * TK;
-    const long long n = seg_count[s];
-    const uint32_t *k = keys + seg_start[s];
+    const SortTile T = tile_of(tab, seg_start, seg_count, tile_start, n_seg, tile);
+    const uint32_t *k = keys + T.seg_base + T.t0;
     for (int d = threadIdx.x; d < ND; d += ST) h[d] = 0;
-    __syncthreads();
+    uint32_t kv[SIPT];
 #pragma unroll
     for (int r = 0; r < SIPT; ++r) {
-        const long long i = i0 + r * ST + threadIdx.x;
-        if (i < n) atomicAdd(&h[(k[i] >> shift) & (ND - 1)], 1u);
+        const int j = r * ST + threadIdx.x;
+        kv[r] = j < T.nk ? k[j] : 0u;
     }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SIPT; ++r)
+        if (r * ST + (int)threadIdx.x < T.nk) atomicAdd(&h[(kv[r] >> shift) & (ND - 1)], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < ND; d += ST) hist[(long long)tile * ND + d] = h[d];
     __syncthreads();  // h is cleared for the next tile of this block
@@ -137,7 +151,7 @@ __global__ void __launch_bounds__(ST)
                    const long long *__restrict__ seg_start, const long long *__restrict__ seg_count,
                    const int *__restrict__ tile_start, int n_seg, int shift,
                    const uint32_t *__restrict__ offs, const int *__restrict__ nt_dev, int nt_host,
-                   int index_vals, const int *__restrict__ run) {
+                   int index_vals, const int *__restrict__ run, const SortTile *__restrict__ tab) {
     constexpr int ND = 1 << BITS, DPT = ND / ST;  // digits per thread (1 or 2)
     static_assert(ND % ST == 0, "digits are a multiple of the block size");
     __shared__ uint32_t wcnt[SNW][ND];
@@ -149,12 +163,12 @@ __global__ void __launch_bounds__(ST)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = nt_dev ? *nt_dev : nt_host;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const int s = find_seg(tile_start, n_seg, tile);
-    const long long base = seg_start[s];
-    const long long t0 = (long long)(tile - tile_start[s]) * TK;
+    const SortTile T = tile_of(tab, seg_start, seg_count, tile_start, n_seg, tile);
+    const long long base = T.seg_base;
+    const long long t0 = T.t0;
     const long long i0 = t0 + (long long)warp * (32 * SIPT);
-    const long long n = seg_count[s];
-    const int nk = (int)min((long long)TK, n - t0);  // keys in this tile
+    const long long n = t0 + T.nk;  // keys of the segment up to the end of this tile
+    const int nk = T.nk;            // keys in this tile
 #pragma unroll
     for (int q = 0; q < DPT; ++q) toff[q * ST + tid] = offs[(long long)tile * ND + q * ST + tid];
     for (int j = lane; j < ND; j += 32) wcnt[warp][j] = 0;
@@ -262,13 +276,14 @@ template <int BITS>
 void sort_pass(const uint32_t *sk, const uint32_t *sv, uint32_t *dk, uint32_t *dv,
                const long long *seg_start, const long long *seg_count, const int *tile_start,
                int n_seg, int n_tiles, int shift, uint32_t *hist, cudaStream_t s,
-               const int *n_tiles_dev, bool index_vals, const int *run) {
+               const int *n_tiles_dev, bool index_vals, const int *run,
+               const SortTile *tab = nullptr) {
     k_sort_hist<BITS><<<n_tiles, ST, 0, s>>>(sk, seg_start, seg_count, tile_start, n_seg, shift,
-                                             hist, n_tiles_dev, n_tiles, run);
+                                             hist, n_tiles_dev, n_tiles, run, tab);
     k_sort_offsets<BITS><<<n_seg, 1 << BITS, 0, s>>>(tile_start, hist, run);
     k_sort_scatter<BITS><<<n_tiles, ST, 0, s>>>(sk, sv, dk, dv, seg_start, seg_count, tile_start,
                                                 n_seg, shift, hist, n_tiles_dev, n_tiles,
-                                                index_vals, run);
+                                                index_vals, run, tab);
 }
 
 }  // namespace
@@ -297,18 +312,18 @@ cudaError_t launch_sort_depth(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys
                               uint32_t *tmp_vals, long long n_keys, const long long *seg_start,
                               const long long *seg_count, const int *tile_start, int n_seg,
                               int n_tiles, uint32_t *hist, const int *wide, cudaStream_t s,
-                              const int *n_tiles_dev) {
+                              const int *n_tiles_dev, const SortTile *tiles) {
     if (n_seg == 0 || n_tiles == 0) return cudaSuccess;
     // bits 0-8, 9-17, 18-25: keys -> tmp -> keys -> tmp
     sort_pass<9>(keys, vals, tmp_keys, tmp_vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 0, hist, s, n_tiles_dev, true, nullptr);
+                 0, hist, s, n_tiles_dev, true, nullptr, tiles);
     sort_pass<9>(tmp_keys, tmp_vals, keys, vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 9, hist, s, n_tiles_dev, false, nullptr);
+                 9, hist, s, n_tiles_dev, false, nullptr, tiles);
     sort_pass<8>(keys, vals, tmp_keys, tmp_vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 18, hist, s, n_tiles_dev, false, nullptr);
+                 18, hist, s, n_tiles_dev, false, nullptr, tiles);
     // bits 26-31 only when some key needs them (*wide): tmp -> keys, then back
     sort_pass<8>(tmp_keys, tmp_vals, keys, vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 26, hist, s, n_tiles_dev, false, wide);
+                 26, hist, s, n_tiles_dev, false, wide, tiles);
     if (n_keys > 0) {
         const int grid = (int)std::min<long long>((n_keys + 255) / 256, 148LL * 8);
         k_sort_copy<<<grid, 256, 0, s>>>(keys, vals, tmp_keys, tmp_vals, n_keys, wide);
