@@ -177,6 +177,7 @@ struct ChunkPlan {
     int g0, n_groups;     // groups of the chunk in the group table
     int max_bx;           // projection blocks (x) for the largest scene of the chunk
     int tiles_total;      // compositing blocks of the chunk (tiles or 2x2 quads)
+    int per_cam;          // compositing blocks of every camera when all are equal, else 0
     int max_sup;          // largest super-tile count of a camera of the chunk
     long long mask_words; // survival-mask words of the chunk
     long long n_gauss;    // sum over cameras of their scene sizes
@@ -227,8 +228,10 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
             ci.tile_off = ch.tiles_total;
             P.tilepre[tp + s] = ch.tiles_total;
             // compositing blocks of this camera: tiles, or 2 x 2 quads of tiles
-            ch.tiles_total += cfg.tiles_per_block == 4 ? ((ci.TX + 1) / 2) * ((ci.TY + 1) / 2)
-                                                       : ci.TX * ci.TY;
+            const int blocks = cfg.tiles_per_block == 4 ? ((ci.TX + 1) / 2) * ((ci.TY + 1) / 2)
+                                                        : ci.TX * ci.TY;
+            ch.tiles_total += blocks;
+            ch.per_cam = s == 0 ? blocks : (ch.per_cam == blocks ? blocks : 0);
             ch.max_sup = std::max(ch.max_sup,
                                   ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE));
             ci.mask_off = ch.mask_words;
@@ -363,7 +366,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                        (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
         if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;
-        CKC(launch_composite(cams, tilepre, ch.m, ch.tiles_total, recs,
+        CKC(launch_composite(cams, tilepre, ch.m, ch.per_cam, ch.tiles_total, recs,
                              (const uint32_t *)ctx->tvals.p, (const uint2 *)ctx->rrect.p,
                              (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
                              cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,

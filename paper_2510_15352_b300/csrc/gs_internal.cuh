@@ -173,7 +173,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, 
 // of tiles (8 pixels per thread). tile_prefix / n_tiles count the blocks: tiles
 // or quads per camera.
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
-                             int n_tiles, const float4 *rec, const uint32_t *vals,
+                             int per_cam, int n_tiles, const float4 *rec, const uint32_t *vals,
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,

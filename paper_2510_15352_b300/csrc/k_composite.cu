@@ -70,13 +70,35 @@ __device__ __forceinline__ float max_p_rect(float u, float v, float a, float b, 
     return best;
 }
 
+// The camera of compositing block b and its first block: b / per_cam when every
+// camera of the chunk has per_cam blocks (no memory access), else a search of
+// the chunk's block prefix.
+__device__ __forceinline__ int block_camera(const int *__restrict__ prefix, int n_slots, int per_cam,
+                                            int b, int &first) {
+    if (per_cam > 0) {
+        const int c = b / per_cam;
+        first = c * per_cam;
+        return c;
+    }
+    int lo = 0, hi = n_slots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    first = prefix[lo];
+    return lo;
+}
+
 // With 8 pixels per thread (one-warp blocks) the register budget is set for 20
 // resident blocks per SM (96 registers, no spills): 29.3 instead of 30.1 ms per
 // 1,024 cameras at 16 blocks; 24 blocks spill less well and run slower.
 template <int PPT, bool STATS>
 __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
-                int n_slots, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
+                int n_slots, int per_cam, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                 const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
                 CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
                 float *__restrict__ finalT, unsigned long long *__restrict__ stats,
@@ -94,16 +116,9 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     __shared__ uint32_t cand[NT * 32];
     __shared__ uint32_t wsum[NWARP];
 
-    int lo = 0, hi = n_slots - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tile_prefix[mid] <= (int)blockIdx.x)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const CamInfo ci = cams[lo];
-    const int t = (int)blockIdx.x - tile_prefix[lo];
+    int first;
+    const CamInfo ci = cams[block_camera(tile_prefix, n_slots, per_cam, (int)blockIdx.x, first)];
+    const int t = (int)blockIdx.x - first;
     const int tx = t % ci.TX, ty = t / ci.TX;
     const int SX = (ci.TX + STILE - 1) / STILE;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -335,7 +350,8 @@ finished:
 template <bool STATS>
 __global__ void __launch_bounds__(128)
     k_composite_quad(const CamInfo *__restrict__ cams, const int *__restrict__ quad_prefix,
-                     int n_slots, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
+                     int n_slots, int per_cam, const float4 *__restrict__ rec,
+                     const uint32_t *__restrict__ vals,
                      const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
                      CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
                      float *__restrict__ finalT, unsigned long long *__restrict__ stats,
@@ -346,17 +362,10 @@ __global__ void __launch_bounds__(128)
     __shared__ uint32_t cand[NT * 32];
     __shared__ uint32_t wsum[NWARP];
 
-    int lo = 0, hi = n_slots - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (quad_prefix[mid] <= (int)blockIdx.x)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const CamInfo ci = cams[lo];
+    int first;
+    const CamInfo ci = cams[block_camera(quad_prefix, n_slots, per_cam, (int)blockIdx.x, first)];
     const int QX = (ci.TX + 1) >> 1;
-    const int qi = (int)blockIdx.x - quad_prefix[lo];
+    const int qi = (int)blockIdx.x - first;
     const int qx = qi % QX, qy = qi / QX;
     const int SX = (ci.TX + STILE - 1) / STILE;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -567,17 +576,17 @@ finished:
 }
 
 template <int PPT>
-cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots, int n_tiles,
+cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots, int per_cam, int n_tiles,
                        const float4 *rec, const uint32_t *vals, const uint2 *rrect,
                        const uint32_t *bitmap, CompParams C, float *rgb, float *depth,
                        float *final_T, unsigned long long *stats, bool collect,
                        const int *status, cudaStream_t s) {
     if (collect)
-        k_composite<PPT, true><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+        k_composite<PPT, true><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, per_cam, rec, vals,
                                                              rrect, bitmap, C, rgb, depth, final_T,
                                                              stats, status);
     else
-        k_composite<PPT, false><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+        k_composite<PPT, false><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, per_cam, rec, vals,
                                                               rrect, bitmap, C, rgb, depth, final_T,
                                                               stats, status);
     return cudaGetLastError();
@@ -586,7 +595,7 @@ cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots,
 }  // namespace
 
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
-                             int n_tiles, const float4 *rec, const uint32_t *vals,
+                             int per_cam, int n_tiles, const float4 *rec, const uint32_t *vals,
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
@@ -594,22 +603,22 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
     if (n_tiles == 0) return cudaSuccess;
     if (tiles_per_block == 4) {
         if (collect)
-            k_composite_quad<true><<<n_tiles, 128, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+            k_composite_quad<true><<<n_tiles, 128, 0, s>>>(cams, tile_prefix, n_slots, per_cam, rec, vals,
                                                             rrect, bitmap, C, rgb, depth, final_T,
                                                             stats, status);
         else
-            k_composite_quad<false><<<n_tiles, 128, 0, s>>>(cams, tile_prefix, n_slots, rec, vals,
+            k_composite_quad<false><<<n_tiles, 128, 0, s>>>(cams, tile_prefix, n_slots, per_cam, rec, vals,
                                                              rrect, bitmap, C, rgb, depth, final_T,
                                                              stats, status);
         return cudaGetLastError();
     }
     if (pixels_per_thread == 8)
-        return launch_ppt<8>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
+        return launch_ppt<8>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C,
                              rgb, depth, final_T, stats, collect, status, s);
     if (pixels_per_thread == 4)
-        return launch_ppt<4>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C,
+        return launch_ppt<4>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C,
                              rgb, depth, final_T, stats, collect, status, s);
-    return launch_ppt<2>(cams, tile_prefix, n_slots, n_tiles, rec, vals, rrect, bitmap, C, rgb,
+    return launch_ppt<2>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C, rgb,
                          depth, final_T, stats, collect, status, s);
 }
 
