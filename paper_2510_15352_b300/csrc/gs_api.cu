@@ -57,7 +57,7 @@ struct gs_context {
     DevBuf d_scenes;
     // chunk workspace
     DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, srect, bitmap;
-    DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist, sorttab;
+    DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist, sorttab, bintab;
     DevBuf wide;  // per chunk: some depth key needs the sort's fourth pass
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
@@ -289,6 +289,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
     CKS(grow(ctx, ctx->sorthist, (Sx / SORT_TILE_KEYS + m + 1) * 512 * 4));
     CKS(grow(ctx, ctx->sorttab, (Sx / SORT_TILE_KEYS + m + 1) * sizeof(SortTile)));
+    CKS(grow(ctx, ctx->bintab, (Sx / BIN_RANKS_SMALL + m + 1) * sizeof(int2)));
     CKS(grow(ctx, ctx->wide, (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->blkpre, (size_t)(m + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->sorttiles, (size_t)(m + 1) * sizeof(int)));
@@ -341,8 +342,8 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                               (int *)ctx->counts.p, st));
         CKC(launch_plan(cams, (const int *)ctx->counts.p, ch.m, ch.bin_ranks, ctx->cap_survivors,
                         (int *)ctx->blkpre.p, (int *)ctx->sorttiles.p, (long long *)ctx->segstart.p,
-                        (long long *)ctx->segcount.p, (SortTile *)ctx->sorttab.p, status, need,
-                        stats + 6, st));
+                        (long long *)ctx->segcount.p, (SortTile *)ctx->sorttab.p,
+                        (int2 *)ctx->bintab.p, status, need, stats + 6, st));
         int *wide = (int *)ctx->wide.p + k;
         CKC(cudaMemsetAsync(wide, 0, sizeof(int), st));
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
@@ -361,7 +362,8 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                               ch.m, ch.sort_grid, (uint32_t *)ctx->sorthist.p, wide, st,
                               (const int *)ctx->sorttiles.p + ch.m, (const SortTile *)ctx->sorttab.p));
         if (E) CKC(cudaEventRecord(E[2], st));
-        CKC(launch_bin(cams, (const int *)ctx->blkpre.p, ch.m, ch.bin_grid, ch.max_sup,
+        CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
+                       ch.bin_grid, ch.max_sup,
                        ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->tvals.p,
                        (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
         if (E) CKC(cudaEventRecord(E[3], st));
@@ -539,7 +541,8 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect, &ctx->srect,
                       &ctx->bitmap,   &ctx->tables, &ctx->status, &ctx->blkpre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
-                      &ctx->sorttiles, &ctx->sorthist, &ctx->sorttab, &ctx->blur_vm, &ctx->wide,
+                      &ctx->sorttiles, &ctx->sorthist, &ctx->sorttab, &ctx->bintab, &ctx->blur_vm,
+                      &ctx->wide,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);

@@ -154,7 +154,7 @@ cudaError_t launch_blur_poses(const float *vm, const float *vel, int n, int k, f
 // Device-side sizing of a chunk (see k_plan.cu).
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks, long long cap_survivors,
                         int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
-                        SortTile *stiles, int *status, long long *need,
+                        SortTile *stiles, int2 *bintab, int *status, long long *need,
                         unsigned long long *survivors, cudaStream_t s);
 
 // Super-tile bitmaps (one row of ceil(count/32) words per 64x64-pixel
@@ -163,7 +163,8 @@ cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks, 
 // bin_ranks: ranks per block, BIN_RANKS or BIN_RANKS_SMALL (the plan kernel's
 // blocks must use the same value).
 int bin_ranks_for(int n_super);
-cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
+cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *bintab, int n_slots,
+                       int n_blocks,
                        int n_super, int bin_ranks, const uint2 *srect, const uint32_t *vals,
                        uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
                        cudaStream_t s);

@@ -27,7 +27,8 @@ namespace {
 
 template <int RPT>  // ranks per thread
 __global__ void __launch_bounds__(BIN_THREADS)
-    k_bin(const CamInfo *__restrict__ cams, const int *__restrict__ blk_prefix, int n_slots,
+    k_bin(const CamInfo *__restrict__ cams, const int *__restrict__ blk_prefix,
+          const int2 *__restrict__ bintab, int n_slots,
           const uint2 *__restrict__ srect, const uint32_t *__restrict__ vals,
           uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
           unsigned long long *__restrict__ n_isect) {
@@ -35,16 +36,9 @@ __global__ void __launch_bounds__(BIN_THREADS)
     extern __shared__ uint32_t sbm[];  // [BIN_WORDS][P]
     const int nblk = blk_prefix[n_slots];
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    int lo = 0, hi = n_slots - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (blk_prefix[mid] <= blk)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const CamInfo ci = cams[lo];
-    const int r0 = (blk - blk_prefix[lo]) * BIN_RANKS;
+    const int2 bt = bintab[blk];  // (camera, first rank) of this binning block
+    const CamInfo ci = cams[bt.x];
+    const int r0 = bt.y;
     const int SX = (ci.TX + STILE - 1) / STILE, SY = (ci.TY + STILE - 1) / STILE;
     const int nsup = SX * SY;
     const int P = nsup | 1;
@@ -103,7 +97,8 @@ int bin_ranks_for(int n_super) {
                : BIN_RANKS_SMALL;
 }
 
-cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, int n_blocks,
+cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *bintab, int n_slots,
+                       int n_blocks,
                        int n_super, int bin_ranks, const uint2 *srect, const uint32_t *vals,
                        uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
                        cudaStream_t s) {
@@ -116,7 +111,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, int n_slots, 
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<n_blocks, BIN_THREADS, smem, s>>>(cams, blk_prefix, n_slots, srect, vals, rrect, bitmap,
+    kern<<<n_blocks, BIN_THREADS, smem, s>>>(cams, blk_prefix, bintab, n_slots, srect, vals, rrect, bitmap,
                                              n_isect);
     return cudaGetLastError();
 }

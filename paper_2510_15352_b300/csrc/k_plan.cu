@@ -43,13 +43,14 @@ __global__ void __launch_bounds__(PT)
            int bin_ranks, long long cap_survivors, int *__restrict__ blkpre,
            int *__restrict__ sorttiles,
            long long *__restrict__ segstart, long long *__restrict__ segcount,
-           SortTile *__restrict__ stiles, int *__restrict__ status, long long *__restrict__ need,
+           SortTile *__restrict__ stiles, int2 *__restrict__ bintab, int *__restrict__ status,
+           long long *__restrict__ need,
            unsigned long long *__restrict__ survivors) {
     __shared__ long long ws64[PT / 32];
     __shared__ int ws32[PT / 32];
     __shared__ long long carry_s, carry_bm;
     __shared__ long long b_off[PT], b_cnt[PT];  // per segment of a batch: first survivor, count
-    __shared__ int b_st[PT];                    // and first sort tile within the batch
+    __shared__ int b_st[PT], b_bb[PT];          // and first sort tile / binning block within the batch
     __shared__ int carry_bb, carry_st, overflow;
     const int tid = threadIdx.x;
     // 1. is the chunk's survivor total within the workspace?
@@ -104,7 +105,20 @@ __global__ void __launch_bounds__(PT)
         b_off[tid] = off_s;
         b_cnt[tid] = c;
         b_st[tid] = off_st - carry_st;  // tiles of this batch before segment i
+        b_bb[tid] = off_bb - carry_bb;  // binning blocks of this batch before camera i
         __syncthreads();
+        // the binning blocks' (camera, first rank), likewise
+        for (int g = tid; g < t_bb; g += PT) {
+            int lo = 0, hi = min(PT, m - b) - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (b_bb[mid] <= g)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            bintab[carry_bb + g] = make_int2(b + lo, (g - b_bb[lo]) * bin_ranks);
+        }
         for (int g = tid; g < t_st; g += PT) {
             int lo = 0, hi = min(PT, m - b) - 1;
             while (lo < hi) {
@@ -137,11 +151,11 @@ __global__ void __launch_bounds__(PT)
 
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks,
                         long long cap_survivors, int *blkpre, int *sorttiles, long long *segstart,
-                        long long *segcount, SortTile *stiles, int *status, long long *need,
-                        unsigned long long *survivors, cudaStream_t s) {
+                        long long *segcount, SortTile *stiles, int2 *bintab, int *status,
+                        long long *need, unsigned long long *survivors, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     k_plan<<<1, PT, 0, s>>>(cams, counts, m, bin_ranks, cap_survivors, blkpre, sorttiles, segstart,
-                            segcount, stiles, status, need, survivors);
+                            segcount, stiles, bintab, status, need, survivors);
     return cudaGetLastError();
 }
 

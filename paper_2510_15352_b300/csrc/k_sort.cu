@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(1 << BITS, 1024 >> BITS)  // 64 registers: 2 o
 
 // Five resident blocks per SM (48 registers, a few spilled): the scatter waits
 // on its loads more than it computes, and the extra block hides more of that
-// (6.2 -> 5.0 ms for the depth sort of 1,024 cameras; six blocks spill more
+// (5.3 -> 5.0 ms for the depth sort of 1,024 cameras; six blocks spill more
 // and are slower).
 template <int BITS>
 __global__ void __launch_bounds__(ST, 5)
