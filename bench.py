@@ -39,7 +39,7 @@ WORKLOAD = "single_1m_sh3_1024cam_640x480"
 # 11 per contributing pair (alpha >= alpha_min: 1 - alpha, T', alpha T, four FMAs),
 # and a lower bound, 22 flops per contributing pair only.
 F_PAIR = 20
-LAUNCHES_PER_CHUNK = 19
+LAUNCHES_PER_CHUNK = 20
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
 # FP32 peak of one B300: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz max clock
@@ -513,7 +513,7 @@ def run_b300(args):
     clk = clocks.stop()
     t_max = max_over_ranks(ms, dist)
     value = whole_job_rate(n * args.steps, world, t_max / 1e3)
-    # per chunk: mask, scan, plan, write, 4 x (hist, offsets, scatter) + copy (the
+    # per chunk: camera table, mask, scan, plan, write, 4 x (hist, offsets, scatter) + copy (the
     # fourth pass and the copy launch always and exit at once unless a depth key
     # needs them), bin, composite
     launches = LAUNCHES_PER_CHUNK * n_chunks

@@ -57,7 +57,8 @@ struct gs_context {
     DevBuf d_scenes;
     // chunk workspace
     DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, srect, bitmap;
-    DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist, sorttab, bintab;
+    DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist, sorttab, bintab,
+        camtab;
     DevBuf wide;  // per chunk: some depth key needs the sort's fourth pass
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
@@ -278,6 +279,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->woff, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->counts, (size_t)m * sizeof(int)));
+    CKS(grow(ctx, ctx->camtab, (size_t)m * cam_proj_bytes()));
     CKS(grow(ctx, ctx->rec, rec_bytes(S)));
     CKS(grow(ctx, ctx->srect, Sx * sizeof(uint2)));
     CKS(grow(ctx, ctx->rrect, Sx * sizeof(uint2)));
@@ -335,8 +337,9 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         if (only && !(*only)[k]) continue;
         cudaEvent_t *E = events ? events + 5 * k : nullptr;
         if (E) CKC(cudaEventRecord(E[0], st));
+        CKC(launch_cam_setup(cams, ch.m, a.vm, a.in, PP, ctx->camtab.p, st));
         CKC(launch_project_mask(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
-                                cams, a.vm, a.in, PP, (uint32_t *)ctx->masks.p, st));
+                                cams, ctx->camtab.p, PP, (uint32_t *)ctx->masks.p, st));
         CKC(launch_scan_masks(cams, (const SceneDev *)ctx->d_scenes.p, ch.m,
                               (const uint32_t *)ctx->masks.p, (uint32_t *)ctx->woff.p,
                               (int *)ctx->counts.p, st));
@@ -347,7 +350,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         int *wide = (int *)ctx->wide.p + k;
         CKC(cudaMemsetAsync(wide, 0, sizeof(int), st));
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
-                                 cams, a.vm, a.in, PP, (const uint32_t *)ctx->masks.p,
+                                 cams, ctx->camtab.p, PP, (const uint32_t *)ctx->masks.p,
                                  (const uint32_t *)ctx->woff.p, recs, with_d,
                                  (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p, wide,
                                  std::log(cfg.alpha_min), status, st));
@@ -541,7 +544,7 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect, &ctx->srect,
                       &ctx->bitmap,   &ctx->tables, &ctx->status, &ctx->blkpre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
-                      &ctx->sorttiles, &ctx->sorthist, &ctx->sorttab, &ctx->bintab, &ctx->blur_vm,
+                      &ctx->sorttiles, &ctx->sorthist, &ctx->sorttab, &ctx->bintab, &ctx->camtab, &ctx->blur_vm,
                       &ctx->wide,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)

@@ -100,18 +100,22 @@ constexpr int GS_STATUS_CAPACITY = 1; // device status word: a chunk exceeded th
 
 // ---- launchers (each defined in its kernel file) ----
 
+// Projection constants of the chunk's cameras (cam_proj_bytes() each, in slot
+// order), read by both projection passes.
+size_t cam_proj_bytes();
+cudaError_t launch_cam_setup(const CamInfo *cams, int m, const float *viewmats, const float *intr,
+                             ProjParams P, void *camtab, cudaStream_t s);
 cudaError_t launch_project_mask(const Group *groups, int n_groups, int max_blocks_x,
-                                const SceneDev *scenes, const CamInfo *cams,
-                                const float *viewmats, const float *intr, ProjParams P,
-                                uint32_t *masks, cudaStream_t s);
+                                const SceneDev *scenes, const CamInfo *cams, const void *camtab,
+                                ProjParams P, uint32_t *masks, cudaStream_t s);
 
 cudaError_t launch_scan_masks(const CamInfo *cams, const SceneDev *scenes, int n_slots,
                               const uint32_t *masks, uint32_t *woff, int *counts,
                               cudaStream_t s);
 
 cudaError_t launch_project_write(const Group *groups, int n_groups, int max_blocks_x,
-                                 const SceneDev *scenes, const CamInfo *cams,
-                                 const float *viewmats, const float *intr, ProjParams P,
+                                 const SceneDev *scenes, const CamInfo *cams, const void *camtab,
+                                 ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, float4 *rec, int rec_d,
                                  uint2 *srect, uint32_t *keys, int *wide,
                                  float ln_alpha_min, const int *status, cudaStream_t s);

@@ -360,8 +360,8 @@ constexpr int MQ = 64;  // queue entries per warp: < 32 left + < 32 appended
 
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project_mask(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
-                   const CamInfo *__restrict__ cams, const float *__restrict__ vms,
-                   const float *__restrict__ intr, ProjParams P, uint32_t *__restrict__ masks) {
+                   const CamInfo *__restrict__ cams, const CamProj *__restrict__ camtab,
+                   ProjParams P, uint32_t *__restrict__ masks) {
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
     if (g0 >= gr.n) return;
@@ -374,9 +374,8 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     __shared__ uint32_t smask[NW][MAX_GROUP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < gr.ncam) {
-        const CamInfo ci = cams[gr.slot0 + tid];
-        cam_setup(cp[tid], vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H, P.guard);
-        moff[tid] = ci.mask_off;
+        cp[tid] = load_cam(camtab[gr.slot0 + tid]);
+        moff[tid] = cams[gr.slot0 + tid].mask_off;
     }
     smask[warp][lane] = 0u;
     smask[warp][lane + 32] = 0u;
@@ -485,8 +484,8 @@ constexpr float LOG2E = 1.4426950408889634f;
 
 __global__ void __launch_bounds__(PROJ_THREADS, 4)
     k_project_write(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
-                    const CamInfo *__restrict__ cams, const float *__restrict__ vms,
-                    const float *__restrict__ intr, ProjParams P,
+                    const CamInfo *__restrict__ cams, const CamProj *__restrict__ camtab,
+                    ProjParams P,
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
                     float4 *__restrict__ rec, int with_d, uint2 *__restrict__ srect,
                     uint32_t *__restrict__ keys, int *__restrict__ wide,
@@ -506,24 +505,19 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SceneDev sc = scenes[gr.scene];
     const int nwords = (int)min((long long)(WG / 32), (gr.n - g0 + 31) >> 5);
-    // 1. stage: cameras, the block's Gaussians, their SH rows and all mask
-    // words, in two rounds of global loads. Round 1: the CamInfo of this
-    // thread's (camera, mask word) entry and (threads < WG) its Gaussian's
-    // attributes. Round 2, issued together: its share of the SH rows, the mask
-    // word and its offset, and (one thread per camera) the view matrix and
-    // intrinsics.
+    // 1. stage: the block's Gaussians, their SH rows and all mask words, in two
+    // rounds of global loads. Round 1: the CamInfo of this thread's (camera,
+    // mask word) entry and (threads < WG) its Gaussian's attributes. Round 2,
+    // issued together: its share of the SH rows and the mask word and its
+    // offset. (The cameras' projection constants come from the chunk's table.)
     static_assert(NE == PROJ_THREADS, "one (camera, mask word) entry per thread");
     const int cl = tid >> 2, wq = tid & 3;
     const bool cam_ok = cl < gr.ncam;
     long long c_moff = 0, c_soff = 0;
-    int c_user = 0, c_W = 0, c_H = 0;
     if (cam_ok) {
         const CamInfo *ci = cams + gr.slot0 + cl;
         c_moff = ci->mask_off;
         c_soff = ci->seg_off;
-        c_user = ci->user;
-        c_W = ci->W;
-        c_H = ci->H;
     }
     if (tid < WG) {
         const long long g = g0 + tid;
@@ -575,7 +569,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
             wo = woff[at];
         }
         if (cam_ok && wq == 0) {
-            cam_setup(cp[cl], vms + 16LL * c_user, intr + 4LL * c_user, c_W, c_H, P.guard);
+            cp[cl] = load_cam(camtab[gr.slot0 + cl]);
             soff[cl] = c_soff;
         }
         smask[tid] = m;
@@ -664,15 +658,36 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
     }
 }
 
+// The projection constants of every camera of a chunk (one thread each), read
+// by both projection passes.
+__global__ void k_cam_setup(const CamInfo *__restrict__ cams, int m, const float *__restrict__ vms,
+                            const float *__restrict__ intr, ProjParams P, CamProj *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    const CamInfo ci = cams[c];
+    CamProj cp;
+    cam_setup(cp, vms + 16LL * ci.user, intr + 4LL * ci.user, ci.W, ci.H, P.guard);
+    out[c] = cp;
+}
+
 }  // namespace
 
+size_t cam_proj_bytes() { return sizeof(CamProj); }
+
+cudaError_t launch_cam_setup(const CamInfo *cams, int m, const float *viewmats, const float *intr,
+                             ProjParams P, void *camtab, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    k_cam_setup<<<(m + 127) / 128, 128, 0, s>>>(cams, m, viewmats, intr, P, (CamProj *)camtab);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project_mask(const Group *groups, int n_groups, int max_blocks_x,
-                                const SceneDev *scenes, const CamInfo *cams,
-                                const float *viewmats, const float *intr, ProjParams P,
-                                uint32_t *masks, cudaStream_t s) {
+                                const SceneDev *scenes, const CamInfo *cams, const void *camtab,
+                                ProjParams P, uint32_t *masks, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(max_blocks_x, n_groups);
-    k_project_mask<<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, viewmats, intr, P, masks);
+    k_project_mask<<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, (const CamProj *)camtab, P,
+                                                 masks);
     return cudaGetLastError();
 }
 
@@ -685,8 +700,8 @@ cudaError_t launch_scan_masks(const CamInfo *cams, const SceneDev *scenes, int n
 }
 
 cudaError_t launch_project_write(const Group *groups, int n_groups, int max_blocks_x,
-                                 const SceneDev *scenes, const CamInfo *cams,
-                                 const float *viewmats, const float *intr, ProjParams P,
+                                 const SceneDev *scenes, const CamInfo *cams, const void *camtab,
+                                 ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, float4 *rec, int with_d,
                                  uint2 *srect, uint32_t *keys, int *wide,
                                  float ln_alpha_min, const int *status, cudaStream_t s) {
@@ -696,7 +711,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
     cudaError_t e = cudaFuncSetAttribute(k_project_write,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, viewmats, intr, P,
+    k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, (const CamProj *)camtab, P,
                                                      masks, woff, rec, with_d, srect, keys, wide,
                                                      ln_alpha_min, status);
     return cudaGetLastError();
