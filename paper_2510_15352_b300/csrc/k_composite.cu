@@ -106,7 +106,6 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     if (status && *status) return;  // the chunk did not fit the workspace: nothing written
     constexpr int NT = 256 / PPT;    // threads per block
     constexpr int CPR = 16 / PPT;    // threads per pixel row
-    constexpr int RPW = 32 / CPR;    // pixel rows per warp
     constexpr int NWARP = NT / 32;
     // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits),
     // s2 = (red, green, blue, -)
@@ -115,6 +114,10 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     // this tile's list (a kept candidate only moves to a lower index)
     __shared__ uint32_t cand[NT * 32];
     __shared__ uint32_t wsum[NWARP];
+    // per warp: the pixel-centre rectangle of its live pixels (x0, x1, y0, y1);
+    // the staging skip test bounds the quadratic over it instead of over the
+    // warp's rows (stopped pixels pass no alpha test), empty when x0 > x1
+    __shared__ float4 wl[NWARP];
 
     int first;
     const CamInfo ci = cams[block_camera(tile_prefix, n_slots, per_cam, (int)blockIdx.x, first)];
@@ -139,6 +142,24 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     }
     const uint32_t warp_bit = 1u << warp;
     unsigned long long ev = 0, al = 0, wi = 0, wbox = 0, wbl = 0;
+    auto live_rect = [&]() {
+        int xlo = 0x7fffffff, xhi = -1;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+            if (thr[k] != INF) {
+                xlo = min(xlo, x0 + k * CPR);
+                xhi = max(xhi, x0 + k * CPR);
+            }
+        int ylo = xhi >= 0 ? y : 0x7fffffff, yhi = xhi >= 0 ? y : -1;
+        xlo = __reduce_min_sync(0xffffffffu, xlo);
+        xhi = __reduce_max_sync(0xffffffffu, xhi);
+        ylo = __reduce_min_sync(0xffffffffu, ylo);
+        yhi = __reduce_max_sync(0xffffffffu, yhi);
+        if (lane == 0)
+            wl[warp] = xhi >= 0 ? make_float4(xlo + 0.5f, xhi + 0.5f, ylo + 0.5f, yhi + 0.5f)
+                                : make_float4(1.0f, 0.0f, 1.0f, 0.0f);
+    };
+    live_rect();  // read after the block's next barrier
 
     const uint32_t *bm = bitmap + ci.bm_off + (long long)((ty / STILE) * SX + tx / STILE) * ci.nw;
     const long long rec0 = ci.seg_off;
@@ -211,23 +232,22 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                 // alpha >= alpha_min region meets the warp's rows and the largest p
                 // over the rows' pixel-centre rectangle reaches the threshold (with a
                 // margin past float32 rounding, so no passing pair is skipped)
-                const float x0 = tx * TILE + 0.5f, x1 = tx * TILE + TILE - 0.5f;
                 uint32_t m = 0;
-                if (a.x + a.z >= x0 && a.x - a.z <= x1) {
 #pragma unroll
-                    for (int k = 0; k < NWARP; ++k) {
-                        const float y0 = ty * TILE + k * RPW + 0.5f, y1 = y0 + (RPW - 1);
-                        if (!(a.y + a.w >= y0 && a.y - a.w <= y1)) continue;
-                        // float32 error of p grows with its terms' size: bound them
-                        const float DX = fmaxf(fabsf(x0 - a.x), fabsf(x1 - a.x));
-                        const float DY = fmaxf(fabsf(y0 - a.y), fabsf(y1 - a.y));
-                        const float terms = fmaf(fabsf(b.x), DX * DX,
-                                                 fmaf(fabsf(b.y), DX * DY, fabsf(b.z) * DY * DY));
-                        const float margin = fmaf(1e-6f, terms, 1e-3f);
-                        if (max_p_rect(a.x, a.y, b.x, b.y, b.z, b.w, x0, x1, y0, y1) >=
-                            P.log2_alpha_min - margin)
-                            m |= 1u << k;
-                    }
+                for (int k = 0; k < NWARP; ++k) {
+                    const float4 L = wl[k];  // live pixel centres of warp k
+                    const float X0 = L.x, X1 = L.y, Y0 = L.z, Y1 = L.w;
+                    if (!(a.x + a.z >= X0 && a.x - a.z <= X1 && a.y + a.w >= Y0 && a.y - a.w <= Y1))
+                        continue;  // (also when the rectangle is empty)
+                    // float32 error of p grows with its terms' size: bound them
+                    const float DX = fmaxf(fabsf(X0 - a.x), fabsf(X1 - a.x));
+                    const float DY = fmaxf(fabsf(Y0 - a.y), fabsf(Y1 - a.y));
+                    const float terms = fmaf(fabsf(b.x), DX * DX,
+                                             fmaf(fabsf(b.y), DX * DY, fabsf(b.z) * DY * DY));
+                    const float margin = fmaf(1e-6f, terms, 1e-3f);
+                    if (max_p_rect(a.x, a.y, b.x, b.y, b.z, b.w, X0, X1, Y0, Y1) >=
+                        P.log2_alpha_min - margin)
+                        m |= 1u << k;
                 }
                 s0[q] = make_float4(a.x, a.y, b.x, b.y);
                 s1[q] = make_float4(b.z, b.w, cc.w, __uint_as_float(m));
@@ -293,6 +313,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
             live = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
+            live_rect();  // for the next staging, after this barrier
             if (!__syncthreads_or(live)) goto finished;
         }
     }
