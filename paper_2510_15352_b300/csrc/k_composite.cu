@@ -93,8 +93,9 @@ __device__ __forceinline__ int block_camera(const int *__restrict__ prefix, int 
 }
 
 // With 8 pixels per thread (one-warp blocks) the register budget is set for 20
-// resident blocks per SM (96 registers, no spills): 29.3 instead of 30.1 ms per
-// 1,024 cameras at 16 blocks; 24 blocks spill less well and run slower.
+// resident blocks per SM (96 registers, no spills). Per 1,024 cameras: 16 blocks
+// 29.0 ms, 18 blocks 28.2 ms, 20 blocks 27.2 ms, 22 blocks 28.6 ms, 24 blocks
+// 31.3 ms (the last two spill).
 template <int PPT, bool STATS>
 __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
