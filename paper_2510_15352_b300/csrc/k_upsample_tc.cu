@@ -564,21 +564,43 @@ __global__ void __launch_bounds__(TC_THREADS)
 // error in the status word, waits for its own loads and MMAs and frees its
 // tensor memory.
 constexpr int WS_THREADS = 192;
-constexpr int WS_NS = 3;   // input stages
-constexpr int WS_NA = 4;   // accumulator sets (2 M-tiles x 32 columns each)
-constexpr int WS_BPS = 2;  // resident blocks per SM
-constexpr int WS_COLS = WS_NA * 64 <= 128 ? 128 : 256;
-static_assert(WS_NA * 64 <= WS_COLS && WS_BPS * WS_COLS <= 512, "accumulators fit tensor memory");
+constexpr int WS_NS = 3;      // input stages
+constexpr int WS_BPS = 2;     // resident blocks per SM
+constexpr int WS_COLS = 256;  // TMEM columns per block: 4 accumulator sets of N = 32, 2 of N = 48
+static_assert(WS_BPS * WS_COLS <= 512, "accumulators fit tensor memory");
 
-template <int CIN>
+// The LR colour and depth tile (with halo, edge-clamped) of one tile, by the
+// 128 epilogue threads with cp.async (4 floats per LR pixel: r, g, b, depth).
+__device__ __forceinline__ void fetch_lr(const float *__restrict__ rgb, const float *__restrict__ dep,
+                                         int h, int w, TileXY t, float *ls) {
+    const int nc = dep ? 4 : 3;
+    for (int i = threadIdx.x; i < (TC_TH + 2) * TC_PW * 4; i += 128) {
+        const int q = i >> 2, c = i & 3;
+        if (c >= nc) continue;
+        const int yy = min(max(t.by - 1 + q / TC_PW, 0), h - 1);
+        const int xx = min(max(t.bx - 1 + q % TC_PW, 0), w - 1);
+        const long long pix = ((long long)t.img * h + yy) * w + xx;
+        cp_async4(smem_u32(ls + i), c < 3 ? rgb + pix * 3 + c : dep + pix);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Shared memory of a warp-specialised block: the input stages, the weights,
+// for the upsampling layer two LR colour-and-depth tiles (the epilogue warps
+// prefetch tile i + 1 while they finish tile i), the biases, the mbarriers
+// full[WS_NS], empty[WS_NS], accf[NA], acce[NA], drain, the TMEM slot and the
+// abort flag. NA accumulator sets of 2 M-tiles fill the block's WS_COLS columns.
+template <int CIN, int COUT, int EPI>
 struct WsSmem {
+    static constexpr int NA = WS_COLS / (2 * tmem_stride<COUT>());
     static constexpr size_t stage_bytes = (size_t)(CIN / 8) * TC_PIN * 16;
-    static constexpr size_t w_bytes = (size_t)9 * CIN * 32 * 2;
+    static constexpr size_t w_bytes = (size_t)9 * CIN * COUT * 2;
+    static constexpr size_t l_bytes = EPI == TC_EPI_UPSAMPLE ? (size_t)(TC_TH + 2) * TC_PW * 4 * 4 : 0;
     static constexpr size_t off_w = WS_NS * stage_bytes;
-    static constexpr size_t off_bias = off_w + w_bytes;
-    static constexpr size_t off_bar = off_bias + 32 * 4;
-    // full[WS_NS], empty[WS_NS], accf[WS_NA], acce[WS_NA], drain
-    static constexpr int n_bar = 2 * WS_NS + 2 * WS_NA + 1;
+    static constexpr size_t off_l = off_w + w_bytes;
+    static constexpr size_t off_bias = off_l + 2 * l_bytes;
+    static constexpr size_t off_bar = off_bias + COUT * 4;
+    static constexpr int n_bar = 2 * WS_NS + 2 * NA + 1;
     static constexpr size_t off_misc = off_bar + (size_t)n_bar * 8;  // TMEM slot, abort flag
     static constexpr size_t total = off_misc + 16;
 };
@@ -606,22 +628,29 @@ __device__ __forceinline__ void ws_fail(volatile int *abort, int *status) {
     atomicOr(status, 1);
 }
 
-template <int CIN>
-__global__ void __launch_bounds__(WS_THREADS)
+// EPI: TC_EPI_RELU_P (hidden layers, COUT = 32, planar BF16 out) or
+// TC_EPI_UPSAMPLE (last layer, COUT = 48, HR image and depth out; the epilogue
+// warps also stage the LR colour and depth tile of each tile with cp.async).
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(WS_THREADS, WS_BPS)
     k_conv_ws(const __grid_constant__ CUtensorMap xmap, int n, int h, int w,
-              const bf16 *__restrict__ wt, const float *__restrict__ bias, bf16 *__restrict__ out,
-              int *__restrict__ status, long long spin_limit, int no_commit_first) {
-    using L = WsSmem<CIN>;
+              const bf16 *__restrict__ wt, const float *__restrict__ bias, void *__restrict__ out,
+              const float *__restrict__ rgb, const float *__restrict__ lr_depth,
+              float *__restrict__ hr_depth, int *__restrict__ status, long long spin_limit,
+              int no_commit_first) {
+    using L = WsSmem<CIN, COUT, EPI>;
+    constexpr int NA = L::NA, CST = tmem_stride<COUT>();
     constexpr int C8 = CIN / 8;
     constexpr int CL = CIN == 16 ? 1 : C8;  // planes stored in memory (and loaded) per image
-    constexpr uint32_t IDESC = idesc_bf16(128, 32);
+    constexpr uint32_t IDESC = idesc_bf16(128, COUT);
     constexpr uint32_t STAGE_TX = (uint32_t)CL * 8 * TC_PW * TC_ROWS_IN * 2;  // bytes per tile
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *ws = smem + L::off_w;
     float *bs = (float *)(smem + L::off_bias);
     uint64_t *bar = (uint64_t *)(smem + L::off_bar);
-    uint64_t *full = bar, *empty = bar + WS_NS, *accf = bar + 2 * WS_NS, *acce = accf + WS_NA;
-    uint64_t *drain = acce + WS_NA;
+    uint64_t *full = bar, *empty = bar + WS_NS, *accf = bar + 2 * WS_NS, *acce = accf + NA;
+    uint64_t *drain = acce + NA;
+    auto lbuf = [&](long long i) { return (float *)(smem + L::off_l + (size_t)(i & 1) * L::l_bytes); };
     uint32_t *tslot = (uint32_t *)(smem + L::off_misc);
     volatile int *abort = (volatile int *)(smem + L::off_misc + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -632,7 +661,7 @@ __global__ void __launch_bounds__(WS_THREADS)
 
     for (int i = tid; i < (int)(L::w_bytes / 16); i += WS_THREADS)
         ((uint4 *)ws)[i] = ((const uint4 *)wt)[i];
-    for (int i = tid; i < 32; i += WS_THREADS) bs[i] = bias ? bias[i] : 0.0f;
+    for (int i = tid; i < COUT; i += WS_THREADS) bs[i] = bias ? bias[i] : 0.0f;
     // planes that are not loaded (the first layer's channels 8-15) are zero
     for (int st = 0; st < WS_NS; ++st)
         for (int i = tid; i < (C8 - CL) * TC_PIN; i += WS_THREADS)
@@ -640,7 +669,7 @@ __global__ void __launch_bounds__(WS_THREADS)
                 make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int b = 0; b < L::n_bar; ++b) {
-            const uint32_t cnt = (b >= 2 * WS_NS + WS_NA && b < 2 * WS_NS + 2 * WS_NA) ? 4u : 1u;
+            const uint32_t cnt = (b >= 2 * WS_NS + NA && b < 2 * WS_NS + 2 * NA) ? 4u : 1u;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + b)), "r"(cnt));
         }
         *abort = 0;
@@ -697,30 +726,30 @@ __global__ void __launch_bounds__(WS_THREADS)
     } else if (warp == 5) {
         // ---- MMA issuer
         if (lane == 0) {
-            const uint64_t b0 = sdesc(smem_u32(ws), 32 * 16, 128);
+            const uint64_t b0 = sdesc(smem_u32(ws), COUT * 16, 128);
             long long done = 0;  // tiles whose MMAs were issued and committed
             for (long long i = 0;; ++i) {
                 const long long tile = blockIdx.x + i * G;
                 if (tile >= n_tiles) break;
-                const int s = (int)(i % WS_NS), a = (int)(i % WS_NA);
+                const int s = (int)(i % WS_NS), a = (int)(i % NA);
                 if (!ws_wait(smem_u32(full + s), (uint32_t)((i / WS_NS) & 1), spin_limit, abort) ||
-                    (i >= WS_NA &&
-                     !ws_wait(smem_u32(acce + a), (uint32_t)((i / WS_NA - 1) & 1), spin_limit, abort))) {
+                    (i >= NA &&
+                     !ws_wait(smem_u32(acce + a), (uint32_t)((i / NA - 1) & 1), spin_limit, abort))) {
                     ws_fail(abort, status);
                     break;
                 }
                 fence_after();
                 const uint64_t a0 = sdesc(smem_u32(stage(i)), TC_PIN * 16, 128);
-                const uint32_t d = tmem + (uint32_t)(a * 2 * 32);
+                const uint32_t d = tmem + (uint32_t)(a * 2 * CST);
 #pragma unroll
                 for (int m = 0; m < TC_MT; ++m)
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
                         for (int ks = 0; ks < CIN / 16; ++ks)
-                            mma_bf16(d + (uint32_t)(m * 32),
+                            mma_bf16(d + (uint32_t)(m * CST),
                                      a0 + (uint64_t)(2 * ks * TC_PIN + m * 128 + (tap / 3) * TC_PW + tap % 3),
-                                     b0 + (uint64_t)((tap * C8 + 2 * ks) * 32), IDESC, (tap | ks) ? 1u : 0u);
+                                     b0 + (uint64_t)((tap * C8 + 2 * ks) * COUT), IDESC, (tap | ks) ? 1u : 0u);
                 mma_commit(smem_u32(empty + s));
                 // (test hook: the first tile's completion is never signalled, so
                 // the epilogue's wait for it gives up and the failure path runs)
@@ -734,28 +763,53 @@ __global__ void __launch_bounds__(WS_THREADS)
             mbar_wait(smem_u32(drain), 0u, TC_SPIN_LIMIT);
             for (long long i = done > WS_NS ? done - WS_NS : 0; i < done; ++i)
                 mbar_wait(smem_u32(empty + i % WS_NS), (uint32_t)((i / WS_NS) & 1), TC_SPIN_LIMIT);
-            for (long long i = done > WS_NA ? done - WS_NA : 0; i < done; ++i)
+            for (long long i = done > NA ? done - NA : 0; i < done; ++i)
                 if (!(no_commit_first && i == 0))
-                    mbar_wait(smem_u32(accf + i % WS_NA), (uint32_t)((i / WS_NA) & 1), TC_SPIN_LIMIT);
+                    mbar_wait(smem_u32(accf + i % NA), (uint32_t)((i / NA) & 1), TC_SPIN_LIMIT);
         }
     } else {
         // ---- epilogue (warps 0-3)
+        constexpr bool UP = EPI == TC_EPI_UPSAMPLE;
+        if (UP && blockIdx.x < n_tiles) fetch_lr(rgb, lr_depth, h, w, tile_xy(blockIdx.x, tx, ty), lbuf(0));
         for (long long i = 0;; ++i) {
             const long long tile = blockIdx.x + i * G;
             if (tile >= n_tiles) break;
-            const int a = (int)(i % WS_NA);
-            const bool ok = ws_wait(smem_u32(accf + a), (uint32_t)((i / WS_NA) & 1), spin_limit, abort);
-            if (!__all_sync(0xffffffffu, ok)) {
+            const int a = (int)(i % NA);
+            const bool ok = ws_wait(smem_u32(accf + a), (uint32_t)((i / NA) & 1), spin_limit, abort);
+            if (UP) {
+                // One barrier of the four epilogue warps that also agrees on
+                // failure (so that all of them leave together): after it, tile
+                // i's LR tile has landed for all four, and every warp is done
+                // with tile i - 1's, whose buffer now takes tile i + 1's.
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                __syncwarp();
+                uint32_t any_fail;
+                asm volatile(
+                    "{\n\t.reg .pred p, q;\n\t"
+                    "setp.ne.u32 p, %1, 0;\n\t"
+                    "bar.red.or.pred q, 1, 128, p;\n\t"
+                    "selp.u32 %0, 1, 0, q;\n\t}\n"
+                    : "=r"(any_fail)
+                    : "r"(ok ? 0u : 1u)
+                    : "memory");
+                if (any_fail) {
+                    if (tid == 0) ws_fail(abort, status);
+                    break;
+                }
+                if (tile + G < n_tiles) fetch_lr(rgb, lr_depth, h, w, tile_xy(tile + G, tx, ty), lbuf(i + 1));
+            } else if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) ws_fail(abort, status);
                 break;
             }
             fence_after();
-            tile_epilogue<32, TC_EPI_RELU_P>(tmem, (uint32_t)(a * 2 * 32), tile_xy(tile, tx, ty), h, w, bs,
-                                             nullptr, out, nullptr, nullptr);
+            tile_epilogue<COUT, UP ? TC_EPI_UPSAMPLE : TC_EPI_RELU_P>(
+                tmem, (uint32_t)(a * 2 * CST), tile_xy(tile, tx, ty), h, w, bs, UP ? lbuf(i) : nullptr, out,
+                hr_depth, nullptr);
             fence_before();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(acce + a)) : "memory");
         }
+        if (UP) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     }
     fence_before();
     __syncthreads();
@@ -783,11 +837,12 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-template <int CIN>
-cudaError_t run_ws(const bf16 *x, int n, int h, int w, const bf16 *wt, const float *bias, bf16 *out,
+template <int CIN, int COUT = 32, int EPI = TC_EPI_RELU_P>
+cudaError_t run_ws(const bf16 *x, int n, int h, int w, const bf16 *wt, const float *bias, void *out,
                    int *status, int n_sm, cudaStream_t s, long long spin_limit = TC_SPIN_LIMIT,
-                   int no_commit_first = 0) {
-    using L = WsSmem<CIN>;
+                   int no_commit_first = 0, const float *rgb = nullptr, const float *lr_depth = nullptr,
+                   float *hr_depth = nullptr) {
+    using L = WsSmem<CIN, COUT, EPI>;
     static_assert(WS_BPS * (L::total + 1024) <= (size_t)228 * 1024, "stages fit shared memory");
     const long long tiles = (long long)((w + TC_TW - 1) / TC_TW) * ((h + TC_TH - 1) / TC_TH) * n;
     if (tiles == 0) return cudaSuccess;
@@ -805,12 +860,12 @@ cudaError_t run_ws(const bf16 *x, int n, int h, int w, const bf16 *wt, const flo
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    auto kern = k_conv_ws<CIN>;
+    auto kern = k_conv_ws<CIN, COUT, EPI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<long long>(tiles, (long long)WS_BPS * n_sm);
-    kern<<<grid, WS_THREADS, L::total, s>>>(map, n, h, w, wt, bias, out, status, spin_limit,
-                                            no_commit_first);
+    kern<<<grid, WS_THREADS, L::total, s>>>(map, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth, status,
+                                            spin_limit, no_commit_first);
     return cudaGetLastError();
 }
 
@@ -879,10 +934,10 @@ cudaError_t up_conv_tc_planar(int layer, const __nv_bfloat16 *x, int n, int h, i
                               const __nv_bfloat16 *wt, const float *bias, void *out,
                               const float *rgb, const float *lr_depth, float *hr_depth,
                               int *status, int n_sm, cudaStream_t s) {
-    if (layer == 0) return run_ws<16>(x, n, h, w, wt, bias, (bf16 *)out, status, n_sm, s);
-    if (layer < 5) return run_ws<32>(x, n, h, w, wt, bias, (bf16 *)out, status, n_sm, s);
-    return run_tc<32, 48, TC_EPI_UPSAMPLE, true>(x, n, h, w, wt, bias, out, rgb, lr_depth, hr_depth,
-                                                 nullptr, status, n_sm, s);
+    if (layer == 0) return run_ws<16>(x, n, h, w, wt, bias, out, status, n_sm, s);
+    if (layer < 5) return run_ws<32>(x, n, h, w, wt, bias, out, status, n_sm, s);
+    return run_ws<32, 48, TC_EPI_UPSAMPLE>(x, n, h, w, wt, bias, out, status, n_sm, s, TC_SPIN_LIMIT, 0,
+                                           rgb, lr_depth, hr_depth);
 }
 
 // Training: the last layer's raw output z = conv + bias (FP32 [n][h][w][48]).
