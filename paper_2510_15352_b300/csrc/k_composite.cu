@@ -223,11 +223,18 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
             nkept += wtotal;
             __syncthreads();
         }
-        // 3. composite the kept records, COMP_BATCH at a time
+        // 3. composite the kept records, COMP_BATCH at a time. With one warp per
+        // block (and no counting), a record no pixel of the tile can take is not
+        // staged at all (order-preserving ballot compaction), so the blend loop
+        // visits only records that may contribute; otherwise every record is
+        // staged with its per-warp mask.
+        constexpr bool COMPACT = NWARP == 1 && !STATS;
         for (uint32_t j0 = 0; j0 < nkept; j0 += COMP_BATCH) {
-            const int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
-            for (int q = tid; q < nb; q += NT) {
-                const long long sl = rec0 + cv[cand[j0 + q]];
+            int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
+            int nstaged = 0;
+            for (int q0 = 0; q0 < nb; q0 += NT) {
+                const int q = q0 + tid;
+                const long long sl = rec0 + cv[cand[j0 + min(q, nb - 1)]];
                 const float4 a = rec[rec_a(sl)], b = rec[rec_b(sl)], cc = rec[rec_c(sl)];
                 // warps some pixel of which can pass the alpha test: the box of the
                 // alpha >= alpha_min region meets the warp's rows and the largest p
@@ -250,10 +257,22 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                         P.log2_alpha_min - margin)
                         m |= 1u << k;
                 }
-                s0[q] = make_float4(a.x, a.y, b.x, b.y);
-                s1[q] = make_float4(b.z, b.w, cc.w, __uint_as_float(m));
-                s2[q] = cc;
+                if (q >= nb) m = 0;
+                int at = q;
+                bool put = q < nb;
+                if (COMPACT) {
+                    const uint32_t bal = __ballot_sync(0xffffffffu, m != 0);
+                    at = nstaged + __popc(bal & ((1u << lane) - 1u));
+                    put = m != 0;
+                    nstaged += __popc(bal);
+                }
+                if (put) {
+                    s0[at] = make_float4(a.x, a.y, b.x, b.y);
+                    s1[at] = make_float4(b.z, b.w, cc.w, __uint_as_float(m));
+                    s2[at] = cc;
+                }
             }
+            if (COMPACT) nb = nstaged;
             __syncthreads();
             live = false;
 #pragma unroll
