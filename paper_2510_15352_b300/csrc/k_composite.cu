@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                         for (int k = 0; k < PPT; ++k) ev += thr[k] != INF ? 1u : 0u;
                     }
                     if (STATS) wi++;
-                    if (!(__float_as_uint(g1.w) & warp_bit)) continue;  // warp-uniform
+                    // warp-uniform (every staged record has the bit when compacted)
+                    if (!COMPACT && !(__float_as_uint(g1.w) & warp_bit)) continue;
                     if (STATS) wbox++;
                     const float4 g0 = s0[j];  // u, v, a', b'
                     // the thread's pixels k = 0..PPT-1 lie at dx = dx0 + k CPR, so
