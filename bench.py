@@ -280,7 +280,7 @@ def upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb_plain, stream, 
         "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
         "stages_ms_per_step": {"render_lr": ms_lr, "cnn": ms_cnn},
         "cnn_roofline": {
-            "kernel": "k_conv_ws (layers 1-5, TMA + tcgen05) + k_conv_tc (layer 6, tcgen05) + k_prep_input_plane",
+            "kernel": "k_conv_ws (6 layers, TMA + tcgen05, warp-specialised) + k_prep_input_plane",
             "bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
             "frac": cnn_tflops / bf16_peak if cnn_tflops else None,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the CNN is timed alone)",
@@ -437,11 +437,121 @@ def run_b300_batched(args):
         "camera_frames_per_s": whole_job_rate(n * args.steps, world, ms / 1e3),
         "clocks": clk, "gpu_launches": None,
     }
+    R.close()
+    if args.up_pairs > 0:
+        ups = upsampled_batched_leg(args, gs, synth, scenes, which, vm, local, stream)
+        if rank == 0:
+            out["upsampled"] = ups
     if rank == 0:
         print(json.dumps(out), flush=True)
-    R.close()
     if dist:
         dist.destroy_process_group()
+
+
+def upsampled_batched_leg(args, gs, synth, scenes, which, vm, local, stream):
+    """The upsampled path on the batched scenes: every one of the batch's
+    cameras at 640x480 (f = 480), rendered at 160x120 (intrinsics / 4) and
+    upsampled by the learned network, against the plain 640x480 render of the
+    same cameras (time and PSNR). The network is trained first (untimed) on
+    renderer pairs of held-out poses cycling through the scenes; each scene is
+    validated on 8 other poses, and the cameras of a scene below 35 dB would be
+    rendered at full resolution instead."""
+    import numpy as np
+    import torch
+    from paper_2510_15352_b300 import upsampler
+    W, H = 640, 480
+    n = len(vm)
+    vm_d = torch.from_numpy(vm).cuda()
+    it_d = torch.tensor([[480.0, 480.0, W / 2.0, H / 2.0]], dtype=torch.float32,
+                        device="cuda").expand(n, 4).contiguous()
+    R = gs.Renderer(device=local, max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
+                    tiles_per_block=args.tpb, camera_group=args.group)
+    sids = [R.add_scene(sc) for sc in scenes]
+    ids = np.array(sids, dtype=np.int32)[which]
+    up = gs.Upsampler(device=local)
+    bil = gs.Upsampler(device=local)
+    try:
+        up.set_params(upsampler.init_params(0))
+        bil.set_params(np.zeros(gs.Upsampler.n_params, np.float32))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = upsampler.train(up, R, sids, W, H, n_pairs=args.up_pairs, frames_per_step=4,
+                                 lr_max=1e-3, lr_min=3e-5, seed=100)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        val = {}
+        for k, sid in enumerate(sids):
+            vmv, itv = synth.make_cameras(8, W, H, 0.75 * W, (0.3, 1.2), seed=7000 + k)
+            val[k] = upsampler.evaluate(up, R, sid, vmv, itv, W, H)["psnr_mean"]
+        slow = np.array([val[int(which[i])] < 35.0 for i in range(n)])
+        fast_idx = torch.from_numpy(np.nonzero(~slow)[0]).cuda()
+        slow_idx = torch.from_numpy(np.nonzero(slow)[0]).cuda()
+        plain = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
+        plain_d = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+        out = torch.empty_like(plain)
+        out_d = torch.empty_like(plain_d)
+        vm_f, it_f, ids_f = vm_d[fast_idx].contiguous(), it_d[fast_idx].contiguous(), ids[~slow]
+        vm_s, it_s, ids_s = vm_d[slow_idx].contiguous(), it_d[slow_idx].contiguous(), ids[slow]
+        out_f = torch.empty((len(ids_f), H, W, 3), dtype=torch.float32, device="cuda")
+        out_fd = torch.empty((len(ids_f), H, W), dtype=torch.float32, device="cuda")
+        out_s = torch.empty((len(ids_s), H, W, 3), dtype=torch.float32, device="cuda")
+        out_sd = torch.empty((len(ids_s), H, W), dtype=torch.float32, device="cuda")
+
+        def plain_step():
+            R.render(ids, vm_d, it_d, W, H, plain, plain_d, stream=stream)
+
+        def up_step():
+            if len(ids_f):
+                R.render_upsampled(up, ids_f, vm_f, it_f, W, H, out_f, out_fd, stream=stream)
+            if len(ids_s):
+                R.render(ids_s, vm_s, it_s, W, H, out_s, out_sd, stream=stream)
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / args.steps
+
+        ms_plain = timed(plain_step)
+        ms_up = timed(up_step)
+        up.check(stream)
+        out[fast_idx] = out_f
+        if len(ids_s):
+            out[slow_idx] = out_s
+        p_net = upsampler.psnr(out, plain).cpu().numpy()
+        # bilinear x4 of the quarter-resolution render, for reference
+        lr = torch.empty((n, H // 4, W // 4, 3), dtype=torch.float32, device="cuda")
+        R.render(ids, vm_d, it_d / 4.0, W // 4, H // 4, lr, stream=stream)
+        ob = torch.empty_like(plain)
+        for c0 in range(0, n, 512):
+            o, _ = bil.forward(lr[c0:c0 + 512])
+            ob[c0:c0 + 512] = o
+        p_bil = upsampler.psnr(ob, plain).cpu().numpy()
+    finally:
+        up.close()
+        bil.close()
+        R.close()
+    return {
+        "value": n / (ms_up / 1e3), "unit": UNIT, "ms_per_step": ms_up,
+        "cameras": n, "render": "all cameras at 640x480 (f = 480): 160x120 render (intrinsics / 4) "
+        "then the learned 4x upsampler (gs_render_batch_upsampled)",
+        "plain_same_cameras": {"value": n / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain},
+        "speedup_vs_plain": ms_plain / ms_up,
+        "fallback_cameras": int(slow.sum()),
+        "psnr_db_mean": float(p_net.mean()), "psnr_db_p5": float(np.percentile(p_net, 5)),
+        "bilinear_psnr_db_mean": float(p_bil.mean()),
+        "bilinear_psnr_db_p5": float(np.percentile(p_bil, 5)),
+        "validation_psnr_db_min_over_scenes": float(min(val.values())),
+        "train_pairs": int(args.up_pairs), "train_s": t_train,
+        "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
+    }
 
 
 def run_b300(args):
