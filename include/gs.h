@@ -363,10 +363,11 @@ gs_status gs_upsampler_set_backend(gs_upsampler *u, int32_t backend);
 gs_status gs_upsample_check(gs_upsampler *u, void *stream);
 
 /* Test hook for the failure path of the tensor-core kernels (no counterpart in
- * the paper): enqueues one hidden-layer convolution on a small internal input
- * whose first MMA completion per block is deliberately never signalled, with
+ * the paper): enqueues a hidden-layer convolution and a last-layer
+ * (upsampling) convolution on a small internal input, in each of which the
+ * first accumulator-ready signal per block is deliberately never sent, with
  * waits that give up after 4,096 polls. Every block then records the time-out,
- * waits for its own MMAs and frees its tensor memory; the next
+ * waits for its own loads and MMAs and frees its tensor memory; the next
  * gs_upsample_check returns GS_ERR_TIMEOUT and the upsampler stays usable. No
  * GPU fault is involved. */
 gs_status gs_upsample_timeout_probe(gs_upsampler *u, void *stream);

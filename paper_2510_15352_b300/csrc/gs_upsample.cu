@@ -43,6 +43,11 @@ cudaError_t up_conv_tc_linear(const __nv_bfloat16 *x, int n, int h, int w,
 cudaError_t up_conv_tc_timeout_probe(const __nv_bfloat16 *x, int n, int h, int w,
                                      const __nv_bfloat16 *wt, const float *bias, __nv_bfloat16 *out,
                                      int *status, int n_sm, long long spin_limit, cudaStream_t s);
+cudaError_t up_conv_tc_timeout_probe_up(const __nv_bfloat16 *x, int n, int h, int w,
+                                        const __nv_bfloat16 *wt, const float *bias,
+                                        const float *rgb, const float *lr_depth, float *hr,
+                                        float *hr_depth, int *status, int n_sm,
+                                        long long spin_limit, cudaStream_t s);
 cudaError_t up_dgrad_tc(int layer, const __nv_bfloat16 *dz, int n, int h, int w,
                         const __nv_bfloat16 *wdt, const __nv_bfloat16 *act, __nv_bfloat16 *dx,
                         int *status, int n_sm, cudaStream_t s);
@@ -298,15 +303,23 @@ gs_status gs_upsample_timeout_probe(gs_upsampler *u, void *stream) {
     DeviceGuard dg(u->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int n = 4, h = 28, w = 32;  // 16 tiles: several blocks
-    const size_t bytes = 2 * align256((size_t)n * h * w * 32 * sizeof(bf16));
-    cudaError_t e = grow(u->work, bytes);
+    const size_t px = (size_t)n * h * w;
+    const size_t act = align256(px * 32 * sizeof(bf16)), lr = align256(px * 4 * sizeof(float));
+    const size_t hr = align256(px * 16 * 4 * sizeof(float));
+    cudaError_t e = grow(u->work, 2 * act + lr + hr);
     if (e != cudaSuccess) return cuda_fail(u, e, "timeout_probe: workspace");
-    bf16 *x = (bf16 *)u->work.p;
-    bf16 *y = (bf16 *)((char *)u->work.p + bytes / 2);
-    e = cudaMemsetAsync(x, 0, bytes / 2, s);
-    if (e == cudaSuccess)
+    char *base = (char *)u->work.p;
+    bf16 *x = (bf16 *)base, *y = (bf16 *)(base + act);
+    float *rgb = (float *)(base + 2 * act), *dep = rgb + px * 3;
+    float *hrgb = (float *)(base + 2 * act + lr), *hdep = hrgb + px * 16 * 3;
+    e = cudaMemsetAsync(base, 0, 2 * act + lr, s);
+    if (e == cudaSuccess)  // a hidden layer
         e = gsk::up_conv_tc_timeout_probe(x, n, h, w, u->wt[1], u->params + layer_off(1) + 32 * 32 * 9,
                                           y, u->status, u->n_sm, 1 << 12, s);
+    if (e == cudaSuccess)  // the last layer
+        e = gsk::up_conv_tc_timeout_probe_up(x, n, h, w, u->wt[5],
+                                             u->params + layer_off(5) + (long long)48 * 32 * 9, rgb, dep,
+                                             hrgb, hdep, u->status, u->n_sm, 1 << 12, s);
     return e == cudaSuccess ? GS_OK : cuda_fail(u, e, "timeout_probe");
 }
 

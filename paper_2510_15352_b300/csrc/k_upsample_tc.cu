@@ -970,4 +970,15 @@ cudaError_t up_conv_tc_timeout_probe(const __nv_bfloat16 *x, int n, int h, int w
     return run_ws<32>(x, n, h, w, wt, bias, out, status, n_sm, s, spin_limit, 1);
 }
 
+// The same for the last layer's kernel (N = 48, upsampling epilogue whose four
+// warps share a barrier): rgb / lr_depth [n][h][w](x3), hr / hr_depth [n][4h][4w](x3).
+cudaError_t up_conv_tc_timeout_probe_up(const __nv_bfloat16 *x, int n, int h, int w,
+                                        const __nv_bfloat16 *wt, const float *bias,
+                                        const float *rgb, const float *lr_depth, float *hr,
+                                        float *hr_depth, int *status, int n_sm,
+                                        long long spin_limit, cudaStream_t s) {
+    return run_ws<32, 48, TC_EPI_UPSAMPLE>(x, n, h, w, wt, bias, hr, status, n_sm, s, spin_limit, 1,
+                                           rgb, lr_depth, hr_depth);
+}
+
 }  // namespace gsk
