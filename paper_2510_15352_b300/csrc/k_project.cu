@@ -9,6 +9,8 @@
 //
 // Two passes keep the survivor order deterministic (Gaussian-index order)
 // without a global sort key that carries the index:
+//   k_cam_setup     -- once per chunk: each camera's projection constants, which
+//                      both passes copy into shared memory per block;
 //   k_project_mask  -- survival bit per (camera, Gaussian), one warp ballot per
 //                      32 Gaussians -> a 32-bit mask word;
 //   k_scan_masks    -- per camera, exclusive prefix of the mask popcounts;
@@ -17,8 +19,9 @@
 //                      the surviving (camera, Gaussian) pairs into a dense item
 //                      list, and for every item
 //                      recomputes the projection, evaluates the SH colour and
-//                      writes the record, the depth key (float bits of z) and
-//                      the slot at a stable position.
+//                      writes the record, the rect and the depth key (float
+//                      bits of z minus those of the near plane) at the pair's
+//                      stable slot.
 // The decision chain is written with explicit fmaf / *_rn intrinsics so both
 // passes round identically.
 #include <type_traits>

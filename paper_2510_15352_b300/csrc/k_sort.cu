@@ -24,6 +24,9 @@
 //                     the tile is put in sorted order in shared memory, then
 //                     written out run by run (coalesced) at segment start +
 //                     run start + rank.
+// A block finds its tile's segment base, offset and key count in a per-tile
+// table when the caller provides one (the render's plan kernel writes it), else
+// by searching the segment table.
 // Stable rank inside a tile: warp w takes keys [256 w, 256 w + 256) in rounds
 // of 32; a key's rank is (equal digits in earlier warps) + (equal digits in
 // earlier rounds of its warp) + (equal digits in lower lanes of its round,
