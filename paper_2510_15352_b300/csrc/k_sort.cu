@@ -193,16 +193,20 @@ __global__ void __launch_bounds__(ST, 5)
     for (int r = 0; r < SIPT; ++r) {
         const bool ok = i0 + r * 32 + lane < n;
         const uint32_t d = (kr[r] >> shift) & (ND - 1);
-        uint32_t peers = __ballot_sync(0xffffffffu, ok);
+        // lanes whose digit differs from this lane's in some bit: per bit, the
+        // ballot XOR this lane's bit spread over 32 bits
+        uint32_t differ = ~__ballot_sync(0xffffffffu, ok);
 #pragma unroll
         for (int b = 0; b < BITS; ++b) {
             const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bal : ~bal;
+            differ |= bal ^ (uint32_t)((int)(d << (31 - b)) >> 31);
         }
+        const uint32_t peers = ~differ;
+        const uint32_t below = peers & lt;
         const uint32_t before = wcnt[warp][d];
-        rk[r] = before + __popc(peers & lt);
+        rk[r] = before + __popc(below);
         __syncwarp();
-        if (ok && (__ffs(peers) - 1) == lane) wcnt[warp][d] = before + __popc(peers);
+        if (ok && below == 0u) wcnt[warp][d] = before + __popc(peers);  // lowest peer lane
         __syncwarp();
     }
     __syncthreads();
