@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(ST, 5)
     constexpr int ND = 1 << BITS, DPT = ND / ST;  // digits per thread (1 or 2)
     static_assert(ND % ST == 0, "digits are a multiple of the block size");
     __shared__ uint32_t wcnt[SNW][ND];
-    __shared__ uint32_t toff[ND];   // where the tile's run of each digit starts in the segment
     __shared__ uint32_t tdig[ND];   // where each digit starts in the tile's sorted order
+    __shared__ uint32_t tmove[ND];  // run start in the segment minus tdig (>= 0)
     __shared__ uint32_t dsum[SNW];
     __shared__ uint32_t skey[TK], sval[TK];
     if (run && !*run) return;
@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(ST, 5)
     const long long i0 = t0 + (long long)warp * (32 * SIPT);
     const long long n = t0 + T.nk;  // keys of the segment up to the end of this tile
     const int nk = T.nk;            // keys in this tile
+    uint32_t toff[DPT];  // where the tile's run of digit q * ST + tid starts in the segment
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) toff[q * ST + tid] = offs[(long long)tile * ND + q * ST + tid];
+    for (int q = 0; q < DPT; ++q) toff[q] = offs[(long long)tile * ND + q * ST + tid];
     for (int j = lane; j < ND; j += 32) wcnt[warp][j] = 0;
     uint32_t kr[SIPT], vr[SIPT], rk[SIPT];
 #pragma unroll
@@ -243,7 +244,9 @@ __global__ void __launch_bounds__(ST, 5)
             before += w < warp ? dsum[w] : 0u;
             all += dsum[w];
         }
-        tdig[q * ST + tid] = carry + before + incl - tot[q];
+        const uint32_t td = carry + before + incl - tot[q];
+        tdig[q * ST + tid] = td;
+        tmove[q * ST + tid] = toff[q] - td;
         carry += all;
         __syncthreads();
     }
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(ST, 5)
     for (int p = tid; p < nk; p += ST) {
         const uint32_t key = skey[p];
         const uint32_t d = (key >> shift) & (ND - 1);
-        const long long at = base + toff[d] + (p - tdig[d]);
+        const long long at = base + tmove[d] + p;
         dk[at] = key;
         dv[at] = sval[p];
     }
