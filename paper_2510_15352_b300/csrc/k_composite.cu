@@ -131,15 +131,22 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
     const float INF = __int_as_float(0x7f800000);
     // Per pixel: T, colour, depth and its own alpha threshold; a pixel that has
     // stopped (or lies outside the image) has threshold +inf, so it passes no
-    // further alpha test and its state stays frozen without a branch.
-    float T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT], thr[PPT];
+    // further alpha test and its state stays frozen without a branch. T and the
+    // sums are held for pixel pairs (k, k + 1) in float2 so the blend updates two
+    // pixels per packed FP32 instruction (each lane rounds as its scalar
+    // counterpart would).
+    constexpr int NPR = PPT / 2;
+    float2 T2[NPR], cr2[NPR], cg2[NPR], cb2[NPR], cd2[NPR];
+    float thr[PPT];
     const int x0 = tx * TILE + tid % CPR;  // pixel k of this thread is x0 + k * CPR
     const float px0 = x0 + 0.5f;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
+    for (int k = 0; k < PPT; ++k)
         thr[k] = (x0 + k * CPR < ci.W && y < ci.H) ? P.log2_alpha_min : INF;
-        T[k] = 1.0f;
-        cr[k] = cg[k] = cb[k] = cd[k] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NPR; ++i) {
+        T2[i] = make_float2(1.0f, 1.0f);
+        cr2[i] = cg2[i] = cb2[i] = cd2[i] = make_float2(0.0f, 0.0f);
     }
     const uint32_t warp_bit = 1u << warp;
     unsigned long long ev = 0, al = 0, wi = 0, wbox = 0, wbl = 0;
@@ -298,36 +305,48 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                     const float P0 = fmaf(t0, dx0, fmaf(g1.x * dy, dy, g1.y));
                     const float D = (float)CPR * fmaf(g0.z, dx0, t0);
                     const float E = (float)(CPR * CPR) * g0.z;
+                    const float2 P02 = make_float2(P0, P0), D2 = make_float2(D, D),
+                                 E2 = make_float2(E, E);
                     float p[PPT];
                     bool any = false;
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        p[k] = k == 0 ? P0 : fmaf((float)k, fmaf((float)k, E, D), P0);
-                        any = any || p[k] >= thr[k];
+                    for (int i = 0; i < NPR; ++i) {
+                        const float2 K = make_float2((float)(2 * i), (float)(2 * i + 1));
+                        const float2 pp = __ffma2_rn(K, __ffma2_rn(K, E2, D2), P02);
+                        p[2 * i] = pp.x;
+                        p[2 * i + 1] = pp.y;
+                        any = any || pp.x >= thr[2 * i] || pp.y >= thr[2 * i + 1];
                     }
                     if (!__any_sync(0xffffffffu, any)) continue;
                     if (STATS) wbl++;
                     const float4 g2 = s2[j];  // red, green, blue
+                    const float2 R2 = make_float2(g2.x, g2.x), G2 = make_float2(g2.y, g2.y),
+                                 B2 = make_float2(g2.z, g2.z), Z2 = make_float2(g1.z, g1.z);
+                    const float2 M1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        // alpha is 0 for a pair that fails the test (and for a
-                        // stopped pixel, whose threshold is +inf); then
-                        // T - alpha T >= T_min holds (T >= T_min for every pixel),
-                        // so "keep" is false exactly when a passing pair would
-                        // take T below T_min: that pair is not added and the
-                        // pixel stops
-                        const bool pass = p[k] >= thr[k];
-                        if (STATS) al += pass ? 1u : 0u;
-                        const float alpha = pass ? fminf(P.alpha_max, ex2_approx(p[k])) : 0.0f;
-                        const float wgt = alpha * T[k];
-                        const bool keep = T[k] - wgt >= P.T_min;
-                        const float wa = keep ? wgt : 0.0f;
-                        cr[k] = fmaf(wa, g2.x, cr[k]);
-                        cg[k] = fmaf(wa, g2.y, cg[k]);
-                        cb[k] = fmaf(wa, g2.z, cb[k]);
-                        cd[k] = fmaf(wa, g1.z, cd[k]);
-                        T[k] -= wa;
-                        thr[k] = keep ? thr[k] : INF;
+                    for (int i = 0; i < NPR; ++i) {
+                        // A pair that passes its alpha test (a stopped pixel,
+                        // threshold +inf, passes none) is added when T - alpha T
+                        // stays >= T_min; otherwise it is not added and the pixel
+                        // stops. A pair that fails adds nothing, whatever its
+                        // (unused) alpha.
+                        const int k = 2 * i;
+                        const bool pass0 = p[k] >= thr[k], pass1 = p[k + 1] >= thr[k + 1];
+                        if (STATS) al += (pass0 ? 1u : 0u) + (pass1 ? 1u : 0u);
+                        const float2 alpha = make_float2(fminf(P.alpha_max, ex2_approx(p[k])),
+                                                         fminf(P.alpha_max, ex2_approx(p[k + 1])));
+                        const float2 wgt = __fmul2_rn(alpha, T2[i]);
+                        const float2 Tn = __ffma2_rn(wgt, M1, T2[i]);  // T - wgt
+                        const bool ok0 = Tn.x >= P.T_min, ok1 = Tn.y >= P.T_min;
+                        const float2 wa = make_float2(pass0 && ok0 ? wgt.x : 0.0f,
+                                                      pass1 && ok1 ? wgt.y : 0.0f);
+                        cr2[i] = __ffma2_rn(wa, R2, cr2[i]);
+                        cg2[i] = __ffma2_rn(wa, G2, cg2[i]);
+                        cb2[i] = __ffma2_rn(wa, B2, cb2[i]);
+                        cd2[i] = __ffma2_rn(wa, Z2, cd2[i]);
+                        T2[i] = __ffma2_rn(wa, M1, T2[i]);  // T - wa
+                        thr[k] = pass0 && !ok0 ? INF : thr[k];
+                        thr[k + 1] = pass1 && !ok1 ? INF : thr[k + 1];
                     }
                 }
             }
@@ -344,8 +363,13 @@ finished:
         const int x = x0 + k * CPR;
         if (x >= ci.W || y >= ci.H) continue;
         const long long pix = ci.pix_off + (long long)y * ci.W + x;
-        float o[5] = {fmaf(T[k], P.bg[0], cr[k]), fmaf(T[k], P.bg[1], cg[k]),
-                      fmaf(T[k], P.bg[2], cb[k]), cd[k], T[k]};
+        const float Tk = k & 1 ? T2[k >> 1].y : T2[k >> 1].x;
+        const float crk = k & 1 ? cr2[k >> 1].y : cr2[k >> 1].x;
+        const float cgk = k & 1 ? cg2[k >> 1].y : cg2[k >> 1].x;
+        const float cbk = k & 1 ? cb2[k >> 1].y : cb2[k >> 1].x;
+        const float cdk = k & 1 ? cd2[k >> 1].y : cd2[k >> 1].x;
+        float o[5] = {fmaf(Tk, P.bg[0], crk), fmaf(Tk, P.bg[1], cgk),
+                      fmaf(Tk, P.bg[2], cbk), cdk, Tk};
         if (P.accumulate) {  // one sub-frame of a blended image (motion blur)
             o[0] = fmaf(P.out_w, o[0], rgb[3 * pix + 0]);
             o[1] = fmaf(P.out_w, o[1], rgb[3 * pix + 1]);
