@@ -25,8 +25,12 @@
 // rounding, so the skip never changes a result); the blend runs only
 // when some lane passes the alpha test (warp vote) and is branch-free: a
 // stopped pixel's alpha threshold becomes +inf, which freezes it. The block
-// stops reading its list once every pixel has stopped. No tensor cores: this
-// is not a dense contraction.
+// stops reading its list once every pixel has stopped. The blend updates T and
+// the sums of two pixels per packed FP32x2 instruction (each lane rounds as
+// the scalar instruction would), and with one warp per tile the records are
+// taken two at a time: both quadratics, then both votes, then the blends, so
+// the two records' latencies overlap. No tensor cores: this is not a dense
+// contraction.
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -285,19 +289,10 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
 #pragma unroll
             for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
             if (__any_sync(0xffffffffu, live)) {
-                for (int j = 0; j < nb; ++j) {
-                    const float4 g1 = s1[j];  // c', log2 o, z, warp mask
-                    if (STATS) {
-#pragma unroll
-                        for (int k = 0; k < PPT; ++k) ev += thr[k] != INF ? 1u : 0u;
-                    }
-                    if (STATS) wi++;
-                    // warp-uniform (every staged record has the bit when compacted)
-                    if (!COMPACT && !(__float_as_uint(g1.w) & warp_bit)) continue;
-                    if (STATS) wbox++;
-                    const float4 g0 = s0[j];  // u, v, a', b'
-                    // the thread's pixels k = 0..PPT-1 lie at dx = dx0 + k CPR, so
-                    // p_k = a'dx^2 + b'dy dx + c'dy^2 + log2 o = P0 + k (D + k E)
+                // p_k = a'dx^2 + b'dy dx + c'dy^2 + log2 o of the thread's pixels
+                // k = 0..PPT-1 (at dx = dx0 + k CPR: P0 + k (D + k E)); true when
+                // some pixel passes its alpha test
+                auto quad_p = [&](const float4 &g0, const float4 &g1, float (&p)[PPT]) {
                     const float dy = py - g0.y;
                     const float dx0 = px0 - g0.x;
                     const float bdy = g0.w * dy;
@@ -307,7 +302,6 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                     const float E = (float)(CPR * CPR) * g0.z;
                     const float2 P02 = make_float2(P0, P0), D2 = make_float2(D, D),
                                  E2 = make_float2(E, E);
-                    float p[PPT];
                     bool any = false;
 #pragma unroll
                     for (int i = 0; i < NPR; ++i) {
@@ -317,11 +311,11 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                         p[2 * i + 1] = pp.y;
                         any = any || pp.x >= thr[2 * i] || pp.y >= thr[2 * i + 1];
                     }
-                    if (!__any_sync(0xffffffffu, any)) continue;
-                    if (STATS) wbl++;
-                    const float4 g2 = s2[j];  // red, green, blue
+                    return any;
+                };
+                auto blend = [&](const float (&p)[PPT], const float4 &g2, float z) {
                     const float2 R2 = make_float2(g2.x, g2.x), G2 = make_float2(g2.y, g2.y),
-                                 B2 = make_float2(g2.z, g2.z), Z2 = make_float2(g1.z, g1.z);
+                                 B2 = make_float2(g2.z, g2.z), Z2 = make_float2(z, z);
                     const float2 M1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
                     for (int i = 0; i < NPR; ++i) {
@@ -347,6 +341,52 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
                         T2[i] = __ffma2_rn(wa, M1, T2[i]);  // T - wa
                         thr[k] = pass0 && !ok0 ? INF : thr[k];
                         thr[k + 1] = pass1 && !ok1 ? INF : thr[k + 1];
+                    }
+                };
+                if constexpr (COMPACT) {
+                    // Records in groups of UNR: their quadratics and votes are
+                    // independent, so their latencies overlap. A record's vote
+                    // sees the thresholds before the group's earlier blends; a
+                    // pixel can only stop there, so the vote may say "some pixel
+                    // passes" when none does (the blend then adds nothing), never
+                    // the reverse.
+                    constexpr int UNR = 2;
+                    int j = 0;
+                    for (; j + UNR <= nb; j += UNR) {
+                        float4 g1u[UNR];
+                        float pu[UNR][PPT];
+                        bool vu[UNR];
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u) g1u[u] = s1[j + u];
+                        // every quadratic before the first vote (a vote is a
+                        // warp-wide step the compiler does not move work across)
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u) vu[u] = quad_p(s0[j + u], g1u[u], pu[u]);
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u) vu[u] = __any_sync(0xffffffffu, vu[u]);
+#pragma unroll
+                        for (int u = 0; u < UNR; ++u)
+                            if (vu[u]) blend(pu[u], s2[j + u], g1u[u].z);
+                    }
+                    for (; j < nb; ++j) {
+                        const float4 g1 = s1[j];
+                        float p[PPT];
+                        if (__any_sync(0xffffffffu, quad_p(s0[j], g1, p))) blend(p, s2[j], g1.z);
+                    }
+                } else {
+                    for (int j = 0; j < nb; ++j) {
+                        const float4 g1 = s1[j];  // c', log2 o, z, warp mask
+                        if (STATS) {
+#pragma unroll
+                            for (int k = 0; k < PPT; ++k) ev += thr[k] != INF ? 1u : 0u;
+                        }
+                        if (STATS) wi++;
+                        if (!(__float_as_uint(g1.w) & warp_bit)) continue;  // warp-uniform
+                        if (STATS) wbox++;
+                        float p[PPT];
+                        if (!__any_sync(0xffffffffu, quad_p(s0[j], g1, p))) continue;
+                        if (STATS) wbl++;
+                        blend(p, s2[j], g1.z);
                     }
                 }
             }
