@@ -62,7 +62,7 @@ struct gs_context {
     DevBuf wide;  // per chunk: some depth key needs the sort's fourth pass
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
-    int workspace_gen = 0;        // bumped when the survivor buffers are reallocated
+    int workspace_gen = 0;        // bumped when a chunk-workspace buffer is reallocated
     // host-API staging
     DevBuf h_vm, h_in, h_rgb, h_depth, h_T;
     DevBuf blur_vm;  // motion-blur sub-frame poses
@@ -275,7 +275,14 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     const long long S = std::max<long long>(ctx->cap_survivors, 1);
     const size_t Sx = (size_t)S;
     const int m = std::max(P.max_m, 1);
-    const bool changed = (ctx->rec.cap < rec_bytes(S));
+    // a captured graph holds these addresses: any reallocation invalidates it
+    DevBuf *held[] = {&ctx->masks,    &ctx->woff,     &ctx->counts,    &ctx->camtab, &ctx->rec,
+                      &ctx->srect,    &ctx->rrect,    &ctx->keys,      &ctx->vals,   &ctx->tkeys,
+                      &ctx->tvals,    &ctx->bitmap,   &ctx->sorthist,  &ctx->sorttab,
+                      &ctx->bintab,   &ctx->wide,     &ctx->blkpre,    &ctx->sorttiles,
+                      &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status};
+    void *before[sizeof(held) / sizeof(held[0])];
+    for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->p;
     CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->woff, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->counts, (size_t)m * sizeof(int)));
@@ -299,7 +306,11 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->segcount, (size_t)m * sizeof(long long)));
     CKS(grow(ctx, ctx->stats, 8 * sizeof(unsigned long long)));
     CKS(grow(ctx, ctx->status, (P.chunks.size() + 2) * sizeof(long long)));
-    if (changed) ctx->workspace_gen++;
+    for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i)
+        if (held[i]->p != before[i]) {
+            ctx->workspace_gen++;
+            break;
+        }
     return GS_OK;
 }
 

@@ -90,3 +90,26 @@ def test_graph_overflow_and_invalidation(torch):
         g2.close()
     finally:
         r.close()
+
+
+def test_graph_invalidated_by_bitmap_growth(torch):
+    """A render at twice the resolution grows the binning bitmaps (more
+    super-tiles per camera) while the survivor buffers keep their size; the
+    graph holds the old bitmap address, so launching it is refused."""
+    from paper_2510_15352_b300 import gs
+    r, ids, vm, it, Ws, Hs, P = _setup(torch, gs, workspace_survivors=4_000_000)
+    try:
+        rgb = torch.zeros((P, 3), device="cuda")
+        dep = torch.zeros((P,), device="cuda")
+        g = r.graph(ids, vm, it, Ws, Hs, rgb, dep)
+        g.launch()
+        g.check()
+        W2, H2 = Ws * 2, Hs * 2
+        r.render_v(ids, vm, it, W2, H2)
+        torch.cuda.synchronize()
+        with pytest.raises(gs.GSError) as e:
+            g.launch()
+        assert e.value.status == gs.GS_ERR_INVALID_ARG
+        g.close()
+    finally:
+        r.close()
