@@ -358,7 +358,11 @@ __device__ __forceinline__ float load_staged_geo(const float4 (*rows)[N], int i,
 // memory; whenever 32 pairs are queued, each lane takes one and runs the exact
 // test (project()); the results are OR-ed into the warp's mask word of that
 // camera. Pairs the prefilter rejects are exactly those project() rejects
-// there, so the words equal one ballot of project() per camera.
+// there, so the words equal one ballot of project() per camera. A queued
+// pair's Gaussian belongs to a lane of the same warp, so the exact test takes
+// its geometry from that lane's registers by shuffles (13 of them) instead of
+// gathering rows of random Gaussians from shared memory (project 8.59 -> 8.52 ms
+// per 1,024 cameras).
 constexpr int MQ = 64;  // queue entries per warp: < 32 left + < 32 appended
 
 __global__ void __launch_bounds__(PROJ_THREADS)
@@ -371,8 +375,6 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     constexpr int NW = PROJ_THREADS / 32;
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long moff[MAX_GROUP];
-    // per Gaussian, as float4 rows: (mean, smax2), M[0..3], M[4..7], (M[8], -)
-    __shared__ float4 sgeo[4][PROJ_THREADS];
     __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane (camera < 64)
     __shared__ uint32_t smask[NW][MAX_GROUP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -393,23 +395,23 @@ __global__ void __launch_bounds__(PROJ_THREADS)
 #pragma unroll
         for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
     }
-    store_geo(sgeo, tid, G, 0.0f);
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
     int nq = 0;  // queued pairs of this warp (warp-uniform)
     // the exact test on queue entries [0, cnt) (cnt <= 32), results OR-ed into smask
     auto drain = [&](int cnt) {
-        bool surv = false;
-        int cam = 0;
+        const int e = lane < cnt ? (int)queue[warp][lane] : 0;
+        const int cam = e >> 5, src = e & 31;
+        GaussGeo H;  // the geometry of lane src's Gaussian (every lane shuffles)
+        H.mx = __shfl_sync(0xffffffffu, G.mx, src);
+        H.my = __shfl_sync(0xffffffffu, G.my, src);
+        H.mz = __shfl_sync(0xffffffffu, G.mz, src);
+        H.smax2 = __shfl_sync(0xffffffffu, G.smax2, src);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) H.M[k] = __shfl_sync(0xffffffffu, G.M[k], src);
         if (lane < cnt) {
-            const int e = queue[warp][lane];
-            cam = e >> 5;
-            const int gl = warp * 32 + (e & 31);
-            GaussGeo H;
-            load_staged_geo(sgeo, gl, H);
             Proj pr;
-            surv = project(load_cam(cp[cam]), H, P, pr);
-            if (surv) atomicOr(&smask[warp][cam], 1u << (e & 31));
+            if (project(load_cam(cp[cam]), H, P, pr)) atomicOr(&smask[warp][cam], 1u << src);
         }
         __syncwarp();
         // move the entries past the drained ones to the front
