@@ -254,6 +254,67 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     return true;
 }
 
+// The prefilter constants of two cameras (c, c + 1), field by field as float2
+// pairs, for prefilter2.
+struct __align__(16) CamPair {
+    float2 R[9], t[3];
+    float2 fx, fy, cx, cy;
+    float2 kk, W, H;
+    float2 pad;
+};
+static_assert(sizeof(CamPair) == 10 * 16, "CamPair is ten float4");
+
+__device__ __forceinline__ CamPair load_pair(const CamPair &src) {
+    CamPair c;
+    const float4 *s4 = reinterpret_cast<const float4 *>(&src);
+    float4 *d4 = reinterpret_cast<float4 *>(&c);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) d4[k] = s4[k];
+    return c;
+}
+
+__device__ __forceinline__ void make_pair(CamPair &d, const CamProj &a, const CamProj &b) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d.R[k] = make_float2(a.R[k], b.R[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d.t[k] = make_float2(a.t[k], b.t[k]);
+    d.fx = make_float2(a.fx, b.fx);
+    d.fy = make_float2(a.fy, b.fy);
+    d.cx = make_float2(a.cx, b.cx);
+    d.cy = make_float2(a.cy, b.cy);
+    d.kk = make_float2(a.kk, b.kk);
+    d.W = make_float2(a.W, b.W);
+    d.H = make_float2(a.H, b.H);
+    d.pad = make_float2(0.0f, 0.0f);
+}
+
+// prefilter() for two cameras at once on packed FP32x2 arithmetic: every
+// operation is the scalar one's, with the same operands in the same order and
+// round-to-nearest in each lane, so in0 / in1 equal prefilter() for cameras
+// c / c + 1 bit for bit.
+__device__ __forceinline__ void prefilter2(const CamPair &c, const GaussGeo &G,
+                                           const ProjParams &P, bool &in0, bool &in1) {
+    const float2 mx = make_float2(G.mx, G.mx), my = make_float2(G.my, G.my),
+                 mz = make_float2(G.mz, G.mz);
+    const float2 px = __ffma2_rn(c.R[0], mx, __ffma2_rn(c.R[1], my, __ffma2_rn(c.R[2], mz, c.t[0])));
+    const float2 py = __ffma2_rn(c.R[3], mx, __ffma2_rn(c.R[4], my, __ffma2_rn(c.R[5], mz, c.t[1])));
+    const float2 z = __ffma2_rn(c.R[6], mx, __ffma2_rn(c.R[7], my, __ffma2_rn(c.R[8], mz, c.t[2])));
+    const float2 iz = make_float2(rcp_a(z.x), rcp_a(z.y));
+    const float2 xz = __fmul2_rn(px, iz), yz = __fmul2_rn(py, iz);
+    const float2 u = __ffma2_rn(c.fx, xz, c.cx), v = __ffma2_rn(c.fy, yz, c.cy);
+    const float2 k2 = __fmul2_rn(__fmul2_rn(c.kk, iz), iz);
+    const float2 e = __ffma2_rn(k2, make_float2(G.smax2, G.smax2),
+                                make_float2(P.dilation, P.dilation));
+    const float sg = 1.002f * P.sigma;
+    const float2 rb = __ffma2_rn(make_float2(sg, sg), make_float2(sqrt_a(e.x), sqrt_a(e.y)),
+                                 make_float2(0.02f, 0.02f));
+    const float2 M1 = make_float2(-1.0f, -1.0f);
+    const float2 ua = __fadd2_rn(u, rb), us = __ffma2_rn(rb, M1, u);  // u + rb, u - rb
+    const float2 va = __fadd2_rn(v, rb), vs = __ffma2_rn(rb, M1, v);
+    in0 = z.x > P.near_plane && !(ua.x < 0.0f || us.x >= c.W.x || va.x < 0.0f || vs.x >= c.H.x);
+    in1 = z.y > P.near_plane && !(ua.y < 0.0f || us.y >= c.W.y || va.y < 0.0f || vs.y >= c.H.y);
+}
+
 // Real SH basis (Condon-Shortley phase), l-major with m = -l..l, constants
 // written as their closed forms sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the
 // factors of the Cartesian polynomials.
@@ -353,7 +414,8 @@ __device__ __forceinline__ float load_staged_geo(const float4 (*rows)[N], int i,
 }
 
 // Mask pass in two phases so that the long exact test runs on full warps:
-// per camera, every lane applies the cheap prefilter to its own Gaussian and
+// per camera (two at a time on packed arithmetic, prefilter2), every lane
+// applies the cheap prefilter to its own Gaussian and
 // the warp appends the passing (camera, Gaussian) pairs to a queue in shared
 // memory; whenever 32 pairs are queued, each lane takes one and runs the exact
 // test (project()); the results are OR-ed into the warp's mask word of that
@@ -374,6 +436,7 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     if (g0 >= gr.n) return;
     constexpr int NW = PROJ_THREADS / 32;
     __shared__ CamProj cp[MAX_GROUP];
+    __shared__ CamPair cpair[MAX_GROUP / 2];  // cameras (2i, 2i + 1) for prefilter2
     __shared__ long long moff[MAX_GROUP];
     __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane (camera < 64)
     __shared__ uint32_t smask[NW][MAX_GROUP];
@@ -381,6 +444,10 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     if (tid < gr.ncam) {
         cp[tid] = load_cam(camtab[gr.slot0 + tid]);
         moff[tid] = cams[gr.slot0 + tid].mask_off;
+    }
+    if (2 * tid < gr.ncam) {  // an odd last camera is paired with itself
+        const int c1 = 2 * tid + 1 < gr.ncam ? 2 * tid + 1 : 2 * tid;
+        make_pair(cpair[tid], load_cam(camtab[gr.slot0 + 2 * tid]), load_cam(camtab[gr.slot0 + c1]));
     }
     smask[warp][lane] = 0u;
     smask[warp][lane + 32] = 0u;
@@ -422,15 +489,19 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         __syncwarp();
         nq = rest;
     };
-    for (int c = 0; c < gr.ncam; ++c) {
-        const CamProj cam = load_cam(cp[c]);
-        float z, iz, xz, yz, u, v;
-        const bool cand = valid && prefilter(cam, G, P, z, iz, xz, yz, u, v);
+    // append this lane's pair with camera c when it passed the prefilter
+    auto append = [&](int c, bool cand) {
         const uint32_t b = __ballot_sync(0xffffffffu, cand);
         if (cand) queue[warp][nq + __popc(b & lt)] = (uint16_t)((c << 5) | lane);
         nq += __popc(b);
         __syncwarp();
         if (nq >= 32) drain(32);
+    };
+    for (int c = 0; c < gr.ncam; c += 2) {  // two cameras per packed prefilter
+        bool in0 = false, in1 = false;
+        if (valid) prefilter2(load_pair(cpair[c >> 1]), G, P, in0, in1);
+        append(c, in0);
+        if (c + 1 < gr.ncam) append(c + 1, in1);
     }
     if (nq > 0) drain(nq);
     __syncwarp();
