@@ -47,8 +47,8 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read + write) of one compositing launch from the ncu capture summarised in
 # profiles/k_composite_single_1m_sh3_16cam_640x480.md (16 cameras, scaled per camera), valid
 # only for the kernel source it was taken on (sha256 prefix below).
-TRAFFIC_SRC_SHA = "0983848fbf2dd6bc"
-TRAFFIC_BYTES_PER_CAMERA = (3.831808e6 + 25.232384e6) / 16
+TRAFFIC_SRC_SHA = "01ffb989a795dfa5"
+TRAFFIC_BYTES_PER_CAMERA = (3.827456e6 + 24.632576e6) / 16
 
 
 def composite_traffic(cams_per_launch: float):

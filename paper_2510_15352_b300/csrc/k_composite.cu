@@ -96,12 +96,15 @@ __device__ __forceinline__ int block_camera(const int *__restrict__ prefix, int 
     return lo;
 }
 
-// With 8 pixels per thread (one-warp blocks) the register budget is set for 20
-// resident blocks per SM (96 registers, no spills). Per 1,024 cameras: 16 blocks
-// 29.0 ms, 18 blocks 28.2 ms, 20 blocks 27.2 ms, 22 blocks 28.6 ms, 24 blocks
-// 31.3 ms (the last two spill).
+// With 8 pixels per thread (one-warp blocks) 20 blocks are resident per SM (96
+// registers; shared memory allows 20). Asking for at least 18 makes ptxas fit the
+// kernel in those 96 registers without spills; asking for 20 gave the same count
+// with a few spilled bytes (21.33 vs 21.28 ms per 1,024 cameras), and 16 gives 116
+// registers and 17 blocks (21.74 ms). Earlier layouts, per 1,024 cameras: 16
+// blocks 29.0 ms, 18 blocks 28.2 ms, 20 blocks 27.2 ms, 22 blocks 28.6 ms, 24
+// blocks 31.3 ms (the last two spill).
 template <int PPT, bool STATS>
-__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 20 : 1)
+__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1)
     k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
                 int n_slots, int per_cam, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
                 const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
