@@ -46,15 +46,18 @@ F_CONTRIB_ONLY = 22
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read + write) of one compositing launch from the ncu capture summarised in
 # profiles/k_composite_single_1m_sh3_16cam_640x480.md (16 cameras, scaled per camera), valid
-# only for the kernel source it was taken on (sha256 prefix below).
-TRAFFIC_SRC_SHA = "01ffb989a795dfa5"
-TRAFFIC_BYTES_PER_CAMERA = (3.827456e6 + 24.632576e6) / 16
+# only for the kernel source it was taken on (sha256 prefix of k_composite.cu followed by
+# gs_internal.cuh, below).
+TRAFFIC_SRC_SHA = "d05b93cbed0c1692"
+TRAFFIC_BYTES_PER_CAMERA = (3.598848e6 + 24.52224e6) / 16
 
 
 def composite_traffic(cams_per_launch: float):
     import hashlib
-    src = os.path.join(ROOT, "paper_2510_15352_b300", "csrc", "k_composite.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("k_composite.cu", "gs_internal.cuh"):  # the kernel and its constants
+        h.update(open(os.path.join(ROOT, "paper_2510_15352_b300", "csrc", name), "rb").read())
+    sha = h.hexdigest()[:16]
     return TRAFFIC_BYTES_PER_CAMERA * cams_per_launch if sha == TRAFFIC_SRC_SHA else None
 
 

@@ -18,7 +18,7 @@ constexpr int BIN_RANKS_SMALL = 256;  // ... or 1 per thread when the bitmap wor
                                       // 1,024 ranks of every super-tile exceed
 constexpr int BIN_SMEM_MAX = 200 * 1024;  // this much shared memory
 constexpr int MAX_TILES = 65536;    // tiles per camera (binning smem: 2 B per tile)
-constexpr int COMP_BATCH = 128;     // Gaussian records staged per compositing sub-batch
+constexpr int COMP_BATCH = 64;      // Gaussian records staged per compositing sub-batch
 
 enum : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 

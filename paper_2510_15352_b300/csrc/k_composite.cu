@@ -10,8 +10,10 @@
 // bitmap row (bit r = the survivor of depth rank r meets the 4x4-tile
 // super-tile), turns the set bits into candidate ranks in shared memory
 // (block prefix of popcounts), keeps the candidates whose exact tile rect
-// holds this tile (order-preserving ballot compaction), then stages up to 128
-// of their records at a time in shared memory and composites them. Per pixel
+// holds this tile (order-preserving ballot compaction), then stages up to
+// COMP_BATCH (64) of their records at a time in shared memory and composites
+// them (64 rather than 128: the skip test's live-pixel rectangle is refreshed
+// twice as often, 21.31 -> 20.48 ms per 1,024 cameras). Per pixel
 // and Gaussian:
 //   p = a'dx^2 + b'dx dy + c'dy^2 + log2(o) = log2(o e^power)
 //   p < log2(alpha_min): skip;  alpha = min(alpha_max, 2^p)
