@@ -15,7 +15,10 @@ rasteriser with EWA projection, 0.3 px dilation, 3-sigma tile culling,
 
 Every function is pinned by ``tests/test_oracle_pins.py`` (closed forms,
 invariants, brute force, textbook SH) and ``tests/test_oracle_mutants.py``
-(planted mistakes must fail a pin).
+(planted mistakes must fail a pin); the motion-blur poses and blend by
+``tests/test_oracle_blur.py`` (camera centres recovered from the poses,
+closed-form sub-frame images of one Gaussian, blend weights; planted
+mistakes in copies of both functions must fail one of those pins).
 """
 from __future__ import annotations
 
