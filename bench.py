@@ -1,21 +1,33 @@
 """Benchmark: 640x480 camera frames/s of batched 3DGS rendering on B300.
 
-Workload (default): one scene of 1,000,000 Gaussians (SH degree 3) and a
-1,024-camera batch at 640x480 (f = 480, robot cameras 0.3-1.2 m high); one
+Headline workload: one scene of 1,000,000 Gaussians (SH degree 3) and a
+4,096-camera batch at 640x480 (f = 480, robot cameras 0.3-1.2 m high); one
 step = one gs_render_batch call over the whole batch (projection + SH + cull,
 depth sort, tile binning, compositing of RGB and depth). Synthetic seeded
-inputs shaped like the paper's workload (thousands of robots at 640x480);
-the scene (236 MB) and the outputs (5 GB per step) are larger than L2.
+inputs shaped like the paper's workload (4,096 robots at 640x480 on one GPU);
+the scene (236 MB) and the outputs (20 GB per step) are larger than L2.
+
+On one GPU the same line also carries the other batch configurations, each
+timed the same way (warm-up, then CUDA events over K steps):
+  batched   32 scenes of 200k-2M Gaussians, 4,096 cameras (Zipf 1.1),
+            alternating 320x240 and 640x480: eager calls and CUDA-graph replay
+  half      the same 32 scenes stored FP16 (geometry) / BF16 (opacity, SH),
+            4,096 cameras at 640x480, FP32 arithmetic
+  upsampled the same 32 scenes, 4,096 cameras at 640x480 rendered at 160x120
+            and upsampled 4x by the learned network (trained first, untimed, on
+            200k renderer pairs), against the plain 640x480 render of the same
+            cameras (time and PSNR)
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
 Prints one JSON line (rank 0). Under torchrun every rank renders its own
-1,024 cameras (weak scaling, no collective on the data path); value is the
+4,096 cameras (weak scaling, no collective on the data path); value is the
 frames of all ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -28,7 +40,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "640x480 camera frames/s, 4096-cam batch; upsampled vs plain at >=35 dB PSNR"
 UNIT = "frames/s"
-WORKLOAD = "single_1m_sh3_1024cam_640x480"
+WORKLOAD = "single_1m_sh3_4096cam_640x480"
+BATCHED = "batched_32scene_4096cam_mixed"
 # Algorithmic FP32 work of the compositing step, per (pixel, Gaussian) pair that the
 # per-pixel algorithm evaluates: every entry of the pixel's tile list up to and
 # including the one at which it stops (lanes of pixels that have stopped, and
@@ -42,26 +55,73 @@ F_PAIR = 20
 LAUNCHES_PER_CHUNK = 20
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
-# FP32 peak of one B300: 148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz max clock
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-# DRAM bytes (read + write) of one compositing launch from the ncu capture summarised in
-# profiles/k_composite_single_1m_sh3_16cam_640x480.md (16 cameras, scaled per camera), valid
-# only for the kernel source it was taken on (sha256 prefix of k_composite.cu followed by
-# gs_internal.cuh, below).
-TRAFFIC_SRC_SHA = "d05b93cbed0c1692"
-TRAFFIC_BYTES_PER_CAMERA = (3.598848e6 + 24.52224e6) / 16
+# FP32 rate derived from unit counts (148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz),
+# reported beside the measured rate for context only
+FP32_NOMINAL_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# DRAM bytes (read, write) of one compositing launch over CAPTURE_CAMERAS cameras of the
+# headline workload (outputs larger than L2), from one ncu capture of dram__bytes_read.sum
+# and dram__bytes_write.sum; valid only for the kernel source it was taken on (sha256
+# prefix of k_composite.cu followed by gs_internal.cuh). None until captured.
+TRAFFIC_CAPTURE = None  # e.g. {"cameras": 64, "read": ..., "write": ..., "src_sha": "..."}
 
 
-def composite_traffic(cams_per_launch: float):
+def _composite_sha() -> str:
     import hashlib
     h = hashlib.sha256()
     for name in ("k_composite.cu", "gs_internal.cuh"):  # the kernel and its constants
         h.update(open(os.path.join(ROOT, "paper_2510_15352_b300", "csrc", name), "rb").read())
-    sha = h.hexdigest()[:16]
-    return TRAFFIC_BYTES_PER_CAMERA * cams_per_launch if sha == TRAFFIC_SRC_SHA else None
+    return h.hexdigest()[:16]
 
 
-def step_roofline(scene, n_cams: int, W: int, H: int, cst: dict, ms_step: float) -> dict:
+def composite_traffic(cams_per_launch: float):
+    """DRAM bytes of one compositing launch of `cams_per_launch` cameras, scaled
+    from the capture by cameras (the kernel's traffic grows with them), or None
+    when no capture of the current kernel source is recorded."""
+    c = TRAFFIC_CAPTURE
+    if not c or c["src_sha"] != _composite_sha():
+        return None
+    return (c["read"] + c["write"]) / c["cameras"] * cams_per_launch
+
+
+def measure_alu_peaks(gs, torch, stream, device: int) -> dict:
+    """Measured arithmetic rates of this GPU (gs_microbench kernels, CUDA events
+    on the launching stream, after warm-up, default clocks): scalar FFMA, packed
+    FP32x2 FMA and the SFU ex2. The FP32 peak is the larger FMA rate."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks = sms * 8 * 4  # 8 resident 256-thread blocks per SM, 4 waves
+    sink = torch.empty(blocks, dtype=torch.float32, device="cuda")
+    out = {}
+    for kind, name, iters in ((0, "ffma", 2048), (1, "ffma2", 2048), (2, "ex2", 512)):
+        ops = ctypes.c_int64(0)
+
+        def launch():
+            rc = gs.gs_microbench(kind, blocks, iters, sink.data_ptr(), ctypes.byref(ops),
+                                  stream.cuda_stream)
+            if rc != 0:
+                raise RuntimeError(f"gs_microbench({kind}) failed: {rc}")
+        for _ in range(3):
+            launch()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = reps * ops.value / (e0.elapsed_time(e1) / 1e3)
+    return {"fp32_tflops": max(out["ffma"], out["ffma2"]) / 1e12,
+            "fp32_ffma_tflops": out["ffma"] / 1e12, "fp32_ffma2_tflops": out["ffma2"] / 1e12,
+            "ex2_per_s": out["ex2"],
+            "fp32_nominal_tflops": FP32_NOMINAL_TFLOPS,
+            "how": f"gs_microbench: {blocks} blocks x 256 threads, 16 independent chains per "
+                   "thread; best of scalar FFMA and packed FFMA2 (2 flops per FMA); "
+                   "ex2.approx.ftz.f32 chains; 5 launches timed with CUDA events"}
+
+
+def step_roofline(scene, n_cams: int, W: int, H: int, cst: dict, ms_step: float,
+                  fp32_tflops: float) -> dict:
     """The whole step against the roofline of the method as the survey states it:
     max(algorithmic bytes / HBM peak, FP32 flops / FP32 peak). Bytes: the scene
     once, a 48-byte record written and read per survivor, a 12-byte
@@ -83,10 +143,10 @@ def step_roofline(scene, n_cams: int, W: int, H: int, cst: dict, ms_step: float)
     nbytes = scene_bytes + 2 * 48 * S + 2 * 12 * I + 16 * px
     flops = 20 * N * n_cams + (150 + 6 * K) * S + F_PAIR * E
     t_b = nbytes / hbm * 1e3
-    t_f = flops / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    t_f = flops / (fp32_tflops * 1e12) * 1e3
     return {"bytes": nbytes, "flops": flops, "ms_bytes": t_b, "ms_flops": t_f,
             "ms_roofline": max(t_b, t_f), "ms_measured": ms_step,
-            "frac": max(t_b, t_f) / ms_step}
+            "frac": max(t_b, t_f) / ms_step, "fp32_peak_tflops": fp32_tflops}
 
 
 def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
@@ -156,11 +216,8 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=64):
-    """The FP64 oracle as it stands on this host's cores, on a bounded sample
-    of the same workload (the first cameras of the batch)."""
-    cores = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+def _oracle_frames(scene, vm, it, W, H, budget_s: float, max_cams: int):
+    """Render cameras 0, 1, ... with the oracle until the budget is spent."""
     import oracle
     orc = oracle.get()
     t0 = time.perf_counter()
@@ -168,11 +225,41 @@ def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=64):
     while done < max_cams and (time.perf_counter() - t0) < budget_s:
         orc.render(scene, vm[done], it[done], W, H)
         done += 1
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
-            "kind": "oracle",
-            "sample": f"{done} of {len(vm)} cameras (cameras 0..{done - 1}), full 640x480 "
-                      f"frames, {dt:.1f} s of CPU work"}
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline(scene, vm, it, W, H, budget_s=15.0, max_cams=64):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample
+    of the same workload (the first cameras of the batch); then the same on
+    one core, in a child process started with OMP_NUM_THREADS=1."""
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    done, dt = _oracle_frames(scene, vm, it, W, H, budget_s, max_cams)
+    out = {"value": done / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+           "kind": "oracle",
+           "sample": f"{done} of {len(vm)} cameras (cameras 0..{done - 1}), full {W}x{H} "
+                     f"frames, {dt:.1f} s of CPU work"}
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-time",
+                            "--workload", WORKLOAD], env=env, capture_output=True, text=True,
+                           timeout=120)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        out["single_core"] = {"value": one["value"], "unit": UNIT, "cores": 1,
+                              "sample": one["sample"]}
+    except Exception as e:  # reported, not fatal: the multi-core figure stands
+        out["single_core"] = {"value": None, "error": str(e)[:200]}
+    return out
+
+
+def oracle_time_main(args):
+    """Child process of cpu_baseline: the oracle on the cores OMP_NUM_THREADS
+    allows, on the first camera(s) of the workload, about 10 s of CPU work."""
+    from paper_2510_15352_b300 import synth
+    scene, vm, it, W, H = synth.workload(WORKLOAD, seed=0, n_cams=4)
+    done, dt = _oracle_frames(scene, vm, it, W, H, 10.0, 4)
+    print(json.dumps({"value": done / dt, "sample": f"{done} camera(s) (cameras 0..{done - 1}), "
+                      f"full {W}x{H} frames, {dt:.1f} s on one core"}))
 
 
 # Algorithmic work of the upsampler per LR pixel: 2 flops per MAC of the six
@@ -194,102 +281,6 @@ def upsampled_launches(n_cams, chunk, w, h):
         group = max(1, min(m, (1 << 30) // per_frame))
         total += LAUNCHES_PER_CHUNK + 7 * -(-m // group)
     return total
-
-
-def upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb_plain, stream, local):
-    """The learned-upsampler path on the same cameras: render at W/4 x H/4
-    (intrinsics / 4), then the CNN to W x H (RGB; depth bilinear). The network
-    is trained first on renderer pairs of held-out poses (untimed), validated
-    on 64 other poses; below 35 dB the scene falls back to the plain render.
-    PSNR is measured against the plain render of the metric cameras."""
-    import numpy as np
-    import torch
-    from paper_2510_15352_b300 import upsampler
-    n = vm_d.shape[0]
-    h, w = H // 4, W // 4
-    up = gs.Upsampler(device=local)
-    bil = gs.Upsampler(device=local)
-    try:
-        up.set_params(upsampler.init_params(0))
-        bil.set_params(np.zeros(gs.Upsampler.n_params, np.float32))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        losses = upsampler.train(up, R, [sid], W, H, n_pairs=args.up_pairs, frames_per_step=4,
-                                 lr_max=1e-3, lr_min=3e-5, seed=100)
-        torch.cuda.synchronize()
-        t_train = time.perf_counter() - t0
-        vmv, itv = synth.make_cameras(64, W, H, 0.75 * W, (0.3, 1.2), seed=7)
-        val = upsampler.evaluate(up, R, sid, vmv, itv, W, H)
-        fallback = val["psnr_mean"] < 35.0
-        it_q = it_d / 4.0
-        lr = torch.empty((n, h, w, 3), dtype=torch.float32, device="cuda")
-        ld = torch.empty((n, h, w), dtype=torch.float32, device="cuda")
-        out = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
-        od = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
-
-        def render_lr():
-            R.render(sid, vm_d, it_q, w, h, lr, ld, stream=stream)
-
-        def cnn():
-            up.forward(lr, ld, out, od, stream=stream)
-
-        def step():
-            if fallback:
-                R.render(sid, vm_d, it_d, W, H, out, od, stream=stream)
-            else:  # one call: quarter-resolution parts and the upsampler overlapped
-                R.render_upsampled(up, sid, vm_d, it_d, W, H, out, od, stream=stream)
-
-        def timed(fn):
-            for _ in range(args.warmup):
-                fn()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            return e0.elapsed_time(e1) / args.steps
-
-        ms_step = timed(step)
-        up.check(stream)
-        # quality of exactly these frames against the plain render
-        p_net = upsampler.psnr(out, rgb_plain)
-        render_lr()
-        ob, _ = bil.forward(lr)
-        p_bil = upsampler.psnr(ob, rgb_plain)
-        torch.cuda.synchronize()
-        p_net, p_bil = p_net.cpu().numpy(), p_bil.cpu().numpy()
-        ms_lr = timed(render_lr) if not fallback else None
-        ms_cnn = timed(cnn) if not fallback else None
-        up.check(stream)
-    finally:
-        up.close()
-        bil.close()
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    bf16_peak = peaks.get("bf16_tflops", 1800.0)
-    cnn_tflops = (CNN_FLOPS_PER_LR_PIXEL * h * w * n / (ms_cnn / 1e3) / 1e12) if ms_cnn else None
-    return {
-        "value": n / (ms_step / 1e3), "unit": UNIT, "ms_per_step": ms_step,
-        "fallback": bool(fallback),
-        "render": f"{w}x{h}, intrinsics / 4, then the learned 4x upsampler to {W}x{H} "
-                  "(gs_render_batch_upsampled: parts of one chunk, upsampler on its own stream)",
-        "psnr_db_mean": float(p_net.mean()), "psnr_db_p5": float(np.percentile(p_net, 5)),
-        "bilinear_psnr_db_mean": float(p_bil.mean()),
-        "bilinear_psnr_db_p5": float(np.percentile(p_bil, 5)),
-        "validation": val, "train_pairs": int(args.up_pairs), "train_s": t_train,
-        "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
-        "stages_ms_per_step": {"render_lr": ms_lr, "cnn": ms_cnn},
-        "cnn_roofline": {
-            "kernel": "k_conv_ws (6 layers, TMA + tcgen05, warp-specialised) + k_prep_input_plane",
-            "bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-            "frac": cnn_tflops / bf16_peak if cnn_tflops else None,
-            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the CNN is timed alone)",
-            "flops_per_lr_pixel": CNN_FLOPS_PER_LR_PIXEL},
-        "gpu_launches_per_step": None if fallback else None,
-    }
 
 
 def run_reference(args):
@@ -324,11 +315,153 @@ def run_reference(args):
     }), flush=True)
 
 
-def run_b300_batched(args):
-    """The batched uneven workload: 32 scenes of 200k-2M Gaussians (SH 3),
-    4,096 cameras over them (Zipf 1.1), alternating 320x240 and 640x480; value
-    in 640x480-equivalent frames/s (pixels / 307,200)."""
+def _timed_steps(torch, stream, step, steps: int, warmup: int, per_step=None):
+    """W warm-up steps, then K steps between CUDA events on `stream`, with a
+    synchronize on both sides. Returns total ms."""
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+        if per_step:
+            per_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, graph: bool,
+                fp32_tflops: float, dist=None, clocks=None) -> dict:
+    """The batched uneven workload (32 scenes of 200k-2M Gaussians, SH 3; 4,096
+    cameras, Zipf 1.1; alternating 320x240 and 640x480) in one gs_render_batch_v
+    call per step, or one replay of a captured CUDA graph per step. Value in
+    640x480-equivalent frames/s (pixels / 307,200); camera frames/s beside it."""
     import numpy as np
+    n = len(vm)
+    vm_d = torch.from_numpy(vm).cuda()
+    it_d = torch.from_numpy(it).cuda()
+    P = int((Ws.astype(np.int64) * Hs).sum())
+    rgb = torch.empty((P, 3), dtype=torch.float32, device="cuda")
+    depth = torch.empty((P,), dtype=torch.float32, device="cuda")
+    kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
+              tiles_per_block=args.tpb, camera_group=args.group)
+    counter = gs.Renderer(device=local, count_pairs=1, **kw)
+    ids_c = np.array([counter.add_scene(sc) for sc in scenes], dtype=np.int32)[which]
+    counter.render_v(ids_c, vm_d, it_d, Ws, Hs, rgb, depth)
+    torch.cuda.synchronize()
+    cst = counter.stats()
+    counter.close()
+    R = gs.Renderer(device=local, time_stages=1, **kw)
+    G = None
+    try:
+        ids = np.array([R.add_scene(sc) for sc in scenes], dtype=np.int32)[which]
+        stage_ms = {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
+        if graph:
+            G = R.graph(ids, vm_d, it_d, Ws, Hs, rgb, depth)
+
+            def step():
+                G.launch(stream)
+            per_step = None
+        else:
+            def step():
+                R.render_v(ids, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
+
+            def per_step():
+                st = R.stats()
+                for k in stage_ms:
+                    stage_ms[k] += st["ms_" + k]
+        if clocks:
+            clocks.start()
+        ms = _timed_steps(torch, stream, step, args.steps, args.warmup, per_step)
+        clk = clocks.stop() if clocks else None
+        ms = max_over_ranks(ms, dist)
+        if G is not None:
+            G.check(stream)
+            # stage times from eager renders of the same batch (events inside a
+            # graph replay are not read back)
+            for _ in range(2):
+                R.render_v(ids, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
+            st = R.stats()
+            stage_ms = {k: st["ms_" + k] * args.steps for k in stage_ms}
+        n_chunks = R.stats()["n_chunks"]
+    finally:
+        if G is not None:
+            G.close()
+        R.close()
+    world = 1 if dist is None else dist.get_world_size()
+    eq_frames = P / (640 * 480)
+    comp_s = stage_ms["composite"] / args.steps / 1e3
+    achieved = F_PAIR * cst["pairs_evaluated"] / comp_s / 1e12 if comp_s else None
+    return {
+        "value": whole_job_rate(eq_frames * args.steps, world, ms / 1e3),
+        "unit": "640x480-equivalent frames/s", "ms_per_step": ms / args.steps,
+        "camera_frames_per_s": whole_job_rate(n * args.steps, world, ms / 1e3),
+        "config": {"workload": BATCHED, "cameras": n, "scenes": len(scenes),
+                   "gaussians": int(sum(sc["mean"].shape[1] for sc in scenes)),
+                   "cameras_640x480": int((Ws == 640).sum()),
+                   "cameras_320x240": int((Ws == 320).sum()),
+                   "frames_640x480_equivalent": eq_frames, "chunk_cameras": args.chunk,
+                   "cuda_graph": bool(graph),
+                   "storage": "f32" if "dequantised" not in scenes[0] else "f16/bf16"},
+        "roofline": {"kernel": "k_composite", "bound": "alu", "achieved": achieved,
+                     "peak": fp32_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_tflops if achieved else None,
+                     "peak_source": "measured (gs_microbench)"},
+        "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+        "gpu_launches": LAUNCHES_PER_CHUNK * n_chunks * args.steps,
+        "clocks": clk,
+    }
+
+
+def half_leg(args, gs, torch, synth, scenes, which, vm, local, stream, fp32_tflops) -> dict:
+    """Reduced-precision storage: the 32 scenes stored as FP16 geometry (mean,
+    log-scale, quaternion) and BF16 appearance (opacity logit, SH), all 4,096
+    cameras at 640x480 (f = 480), FP32 arithmetic; one gs_render_batch per step."""
+    import numpy as np
+    n, W, H = len(vm), 640, 480
+    it = np.tile(np.array([480.0, 480.0, W / 2, H / 2], np.float32), (n, 1))
+    vm_d = torch.from_numpy(vm).cuda()
+    it_d = torch.from_numpy(it).cuda()
+    rgb = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
+    depth = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+    R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
+                    pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
+                    camera_group=args.group)
+    try:
+        nbytes = 0
+        sids = []
+        for sc in scenes:
+            h = synth.to_half(sc)
+            h.pop("dequantised")
+            nbytes += sum(int(h[k].nbytes) for k in ("mean", "log_scale", "quat",
+                                                      "logit_opacity", "sh"))
+            sids.append(R.add_scene(h))
+        ids = np.array(sids, dtype=np.int32)[which]
+        stage_ms = {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
+
+        def step():
+            R.render(ids, vm_d, it_d, W, H, rgb, depth, stream=stream)
+
+        def per_step():
+            st = R.stats()
+            for k in stage_ms:
+                stage_ms[k] += st["ms_" + k]
+        ms = _timed_steps(torch, stream, step, args.steps, args.warmup, per_step)
+    finally:
+        R.close()
+    return {"value": n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "config": {"workload": "batched_32scene_4096cam_640x480_half", "cameras": n,
+                       "width": W, "height": H, "scenes": len(scenes),
+                       "storage": "mean, log_scale, quat FP16; logit_opacity, sh BF16",
+                       "scene_bytes": nbytes},
+            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()}}
+
+
+def run_b300_batched(args):
+    """--workload batched_32scene_4096cam_mixed as the headline line."""
     import torch
     rank, local, world = env_rank()
     torch.cuda.set_device(local)
@@ -338,131 +471,37 @@ def run_b300_batched(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2510_15352_b300 import gs, synth
     scenes, which, vm, it, Ws, Hs = synth.make_batched(seed=rank, n_cams=args.cams or 4096)
-    if args.precision == "half":
-        scenes = [synth.to_half(s) for s in scenes]
-    n = len(vm)
-    vm_d = torch.from_numpy(vm).cuda()
-    it_d = torch.from_numpy(it).cuda()
-    P = int((Ws.astype(np.int64) * Hs).sum())
-    tuned = None
-    if args.autotune:
-        # the autotuner's timed search over layouts, camera groups and chunk
-        # sizes for this batch (untimed here); its choice is used below
-        from paper_2510_15352_b300 import autotune
-        tuned = autotune.tune(scenes, which, vm, it, Ws, Hs, device=local, cache_path=None)
-        cfg = autotune.config_of(tuned)
-        args.ppt = cfg["pixels_per_thread"]
-        args.tpb = cfg.get("tiles_per_block", 1)
-        args.group = cfg["camera_group"]
-        args.chunk = cfg["max_chunk_cameras"]
-    rgb = torch.empty((P, 3), dtype=torch.float32, device="cuda")
-    depth = torch.empty((P,), dtype=torch.float32, device="cuda")
-    counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk,
-                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
-                          camera_group=args.group)
-    ids_c = np.array([counter.add_scene(s) for s in scenes], dtype=np.int32)[which]
-    counter.render_v(ids_c, vm_d, it_d, Ws, Hs, rgb, depth)
-    torch.cuda.synchronize()
-    cst = counter.stats()
-    counter.close()
-    R = gs.Renderer(device=local, time_stages=0 if args.graph else 1,
-                    max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
-                          camera_group=args.group)
-    ids = np.array([R.add_scene(s) for s in scenes], dtype=np.int32)[which]
     stream = torch.cuda.current_stream()
-    graph = R.graph(ids, vm_d, it_d, Ws, Hs, rgb, depth) if args.graph else None
-
-    def step():
-        if graph is not None:
-            graph.launch(stream)
-        else:
-            R.render_v(ids, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    peaks = measure_alu_peaks(gs, torch, stream, local)
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ms_comp, stage_ms = 0.0, {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-        if graph is None:
-            st = R.stats()
-            for k in stage_ms:
-                stage_ms[k] += st["ms_" + k]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
-    clk = clocks.stop()
-    if graph is not None:
-        graph.check(stream)
-        # stage times from one eager render of the same batch (events inside a
-        # graph replay are not read back)
-        R2 = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
-                         pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
-                          camera_group=args.group)
-        ids2 = np.array([R2.add_scene(s) for s in scenes], dtype=np.int32)[which]
-        for _ in range(2):
-            R2.render_v(ids2, vm_d, it_d, Ws, Hs, rgb, depth, stream=stream)
-        st = R2.stats()
-        stage_ms = {k: st["ms_" + k] * args.steps for k in stage_ms}
-        R2.close()
-        graph.close()
-    eq_frames = P / (640 * 480)
-    achieved = F_PAIR * cst["pairs_evaluated"] / (stage_ms["composite"] / args.steps / 1e3) / 1e12
-    out = {
-        "metric": METRIC, "value": whole_job_rate(eq_frames * args.steps, world, ms / 1e3),
-        "unit": UNIT,
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batched_32scene_4096cam_mixed", "cameras": n,
-                   "scenes": len(scenes), "gaussians": int(sum(s["mean"].shape[1] for s in scenes)),
-                   "cameras_640x480": int((Ws == 640).sum()), "cameras_320x240": int((Ws == 320).sum()),
-                   "frames_640x480_equivalent": eq_frames, "chunk_cameras": args.chunk,
-                   "pixels_per_thread": args.ppt, "tiles_per_block": args.tpb,
-                       "storage": args.precision,
-                   "cuda_graph": bool(args.graph), "camera_group": args.group,
-                   "autotuned": None if tuned is None else {
-                       "candidates": len(tuned["timings"]), "best_ms": tuned["ms"],
-                       "worst_ms": max(t[0] for t in tuned["timings"])}},
-        "roofline": {"kernel": "k_composite", "bound": "alu", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None},
-        "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
-        "camera_frames_per_s": whole_job_rate(n * args.steps, world, ms / 1e3),
-        "clocks": clk, "gpu_launches": None,
-    }
-    R.close()
-    if args.up_pairs > 0:
-        ups = upsampled_batched_leg(args, gs, synth, scenes, which, vm, local, stream)
-        if rank == 0:
-            out["upsampled"] = ups
+    leg = batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, args.graph,
+                      peaks["fp32_tflops"], dist, ClockSampler(local))
     if rank == 0:
+        out = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": leg["ms_per_step"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": leg["config"], "roofline": leg["roofline"],
+               "stages_ms_per_step": leg["stages_ms_per_step"],
+               "camera_frames_per_s": leg["camera_frames_per_s"], "alu_peaks": peaks,
+               "clocks": leg["clocks"], "gpu_launches": leg["gpu_launches"]}
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def upsampled_batched_leg(args, gs, synth, scenes, which, vm, local, stream):
+def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stream) -> dict:
     """The upsampled path on the batched scenes: every one of the batch's
     cameras at 640x480 (f = 480), rendered at 160x120 (intrinsics / 4) and
     upsampled by the learned network, against the plain 640x480 render of the
     same cameras (time and PSNR). The network is trained first (untimed) on
     renderer pairs of held-out poses cycling through the scenes; each scene is
-    validated on 8 other poses, and the cameras of a scene below 35 dB would be
-    rendered at full resolution instead."""
+    validated on 8 other poses, and the cameras of a scene below 35 dB are
+    rendered at full resolution instead (the fallback)."""
     import numpy as np
-    import torch
     from paper_2510_15352_b300 import upsampler
     W, H = 640, 480
+    h, w = H // 4, W // 4
     n = len(vm)
     vm_d = torch.from_numpy(vm).cuda()
     it_d = torch.tensor([[480.0, 480.0, W / 2.0, H / 2.0]], dtype=torch.float32,
@@ -491,14 +530,15 @@ def upsampled_batched_leg(args, gs, synth, scenes, which, vm, local, stream):
         slow_idx = torch.from_numpy(np.nonzero(slow)[0]).cuda()
         plain = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
         plain_d = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
-        out = torch.empty_like(plain)
-        out_d = torch.empty_like(plain_d)
         vm_f, it_f, ids_f = vm_d[fast_idx].contiguous(), it_d[fast_idx].contiguous(), ids[~slow]
         vm_s, it_s, ids_s = vm_d[slow_idx].contiguous(), it_d[slow_idx].contiguous(), ids[slow]
         out_f = torch.empty((len(ids_f), H, W, 3), dtype=torch.float32, device="cuda")
         out_fd = torch.empty((len(ids_f), H, W), dtype=torch.float32, device="cuda")
         out_s = torch.empty((len(ids_s), H, W, 3), dtype=torch.float32, device="cuda")
         out_sd = torch.empty((len(ids_s), H, W), dtype=torch.float32, device="cuda")
+        lr = torch.empty((n, h, w, 3), dtype=torch.float32, device="cuda")
+        ld = torch.empty((n, h, w), dtype=torch.float32, device="cuda")
+        it_q = it_d / 4.0
 
         def plain_step():
             R.render(ids, vm_d, it_d, W, H, plain, plain_d, stream=stream)
@@ -509,43 +549,45 @@ def upsampled_batched_leg(args, gs, synth, scenes, which, vm, local, stream):
             if len(ids_s):
                 R.render(ids_s, vm_s, it_s, W, H, out_s, out_sd, stream=stream)
 
-        def timed(fn):
-            for _ in range(args.warmup):
-                fn()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            return e0.elapsed_time(e1) / args.steps
+        def lr_step():
+            R.render(ids, vm_d, it_q, w, h, lr, ld, stream=stream)
 
-        ms_plain = timed(plain_step)
-        ms_up = timed(up_step)
+        def cnn_step():
+            up.forward(lr, ld, plain, plain_d, stream=stream)  # plain reused as scratch
+
+        ms_plain = _timed_steps(torch, stream, plain_step, args.steps, args.warmup) / args.steps
+        ms_up = _timed_steps(torch, stream, up_step, args.steps, args.warmup) / args.steps
         up.check(stream)
+        out = torch.empty_like(plain)
         out[fast_idx] = out_f
         if len(ids_s):
             out[slow_idx] = out_s
         p_net = upsampler.psnr(out, plain).cpu().numpy()
         # bilinear x4 of the quarter-resolution render, for reference
-        lr = torch.empty((n, H // 4, W // 4, 3), dtype=torch.float32, device="cuda")
-        R.render(ids, vm_d, it_d / 4.0, W // 4, H // 4, lr, stream=stream)
+        lr_step()
         ob = torch.empty_like(plain)
         for c0 in range(0, n, 512):
             o, _ = bil.forward(lr[c0:c0 + 512])
             ob[c0:c0 + 512] = o
         p_bil = upsampler.psnr(ob, plain).cpu().numpy()
+        del out, ob
+        ms_lr = _timed_steps(torch, stream, lr_step, args.steps, args.warmup) / args.steps
+        ms_cnn = _timed_steps(torch, stream, cnn_step, args.steps, args.warmup) / args.steps
+        up.check(stream)
     finally:
         up.close()
         bil.close()
         R.close()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = peaks.get("bf16_tflops", 1800.0)
+    cnn_tflops = CNN_FLOPS_PER_LR_PIXEL * h * w * n / (ms_cnn / 1e3) / 1e12
     return {
         "value": n / (ms_up / 1e3), "unit": UNIT, "ms_per_step": ms_up,
         "cameras": n, "render": "all cameras at 640x480 (f = 480): 160x120 render (intrinsics / 4) "
         "then the learned 4x upsampler (gs_render_batch_upsampled)",
-        "plain_same_cameras": {"value": n / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain},
+        "plain_same_cameras": {"value": n / (ms_plain / 1e3), "unit": UNIT,
+                               "ms_per_step": ms_plain},
         "speedup_vs_plain": ms_plain / ms_up,
         "fallback_cameras": int(slow.sum()),
         "psnr_db_mean": float(p_net.mean()), "psnr_db_p5": float(np.percentile(p_net, 5)),
@@ -554,6 +596,15 @@ def upsampled_batched_leg(args, gs, synth, scenes, which, vm, local, stream):
         "validation_psnr_db_min_over_scenes": float(min(val.values())),
         "train_pairs": int(args.up_pairs), "train_s": t_train,
         "train_loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-20:]))],
+        "stages_ms_per_step": {"render_160x120": ms_lr, "cnn": ms_cnn},
+        "cnn_roofline": {
+            "kernel": "k_conv_ws (6 layers, TMA + tcgen05, warp-specialised) + k_prep_input_plane",
+            "bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": cnn_tflops / bf16_peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the CNN is timed alone)",
+            "flops_per_lr_pixel": CNN_FLOPS_PER_LR_PIXEL},
+        "gpu_launches_per_step": upsampled_launches(len(ids_f), args.chunk, w, h)
+        + (LAUNCHES_PER_CHUNK * -(-len(ids_s) // args.chunk) if len(ids_s) else 0),
     }
 
 
@@ -575,11 +626,14 @@ def run_b300(args):
     it_d = torch.from_numpy(it).cuda()
     rgb = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
     depth = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    peaks = measure_alu_peaks(gs, torch, stream, local)
+    fp32 = peaks["fp32_tflops"]
 
     # algorithmic work of the compositing kernel on these inputs (counting run)
-    counter = gs.Renderer(device=local, count_pairs=1, max_chunk_cameras=args.chunk,
-                          pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
-                          camera_group=args.group)
+    kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
+              tiles_per_block=args.tpb, camera_group=args.group)
+    counter = gs.Renderer(device=local, count_pairs=1, **kw)
     sid_c = counter.add_scene(scene)
     counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
     torch.cuda.synchronize()
@@ -589,14 +643,22 @@ def run_b300(args):
     flops_itemised = F_EVAL_ITEMISED * cst["pairs_evaluated"] + F_CONTRIB_ITEMISED * cst["pairs_alpha"]
     flops_contrib = F_CONTRIB_ONLY * cst["pairs_alpha"]
 
-    R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
-                    pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
-                          camera_group=args.group)
+    R = gs.Renderer(device=local, time_stages=1, **kw)
     sid = R.add_scene(scene)
-    stream = torch.cuda.current_stream()
 
     def step():
         R.render(sid, vm_d, it_d, W, H, rgb, depth, stream=stream)
+
+    ms_comp, n_chunks = 0.0, 0
+    stage_ms = {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
+
+    def per_step():
+        nonlocal ms_comp, n_chunks
+        st = R.stats()  # waits for this step's stage events
+        ms_comp += st["ms_composite"]
+        n_chunks += st["n_chunks"]
+        for k in stage_ms:
+            stage_ms[k] += st["ms_" + k]
 
     for _ in range(args.warmup):
         step()
@@ -605,24 +667,9 @@ def run_b300(args):
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ms_comp, n_chunks = 0.0, 0
-    stage_ms = {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-        st = R.stats()  # waits for this step's stage events
-        ms_comp += st["ms_composite"]
-        n_chunks += st["n_chunks"]
-        for k in stage_ms:
-            stage_ms[k] += st["ms_" + k]
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms = _timed_steps(torch, stream, step, args.steps, 0, per_step)
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     t_max = max_over_ranks(ms, dist)
     value = whole_job_rate(n * args.steps, world, t_max / 1e3)
@@ -647,40 +694,51 @@ def run_b300(args):
         te = max_over_ranks(time.perf_counter() - t0, dist)
         e2e = {"value": whole_job_rate(n * args.e2e_steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": int(hvm.numel() * 4 + hit.numel() * 4),
-               "d2h_bytes_per_step": int(hrgb.numel() * 4 + hdep.numel() * 4)}
-
+               "d2h_bytes_per_step": int(hrgb.numel() * 4 + hdep.numel() * 4),
+               "steps": args.e2e_steps}
+        del hrgb, hdep
+    R.close()
+    out = None
     if rank == 0:
-        comp_ms_per_launch = ms_comp / max(n_chunks, 1)
-        achieved = flops_per_step / (ms_comp / args.steps / 1e3) / 1e12 if ms_comp else None
+        comp_s = ms_comp / args.steps / 1e3
+        achieved = flops_per_step / comp_s / 1e12 if ms_comp else None
+        cams_per_launch = n / max(n_chunks / args.steps, 1)
+        traffic = composite_traffic(cams_per_launch)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cameras_per_gpu": n, "width": W, "height": H,
-                       "gaussians": 1_000_000, "sh_degree": 3, "chunk_cameras": args.chunk,
-                       "pixels_per_thread": args.ppt, "tiles_per_block": args.tpb,
-                       "storage": args.precision,
-                       "l2": "inputs larger than L2 (scene 236 MB; 5 GB of outputs per step)"},
+                       "gaussians": int(scene["mean"].shape[1]), "sh_degree": 3,
+                       "chunk_cameras": args.chunk, "pixels_per_thread": args.ppt,
+                       "tiles_per_block": args.tpb, "storage": args.precision,
+                       "l2": "inputs larger than L2 (scene 236 MB; 20 GB of outputs per step)"},
             "roofline": {
                 "kernel": "k_composite", "bound": "alu", "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS if achieved else None,
-                "traffic": composite_traffic(n / max(n_chunks / args.steps, 1)),
-                "traffic_unit": "bytes per launch (ncu capture scaled by cameras)",
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz",
-                "ms_per_launch": comp_ms_per_launch,
+                "peak": fp32, "unit": "TFLOP/s",
+                "frac": achieved / fp32 if achieved else None,
+                "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (ncu capture scaled by cameras)",
+                "algorithmic_output_bytes_per_launch": 16 * W * H * cams_per_launch,
+                "traffic_over_output_bytes": (traffic / (16 * W * H * cams_per_launch)
+                                              if traffic else None),
+                "peak_source": "measured (gs_microbench, best of FFMA and FFMA2)",
+                "ms_per_launch": ms_comp / max(n_chunks, 1),
                 "launches_per_step": n_chunks / args.steps,
                 "composite_share_of_step": ms_comp / t_max,
                 "pairs_evaluated_per_step": cst["pairs_evaluated"],
                 "pairs_alpha_per_step": cst["pairs_alpha"],
                 "flops_per_pair": F_PAIR,
-                "frac_itemised": (flops_itemised / (ms_comp / args.steps / 1e3) / 1e12
-                                  / FP32_PEAK_TFLOPS) if ms_comp else None,
-                "frac_contributing_only": (flops_contrib / (ms_comp / args.steps / 1e3) / 1e12
-                                           / FP32_PEAK_TFLOPS) if ms_comp else None,
+                "frac_itemised": flops_itemised / comp_s / 1e12 / fp32 if ms_comp else None,
+                "frac_contributing_only": flops_contrib / comp_s / 1e12 / fp32 if ms_comp else None,
+                "ex2_per_s_achieved": cst["pairs_evaluated"] / comp_s if ms_comp else None,
+                "ex2_peak_per_s": peaks["ex2_per_s"],
+                "ex2_frac": (cst["pairs_evaluated"] / comp_s / peaks["ex2_per_s"]
+                             if ms_comp else None),
             },
-            "step_roofline": step_roofline(scene, n, W, H, cst, t_max / args.steps),
+            "alu_peaks": peaks,
+            "step_roofline": step_roofline(scene, n, W, H, cst, t_max / args.steps, fp32),
             "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "stats": {"survivors_per_step": cst["survivors"],
                       "composite_warp_iters": cst["warp_iters"],
@@ -691,15 +749,24 @@ def run_b300(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(scene, vm, it, W, H)
-    if args.up_pairs > 0:
-        ups = upsampled_leg(args, gs, synth, R, sid, vm_d, it_d, W, H, rgb, stream, local)
-        ups["gpu_launches_per_step"] = upsampled_launches(n, args.chunk, W // 4, H // 4)
-        ups["speedup_vs_plain"] = ups["value"] / (n / (t_max / args.steps / 1e3))
-        if rank == 0:
-            out["upsampled"] = ups
+    del rgb, depth
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_extras:
+        # the other batch configurations, on the 32-scene set
+        scenes, which, bvm, bit, Ws, Hs = synth.make_batched(seed=0, n_cams=4096)
+        out["batched"] = {
+            "eager": batched_leg(args, gs, torch, scenes, which, bvm, bit, Ws, Hs, local,
+                                 stream, False, fp32, clocks=ClockSampler(local)),
+            "graph": batched_leg(args, gs, torch, scenes, which, bvm, bit, Ws, Hs, local,
+                                 stream, True, fp32, clocks=ClockSampler(local))}
+        torch.cuda.empty_cache()
+        out["half"] = half_leg(args, gs, torch, synth, scenes, which, bvm, local, stream, fp32)
+        torch.cuda.empty_cache()
+        if args.up_pairs > 0:
+            out["upsampled"] = upsampled_batched_leg(args, gs, torch, synth, scenes, which, bvm,
+                                                     local, stream)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    R.close()
     if dist:
         dist.destroy_process_group()
 
@@ -710,9 +777,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
-    ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 1024)")
-    ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batched_32scene_4096cam_mixed"])
+    ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 4096)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED])
     ap.add_argument("--chunk", type=int, default=512, help="cameras per internal chunk")
     ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
     ap.add_argument("--group", type=int, default=64,
@@ -720,19 +786,22 @@ def main():
     ap.add_argument("--tpb", type=int, default=1,
                     help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
     ap.add_argument("--precision", choices=["f32", "half"], default="f32",
-                    help="scene attribute storage (half: FP16 geometry, BF16 appearance)")
+                    help="headline scene storage (half: FP16 geometry, BF16 appearance)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--graph", action="store_true",
-                    help="time replays of one captured CUDA graph (batched workload)")
+                    help="--workload batched_...: time replays of one captured CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--autotune", action="store_true",
-                    help="batched workload: pick the launch configuration with the autotuner first")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only (no batched, half and upsampled legs)")
     ap.add_argument("--up-pairs", type=int, default=200_000,
-                    help="training pairs of the learned upsampler (0: skip the upsampled path)")
+                    help="training pairs of the learned upsampler (0: skip the upsampled leg)")
+    ap.add_argument("--oracle-time", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.oracle_time:
+        oracle_time_main(args)
+    elif args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batched_32scene_4096cam_mixed":
+    elif args.workload == BATCHED:
         run_b300_batched(args)
     else:
         run_b300(args)

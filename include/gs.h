@@ -300,6 +300,22 @@ gs_status gs_sort_segments_noalloc(uint32_t *keys, uint32_t *vals, int64_t n,
                                    const int64_t *seg_start, const int64_t *seg_count,
                                    int32_t n_seg, void *stream);
 
+/* ---- Measurement ----
+ * Arithmetic-rate microbenchmarks for the renderer's roofline (the paper has
+ * no counterpart: it reports whole-simulator throughput only). The compositing
+ * pass is bound by FP32 arithmetic and the SFU exponential, and the device's
+ * rates for these are measured rather than derived from unit counts.
+ *   kind    0 = scalar FP32 FMA, 1 = packed FP32x2 FMA, 2 = ex2.approx.ftz.f32
+ *   blocks  grid size (256 threads each; a multiple of the SM count fills the GPU)
+ *   iters   rounds per thread (each round: 8 x 16 operations per thread)
+ *   sink    DEVICE float32 [blocks], never written in practice (keeps the work)
+ *   ops     HOST, receives the work of the launch: flops (2 per FMA) for kinds
+ *           0 and 1, exponentials for kind 2
+ * Enqueues one kernel on `stream` and returns; time it with events on that
+ * stream. Errors: INVALID_ARG, CUDA (launch failure). */
+gs_status gs_microbench(int32_t kind, int32_t blocks, int32_t iters, float *sink, int64_t *ops,
+                        void *stream);
+
 /* ---- Learned 4x upsampler ----
  * The paper renders every robot camera at 640x480 (Sec. 3.2) and has no
  * upsampler; this is a service of this library: a small residual CNN that

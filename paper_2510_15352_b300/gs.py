@@ -101,6 +101,7 @@ SIGNATURES = {
     "gs_upsample_timeout_probe": (ctypes.c_int, [_vp, _vp]),
     "gs_render_batch_upsampled": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _i32, _i32, _vp,
                                                  _vp, _vp]),
+    "gs_microbench": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _vp]),
 }
 
 
@@ -157,6 +158,7 @@ gs_upsampler_set_backend = lib.gs_upsampler_set_backend
 gs_upsample_check = lib.gs_upsample_check
 gs_upsample_timeout_probe = lib.gs_upsample_timeout_probe
 gs_render_batch_upsampled = lib.gs_render_batch_upsampled
+gs_microbench = lib.gs_microbench
 GS_UPSAMPLE_TCGEN05, GS_UPSAMPLE_MMA_SYNC = 0, 1
 
 

@@ -92,12 +92,16 @@ def make_cameras(n: int, W: int, H: int, focal: float, height=(0.5, 0.5),
 # small: 1 scene of 20,000 Gaussians, SH degree 0, 8 cameras at 160x120,
 #        f = 120, camera height 0.5 m.
 # full:  1 scene of 1,000,000 Gaussians, SH degree 3, 1,024 cameras at
-#        640x480, f = 480, camera height uniform in [0.3, 1.2] m.
+#        640x480, f = 480, camera height uniform in [0.3, 1.2] m; with 4,096
+#        cameras (the benchmark's batch) or 1,024.
 
 WORKLOADS = {
     "small_20k_8cam_160x120": dict(n=20_000, deg=0, cams=8, W=160, H=120, f=120.0,
                                    height=(0.5, 0.5)),
     "single_1m_sh3_1024cam_640x480": dict(n=1_000_000, deg=3, cams=1024, W=640, H=480,
+                                          f=480.0, height=(0.3, 1.2)),
+    # the same scene and camera distribution with the paper's 4,096 robots
+    "single_1m_sh3_4096cam_640x480": dict(n=1_000_000, deg=3, cams=4096, W=640, H=480,
                                           f=480.0, height=(0.3, 1.2)),
 }
 

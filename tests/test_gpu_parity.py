@@ -433,16 +433,25 @@ def test_errors_are_reported(torch, gsmod, R):
 
 def test_full_size_workload_sampled_cameras(torch, R, orc):
     """1M Gaussians (SH degree 3), 1,024 cameras at 640x480 in one call with
-    the default chunking (the benchmark's launch configuration); three
-    cameras across the batch are checked against the oracle pixel by pixel."""
+    the default chunking (the benchmark's launch configuration); 16 cameras
+    drawn across the batch (seed 1) are checked against the oracle pixel by
+    pixel. Every pixel must match the oracle's primary result, or, where the
+    oracle met a near-threshold decision, one of its alternatives: no
+    unresolved pixel is allowed. The counts are printed."""
     scene, vm, it, W, H = synth.workload("single_1m_sh3_1024cam_640x480")
     sid = R.add_scene(scene)
     try:
         rgb, depth, T = R.render(sid, dev(torch, vm), dev(torch, it), W, H, want_T=True)
         torch.cuda.synchronize()
-        for c in (0, 517, 1023):
+        cams = np.sort(np.random.default_rng(1).choice(len(vm), size=16, replace=False))
+        tot = {"pixels": 0, "flagged": 0, "resolved_by_alternative": 0}
+        for c in cams:
             ref = orc.render(scene, vm[c], it[c], W, H, bands=BANDS)
-            r = compare_camera(rgb[c].cpu().numpy(), depth[c].cpu().numpy(), T[c].cpu().numpy(), ref)
-            assert len(r["unresolved"]) <= 1e-4 * r["pixels"], r
+            r = compare_camera(rgb[c].cpu().numpy(), depth[c].cpu().numpy(), T[c].cpu().numpy(),
+                               ref)
+            assert not r["unresolved"], (int(c), r)
+            for k in tot:
+                tot[k] += r[k]
+        print(f"\nfull size, cameras {cams.tolist()}: {tot}")
     finally:
         R.remove_scene(sid)

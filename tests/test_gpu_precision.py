@@ -62,7 +62,7 @@ def test_half_storage_full_size_sampled(torch, orc):
     for c in (0, 63):
         ref = orc.render(half["dequantised"], vm[c], it[c], W, H, bands=BANDS)
         r = compare_camera(rgb[c], depth[c], T[c], ref)
-        assert len(r["unresolved"]) <= 1e-4 * r["pixels"], r
+        assert not r["unresolved"], (c, r)
         full = orc.render(scene, vm[c], it[c], W, H)
         e = np.abs(rgb[c] - full["rgb"]).max(axis=-1)
         errs.append((float(e.mean()), float(np.percentile(e, 99)), float(e.max())))
