@@ -52,7 +52,7 @@ BATCHED = "batched_32scene_4096cam_mixed"
 # 11 per contributing pair (alpha >= alpha_min: 1 - alpha, T', alpha T, four FMAs),
 # and a lower bound, 22 flops per contributing pair only.
 F_PAIR = 20
-LAUNCHES_PER_CHUNK = 20
+LAUNCHES_PER_CHUNK = 22
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
 # FP32 rate derived from unit counts (148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz),

@@ -60,6 +60,8 @@ struct gs_context {
     DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist, sorttab, bintab,
         camtab;
     DevBuf wide;  // per chunk: some depth key needs the sort's fourth pass
+    DevBuf oidx;  // per survivor slot: the Gaussian's caller index (depth tie-break)
+    DevBuf ties, nruns;  // long runs of equal depth keys (list, per-chunk count)
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
     int workspace_gen = 0;        // bumped when a chunk-workspace buffer is reallocated
@@ -184,6 +186,7 @@ struct ChunkPlan {
     long long n_gauss;    // sum over cameras of their scene sizes
     int sort_grid, bin_grid;
     int bin_ranks;        // depth ranks per binning block (from max_sup)
+    int max_deg;          // largest SH degree of the chunk's scenes
 };
 
 struct Plan {
@@ -235,6 +238,7 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
             ch.per_cam = s == 0 ? blocks : (ch.per_cam == blocks ? blocks : 0);
             ch.max_sup = std::max(ch.max_sup,
                                   ((ci.TX + STILE - 1) / STILE) * ((ci.TY + STILE - 1) / STILE));
+            ch.max_deg = std::max(ch.max_deg, sd.deg);
             ci.mask_off = ch.mask_words;
             ch.mask_words += (sd.n + 31) / 32;
             ch.n_gauss += sd.n;
@@ -280,7 +284,8 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
                       &ctx->srect,    &ctx->rrect,    &ctx->keys,      &ctx->vals,   &ctx->tkeys,
                       &ctx->tvals,    &ctx->bitmap,   &ctx->sorthist,  &ctx->sorttab,
                       &ctx->bintab,   &ctx->wide,     &ctx->blkpre,    &ctx->sorttiles,
-                      &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status};
+                      &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status,
+                      &ctx->oidx,     &ctx->ties,     &ctx->nruns};
     void *before[sizeof(held) / sizeof(held[0])];
     for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->p;
     CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
@@ -294,6 +299,9 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->vals, Sx * 4));
     CKS(grow(ctx, ctx->tkeys, Sx * 4));
     CKS(grow(ctx, ctx->tvals, Sx * 4));
+    CKS(grow(ctx, ctx->oidx, Sx * 4));
+    CKS(grow(ctx, ctx->ties, (Sx / 33 + 2) * tie_run_bytes()));
+    CKS(grow(ctx, ctx->nruns, (P.chunks.size() + 1) * sizeof(int)));
     // bounds implied by S: bitmap words <= max_sup * (S/32 + m), sort tiles <= S/2048 + m
     CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
     CKS(grow(ctx, ctx->sorthist, (Sx / SORT_TILE_KEYS + m + 1) * 512 * 4));
@@ -363,8 +371,9 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
                                  cams, ctx->camtab.p, PP, (const uint32_t *)ctx->masks.p,
                                  (const uint32_t *)ctx->woff.p, recs, with_d,
-                                 (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p, wide,
-                                 std::log(cfg.alpha_min), status, st));
+                                 (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p,
+                                 (uint32_t *)ctx->oidx.p, wide, std::log(cfg.alpha_min), status,
+                                 ch.max_deg, st));
         if (E) CKC(cudaEventRecord(E[1], st));
         if (a.upto == UPTO_PROJECT) break;
         CKC(launch_sort_depth((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
@@ -375,6 +384,14 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                               (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
                               ch.m, ch.sort_grid, (uint32_t *)ctx->sorthist.p, wide, st,
                               (const int *)ctx->sorttiles.p + ch.m, (const SortTile *)ctx->sorttab.p));
+        // equal depths in the Gaussians' index order (the sort left them in storage order)
+        int *nruns = (int *)ctx->nruns.p + k;
+        CKC(cudaMemsetAsync(nruns, 0, sizeof(int), st));
+        CKC(launch_tie_order((uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
+                             (uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
+                             (const uint32_t *)ctx->oidx.p, (const SortTile *)ctx->sorttab.p,
+                             (const int *)ctx->sorttiles.p + ch.m, ch.sort_grid, ctx->ties.p,
+                             (long long)(ctx->ties.cap / tie_run_bytes()), nruns, st));
         if (E) CKC(cudaEventRecord(E[2], st));
         CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
                        ch.bin_grid, ch.max_sup,
@@ -556,7 +573,7 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->bitmap,   &ctx->tables, &ctx->status, &ctx->blkpre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
                       &ctx->sorttiles, &ctx->sorthist, &ctx->sorttab, &ctx->bintab, &ctx->camtab, &ctx->blur_vm,
-                      &ctx->wide,
+                      &ctx->wide,     &ctx->oidx,  &ctx->ties,    &ctx->nruns,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -592,28 +609,76 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
     const int K = (d->sh_degree + 1) * (d->sh_degree + 1);
     const size_t gs = dtype_size(d->geometry_dtype), as = dtype_size(d->appearance_dtype);
     const size_t sz[5] = {3 * n * gs, 3 * n * gs, 4 * n * gs, n * as, (size_t)K * 3 * n * as};
+    const size_t esz[5] = {gs, gs, gs, as, as};
+    const int rows[5] = {3, 3, 4, 1, 3 * K};
     const void *src[5] = {d->mean, d->log_scale, d->quat, d->logit_opacity, d->sh};
     size_t total = 0, offs[5];
     for (int i = 0; i < 5; ++i) {
         offs[i] = total;
         total += align_up(sz[i], 256);
     }
+    const long long nblk = scene_blocks(n);
+    const size_t off_orig = total;
+    total += align_up((size_t)n * 4, 256);
+    const size_t off_bounds = total;
+    total += align_up((size_t)nblk * 2 * sizeof(float4), 256);
     SceneSlot slot;
     slot.live = true;
-    if (total > 0) {
+    if (n > 0) {
         cudaError_t e = cudaMalloc(&slot.storage, total);
         if (e != cudaSuccess)
             return fail(ctx, GS_ERR_OOM, "scene storage (%zu bytes): %s", total, cudaGetErrorString(e));
-        for (int i = 0; i < 5; ++i)
-            if (sz[i]) {
-                e = cudaMemcpy((char *)slot.storage + offs[i], src[i], sz[i],
+        // The caller's arrays go to a temporary buffer first; the scene is stored
+        // in Morton order of the means (see k_scene.cu), orig[p] = caller index.
+        const long long nt = sort_tiles_for(n);
+        const size_t off_raw = 0, raw_bytes = offs[4] + align_up(sz[4], 256);
+        const size_t off_code = raw_bytes, u32n = align_up((size_t)n * 4, 256);
+        const size_t off_idx = off_code + u32n, off_tk = off_idx + u32n, off_tv = off_tk + u32n;
+        const size_t off_hist = off_tv + u32n, hist_bytes = align_up((size_t)nt * 256 * 4, 256);
+        const size_t off_meta = off_hist + hist_bytes, tmp_bytes = off_meta + 256;
+        void *tmp = nullptr;
+        e = cudaMalloc(&tmp, tmp_bytes);
+        if (e != cudaSuccess) {
+            cudaFree(slot.storage);
+            return fail(ctx, GS_ERR_OOM, "scene set-up (%zu bytes): %s", tmp_bytes,
+                        cudaGetErrorString(e));
+        }
+        char *t = (char *)tmp;
+        char *st = (char *)slot.storage;
+        long long *segs = (long long *)(t + off_meta);         // [0] start, [1] count
+        int *tstart = (int *)(t + off_meta + 16);              // [0] 0, [1] tiles
+        unsigned *box = (unsigned *)(t + off_meta + 32);       // 6 words
+        uint32_t *code = (uint32_t *)(t + off_code), *idx = (uint32_t *)(t + off_idx);
+        const long long meta_ll[2] = {0, n};
+        const int meta_i[2] = {0, (int)nt};
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+            if (sz[i])
+                e = cudaMemcpy(t + off_raw + offs[i], src[i], sz[i],
                                d->memory == GS_MEM_HOST ? cudaMemcpyHostToDevice
                                                         : cudaMemcpyDeviceToDevice);
-                if (e != cudaSuccess) {
-                    cudaFree(slot.storage);
-                    return fail(ctx, GS_ERR_CUDA, "scene copy: %s", cudaGetErrorString(e));
-                }
-            }
+        if (e == cudaSuccess) e = cudaMemcpy(segs, meta_ll, sizeof(meta_ll), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(tstart, meta_i, sizeof(meta_i), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_scene_morton(t + off_raw + offs[0], d->geometry_dtype, n, box, code, idx,
+                                    nullptr);
+        if (e == cudaSuccess)
+            e = launch_sort_segments(code, idx, (uint32_t *)(t + off_tk), (uint32_t *)(t + off_tv),
+                                     segs, segs + 1, tstart, 1, (int)nt,
+                                     (uint32_t *)(t + off_hist), nullptr);
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+            e = launch_gather_rows(t + off_raw + offs[i], st + offs[i], (int)esz[i], idx, n,
+                                   rows[i], nullptr);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(st + off_orig, idx, (size_t)n * 4, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = launch_block_bounds(st + offs[0], st + offs[1], d->geometry_dtype, n,
+                                    (float4 *)(st + off_bounds), nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(tmp);
+        if (e != cudaSuccess) {
+            cudaFree(slot.storage);
+            return fail(ctx, GS_ERR_CUDA, "scene set-up: %s", cudaGetErrorString(e));
+        }
     }
     char *b = (char *)slot.storage;
     slot.dev.mean = b + offs[0];
@@ -621,6 +686,8 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
     slot.dev.quat = b + offs[2];
     slot.dev.logit = b + offs[3];
     slot.dev.sh = b + offs[4];
+    slot.dev.orig = (const int *)(b + off_orig);
+    slot.dev.bounds = (const float4 *)(b + off_bounds);
     slot.dev.n = n;
     slot.dev.deg = d->sh_degree;
     slot.dev.geo_dtype = d->geometry_dtype;
@@ -1009,9 +1076,14 @@ gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewm
     if (S > cap) return fail(ctx, GS_ERR_CAPACITY, "%lld survivors > cap %lld", S, (long long)cap);
     std::vector<SlotRec> h((size_t)S);
     CKS(copy_records(ctx, S, h));
+    // slots follow the storage order; report in the caller's Gaussian-index order
+    std::vector<long long> order((size_t)S);
+    for (long long i = 0; i < S; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(),
+              [&](long long x, long long y) { return h[x].d.z < h[y].d.z; });
     const float L2E = 1.4426950408889634f;
     for (long long i = 0; i < S; ++i) {
-        const SlotRec &R = h[i];
+        const SlotRec &R = h[order[i]];
         // undo the folding of the compositing constants (see SlotRec)
         const float v[12] = {R.a.x,
                              R.a.y,

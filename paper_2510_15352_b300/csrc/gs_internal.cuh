@@ -37,8 +37,14 @@ struct CompParams {
 };
 
 // A scene resident in device memory (structure of arrays, see gs.h).
+// The Gaussians are stored in the library's spatial order (k_scene.cu): orig[p]
+// is the caller's index of the Gaussian at position p; bounds holds two float4
+// per block of PROJ_THREADS positions (min of the means and the largest
+// squared scale; max of the means and a finite flag).
 struct SceneDev {
     const void *mean, *log_scale, *quat, *logit, *sh;
+    const int *orig;
+    const float4 *bounds;
     long long n;
     int deg, geo_dtype, app_dtype, pad;
 };
@@ -117,8 +123,20 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams, const void *camtab,
                                  ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, float4 *rec, int rec_d,
-                                 uint2 *srect, uint32_t *keys, int *wide,
-                                 float ln_alpha_min, const int *status, cudaStream_t s);
+                                 uint2 *srect, uint32_t *keys, uint32_t *oidx, int *wide,
+                                 float ln_alpha_min, const int *status, int max_deg,
+                                 cudaStream_t s);
+
+// Scene set-up (k_scene.cu): Morton codes of the means (box: 6 words of
+// scratch) with idx = 0..n-1, to be sorted as (code, idx); a gather of `rows`
+// attribute rows of n elements by perm; the projection-block bounds.
+cudaError_t launch_scene_morton(const void *mean, int dtype, long long n, unsigned *box,
+                                uint32_t *code, uint32_t *idx, cudaStream_t s);
+cudaError_t launch_gather_rows(const void *src, void *dst, int elem_bytes, const uint32_t *perm,
+                               long long n, int rows, cudaStream_t s);
+long long scene_blocks(long long n);
+cudaError_t launch_block_bounds(const void *mean, const void *log_scale, int dtype, long long n,
+                                float4 *bounds, cudaStream_t s);
 
 // Segmented sort: tile_start[n_seg + 1] is the prefix of sort_tiles_for(count)
 // over the segments; hist needs 256 uint32 per tile. n_tiles blocks are
@@ -141,12 +159,26 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
 struct SortTile {
     long long seg_base;
     int t0, nk;
+    int seg_n;  // keys of the whole segment
+    int pad;
 };
 cudaError_t launch_sort_depth(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
                               uint32_t *tmp_vals, long long n_keys, const long long *seg_start,
                               const long long *seg_count, const int *tile_start, int n_seg,
                               int n_tiles, uint32_t *hist, const int *wide, cudaStream_t s,
                               const int *n_tiles_dev, const SortTile *tiles);
+
+// Equal depths after the depth sort (k_ties.cu): within every run of equal
+// keys of a segment, the values (slots) are put in the order of the Gaussians'
+// caller indices (oidx[seg_base + slot]); short runs in place, longer ones
+// listed (runs: capacity entries of tie_run_bytes(), *n_runs zeroed before) and sorted one block
+// per run. keys / vals are the sorted arrays; scratch_k / scratch_v the sort's
+// other buffers (free after it).
+size_t tie_run_bytes();  // bytes per listed long run
+cudaError_t launch_tie_order(uint32_t *keys, uint32_t *vals, uint32_t *scratch_k,
+                             uint32_t *scratch_v, const uint32_t *oidx, const SortTile *tiles,
+                             const int *n_tiles_dev, int grid, void *runs, long long capacity,
+                             int *n_runs, cudaStream_t s);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
 // Intrinsics scaled by 1/f (see k_blur.cu).

@@ -1,27 +1,31 @@
 // k_project.cu -- projection, SH colour and culling of Gaussians for a batch of
 // cameras (the EWA splatting step of the 3DGS renderer the paper uses, Sec. 3.2).
 //
-// Layout of the work: a block holds 256 consecutive Gaussians of one scene and
-// loops over a group of up to 64 cameras of that scene, so each Gaussian's
-// attributes are read from HBM once per camera group instead of once per
-// camera. Attribute loads are structure-of-arrays: consecutive threads read
-// consecutive addresses of each attribute row.
+// Layout of the work: a block holds 256 consecutive (stored) Gaussians of one
+// scene and loops over a group of up to 64 cameras of that scene, so each
+// Gaussian's attributes are read from HBM once per camera group instead of once
+// per camera. Attribute loads are structure-of-arrays: consecutive threads read
+// consecutive addresses of each attribute row. Scenes are stored in spatial
+// (Morton) order (k_scene.cu), so a block's Gaussians are close together and
+// most blocks are, for a given camera, entirely outside the view or entirely
+// inside it; the mask pass tests the block's box first and the Gaussians one
+// by one only when the box straddles the view's edges.
 //
-// Two passes keep the survivor order deterministic (Gaussian-index order)
-// without a global sort key that carries the index:
+// Two passes keep the survivor order deterministic (storage order within a
+// camera; the tie-break pass after the depth sort restores index order among
+// equal depths) without a global sort key that carries the index:
 //   k_cam_setup     -- once per chunk: each camera's projection constants, which
 //                      both passes copy into shared memory per block;
-//   k_project_mask  -- survival bit per (camera, Gaussian), one warp ballot per
-//                      32 Gaussians -> a 32-bit mask word;
+//   k_project_mask  -- survival bit per (camera, Gaussian), one 32-bit mask word
+//                      per warp and camera: zero or all ones from the block test,
+//                      else per Gaussian (prefilter, then the exact test);
 //   k_scan_masks    -- per camera, exclusive prefix of the mask popcounts;
-//   k_project_write -- stages the block's 128 Gaussians (geometry and SH) and
-//                      the mask words of its cameras in shared memory, compacts
-//                      the surviving (camera, Gaussian) pairs into a dense item
-//                      list, and for every item
-//                      recomputes the projection, evaluates the SH colour and
-//                      writes the record, the rect and the depth key (float
-//                      bits of z minus those of the near plane) at the pair's
-//                      stable slot.
+//   k_project_write -- every lane holds one Gaussian (geometry, opacity, SH) in
+//                      registers and walks the group's cameras; where its bit is
+//                      set it recomputes the projection, evaluates the SH colour
+//                      and writes the record, the rect, the depth key (float bits
+//                      of z minus those of the near plane) and the Gaussian's
+//                      caller index at the pair's stable slot.
 // The decision chain is written with explicit fmaf / *_rn intrinsics so both
 // passes round identically.
 #include <type_traits>
@@ -345,72 +349,66 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     }
 }
 
-// Colour of one Gaussian seen from camera c. The block's SH coefficients are
-// staged in shared memory as float4 rows: shq[r * WG + local] holds the
-// coefficients of flat index 4r .. 4r + 3 (flat index 3k + ch; zero past 3K),
-// so one 16-byte load brings four of them.
-template <int WGN>
-__device__ __forceinline__ void sh_colour(const float4 *__restrict__ shq, int deg, int local,
-                                          const CamProj &c, const GaussGeo &G, float rgb[3]) {
-    const int K = (deg + 1) * (deg + 1);
-    float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
-    const float dd = dx * dx + dy * dy + dz * dz;
-    if (dd > 0.0f) {
-        const float inv = rsqrt_a(dd);
-        dx *= inv;
-        dy *= inv;
-        dz *= inv;
-    } else {
-        dx = 0.0f;
-        dy = 0.0f;
-        dz = 1.0f;
-    }
-    float Y[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) Y[k] = 0.0f;
-    sh_basis(deg, dx, dy, dz, Y);
-    float acc[3] = {0.5f, 0.5f, 0.5f};
-    const int nq = (3 * K + 3) / 4;
-#pragma unroll
-    for (int r = 0; r < 12; ++r) {
-        if (r < nq) {
-            const float4 q = shq[r * WGN + local];
-            const float v[4] = {q.x, q.y, q.z, q.w};
-            // per channel the terms still add in order of k
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[(4 * r + j) % 3] = fmaf(v[j], Y[(4 * r + j) / 3], acc[(4 * r + j) % 3]);
-        }
-    }
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.0f);
-}
+// A block of Gaussians against one camera, before its Gaussians one by one:
+// BLK_OUT when the exact test culls every Gaussian of the block, BLK_IN when it
+// keeps every one, BLK_PART otherwise. The block is the box of its means (lo,
+// hi) and its largest squared scale (lo.w); hi.w = 0 flags a non-finite value
+// (always BLK_PART). Over the box, a camera-space linear form a.mu + b ranges
+// over its centre value -+ |a|.e (e: half extents), widened for float32
+// rounding. For z > near, u + rb < 0 is fx x + cx z + rb z < 0, and rb z (the
+// prefilter's radius bound times z) is at most
+// B = 1.002 sigma sqrt(kk S + dil Z^2) + 0.02 Z over the block (S, Z its
+// largest squared scale and depth); the test adds 1 % and one pixel times Z.
+// The other three sides likewise. Inside: every mean at least one pixel within
+// the image (u in [1, W - 1], v in [1, H - 1]) and in front of the near plane
+// with a margin, where project() keeps every Gaussian whatever its size.
+enum { BLK_OUT = 0, BLK_IN = 1, BLK_PART = 2 };
 
-// A Gaussian's geometry staged in shared memory as four float4 rows (row r of
-// Gaussian i at rows[r][i]): (mean, smax2), M[0..3], M[4..7], (M[8], extra).
-template <int N>
-__device__ __forceinline__ void store_geo(float4 (*rows)[N], int i, const GaussGeo &G, float extra) {
-    rows[0][i] = make_float4(G.mx, G.my, G.mz, G.smax2);
-    rows[1][i] = make_float4(G.M[0], G.M[1], G.M[2], G.M[3]);
-    rows[2][i] = make_float4(G.M[4], G.M[5], G.M[6], G.M[7]);
-    rows[3][i] = make_float4(G.M[8], extra, 0.0f, 0.0f);
-}
-template <int N>
-__device__ __forceinline__ float load_staged_geo(const float4 (*rows)[N], int i, GaussGeo &G) {
-    const float4 a = rows[0][i], b = rows[1][i], c = rows[2][i], d = rows[3][i];
-    G.mx = a.x;
-    G.my = a.y;
-    G.mz = a.z;
-    G.smax2 = a.w;
-    G.M[0] = b.x;
-    G.M[1] = b.y;
-    G.M[2] = b.z;
-    G.M[3] = b.w;
-    G.M[4] = c.x;
-    G.M[5] = c.y;
-    G.M[6] = c.z;
-    G.M[7] = c.w;
-    G.M[8] = d.x;
-    return d.y;
+__device__ __forceinline__ int classify_block(const CamProj &c, float4 lo, float4 hi,
+                                              const ProjParams &P) {
+    if (!(hi.w > 0.0f)) return BLK_PART;
+    const float mx = 0.5f * (lo.x + hi.x), my = 0.5f * (lo.y + hi.y), mz = 0.5f * (lo.z + hi.z);
+    const float ex = 0.5f * (hi.x - lo.x), ey = 0.5f * (hi.y - lo.y), ez = 0.5f * (hi.z - lo.z);
+    float rlo, rhi;
+    auto range = [&](float ax, float ay, float az, float b) {
+        const float cv = fmaf(ax, mx, fmaf(ay, my, fmaf(az, mz, b)));
+        const float rad = fabsf(ax) * ex + fabsf(ay) * ey + fabsf(az) * ez;
+        const float slack =
+            1e-5f * (fabsf(ax * mx) + fabsf(ay * my) + fabsf(az * mz) + fabsf(b) + rad) + 1e-6f;
+        rlo = cv - rad - slack;
+        rhi = cv + rad + slack;
+    };
+    range(c.R[6], c.R[7], c.R[8], c.t[2]);
+    const float zlo = rlo, zhi = rhi;
+    if (zhi <= P.near_plane) return BLK_OUT;
+    const float Z = fmaxf(zhi, P.near_plane);
+    const float B = fmaf(1.01f, fmaf(1.002f * P.sigma, sqrtf(fmaf(c.kk, lo.w, P.dilation * Z * Z)),
+                                     0.02f * Z), Z);
+    // coefficients of fx x + k z and fy y + k z in world coordinates
+    const float ax0 = c.fx * c.R[0], ax1 = c.fx * c.R[1], ax2 = c.fx * c.R[2], bx = c.fx * c.t[0];
+    const float ay0 = c.fy * c.R[3], ay1 = c.fy * c.R[4], ay2 = c.fy * c.R[5], by = c.fy * c.t[1];
+    auto side = [&](float a0, float a1, float a2, float b, float k) {
+        range(fmaf(k, c.R[6], a0), fmaf(k, c.R[7], a1), fmaf(k, c.R[8], a2), fmaf(k, c.t[2], b));
+    };
+    side(ax0, ax1, ax2, bx, c.cx);  // u >= 0 side
+    if (rhi + B < 0.0f) return BLK_OUT;
+    side(ax0, ax1, ax2, bx, c.cx - c.W);  // u < W side
+    if (rlo - B >= 0.0f) return BLK_OUT;
+    side(ay0, ay1, ay2, by, c.cy);
+    if (rhi + B < 0.0f) return BLK_OUT;
+    side(ay0, ay1, ay2, by, c.cy - c.H);
+    if (rlo - B >= 0.0f) return BLK_OUT;
+    // inside: every mean with z > near (margin) and 1 <= u <= W - 1, 1 <= v <= H - 1
+    if (!(zlo > fmaf(1.001f, P.near_plane, 1e-4f))) return BLK_PART;
+    side(ax0, ax1, ax2, bx, c.cx - 1.0f);
+    if (!(rlo >= 0.0f)) return BLK_PART;
+    side(ax0, ax1, ax2, bx, c.cx - c.W + 1.0f);
+    if (!(rhi <= 0.0f)) return BLK_PART;
+    side(ay0, ay1, ay2, by, c.cy - 1.0f);
+    if (!(rlo >= 0.0f)) return BLK_PART;
+    side(ay0, ay1, ay2, by, c.cy - c.H + 1.0f);
+    if (!(rhi <= 0.0f)) return BLK_PART;
+    return BLK_IN;
 }
 
 // Mask pass in two phases so that the long exact test runs on full warps:
@@ -440,10 +438,14 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     __shared__ long long moff[MAX_GROUP];
     __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane (camera < 64)
     __shared__ uint32_t smask[NW][MAX_GROUP];
+    __shared__ uint8_t cls[MAX_GROUP];                // BLK_OUT / BLK_IN / BLK_PART per camera
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SceneDev sc = scenes[gr.scene];
     if (tid < gr.ncam) {
-        cp[tid] = load_cam(camtab[gr.slot0 + tid]);
+        const CamProj c = load_cam(camtab[gr.slot0 + tid]);
+        cp[tid] = c;
         moff[tid] = cams[gr.slot0 + tid].mask_off;
+        cls[tid] = (uint8_t)classify_block(c, sc.bounds[2 * blockIdx.x], sc.bounds[2 * blockIdx.x + 1], P);
     }
     if (2 * tid < gr.ncam) {  // an odd last camera is paired with itself
         const int c1 = 2 * tid + 1 < gr.ncam ? 2 * tid + 1 : 2 * tid;
@@ -451,7 +453,6 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     }
     smask[warp][lane] = 0u;
     smask[warp][lane + 32] = 0u;
-    const SceneDev sc = scenes[gr.scene];
     const long long g = g0 + tid;
     const bool valid = g < gr.n;
     GaussGeo G;
@@ -497,11 +498,19 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         __syncwarp();
         if (nq >= 32) drain(32);
     };
+    // the block's valid Gaussians: the mask word of a camera that keeps them all
+    const uint32_t all = __ballot_sync(0xffffffffu, valid);
     for (int c = 0; c < gr.ncam; c += 2) {  // two cameras per packed prefilter
+        const int k0 = cls[c], k1 = c + 1 < gr.ncam ? cls[c + 1] : BLK_OUT;
+        if (lane == 0) {
+            if (k0 == BLK_IN) smask[warp][c] = all;
+            if (k1 == BLK_IN) smask[warp][c + 1] = all;
+        }
+        if (k0 != BLK_PART && k1 != BLK_PART) continue;  // block-uniform
         bool in0 = false, in1 = false;
         if (valid) prefilter2(load_pair(cpair[c >> 1]), G, P, in0, in1);
-        append(c, in0);
-        if (c + 1 < gr.ncam) append(c + 1, in1);
+        append(c, in0 && k0 == BLK_PART);
+        if (c + 1 < gr.ncam) append(c + 1, in1 && k1 == BLK_PART);
     }
     if (nq > 0) drain(nq);
     __syncwarp();
@@ -555,146 +564,131 @@ __global__ void __launch_bounds__(1024)
     if (tid == 0) counts[blockIdx.x] = (int)carry;
 }
 
-constexpr int WG = 128;     // Gaussians per write block (4 mask words per camera)
 constexpr float LOG2E = 1.4426950408889634f;
 
-__global__ void __launch_bounds__(PROJ_THREADS, 4)
+// Colour of one Gaussian seen from camera c with its SH coefficients in
+// registers (sh[3 k + ch], zero past the scene's degree): per channel the
+// terms add in order of k, as in the definition.
+template <int DEG>
+__device__ __forceinline__ void sh_colour_reg(const float *sh, const CamProj &c,
+                                              const GaussGeo &G, float rgb[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
+    const float dd = dx * dx + dy * dy + dz * dz;
+    if (dd > 0.0f) {
+        const float inv = rsqrt_a(dd);
+        dx *= inv;
+        dy *= inv;
+        dz *= inv;
+    } else {
+        dx = 0.0f;
+        dy = 0.0f;
+        dz = 1.0f;
+    }
+    float Y[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Y[k] = 0.0f;
+    sh_basis(DEG, dx, dy, dz, Y);
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(sh[3 * k + ch], Y[k], acc[ch]);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.0f);
+}
+
+// SH coefficient rows of Gaussian g into registers (zero past the scene's rows).
+template <typename T, int NC>
+__device__ __forceinline__ void load_sh(const SceneDev &sc, long long g, float *sh) {
+    const int rows = 3 * (sc.deg + 1) * (sc.deg + 1);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) sh[i] = i < rows ? ldt<T>(sc.sh, (long long)i * sc.n + g) : 0.0f;
+}
+
+// Write pass: a block holds the same PROJ_THREADS Gaussians as a mask block and
+// every lane owns one of them: its geometry, opacity and SH coefficients are
+// read from HBM once, into registers, and used for every camera of the group.
+// The warp walks the group's cameras; for a camera whose mask word of this
+// warp is zero it moves on at once, else the lanes whose bit is set recompute
+// the projection (the same arithmetic as the mask pass), evaluate the colour
+// from their registers and write the record at the pair's stable slot (the
+// word's offset plus the set bits below the lane), so the lanes of a word write
+// consecutive slots. With Gaussians stored in spatial order a camera sees
+// either most or none of a warp's 32, so few lanes idle. DEG is the largest SH
+// degree of the chunk's scenes (lower degrees run with zero coefficients,
+// which add nothing).
+template <int DEG>
+__global__ void __launch_bounds__(PROJ_THREADS, 2)
     k_project_write(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
                     const CamInfo *__restrict__ cams, const CamProj *__restrict__ camtab,
                     ProjParams P,
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
                     float4 *__restrict__ rec, int with_d, uint2 *__restrict__ srect,
-                    uint32_t *__restrict__ keys, int *__restrict__ wide,
-                    float ln_alpha_min, const int *__restrict__ status) {
+                    uint32_t *__restrict__ keys, uint32_t *__restrict__ oidx,
+                    int *__restrict__ wide, float ln_alpha_min, const int *__restrict__ status) {
     const Group gr = groups[blockIdx.y];
-    const long long g0 = (long long)blockIdx.x * WG;
+    const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
     if (g0 >= gr.n) return;
     if (status && *status) return;  // the chunk was planned empty: workspace too small
-    constexpr int NE = MAX_GROUP * (WG / 32);  // (camera, mask word) entries
+    constexpr int NW = PROJ_THREADS / 32;
+    constexpr int NC = 3 * (DEG + 1) * (DEG + 1);
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ long long soff[MAX_GROUP];
-    __shared__ float4 sgeo[4][WG];  // geometry rows (store_geo), extra = log2(opacity)
-    __shared__ uint32_t smask[NE], swoff[NE];
-    __shared__ uint16_t items[MAX_GROUP * WG];
-    __shared__ uint32_t wtot[NE / 32];
-    extern __shared__ float4 shq[];  // SH: float4 rows [flat index / 4][WG] (sh_colour)
+    __shared__ uint32_t sword[MAX_GROUP][NW], swoff[MAX_GROUP][NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SceneDev sc = scenes[gr.scene];
-    const int nwords = (int)min((long long)(WG / 32), (gr.n - g0 + 31) >> 5);
-    // 1. stage: the block's Gaussians, their SH rows and all mask words, in two
-    // rounds of global loads. Round 1: the CamInfo of this thread's (camera,
-    // mask word) entry and (threads < WG) its Gaussian's attributes. Round 2,
-    // issued together: its share of the SH rows and the mask word and its
-    // offset. (The cameras' projection constants come from the chunk's table.)
-    static_assert(NE == PROJ_THREADS, "one (camera, mask word) entry per thread");
-    const int cl = tid >> 2, wq = tid & 3;
-    const bool cam_ok = cl < gr.ncam;
-    long long c_moff = 0, c_soff = 0;
-    if (cam_ok) {
-        const CamInfo *ci = cams + gr.slot0 + cl;
-        c_moff = ci->mask_off;
-        c_soff = ci->seg_off;
-    }
-    if (tid < WG) {
-        const long long g = g0 + tid;
-        GaussGeo G;
-        float opacity = 0.0f;
-        if (g < gr.n) {
-            load_geo(sc, g, G);
-            opacity = 1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype)));
-        } else {
-            G.mx = G.my = G.mz = G.smax2 = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
-        }
-        store_geo(sgeo, tid, G, lg2_a(opacity));
-    }
-    // SH: thread t stages Gaussian t % WG in float4 rows t / WG, t / WG + 2, ...
-    // (four coefficient rows each; loads coalesced over consecutive Gaussians)
-    constexpr int RSTEP = PROJ_THREADS / WG, SH_Q = 12 / RSTEP;  // float4 rows per thread
-    const int K3 = 3 * (sc.deg + 1) * (sc.deg + 1);
-    const int nq = (K3 + 3) / 4;
-    const int sl = tid % WG;
-    float4 shv[SH_Q];
-    auto sh_load = [&](auto tag) {
-        using T = decltype(tag);
-        const long long g = g0 + sl;
-#pragma unroll
-        for (int u = 0; u < SH_Q; ++u) {
-            const int r = tid / WG + RSTEP * u;
-            float v[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = 4 * r + j;
-                v[j] = (i < K3 && g < gr.n) ? ldt<T>(sc.sh, (long long)i * sc.n + g) : 0.0f;
-            }
-            shv[u] = make_float4(v[0], v[1], v[2], v[3]);
-        }
-    };
-    if (sc.app_dtype == DT_F32)
-        sh_load(float{});
-    else if (sc.app_dtype == DT_F16)
-        sh_load(__half{});
-    else
-        sh_load(__nv_bfloat16{});
-    {
-        uint32_t m = 0, wo = 0;
-        if (cam_ok && wq < nwords) {
-            const long long at = c_moff + (g0 >> 5) + wq;
+    // the mask word and slot offset of every (camera, warp): consecutive
+    // threads read consecutive words of one camera
+    for (int e = tid; e < gr.ncam * NW; e += PROJ_THREADS) {
+        const int c = e / NW, w = e % NW;
+        const long long wi = (g0 >> 5) + w;
+        uint32_t m = 0u, o = 0u;
+        if ((wi << 5) < gr.n) {
+            const long long at = cams[gr.slot0 + c].mask_off + wi;
             m = masks[at];
-            wo = woff[at];
+            o = woff[at];
         }
-        if (cam_ok && wq == 0) {
-            cp[cl] = load_cam(camtab[gr.slot0 + cl]);
-            soff[cl] = c_soff;
-        }
-        smask[tid] = m;
-        swoff[tid] = wo;
+        sword[c][w] = m;
+        swoff[c][w] = o;
     }
-#pragma unroll
-    for (int u = 0; u < SH_Q; ++u) {
-        const int r = tid / WG + RSTEP * u;
-        if (r < nq) shq[r * WG + sl] = shv[u];
+    if (tid < gr.ncam) {
+        cp[tid] = load_cam(camtab[gr.slot0 + tid]);
+        soff[tid] = cams[gr.slot0 + tid].seg_off;
     }
-    __syncthreads();
-    // 2. item positions: exclusive prefix of the entries' popcounts
-    uint32_t cnt = 0, incl = 0;
-    if (tid < NE) {
-        cnt = __popc(smask[tid]);
-        incl = cnt;
+    // this lane's Gaussian, into registers
+    const long long g = g0 + tid;
+    const bool valid = g < gr.n;
+    GaussGeo G;
+    float sh[NC];
+    float log2o = 0.0f;
+    uint32_t gidx = 0u;
+    if (valid) {
+        load_geo(sc, g, G);
+        log2o = lg2_a(1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype))));
+        if (sc.app_dtype == DT_F32)
+            load_sh<float, NC>(sc, g, sh);
+        else if (sc.app_dtype == DT_F16)
+            load_sh<__half, NC>(sc, g, sh);
+        else
+            load_sh<__nv_bfloat16, NC>(sc, g, sh);
+        gidx = (uint32_t)sc.orig[g];
+    } else {
+        G.mx = G.my = G.mz = G.smax2 = 0.0f;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += v;
-        }
-        if (lane == 31) wtot[warp] = incl;
-    }
-    __syncthreads();
-    if (tid < NE) {
-        uint32_t before = 0;
+        for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < NE / 32; ++k) before += k < warp ? wtot[k] : 0u;
-        uint32_t pos = before + incl - cnt;
-        uint32_t m = smask[tid];
-        const uint32_t hi = (uint32_t)(tid >> 2) << 7, lo = (uint32_t)(tid & 3) * 32u;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            items[pos++] = (uint16_t)(hi | (lo + b));
-            m &= m - 1u;
-        }
+        for (int i = 0; i < NC; ++i) sh[i] = 0.0f;
     }
     __syncthreads();
-    uint32_t total = 0;
-#pragma unroll
-    for (int k = 0; k < NE / 32; ++k) total += wtot[k];
-    // 3. every surviving (camera, Gaussian) pair, densely
-    for (int i = tid; i < (int)total; i += PROJ_THREADS) {
-        const int it = items[i];
-        const int c = it >> 7, local = it & 127, w = local >> 5, bit = local & 31;
-        const int e = c * 4 + w;
-        const uint32_t slot = swoff[e] + __popc(smask[e] & ((1u << bit) - 1u));
-        GaussGeo G;
-        const float log2o = load_staged_geo(sgeo, local, G);
+    const uint32_t lt = (1u << lane) - 1u;
+    // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o/alpha_min):
+    // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
+    // rounding of the per-pixel test can never pass a pixel outside it
+    const float q = 2.0f * fmaf(log2o, 0.6931471805599453f, -ln_alpha_min);
+    for (int c = 0; c < gr.ncam; ++c) {
+        const uint32_t word = sword[c][warp];
+        if (!((word >> lane) & 1u)) continue;
         const CamProj cam = load_cam(cp[c]);
         Proj pr;
         if (!project(cam, G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
@@ -705,17 +699,13 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
             pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
         }
         float rgb[3];
-        sh_colour<WG>(shq, sc.deg, local, cam, G, rgb);
-        // box of the alpha >= alpha_min region d^T Sigma'^-1 d <= q = 2 ln(o/alpha_min):
-        // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
-        // rounding of the per-pixel test can never pass a pixel outside it
-        const float q = 2.0f * fmaf(log2o, 0.6931471805599453f, -ln_alpha_min);
+        sh_colour_reg<DEG>(sh, cam, G, rgb);
         float hx = -1e30f, hy = -1e30f;
         if (q >= 0.0f) {
             hx = fmaf(1.002f, sqrt_a(q * pr.sa), 0.02f);
             hy = fmaf(1.002f, sqrt_a(q * pr.sc), 0.02f);
         }
-        const long long at = soff[c] + slot;
+        const long long at = soff[c] + swoff[c][warp] + __popc(word & lt);
         const uint2 rect = make_uint2((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
                                       (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16));
         rec[rec_a(at)] = make_float4(pr.u, pr.v, hx, hy);
@@ -723,13 +713,14 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
         rec[rec_c(at)] = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
         if (with_d)
             reinterpret_cast<uint4 *>(rec)[rec_d(at)] =
-                make_uint4(rect.x, rect.y, (uint32_t)(g0 + local), __float_as_uint(pr.r));
+                make_uint4(rect.x, rect.y, gidx, __float_as_uint(pr.r));
         srect[at] = rect;
         // depth key: float bits of z minus those of the near plane (z > near, so
         // non-negative and in the same order); its value, the slot, is implied
         // by the position. Keys of 2^26 or more need the depth sort's 4th pass.
         const uint32_t kz = __float_as_uint(pr.z) - __float_as_uint(P.near_plane);
         keys[at] = kz;
+        oidx[at] = gidx;
         if (kz >= (1u << 26)) atomicOr(wide, 1);
     }
 }
@@ -779,17 +770,23 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams, const void *camtab,
                                  ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, float4 *rec, int with_d,
-                                 uint2 *srect, uint32_t *keys, int *wide,
-                                 float ln_alpha_min, const int *status, cudaStream_t s) {
+                                 uint2 *srect, uint32_t *keys, uint32_t *oidx, int *wide,
+                                 float ln_alpha_min, const int *status, int max_deg,
+                                 cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
-    dim3 grid(2 * max_blocks_x, n_groups);  // 128 Gaussians per block
-    const int smem = 12 * WG * (int)sizeof(float4);        // SH of degree <= 3
-    cudaError_t e = cudaFuncSetAttribute(k_project_write,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_project_write<<<grid, PROJ_THREADS, smem, s>>>(groups, scenes, cams, (const CamProj *)camtab, P,
-                                                     masks, woff, rec, with_d, srect, keys, wide,
-                                                     ln_alpha_min, status);
+    dim3 grid(max_blocks_x, n_groups);  // PROJ_THREADS Gaussians per block, as the mask pass
+    const CamProj *ct = (const CamProj *)camtab;
+#define GS_WRITE(D)                                                                              \
+    k_project_write<D><<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, ct, P, masks, woff,   \
+                                                     rec, with_d, srect, keys, oidx, wide,        \
+                                                     ln_alpha_min, status)
+    switch (max_deg) {
+        case 0: GS_WRITE(0); break;
+        case 1: GS_WRITE(1); break;
+        case 2: GS_WRITE(2); break;
+        default: GS_WRITE(3); break;
+    }
+#undef GS_WRITE
     return cudaGetLastError();
 }
 

@@ -65,7 +65,8 @@ __device__ __forceinline__ SortTile tile_of(const SortTile *__restrict__ tab,
     if (tab) return tab[tile];
     const int s = find_seg(tile_start, n_seg, tile);
     const int t0 = (tile - tile_start[s]) * TK;
-    return SortTile{seg_start[s], t0, (int)min((long long)TK, seg_count[s] - t0)};
+    return SortTile{seg_start[s], t0, (int)min((long long)TK, seg_count[s] - t0),
+                    (int)seg_count[s], 0};
 }
 
 // Digit histogram of every tile: BITS-bit digit at `shift`. With a skip flag

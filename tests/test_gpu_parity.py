@@ -267,6 +267,49 @@ def test_edge_case_pixels(torch, R, orc, name):
         R.remove_scene(sid)
 
 
+def _tie_scene(n):
+    """n Gaussians at exactly one depth (z = 2, identity camera) on a short line
+    whose x falls with the index, so the library's spatial storage order (Morton
+    order of the means, increasing with x here) runs against the index order:
+    the stable depth sort alone would leave equal depths in storage order."""
+    rng = np.random.default_rng(n)
+    x = np.linspace(0.05, -0.05, n) if n > 1 else np.zeros(1)
+    m = np.c_[x, np.full(n, 0.01), np.full(n, 2.0)]
+    return scene_from(m, [math.log(0.08)] * 3, [1, 0, 0, 0], rng.normal(-0.5, 0.5, n),
+                      colours=rng.uniform(0, 1, (n, 3)))
+
+
+@pytest.mark.parametrize("n", [3, 100, 1500])
+def test_equal_depths_follow_index_order(torch, R, orc, n):
+    """Runs of equal depth keys of length 3 (reordered in place), 100 and 1,500
+    (sorted by one block, over one and several 1,024-entry tiles): every tile
+    list orders them by Gaussian index, exactly as the oracle's (z, index)
+    order, and the pixels match the oracle."""
+    scene = _tie_scene(n)
+    W, H = 64, 48
+    vm, it = identity_camera(W, H, 60.0)
+    sid = R.add_scene(scene)
+    try:
+        off, gl = R.debug_tile_lists(sid, dev(torch, vm), dev(torch, it), W, H, cap=1_000_000)
+        ref = orc.tile_lists(scene, vm, it, W, H, bands=BANDS)
+        longest = 0
+        for t in range(len(off) - 1):
+            got = gl[off[t]:off[t + 1]]
+            o0, o1 = ref["off"][t], ref["off"][t + 1]
+            fl, g = ref["flags"][o0:o1], ref["g"][o0:o1]
+            ambiguous = set(g[(fl & 2) != 0].tolist())
+            want = [int(x) for x, f in zip(g, fl) if (f & 1) and int(x) not in ambiguous]
+            got = [int(x) for x in got if int(x) not in ambiguous]
+            assert got == want, (t, got[:10], want[:10])
+            assert want == sorted(want)  # all at one depth: index order
+            longest = max(longest, len(want))
+        assert longest == n
+        rgb, depth, T = render_np(torch, R, sid, vm[None], it[None], W, H)
+        assert_camera_parity(rgb[0], depth[0], T[0], orc.render(scene, vm, it, W, H, bands=BANDS))
+    finally:
+        R.remove_scene(sid)
+
+
 def test_many_chunks_and_scenes(torch, gsmod, orc):
     """Cameras of three scenes, interleaved, rendered in chunks of 3 cameras
     with camera groups of 2: the output of camera i is camera i's view."""
