@@ -347,7 +347,7 @@ def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, g
     rgb = torch.empty((P, 3), dtype=torch.float32, device="cuda")
     depth = torch.empty((P,), dtype=torch.float32, device="cuda")
     kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
-              tiles_per_block=args.tpb, camera_group=args.group)
+              tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch)
     counter = gs.Renderer(device=local, count_pairs=1, **kw)
     ids_c = np.array([counter.add_scene(sc) for sc in scenes], dtype=np.int32)[which]
     counter.render_v(ids_c, vm_d, it_d, Ws, Hs, rgb, depth)
@@ -404,6 +404,8 @@ def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, g
                    "cameras_640x480": int((Ws == 640).sum()),
                    "cameras_320x240": int((Ws == 320).sum()),
                    "frames_640x480_equivalent": eq_frames, "chunk_cameras": args.chunk,
+                   "pixels_per_thread": args.ppt, "tiles_per_block": args.tpb,
+                   "comp_batch": args.comp_batch, "camera_group": args.group,
                    "cuda_graph": bool(graph),
                    "storage": "f32" if "dequantised" not in scenes[0] else "f16/bf16"},
         "roofline": {"kernel": "k_composite", "bound": "alu", "achieved": achieved,
@@ -429,7 +431,7 @@ def half_leg(args, gs, torch, synth, scenes, which, vm, local, stream, fp32_tflo
     depth = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
     R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
                     pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
-                    camera_group=args.group)
+                    camera_group=args.group, comp_batch=args.comp_batch)
     try:
         nbytes = 0
         sids = []
@@ -507,7 +509,7 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
     it_d = torch.tensor([[480.0, 480.0, W / 2.0, H / 2.0]], dtype=torch.float32,
                         device="cuda").expand(n, 4).contiguous()
     R = gs.Renderer(device=local, max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
-                    tiles_per_block=args.tpb, camera_group=args.group)
+                    tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch)
     sids = [R.add_scene(sc) for sc in scenes]
     ids = np.array(sids, dtype=np.int32)[which]
     up = gs.Upsampler(device=local)
@@ -632,7 +634,7 @@ def run_b300(args):
 
     # algorithmic work of the compositing kernel on these inputs (counting run)
     kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
-              tiles_per_block=args.tpb, camera_group=args.group)
+              tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch)
     counter = gs.Renderer(device=local, count_pairs=1, **kw)
     sid_c = counter.add_scene(scene)
     counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
@@ -759,6 +761,26 @@ def run_b300(args):
                                  stream, False, fp32, clocks=ClockSampler(local)),
             "graph": batched_leg(args, gs, torch, scenes, which, bvm, bit, Ws, Hs, local,
                                  stream, True, fp32, clocks=ClockSampler(local))}
+        # the autotuner's search on this batch (untimed), then graph replays of
+        # its choice, timed like the other legs
+        from paper_2510_15352_b300 import autotune
+        t0 = time.perf_counter()
+        tuned = autotune.tune(scenes, which, bvm, bit, Ws, Hs, device=local, cache_path=None)
+        t_search = time.perf_counter() - t0
+        cfg = autotune.config_of(tuned)
+        targs = argparse.Namespace(**vars(args))
+        targs.ppt, targs.tpb = cfg["pixels_per_thread"], cfg["tiles_per_block"]
+        targs.comp_batch, targs.group = cfg["comp_batch"], cfg["camera_group"]
+        targs.chunk = cfg["max_chunk_cameras"]
+        leg = batched_leg(targs, gs, torch, scenes, which, bvm, bit, Ws, Hs, local, stream, True,
+                          fp32, clocks=ClockSampler(local))
+        default_ms = [t[0] for t in tuned["timings"] if t[1] == {**autotune.DEFAULTS}]
+        leg["autotuner"] = {"chosen": cfg, "is_default": cfg == dict(autotune.DEFAULTS),
+                            "candidates": len(tuned["timings"]), "search_s": t_search,
+                            "best_ms": tuned["ms"],
+                            "default_ms": default_ms[0] if default_ms else None,
+                            "timings": [[round(t[0], 3), t[1]] for t in tuned["timings"]]}
+        out["batched"]["autotuned"] = leg
         torch.cuda.empty_cache()
         out["half"] = half_leg(args, gs, torch, synth, scenes, which, bvm, local, stream, fp32)
         torch.cuda.empty_cache()
@@ -785,6 +807,8 @@ def main():
                     help="cameras sharing one Gaussian load in the projection (<= 64)")
     ap.add_argument("--tpb", type=int, default=1,
                     help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
+    ap.add_argument("--comp-batch", type=int, default=64,
+                    help="records staged per compositing batch (32|64|96|128, with --ppt 8)")
     ap.add_argument("--precision", choices=["f32", "half"], default="f32",
                     help="headline scene storage (half: FP16 geometry, BF16 appearance)")
     ap.add_argument("--e2e-steps", type=int, default=2)

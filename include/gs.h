@@ -76,7 +76,13 @@ typedef struct gs_config {
     int64_t workspace_survivors; /* surviving (camera, Gaussian) pairs per chunk the
                                     workspace starts with (0: a third of the Gaussians a
                                     chunk sees); it grows when a render needs more */
-    int32_t reserved[4];
+    int32_t sync_errors;   /* 0: render calls only enqueue work; a chunk that does not
+                              fit the workspace is reported later (sticky, see
+                              gs_render_batch). 1: each render call waits for its
+                              status and renders such chunks again at once (0) */
+    int32_t comp_batch;    /* records staged per compositing batch with 8 pixels per
+                              thread: 32, 64, 96 or 128 (64; 0 = 64) */
+    int32_t reserved[2];
 } gs_config;
 
 /* A scene: n Gaussians stored as structure of arrays.
@@ -137,6 +143,13 @@ gs_status gs_config_default(gs_config *out);
  * owns scene storage and the render workspace. *out is NULL on failure. */
 gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **out);
 
+/* Replace a context's launch parameters (chunk size, camera group, compositing
+ * layout and batch, counting, stage timing, sync_errors) after waiting for its
+ * last render call; the rasteriser constants (near plane ... background) must
+ * equal the context's. Scenes and workspace are kept. A service of the library
+ * (used by its autotuner); the paper has no counterpart. Errors: INVALID_ARG. */
+gs_status gs_context_set_config(gs_context *ctx, const gs_config *cfg);
+
 /* Free a context and everything it owns (NULL is a no-op). Waits for its work. */
 void gs_context_destroy(gs_context *ctx);
 
@@ -144,15 +157,24 @@ void gs_context_destroy(gs_context *ctx);
 const char *gs_last_error(gs_context *ctx);
 
 /* Copy a scene into the context (the caller keeps ownership of its arrays).
- * The copy is done before the call returns. *scene_id stays valid until
- * gs_scene_destroy. Errors: INVALID_ARG (n < 0, degree or dtype out of range,
- * NULL pointer with n > 0), OOM, CUDA. */
+ * A scene is one of the paper's reconstructed environments as 3D Gaussians
+ * (Sec. 3.1-3.2: mean, scale, rotation, opacity, SH colour per Gaussian). The
+ * copy is done before the call returns; the library stores the Gaussians in a
+ * spatial (Morton) order of their means and keeps each one's index in the
+ * caller's arrays, which is the index the renderer orders equal depths by and
+ * the inspection calls report. *scene_id stays valid until gs_scene_destroy.
+ * Temporary device memory of about the scene's size is used during the call.
+ * Errors: INVALID_ARG (n < 0, degree or dtype out of range, NULL pointer with
+ * n > 0), OOM, CUDA. */
 gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *desc, int32_t *scene_id);
 
 /* Release a scene's storage. Errors: NOT_FOUND. */
 gs_status gs_scene_destroy(gs_context *ctx, int32_t scene_id);
 
-/* Render n_cams cameras of size width x height.
+/* Render n_cams cameras of size width x height: the batched renderer of the
+ * simulator, one camera per robot, RGB and expected depth from the same
+ * compositing pass (Sec. 3.2 "3D Gaussian Splatting as a Drop-in Renderer";
+ * Sec. 3.3 and Fig. 4 for depth; Sec. 3.3: 4,096 environments at 640x480).
  *   scene_ids   HOST   [n_cams] scene of each camera (the library groups cameras
  *                      by scene so one Gaussian load serves many cameras)
  *   viewmats    DEVICE [n_cams][16] float32, row-major world->camera
@@ -160,9 +182,16 @@ gs_status gs_scene_destroy(gs_context *ctx, int32_t scene_id);
  *   rgb         DEVICE [n_cams][height][width][3] float32, written
  *   depth       DEVICE [n_cams][height][width] float32, written
  *   final_T     DEVICE [n_cams][height][width] float32 or NULL
- * Work is enqueued on `stream`; the call also synchronises that stream once
- * per chunk of cameras (to size the workspace exactly), so when it returns
- * GS_OK every chunk but the last has completed and the last is enqueued.
+ * Work is enqueued on `stream` and, with the default sync_errors = 0, the call
+ * returns without waiting for it (it waits only when the workspace has to
+ * grow, or for a staging buffer that a call two calls back still copies
+ * from). Calls on one context run in call order even on different streams.
+ * A chunk of cameras whose survivors exceed the workspace is not rendered;
+ * the device records it in a sticky status word and a later render call,
+ * gs_sync or gs_get_stats returns GS_ERR_CAPACITY (once); the images of that
+ * call are then not valid, the workspace has grown to the size recorded, and
+ * rendering again succeeds. With sync_errors = 1 the call instead waits for
+ * its status and renders such chunks again before it returns.
  * Output buffers must not overlap the inputs. n_cams == 0 is a no-op.
  * Errors: INVALID_ARG, NOT_FOUND, CAPACITY (more than 65536 16x16 tiles per camera),
  * OOM, CUDA. */
@@ -171,7 +200,9 @@ gs_status gs_render_batch(gs_context *ctx, int32_t n_cams, const int32_t *scene_
                           int32_t height, float *rgb, float *depth, float *final_T,
                           void *stream);
 
-/* gs_render_batch with a size per camera (a batch may mix resolutions).
+/* gs_render_batch with a size per camera (a batch may mix resolutions; many
+ * robots over scenes of uneven size, Sec. 3.3: 4,096 environments over 128
+ * scenes).
  *   widths, heights  HOST [n_cams] camera sizes (each as in gs_render_batch)
  *   pixel_offsets    HOST [n_cams] index of camera i's first pixel in the packed
  *                    outputs: camera i writes rgb[3 * (off_i + y * W_i + x) + ch],
@@ -200,7 +231,8 @@ gs_status gs_render_motion_blur(gs_context *ctx, int32_t n_cams, const int32_t *
                                 float *final_T, void *stream);
 
 /* Record the render of a fixed batch of cameras (arguments as gs_render_batch_v,
- * no stream) into a CUDA graph. The call renders the batch once (which sizes the
+ * no stream) into a CUDA graph (the paper's vectorised simulator renders the
+ * same batch of environment cameras every camera step, Sec. 3.3). The call renders the batch once (which sizes the
  * workspace; the graph keeps 1.25x headroom over the survivors it saw), then
  * captures the whole kernel sequence -- projection, sort, binning, compositing
  * for every chunk, with no host round trip inside -- into one graph. Later
@@ -227,7 +259,8 @@ gs_status gs_graph_check(gs_graph *g, void *stream);
 /* Free the graph (NULL is a no-op). */
 void gs_graph_destroy(gs_graph *g);
 
-/* Same as gs_render_batch with every array in HOST memory: the call copies the
+/* Same as gs_render_batch (Sec. 3.2) with every array in HOST memory, for a
+ * host-side consumer of the frames: the call copies the
  * cameras to the device, renders into context-owned device buffers in parts of
  * at most min(max_chunk_cameras, 128) cameras and copies each part back on a
  * second stream while the next part renders (pinned host buffers make the copies asynchronous DMA).
@@ -237,9 +270,19 @@ gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *s
                                int32_t height, float *rgb, float *depth, float *final_T,
                                void *stream);
 
-/* Counters (and stage times with time_stages) of the last render call. Waits for
- * the last call's work when its counters or times are still on the device. */
+/* Counters (and stage times with time_stages) of the last render call (a
+ * service of the library; the paper reports whole-simulator throughput only).
+ * Waits for the last render call's work. Returns GS_ERR_CAPACITY (after
+ * filling *out) when a render call of this context had a chunk that did not
+ * fit the workspace and that has not been reported yet (see gs_render_batch);
+ * the report clears it. */
 gs_status gs_get_stats(gs_context *ctx, gs_stats *out);
+
+/* Wait for `stream` and the context's last render call, then report a pending
+ * device-detected error of an earlier asynchronous render call (as
+ * gs_get_stats does; GS_OK if there is none). The paper has no counterpart:
+ * it is the completion point of the asynchronous render calls. */
+gs_status gs_sync(gs_context *ctx, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Inspection entry points (used by the test suite). Each runs the hot-path

@@ -1,18 +1,25 @@
 """Autotuner for the batched renderer's launch parameters.
 
 It times real renders of the caller's batch (CUDA events on the render
-stream, after a warm-up render) over:
+stream, after a warm-up render) with one context whose launch parameters are
+changed between candidates (gs_context_set_config; the scenes are uploaded
+once), over:
   pixels_per_thread   2, 4 or 8 -- the compositing layout: each warp of a tile
                       block covers 4x16, 8x16 or 16x16 pixels (the shape of the
                       pixel region over which Gaussians are culled and blended);
   tiles_per_block     1 or 4 -- with 8 pixels per thread, one tile per block or a
                       2x2 quad of tiles sharing the list scan and record staging;
+  comp_batch          32, 64, 96 or 128 -- Gaussian records staged per
+                      compositing batch (8 pixels per thread, one tile per block);
   camera_group        cameras of one scene that share one Gaussian load in the
                       projection kernels (Gaussian batch per projection block);
-  max_chunk_cameras   cameras per chunk of the render pipeline,
-and keeps the fastest. Results are cached in a JSON file keyed by the GPU and a
-signature of the batch (camera count, resolutions, scene sizes, SH degrees),
-so a later run with the same kind of batch skips the search.
+  max_chunk_cameras   cameras per chunk of the render pipeline.
+The search is staged: first the compositing knobs (layout and batch) with the
+default pipeline knobs, then the pipeline knobs (camera group and chunk) with
+the best compositing knobs; the fastest candidate is kept. Results are cached
+in a JSON file keyed by the GPU and a signature of the batch (camera count,
+resolutions, scene sizes, SH degrees), so a later run with the same kind of
+batch skips the search.
 """
 from __future__ import annotations
 
@@ -26,9 +33,15 @@ import numpy as np
 DEFAULT_SPACE = {
     "pixels_per_thread": (2, 4, 8),
     "tiles_per_block": (1, 4),
+    "comp_batch": (32, 64, 96, 128),
     "camera_group": (32, 64),
     "max_chunk_cameras": (128, 256, 512),
 }
+# the stages of the search: compositing knobs first, then the pipeline knobs
+STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch"),
+          ("camera_group", "max_chunk_cameras"))
+DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 64,
+            "camera_group": 64, "max_chunk_cameras": 512}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
 
@@ -65,16 +78,28 @@ def store_cache(entry_key: str, entry: dict, path: str = DEFAULT_CACHE) -> None:
     os.replace(tmp, path)
 
 
-def candidates(space: dict | None = None):
-    """Every combination of the space, except quads with fewer than 8 pixels per
-    thread (the library runs those as one tile per block: a duplicate)."""
+def _distinct(c: dict) -> bool:
+    """False for combinations the library runs as another one: quads need 8
+    pixels per thread, and the batch is a knob of the 8-pixel, one-tile layout
+    only (others stage 64)."""
+    ppt, tpb = c.get("pixels_per_thread", 8), c.get("tiles_per_block", 1)
+    if tpb == 4 and ppt != 8:
+        return False
+    if c.get("comp_batch", 64) != 64 and (ppt != 8 or tpb != 1):
+        return False
+    return True
+
+
+def candidates(space: dict | None = None, keys=None, base: dict | None = None):
+    """Every distinct combination of `keys` of the space (all keys by default),
+    the other knobs taken from `base`."""
     space = space or DEFAULT_SPACE
-    keys = sorted(space)
+    keys = sorted(k for k in (keys or space) if k in space)
     for vals in itertools.product(*(space[k] for k in keys)):
-        c = dict(zip(keys, vals))
-        if c.get("tiles_per_block", 1) == 4 and c.get("pixels_per_thread", 8) != 8:
-            continue
-        yield c
+        c = dict(base or {})
+        c.update(zip(keys, vals))
+        if _distinct(c):
+            yield c
 
 
 def tune(scenes, scene_of_camera, viewmats, intrinsics, widths, heights, device: int = 0,
@@ -97,11 +122,14 @@ def tune(scenes, scene_of_camera, viewmats, intrinsics, widths, heights, device:
     rgb = torch.empty((P, 3), dtype=torch.float32, device=vm.device)
     depth = torch.empty((P,), dtype=torch.float32, device=vm.device)
     stream = torch.cuda.current_stream(device)
+    space = space or DEFAULT_SPACE
     timings = []
-    for cand in candidates(space):
-        r = gs.Renderer(device=device, **cand)
-        try:
-            ids = np.array([r.add_scene(s) for s in scenes], dtype=np.int32)[scene_of_camera]
+    r = gs.Renderer(device=device)
+    try:
+        ids = np.array([r.add_scene(s) for s in scenes], dtype=np.int32)[scene_of_camera]
+
+        def measure(cand):
+            r.set_config(**cand)
             r.render_v(ids, vm, it, widths, heights, rgb, depth, stream=stream)  # warm-up
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -109,10 +137,20 @@ def tune(scenes, scene_of_camera, viewmats, intrinsics, widths, heights, device:
             for _ in range(repeats):
                 r.render_v(ids, vm, it, widths, heights, rgb, depth, stream=stream)
             e1.record(stream)
-            torch.cuda.synchronize(device)
-            timings.append((e0.elapsed_time(e1) / repeats, cand))
-        finally:
-            r.close()
+            r.sync(stream)
+            ms = e0.elapsed_time(e1) / repeats
+            timings.append((ms, dict(cand)))
+            return ms
+
+        best = {k: v for k, v in DEFAULTS.items() if k in space}
+        for keys in STAGES:
+            stage = [c for c in candidates(space, keys, best)]
+            if not stage:
+                continue
+            ms = [measure(c) for c in stage]
+            best = stage[int(np.argmin(ms))]
+    finally:
+        r.close()
     best_ms, best = min(timings, key=lambda t: t[0])
     entry = dict(best)
     entry["ms"] = best_ms

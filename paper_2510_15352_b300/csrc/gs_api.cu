@@ -79,6 +79,18 @@ struct gs_context {
     cudaEvent_t up_done = nullptr;
     DevBuf lr_in, lr_rgb, lr_depth;           // upsampled entry point: quarter-resolution frames
     int ev_used = 0;              // chunks whose events the last call recorded
+    // asynchronous calls: a sticky device word ([0] largest chunk need seen, [1]
+    // a chunk did not fit), read back into pinned memory after every call and
+    // looked at by a later call, gs_sync or gs_get_stats
+    DevBuf sticky;
+    PinBuf sticky_h;
+    cudaEvent_t sticky_ev = nullptr;
+    bool sticky_pending = false;
+    PinBuf tab_pin[2];            // pinned staging of the per-call tables, two in turn
+    cudaEvent_t tab_ev[2] = {nullptr, nullptr};  // after each one's last copy
+    int tab_next = 0;
+    cudaEvent_t done_ev = nullptr;  // end of the last render call's work (orders streams)
+    bool done_valid = false;
 };
 
 struct gs_graph {
@@ -169,6 +181,7 @@ struct RenderArgs {
     Stage upto;
     float out_w = 1.0f;        // outputs = out_w * value (+ existing outputs if accumulate)
     int accumulate = 0;
+    bool force_sync = false;   // wait for the status and re-render overflowed chunks here
     int cam_w(int i) const { return Ws ? Ws[i] : W; }
     int cam_h(int i) const { return Hs ? Hs[i] : H; }
     long long cam_pix(int i) const { return pix_off ? pix_off[i] : (long long)i * W * H; }
@@ -365,7 +378,8 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(launch_plan(cams, (const int *)ctx->counts.p, ch.m, ch.bin_ranks, ctx->cap_survivors,
                         (int *)ctx->blkpre.p, (int *)ctx->sorttiles.p, (long long *)ctx->segstart.p,
                         (long long *)ctx->segcount.p, (SortTile *)ctx->sorttab.p,
-                        (int2 *)ctx->bintab.p, status, need, stats + 6, st));
+                        (int2 *)ctx->bintab.p, status, need, stats + 6,
+                        (unsigned long long *)ctx->sticky.p, st));
         int *wide = (int *)ctx->wide.p + k;
         CKC(cudaMemsetAsync(wide, 0, sizeof(int), st));
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
@@ -403,7 +417,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                              (const uint32_t *)ctx->tvals.p, (const uint2 *)ctx->rrect.p,
                              (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
                              cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,
-                             status, st));
+                             cfg.comp_batch, status, st));
         if (E) CKC(cudaEventRecord(E[4], st));
     }
     return GS_OK;
@@ -417,6 +431,54 @@ gs_status upload_tables(gs_context *ctx, const Plan &P, DevBuf &dst, cudaStream_
     if (!P.groups.empty()) memcpy(h + P.off_groups, P.groups.data(), P.groups.size() * sizeof(Group));
     memcpy(h + P.off_tilepre, P.tilepre.data(), P.tilepre.size() * sizeof(int));
     CKC(cudaMemcpyAsync(dst.p, h, P.table_bytes, cudaMemcpyHostToDevice, st));
+    return GS_OK;
+}
+
+// The per-call tables through one of two pinned staging buffers in turn: a
+// buffer is refilled only after its previous copy has run, so an asynchronous
+// call never overwrites tables a queued copy still reads.
+gs_status upload_tables_ring(gs_context *ctx, const Plan &P, cudaStream_t st) {
+    const int i = ctx->tab_next;
+    ctx->tab_next ^= 1;
+    if (!ctx->tab_ev[i]) CKC(cudaEventCreateWithFlags(&ctx->tab_ev[i], cudaEventDisableTiming));
+    CKC(cudaEventSynchronize(ctx->tab_ev[i]));
+    CKS(grow_pinned(ctx, ctx->tab_pin[i], P.table_bytes));
+    CKS(grow(ctx, ctx->tables, P.table_bytes));
+    char *h = (char *)ctx->tab_pin[i].p;
+    memcpy(h, P.cams.data(), P.cams.size() * sizeof(CamInfo));
+    if (!P.groups.empty()) memcpy(h + P.off_groups, P.groups.data(), P.groups.size() * sizeof(Group));
+    memcpy(h + P.off_tilepre, P.tilepre.data(), P.tilepre.size() * sizeof(int));
+    CKC(cudaMemcpyAsync(ctx->tables.p, h, P.table_bytes, cudaMemcpyHostToDevice, st));
+    CKC(cudaEventRecord(ctx->tab_ev[i], st));
+    return GS_OK;
+}
+
+// The sticky status of earlier calls, from its last read-back (waiting for it
+// only when `wait`). The workspace plan grows to the largest chunk seen; a
+// chunk that did not fit is reported once (GS_ERR_CAPACITY) and the device
+// flag cleared on `st`.
+gs_status poll_sticky(gs_context *ctx, bool wait, cudaStream_t st) {
+    if (!ctx->sticky_pending) return GS_OK;
+    if (wait) {
+        CKC(cudaEventSynchronize(ctx->sticky_ev));
+    } else {
+        const cudaError_t q = cudaEventQuery(ctx->sticky_ev);
+        if (q == cudaErrorNotReady) return GS_OK;
+        CKC(q);
+    }
+    ctx->sticky_pending = false;
+    const unsigned long long *h = (const unsigned long long *)ctx->sticky_h.p;
+    const long long need = (long long)h[0];
+    ctx->last_chunk_survivors = std::max(ctx->last_chunk_survivors, need);
+    if (h[1]) {
+        ctx->cap_survivors = std::max(ctx->cap_survivors, need + need / 8 + 1024);
+        CKC(cudaMemsetAsync((unsigned long long *)ctx->sticky.p + 1, 0, 8, st));
+        return fail(ctx, GS_ERR_CAPACITY,
+                    "an earlier render call had a chunk of %lld survivors, more than the "
+                    "workspace held: its images are not valid (the workspace has grown; render "
+                    "again)",
+                    need);
+    }
     return GS_OK;
 }
 
@@ -434,11 +496,22 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             CKC(cudaEventCreate(&e));
             ctx->ev.push_back(e);
         }
+    if (!ctx->sticky.p) {
+        CKS(grow(ctx, ctx->sticky, 2 * sizeof(unsigned long long)));
+        CKC(cudaMemset(ctx->sticky.p, 0, 2 * sizeof(unsigned long long)));
+        CKS(grow_pinned(ctx, ctx->sticky_h, 2 * sizeof(unsigned long long)));
+        CKC(cudaEventCreateWithFlags(&ctx->sticky_ev, cudaEventDisableTiming));
+        CKC(cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming));
+    }
+    // an error an earlier asynchronous call left is reported by this one
+    CKS(poll_sticky(ctx, false, a.st));
+    if (ctx->done_valid) CKC(cudaStreamWaitEvent(a.st, ctx->done_ev, 0));  // calls in order
     const size_t status_bytes = sizeof(long long) + P.chunks.size() * sizeof(int);
+    const bool sync = ctx->cfg.sync_errors != 0 || a.force_sync;
     std::vector<char> redo;
     for (int attempt = 0; attempt < 2; ++attempt) {
         CKS(size_workspace(ctx, P));
-        CKS(upload_tables(ctx, P, ctx->tables, a.st));
+        CKS(upload_tables_ring(ctx, P, a.st));
         if (attempt == 0) CKC(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), a.st));
         CKC(cudaMemsetAsync(ctx->status.p, 0, status_bytes, a.st));
         // the second pass renders only the chunks that overflowed (the others are
@@ -446,6 +519,14 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         CKS(enqueue_render(ctx, a, P, (char *)ctx->tables.p, a.st,
                            timing && attempt == 0 ? ctx->ev.data() : nullptr,
                            attempt ? &redo : nullptr));
+        if (!sync) {
+            // no host wait: the sticky word is read back for a later call
+            CKC(cudaMemcpyAsync(ctx->sticky_h.p, ctx->sticky.p, 2 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, a.st));
+            CKC(cudaEventRecord(ctx->sticky_ev, a.st));
+            ctx->sticky_pending = true;
+            break;
+        }
         CKS(grow_pinned(ctx, ctx->pin[1], status_bytes + 64));
         char *hs = (char *)ctx->pin[1].p;
         CKC(cudaMemcpyAsync(hs, ctx->status.p, status_bytes, cudaMemcpyDeviceToHost, a.st));
@@ -462,7 +543,11 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
             return fail(ctx, GS_ERR_CAPACITY, "workspace overflow after resizing (%lld survivors)",
                         need);
         ctx->cap_survivors = need + need / 8 + 1024;  // exact need plus headroom; render again
+        // re-rendered here: not an error for a later call
+        CKC(cudaMemsetAsync((unsigned long long *)ctx->sticky.p + 1, 0, 8, a.st));
     }
+    CKC(cudaEventRecord(ctx->done_ev, a.st));
+    ctx->done_valid = true;
     gs_stats stt{};
     stt.n_cameras = a.n;
     stt.n_chunks = (int)P.chunks.size();
@@ -500,7 +585,7 @@ gs_status validate(gs_context *ctx, int n, const int32_t *scene_ids, const void 
 
 extern "C" {
 
-int32_t gs_abi_version(void) { return 3; }
+int32_t gs_abi_version(void) { return 4; }
 
 const char *gs_status_string(gs_status s) {
     switch (s) {
@@ -531,7 +616,27 @@ gs_status gs_config_default(gs_config *out) {
     out->time_stages = 0;
     out->pixels_per_thread = 8;
     out->tiles_per_block = 1;
+    out->comp_batch = COMP_BATCH;
+    out->sync_errors = 0;
     return GS_OK;
+}
+
+// Checks a configuration and fills its defaults (0 fields that mean a default).
+static bool check_config(gs_config &c) {
+    if (!(c.near_plane > 0.0f) || !(c.dilation >= 0.0f) || !(c.sigma_cull > 0.0f) ||
+        !(c.alpha_min > 0.0f) || !(c.alpha_max > 0.0f && c.alpha_max < 1.0f) ||
+        !(c.T_min > 0.0f && c.T_min < 1.0f) || c.max_chunk_cameras < 1 || c.camera_group < 1 ||
+        c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) || c.workspace_survivors < 0 ||
+        (c.pixels_per_thread != 2 && c.pixels_per_thread != 4 && c.pixels_per_thread != 8) ||
+        (c.tiles_per_block != 0 && c.tiles_per_block != 1 && c.tiles_per_block != 4) ||
+        (c.comp_batch != 0 && c.comp_batch != 32 && c.comp_batch != 64 && c.comp_batch != 96 &&
+         c.comp_batch != 128) ||
+        (c.sync_errors != 0 && c.sync_errors != 1))
+        return false;
+    // 0 (a zero-initialised config) means 1; quads use 8 pixels per thread
+    if (c.tiles_per_block == 0 || c.pixels_per_thread != 8) c.tiles_per_block = 1;
+    if (c.comp_batch == 0) c.comp_batch = COMP_BATCH;
+    return true;
 }
 
 gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **out) {
@@ -542,15 +647,7 @@ gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **o
         c = *cfg;
     else
         gs_config_default(&c);
-    if (!(c.near_plane > 0.0f) || !(c.dilation >= 0.0f) || !(c.sigma_cull > 0.0f) ||
-        !(c.alpha_min > 0.0f) || !(c.alpha_max > 0.0f && c.alpha_max < 1.0f) ||
-        !(c.T_min > 0.0f && c.T_min < 1.0f) || c.max_chunk_cameras < 1 || c.camera_group < 1 ||
-        c.camera_group > MAX_GROUP || !(c.guard_band >= 1.0f) || c.workspace_survivors < 0 ||
-        (c.pixels_per_thread != 2 && c.pixels_per_thread != 4 && c.pixels_per_thread != 8) ||
-        (c.tiles_per_block != 0 && c.tiles_per_block != 1 && c.tiles_per_block != 4))
-        return GS_ERR_INVALID_ARG;
-    // 0 (a zero-initialised config) means 1; quads use 8 pixels per thread
-    if (c.tiles_per_block == 0 || c.pixels_per_thread != 8) c.tiles_per_block = 1;
+    if (!check_config(c)) return GS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return GS_ERR_INVALID_ARG;
@@ -559,6 +656,22 @@ gs_status gs_context_create(const gs_config *cfg, int32_t device, gs_context **o
     ctx->cfg = c;
     ctx->device = device;
     *out = ctx;
+    return GS_OK;
+}
+
+gs_status gs_context_set_config(gs_context *ctx, const gs_config *cfg) {
+    if (!ctx || !cfg) return GS_ERR_INVALID_ARG;
+    gs_config c = *cfg;
+    if (!check_config(c)) return fail(ctx, GS_ERR_INVALID_ARG, "invalid configuration");
+    const gs_config &o = ctx->cfg;
+    if (c.near_plane != o.near_plane || c.dilation != o.dilation || c.guard_band != o.guard_band ||
+        c.sigma_cull != o.sigma_cull || c.alpha_min != o.alpha_min || c.alpha_max != o.alpha_max ||
+        c.T_min != o.T_min || c.background[0] != o.background[0] ||
+        c.background[1] != o.background[1] || c.background[2] != o.background[2])
+        return fail(ctx, GS_ERR_INVALID_ARG, "the rasteriser constants of a context are fixed");
+    CKC(cudaSetDevice(ctx->device));
+    if (ctx->done_valid) CKC(cudaEventSynchronize(ctx->done_ev));
+    ctx->cfg = c;
     return GS_OK;
 }
 
@@ -579,6 +692,14 @@ void gs_context_destroy(gs_context *ctx) {
         if (b->p) cudaFree(b->p);
     for (auto &p : ctx->pin)
         if (p.p) cudaFreeHost(p.p);
+    for (auto &p : ctx->tab_pin)
+        if (p.p) cudaFreeHost(p.p);
+    if (ctx->sticky_h.p) cudaFreeHost(ctx->sticky_h.p);
+    if (ctx->sticky.p) cudaFree(ctx->sticky.p);
+    for (auto &e : ctx->tab_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->sticky_ev) cudaEventDestroy(ctx->sticky_ev);
+    if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
     for (auto &e : ctx->ev) cudaEventDestroy(e);
     for (auto &e : ctx->part_done) cudaEventDestroy(e);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -792,13 +913,24 @@ gs_status gs_graph_create(gs_context *ctx, int32_t n_cams, const int32_t *scene_
     if (!ctx || !out) return GS_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_cams < 1) return fail(ctx, GS_ERR_INVALID_ARG, "a graph needs at least one camera");
-    // size everything with one eager render of the same cameras
-    CKS(gs_render_batch_v(ctx, n_cams, scene_ids, viewmats, intrinsics, widths, heights,
-                          pixel_offsets, rgb, depth, final_T, nullptr));
-    CKC(cudaDeviceSynchronize());
+    // size everything with one eager render of the same cameras (waiting for its
+    // status, so the survivors of its largest chunk are known)
+    if (!widths || !heights || !pixel_offsets)
+        return fail(ctx, GS_ERR_INVALID_ARG, "NULL per-camera size or offset array");
+    for (int i = 0; i < n_cams; ++i) {
+        CKS(validate(ctx, 1, scene_ids + i, viewmats, intrinsics, widths[i], heights[i], rgb,
+                     depth, true));
+        if (pixel_offsets[i] < 0) return fail(ctx, GS_ERR_INVALID_ARG, "negative pixel offset");
+    }
+    ctx->err.clear();
+    CKC(cudaSetDevice(ctx->device));
     RenderArgs a{n_cams, scene_ids, viewmats, intrinsics, 0,
                  0,      widths,    heights,  pixel_offsets, rgb,
                  depth,  final_T,   nullptr,  UPTO_ALL};
+    a.force_sync = true;
+    CKS(render_impl(ctx, a));
+    CKC(cudaDeviceSynchronize());
+    a.force_sync = false;
     Plan P;
     build_plan(ctx, a, P);
     // headroom for cameras that move between launches: 1.25x the largest chunk seen
@@ -872,11 +1004,15 @@ gs_status gs_graph_check(gs_graph *g, void *stream) {
     CKC(cudaMemcpy(h.data(), ctx->status.p, h.size(), cudaMemcpyDeviceToHost));
     const int *st = (const int *)(h.data() + sizeof(long long));
     for (int k = 0; k < g->n_chunks; ++k)
-        if (st[k])
+        if (st[k]) {
+            // reported here, not again by a later call
+            if (ctx->sticky.p)
+                CKC(cudaMemset((unsigned long long *)ctx->sticky.p + 1, 0, sizeof(unsigned long long)));
             return fail(ctx, GS_ERR_CAPACITY,
                         "a graph launch exceeded the workspace (%lld survivors in a chunk): "
                         "render eagerly once and create the graph again",
                         *(const long long *)h.data());
+        }
     return GS_OK;
 }
 
@@ -936,6 +1072,7 @@ gs_status gs_render_batch_host(gs_context *ctx, int32_t n_cams, const int32_t *s
                      final_T ? (float *)ctx->h_T.p + p0 : nullptr,
                      st,
                      UPTO_ALL};
+        a.force_sync = true;  // a part is copied out only once it is complete
         gs_status rs = render_impl(ctx, a);
         if (rs != GS_OK) {
             cudaStreamSynchronize(ctx->copy_stream);
@@ -995,6 +1132,7 @@ gs_status gs_render_batch_upsampled(gs_context *ctx, gs_upsampler *up, int32_t n
         float *ld = (float *)ctx->lr_depth.p + (size_t)c0 * lpx;
         RenderArgs a{m,  scene_ids + c0, viewmats + 16LL * c0, (const float *)ctx->lr_in.p + 4LL * c0,
                      w,  h,  nullptr, nullptr, nullptr, lr, ld, nullptr, st, UPTO_ALL};
+        a.force_sync = true;  // the upsampler reads a part only once it is complete
         CKS(render_impl(ctx, a));
         CKC(cudaEventRecord(ctx->part_done[k], st));
         CKC(cudaStreamWaitEvent(ctx->up_stream, ctx->part_done[k], 0));
@@ -1008,10 +1146,19 @@ gs_status gs_render_batch_upsampled(gs_context *ctx, gs_upsampler *up, int32_t n
     return GS_OK;
 }
 
+gs_status gs_sync(gs_context *ctx, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    CKC(cudaSetDevice(ctx->device));
+    CKC(cudaStreamSynchronize((cudaStream_t)stream));
+    if (ctx->done_valid) CKC(cudaEventSynchronize(ctx->done_ev));
+    return poll_sticky(ctx, true, (cudaStream_t)stream);
+}
+
 gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
     if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    CKC(cudaSetDevice(ctx->device));
+    if (ctx->done_valid) CKC(cudaEventSynchronize(ctx->done_ev));  // the last call is complete
     if (ctx->stats_pending && ctx->stats.p) {
-        CKC(cudaSetDevice(ctx->device));
         unsigned long long h[8];
         CKC(cudaMemcpy(h, ctx->stats.p, sizeof(h), cudaMemcpyDeviceToHost));
         ctx->last.pairs_evaluated = (int64_t)h[0];
@@ -1039,7 +1186,7 @@ gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
         ctx->stats_pending = false;
     }
     *out = ctx->last;
-    return GS_OK;
+    return poll_sticky(ctx, true, nullptr);  // a chunk of an earlier call did not fit
 }
 
 // The first S records of the last render (all four fields) to the host.
@@ -1067,6 +1214,7 @@ gs_status gs_debug_project(gs_context *ctx, int32_t scene_id, const float *viewm
     cudaStream_t st = (cudaStream_t)stream;
     RenderArgs a{1,       &scene_id, viewmat, intrinsics, width, height, nullptr, nullptr,
                  nullptr, nullptr,   nullptr, nullptr,    st,    UPTO_PROJECT};
+    a.force_sync = true;
     CKS(render_impl(ctx, a));
     CKC(cudaStreamSynchronize(st));
     gs_stats tmp;
@@ -1119,6 +1267,7 @@ gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *vi
     cudaStream_t st = (cudaStream_t)stream;
     RenderArgs a{1,       &scene_id, viewmat, intrinsics, width, height, nullptr, nullptr,
                  nullptr, nullptr,   nullptr, nullptr,    st,    UPTO_BIN};
+    a.force_sync = true;
     CKS(render_impl(ctx, a));
     CKC(cudaStreamSynchronize(st));
     gs_stats tmp;

@@ -19,6 +19,7 @@ constexpr int BIN_RANKS_SMALL = 256;  // ... or 1 per thread when the bitmap wor
 constexpr int BIN_SMEM_MAX = 200 * 1024;  // this much shared memory
 constexpr int MAX_TILES = 65536;    // tiles per camera (binning smem: 2 B per tile)
 constexpr int COMP_BATCH = 64;      // Gaussian records staged per compositing sub-batch
+                                    // (default; 32 / 96 / 128 selectable for 8 px per thread)
 
 enum : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 
@@ -191,7 +192,8 @@ cudaError_t launch_blur_poses(const float *vm, const float *vel, int n, int k, f
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks, long long cap_survivors,
                         int *blkpre, int *sorttiles, long long *segstart, long long *segcount,
                         SortTile *stiles, int2 *bintab, int *status, long long *need,
-                        unsigned long long *survivors, cudaStream_t s);
+                        unsigned long long *survivors, unsigned long long *sticky,
+                        cudaStream_t s);
 
 // Super-tile bitmaps (one row of ceil(count/32) words per 64x64-pixel
 // super-tile) and the rank-ordered tile rects.
@@ -214,6 +216,7 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
-                             int tiles_per_block, const int *status, cudaStream_t s);
+                             int tiles_per_block, int comp_batch, const int *status,
+                             cudaStream_t s);
 
 }  // namespace gsk

@@ -11,9 +11,11 @@
 // super-tile), turns the set bits into candidate ranks in shared memory
 // (block prefix of popcounts), keeps the candidates whose exact tile rect
 // holds this tile (order-preserving ballot compaction), then stages up to
-// COMP_BATCH (64) of their records at a time in shared memory and composites
-// them (64 rather than 128: the skip test's live-pixel rectangle is refreshed
-// twice as often, 21.31 -> 20.48 ms per 1,024 cameras). Per pixel
+// a batch of their records at a time in shared memory and composites them
+// (COMP_BATCH = 64 by default; with 8 pixels per thread the batch is a template
+// parameter, 32, 64, 96 or 128, chosen by the configuration / autotuner: a
+// smaller batch refreshes the skip test's live-pixel rectangle more often, a
+// larger one amortises the staging). Per pixel
 // and Gaussian:
 //   p = a'dx^2 + b'dx dy + c'dy^2 + log2(o) = log2(o e^power)
 //   p < log2(alpha_min): skip;  alpha = min(alpha_max, 2^p)
@@ -105,7 +107,7 @@ __device__ __forceinline__ int block_camera(const int *__restrict__ prefix, int 
 // registers and 17 blocks (21.74 ms). Earlier layouts, per 1,024 cameras: 16
 // blocks 29.0 ms, 18 blocks 28.2 ms, 20 blocks 27.2 ms, 22 blocks 28.6 ms, 24
 // blocks 31.3 ms (the last two spill).
-template <int PPT, bool STATS>
+template <int PPT, bool STATS, int CB>
 __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1)
     k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
                 int n_slots, int per_cam, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1)
     constexpr int NWARP = NT / 32;
     // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits),
     // s2 = (red, green, blue, -)
-    __shared__ float4 s0[COMP_BATCH], s1[COMP_BATCH], s2[COMP_BATCH];
+    __shared__ float4 s0[CB], s1[CB], s2[CB];
     // candidate ranks of one round in order; compacted in place to the ranks of
     // this tile's list (a kept candidate only moves to a lower index)
     __shared__ uint32_t cand[NT * 32];
@@ -239,14 +241,14 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1)
             nkept += wtotal;
             __syncthreads();
         }
-        // 3. composite the kept records, COMP_BATCH at a time. With one warp per
+        // 3. composite the kept records, CB at a time. With one warp per
         // block (and no counting), a record no pixel of the tile can take is not
         // staged at all (order-preserving ballot compaction), so the blend loop
         // visits only records that may contribute; otherwise every record is
         // staged with its per-warp mask.
         constexpr bool COMPACT = NWARP == 1 && !STATS;
-        for (uint32_t j0 = 0; j0 < nkept; j0 += COMP_BATCH) {
-            int nb = (int)min((uint32_t)COMP_BATCH, nkept - j0);
+        for (uint32_t j0 = 0; j0 < nkept; j0 += CB) {
+            int nb = (int)min((uint32_t)CB, nkept - j0);
             int nstaged = 0;
             for (int q0 = 0; q0 < nb; q0 += NT) {
                 const int q = q0 + tid;
@@ -690,16 +692,24 @@ template <int PPT>
 cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots, int per_cam, int n_tiles,
                        const float4 *rec, const uint32_t *vals, const uint2 *rrect,
                        const uint32_t *bitmap, CompParams C, float *rgb, float *depth,
-                       float *final_T, unsigned long long *stats, bool collect,
+                       float *final_T, unsigned long long *stats, bool collect, int comp_batch,
                        const int *status, cudaStream_t s) {
-    if (collect)
-        k_composite<PPT, true><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, per_cam, rec, vals,
-                                                             rrect, bitmap, C, rgb, depth, final_T,
-                                                             stats, status);
-    else
-        k_composite<PPT, false><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, per_cam, rec, vals,
-                                                              rrect, bitmap, C, rgb, depth, final_T,
-                                                              stats, status);
+#define GS_COMP(ST, CBV)                                                                          \
+    k_composite<PPT, ST, CBV><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, per_cam,  \
+                                                            rec, vals, rrect, bitmap, C, rgb,     \
+                                                            depth, final_T, stats, status)
+    if (collect) {
+        GS_COMP(true, COMP_BATCH);
+    } else if (PPT == 8 && comp_batch == 32) {  // the render layout: batch sizes to tune
+        GS_COMP(false, 32);
+    } else if (PPT == 8 && comp_batch == 96) {
+        GS_COMP(false, 96);
+    } else if (PPT == 8 && comp_batch == 128) {
+        GS_COMP(false, 128);
+    } else {
+        GS_COMP(false, COMP_BATCH);
+    }
+#undef GS_COMP
     return cudaGetLastError();
 }
 
@@ -710,7 +720,8 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
-                             int tiles_per_block, const int *status, cudaStream_t s) {
+                             int tiles_per_block, int comp_batch, const int *status,
+                             cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
     if (tiles_per_block == 4) {
         if (collect)
@@ -725,12 +736,12 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
     }
     if (pixels_per_thread == 8)
         return launch_ppt<8>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C,
-                             rgb, depth, final_T, stats, collect, status, s);
+                             rgb, depth, final_T, stats, collect, comp_batch, status, s);
     if (pixels_per_thread == 4)
         return launch_ppt<4>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C,
-                             rgb, depth, final_T, stats, collect, status, s);
+                             rgb, depth, final_T, stats, collect, comp_batch, status, s);
     return launch_ppt<2>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C, rgb,
-                         depth, final_T, stats, collect, status, s);
+                         depth, final_T, stats, collect, comp_batch, status, s);
 }
 
 }  // namespace gsk

@@ -6,7 +6,8 @@
 // of the sort tiles, the segment table of the sort and one SortTile entry per
 // sort tile. When the chunk's
 // survivors exceed the workspace, it records the size needed, raises the status
-// word and plans an empty chunk (every count 0), so the later kernels do
+// word (and the context's sticky word, kept across calls until the host reports
+// it) and plans an empty chunk (every count 0), so the later kernels do
 // nothing and the host can grow the workspace and render again.
 #include "gs_internal.cuh"
 
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(PT)
            long long *__restrict__ segstart, long long *__restrict__ segcount,
            SortTile *__restrict__ stiles, int2 *__restrict__ bintab, int *__restrict__ status,
            long long *__restrict__ need,
-           unsigned long long *__restrict__ survivors) {
+           unsigned long long *__restrict__ survivors,
+           unsigned long long *__restrict__ sticky) {
     __shared__ long long ws64[PT / 32];
     __shared__ int ws32[PT / 32];
     __shared__ long long carry_s, carry_bm;
@@ -61,9 +63,11 @@ __global__ void __launch_bounds__(PT)
     if (tid == 0) {
         overflow = tot > cap_survivors;
         atomicMax((unsigned long long *)need, (unsigned long long)tot);  // largest chunk
-        if (overflow)
+        if (sticky) atomicMax(sticky, (unsigned long long)tot);  // kept across calls
+        if (overflow) {
             *status = GS_STATUS_CAPACITY;
-        else
+            if (sticky) atomicOr(sticky + 1, 1ull);  // reported by a later call or gs_sync
+        } else
             atomicAdd(survivors, (unsigned long long)tot);
         carry_s = carry_bm = 0;
         carry_bb = carry_st = 0;
@@ -153,10 +157,11 @@ __global__ void __launch_bounds__(PT)
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks,
                         long long cap_survivors, int *blkpre, int *sorttiles, long long *segstart,
                         long long *segcount, SortTile *stiles, int2 *bintab, int *status,
-                        long long *need, unsigned long long *survivors, cudaStream_t s) {
+                        long long *need, unsigned long long *survivors,
+                        unsigned long long *sticky, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     k_plan<<<1, PT, 0, s>>>(cams, counts, m, bin_ranks, cap_survivors, blkpre, sorttiles, segstart,
-                            segcount, stiles, bintab, status, need, survivors);
+                            segcount, stiles, bintab, status, need, survivors, sticky);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgs_b300.so")
-ABI_VERSION = 3
+ABI_VERSION = 4
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, \
     GS_ERR_NOT_FOUND = range(7)
@@ -31,7 +31,8 @@ class gs_config(ctypes.Structure):
                 ("max_chunk_cameras", ctypes.c_int32), ("camera_group", ctypes.c_int32),
                 ("count_pairs", ctypes.c_int32), ("time_stages", ctypes.c_int32),
                 ("pixels_per_thread", ctypes.c_int32), ("tiles_per_block", ctypes.c_int32),
-                ("workspace_survivors", ctypes.c_int64), ("reserved", ctypes.c_int32 * 4)]
+                ("workspace_survivors", ctypes.c_int64), ("sync_errors", ctypes.c_int32),
+                ("comp_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class gs_scene_desc(ctypes.Structure):
@@ -60,6 +61,7 @@ SIGNATURES = {
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gs_config_default": (ctypes.c_int, [ctypes.POINTER(gs_config)]),
     "gs_context_create": (ctypes.c_int, [ctypes.POINTER(gs_config), _i32, ctypes.POINTER(_vp)]),
+    "gs_context_set_config": (ctypes.c_int, [_vp, _vp]),
     "gs_context_destroy": (None, [_vp]),
     "gs_last_error": (ctypes.c_char_p, [_vp]),
     "gs_scene_create": (ctypes.c_int, [_vp, ctypes.POINTER(gs_scene_desc),
@@ -79,6 +81,7 @@ SIGNATURES = {
     "gs_graph_check": (ctypes.c_int, [_vp, _vp]),
     "gs_graph_destroy": (None, [_vp]),
     "gs_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gs_stats)]),
+    "gs_sync": (ctypes.c_int, [_vp, _vp]),
     "gs_debug_project": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64,
                                         ctypes.POINTER(_i64), _vp]),
     "gs_debug_tile_lists": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _i64,
@@ -128,6 +131,7 @@ gs_status_string = lib.gs_status_string
 gs_config_default = lib.gs_config_default
 gs_context_create = lib.gs_context_create
 gs_context_destroy = lib.gs_context_destroy
+gs_context_set_config = lib.gs_context_set_config
 gs_last_error = lib.gs_last_error
 gs_scene_create = lib.gs_scene_create
 gs_scene_destroy = lib.gs_scene_destroy
@@ -140,6 +144,7 @@ gs_graph_launch = lib.gs_graph_launch
 gs_graph_check = lib.gs_graph_check
 gs_graph_destroy = lib.gs_graph_destroy
 gs_get_stats = lib.gs_get_stats
+gs_sync = lib.gs_sync
 gs_debug_project = lib.gs_debug_project
 gs_debug_tile_lists = lib.gs_debug_tile_lists
 gs_sort_segments = lib.gs_sort_segments
@@ -200,6 +205,15 @@ class Renderer:
             raise GSError(st, "context creation")
         self.ctx = h
         self.device = device
+        self.overrides = dict(config)
+
+    def set_config(self, **config):
+        """gs_context_set_config: new launch parameters (defaults for those not
+        given), scenes and workspace kept."""
+        cfg = default_config(**config)
+        self._check(gs_context_set_config(self.ctx, ctypes.byref(cfg)))
+        self.cfg = cfg
+        self.overrides = dict(config)
 
     def close(self):
         if self.ctx:
@@ -365,6 +379,11 @@ class Renderer:
                                          intrinsics.data_ptr(), W, H, rgb.data_ptr(),
                                          depth.data_ptr(), _ptr(final_T), _stream(stream)))
         return rgb, depth, final_T
+
+    def sync(self, stream=None) -> None:
+        """gs_sync: wait for the stream and the last render call; raise a
+        pending device-detected error of an earlier call."""
+        self._check(gs_sync(self.ctx, _stream(stream)))
 
     def stats(self) -> dict:
         s = gs_stats()

@@ -61,7 +61,8 @@ def test_graph_replay_matches_eager(torch):
 
 def test_graph_overflow_and_invalidation(torch):
     from paper_2510_15352_b300 import gs
-    r, ids, vm, it, Ws, Hs, P = _setup(torch, gs, workspace_survivors=1000)
+    # sync_errors = 1: the eager render below grows the workspace within the call
+    r, ids, vm, it, Ws, Hs, P = _setup(torch, gs, workspace_survivors=1000, sync_errors=1)
     try:
         rgb = torch.zeros((P, 3), device="cuda")
         dep = torch.zeros((P,), device="cuda")

@@ -441,10 +441,11 @@ def test_host_entry_point_in_parts(torch, gsmod):
 
 
 def test_workspace_overflow_is_retried(torch, gsmod, orc):
-    """A workspace far too small for the batch: the first pass overflows, the
-    call grows it to the exact need and renders again, with the same result."""
+    """A workspace far too small for the batch, with sync_errors = 1: the first
+    pass overflows, the call grows it to the exact need and renders again, with
+    the same result."""
     scene, vm, it, W, H = small_workload()
-    r = gsmod.Renderer(device=0, workspace_survivors=10)
+    r = gsmod.Renderer(device=0, workspace_survivors=10, sync_errors=1)
     try:
         sid = r.add_scene(scene)
         rgb, depth, T = render_np(torch, r, sid, vm, it, W, H)
