@@ -347,7 +347,8 @@ def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, g
     rgb = torch.empty((P, 3), dtype=torch.float32, device="cuda")
     depth = torch.empty((P,), dtype=torch.float32, device="cuda")
     kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
-              tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch)
+              tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch,
+              persistent=args.persistent)
     counter = gs.Renderer(device=local, count_pairs=1, **kw)
     ids_c = np.array([counter.add_scene(sc) for sc in scenes], dtype=np.int32)[which]
     counter.render_v(ids_c, vm_d, it_d, Ws, Hs, rgb, depth)
@@ -406,6 +407,7 @@ def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, g
                    "frames_640x480_equivalent": eq_frames, "chunk_cameras": args.chunk,
                    "pixels_per_thread": args.ppt, "tiles_per_block": args.tpb,
                    "comp_batch": args.comp_batch, "camera_group": args.group,
+                   "persistent": args.persistent,
                    "cuda_graph": bool(graph),
                    "storage": "f32" if "dequantised" not in scenes[0] else "f16/bf16"},
         "roofline": {"kernel": "k_composite", "bound": "alu", "achieved": achieved,
@@ -431,7 +433,8 @@ def half_leg(args, gs, torch, synth, scenes, which, vm, local, stream, fp32_tflo
     depth = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
     R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
                     pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
-                    camera_group=args.group, comp_batch=args.comp_batch)
+                    camera_group=args.group, comp_batch=args.comp_batch,
+              persistent=args.persistent)
     try:
         nbytes = 0
         sids = []
@@ -509,7 +512,8 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
     it_d = torch.tensor([[480.0, 480.0, W / 2.0, H / 2.0]], dtype=torch.float32,
                         device="cuda").expand(n, 4).contiguous()
     R = gs.Renderer(device=local, max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
-                    tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch)
+                    tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch,
+              persistent=args.persistent)
     sids = [R.add_scene(sc) for sc in scenes]
     ids = np.array(sids, dtype=np.int32)[which]
     up = gs.Upsampler(device=local)
@@ -634,7 +638,8 @@ def run_b300(args):
 
     # algorithmic work of the compositing kernel on these inputs (counting run)
     kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
-              tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch)
+              tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch,
+              persistent=args.persistent)
     counter = gs.Renderer(device=local, count_pairs=1, **kw)
     sid_c = counter.add_scene(scene)
     counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
@@ -772,6 +777,7 @@ def run_b300(args):
         targs.ppt, targs.tpb = cfg["pixels_per_thread"], cfg["tiles_per_block"]
         targs.comp_batch, targs.group = cfg["comp_batch"], cfg["camera_group"]
         targs.chunk = cfg["max_chunk_cameras"]
+        targs.persistent = cfg["persistent"]
         leg = batched_leg(targs, gs, torch, scenes, which, bvm, bit, Ws, Hs, local, stream, True,
                           fp32, clocks=ClockSampler(local))
         default_ms = [t[0] for t in tuned["timings"] if t[1] == {**autotune.DEFAULTS}]
@@ -809,6 +815,8 @@ def main():
                     help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
     ap.add_argument("--comp-batch", type=int, default=64,
                     help="records staged per compositing batch (32|64|96|128, with --ppt 8)")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="1: binning + compositing as one persistent launch (with --ppt 8)")
     ap.add_argument("--precision", choices=["f32", "half"], default="f32",
                     help="headline scene storage (half: FP16 geometry, BF16 appearance)")
     ap.add_argument("--e2e-steps", type=int, default=2)

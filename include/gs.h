@@ -82,7 +82,13 @@ typedef struct gs_config {
                               status and renders such chunks again at once (0) */
     int32_t comp_batch;    /* records staged per compositing batch with 8 pixels per
                               thread: 32, 64, 96 or 128 (64; 0 = 64) */
-    int32_t reserved[2];
+    int32_t persistent;    /* 1: binning and compositing of a chunk run as one persistent
+                              launch pulling (camera, stage) work items from a device
+                              queue (8 pixels per thread, one tile per block, no pair
+                              counting, images of at most 128 64x64-pixel super-tiles;
+                              other calls use separate launches). Its stage time is
+                              reported as compositing. (0) */
+    int32_t reserved[1];
 } gs_config;
 
 /* A scene: n Gaussians stored as structure of arrays.
@@ -283,6 +289,18 @@ gs_status gs_get_stats(gs_context *ctx, gs_stats *out);
  * gs_get_stats does; GS_OK if there is none). The paper has no counterpart:
  * it is the completion point of the asynchronous render calls. */
 gs_status gs_sync(gs_context *ctx, void *stream);
+
+/* Test of the persistent launch's bounded waits (see gs_config.persistent; the
+ * paper has no counterpart): renders one camera (arguments as gs_render_batch,
+ * viewmat / intrinsics in DEVICE memory) through the persistent binning +
+ * compositing launch with the camera's tiles made to wait for one binning item
+ * more than exists, and a bound of 4,096 polls. The waits give up, the tiles
+ * are left unwritten, and the call returns GS_ERR_TIMEOUT after waiting for
+ * `stream`; the context stays usable (the next render is complete). Any other
+ * status means the bounded wait did not behave as documented. */
+gs_status gs_render_timeout_probe(gs_context *ctx, int32_t scene_id, const float *viewmat,
+                                  const float *intrinsics, int32_t width, int32_t height,
+                                  float *rgb, float *depth, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Inspection entry points (used by the test suite). Each runs the hot-path

@@ -11,6 +11,9 @@ once), over:
                       2x2 quad of tiles sharing the list scan and record staging;
   comp_batch          32, 64, 96 or 128 -- Gaussian records staged per
                       compositing batch (8 pixels per thread, one tile per block);
+  persistent          0 or 1 -- binning and compositing as separate launches or
+                      as one persistent launch pulling work items from a device
+                      queue (8 pixels per thread, one tile per block);
   camera_group        cameras of one scene that share one Gaussian load in the
                       projection kernels (Gaussian batch per projection block);
   max_chunk_cameras   cameras per chunk of the render pipeline.
@@ -34,13 +37,14 @@ DEFAULT_SPACE = {
     "pixels_per_thread": (2, 4, 8),
     "tiles_per_block": (1, 4),
     "comp_batch": (32, 64, 96, 128),
+    "persistent": (0, 1),
     "camera_group": (32, 64),
     "max_chunk_cameras": (128, 256, 512),
 }
 # the stages of the search: compositing knobs first, then the pipeline knobs
-STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch"),
+STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch", "persistent"),
           ("camera_group", "max_chunk_cameras"))
-DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 64,
+DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 64, "persistent": 0,
             "camera_group": 64, "max_chunk_cameras": 512}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
@@ -80,12 +84,12 @@ def store_cache(entry_key: str, entry: dict, path: str = DEFAULT_CACHE) -> None:
 
 def _distinct(c: dict) -> bool:
     """False for combinations the library runs as another one: quads need 8
-    pixels per thread, and the batch is a knob of the 8-pixel, one-tile layout
-    only (others stage 64)."""
+    pixels per thread, and the batch and the persistent launch are knobs of the
+    8-pixel, one-tile layout only (others stage 64 in separate launches)."""
     ppt, tpb = c.get("pixels_per_thread", 8), c.get("tiles_per_block", 1)
     if tpb == 4 and ppt != 8:
         return False
-    if c.get("comp_batch", 64) != 64 and (ppt != 8 or tpb != 1):
+    if (c.get("comp_batch", 64) != 64 or c.get("persistent", 0)) and (ppt != 8 or tpb != 1):
         return False
     return True
 

@@ -91,6 +91,10 @@ struct gs_context {
     int tab_next = 0;
     cudaEvent_t done_ev = nullptr;  // end of the last render call's work (orders streams)
     bool done_valid = false;
+    DevBuf pq;                    // persistent launch: queue head + per-camera binning counts
+    int pgrid[4] = {0, 0, 0, 0};  // its resident grid, per compositing batch (32/64/96/128)
+    int probe_extra = 0;          // timeout probe: camera 0 waits for items that never come
+    int probe_limit = 0;          // timeout probe: polls before giving up (0: the default)
 };
 
 struct gs_graph {
@@ -200,6 +204,7 @@ struct ChunkPlan {
     int sort_grid, bin_grid;
     int bin_ranks;        // depth ranks per binning block (from max_sup)
     int max_deg;          // largest SH degree of the chunk's scenes
+    bool persistent;      // binning + compositing in one persistent launch
 };
 
 struct Plan {
@@ -273,7 +278,9 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
         P.tilepre[tp + ch.m] = ch.tiles_total;
         tp += ch.m + 1;
         ch.sort_grid = (int)std::max<long long>(1, std::min<long long>(sort_up, 32 * 1184));
-        ch.bin_ranks = bin_ranks_for(ch.max_sup);
+        ch.persistent = cfg.persistent && cfg.pixels_per_thread == 8 && cfg.tiles_per_block == 1 &&
+                        !cfg.count_pairs && ch.max_sup <= persistent_max_super();
+        ch.bin_ranks = ch.persistent ? BIN_RANKS_SMALL : bin_ranks_for(ch.max_sup);
         if (ch.bin_ranks == BIN_RANKS) bin_up = (bin_up + 3) / 4;
         ch.bin_grid = (int)std::max<long long>(1, std::min<long long>(bin_up, 32 * 1184));
         P.max_mask_words = std::max(P.max_mask_words, ch.mask_words);
@@ -298,7 +305,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
                       &ctx->tvals,    &ctx->bitmap,   &ctx->sorthist,  &ctx->sorttab,
                       &ctx->bintab,   &ctx->wide,     &ctx->blkpre,    &ctx->sorttiles,
                       &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status,
-                      &ctx->oidx,     &ctx->ties,     &ctx->nruns};
+                      &ctx->oidx,     &ctx->ties,     &ctx->nruns,    &ctx->pq};
     void *before[sizeof(held) / sizeof(held[0])];
     for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->p;
     CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
@@ -315,6 +322,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->oidx, Sx * 4));
     CKS(grow(ctx, ctx->ties, (Sx / 33 + 2) * tie_run_bytes()));
     CKS(grow(ctx, ctx->nruns, (P.chunks.size() + 1) * sizeof(int)));
+    CKS(grow(ctx, ctx->pq, (size_t)(m + 2) * sizeof(int)));
     // bounds implied by S: bitmap words <= max_sup * (S/32 + m), sort tiles <= S/2048 + m
     CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
     CKS(grow(ctx, ctx->sorthist, (Sx / SORT_TILE_KEYS + m + 1) * 512 * 4));
@@ -407,17 +415,39 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                              (const int *)ctx->sorttiles.p + ch.m, ch.sort_grid, ctx->ties.p,
                              (long long)(ctx->ties.cap / tie_run_bytes()), nruns, st));
         if (E) CKC(cudaEventRecord(E[2], st));
-        CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
-                       ch.bin_grid, ch.max_sup,
-                       ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->tvals.p,
-                       (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
+        const bool persist = ch.persistent && a.upto == UPTO_ALL;
+        if (!persist)
+            CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
+                           ch.bin_grid, ch.max_sup,
+                           ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->tvals.p,
+                           (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
         if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;
-        CKC(launch_composite(cams, tilepre, ch.m, ch.per_cam, ch.tiles_total, recs,
-                             (const uint32_t *)ctx->tvals.p, (const uint2 *)ctx->rrect.p,
-                             (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
-                             cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,
-                             cfg.comp_batch, status, st));
+        if (persist) {
+            // binning and compositing in one persistent launch (its time counts as
+            // compositing): queue head and per-camera binning counts start at zero
+            const int ci = cfg.comp_batch == 32 ? 0 : cfg.comp_batch == 96 ? 2
+                         : cfg.comp_batch == 128 ? 3 : 1;
+            if (ctx->pgrid[ci] <= 0) ctx->pgrid[ci] = persistent_grid(cfg.comp_batch);
+            if (ctx->pgrid[ci] <= 0) return fail(ctx, GS_ERR_CUDA, "persistent grid size query failed");
+            int *pq = (int *)ctx->pq.p;
+            CKC(cudaMemsetAsync(pq, 0, (size_t)(ch.m + 1) * sizeof(int), st));
+            CKC(launch_bin_composite(cams, tilepre, ch.m, ch.per_cam, ch.tiles_total, recs,
+                                     (const uint32_t *)ctx->tvals.p, (uint2 *)ctx->rrect.p, C,
+                                     a.rgb, a.depth, a.T, cfg.comp_batch, status,
+                                     (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p,
+                                     (const uint2 *)ctx->srect.p, (uint32_t *)ctx->bitmap.p,
+                                     stats + 2, pq, pq + 1,
+                                     ctx->probe_limit > 0 ? ctx->probe_limit : (1 << 18),
+                                     ctx->probe_extra, (unsigned long long *)ctx->sticky.p,
+                                     ctx->pgrid[ci], st));
+        } else {
+            CKC(launch_composite(cams, tilepre, ch.m, ch.per_cam, ch.tiles_total, recs,
+                                 (const uint32_t *)ctx->tvals.p, (const uint2 *)ctx->rrect.p,
+                                 (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
+                                 cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,
+                                 cfg.comp_batch, status, st));
+        }
         if (E) CKC(cudaEventRecord(E[4], st));
     }
     return GS_OK;
@@ -470,6 +500,14 @@ gs_status poll_sticky(gs_context *ctx, bool wait, cudaStream_t st) {
     const unsigned long long *h = (const unsigned long long *)ctx->sticky_h.p;
     const long long need = (long long)h[0];
     ctx->last_chunk_survivors = std::max(ctx->last_chunk_survivors, need);
+    if (h[1] & 2ull) {  // a persistent launch's bounded wait gave up
+        CKC(cudaMemsetAsync((unsigned long long *)ctx->sticky.p + 1, 0, 8, st));
+        if (h[1] & 1ull)
+            ctx->cap_survivors = std::max(ctx->cap_survivors, need + need / 8 + 1024);
+        return fail(ctx, GS_ERR_TIMEOUT,
+                    "a render call's persistent binning + compositing launch gave up waiting "
+                    "for a camera's binning: some of its tiles are not written");
+    }
     if (h[1]) {
         ctx->cap_survivors = std::max(ctx->cap_survivors, need + need / 8 + 1024);
         CKC(cudaMemsetAsync((unsigned long long *)ctx->sticky.p + 1, 0, 8, st));
@@ -545,6 +583,21 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
         ctx->cap_survivors = need + need / 8 + 1024;  // exact need plus headroom; render again
         // re-rendered here: not an error for a later call
         CKC(cudaMemsetAsync((unsigned long long *)ctx->sticky.p + 1, 0, 8, a.st));
+    }
+    if (sync) {  // this call's persistent waits: read the sticky word now
+        CKS(grow_pinned(ctx, ctx->pin[1], 64));
+        unsigned long long *hs = (unsigned long long *)ctx->pin[1].p;
+        CKC(cudaMemcpyAsync(hs, ctx->sticky.p, 2 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, a.st));
+        CKC(cudaStreamSynchronize(a.st));
+        if (hs[1] & 2ull) {
+            CKC(cudaMemsetAsync((unsigned long long *)ctx->sticky.p + 1, 0, 8, a.st));
+            CKC(cudaEventRecord(ctx->done_ev, a.st));
+            ctx->done_valid = true;
+            return fail(ctx, GS_ERR_TIMEOUT,
+                        "the persistent binning + compositing launch gave up waiting for a "
+                        "camera's binning: some of its tiles are not written");
+        }
     }
     CKC(cudaEventRecord(ctx->done_ev, a.st));
     ctx->done_valid = true;
@@ -631,7 +684,7 @@ static bool check_config(gs_config &c) {
         (c.tiles_per_block != 0 && c.tiles_per_block != 1 && c.tiles_per_block != 4) ||
         (c.comp_batch != 0 && c.comp_batch != 32 && c.comp_batch != 64 && c.comp_batch != 96 &&
          c.comp_batch != 128) ||
-        (c.sync_errors != 0 && c.sync_errors != 1))
+        (c.sync_errors != 0 && c.sync_errors != 1) || (c.persistent != 0 && c.persistent != 1))
         return false;
     // 0 (a zero-initialised config) means 1; quads use 8 pixels per thread
     if (c.tiles_per_block == 0 || c.pixels_per_thread != 8) c.tiles_per_block = 1;
@@ -1003,6 +1056,15 @@ gs_status gs_graph_check(gs_graph *g, void *stream) {
     std::vector<char> h(sizeof(long long) + g->n_chunks * sizeof(int));
     CKC(cudaMemcpy(h.data(), ctx->status.p, h.size(), cudaMemcpyDeviceToHost));
     const int *st = (const int *)(h.data() + sizeof(long long));
+    if (ctx->sticky.p) {
+        unsigned long long sk[2];
+        CKC(cudaMemcpy(sk, ctx->sticky.p, sizeof(sk), cudaMemcpyDeviceToHost));
+        if (sk[1] & 2ull) {
+            CKC(cudaMemset((unsigned long long *)ctx->sticky.p + 1, 0, sizeof(unsigned long long)));
+            return fail(ctx, GS_ERR_TIMEOUT,
+                        "a graph launch's persistent binning + compositing gave up waiting");
+        }
+    }
     for (int k = 0; k < g->n_chunks; ++k)
         if (st[k]) {
             // reported here, not again by a later call
@@ -1152,6 +1214,29 @@ gs_status gs_sync(gs_context *ctx, void *stream) {
     CKC(cudaStreamSynchronize((cudaStream_t)stream));
     if (ctx->done_valid) CKC(cudaEventSynchronize(ctx->done_ev));
     return poll_sticky(ctx, true, (cudaStream_t)stream);
+}
+
+gs_status gs_render_timeout_probe(gs_context *ctx, int32_t scene_id, const float *viewmat,
+                                  const float *intrinsics, int32_t width, int32_t height,
+                                  float *rgb, float *depth, void *stream) {
+    CKS(validate(ctx, 1, &scene_id, viewmat, intrinsics, width, height, rgb, depth, true));
+    ctx->err.clear();
+    CKC(cudaSetDevice(ctx->device));
+    const gs_config saved = ctx->cfg;
+    ctx->cfg.persistent = 1;
+    ctx->cfg.pixels_per_thread = 8;
+    ctx->cfg.tiles_per_block = 1;
+    ctx->cfg.count_pairs = 0;
+    ctx->probe_extra = 1;     // camera 0's tiles wait for a binning item that never comes
+    ctx->probe_limit = 4096;  // and give up after 4,096 polls
+    RenderArgs a{1,   &scene_id, viewmat, intrinsics, width,  height,
+                 nullptr, nullptr, nullptr, rgb, depth, nullptr, (cudaStream_t)stream, UPTO_ALL};
+    a.force_sync = true;
+    const gs_status r = render_impl(ctx, a);
+    ctx->cfg = saved;
+    ctx->probe_extra = 0;
+    ctx->probe_limit = 0;
+    return r;
 }
 
 gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {

@@ -207,6 +207,22 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *b
                        uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
                        cudaStream_t s);
 
+// Binning and compositing of a chunk in one persistent launch (k_composite.cu):
+// 8 pixels per thread, binning items of BIN_RANKS_SMALL ranks (the plan must
+// use that), cameras of at most persistent_max_super() super-tiles. head and
+// bin_done ([n_slots] ints) must be zero at launch; a wait that gives up after
+// wait_limit polls sets sticky[1] |= 2. grid = persistent_grid(comp_batch).
+int persistent_max_super();
+int persistent_grid(int comp_batch);
+cudaError_t launch_bin_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
+                                 int per_cam, int n_tiles, const float4 *rec, const uint32_t *vals,
+                                 uint2 *rrect, CompParams C, float *rgb, float *depth,
+                                 float *final_T, int comp_batch, const int *status,
+                                 const int *blk_prefix, const int2 *bintab, const uint2 *srect,
+                                 uint32_t *bitmap, unsigned long long *n_isect, int *head,
+                                 int *bin_done, int wait_limit, int extra_need,
+                                 unsigned long long *sticky, int grid, cudaStream_t s);
+
 // tiles_per_block 1: one block per tile, pixels_per_thread 2, 4 or 8 (blocks of
 // 128, 64 or 32 threads); tiles_per_block 4: one block of 4 warps per 2 x 2 quad
 // of tiles (8 pixels per thread). tile_prefix / n_tiles count the blocks: tiles

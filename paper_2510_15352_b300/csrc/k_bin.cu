@@ -19,7 +19,7 @@
 // odd row pitch (P >= number of super-tiles): the lanes of a warp set bits of
 // one word in the super-tiles their rects meet, which then fall in different
 // banks, and the write-out reads 32 words of one super-tile from 32 banks.
-#include "gs_internal.cuh"
+#include "bin_core.cuh"
 
 namespace gsk {
 
@@ -32,60 +32,12 @@ __global__ void __launch_bounds__(BIN_THREADS)
           const uint2 *__restrict__ srect, const uint32_t *__restrict__ vals,
           uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
           unsigned long long *__restrict__ n_isect) {
-    constexpr int BIN_RANKS = RPT * BIN_THREADS, BIN_WORDS = BIN_RANKS / 32;
-    extern __shared__ uint32_t sbm[];  // [BIN_WORDS][P]
+    extern __shared__ uint32_t sbm[];  // [ranks / 32][P]
     const int nblk = blk_prefix[n_slots];
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int2 bt = bintab[blk];  // (camera, first rank) of this binning block
-    const CamInfo ci = cams[bt.x];
-    const int r0 = bt.y;
-    const int SX = (ci.TX + STILE - 1) / STILE, SY = (ci.TY + STILE - 1) / STILE;
-    const int nsup = SX * SY;
-    const int P = nsup | 1;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < P * BIN_WORDS; i += BIN_THREADS) sbm[i] = 0u;
-    // rank r0 + j * BIN_THREADS + tid: word j * (BIN_THREADS / 32) + warp, bit lane
-    uint32_t slot[RPT];
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        const int r = r0 + j * BIN_THREADS + tid;
-        slot[j] = r < ci.count ? vals[ci.seg_off + r] : 0u;
-    }
-    uint2 d[RPT];
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        const int r = r0 + j * BIN_THREADS + tid;
-        d[j] = r < ci.count ? srect[ci.seg_off + slot[j]] : make_uint2(1u, 1u);  // empty rect
-    }
-    __syncthreads();  // sbm cleared
-    unsigned long long area = 0;
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        const int r = r0 + j * BIN_THREADS + tid;
-        if (r >= ci.count) continue;
-        rrect[ci.seg_off + r] = d[j];
-        const int x0 = (int)(d[j].x & 0xffffu), x1 = (int)(d[j].x >> 16);
-        const int y0 = (int)(d[j].y & 0xffffu), y1 = (int)(d[j].y >> 16);
-        if (x1 >= x0 && y1 >= y0) {
-            area += (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
-            const uint32_t bit = 1u << lane;
-            const int word = j * (BIN_THREADS / 32) + warp;
-            for (int sy = y0 / STILE; sy <= y1 / STILE; ++sy)
-                for (int sx = x0 / STILE; sx <= x1 / STILE; ++sx)
-                    atomicOr(&sbm[word * P + sy * SX + sx], bit);
-        }
-    }
-    __syncthreads();
-    const int w0 = r0 >> 5;
-    const int nwb = min(BIN_WORDS, ci.nw - w0);
-    for (int i = tid; i < nsup * BIN_WORDS; i += BIN_THREADS) {
-        const int st = i / BIN_WORDS, k = i - st * BIN_WORDS;
-        if (k < nwb) bitmap[ci.bm_off + (long long)st * ci.nw + w0 + k] = sbm[k * P + st];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) area += __shfl_down_sync(0xffffffffu, area, o);
-    if (lane == 0 && area) atomicAdd(n_isect, area);
-    __syncthreads();  // sbm is cleared for the next block of ranks
+        const int2 bt = bintab[blk];  // (camera, first rank) of this binning block
+        const CamInfo ci = cams[bt.x];
+        bin_item<BIN_THREADS, RPT>(sbm, ci, bt.y, srect, vals, rrect, bitmap, n_isect);
     }
 }
 

@@ -35,11 +35,15 @@
 // taken two at a time: both quadratics, then both votes, then the blends, so
 // the two records' latencies overlap. No tensor cores: this is not a dense
 // contraction.
+#include "bin_core.cuh"
 #include "gs_internal.cuh"
 
 namespace gsk {
 
 namespace {
+
+constexpr int PB_RPT = 8;     // depth ranks per lane of a persistent binning item (256)
+constexpr int PB_MAXP = 129;  // super-tile row pitch its shared memory holds
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -107,33 +111,57 @@ __device__ __forceinline__ int block_camera(const int *__restrict__ prefix, int 
 // registers and 17 blocks (21.74 ms). Earlier layouts, per 1,024 cameras: 16
 // blocks 29.0 ms, 18 blocks 28.2 ms, 20 blocks 27.2 ms, 22 blocks 28.6 ms, 24
 // blocks 31.3 ms (the last two spill).
-template <int PPT, bool STATS, int CB>
-__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1)
-    k_composite(const CamInfo *__restrict__ cams, const int *__restrict__ tile_prefix,
-                int n_slots, int per_cam, const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
-                const uint2 *__restrict__ rrect, const uint32_t *__restrict__ bitmap,
-                CompParams P, float *__restrict__ rgb, float *__restrict__ depth,
-                float *__restrict__ finalT, unsigned long long *__restrict__ stats,
-                const int *__restrict__ status) {
-    if (status && *status) return;  // the chunk did not fit the workspace: nothing written
-    constexpr int NT = 256 / PPT;    // threads per block
-    constexpr int CPR = 16 / PPT;    // threads per pixel row
-    constexpr int NWARP = NT / 32;
+// Shared memory of one compositing block (NT = 256 / PPT threads).
+template <int PPT, int CB>
+struct CompSmem {
     // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits),
     // s2 = (red, green, blue, -)
-    __shared__ float4 s0[CB], s1[CB], s2[CB];
+    float4 s0[CB], s1[CB], s2[CB];
     // candidate ranks of one round in order; compacted in place to the ranks of
     // this tile's list (a kept candidate only moves to a lower index)
-    __shared__ uint32_t cand[NT * 32];
-    __shared__ uint32_t wsum[NWARP];
+    uint32_t cand[(256 / PPT) * 32];
+    uint32_t wsum[(256 / PPT) / 32];
     // per warp: the pixel-centre rectangle of its live pixels (x0, x1, y0, y1);
     // the staging skip test bounds the quadratic over it instead of over the
     // warp's rows (stopped pixels pass no alpha test), empty when x0 > x1
-    __shared__ float4 wl[NWARP];
+    float4 wl[(256 / PPT) / 32];
+};
 
-    int first;
-    const CamInfo ci = cams[block_camera(tile_prefix, n_slots, per_cam, (int)blockIdx.x, first)];
-    const int t = (int)blockIdx.x - first;
+// One tile t of camera ci, composited by the whole block (see the file header).
+// Arguments of a compositing launch (read from the kernel's parameter space).
+struct CompArgs {
+    const CamInfo *cams;
+    const int *tile_prefix;
+    int n_slots, per_cam;
+    const float4 *rec;
+    const uint32_t *vals;
+    const uint2 *rrect;
+    const uint32_t *bitmap;
+    CompParams P;
+    float *rgb, *depth, *finalT;
+    unsigned long long *stats;
+    const int *status;
+};
+
+// L2ONLY: the bitmap words and rank-ordered rects are read through L2 only
+// (the persistent kernel writes them during the same launch, on other SMs).
+template <int PPT, bool STATS, int CB, bool L2ONLY = false>
+__device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const CompArgs &A) {
+    const float4 *__restrict__ rec = A.rec;
+    const uint32_t *__restrict__ vals = A.vals;
+    const uint2 *__restrict__ rrect = A.rrect;
+    const uint32_t *__restrict__ bitmap = A.bitmap;
+    const CompParams &P = A.P;
+    float *__restrict__ rgb = A.rgb;
+    float *__restrict__ depth = A.depth;
+    float *__restrict__ finalT = A.finalT;
+    unsigned long long *__restrict__ stats = A.stats;
+    constexpr int NT = 256 / PPT;    // threads per block
+    constexpr int CPR = 16 / PPT;    // threads per pixel row
+    constexpr int NWARP = NT / 32;
+    __shared__ CompSmem<PPT, CB> sm;  // one per block of every kernel that composites
+    float4 *s0 = sm.s0, *s1 = sm.s1, *s2 = sm.s2, *wl = sm.wl;
+    uint32_t *cand = sm.cand, *wsum = sm.wsum;
     const int tx = t % ci.TX, ty = t / ci.TX;
     const int SX = (ci.TX + STILE - 1) / STILE;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -191,7 +219,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1)
         if (!__syncthreads_or(live)) break;
         // 1. candidates: set bits of NT words of the super-tile row, in rank order
         const int w = wb + tid;
-        uint32_t word = w < ci.nw ? bm[w] : 0u;
+        uint32_t word = w < ci.nw ? (L2ONLY ? __ldcg(bm + w) : bm[w]) : 0u;
         uint32_t c = __popc(word);
         uint32_t incl = c;
 #pragma unroll
@@ -223,7 +251,7 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1)
             uint32_t rk = 0;
             if (q < total) {
                 rk = cand[q];
-                const uint2 rr = crr[rk];
+                const uint2 rr = L2ONLY ? __ldcg(crr + rk) : crr[rk];
                 keep = tx >= (int)(rr.x & 0xffffu) && tx <= (int)(rr.x >> 16) &&
                        ty >= (int)(rr.y & 0xffffu) && ty <= (int)(rr.y >> 16);
             }
@@ -445,6 +473,90 @@ finished:
             atomicAdd(&stats[3], wi);  // per warp: the same count on every lane
             atomicAdd(&stats[4], wbox);
             atomicAdd(&stats[5], wbl);
+        }
+    }
+}
+
+
+template <int PPT, bool STATS, int CB>
+__global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1) k_composite(const CompArgs A) {
+    if (A.status && *A.status) return;  // the chunk did not fit the workspace: nothing written
+    int first;
+    const CamInfo ci = A.cams[block_camera(A.tile_prefix, A.n_slots, A.per_cam, (int)blockIdx.x, first)];
+    composite_tile<PPT, STATS, CB>(ci, (int)blockIdx.x - first, A);
+}
+
+// Binning and compositing of a chunk in one persistent launch (8 pixels per
+// thread, one warp per block, as many blocks as are resident). A device queue
+// (an atomic counter) hands out work items in order: first the binning items
+// (256 depth ranks of one camera each, bin_item at warp granularity), then one
+// compositing item per (camera, tile) across all cameras and scenes of the
+// chunk. A tile may be composited only when every binning item of its camera
+// is done: its warp polls the camera's counter (written after a fence by each
+// binning item) with a bounded number of polls, and when the bound is reached
+// it raises the timeout bit of the context's sticky status word (reported as
+// GS_ERR_TIMEOUT by the host) and leaves the tile unwritten instead of
+// waiting on. Binning items are handed out before any tile and never wait, so
+// in a correct launch every wait ends; the bound only guards the device.
+struct BinCompQueue {
+    const int *blk_prefix;        // [n_slots + 1] binning items per camera, prefix
+    const int2 *bintab;           // (camera, first rank) of every binning item
+    const uint2 *srect;
+    uint2 *rrect;
+    uint32_t *bitmap;
+    unsigned long long *n_isect;
+    int *head;                    // next item (zero at launch)
+    int *bin_done;                // [n_slots] binning items completed per camera (zero)
+    int n_tiles;                  // compositing items (tiles of the chunk)
+    int wait_limit;               // polls of a camera's counter before giving up
+    int extra_need;               // timeout probe: camera 0 waits for this many more items
+    unsigned long long *sticky;   // [1] |= 2 when a wait gives up
+};
+
+template <int CB>
+__global__ void __launch_bounds__(32, 16) k_bin_composite(const CompArgs A, const BinCompQueue Q) {
+    if (A.status && *A.status) return;  // the chunk did not fit the workspace: nothing written
+    __shared__ uint32_t sbm[(32 * PB_RPT / 32) * PB_MAXP];
+    const int lane = threadIdx.x;
+    const int nbin = Q.blk_prefix[A.n_slots];
+    const int total = nbin + Q.n_tiles;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(Q.head, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        if (item < nbin) {
+            const int2 bt = Q.bintab[item];
+            const CamInfo ci = A.cams[bt.x];
+            bin_item<32, PB_RPT>(sbm, ci, bt.y, Q.srect, A.vals, Q.rrect, Q.bitmap, Q.n_isect);
+            __threadfence();  // this item's rects and words before its count
+            if (lane == 0) atomicAdd(Q.bin_done + bt.x, 1);
+        } else {
+            const int t = item - nbin;
+            int first;
+            const int c = block_camera(A.tile_prefix, A.n_slots, A.per_cam, t, first);
+            const int need = Q.blk_prefix[c + 1] - Q.blk_prefix[c] + (c == 0 ? Q.extra_need : 0);
+            int ok = 1;
+            if (lane == 0) {
+                const volatile int *done = Q.bin_done + c;
+                const volatile unsigned long long *flag = Q.sticky + 1;
+                int polls = 0;
+                while (*done < need) {
+                    // give up after wait_limit polls, or at once when another wait has
+                    // given up (so no launch ever holds more than one bounded wait per warp)
+                    if (++polls > Q.wait_limit || (*flag & 2ull)) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (!ok) atomicOr(Q.sticky + 1, 2ull);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) continue;  // the tile stays unwritten; the host reports the timeout
+            __threadfence();
+            const CamInfo ci = A.cams[c];
+            composite_tile<8, false, CB, true>(ci, t - first, A);
         }
     }
 }
@@ -694,10 +806,9 @@ cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots,
                        const uint32_t *bitmap, CompParams C, float *rgb, float *depth,
                        float *final_T, unsigned long long *stats, bool collect, int comp_batch,
                        const int *status, cudaStream_t s) {
-#define GS_COMP(ST, CBV)                                                                          \
-    k_composite<PPT, ST, CBV><<<n_tiles, 256 / PPT, 0, s>>>(cams, tile_prefix, n_slots, per_cam,  \
-                                                            rec, vals, rrect, bitmap, C, rgb,     \
-                                                            depth, final_T, stats, status)
+    const CompArgs A{cams, tile_prefix, n_slots, per_cam, rec, vals, rrect, bitmap,
+                     C, rgb, depth, final_T, stats, status};
+#define GS_COMP(ST, CBV) k_composite<PPT, ST, CBV><<<n_tiles, 256 / PPT, 0, s>>>(A)
     if (collect) {
         GS_COMP(true, COMP_BATCH);
     } else if (PPT == 8 && comp_batch == 32) {  // the render layout: batch sizes to tune
@@ -714,6 +825,45 @@ cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots,
 }
 
 }  // namespace
+
+int persistent_max_super() { return PB_MAXP - 1; }
+
+cudaError_t launch_bin_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
+                                 int per_cam, int n_tiles, const float4 *rec, const uint32_t *vals,
+                                 uint2 *rrect, CompParams C, float *rgb, float *depth,
+                                 float *final_T, int comp_batch, const int *status,
+                                 const int *blk_prefix, const int2 *bintab, const uint2 *srect,
+                                 uint32_t *bitmap, unsigned long long *n_isect, int *head,
+                                 int *bin_done, int wait_limit, int extra_need,
+                                 unsigned long long *sticky, int grid, cudaStream_t s) {
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    const CompArgs A{cams, tile_prefix, n_slots, per_cam, rec, vals, rrect, bitmap,
+                     C, rgb, depth, final_T, nullptr, status};
+    const BinCompQueue Q{blk_prefix, bintab, srect, rrect, bitmap, n_isect, head, bin_done,
+                         n_tiles, wait_limit, extra_need, sticky};
+    switch (comp_batch) {
+        case 32: k_bin_composite<32><<<grid, 32, 0, s>>>(A, Q); break;
+        case 96: k_bin_composite<96><<<grid, 32, 0, s>>>(A, Q); break;
+        case 128: k_bin_composite<128><<<grid, 32, 0, s>>>(A, Q); break;
+        default: k_bin_composite<COMP_BATCH><<<grid, 32, 0, s>>>(A, Q); break;
+    }
+    return cudaGetLastError();
+}
+
+int persistent_grid(int comp_batch) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cudaError_t e;
+    switch (comp_batch) {
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_composite<32>, 32, 0); break;
+        case 96: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_composite<96>, 32, 0); break;
+        case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_composite<128>, 32, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bin_composite<COMP_BATCH>, 32, 0); break;
+    }
+    if (e != cudaSuccess || per < 1) return 0;
+    return sms * per;
+}
 
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
                              int per_cam, int n_tiles, const float4 *rec, const uint32_t *vals,

@@ -32,7 +32,8 @@ class gs_config(ctypes.Structure):
                 ("count_pairs", ctypes.c_int32), ("time_stages", ctypes.c_int32),
                 ("pixels_per_thread", ctypes.c_int32), ("tiles_per_block", ctypes.c_int32),
                 ("workspace_survivors", ctypes.c_int64), ("sync_errors", ctypes.c_int32),
-                ("comp_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("comp_batch", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class gs_scene_desc(ctypes.Structure):
@@ -82,6 +83,7 @@ SIGNATURES = {
     "gs_graph_destroy": (None, [_vp]),
     "gs_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gs_stats)]),
     "gs_sync": (ctypes.c_int, [_vp, _vp]),
+    "gs_render_timeout_probe": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp]),
     "gs_debug_project": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64,
                                         ctypes.POINTER(_i64), _vp]),
     "gs_debug_tile_lists": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _i64,
@@ -145,6 +147,7 @@ gs_graph_check = lib.gs_graph_check
 gs_graph_destroy = lib.gs_graph_destroy
 gs_get_stats = lib.gs_get_stats
 gs_sync = lib.gs_sync
+gs_render_timeout_probe = lib.gs_render_timeout_probe
 gs_debug_project = lib.gs_debug_project
 gs_debug_tile_lists = lib.gs_debug_tile_lists
 gs_sort_segments = lib.gs_sort_segments
@@ -379,6 +382,14 @@ class Renderer:
                                          intrinsics.data_ptr(), W, H, rgb.data_ptr(),
                                          depth.data_ptr(), _ptr(final_T), _stream(stream)))
         return rgb, depth, final_T
+
+    def timeout_probe(self, sid: int, viewmat, intr, W: int, H: int, stream=None) -> int:
+        """gs_render_timeout_probe: the status it returns (GS_ERR_TIMEOUT expected)."""
+        import torch
+        rgb = torch.empty((1, H, W, 3), dtype=torch.float32, device=viewmat.device)
+        depth = torch.empty((1, H, W), dtype=torch.float32, device=viewmat.device)
+        return int(gs_render_timeout_probe(self.ctx, sid, viewmat.data_ptr(), intr.data_ptr(), W, H,
+                                           rgb.data_ptr(), depth.data_ptr(), _stream(stream)))
 
     def sync(self, stream=None) -> None:
         """gs_sync: wait for the stream and the last render call; raise a

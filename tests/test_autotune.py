@@ -10,21 +10,22 @@ from paper_2510_15352_b300 import autotune, synth
 
 def test_candidates_cover_the_space():
     c = list(autotune.candidates())
-    # layouts (2,1) (4,1) (8,1) x 4 batches (8,4) x groups x chunks
-    assert len(c) == 7 * 2 * 3
+    # layouts (2,1) (4,1) (8,1) x 4 batches x 2 launch forms (8,4) x groups x chunks
+    assert len(c) == 11 * 2 * 3
     assert {x["pixels_per_thread"] for x in c} == {2, 4, 8}
     assert {(x["pixels_per_thread"], x["tiles_per_block"]) for x in c} == {(2, 1), (4, 1), (8, 1), (8, 4)}
     assert {x["comp_batch"] for x in c if x["pixels_per_thread"] == 8 and x["tiles_per_block"] == 1} \
         == {32, 64, 96, 128}
-    assert all(x["comp_batch"] == 64 for x in c if x["pixels_per_thread"] != 8 or x["tiles_per_block"] != 1)
+    assert all(x["comp_batch"] == 64 and x["persistent"] == 0
+               for x in c if x["pixels_per_thread"] != 8 or x["tiles_per_block"] != 1)
 
 
 def test_staged_search_space():
     """The search's stages: the compositing knobs with the default pipeline
-    knobs (7 candidates), then the pipeline knobs (6)."""
+    knobs (11 candidates), then the pipeline knobs (6)."""
     best = dict(autotune.DEFAULTS)
     s1 = list(autotune.candidates(None, autotune.STAGES[0], best))
-    assert len(s1) == 7 and all(c["camera_group"] == 64 and c["max_chunk_cameras"] == 512 for c in s1)
+    assert len(s1) == 11 and all(c["camera_group"] == 64 and c["max_chunk_cameras"] == 512 for c in s1)
     s2 = list(autotune.candidates(None, autotune.STAGES[1], s1[0]))
     assert len(s2) == 6 and all(c["comp_batch"] == s1[0]["comp_batch"] for c in s2)
 
