@@ -283,6 +283,39 @@ def upsampled_launches(n_cams, chunk, w, h):
     return total
 
 
+def run_cnn_only(args):
+    """--cnn-frames F: the learned upsampler's inference alone (gs_upsample_forward,
+    RGB + depth) on F random 160x120 frames with random-init weights, per backend
+    (tcgen05 and mma.sync), CUDA events after warm-up; one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2510_15352_b300 import gs, upsampler
+    n, h, w = args.cnn_frames, 120, 160
+    up = gs.Upsampler(0)
+    try:
+        rng = np.random.default_rng(0)
+        up.set_params(upsampler.init_params(0)
+                      + rng.normal(0, 0.01, gs.Upsampler.n_params).astype(np.float32))
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        lr = torch.rand((n, h, w, 3), device="cuda", generator=gen)
+        ld = torch.rand((n, h, w), device="cuda", generator=gen)
+        hr = torch.empty((n, 4 * h, 4 * w, 3), device="cuda")
+        hd = torch.empty((n, 4 * h, 4 * w), device="cuda")
+        stream = torch.cuda.current_stream()
+        out = {}
+        for backend in ("tcgen05", "mma_sync"):
+            up.set_backend(backend)
+            ms = _timed_steps(torch, stream, lambda: up.forward(lr, ld, hr, hd), args.steps,
+                              args.warmup)
+            up.check()
+            out[backend] = ms / args.steps
+    finally:
+        up.close()
+    print(json.dumps({"cnn_frames": n, "lr": [w, h], "ms": out,
+                      "tflops": {k: CNN_FLOPS_PER_LR_PIXEL * h * w * n / (v / 1e3) / 1e12
+                                 for k, v in out.items()}}), flush=True)
+
+
 def run_reference(args):
     rank, _, world = env_rank()
     if rank != 0:
@@ -434,7 +467,7 @@ def half_leg(args, gs, torch, synth, scenes, which, vm, local, stream, fp32_tflo
     R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
                     pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
                     camera_group=args.group, comp_batch=args.comp_batch,
-              persistent=args.persistent)
+                    persistent=args.persistent)
     try:
         nbytes = 0
         sids = []
@@ -513,7 +546,7 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
                         device="cuda").expand(n, 4).contiguous()
     R = gs.Renderer(device=local, max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
                     tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch,
-              persistent=args.persistent)
+                    persistent=args.persistent)
     sids = [R.add_scene(sc) for sc in scenes]
     ids = np.array(sids, dtype=np.int32)[which]
     up = gs.Upsampler(device=local)
@@ -828,9 +861,13 @@ def main():
     ap.add_argument("--up-pairs", type=int, default=200_000,
                     help="training pairs of the learned upsampler (0: skip the upsampled leg)")
     ap.add_argument("--oracle-time", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cnn-frames", type=int, default=0,
+                    help="time only the upsampler's inference on this many 160x120 frames")
     args = ap.parse_args()
     if args.oracle_time:
         oracle_time_main(args)
+    elif args.cnn_frames > 0:
+        run_cnn_only(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == BATCHED:

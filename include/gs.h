@@ -354,7 +354,9 @@ gs_status gs_sort_segments(gs_context *ctx, uint32_t *keys, uint32_t *vals, int6
  * Limits: n <= 2,097,152 keys and n_seg <= 4,096 segments, else
  * GS_ERR_CAPACITY with nothing done. The first call on a device looks up the
  * array's device address (a CUDA runtime query): make it before any stream
- * capture. All calls share the array and it keeps the last call's contents,
+ * capture. The address is kept for the life of the process: a cudaDeviceReset of
+ * that device after the first call is not supported. All calls share the array
+ * and it keeps the last call's contents,
  * so calls that may overlap on the GPU (other streams or host threads) race
  * and must be serialised by the caller. Work is enqueued on `stream`. */
 gs_status gs_sort_segments_noalloc(uint32_t *keys, uint32_t *vals, int64_t n,
@@ -426,11 +428,10 @@ gs_status gs_upsample_forward(gs_upsampler *u, int32_t n, int32_t h, int32_t w,
                               const float *lr_rgb, const float *lr_depth, float *hr_rgb,
                               float *hr_depth, void *stream);
 
-/* Kernels of gs_upsample_forward and of the forward and backward-data passes of
- * gs_upsample_grad: the 5th-generation tensor cores (tcgen05.mma with
+/* Kernels of gs_upsample_forward and of gs_upsample_grad (forward, backward-data
+ * and weight-gradient passes): the 5th-generation tensor cores (tcgen05.mma with
  * tensor-memory accumulators; the default) or warp-level mma.sync. Both compute
- * the same network with BF16 operands and FP32 accumulation; the weight
- * gradient always runs on mma.sync. */
+ * the same network with BF16 operands and FP32 accumulation. */
 enum { GS_UPSAMPLE_TCGEN05 = 0, GS_UPSAMPLE_MMA_SYNC = 1 };
 gs_status gs_upsampler_set_backend(gs_upsampler *u, int32_t backend);
 

@@ -27,6 +27,8 @@ cudaError_t up_conv_dgrad(int layer, const __nv_bfloat16 *dz, int n, int h, int 
                           __nv_bfloat16 *dx, cudaStream_t s);
 cudaError_t up_wgrad(int layer, const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int n, int h,
                      int w, float *gW, float *gb, int n_sm, cudaStream_t s);
+cudaError_t up_wgrad_tc(int layer, const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int n, int h,
+                        int w, float *gW, float *gb, int *status, int n_sm, cudaStream_t s);
 cudaError_t up_loss(const float *z, const float *rgb, const float *target, int n, int h, int w,
                     __nv_bfloat16 *dz, float *loss, cudaStream_t s);
 cudaError_t up_bilinear1(const float *src, int n, int h, int w, float *dst, cudaStream_t s);
@@ -385,7 +387,8 @@ gs_status gs_upsample_grad(gs_upsampler *u, int32_t n, int32_t h, int32_t w, con
     for (int l = 5; l >= 0 && e == cudaSuccess; --l) {
         float *gW = u->grads + layer_off(l);
         float *gb = gW + (long long)L_CO[l] * L_CI[l] * 9;
-        e = gsk::up_wgrad(l, act[l], dz, n, h, w, gW, gb, u->n_sm, s);
+        e = tc ? gsk::up_wgrad_tc(l, act[l], dz, n, h, w, gW, gb, u->status, u->n_sm, s)
+               : gsk::up_wgrad(l, act[l], dz, n, h, w, gW, gb, u->n_sm, s);
         if (e == cudaSuccess && l > 0) {
             bf16 *dst = (dz == dzA) ? dzB : dzA;
             e = tc ? gsk::up_dgrad_tc(l, dz, n, h, w, u->wdt[l], act[l], dst, u->status, u->n_sm, s)

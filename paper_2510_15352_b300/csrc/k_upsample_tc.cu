@@ -906,6 +906,199 @@ cudaError_t run_tc(const bf16 *x, int n, int h, int w, const bf16 *wt, const flo
     return cudaGetLastError();
 }
 
+// ---- weight gradient on the tensor cores ----
+// gW[co][ci][tap] = sum_p dz[p][co] x[p + off(tap)][ci] over every output pixel p,
+// as D = A B^T with K = pixels, taken in tiles of 128 output pixels (8 rows x 16
+// columns): A is the im2col of the tile, row r = tap CIN + ci, column p (rows
+// past 9 CIN stay zero); B is dz^T of the tile, row co. Both are staged K-major
+// with no swizzle -- element (r, k) at byte (k / 8) LBO + (r / 8) 128 +
+// (r % 8) 16 + (k % 8) 2, LBO = rows / 8 * 128 -- the layout the forward kernels
+// use for their operands. M runs over the stacked taps in tiles of 128 rows, N
+// = COUT. The accumulators stay in tensor memory across all tiles of a block;
+// at the end each warp reads its 32 lanes and adds them to gW (FP32 atomics, one
+// per weight per block). The bias gradient is summed from the staged dz^T.
+constexpr int WG_TH = 8, WG_TW = 16, WG_K = WG_TH * WG_TW;  // output pixels per tile (K)
+constexpr int WG_XH = WG_TH + 2, WG_XW = WG_TW + 2;         // input tile with halo
+constexpr int WG_THREADS = 128;
+
+template <int CIN, int COUT>
+struct WgSmem {
+    static constexpr int ROWS = 9 * CIN, MT = (ROWS + 127) / 128, RP = MT * 128;
+    static constexpr int LBO_A = RP / 8 * 128, LBO_B = COUT / 8 * 128;
+    static constexpr size_t a_bytes = (size_t)(WG_K / 8) * LBO_A;
+    static constexpr size_t b_bytes = (size_t)(WG_K / 8) * LBO_B;
+    static constexpr size_t x_bytes = (size_t)WG_XH * WG_XW * CIN * 2;
+    static constexpr size_t off_b = a_bytes, off_x = off_b + b_bytes;
+    static constexpr size_t off_bar = (off_x + x_bytes + 15) / 16 * 16;
+    static constexpr size_t total = off_bar + 32;
+    static constexpr int CST = tmem_stride<COUT>();
+    static constexpr int NCOL = MT * CST <= 32 ? 32 : MT * CST <= 64 ? 64 : MT * CST <= 128 ? 128 : 256;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    k_wgrad_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int n, int h, int w,
+               float *__restrict__ gW, float *__restrict__ gb, int cin_real, int *status) {
+    using L = WgSmem<CIN, COUT>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *As = smem, *Bs = smem + L::off_b;
+    bf16 *Xs = (bf16 *)(smem + L::off_x);
+    uint64_t *bar = (uint64_t *)(smem + L::off_bar);
+    uint32_t *tslot = (uint32_t *)(smem + L::off_bar + 8);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = (w + WG_TW - 1) / WG_TW, ty = (h + WG_TH - 1) / WG_TH;
+    const long long n_tiles = (long long)tx * ty * n;
+    // the padding rows of A stay zero; the other rows are rewritten per tile
+    for (size_t i = tid; i < L::a_bytes / 16; i += WG_THREADS) ((uint4 *)As)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(L::NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t IDESC = idesc_bf16(128, COUT);
+    float bacc = 0.0f;
+    uint32_t phase = 0u;
+    bool failed = false;
+    long long done = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++done) {
+        const int img = (int)(tile / ((long long)tx * ty));
+        const int rem = (int)(tile - (long long)img * tx * ty);
+        const int by = (rem / tx) * WG_TH, bx = (rem % tx) * WG_TW;
+        // 1. the input tile with its halo (NHWC, zero outside the image)
+        constexpr int C8 = CIN / 8, D8 = COUT / 8;
+        for (int i = tid; i < WG_XH * WG_XW * C8; i += WG_THREADS) {
+            const int p = i / C8, c8 = i - p * C8;
+            const int yy = by - 1 + p / WG_XW, xx = bx - 1 + p % WG_XW;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (yy >= 0 && yy < h && xx >= 0 && xx < w)
+                v = *(const uint4 *)(x + (((long long)img * h + yy) * w + xx) * CIN + c8 * 8);
+            *(uint4 *)(Xs + p * CIN + c8 * 8) = v;
+        }
+        // 2. B = dz^T: 8 channels of one pixel, scattered to 8 rows of column p
+        for (int i = tid; i < WG_K * D8; i += WG_THREADS) {
+            const int p = i / D8, c8 = i - p * D8;
+            const int yy = by + p / WG_TW, xx = bx + p % WG_TW;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (yy < h && xx < w)
+                v = *(const uint4 *)(dz + (((long long)img * h + yy) * w + xx) * COUT + c8 * 8);
+            const uint16_t *e = (const uint16_t *)&v;
+            unsigned char *col = Bs + (p / 8) * L::LBO_B + c8 * 128 + (p % 8) * 2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *(uint16_t *)(col + j * 16) = e[j];
+        }
+        __syncthreads();  // Xs and Bs complete
+        // 3. A = im2col: 8 channels of input pixel p + off(tap) to 8 rows of column p
+        for (int i = tid; i < WG_K * 9 * C8; i += WG_THREADS) {
+            const int p = i / (9 * C8), q = i - p * (9 * C8);
+            const int tap = q / C8, c8 = q - tap * C8;
+            const int py = p / WG_TW + tap / 3, px = p % WG_TW + tap % 3;
+            const uint4 v = *(const uint4 *)(Xs + (py * WG_XW + px) * CIN + c8 * 8);
+            const uint16_t *e = (const uint16_t *)&v;
+            const int r0 = tap * CIN + c8 * 8;  // a multiple of 8: rows r0 .. r0 + 7
+            unsigned char *col = As + (p / 8) * L::LBO_A + (r0 / 8) * 128 + (p % 8) * 2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *(uint16_t *)(col + j * 16) = e[j];
+        }
+        // the bias gradient from the staged dz^T (row co, pixels of this tile)
+        if (tid < COUT) {
+            for (int p = 0; p < WG_K; ++p) {
+                const unsigned char *b = Bs + (p / 8) * L::LBO_B + (tid / 8) * 128 + (tid % 8) * 16 + (p % 8) * 2;
+                bacc += __bfloat162float(*(const bf16 *)b);
+            }
+        }
+        // generic-proxy writes -> visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+            const uint64_t a0 = sdesc(smem_u32(As), L::LBO_A, 128);
+            const uint64_t b0 = sdesc(smem_u32(Bs), L::LBO_B, 128);
+#pragma unroll
+            for (int m = 0; m < L::MT; ++m)
+#pragma unroll
+                for (int ks = 0; ks < WG_K / 16; ++ks)
+                    mma_bf16(tmem + (uint32_t)(m * L::CST),
+                             a0 + (uint64_t)(m * 128 + ks * 2 * (L::LBO_A / 16)),
+                             b0 + (uint64_t)(ks * 2 * (L::LBO_B / 16)), IDESC,
+                             (done > 0 || ks > 0) ? 1u : 0u);
+            mma_commit(smem_u32(bar));
+        }
+        __syncwarp();
+        // the MMAs read As / Bs: wait before the next tile restages them
+        const bool ok = mbar_wait(smem_u32(bar), phase, TC_SPIN_LIMIT);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        fence_after();
+    }
+    if (failed) {
+        // one more commit tracks every MMA issued; wait for it (bounded) before
+        // the accumulators are freed
+        if (tid == 0) {
+            atomicOr(status, 1);
+            mma_commit(smem_u32(bar));
+        }
+        __syncwarp();
+        mbar_wait(smem_u32(bar), phase, TC_SPIN_LIMIT);
+    } else if (done > 0) {
+        // D[r][co] of M-tile m: lane 32 warp + lane of the sub-partition, column m CST + co
+#pragma unroll 1
+        for (int m = 0; m < L::MT; ++m) {
+            const int r = m * 128 + warp * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * L::CST);
+            float v[32];
+            tmem_ld32(taddr, v);
+            const int tap = r / CIN, ci = r - tap * CIN;
+            const bool valid = r < L::ROWS && ci < cin_real;
+            if (valid)
+#pragma unroll
+                for (int co = 0; co < 32; ++co)
+                    atomicAdd(&gW[((long long)co * cin_real + ci) * 9 + tap], v[co]);
+            if (COUT > 32) {
+                float v2[16];
+                tmem_ld16(taddr + 32, v2);
+                if (valid)
+#pragma unroll
+                    for (int co = 0; co < 16; ++co)
+                        atomicAdd(&gW[((long long)(32 + co) * cin_real + ci) * 9 + tap], v2[co]);
+            }
+        }
+        if (tid < COUT) atomicAdd(&gb[tid], bacc);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L::NCOL));
+}
+
+template <int CIN, int COUT>
+cudaError_t run_wgrad_tc(const bf16 *x, const bf16 *dz, int n, int h, int w, float *gW, float *gb,
+                         int cin_real, int *status, int n_sm, cudaStream_t s) {
+    using L = WgSmem<CIN, COUT>;
+    const long long tiles = (long long)((w + WG_TW - 1) / WG_TW) * ((h + WG_TH - 1) / WG_TH) * n;
+    if (tiles == 0) return cudaSuccess;
+    auto kern = k_wgrad_tc<CIN, COUT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<long long>(tiles, (long long)n_sm);
+    kern<<<grid, WG_THREADS, L::total, s>>>(x, dz, n, h, w, gW, gb, cin_real, status);
+    return cudaGetLastError();
+}
+
+
 }  // namespace
 
 // Forward convolution of layer `layer` on the tensor cores. Layers 0-4 write
@@ -958,6 +1151,13 @@ cudaError_t up_dgrad_tc(int layer, const __nv_bfloat16 *dz, int n, int h, int w,
                                            act, status, n_sm, s);
     return run_tc<32, 32, TC_EPI_GATE>(dz, n, h, w, wdt, nullptr, dx, nullptr, nullptr, nullptr, act,
                                        status, n_sm, s);
+}
+
+cudaError_t up_wgrad_tc(int layer, const __nv_bfloat16 *x, const __nv_bfloat16 *dz, int n, int h,
+                        int w, float *gW, float *gb, int *status, int n_sm, cudaStream_t s) {
+    if (layer == 0) return run_wgrad_tc<16, 32>(x, dz, n, h, w, gW, gb, 6, status, n_sm, s);
+    if (layer < 5) return run_wgrad_tc<32, 32>(x, dz, n, h, w, gW, gb, 32, status, n_sm, s);
+    return run_wgrad_tc<32, 48>(x, dz, n, h, w, gW, gb, 32, status, n_sm, s);
 }
 
 // Test hook for the failure path: one hidden-layer convolution whose first

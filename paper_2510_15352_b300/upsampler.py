@@ -115,46 +115,3 @@ def train(up: "gs.Upsampler", renderer: "gs.Renderer", scene_ids, W: int, H: int
         if log:
             log(f"pairs {step * frames_per_step}: loss {float(losses[-1].item()):.3e}")
     return [float(x) for x in torch.cat(losses).cpu()]
-
-
-def time_forward(n_frames: int = 128, h: int = 120, w: int = 160, repeats: int = 5,
-                 warmup: int = 3, device: int = 0) -> dict:
-    """Milliseconds of gs_upsample_forward (RGB + depth) on n_frames random
-    frames of h x w for each backend (CUDA events, after warm-up), with
-    random-init weights."""
-    import torch
-    up = gs.Upsampler(device)
-    try:
-        rng = np.random.default_rng(0)
-        up.set_params(init_params(0) + rng.normal(0, 0.01, gs.Upsampler.n_params).astype(np.float32))
-        gen = torch.Generator(device="cuda").manual_seed(0)
-        lr = torch.rand((n_frames, h, w, 3), device="cuda", generator=gen)
-        ld = torch.rand((n_frames, h, w), device="cuda", generator=gen)
-        hr = torch.empty((n_frames, 4 * h, 4 * w, 3), device="cuda")
-        hd = torch.empty((n_frames, 4 * h, 4 * w), device="cuda")
-        out = {}
-        for backend in ("tcgen05", "mma_sync"):
-            up.set_backend(backend)
-            for _ in range(warmup):
-                up.forward(lr, ld, hr, hd)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(repeats):
-                up.forward(lr, ld, hr, hd)
-            e1.record()
-            up.check()
-            out[backend] = e0.elapsed_time(e1) / repeats
-        return out
-    finally:
-        up.close()
-
-
-if __name__ == "__main__":
-    import argparse
-    import json
-    ap = argparse.ArgumentParser(description="time the learned upsampler's inference kernels")
-    ap.add_argument("--time-frames", type=int, default=128)
-    a = ap.parse_args()
-    print(json.dumps({"frames": a.time_frames, "ms": time_forward(a.time_frames)}))
