@@ -191,7 +191,10 @@ gs_status gs_scene_destroy(gs_context *ctx, int32_t scene_id);
  * Work is enqueued on `stream` and, with the default sync_errors = 0, the call
  * returns without waiting for it (it waits only when the workspace has to
  * grow, or for a staging buffer that a call two calls back still copies
- * from). Calls on one context run in call order even on different streams.
+ * from). The exception is a call whose chunks see more Gaussians than any call
+ * before on this context: it sizes the workspace, so it waits for its status
+ * and renders an overflowed chunk again before it returns. Calls on one
+ * context run in call order even on different streams.
  * A chunk of cameras whose survivors exceed the workspace is not rendered;
  * the device records it in a sticky status word and a later render call,
  * gs_sync or gs_get_stats returns GS_ERR_CAPACITY (once); the images of that

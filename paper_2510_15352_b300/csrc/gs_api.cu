@@ -91,6 +91,7 @@ struct gs_context {
     int tab_next = 0;
     cudaEvent_t done_ev = nullptr;  // end of the last render call's work (orders streams)
     bool done_valid = false;
+    long long proven_gauss = 0;   // largest per-chunk Gaussian count a waited-for call rendered
     DevBuf pq;                    // persistent launch: queue head + per-camera binning counts
     int pgrid[4] = {0, 0, 0, 0};  // its resident grid, per compositing batch (32/64/96/128)
     int probe_extra = 0;          // timeout probe: camera 0 waits for items that never come
@@ -545,7 +546,10 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     CKS(poll_sticky(ctx, false, a.st));
     if (ctx->done_valid) CKC(cudaStreamWaitEvent(a.st, ctx->done_ev, 0));  // calls in order
     const size_t status_bytes = sizeof(long long) + P.chunks.size() * sizeof(int);
-    const bool sync = ctx->cfg.sync_errors != 0 || a.force_sync;
+    // A call whose chunks see more Gaussians than any call before on this context
+    // waits for its status and re-renders in place: it sizes the workspace. Later
+    // calls of that size only enqueue.
+    const bool sync = ctx->cfg.sync_errors != 0 || a.force_sync || P.max_gauss > ctx->proven_gauss;
     std::vector<char> redo;
     for (int attempt = 0; attempt < 2; ++attempt) {
         CKS(size_workspace(ctx, P));
@@ -601,6 +605,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     }
     CKC(cudaEventRecord(ctx->done_ev, a.st));
     ctx->done_valid = true;
+    if (sync) ctx->proven_gauss = std::max(ctx->proven_gauss, P.max_gauss);
     gs_stats stt{};
     stt.n_cameras = a.n;
     stt.n_chunks = (int)P.chunks.size();

@@ -940,7 +940,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     k_wgrad_tc(const bf16 *__restrict__ x, const bf16 *__restrict__ dz, int n, int h, int w,
                float *__restrict__ gW, float *__restrict__ gb, int cin_real, int *status) {
     using L = WgSmem<CIN, COUT>;
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *As = smem, *Bs = smem + L::off_b;
     bf16 *Xs = (bf16 *)(smem + L::off_x);
     uint64_t *bar = (uint64_t *)(smem + L::off_bar);

@@ -55,13 +55,30 @@ def test_render_returns_before_the_render_completes(torch):
         b.close()
 
 
+def _looking_away(torch, vm):
+    """The same cameras turned to look straight up from high above the scene
+    (almost nothing survives)."""
+    up = torch.from_numpy(vm).cuda().clone()
+    look_up = torch.tensor([[1.0, 0, 0], [0, 0, 1.0], [0, -1.0, 0]], device="cuda")
+    up[:, :3, :3] = look_up
+    up[:, :3, 3] = -(look_up @ torch.tensor([5.0, 5.0, 20.0], device="cuda"))
+    return up
+
+
 def test_overflow_is_reported_later_and_rendering_again_succeeds(torch, orc):
+    """The first call of a batch size sizes the workspace (it waits); when the
+    cameras then turn so that a chunk needs more, an asynchronous call cannot
+    render it: the error comes with gs_sync (or gs_get_stats), once, and a
+    render after it is complete and correct."""
     from paper_2510_15352_b300 import gs
     scene, vm, it, W, H = synth.workload("small_20k_8cam_160x120")
     vm_d, it_d = torch.from_numpy(vm).cuda(), torch.from_numpy(it).cuda()
+    away = _looking_away(torch, vm)
     r = gs.Renderer(device=0, sync_errors=0, workspace_survivors=10)
     try:
         sid = r.add_scene(scene)
+        r.render(sid, away, it_d, W, H)  # sizes the workspace for almost no survivors
+        r.sync()
         r.render(sid, vm_d, it_d, W, H, want_T=True)  # returns: the overflow is on the device
         with pytest.raises(gs.GSError) as e:
             r.sync()
@@ -78,6 +95,8 @@ def test_overflow_is_reported_later_and_rendering_again_succeeds(torch, orc):
         r2 = gs.Renderer(device=0, sync_errors=0, workspace_survivors=10)
         try:
             s2 = r2.add_scene(scene)
+            r2.render(s2, away, it_d, W, H)
+            r2.sync()
             r2.render(s2, vm_d, it_d, W, H)
             with pytest.raises(gs.GSError) as e:
                 r2.stats()
