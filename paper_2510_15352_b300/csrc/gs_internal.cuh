@@ -40,8 +40,8 @@ struct CompParams {
 // A scene resident in device memory (structure of arrays, see gs.h).
 // The Gaussians are stored in the library's spatial order (k_scene.cu): orig[p]
 // is the caller's index of the Gaussian at position p; bounds holds two float4
-// per block of PROJ_THREADS positions (min of the means and the largest
-// squared scale; max of the means and a finite flag).
+// per group of 32 positions (min of the means and the largest squared scale;
+// max of the means and a finite flag).
 struct SceneDev {
     const void *mean, *log_scale, *quat, *logit, *sh;
     const int *orig;

@@ -44,6 +44,7 @@ namespace {
 
 constexpr int PB_RPT = 8;     // depth ranks per lane of a persistent binning item (256)
 constexpr int PB_MAXP = 129;  // super-tile row pitch its shared memory holds
+constexpr int PB_BATCH_BIN = 4, PB_BATCH_TILE = 8;  // items per queue unit
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -491,7 +492,8 @@ __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1) k_composite(cons
 // (an atomic counter) hands out work items in order: first the binning items
 // (256 depth ranks of one camera each, bin_item at warp granularity), then one
 // compositing item per (camera, tile) across all cameras and scenes of the
-// chunk. A tile may be composited only when every binning item of its camera
+// chunk; a warp takes a unit of 4 binning items or 8 tiles per atomic on the
+// queue head. A tile may be composited only when every binning item of its camera
 // is done: its warp polls the camera's counter (written after a fence by each
 // binning item) with a bounded number of polls, and when the bound is reached
 // it raises the timeout bit of the context's sticky status word (reported as
@@ -519,20 +521,35 @@ __global__ void __launch_bounds__(32, 16) k_bin_composite(const CompArgs A, cons
     __shared__ uint32_t sbm[(32 * PB_RPT / 32) * PB_MAXP];
     const int lane = threadIdx.x;
     const int nbin = Q.blk_prefix[A.n_slots];
-    const int total = nbin + Q.n_tiles;
+    // work units: PB_BATCH_BIN binning items or PB_BATCH_TILE tiles per unit, so a
+    // warp takes one unit per atomic on the queue head (one counter for the launch)
+    const int ubin = (nbin + PB_BATCH_BIN - 1) / PB_BATCH_BIN;
+    const int total = ubin + (Q.n_tiles + PB_BATCH_TILE - 1) / PB_BATCH_TILE;
+    int item = 0, item_end = 0;
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(Q.head, 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
-        if (item < nbin) {
+        if (item == item_end) {
+            int u = 0;
+            if (lane == 0) u = atomicAdd(Q.head, 1);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (u >= total) break;
+            if (u < ubin) {
+                item = u * PB_BATCH_BIN;
+                item_end = min(item + PB_BATCH_BIN, nbin);
+            } else {
+                item = nbin + (u - ubin) * PB_BATCH_TILE;
+                item_end = min(item + PB_BATCH_TILE, nbin + Q.n_tiles);
+            }
+        }
+        const int it_now = item++;
+        if (it_now < nbin) {
+            const int item = it_now;
             const int2 bt = Q.bintab[item];
             const CamInfo ci = A.cams[bt.x];
             bin_item<32, PB_RPT>(sbm, ci, bt.y, Q.srect, A.vals, Q.rrect, Q.bitmap, Q.n_isect);
             __threadfence();  // this item's rects and words before its count
             if (lane == 0) atomicAdd(Q.bin_done + bt.x, 1);
         } else {
-            const int t = item - nbin;
+            const int t = it_now - nbin;
             int first;
             const int c = block_camera(A.tile_prefix, A.n_slots, A.per_cam, t, first);
             const int need = Q.blk_prefix[c + 1] - Q.blk_prefix[c] + (c == 0 ? Q.extra_need : 0);

@@ -6,10 +6,10 @@
 // Gaussian's attributes are read from HBM once per camera group instead of once
 // per camera. Attribute loads are structure-of-arrays: consecutive threads read
 // consecutive addresses of each attribute row. Scenes are stored in spatial
-// (Morton) order (k_scene.cu), so a block's Gaussians are close together and
-// most blocks are, for a given camera, entirely outside the view or entirely
-// inside it; the mask pass tests the block's box first and the Gaussians one
-// by one only when the box straddles the view's edges.
+// (Morton) order (k_scene.cu), so a warp's 32 Gaussians are close together and
+// most such groups are, for a given camera, entirely outside the view or
+// entirely inside it; the mask pass tests the group's box first and the
+// Gaussians one by one only when the box straddles the view's edges.
 //
 // Two passes keep the survivor order deterministic (storage order within a
 // camera; the tie-break pass after the depth sort restores index order among
@@ -17,7 +17,7 @@
 //   k_cam_setup     -- once per chunk: each camera's projection constants, which
 //                      both passes copy into shared memory per block;
 //   k_project_mask  -- survival bit per (camera, Gaussian), one 32-bit mask word
-//                      per warp and camera: zero or all ones from the block test,
+//                      per warp and camera: zero or all ones from the group test,
 //                      else per Gaussian (prefilter, then the exact test);
 //   k_scan_masks    -- per camera, exclusive prefix of the mask popcounts;
 //   k_project_write -- every lane holds one Gaussian (geometry, opacity, SH) in
@@ -203,12 +203,28 @@ __device__ __forceinline__ bool prefilter(const CamProj &c, const GaussGeo &G, c
     return !(u + rb < 0.0f || u - rb >= c.W || v + rb < 0.0f || v - rb >= c.H);
 }
 
+// CULL = false: the values of a pair known to survive (the write pass), without
+// the radius bound and the cull tests; every value is computed by the same
+// operations as with CULL = true, so it is the same bit for bit.
+template <bool CULL = true>
 __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
                                         const ProjParams &P, Proj &o) {
     float z, iz, xz, yz, u, v;
-    const bool pre = prefilter(c, G, P, z, iz, xz, yz, u, v);
-    o.z = z;
-    if (!pre) return false;
+    if (CULL) {
+        const bool pre = prefilter(c, G, P, z, iz, xz, yz, u, v);
+        o.z = z;
+        if (!pre) return false;
+    } else {
+        const float px = fmaf(c.R[0], G.mx, fmaf(c.R[1], G.my, fmaf(c.R[2], G.mz, c.t[0])));
+        const float py = fmaf(c.R[3], G.mx, fmaf(c.R[4], G.my, fmaf(c.R[5], G.mz, c.t[1])));
+        z = fmaf(c.R[6], G.mx, fmaf(c.R[7], G.my, fmaf(c.R[8], G.mz, c.t[2])));
+        iz = rcp_a(z);
+        xz = __fmul_rn(px, iz);
+        yz = __fmul_rn(py, iz);
+        u = fmaf(c.fx, xz, c.cx);
+        v = fmaf(c.fy, yz, c.cy);
+        o.z = z;
+    }
     const float xc = fminf(fmaxf(xz, -c.lxn), c.lxp);
     const float yc = fminf(fmaxf(yz, -c.lyn), c.lyp);
     const float j00 = __fmul_rn(c.fx, iz), j02 = -__fmul_rn(__fmul_rn(c.fx, xc), iz);
@@ -233,8 +249,8 @@ __device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
     const float hd = __fmul_rn(0.5f, __fsub_rn(a, cc));
     const float lmax = fmaf(0.5f, __fadd_rn(a, cc), sqrt_a(fmaf(hd, hd, __fmul_rn(b, b))));
     const float r = __fmul_rn(P.sigma, sqrt_a(lmax));
-    if (!(__fadd_rn(u, r) >= 0.0f) || !(__fsub_rn(u, r) < c.W) || !(__fadd_rn(v, r) >= 0.0f) ||
-        !(__fsub_rn(v, r) < c.H))
+    if (CULL && (!(__fadd_rn(u, r) >= 0.0f) || !(__fsub_rn(u, r) < c.W) ||
+                 !(__fadd_rn(v, r) >= 0.0f) || !(__fsub_rn(v, r) < c.H)))
         return false;
     o.x0 = (int)fmaxf(floorf(__fmul_rn(__fsub_rn(u, r), 0.0625f)), 0.0f);
     o.x1 = (int)fminf(floorf(__fmul_rn(__fadd_rn(u, r), 0.0625f)), (float)(c.TX - 1));
@@ -349,11 +365,11 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
     }
 }
 
-// A block of Gaussians against one camera, before its Gaussians one by one:
-// BLK_OUT when the exact test culls every Gaussian of the block, BLK_IN when it
-// keeps every one, BLK_PART otherwise. The block is the box of its means (lo,
-// hi) and its largest squared scale (lo.w); hi.w = 0 flags a non-finite value
-// (always BLK_PART). Over the box, a camera-space linear form a.mu + b ranges
+// A group of Gaussians (a warp's 32) against one camera, before the Gaussians
+// one by one: BLK_OUT when the exact test culls every Gaussian of the group,
+// BLK_IN when it keeps every one, BLK_PART otherwise. The group is the box of
+// its means (lo, hi) and its largest squared scale (lo.w); hi.w = 0 flags a
+// non-finite value (always BLK_PART). Over the box, a camera-space linear form a.mu + b ranges
 // over its centre value -+ |a|.e (e: half extents), widened for float32
 // rounding. For z > near, u + rb < 0 is fx x + cx z + rb z < 0, and rb z (the
 // prefilter's radius bound times z) is at most
@@ -425,7 +441,7 @@ __device__ __forceinline__ int classify_block(const CamProj &c, float4 lo, float
 // per 1,024 cameras).
 constexpr int MQ = 64;  // queue entries per warp: < 32 left + < 32 appended
 
-__global__ void __launch_bounds__(PROJ_THREADS)
+__global__ void __launch_bounds__(PROJ_THREADS, 4)
     k_project_mask(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
                    const CamInfo *__restrict__ cams, const CamProj *__restrict__ camtab,
                    ProjParams P, uint32_t *__restrict__ masks) {
@@ -438,14 +454,12 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     __shared__ long long moff[MAX_GROUP];
     __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane (camera < 64)
     __shared__ uint32_t smask[NW][MAX_GROUP];
-    __shared__ uint8_t cls[MAX_GROUP];                // BLK_OUT / BLK_IN / BLK_PART per camera
+    __shared__ uint8_t cls[NW][MAX_GROUP];            // per warp: BLK_OUT / IN / PART per camera
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SceneDev sc = scenes[gr.scene];
     if (tid < gr.ncam) {
-        const CamProj c = load_cam(camtab[gr.slot0 + tid]);
-        cp[tid] = c;
+        cp[tid] = load_cam(camtab[gr.slot0 + tid]);
         moff[tid] = cams[gr.slot0 + tid].mask_off;
-        cls[tid] = (uint8_t)classify_block(c, sc.bounds[2 * blockIdx.x], sc.bounds[2 * blockIdx.x + 1], P);
     }
     if (2 * tid < gr.ncam) {  // an odd last camera is paired with itself
         const int c1 = 2 * tid + 1 < gr.ncam ? 2 * tid + 1 : 2 * tid;
@@ -464,6 +478,19 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
     }
     __syncthreads();
+    // the warp's 32 Gaussians as a group against each camera (lane c: cameras c, c + 32)
+    {
+        const long long wb = (g0 >> 5) + warp;
+        const bool live = (wb << 5) < gr.n;
+        float4 blo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), bhi = blo;
+        if (live) {
+            blo = sc.bounds[2 * wb];
+            bhi = sc.bounds[2 * wb + 1];
+        }
+        for (int c = lane; c < gr.ncam; c += 32)
+            cls[warp][c] = live ? (uint8_t)classify_block(load_cam(cp[c]), blo, bhi, P) : (uint8_t)BLK_OUT;
+        __syncwarp();
+    }
     const uint32_t lt = (1u << lane) - 1u;
     int nq = 0;  // queued pairs of this warp (warp-uniform)
     // the exact test on queue entries [0, cnt) (cnt <= 32), results OR-ed into smask
@@ -501,12 +528,12 @@ __global__ void __launch_bounds__(PROJ_THREADS)
     // the block's valid Gaussians: the mask word of a camera that keeps them all
     const uint32_t all = __ballot_sync(0xffffffffu, valid);
     for (int c = 0; c < gr.ncam; c += 2) {  // two cameras per packed prefilter
-        const int k0 = cls[c], k1 = c + 1 < gr.ncam ? cls[c + 1] : BLK_OUT;
+        const int k0 = cls[warp][c], k1 = c + 1 < gr.ncam ? cls[warp][c + 1] : BLK_OUT;
         if (lane == 0) {
             if (k0 == BLK_IN) smask[warp][c] = all;
             if (k1 == BLK_IN) smask[warp][c + 1] = all;
         }
-        if (k0 != BLK_PART && k1 != BLK_PART) continue;  // block-uniform
+        if (k0 != BLK_PART && k1 != BLK_PART) continue;  // warp-uniform
         bool in0 = false, in1 = false;
         if (valid) prefilter2(load_pair(cpair[c >> 1]), G, P, in0, in1);
         append(c, in0 && k0 == BLK_PART);
@@ -691,13 +718,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 2)
         if (!((word >> lane) & 1u)) continue;
         const CamProj cam = load_cam(cp[c]);
         Proj pr;
-        if (!project(cam, G, P, pr)) {  // cannot happen: same arithmetic as the mask pass
-            pr.x0 = 1;
-            pr.x1 = 0;
-            pr.y0 = 1;
-            pr.y1 = 0;
-            pr.u = pr.v = pr.A = pr.B = pr.C = pr.r = pr.sa = pr.sc = 0.0f;
-        }
+        project<false>(cam, G, P, pr);  // the mask pass kept this pair
         float rgb[3];
         sh_colour_reg<DEG>(sh, cam, G, rgb);
         float hx = -1e30f, hy = -1e30f;

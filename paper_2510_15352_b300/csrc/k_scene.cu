@@ -1,11 +1,10 @@
 // k_scene.cu -- spatial order of a scene's Gaussians, set up once at upload,
 // and the bounds of the projection blocks.
 //
-// The projection passes work on blocks of PROJ_THREADS consecutive Gaussians
-// and test each block against each camera of a group before its Gaussians:
-// a block entirely outside the view culls all of them, a block entirely inside
-// keeps all of them, and only the blocks in between are tested Gaussian by
-// Gaussian. That pays only when a block's Gaussians are close together in
+// The projection's mask pass tests each warp's 32 consecutive Gaussians as a
+// group against each camera before the Gaussians themselves: a group entirely
+// outside the view culls all of them, a group entirely inside keeps all of
+// them, and only the groups in between are tested Gaussian by Gaussian. That pays only when a block's Gaussians are close together in
 // space, so the library stores a scene in Morton (Z-curve) order of the means:
 // 10 bits per axis of the means' bounding box, a stable radix sort of the
 // 30-bit codes, then a gather of every attribute row. orig[p] keeps the
@@ -111,14 +110,15 @@ __global__ void k_gather_rows(const E *__restrict__ src, E *__restrict__ dst,
     }
 }
 
-// Per block of PROJ_THREADS stored Gaussians: bounds[2b] = (min x, y, z of the
-// means, largest squared scale), bounds[2b + 1] = (max x, y, z, 1 if every
-// mean and scale of the block is finite else 0). The squared scale is computed
-// exactly as the projection computes it (expf of the stored log-scale).
+// Per group of 32 stored Gaussians (one warp of the projection): bounds[2b] =
+// (min x, y, z of the means, largest squared scale), bounds[2b + 1] = (max x,
+// y, z, 1 if every mean and scale of the group is finite else 0). The squared
+// scale is computed exactly as the projection computes it (expf of the stored
+// log-scale).
 template <typename T>
-__global__ void __launch_bounds__(PROJ_THREADS)
+__global__ void __launch_bounds__(256)
     k_block_bounds(const void *mean, const void *log_scale, long long n, float4 *bounds) {
-    const long long g = (long long)blockIdx.x * PROJ_THREADS + threadIdx.x;
+    const long long g = blockIdx.x * 256LL + threadIdx.x;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     float s2 = 0.0f;
     int finite = 1;
@@ -135,7 +135,6 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         s2 = sm * sm;
         finite &= isfinite(s2);
     }
-    __shared__ float red[PROJ_THREADS / 32][8];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
 #pragma unroll
@@ -146,33 +145,10 @@ __global__ void __launch_bounds__(PROJ_THREADS)
         s2 = fmaxf(s2, __shfl_xor_sync(0xffffffffu, s2, d));
         finite &= __shfl_xor_sync(0xffffffffu, finite, d);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[warp][0] = lo[0];
-        red[warp][1] = lo[1];
-        red[warp][2] = lo[2];
-        red[warp][3] = s2;
-        red[warp][4] = hi[0];
-        red[warp][5] = hi[1];
-        red[warp][6] = hi[2];
-        red[warp][7] = (float)finite;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float4 a = make_float4(red[0][0], red[0][1], red[0][2], red[0][3]);
-        float4 b = make_float4(red[0][4], red[0][5], red[0][6], red[0][7]);
-        for (int w = 1; w < PROJ_THREADS / 32; ++w) {
-            a.x = fminf(a.x, red[w][0]);
-            a.y = fminf(a.y, red[w][1]);
-            a.z = fminf(a.z, red[w][2]);
-            a.w = fmaxf(a.w, red[w][3]);
-            b.x = fmaxf(b.x, red[w][4]);
-            b.y = fmaxf(b.y, red[w][5]);
-            b.z = fmaxf(b.z, red[w][6]);
-            b.w = fminf(b.w, red[w][7]);
-        }
-        bounds[2 * blockIdx.x] = a;
-        bounds[2 * blockIdx.x + 1] = b;
+    const long long wb = g >> 5;
+    if ((threadIdx.x & 31) == 0 && (wb << 5) < n) {
+        bounds[2 * wb] = make_float4(lo[0], lo[1], lo[2], s2);
+        bounds[2 * wb + 1] = make_float4(hi[0], hi[1], hi[2], (float)finite);
     }
 }
 
@@ -214,15 +190,14 @@ cudaError_t launch_gather_rows(const void *src, void *dst, int elem_bytes, const
     return cudaGetLastError();
 }
 
-long long scene_blocks(long long n) { return (n + PROJ_THREADS - 1) / PROJ_THREADS; }
+long long scene_blocks(long long n) { return (n + 31) / 32; }
 
 cudaError_t launch_block_bounds(const void *mean, const void *log_scale, int dtype, long long n,
                                 float4 *bounds, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     by_dtype(dtype, [&](auto tag) {
         using T = decltype(tag);
-        k_block_bounds<T><<<(unsigned)scene_blocks(n), PROJ_THREADS, 0, s>>>(mean, log_scale, n,
-                                                                             bounds);
+        k_block_bounds<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mean, log_scale, n, bounds);
     });
     return cudaGetLastError();
 }

@@ -34,6 +34,38 @@ struct TieRun {
     int len, pad;
 };
 
+// Sorts a run of equal keys [j, j + L) of the segment at base by the caller index.
+__device__ __noinline__ void order_run(uint32_t *__restrict__ vals, const uint32_t *__restrict__ oidx,
+                                       long long base, int j, int L, TieRun *__restrict__ runs,
+                                       long long capacity, int *__restrict__ n_runs) {
+    if (L <= SHORT) {
+        uint32_t *v = vals + base + j;
+        uint32_t sv[SHORT], so[SHORT];
+        for (int i = 0; i < L; ++i) {
+            sv[i] = v[i];
+            so[i] = oidx[base + sv[i]];
+        }
+        for (int i = 1; i < L; ++i) {  // insertion by index (indices are distinct)
+            const uint32_t a = so[i], b = sv[i];
+            int t = i - 1;
+            while (t >= 0 && so[t] > a) {
+                so[t + 1] = so[t];
+                sv[t + 1] = sv[t];
+                --t;
+            }
+            so[t + 1] = a;
+            sv[t + 1] = b;
+        }
+        for (int i = 0; i < L; ++i) v[i] = sv[i];
+    } else {
+        const int r = atomicAdd(n_runs, 1);
+        if (r < capacity) runs[r] = TieRun{base + j, base, L, 0};
+    }
+}
+
+// One sort tile (2,048 keys) per block pass; thread t looks at the TPT
+// consecutive keys from t0 + TPT t, loaded together with the key before them
+// and the one after (the lanes' loads are issued at once, not one by one).
 __global__ void __launch_bounds__(TT)
     k_tie_detect(const uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                  const uint32_t *__restrict__ oidx, const SortTile *__restrict__ tiles,
@@ -43,40 +75,29 @@ __global__ void __launch_bounds__(TT)
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         const SortTile T = tiles[tile];
         const uint32_t *k = keys + T.seg_base;
+        const int j0 = T.t0 + TPT * (int)threadIdx.x;
         const int end = T.t0 + T.nk;
-#pragma unroll 1
-        for (int q = 0; q < TPT; ++q) {
-            const int j = T.t0 + q * TT + (int)threadIdx.x;
-            if (j >= end) break;
-            const uint32_t kj = k[j];
-            if (j + 1 >= T.seg_n || k[j + 1] != kj) continue;  // no equal successor
-            if (j > 0 && k[j - 1] == kj) continue;              // not the run's first entry
+        if (j0 >= end) continue;
+        uint32_t kv[TPT + 2];  // keys j0 - 1 .. j0 + TPT (0xffffffff... outside the segment)
+#pragma unroll
+        for (int q = 0; q < TPT + 2; ++q) {
+            const int j = j0 - 1 + q;
+            kv[q] = (j >= 0 && j < T.seg_n) ? k[j] : (q == 0 ? 0xfffffffeu : 0xffffffffu);
+        }
+        // a run starts at j when k[j] == k[j + 1] and (j is the first or k[j - 1] != k[j]);
+        // the sentinels differ from each other, so no run starts past the segment
+        uint32_t starts = 0u;
+#pragma unroll
+        for (int q = 1; q <= TPT; ++q)
+            if (j0 - 1 + q < end && kv[q] == kv[q + 1] && kv[q - 1] != kv[q]) starts |= 1u << q;
+        while (starts) {
+            const int q = __ffs(starts) - 1;
+            starts &= starts - 1u;
+            const int j = j0 - 1 + q;
+            const uint32_t kj = kv[q];
             int e = j + 2;
             while (e < T.seg_n && k[e] == kj) ++e;
-            const int L = e - j;
-            if (L <= SHORT) {
-                uint32_t *v = vals + T.seg_base + j;
-                uint32_t sv[SHORT], so[SHORT];
-                for (int i = 0; i < L; ++i) {
-                    sv[i] = v[i];
-                    so[i] = oidx[T.seg_base + sv[i]];
-                }
-                for (int i = 1; i < L; ++i) {  // insertion by index (indices are distinct)
-                    const uint32_t a = so[i], b = sv[i];
-                    int t = i - 1;
-                    while (t >= 0 && so[t] > a) {
-                        so[t + 1] = so[t];
-                        sv[t + 1] = sv[t];
-                        --t;
-                    }
-                    so[t + 1] = a;
-                    sv[t + 1] = b;
-                }
-                for (int i = 0; i < L; ++i) v[i] = sv[i];
-            } else {
-                const int r = atomicAdd(n_runs, 1);
-                if (r < capacity) runs[r] = TieRun{T.seg_base + j, T.seg_base, L, 0};
-            }
+            order_run(vals, oidx, T.seg_base, j, e - j, runs, capacity, n_runs);
         }
     }
 }
