@@ -593,12 +593,13 @@ __global__ void __launch_bounds__(1024)
 
 constexpr float LOG2E = 1.4426950408889634f;
 
-// Colour of one Gaussian seen from camera c with its SH coefficients in
-// registers (sh[3 k + ch], zero past the scene's degree): per channel the
-// terms add in order of k, as in the definition.
+// Colour of one Gaussian seen from camera c with its SH coefficients in the
+// lane's own shared-memory column (shc[(3 k + ch) PROJ_THREADS], zero past the
+// scene's degree; consecutive lanes read consecutive words, no bank conflict):
+// per channel the terms add in order of k, as in the definition.
 template <int DEG>
-__device__ __forceinline__ void sh_colour_reg(const float *sh, const CamProj &c,
-                                              const GaussGeo &G, float rgb[3]) {
+__device__ __forceinline__ void sh_colour_smem(const float *shc, const CamProj &c,
+                                               const GaussGeo &G, float rgb[3]) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
     const float dd = dx * dx + dy * dy + dz * dz;
@@ -620,7 +621,7 @@ __device__ __forceinline__ void sh_colour_reg(const float *sh, const CamProj &c,
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(sh[3 * k + ch], Y[k], acc[ch]);
+        for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(shc[(3 * k + ch) * PROJ_THREADS], Y[k], acc[ch]);
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.0f);
 }
@@ -634,8 +635,11 @@ __device__ __forceinline__ void load_sh(const SceneDev &sc, long long g, float *
 }
 
 // Write pass: a block holds the same PROJ_THREADS Gaussians as a mask block and
-// every lane owns one of them: its geometry, opacity and SH coefficients are
-// read from HBM once, into registers, and used for every camera of the group.
+// every lane owns one of them: its geometry and opacity are read from HBM once
+// into registers and its SH coefficients into its own shared-memory column
+// (80 registers, three blocks per SM; with the coefficients in registers the
+// kernel needed 128 and ran two blocks per SM, 0.7 ms per step slower), and
+// used for every camera of the group.
 // The warp walks the group's cameras; for a camera whose mask word of this
 // warp is zero it moves on at once, else the lanes whose bit is set recompute
 // the projection (the same arithmetic as the mask pass), evaluate the colour
@@ -646,7 +650,7 @@ __device__ __forceinline__ void load_sh(const SceneDev &sc, long long g, float *
 // degree of the chunk's scenes (lower degrees run with zero coefficients,
 // which add nothing).
 template <int DEG>
-__global__ void __launch_bounds__(PROJ_THREADS, 2)
+__global__ void __launch_bounds__(PROJ_THREADS, 3)
     k_project_write(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
                     const CamInfo *__restrict__ cams, const CamProj *__restrict__ camtab,
                     ProjParams P,
@@ -687,25 +691,29 @@ __global__ void __launch_bounds__(PROJ_THREADS, 2)
     const long long g = g0 + tid;
     const bool valid = g < gr.n;
     GaussGeo G;
-    float sh[NC];
+    extern __shared__ float shs[];  // [NC][PROJ_THREADS]: this lane's column
+    float *shc = shs + tid;
     float log2o = 0.0f;
     uint32_t gidx = 0u;
     if (valid) {
         load_geo(sc, g, G);
         log2o = lg2_a(1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype))));
+        float sh[NC];
         if (sc.app_dtype == DT_F32)
             load_sh<float, NC>(sc, g, sh);
         else if (sc.app_dtype == DT_F16)
             load_sh<__half, NC>(sc, g, sh);
         else
             load_sh<__nv_bfloat16, NC>(sc, g, sh);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) shc[i * PROJ_THREADS] = sh[i];
         gidx = (uint32_t)sc.orig[g];
     } else {
         G.mx = G.my = G.mz = G.smax2 = 0.0f;
 #pragma unroll
         for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NC; ++i) sh[i] = 0.0f;
+        for (int i = 0; i < NC; ++i) shc[i * PROJ_THREADS] = 0.0f;
     }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
@@ -720,7 +728,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 2)
         Proj pr;
         project<false>(cam, G, P, pr);  // the mask pass kept this pair
         float rgb[3];
-        sh_colour_reg<DEG>(sh, cam, G, rgb);
+        sh_colour_smem<DEG>(shc, cam, G, rgb);
         float hx = -1e30f, hy = -1e30f;
         if (q >= 0.0f) {
             hx = fmaf(1.002f, sqrt_a(q * pr.sa), 0.02f);
@@ -798,9 +806,11 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
     dim3 grid(max_blocks_x, n_groups);  // PROJ_THREADS Gaussians per block, as the mask pass
     const CamProj *ct = (const CamProj *)camtab;
 #define GS_WRITE(D)                                                                              \
-    k_project_write<D><<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, ct, P, masks, woff,   \
-                                                     rec, with_d, srect, keys, oidx, wide,        \
-                                                     ln_alpha_min, status)
+    cudaFuncSetAttribute(k_project_write<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                         3 * (D + 1) * (D + 1) * PROJ_THREADS * 4);                                  \
+    k_project_write<D><<<grid, PROJ_THREADS, 3 * (D + 1) * (D + 1) * PROJ_THREADS * 4, s>>>(      \
+        groups, scenes, cams, ct, P, masks, woff, rec, with_d, srect, keys, oidx, wide,           \
+        ln_alpha_min, status)
     switch (max_deg) {
         case 0: GS_WRITE(0); break;
         case 1: GS_WRITE(1); break;

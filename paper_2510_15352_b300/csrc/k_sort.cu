@@ -196,12 +196,13 @@ __global__ void __launch_bounds__(ST, 5)
         const bool ok = i0 + r * 32 + lane < n;
         const uint32_t d = (kr[r] >> shift) & (ND - 1);
         // lanes whose digit differs from this lane's in some bit: per bit, the
-        // ballot XOR this lane's bit spread over 32 bits
+        // ballot XOR this lane's bit spread over 32 bits (0 - bit)
         uint32_t differ = ~__ballot_sync(0xffffffffu, ok);
 #pragma unroll
         for (int b = 0; b < BITS; ++b) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-            differ |= bal ^ (uint32_t)((int)(d << (31 - b)) >> 31);
+            const uint32_t t = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, t);
+            differ |= bal ^ (0u - t);
         }
         const uint32_t peers = ~differ;
         const uint32_t below = peers & lt;
