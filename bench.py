@@ -52,7 +52,10 @@ BATCHED = "batched_32scene_4096cam_mixed"
 # 11 per contributing pair (alpha >= alpha_min: 1 - alpha, T', alpha T, four FMAs),
 # and a lower bound, 22 flops per contributing pair only.
 F_PAIR = 20
-LAUNCHES_PER_CHUNK = 22
+# kernels per render chunk: camera table, mask, mask scan, plan, write; depth
+# order: count, scan, scatter, window, listed windows, listed runs (the last two
+# launch always and exit at once when nothing is listed); bin, composite
+LAUNCHES_PER_CHUNK = 13
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
 # FP32 rate derived from unit counts (148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz),
@@ -713,9 +716,6 @@ def run_b300(args):
     clk = clocks.stop()
     t_max = max_over_ranks(ms, dist)
     value = whole_job_rate(n * args.steps, world, t_max / 1e3)
-    # per chunk: camera table, mask, scan, plan, write, 4 x (hist, offsets, scatter) + copy (the
-    # fourth pass and the copy launch always and exit at once unless a depth key
-    # needs them), bin, composite
     launches = LAUNCHES_PER_CHUNK * n_chunks
 
     # end to end: host cameras in, host frames out, through the host entry point

@@ -57,11 +57,11 @@ struct gs_context {
     DevBuf d_scenes;
     // chunk workspace
     DevBuf masks, woff, counts, rec, keys, vals, tkeys, tvals, rrect, srect, bitmap;
-    DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorthist, sorttab, bintab,
-        camtab;
-    DevBuf wide;  // per chunk: some depth key needs the sort's fourth pass
+    DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorttab, bintab, camtab;
+    DevBuf seg_tk, seg_tv, seg_tiles, seg_hist;  // gs_sort_segments' own scratch
     DevBuf oidx;  // per survivor slot: the Gaussian's caller index (depth tie-break)
-    DevBuf ties, nruns;  // long runs of equal depth keys (list, per-chunk count)
+    DevBuf dcount, dwin, dbig;  // depth order: bucket counts, windows, listed windows
+    DevBuf ties, nruns;  // long runs of equal depth keys (list); per chunk 2 list counts
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
     int workspace_gen = 0;        // bumped when a chunk-workspace buffer is reallocated
@@ -303,12 +303,14 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     // a captured graph holds these addresses: any reallocation invalidates it
     DevBuf *held[] = {&ctx->masks,    &ctx->woff,     &ctx->counts,    &ctx->camtab, &ctx->rec,
                       &ctx->srect,    &ctx->rrect,    &ctx->keys,      &ctx->vals,   &ctx->tkeys,
-                      &ctx->tvals,    &ctx->bitmap,   &ctx->sorthist,  &ctx->sorttab,
-                      &ctx->bintab,   &ctx->wide,     &ctx->blkpre,    &ctx->sorttiles,
+                      &ctx->tvals,    &ctx->bitmap,   &ctx->dcount,    &ctx->sorttab,
+                      &ctx->bintab,   &ctx->dwin,     &ctx->dbig,      &ctx->blkpre,
+                      &ctx->sorttiles,
                       &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status,
                       &ctx->oidx,     &ctx->ties,     &ctx->nruns,    &ctx->pq};
-    void *before[sizeof(held) / sizeof(held[0])];
-    for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->p;
+    // (compared by capacity: a reallocation may return the freed address)
+    size_t before[sizeof(held) / sizeof(held[0])];
+    for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->cap;
     CKS(grow(ctx, ctx->masks, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->woff, (size_t)std::max<long long>(P.max_mask_words, 1) * 4));
     CKS(grow(ctx, ctx->counts, (size_t)m * sizeof(int)));
@@ -316,20 +318,25 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->rec, rec_bytes(S)));
     CKS(grow(ctx, ctx->srect, Sx * sizeof(uint2)));
     CKS(grow(ctx, ctx->rrect, Sx * sizeof(uint2)));
+    // (+4 elements: the depth order's window pass copies 16-byte pieces, up to
+    // 3 elements past a window's end)
     CKS(grow(ctx, ctx->keys, Sx * 4));
-    CKS(grow(ctx, ctx->vals, Sx * 4));
-    CKS(grow(ctx, ctx->tkeys, Sx * 4));
-    CKS(grow(ctx, ctx->tvals, Sx * 4));
+    CKS(grow(ctx, ctx->vals, (Sx + 4) * 4));
+    CKS(grow(ctx, ctx->tkeys, (Sx + 4) * 4));
+    CKS(grow(ctx, ctx->tvals, (Sx + 4) * 4));
     CKS(grow(ctx, ctx->oidx, Sx * 4));
     CKS(grow(ctx, ctx->ties, (Sx / 33 + 2) * tie_run_bytes()));
-    CKS(grow(ctx, ctx->nruns, (P.chunks.size() + 1) * sizeof(int)));
+    CKS(grow(ctx, ctx->nruns, 2 * (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->pq, (size_t)(m + 2) * sizeof(int)));
     // bounds implied by S: bitmap words <= max_sup * (S/32 + m), sort tiles <= S/2048 + m
     CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
-    CKS(grow(ctx, ctx->sorthist, (Sx / SORT_TILE_KEYS + m + 1) * 512 * 4));
-    CKS(grow(ctx, ctx->sorttab, (Sx / SORT_TILE_KEYS + m + 1) * sizeof(SortTile)));
+    const size_t sort_tiles = Sx / SORT_TILE_KEYS + m + 1;
+    CKS(grow(ctx, ctx->sorttab, sort_tiles * sizeof(SortTile)));
+    CKS(grow(ctx, ctx->dcount, (size_t)m * DEPTH_BUCKETS * 4));
+    const size_t windows = sort_tiles * (SORT_TILE_KEYS / DEPTH_WINDOW);
+    CKS(grow(ctx, ctx->dwin, windows * depth_window_bytes()));
+    CKS(grow(ctx, ctx->dbig, windows * depth_big_bytes()));
     CKS(grow(ctx, ctx->bintab, (Sx / BIN_RANKS_SMALL + m + 1) * sizeof(int2)));
-    CKS(grow(ctx, ctx->wide, (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->blkpre, (size_t)(m + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->sorttiles, (size_t)(m + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->segstart, (size_t)m * sizeof(long long)));
@@ -337,7 +344,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->stats, 8 * sizeof(unsigned long long)));
     CKS(grow(ctx, ctx->status, (P.chunks.size() + 2) * sizeof(long long)));
     for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i)
-        if (held[i]->p != before[i]) {
+        if (held[i]->cap != before[i]) {
             ctx->workspace_gen++;
             break;
         }
@@ -389,32 +396,23 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                         (long long *)ctx->segcount.p, (SortTile *)ctx->sorttab.p,
                         (int2 *)ctx->bintab.p, status, need, stats + 6,
                         (unsigned long long *)ctx->sticky.p, st));
-        int *wide = (int *)ctx->wide.p + k;
-        CKC(cudaMemsetAsync(wide, 0, sizeof(int), st));
         CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
                                  cams, ctx->camtab.p, PP, (const uint32_t *)ctx->masks.p,
                                  (const uint32_t *)ctx->woff.p, recs, with_d,
                                  (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p,
-                                 (uint32_t *)ctx->oidx.p, wide, std::log(cfg.alpha_min), status,
+                                 (uint32_t *)ctx->oidx.p, std::log(cfg.alpha_min), status,
                                  ch.max_deg, st));
         if (E) CKC(cudaEventRecord(E[1], st));
         if (a.upto == UPTO_PROJECT) break;
-        CKC(launch_sort_depth((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
-                              (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
-                              (long long)std::min<long long>(ctx->cap_survivors,
-                                                             (long long)(ctx->keys.cap / 4)),
-                              (const long long *)ctx->segstart.p,
-                              (const long long *)ctx->segcount.p, (const int *)ctx->sorttiles.p,
-                              ch.m, ch.sort_grid, (uint32_t *)ctx->sorthist.p, wide, st,
-                              (const int *)ctx->sorttiles.p + ch.m, (const SortTile *)ctx->sorttab.p));
-        // equal depths in the Gaussians' index order (the sort left them in storage order)
-        int *nruns = (int *)ctx->nruns.p + k;
-        CKC(cudaMemsetAsync(nruns, 0, sizeof(int), st));
-        CKC(launch_tie_order((uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
-                             (uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
-                             (const uint32_t *)ctx->oidx.p, (const SortTile *)ctx->sorttab.p,
-                             (const int *)ctx->sorttiles.p + ch.m, ch.sort_grid, ctx->ties.p,
-                             (long long)(ctx->ties.cap / tie_run_bytes()), nruns, st));
+        // every camera's survivors in (depth, caller index) order, into tkeys / tvals
+        CKC(launch_depth_order((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
+                               (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
+                               (const uint32_t *)ctx->oidx.p, (const SortTile *)ctx->sorttab.p,
+                               (const int *)ctx->sorttiles.p, ch.m, ch.sort_grid,
+                               (uint32_t *)ctx->dcount.p, ctx->dwin.p, ctx->dbig.p,
+                               (long long)(ctx->dbig.cap / depth_big_bytes()), ctx->ties.p,
+                               (long long)(ctx->ties.cap / tie_run_bytes()),
+                               (int *)ctx->nruns.p + 2 * k, st));
         if (E) CKC(cudaEventRecord(E[2], st));
         const bool persist = ch.persistent && a.upto == UPTO_ALL;
         if (!persist)
@@ -743,8 +741,10 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->keys,     &ctx->vals,  &ctx->tkeys,   &ctx->tvals,   &ctx->rrect, &ctx->srect,
                       &ctx->bitmap,   &ctx->tables, &ctx->status, &ctx->blkpre,
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
-                      &ctx->sorttiles, &ctx->sorthist, &ctx->sorttab, &ctx->bintab, &ctx->camtab, &ctx->blur_vm,
-                      &ctx->wide,     &ctx->oidx,  &ctx->ties,    &ctx->nruns,
+                      &ctx->sorttiles, &ctx->seg_tk, &ctx->seg_tv, &ctx->seg_tiles, &ctx->seg_hist,
+                      &ctx->sorttab, &ctx->bintab, &ctx->camtab, &ctx->blur_vm,
+                      &ctx->oidx,     &ctx->dcount, &ctx->dwin,   &ctx->dbig,    &ctx->ties,
+                      &ctx->nruns,    &ctx->pq,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -1428,16 +1428,17 @@ gs_status gs_sort_segments(gs_context *ctx, uint32_t *keys, uint32_t *vals, int6
         nt += sort_tiles_for(hc[i]);
     }
     tiles[n_seg] = nt;
-    CKS(grow(ctx, ctx->tkeys, (size_t)std::max<int64_t>(n, 1) * 4));
-    CKS(grow(ctx, ctx->tvals, (size_t)std::max<int64_t>(n, 1) * 4));
-    CKS(grow(ctx, ctx->sorttiles, tiles.size() * sizeof(int)));
-    CKS(grow(ctx, ctx->sorthist, (size_t)std::max(nt, 1) * 256 * 4));
-    CKC(cudaMemcpyAsync(ctx->sorttiles.p, tiles.data(), tiles.size() * sizeof(int),
+    // scratch of its own: a render may still be running on the workspace
+    CKS(grow(ctx, ctx->seg_tk, (size_t)std::max<int64_t>(n, 1) * 4));
+    CKS(grow(ctx, ctx->seg_tv, (size_t)std::max<int64_t>(n, 1) * 4));
+    CKS(grow(ctx, ctx->seg_tiles, tiles.size() * sizeof(int)));
+    CKS(grow(ctx, ctx->seg_hist, (size_t)std::max(nt, 1) * 256 * 4));
+    CKC(cudaMemcpyAsync(ctx->seg_tiles.p, tiles.data(), tiles.size() * sizeof(int),
                         cudaMemcpyHostToDevice, st));
-    CKC(launch_sort_segments(keys, vals, (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
+    CKC(launch_sort_segments(keys, vals, (uint32_t *)ctx->seg_tk.p, (uint32_t *)ctx->seg_tv.p,
                              (const long long *)seg_start, (const long long *)seg_count,
-                             (const int *)ctx->sorttiles.p, n_seg, nt,
-                             (uint32_t *)ctx->sorthist.p, st));
+                             (const int *)ctx->seg_tiles.p, n_seg, nt,
+                             (uint32_t *)ctx->seg_hist.p, st));
     CKC(cudaStreamSynchronize(st));  // the host tile table must outlive the copy
     return GS_OK;
 }

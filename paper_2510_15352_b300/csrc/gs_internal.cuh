@@ -124,7 +124,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams, const void *camtab,
                                  ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, float4 *rec, int rec_d,
-                                 uint2 *srect, uint32_t *keys, uint32_t *oidx, int *wide,
+                                 uint2 *srect, uint32_t *keys, uint32_t *oidx,
                                  float ln_alpha_min, const int *status, int max_deg,
                                  cudaStream_t s);
 
@@ -151,35 +151,38 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
                                  int n_tiles, uint32_t *hist, cudaStream_t s,
                                  const int *n_tiles_dev = nullptr, bool index_vals = false);
 
-// The render's depth sort: keys are z bits minus the near plane's bits; three
-// passes (9, 9, 8 bits) and, when *wide, a fourth pass and a copy. The sorted
-// keys and values end in tmp_keys / tmp_vals. hist needs 512 uint32 per tile.
 // One sort tile of a segmented sort: the segment's first key, the tile's
-// first key within the segment and its key count (a direct lookup for the sort
-// kernels, whose blocks would otherwise search the segment table first).
+// first key within the segment, its key count, the segment's count and index
+// (a direct lookup for the sort kernels, whose blocks would otherwise search
+// the segment table first).
 struct SortTile {
     long long seg_base;
     int t0, nk;
     int seg_n;  // keys of the whole segment
-    int pad;
+    int seg;    // the segment's index
 };
-cudaError_t launch_sort_depth(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
-                              uint32_t *tmp_vals, long long n_keys, const long long *seg_start,
-                              const long long *seg_count, const int *tile_start, int n_seg,
-                              int n_tiles, uint32_t *hist, const int *wide, cudaStream_t s,
-                              const int *n_tiles_dev, const SortTile *tiles);
 
-// Equal depths after the depth sort (k_ties.cu): within every run of equal
-// keys of a segment, the values (slots) are put in the order of the Gaussians'
-// caller indices (oidx[seg_base + slot]); short runs in place, longer ones
-// listed (runs: capacity entries of tie_run_bytes(), *n_runs zeroed before) and sorted one block
-// per run. keys / vals are the sorted arrays; scratch_k / scratch_v the sort's
-// other buffers (free after it).
-size_t tie_run_bytes();  // bytes per listed long run
-cudaError_t launch_tie_order(uint32_t *keys, uint32_t *vals, uint32_t *scratch_k,
-                             uint32_t *scratch_v, const uint32_t *oidx, const SortTile *tiles,
-                             const int *n_tiles_dev, int grid, void *runs, long long capacity,
-                             int *n_runs, cudaStream_t s);
+// The render's depth order (k_depth.cu): every segment (camera) of keys (z bits
+// minus the near plane's bits, slot order) sorted by (key, oidx[seg_base +
+// slot]) into sk / sv (keys, slots); keys / vals are scratch afterwards.
+// vals, sk and sv hold at least 4 elements past the chunk's survivors (the
+// window pass copies 16-byte pieces).
+// tiles / tile_start: the chunk's SortTile table and per-segment tile prefix
+// (tile_start[m] the total, on the device). Work buffers: count
+// (DEPTH_BUCKETS uint32 per segment), win (SORT_TILE_KEYS / DEPTH_WINDOW
+// entries of depth_window_bytes() per sort tile), big (big_cap entries of
+// depth_big_bytes()), runs (run_cap entries of tie_run_bytes()), counters
+// (2 ints, zeroed by the call). grid: blocks of the per-tile kernels.
+size_t depth_window_bytes();
+size_t depth_big_bytes();
+size_t tie_run_bytes();
+constexpr int DEPTH_BUCKETS = 2048;  // per camera
+constexpr int DEPTH_WINDOW = 512;    // window stride (SORT_TILE_KEYS / 4)
+cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
+                               const uint32_t *oidx, const SortTile *tiles, const int *tile_start,
+                               int m, int grid, uint32_t *count, void *win,
+                               void *big, long long big_cap, void *runs, long long run_cap,
+                               int *counters, cudaStream_t s);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
 // Intrinsics scaled by 1/f (see k_blur.cu).

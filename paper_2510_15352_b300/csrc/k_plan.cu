@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(PT)
             const int t0 = (g - b_st[lo]) * SORT_TILE_KEYS;
             stiles[carry_st + g] = SortTile{b_off[lo], t0,
                                             (int)min((long long)SORT_TILE_KEYS, b_cnt[lo] - t0),
-                                            (int)b_cnt[lo], 0};
+                                            (int)b_cnt[lo], b + lo};
         }
         __syncthreads();
         if (tid == 0) {

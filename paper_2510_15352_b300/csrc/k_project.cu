@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
                     const uint32_t *__restrict__ masks, const uint32_t *__restrict__ woff,
                     float4 *__restrict__ rec, int with_d, uint2 *__restrict__ srect,
                     uint32_t *__restrict__ keys, uint32_t *__restrict__ oidx,
-                    int *__restrict__ wide, float ln_alpha_min, const int *__restrict__ status) {
+                    float ln_alpha_min, const int *__restrict__ status) {
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
     if (g0 >= gr.n) return;
@@ -746,11 +746,10 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
         srect[at] = rect;
         // depth key: float bits of z minus those of the near plane (z > near, so
         // non-negative and in the same order); its value, the slot, is implied
-        // by the position. Keys of 2^26 or more need the depth sort's 4th pass.
+        // by the position.
         const uint32_t kz = __float_as_uint(pr.z) - __float_as_uint(P.near_plane);
         keys[at] = kz;
         oidx[at] = gidx;
-        if (kz >= (1u << 26)) atomicOr(wide, 1);
     }
 }
 
@@ -799,7 +798,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  const SceneDev *scenes, const CamInfo *cams, const void *camtab,
                                  ProjParams P,
                                  const uint32_t *masks, const uint32_t *woff, float4 *rec, int with_d,
-                                 uint2 *srect, uint32_t *keys, uint32_t *oidx, int *wide,
+                                 uint2 *srect, uint32_t *keys, uint32_t *oidx,
                                  float ln_alpha_min, const int *status, int max_deg,
                                  cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
@@ -809,7 +808,7 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
     cudaFuncSetAttribute(k_project_write<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                          3 * (D + 1) * (D + 1) * PROJ_THREADS * 4);                                  \
     k_project_write<D><<<grid, PROJ_THREADS, 3 * (D + 1) * (D + 1) * PROJ_THREADS * 4, s>>>(      \
-        groups, scenes, cams, ct, P, masks, woff, rec, with_d, srect, keys, oidx, wide,           \
+        groups, scenes, cams, ct, P, masks, woff, rec, with_d, srect, keys, oidx,                 \
         ln_alpha_min, status)
     switch (max_deg) {
         case 0: GS_WRITE(0); break;

@@ -1,20 +1,8 @@
 // k_sort.cu -- segmented, stable LSD radix sort of uint32 keys with uint32
-// values: the (camera, depth, index) part of the renderer's sort order.
+// values (gs_sort_segments, the scene set-up's Morton order). The render's
+// depth order has its own kernels (k_depth.cu).
 //
-// Each camera's survivors form one segment, written in Gaussian-index order by
-// the projection pass; a stable sort on the depth key (float bits of z, which
-// are monotone for z > 0) then orders every segment by (depth, index), the
-// order in which the 3DGS renderer composites a tile (Sec. 3.2 of the paper
-// uses that renderer). The tile is the last, most significant digit of the
-// full key; the binning pass applies it as a stable counting sort.
-//
-// The generic sort (gs_sort_segments) makes four 8-bit passes, ping-ponging
-// between the caller's buffers and scratch. The render's depth sort takes keys
-// already offset by the near plane's bits (z > near, so key - bits(near) is
-// non-negative and keeps the order) and makes three passes of 9, 9 and 8 bits,
-// enough for every z below 2^26 ulps above the near plane (z < 51 m for a 0.2 m
-// near plane); a fourth 6-bit pass and a copy run only when the projection
-// flagged a wider key.
+// Four 8-bit passes, ping-ponging between the caller's buffers and scratch.
 // Every segment is cut into tiles of 2048 keys and each pass runs three
 // kernels over all tiles of all segments at once:
 //   k_sort_hist    -- digit histogram of every tile;
@@ -24,9 +12,8 @@
 //                     the tile is put in sorted order in shared memory, then
 //                     written out run by run (coalesced) at segment start +
 //                     run start + rank.
-// A block finds its tile's segment base, offset and key count in a per-tile
-// table when the caller provides one (the render's plan kernel writes it), else
-// by searching the segment table.
+// A block finds its tile's segment base, offset and key count by searching the
+// segment table.
 // Stable rank inside a tile: warp w takes keys [256 w, 256 w + 256) in rounds
 // of 32; a key's rank is (equal digits in earlier warps) + (equal digits in
 // earlier rounds of its warp) + (equal digits in lower lanes of its round,
@@ -56,33 +43,28 @@ __device__ __forceinline__ int find_seg(const int *__restrict__ tile_start, int 
     return lo;
 }
 
-// Where tile `tile` lies: from the SortTile table when there is one (one
-// load), else by searching the segment table.
-__device__ __forceinline__ SortTile tile_of(const SortTile *__restrict__ tab,
-                                            const long long *__restrict__ seg_start,
+// Where tile `tile` lies, from the segment table.
+__device__ __forceinline__ SortTile tile_of(const long long *__restrict__ seg_start,
                                             const long long *__restrict__ seg_count,
                                             const int *__restrict__ tile_start, int n_seg, int tile) {
-    if (tab) return tab[tile];
     const int s = find_seg(tile_start, n_seg, tile);
     const int t0 = (tile - tile_start[s]) * TK;
     return SortTile{seg_start[s], t0, (int)min((long long)TK, seg_count[s] - t0),
-                    (int)seg_count[s], 0};
+                    (int)seg_count[s], s};
 }
 
-// Digit histogram of every tile: BITS-bit digit at `shift`. With a skip flag
-// that is zero, the pass does nothing (an optional pass of the depth sort).
+// Digit histogram of every tile: BITS-bit digit at `shift`.
 template <int BITS>
 __global__ void __launch_bounds__(ST)
     k_sort_hist(const uint32_t *__restrict__ keys, const long long *__restrict__ seg_start,
                 const long long *__restrict__ seg_count, const int *__restrict__ tile_start,
                 int n_seg, int shift, uint32_t *__restrict__ hist, const int *__restrict__ nt_dev,
-                int nt_host, const int *__restrict__ run, const SortTile *__restrict__ tab) {
+                int nt_host) {
     constexpr int ND = 1 << BITS;
     __shared__ uint32_t h[ND];
-    if (run && !*run) return;
     const int nt = nt_dev ? *nt_dev : nt_host;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const SortTile T = tile_of(tab, seg_start, seg_count, tile_start, n_seg, tile);
+    const SortTile T = tile_of(seg_start, seg_count, tile_start, n_seg, tile);
     const uint32_t *k = keys + T.seg_base + T.t0;
     for (int d = threadIdx.x; d < ND; d += ST) h[d] = 0;
     uint32_t kv[SIPT];
@@ -105,11 +87,9 @@ __global__ void __launch_bounds__(ST)
 // hist[tile][d] becomes the offset (within the segment) of the run of digit d
 // of that tile.
 template <int BITS>
-__global__ void __launch_bounds__(1 << BITS, 1024 >> BITS)  // 64 registers: 2 or 4 blocks per SM
-    k_sort_offsets(const int *__restrict__ tile_start, uint32_t *__restrict__ hist,
-                   const int *__restrict__ run) {
+__global__ void __launch_bounds__(1 << BITS, 1024 >> BITS)  // 64 registers: 4 blocks per SM
+    k_sort_offsets(const int *__restrict__ tile_start, uint32_t *__restrict__ hist) {
     constexpr int ND = 1 << BITS, NWD = ND / 32;
-    if (run && !*run) return;
     const int s = blockIdx.x, d = threadIdx.x, lane = d & 31, warp = d >> 5;
     const int t0 = tile_start[s], t1 = tile_start[s + 1];
     uint32_t run_d = 0;
@@ -148,10 +128,8 @@ __global__ void __launch_bounds__(1 << BITS, 1024 >> BITS)  // 64 registers: 2 o
     }
 }
 
-// Five resident blocks per SM (48 registers, a few spilled): the scatter waits
-// on its loads more than it computes, and the extra block hides more of that
-// (5.3 -> 5.0 ms for the depth sort of 1,024 cameras; six blocks spill more
-// and are slower).
+// Five resident blocks per SM: the scatter waits on its loads more than it
+// computes, and the extra block hides more of that.
 template <int BITS>
 __global__ void __launch_bounds__(ST, 5)
     k_sort_scatter(const uint32_t *__restrict__ sk, const uint32_t *__restrict__ sv,
@@ -159,7 +137,7 @@ __global__ void __launch_bounds__(ST, 5)
                    const long long *__restrict__ seg_start, const long long *__restrict__ seg_count,
                    const int *__restrict__ tile_start, int n_seg, int shift,
                    const uint32_t *__restrict__ offs, const int *__restrict__ nt_dev, int nt_host,
-                   int index_vals, const int *__restrict__ run, const SortTile *__restrict__ tab) {
+                   int index_vals) {
     constexpr int ND = 1 << BITS, DPT = ND / ST;  // digits per thread (1 or 2)
     static_assert(ND % ST == 0, "digits are a multiple of the block size");
     __shared__ uint32_t wcnt[SNW][ND];
@@ -167,11 +145,10 @@ __global__ void __launch_bounds__(ST, 5)
     __shared__ uint32_t tmove[ND];  // run start in the segment minus tdig (>= 0)
     __shared__ uint32_t dsum[SNW];
     __shared__ uint32_t skey[TK], sval[TK];
-    if (run && !*run) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = nt_dev ? *nt_dev : nt_host;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const SortTile T = tile_of(tab, seg_start, seg_count, tile_start, n_seg, tile);
+    const SortTile T = tile_of(seg_start, seg_count, tile_start, n_seg, tile);
     const long long base = T.seg_base;
     const long long t0 = T.t0;
     const long long i0 = t0 + (long long)warp * (32 * SIPT);
@@ -276,30 +253,17 @@ __global__ void __launch_bounds__(ST, 5)
     }
 }
 
-// Copy of the values (and keys) of every segment, src -> dst, when *run.
-__global__ void k_sort_copy(const uint32_t *__restrict__ sk, const uint32_t *__restrict__ sv,
-                            uint32_t *__restrict__ dk, uint32_t *__restrict__ dv, long long n,
-                            const int *__restrict__ run) {
-    if (!*run) return;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        dk[i] = sk[i];
-        dv[i] = sv[i];
-    }
-}
-
 template <int BITS>
 void sort_pass(const uint32_t *sk, const uint32_t *sv, uint32_t *dk, uint32_t *dv,
                const long long *seg_start, const long long *seg_count, const int *tile_start,
                int n_seg, int n_tiles, int shift, uint32_t *hist, cudaStream_t s,
-               const int *n_tiles_dev, bool index_vals, const int *run,
-               const SortTile *tab = nullptr) {
+               const int *n_tiles_dev, bool index_vals) {
     k_sort_hist<BITS><<<n_tiles, ST, 0, s>>>(sk, seg_start, seg_count, tile_start, n_seg, shift,
-                                             hist, n_tiles_dev, n_tiles, run, tab);
-    k_sort_offsets<BITS><<<n_seg, 1 << BITS, 0, s>>>(tile_start, hist, run);
+                                             hist, n_tiles_dev, n_tiles);
+    k_sort_offsets<BITS><<<n_seg, 1 << BITS, 0, s>>>(tile_start, hist);
     k_sort_scatter<BITS><<<n_tiles, ST, 0, s>>>(sk, sv, dk, dv, seg_start, seg_count, tile_start,
                                                 n_seg, shift, hist, n_tiles_dev, n_tiles,
-                                                index_vals, run, tab);
+                                                index_vals);
 }
 
 }  // namespace
@@ -315,36 +279,12 @@ cudaError_t launch_sort_segments(uint32_t *keys, uint32_t *vals, uint32_t *tmp_k
     uint32_t *src_k = keys, *src_v = vals, *dst_k = tmp_keys, *dst_v = tmp_vals;
     for (int pass = 0; pass < 4; ++pass) {
         sort_pass<8>(src_k, src_v, dst_k, dst_v, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                     8 * pass, hist, s, n_tiles_dev, index_vals && pass == 0, nullptr);
+                     8 * pass, hist, s, n_tiles_dev, index_vals && pass == 0);
         uint32_t *t;
         t = src_k; src_k = dst_k; dst_k = t;
         t = src_v; src_v = dst_v; dst_v = t;
     }
     // four passes: the sorted data is back in keys / vals
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sort_depth(uint32_t *keys, uint32_t *vals, uint32_t *tmp_keys,
-                              uint32_t *tmp_vals, long long n_keys, const long long *seg_start,
-                              const long long *seg_count, const int *tile_start, int n_seg,
-                              int n_tiles, uint32_t *hist, const int *wide, cudaStream_t s,
-                              const int *n_tiles_dev, const SortTile *tiles) {
-    if (n_seg == 0 || n_tiles == 0) return cudaSuccess;
-    // bits 0-8, 9-17, 18-25: keys -> tmp -> keys -> tmp
-    sort_pass<9>(keys, vals, tmp_keys, tmp_vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 0, hist, s, n_tiles_dev, true, nullptr, tiles);
-    sort_pass<9>(tmp_keys, tmp_vals, keys, vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 9, hist, s, n_tiles_dev, false, nullptr, tiles);
-    sort_pass<8>(keys, vals, tmp_keys, tmp_vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 18, hist, s, n_tiles_dev, false, nullptr, tiles);
-    // bits 26-31 only when some key needs them (*wide): tmp -> keys, then back
-    sort_pass<8>(tmp_keys, tmp_vals, keys, vals, seg_start, seg_count, tile_start, n_seg, n_tiles,
-                 26, hist, s, n_tiles_dev, false, wide, tiles);
-    if (n_keys > 0) {
-        const int grid = (int)std::min<long long>((n_keys + 255) / 256, 148LL * 8);
-        k_sort_copy<<<grid, 256, 0, s>>>(keys, vals, tmp_keys, tmp_vals, n_keys, wide);
-    }
-    // the sorted data is in tmp_keys / tmp_vals
     return cudaGetLastError();
 }
 

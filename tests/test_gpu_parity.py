@@ -400,10 +400,10 @@ def test_host_entry_point_equals_device_entry_point(torch, R):
         R.remove_scene(sid)
 
 
-def test_far_depths_take_the_fourth_sort_pass(torch, R, orc):
-    """Depths from 0.5 m to 400 m: keys (z bits minus the near plane's) above
-    2^26 switch on the depth sort's 4th pass; pixels and tile lists still match
-    the oracle."""
+def test_far_depths_share_the_last_bucket(torch, R, orc):
+    """Depths from 0.5 m to 400 m: keys (z bits minus the near plane's) of 2^26
+    and more all fall in the depth order's last bucket, which is then ordered by
+    the full key; pixels and tile lists still match the oracle."""
     rng = np.random.default_rng(17)
     n = 600
     z = np.exp(rng.uniform(np.log(0.5), np.log(400.0), n))
@@ -421,6 +421,62 @@ def test_far_depths_take_the_fourth_sort_pass(torch, R, orc):
         assert float(np.max(np.where(T[0] < 1, depth[0], 0))) > 0.0
         off_g, gl = R.debug_tile_lists(sid, dev(torch, vm), dev(torch, it), 64, 48, cap=1_000_000)
         assert check_tile_lists(off_g, gl, orc.tile_lists(scene, vm, it, 64, 48, bands=BANDS)) <= 1
+    finally:
+        R.remove_scene(sid)
+
+
+def _one_bucket_scene(gsmod, n_distinct, n_equal, seed):
+    """Gaussians whose float32 depths all fall in one bucket of the depth order
+    (key = bits(z) - bits(near), bucket = key >> 16, seen by the identity
+    camera, for which z is the mean's z exactly): n_distinct depths a few ulps
+    apart plus n_equal copies of one of them, with caller indices in random
+    order against depth. Small footprints spread over a 64 x 48 view."""
+    rng = np.random.default_rng(seed)
+    nb = int(np.float32(gsmod.default_config().near_plane).view(np.uint32))
+    k0 = ((int(np.float32(2.0).view(np.uint32)) - nb) >> 16) << 16  # a bucket's first key
+    step = 65535 // n_distinct
+    offs = np.arange(n_distinct, dtype=np.int64) * step
+    offs = np.concatenate([offs, np.full(n_equal, offs[n_distinct // 2])])
+    z = (nb + k0 + offs).astype(np.uint32).view(np.float32).astype(np.float64)
+    n = len(z)
+    perm = rng.permutation(n)
+    z = z[perm]
+    xy = np.column_stack([rng.uniform(-0.9, 0.9, n), rng.uniform(-0.65, 0.65, n)])
+    means = np.column_stack([xy, z])
+    return scene_from(means, [math.log(0.012)] * 3, [1, 0, 0, 0], rng.normal(-1.0, 0.5, n),
+                      colours=rng.uniform(0, 1, (n, 3)))
+
+
+@pytest.mark.parametrize("n_distinct,n_equal", [(9000, 0), (400, 150)])
+def test_crowded_depth_bucket(torch, gsmod, R, orc, n_distinct, n_equal):
+    """One bucket of 9,000 distinct depths (more than a shared-memory window
+    holds), and one of 400 depths plus 150 at one depth (a counting-sort bin too
+    crowded for the insertion, and a run of equal keys longer than the in-place
+    limit): both go to the one-block sort in global memory. Tile lists are the
+    oracle's (z, index) order exactly and pixels match."""
+    scene = _one_bucket_scene(gsmod, n_distinct, n_equal, seed=n_distinct + n_equal)
+    W, H = 64, 48
+    vm, it = identity_camera(W, H, 60.0)
+    # depths are exact in float32 and float64 (identity camera): no depth band
+    bands = O.Bands(px_abs=BANDS.px_abs, px_rel=BANDS.px_rel, z_abs=0.0, z_rel=0.0,
+                    ln_alpha=BANDS.ln_alpha, T_rel=BANDS.T_rel, max_flips=BANDS.max_flips,
+                    max_leaves=BANDS.max_leaves)
+    sid = R.add_scene(scene)
+    try:
+        off, gl = R.debug_tile_lists(sid, dev(torch, vm), dev(torch, it), W, H, cap=4_000_000)
+        ref = orc.tile_lists(scene, vm, it, W, H, bands=bands)
+        longest = 0
+        for t in range(len(off) - 1):
+            o0, o1 = ref["off"][t], ref["off"][t + 1]
+            fl, g = ref["flags"][o0:o1], ref["g"][o0:o1]
+            ambiguous = set(g[(fl & 2) != 0].tolist())  # membership within rounding
+            want = [int(x) for x, f in zip(g, fl) if (f & 1) and int(x) not in ambiguous]
+            got = [int(x) for x in gl[off[t]:off[t + 1]] if int(x) not in ambiguous]
+            assert got == want, (t, got[:10], want[:10])
+            longest = max(longest, len(want))
+        assert longest > 50
+        rgb, depth, T = render_np(torch, R, sid, vm[None], it[None], W, H)
+        assert_camera_parity(rgb[0], depth[0], T[0], orc.render(scene, vm, it, W, H, bands=bands))
     finally:
         R.remove_scene(sid)
 
