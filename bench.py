@@ -784,7 +784,10 @@ def run_b300(args):
                       "composite_warp_iters": cst["warp_iters"],
                       "composite_warp_iters_box": cst["warp_iters_box"],
                       "composite_warp_iters_blend": cst["warp_iters_blend"],
-                      "intersections_per_step": cst["intersections"]},
+                      "intersections_per_step": cst["intersections"],
+                      "depth_order": {"windows_to_block_sort": cst["sort_windows_listed"],
+                                      "equal_key_runs": cst["sort_equal_runs"],
+                                      "runs_over_32": cst["sort_long_runs"]}},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -131,6 +131,12 @@ typedef struct gs_stats {
                                  pixels; only with count_pairs */
     int64_t warp_iters_box;   /* of those, Gaussians whose alpha box meets the warp's rows */
     int64_t warp_iters_blend; /* of those, Gaussians some lane of the warp blends */
+    int64_t sort_windows_listed; /* depth-order windows left to the one-block sort in global
+                                    memory (over 2,048 keys, over 512 buckets, or a bin of
+                                    more than 32 keys) */
+    int64_t sort_equal_runs;  /* runs of equal depth keys the window pass listed for ordering
+                                 by caller index */
+    int64_t sort_long_runs;   /* runs of more than 32 equal keys (one block each) */
 } gs_stats;
 
 typedef struct gs_context gs_context;

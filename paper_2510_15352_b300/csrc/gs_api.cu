@@ -60,7 +60,7 @@ struct gs_context {
     DevBuf tables, blkpre, segstart, segcount, stats, status, sorttiles, sorttab, bintab, camtab;
     DevBuf seg_tk, seg_tv, seg_tiles, seg_hist;  // gs_sort_segments' own scratch
     DevBuf oidx;  // per survivor slot: the Gaussian's caller index (depth tie-break)
-    DevBuf dcount, dwin, dbig;  // depth order: bucket counts, windows, listed windows
+    DevBuf dcount, dwin, dbig, deq;  // depth order: bucket counts, windows, listed windows / runs
     DevBuf ties, nruns;  // long runs of equal depth keys (list); per chunk 2 list counts
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
@@ -304,7 +304,8 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     DevBuf *held[] = {&ctx->masks,    &ctx->woff,     &ctx->counts,    &ctx->camtab, &ctx->rec,
                       &ctx->srect,    &ctx->rrect,    &ctx->keys,      &ctx->vals,   &ctx->tkeys,
                       &ctx->tvals,    &ctx->bitmap,   &ctx->dcount,    &ctx->sorttab,
-                      &ctx->bintab,   &ctx->dwin,     &ctx->dbig,      &ctx->blkpre,
+                      &ctx->bintab,   &ctx->dwin,     &ctx->dbig,      &ctx->deq,
+                      &ctx->blkpre,
                       &ctx->sorttiles,
                       &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status,
                       &ctx->oidx,     &ctx->ties,     &ctx->nruns,    &ctx->pq};
@@ -326,7 +327,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->tvals, (Sx + 4) * 4));
     CKS(grow(ctx, ctx->oidx, Sx * 4));
     CKS(grow(ctx, ctx->ties, (Sx / 33 + 2) * tie_run_bytes()));
-    CKS(grow(ctx, ctx->nruns, 2 * (P.chunks.size() + 1) * sizeof(int)));
+    CKS(grow(ctx, ctx->nruns, 3 * (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->pq, (size_t)(m + 2) * sizeof(int)));
     // bounds implied by S: bitmap words <= max_sup * (S/32 + m), sort tiles <= S/2048 + m
     CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
@@ -336,6 +337,9 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     const size_t windows = sort_tiles * (SORT_TILE_KEYS / DEPTH_WINDOW);
     CKS(grow(ctx, ctx->dwin, windows * depth_window_bytes()));
     CKS(grow(ctx, ctx->dbig, windows * depth_big_bytes()));
+    // runs of equal depth keys: about one per 500 survivors on the full-size
+    // workloads; a window orders its runs itself when the list is full
+    CKS(grow(ctx, ctx->deq, (Sx / 64 + 64) * depth_eq_bytes()));
     CKS(grow(ctx, ctx->bintab, (Sx / BIN_RANKS_SMALL + m + 1) * sizeof(int2)));
     CKS(grow(ctx, ctx->blkpre, (size_t)(m + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->sorttiles, (size_t)(m + 1) * sizeof(int)));
@@ -408,11 +412,12 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         CKC(launch_depth_order((uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
                                (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
                                (const uint32_t *)ctx->oidx.p, (const SortTile *)ctx->sorttab.p,
-                               (const int *)ctx->sorttiles.p, ch.m, ch.sort_grid,
-                               (uint32_t *)ctx->dcount.p, ctx->dwin.p, ctx->dbig.p,
-                               (long long)(ctx->dbig.cap / depth_big_bytes()), ctx->ties.p,
-                               (long long)(ctx->ties.cap / tie_run_bytes()),
-                               (int *)ctx->nruns.p + 2 * k, st));
+                               (const int *)ctx->sorttiles.p, (const long long *)ctx->segstart.p,
+                               ch.m, ch.sort_grid, (uint32_t *)ctx->dcount.p, ctx->dwin.p,
+                               ctx->dbig.p, (long long)(ctx->dbig.cap / depth_big_bytes()),
+                               ctx->deq.p, (long long)(ctx->deq.cap / depth_eq_bytes()),
+                               ctx->ties.p, (long long)(ctx->ties.cap / tie_run_bytes()),
+                               (int *)ctx->nruns.p + 3 * k, st));
         if (E) CKC(cudaEventRecord(E[2], st));
         const bool persist = ch.persistent && a.upto == UPTO_ALL;
         if (!persist)
@@ -641,7 +646,7 @@ gs_status validate(gs_context *ctx, int n, const int32_t *scene_ids, const void 
 
 extern "C" {
 
-int32_t gs_abi_version(void) { return 4; }
+int32_t gs_abi_version(void) { return 5; }
 
 const char *gs_status_string(gs_status s) {
     switch (s) {
@@ -743,7 +748,8 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->segstart, &ctx->segcount, &ctx->stats, &ctx->h_vm,   &ctx->h_in,
                       &ctx->sorttiles, &ctx->seg_tk, &ctx->seg_tv, &ctx->seg_tiles, &ctx->seg_hist,
                       &ctx->sorttab, &ctx->bintab, &ctx->camtab, &ctx->blur_vm,
-                      &ctx->oidx,     &ctx->dcount, &ctx->dwin,   &ctx->dbig,    &ctx->ties,
+                      &ctx->oidx,     &ctx->dcount, &ctx->dwin,   &ctx->dbig,    &ctx->deq,
+                      &ctx->ties,
                       &ctx->nruns,    &ctx->pq,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
@@ -1258,6 +1264,17 @@ gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
         ctx->last.warp_iters_box = (int64_t)h[4];
         ctx->last.warp_iters_blend = (int64_t)h[5];
         ctx->last.survivors = (int64_t)h[6];
+        // the depth order's lists, per chunk: long runs, listed windows, equal runs
+        const int nc = ctx->last.n_chunks;
+        if (nc > 0 && ctx->nruns.p && ctx->nruns.cap >= 3 * (size_t)nc * sizeof(int)) {
+            std::vector<int> cnt(3 * (size_t)nc);
+            CKC(cudaMemcpy(cnt.data(), ctx->nruns.p, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost));
+            for (int c = 0; c < nc; ++c) {
+                ctx->last.sort_long_runs += cnt[3 * c];
+                ctx->last.sort_windows_listed += cnt[3 * c + 1];
+                ctx->last.sort_equal_runs += cnt[3 * c + 2];
+            }
+        }
         float ms[4] = {0, 0, 0, 0};
         for (int c = 0; c < ctx->ev_used; ++c) {
             cudaEvent_t *E = &ctx->ev[5 * c];

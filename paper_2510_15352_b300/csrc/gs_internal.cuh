@@ -164,25 +164,27 @@ struct SortTile {
 
 // The render's depth order (k_depth.cu): every segment (camera) of keys (z bits
 // minus the near plane's bits, slot order) sorted by (key, oidx[seg_base +
-// slot]) into sk / sv (keys, slots); keys / vals are scratch afterwards.
-// vals, sk and sv hold at least 4 elements past the chunk's survivors (the
-// window pass copies 16-byte pieces).
-// tiles / tile_start: the chunk's SortTile table and per-segment tile prefix
-// (tile_start[m] the total, on the device). Work buffers: count
+// slot]); the slots in that order end in sv. sk, keys and vals are scratch
+// (sk and sv hold at least 4 elements past the chunk's survivors: the window
+// pass copies 16-byte pieces). tiles / tile_start: the chunk's SortTile table
+// and per-segment tile prefix (tile_start[m] the total, on the device);
+// seg_start: the segments' first positions. Work buffers: count
 // (DEPTH_BUCKETS uint32 per segment), win (SORT_TILE_KEYS / DEPTH_WINDOW
 // entries of depth_window_bytes() per sort tile), big (big_cap entries of
-// depth_big_bytes()), runs (run_cap entries of tie_run_bytes()), counters
-// (2 ints, zeroed by the call). grid: blocks of the per-tile kernels.
+// depth_big_bytes()), eq (eq_cap entries of depth_eq_bytes()), runs (run_cap
+// entries of tie_run_bytes()), counters (3 ints, zeroed by the call). grid:
+// blocks of the per-tile kernels. Chunk positions must stay below 2^32.
 size_t depth_window_bytes();
 size_t depth_big_bytes();
+size_t depth_eq_bytes();
 size_t tie_run_bytes();
 constexpr int DEPTH_BUCKETS = 2048;  // per camera
 constexpr int DEPTH_WINDOW = 512;    // window stride (SORT_TILE_KEYS / 4)
 cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
                                const uint32_t *oidx, const SortTile *tiles, const int *tile_start,
-                               int m, int grid, uint32_t *count, void *win,
-                               void *big, long long big_cap, void *runs, long long run_cap,
-                               int *counters, cudaStream_t s);
+                               const long long *seg_start, int m, int grid, uint32_t *count,
+                               void *win, void *big, long long big_cap, void *eq, long long eq_cap,
+                               void *runs, long long run_cap, int *counters, cudaStream_t s);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
 // Intrinsics scaled by 1/f (see k_blur.cu).

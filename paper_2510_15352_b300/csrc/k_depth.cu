@@ -19,26 +19,30 @@
 //   k_depth_scatter each tile grouped by bucket in shared memory, its share of
 //                   every bucket reserved with one global atomic on the bucket's
 //                   cursor (after the pass, the cursor is the bucket's end), then
-//                   written out run by run: key, slot and the Gaussian's caller
-//                   index (read in slot order);
+//                   written out run by run (key and slot);
 //   k_depth_window  each window sorted in shared memory by a block of 256
 //                   threads: a counting sort in which a bucket of c keys gets c
 //                   bins (by the key's low bits), then each key's rank inside its
-//                   bin by (key, caller index); the slots are written back. The next
-//                   window is copied in (cp.async) while one is sorted. A window
-//                   of more than 2,048 keys, over more than 512 buckets, or with
-//                   a bin of more than 32 keys is listed instead;
+//                   bin (equal keys by staged position); the slots are written
+//                   back and every run of equal keys is listed. The next window
+//                   is copied in (cp.async) while one is sorted. A window of
+//                   more than 2,048 keys, over more than 512 buckets, or with a
+//                   bin of more than 32 keys is listed instead;
 //   k_depth_big     a listed window sorted by one block (stable LSD radix sort,
-//                   8 bits per pass, through global scratch), then its runs of
-//                   equal keys put in caller-index order (short runs in place,
-//                   longer ones listed);
-//   k_tie_long      a listed run of equal keys sorted by caller index, one block.
+//                   8 bits per pass, in shared memory up to 4,096 keys, else
+//                   through global scratch), then its runs of equal keys put in
+//                   caller-index order (short runs in place, longer ones listed);
+//   k_tie_long      a listed run of more than 32 equal keys sorted by caller
+//                   index, one block;
+//   k_tie_short     the runs of equal keys the window pass listed, one thread
+//                   each: slots in caller-index order.
 //
 // A bucket is 1/256 of the depth; on the full-size workloads the largest hold
-// about 1,400 keys, so windows average 512 keys and stay below 2,048. Listed
-// windows come from crowds of (nearly) equal depths. Nothing after the depth
-// order reads the sorted keys, so only the windows listed for the global
-// block sort keep theirs up to date.
+// about 1,400 keys, so windows average 512 keys and few pass 2,048 (about one
+// per camera goes to k_depth_big). Equal float32 depths are common: about
+// 1,800 runs per camera, nearly all pairs. Nothing after the depth order reads
+// the sorted keys, so only the windows listed for the block sort keep theirs
+// up to date.
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -58,7 +62,8 @@ constexpr int WPT = 8;                     // keys per thread of a window block
 constexpr int WCAP = WT * WPT;             // largest window sorted in shared memory (2048)
 constexpr int BIN_MAX = 32;                // largest bin the insertion finishes
 constexpr int SHORT = 32;                  // runs up to this length are ordered in place
-constexpr int LT = 1024;                   // threads of a global-memory block sort
+constexpr int LT = 1024;                   // threads of a listed window's block sort
+constexpr int BCAP = 4096;                 // listed windows up to this size sort in shared memory
 constexpr int LW = LT / 32;
 static_assert(NB % 1024 == 0, "the scan kernel's 1024 threads own NB / 1024 buckets each");
 static_assert(NB << BSH == 1 << 26, "the buckets cover keys below 2^26");
@@ -196,30 +201,27 @@ __global__ void __launch_bounds__(1024)
 
 // One sort tile per block pass: the tile grouped by bucket in shared memory
 // (ranks from shared-memory atomics), the tile's share of each bucket reserved
-// with one global atomic, then written out run by run: key, slot and the
-// Gaussian's caller index (read in slot order from oidx).
+// with one global atomic, then written out run by run (key and slot).
 __global__ void __launch_bounds__(BT)
-    k_depth_scatter(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ oidx,
-                    uint32_t *__restrict__ dk, uint32_t *__restrict__ dv,
-                    uint32_t *__restrict__ dox, const SortTile *__restrict__ tiles,
+    k_depth_scatter(const uint32_t *__restrict__ keys, uint32_t *__restrict__ dk,
+                    uint32_t *__restrict__ dv, const SortTile *__restrict__ tiles,
                     const int *__restrict__ n_tiles_dev, uint32_t *__restrict__ cursor) {
     constexpr int DPT = NB / BT;  // buckets per thread (8)
     __shared__ uint32_t h[NB];     // counts, then where each bucket starts in the tile
     __shared__ int move[NB];       // segment position of the tile's bucket run minus h
-    __shared__ uint32_t skey[SORT_TILE_KEYS], sval[SORT_TILE_KEYS], soid[SORT_TILE_KEYS];
+    __shared__ uint32_t skey[SORT_TILE_KEYS], sval[SORT_TILE_KEYS];
     __shared__ uint32_t ws[BT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = *n_tiles_dev;
     for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         const SortTile T = tiles[tile];
-        const uint32_t *k = keys + T.seg_base + T.t0, *o = oidx + T.seg_base + T.t0;
+        const uint32_t *k = keys + T.seg_base + T.t0;
         for (int d = tid; d < NB; d += BT) h[d] = 0;
-        uint32_t kv[BPT], ov[BPT], rk[BPT];
+        uint32_t kv[BPT], rk[BPT];
 #pragma unroll
         for (int r = 0; r < BPT; ++r) {
             const int j = r * BT + tid;
             kv[r] = j < T.nk ? k[j] : 0u;
-            ov[r] = j < T.nk ? o[j] : 0u;
         }
         __syncthreads();
 #pragma unroll
@@ -261,7 +263,6 @@ __global__ void __launch_bounds__(BT)
                 const uint32_t p = h[bucket_of(kv[r])] + rk[r];
                 skey[p] = kv[r];
                 sval[p] = (uint32_t)(T.t0 + j);  // the survivor's slot
-                soid[p] = ov[r];
             }
         }
         __syncthreads();
@@ -271,7 +272,6 @@ __global__ void __launch_bounds__(BT)
             const long long at = T.seg_base + move[bucket_of(key)] + p;
             dk[at] = key;
             dv[at] = sval[p];
-            dox[at] = soid[p];
         }
         __syncthreads();  // shared arrays are rebuilt for the block's next tile
     }
@@ -328,13 +328,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int SPAN = 512;  // buckets a window sorted here may span (its bounds are staged)
 
-// One stage: a window's keys, caller indices and slots, copied in 16-byte
-// pieces from the 16-byte boundary at or before the window's first position
-// (so element i of the window is at [shift + i], shift = first position mod
-// 4), and its buckets' bounds e[j] = start of bucket bf + j (e[nb] = end of the
-// last). Sizes are multiples of 4 words: every array stays 16-byte aligned.
+// One stage: a window's keys and slots, copied in 16-byte pieces from the
+// 16-byte boundary at or before the window's first position (so element i of
+// the window is at [shift + i], shift = first position mod 4), and its
+// buckets' bounds e[j] = start of bucket bf + j (e[nb] = end of the last).
+// Sizes are multiples of 4 words: every array stays 16-byte aligned.
 struct WinStage {
-    uint32_t k[WCAP + 8], o[WCAP + 8], v[WCAP + 8];
+    uint32_t k[WCAP + 8], v[WCAP + 8];
     uint32_t e[SPAN + 4];  // SPAN + 1 used
 };
 static_assert(sizeof(WinStage) % 16 == 0, "the bins after the stages are read as uint4");
@@ -366,7 +366,6 @@ __device__ __forceinline__ bool sorted_here(const int4 &w) {
 
 // Starts the copies of a window (if it is sorted here) into a stage.
 __device__ __forceinline__ void stage_item(const WinItem &I, const uint32_t *__restrict__ K,
-                                           const uint32_t *__restrict__ O,
                                            const uint32_t *__restrict__ V,
                                            const uint32_t *__restrict__ ends, WinStage *S) {
     if (sorted_here(I.w)) {
@@ -376,7 +375,6 @@ __device__ __forceinline__ void stage_item(const WinItem &I, const uint32_t *__r
         const int pieces = (int)((at - a0) + n + 3) >> 2;  // <= (WCAP + 6) / 4
         for (int c = threadIdx.x; c < pieces; c += WT) {
             cp_async16(S->k + 4 * c, K + a0 + 4 * c);
-            cp_async16(S->o + 4 * c, O + a0 + 4 * c);
             cp_async16(S->v + 4 * c, V + a0 + 4 * c);
         }
         // e[j] = ends[bf + j - 1] (0 for bucket 0's start)
@@ -392,34 +390,48 @@ __device__ __forceinline__ void stage_item(const WinItem &I, const uint32_t *__r
     cp_async_commit();
 }
 
+// A run of equal keys left for k_tie_short: its first position in the chunk
+// and (segment << 6) | length (length <= BIN_MAX: equal keys share a bin).
+struct EqRun {
+    uint32_t pos, seg_len;
+};
+constexpr int LOCAL_RUNS = 64;  // runs a window orders itself when the list is full
+
 // Each block takes windows blockIdx.x, + gridDim.x, ...; while it sorts one,
 // the next is copied into the other stage. ends[seg][b]: the end of bucket b
 // (the scatter's final cursor). A key of bucket b goes to one of the bucket's
-// c bins by its low bits (one bin per key on average); a key's rank inside
-// its bin is by (key, caller index). Only the slots are written back:
-// nothing after the depth order reads the keys.
-__global__ void __launch_bounds__(WT, 3)
-    k_depth_window(const uint32_t *__restrict__ K, const uint32_t *__restrict__ O,
-                   uint32_t *__restrict__ V, const SortTile *__restrict__ tiles,
+// c bins by its low bits (one bin per key on average); its place is the bin's
+// start plus the number of the bin's keys below it, equal keys by their staged
+// position. A run of equal keys is listed for k_tie_short, which puts it in
+// caller-index order (about one run per 500 keys on the full-size workloads);
+// when the list is full the window orders the run itself. Only the slots are
+// written back: nothing after the depth order reads the keys.
+__global__ void __launch_bounds__(WT, 4)
+    k_depth_window(const uint32_t *__restrict__ K, uint32_t *__restrict__ V,
+                   const uint32_t *__restrict__ oidx, const SortTile *__restrict__ tiles,
                    const int *__restrict__ n_tiles_dev, const int4 *__restrict__ win,
                    const uint32_t *__restrict__ ends, BigWin *__restrict__ big, long long big_cap,
-                   int *__restrict__ n_big) {
+                   int *__restrict__ n_big, EqRun *__restrict__ eq, long long eq_cap,
+                   int *__restrict__ n_eq) {
     extern __shared__ __align__(16) unsigned char wsm_raw[];
     WinStage *stages = reinterpret_cast<WinStage *>(wsm_raw);
     uint32_t *bins = reinterpret_cast<uint32_t *>(wsm_raw + 2 * sizeof(WinStage));
     __shared__ uint32_t wsum[WT / 32];
+    __shared__ uint2 local_runs[LOCAL_RUNS];  // (first position in the window, length)
+    __shared__ int n_local;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int items = WPS * *n_tiles_dev;
     const int G = gridDim.x;
     for (int b = tid; b < WT * BW_MAX; b += WT) bins[b] = 0;
+    if (tid == 0) n_local = 0;
     int it = blockIdx.x;
     WinItem cur = load_item(win, tiles, it, items);
-    stage_item(cur, K, O, V, ends, stages);
+    stage_item(cur, K, V, ends, stages);
     WinItem nxt = load_item(win, tiles, it + G, items);
     for (int st = 0; it < items; it += G, st ^= 1) {
         cp_async_wait_all();
         __syncthreads();  // this window is staged; the other stage is free
-        stage_item(nxt, K, O, V, ends, stages + (st ^ 1));
+        stage_item(nxt, K, V, ends, stages + (st ^ 1));
         const WinItem I = cur;
         cur = nxt;
         nxt = load_item(win, tiles, it + 2 * G, items);
@@ -430,14 +442,13 @@ __global__ void __launch_bounds__(WT, 3)
         }
         WinStage &S = stages[st];
         const int sh = (int)((I.base + I.w.x) & 3);
-        uint32_t kr[WPT], orr[WPT], vr[WPT], br[WPT];  // key, index, slot, bin | rank << 16
+        uint32_t kr[WPT], vr[WPT], br[WPT];  // key, slot, bin | rank << 16
 #pragma unroll
         for (int r = 0; r < WPT; ++r) {
             if (r * WT >= n) break;
             const int i = r * WT + tid;
             if (i < n) {
                 kr[r] = S.k[sh + i];
-                orr[r] = S.o[sh + i];
                 vr[r] = S.v[sh + i];
                 const uint32_t j = bucket_of(kr[r]) - (uint32_t)I.w.z;
                 const uint32_t lo = S.e[j], cnt = S.e[j + 1] - lo;
@@ -491,20 +502,15 @@ __global__ void __launch_bounds__(WT, 3)
             }
         }
         __syncthreads();
-        // keys and indices grouped by bin (the slots stay in registers) ...
+        // keys grouped by bin (the slots stay in registers) ...
 #pragma unroll
         for (int r = 0; r < WPT; ++r) {
             if (r * WT >= n) break;
-            if (r * WT + tid < n) {
-                const uint32_t p = bins[br[r] & 0xffffu] + (br[r] >> 16);
-                S.k[p] = kr[r];
-                S.o[p] = orr[r];
-            }
+            if (r * WT + tid < n) S.k[bins[br[r] & 0xffffu] + (br[r] >> 16)] = kr[r];
         }
         __syncthreads();
-        // ... then each key's place: its bin's start plus the number of the bin's
-        // keys below it in (key, caller index) order (a total order: the indices
-        // of a camera are distinct); the slot goes there
+        // ... then each key's place: its bin's start, plus the bin's keys below
+        // it, plus its equals staged before it; the slot goes there
 #pragma unroll
         for (int r = 0; r < WPT; ++r) {
             if (r * WT >= n) break;
@@ -512,16 +518,47 @@ __global__ void __launch_bounds__(WT, 3)
                 const uint32_t bin = br[r] & 0xffffu;
                 const uint32_t first = bins[bin];
                 const uint32_t end = bin + 1 < (uint32_t)n ? bins[bin + 1] : (uint32_t)n;
-                uint32_t p = first;
-                if (end - first > 1u)
-                    for (uint32_t j = first; j < end; ++j)
-                        p += (S.k[j] < kr[r] || (S.k[j] == kr[r] && S.o[j] < orr[r])) ? 1u : 0u;
-                S.v[p] = vr[r];
+                const uint32_t mine = first + (br[r] >> 16);
+                uint32_t less = 0, eq_before = 0, eq_all = 1;
+                if (end - first > 1u) {
+                    eq_all = 0;
+                    for (uint32_t j = first; j < end; ++j) {
+                        const uint32_t kj = S.k[j];
+                        less += kj < kr[r] ? 1u : 0u;
+                        eq_all += kj == kr[r] ? 1u : 0u;
+                        eq_before += (kj == kr[r] && j < mine) ? 1u : 0u;
+                    }
+                }
+                S.v[first + less + eq_before] = vr[r];
+                if (eq_all > 1u && eq_before == 0u) {  // the first of a run of equal keys
+                    const int q = atomicAdd(n_eq, 1);
+                    if (q < eq_cap) {
+                        eq[q] = EqRun{(uint32_t)(I.base + I.w.x + first + less),
+                                      ((uint32_t)I.seg << 6) | eq_all};
+                    } else {
+                        const int l = atomicAdd(&n_local, 1);
+                        if (l < LOCAL_RUNS) local_runs[l] = make_uint2(first + less, eq_all);
+                    }
+                }
             }
         }
         __syncthreads();
         for (int q = 0; q < BW; q += 4)
             *reinterpret_cast<uint4 *>(&bins[b0 + q]) = make_uint4(0, 0, 0, 0);
+        const int nl = n_local;
+        if (nl > 0) {  // the list was full: this window orders its runs itself
+            if (nl > LOCAL_RUNS) {  // (or, with too many of them, the global block sort does)
+                __syncthreads();
+                if (tid == 0) {
+                    n_local = 0;
+                    list_window(big, big_cap, n_big, I.base, I.w.x, n);
+                }
+                continue;
+            }
+            if (tid < nl) order_short_run(S.v + local_runs[tid].x, oidx, I.base, (int)local_runs[tid].y);
+            __syncthreads();
+            if (tid == 0) n_local = 0;
+        }
         uint32_t *ov = V + I.base + I.w.x;
         for (int i = tid; i < n; i += WT) ov[i] = S.v[i];
     }
@@ -653,30 +690,49 @@ __global__ void __launch_bounds__(LT)
                 const BigWin *__restrict__ big, long long big_cap, const int *__restrict__ n_big,
                 TieRun *__restrict__ runs, long long run_cap, int *__restrict__ n_runs) {
     __shared__ BlockSortSmem S;
+    extern __shared__ __align__(16) uint32_t bsm[];  // [4][BCAP]: a window and its scratch
     const long long nb = min((long long)*n_big, big_cap);
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
         const BigWin W = big[b];
         const long long at = W.seg_base + W.lo;
+        // a window of up to BCAP keys is sorted in shared memory
+        const bool local = W.n <= BCAP;
+        uint32_t *ak = local ? bsm : K + at, *av = local ? bsm + BCAP : V + at;
+        uint32_t *bk = local ? bsm + 2 * BCAP : SK + at, *bv = local ? bsm + 3 * BCAP : SV + at;
+        if (local) {
+            for (int i = threadIdx.x; i < W.n; i += LT) {
+                ak[i] = K[at + i];
+                av[i] = V[at + i];
+            }
+            __syncthreads();
+        }
         uint32_t lo, hi;
-        block_range(K + at, W.n, S, lo, hi);
+        block_range(ak, W.n, S, lo, hi);
         const int passes = passes_for(hi - lo);
-        if (passes) block_sort(K + at, V + at, SK + at, SV + at, W.n, lo, passes, S);
+        if (passes) block_sort(ak, av, bk, bv, W.n, lo, passes, S);
         __syncthreads();
-        const uint32_t *k = K + at;
         for (int p = threadIdx.x; p < W.n - 1; p += LT) {
-            const uint32_t kp = k[p];
-            if (k[p + 1] == kp && (p == 0 || k[p - 1] != kp)) {
+            const uint32_t kp = ak[p];
+            if (ak[p + 1] == kp && (p == 0 || ak[p - 1] != kp)) {
                 int e = p + 2;
-                while (e < W.n && k[e] == kp) ++e;
+                while (e < W.n && ak[e] == kp) ++e;
                 if (e - p <= SHORT)
-                    order_short_run(V + at + p, oidx, W.seg_base, e - p);
-                else
+                    order_short_run(av + p, oidx, W.seg_base, e - p);
+                else  // k_tie_long reads the run from K and V (written back below)
                     list_run(runs, run_cap, n_runs, at + p, W.seg_base, e - p);
             }
         }
         __syncthreads();
+        if (local) {
+            for (int i = threadIdx.x; i < W.n; i += LT) {
+                K[at + i] = ak[i];
+                V[at + i] = av[i];
+            }
+            __syncthreads();
+        }
     }
 }
+constexpr size_t BIG_SMEM = 4 * BCAP * sizeof(uint32_t);
 
 // A listed run of equal keys: the keys array holds the caller indices of its
 // slots while one block sorts them, and gets the key back at the end.
@@ -702,17 +758,30 @@ __global__ void __launch_bounds__(LT)
     }
 }
 
+// The listed runs of equal keys (one thread per run): slots in caller-index order.
+__global__ void k_tie_short(uint32_t *__restrict__ V, const uint32_t *__restrict__ oidx,
+                            const long long *__restrict__ seg_start, const EqRun *__restrict__ eq,
+                            long long eq_cap, const int *__restrict__ n_eq) {
+    const long long ne = min((long long)*n_eq, eq_cap);
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < ne;
+         r += (long long)gridDim.x * blockDim.x) {
+        const EqRun R = eq[r];
+        order_short_run(V + R.pos, oidx, seg_start[R.seg_len >> 6], (int)(R.seg_len & 63u));
+    }
+}
+
 }  // namespace
 
 size_t depth_window_bytes() { return sizeof(int4); }
 size_t depth_big_bytes() { return sizeof(BigWin); }
+size_t depth_eq_bytes() { return sizeof(EqRun); }
 size_t tie_run_bytes() { return sizeof(TieRun); }
 
 cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
                                const uint32_t *oidx, const SortTile *tiles, const int *tile_start,
-                               int m, int grid, uint32_t *count, void *win,
-                               void *big, long long big_cap, void *runs, long long run_cap,
-                               int *counters, cudaStream_t s) {
+                               const long long *seg_start, int m, int grid, uint32_t *count,
+                               void *win, void *big, long long big_cap, void *eq, long long eq_cap,
+                               void *runs, long long run_cap, int *counters, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     // per device, once: SM count and resident window blocks per SM
     static int sm_count[64] = {0}, win_per_sm[64] = {0};
@@ -727,6 +796,9 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
             e = cudaFuncSetAttribute(k_depth_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)WINDOW_SMEM);
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_depth_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)BIG_SMEM);
+        if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_depth_window, WT, WINDOW_SMEM);
         if (e != cudaSuccess) return e;
         win_per_sm[dev] = std::max(per, 1);
@@ -736,20 +808,24 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
     const int *n_tiles_dev = tile_start + m;
     e = cudaMemsetAsync(count, 0, (size_t)m * NB * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), s);
+    e = cudaMemsetAsync(counters, 0, 3 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     int4 *w4 = (int4 *)win;
     k_depth_count<<<grid, BT, 0, s>>>(keys, tiles, n_tiles_dev, count);
     k_depth_scan<<<m, 1024, 0, s>>>(count, w4, tile_start);
-    // keys, slots and caller indices in bucket order: sk, sv, vals
-    k_depth_scatter<<<grid, BT, 0, s>>>(keys, oidx, sk, sv, vals, tiles, n_tiles_dev, count);
+    k_depth_scatter<<<grid, BT, 0, s>>>(keys, sk, sv, tiles, n_tiles_dev, count);
     k_depth_window<<<std::min(WPS * grid, sms * win_per_sm[dev]), WT, WINDOW_SMEM, s>>>(
-        sk, vals, sv, tiles, n_tiles_dev, w4, count, (BigWin *)big, big_cap, counters + 1);
+        sk, sv, oidx, tiles, n_tiles_dev, w4, count, (BigWin *)big, big_cap, counters + 1,
+        (EqRun *)eq, eq_cap, counters + 2);
     // listed windows: keys and slots sorted through the free keys / vals arrays
-    k_depth_big<<<sms, LT, 0, s>>>(sk, sv, keys, vals, oidx, (const BigWin *)big, big_cap,
+    k_depth_big<<<sms, LT, BIG_SMEM, s>>>(sk, sv, keys, vals, oidx, (const BigWin *)big, big_cap,
                                    counters + 1, (TieRun *)runs, run_cap, counters);
     k_tie_long<<<sms, LT, 0, s>>>(sk, sv, keys, vals, oidx, (const TieRun *)runs, run_cap,
                                   counters);
+    // last: a listed window's runs are already in order when the block sort has
+    // written it, so ordering them again changes nothing
+    k_tie_short<<<sms * 4, 256, 0, s>>>(sv, oidx, seg_start, (const EqRun *)eq, eq_cap,
+                                        counters + 2);
     return cudaGetLastError();
 }
 

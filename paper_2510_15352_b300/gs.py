@@ -15,7 +15,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgs_b300.so")
-ABI_VERSION = 4
+ABI_VERSION = 5
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, \
     GS_ERR_NOT_FOUND = range(7)
@@ -52,7 +52,8 @@ class gs_stats(ctypes.Structure):
                 ("ms_bin", ctypes.c_float), ("ms_composite", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("reserved0", ctypes.c_int32),
                 ("warp_iters", ctypes.c_int64), ("warp_iters_box", ctypes.c_int64),
-                ("warp_iters_blend", ctypes.c_int64)]
+                ("warp_iters_blend", ctypes.c_int64), ("sort_windows_listed", ctypes.c_int64),
+                ("sort_equal_runs", ctypes.c_int64), ("sort_long_runs", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); the same set as include/gs.h declares

@@ -311,6 +311,11 @@ def test_equal_depths_follow_index_order(torch, R, orc, n):
             longest = max(longest, len(want))
         assert longest == n
         rgb, depth, T = render_np(torch, R, sid, vm[None], it[None], W, H)
+        st = R.stats()
+        if n <= 32:  # ordered after the window pass listed it
+            assert st["sort_equal_runs"] >= 1
+        else:  # a crowded bin: the one-block sort, a run of more than 32 keys
+            assert st["sort_windows_listed"] >= 1 and st["sort_long_runs"] >= 1
         assert_camera_parity(rgb[0], depth[0], T[0], orc.render(scene, vm, it, W, H, bands=bands))
     finally:
         R.remove_scene(sid)
@@ -476,6 +481,10 @@ def test_crowded_depth_bucket(torch, gsmod, R, orc, n_distinct, n_equal):
             longest = max(longest, len(want))
         assert longest > 50
         rgb, depth, T = render_np(torch, R, sid, vm[None], it[None], W, H)
+        st = R.stats()
+        assert st["sort_windows_listed"] >= 1  # the path under test ran
+        if n_equal > 32:
+            assert st["sort_long_runs"] >= 1
         assert_camera_parity(rgb[0], depth[0], T[0], orc.render(scene, vm, it, W, H, bands=bands))
     finally:
         R.remove_scene(sid)
