@@ -547,13 +547,13 @@ def test_errors_are_reported(torch, gsmod, R):
 # ------------------------------------------------------------- full size
 
 def test_full_size_workload_sampled_cameras(torch, R, orc):
-    """1M Gaussians (SH degree 3), 1,024 cameras at 640x480 in one call with
-    the default chunking (the benchmark's launch configuration); 16 cameras
+    """1M Gaussians (SH degree 3), 4,096 cameras at 640x480 in one call with
+    the default chunking (the benchmark's workload and launch configuration); 16 cameras
     drawn across the batch (seed 1) are checked against the oracle pixel by
     pixel. Every pixel must match the oracle's primary result, or, where the
     oracle met a near-threshold decision, one of its alternatives: no
     unresolved pixel is allowed. The counts are printed."""
-    scene, vm, it, W, H = synth.workload("single_1m_sh3_1024cam_640x480")
+    scene, vm, it, W, H = synth.workload("single_1m_sh3_4096cam_640x480")
     sid = R.add_scene(scene)
     try:
         rgb, depth, T = R.render(sid, dev(torch, vm), dev(torch, it), W, H, want_T=True)
