@@ -206,9 +206,10 @@ __global__ void __launch_bounds__(BT)
     k_depth_scatter(const uint32_t *__restrict__ keys, uint32_t *__restrict__ dk,
                     uint32_t *__restrict__ dv, const SortTile *__restrict__ tiles,
                     const int *__restrict__ n_tiles_dev, uint32_t *__restrict__ cursor) {
-    constexpr int DPT = NB / BT;  // buckets per thread (8)
-    __shared__ uint32_t h[NB];     // counts, then where each bucket starts in the tile
-    __shared__ int move[NB];       // segment position of the tile's bucket run minus h
+    constexpr int DPT = NB / BT;  // buckets per thread (8), read and written as uint4 pairs
+    static_assert(DPT == 8, "two uint4 per thread");
+    __shared__ __align__(16) uint32_t h[NB];  // counts, then where each bucket starts in the tile
+    __shared__ __align__(16) int move[NB];    // segment position of the tile's bucket run minus h
     __shared__ uint32_t skey[SORT_TILE_KEYS], sval[SORT_TILE_KEYS];
     __shared__ uint32_t ws[BT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -229,12 +230,18 @@ __global__ void __launch_bounds__(BT)
             rk[r] = r * BT + tid < T.nk ? atomicAdd(&h[bucket_of(kv[r])], 1u) : 0u;
         __syncthreads();
         // thread tid owns buckets DPT tid .. DPT tid + DPT - 1: reserve the
-        // tile's share of each, and its start within the tile
+        // tile's share of each, and its start within the tile (16-byte shared
+        // accesses: word-wise, lanes 4 apart would share a bank)
         uint32_t c[DPT], g[DPT], sum = 0;
         uint32_t *cur = cursor + (long long)T.seg * NB;
+        {
+            const uint4 a = *reinterpret_cast<const uint4 *>(&h[DPT * tid]);
+            const uint4 b = *reinterpret_cast<const uint4 *>(&h[DPT * tid + 4]);
+            c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+            c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+        }
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
-            c[q] = h[DPT * tid + q];
             g[q] = c[q] ? atomicAdd(cur + DPT * tid + q, c[q]) : 0u;
             sum += c[q];
         }
@@ -248,12 +255,18 @@ __global__ void __launch_bounds__(BT)
         __syncthreads();
         uint32_t run = incl - sum;
         for (int w = 0; w < warp; ++w) run += ws[w];
+        uint32_t st[DPT];
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
-            h[DPT * tid + q] = run;
-            move[DPT * tid + q] = (int)g[q] - (int)run;
+            st[q] = run;
             run += c[q];
         }
+        *reinterpret_cast<uint4 *>(&h[DPT * tid]) = make_uint4(st[0], st[1], st[2], st[3]);
+        *reinterpret_cast<uint4 *>(&h[DPT * tid + 4]) = make_uint4(st[4], st[5], st[6], st[7]);
+        *reinterpret_cast<int4 *>(&move[DPT * tid]) =
+            make_int4((int)(g[0] - st[0]), (int)(g[1] - st[1]), (int)(g[2] - st[2]), (int)(g[3] - st[3]));
+        *reinterpret_cast<int4 *>(&move[DPT * tid + 4]) =
+            make_int4((int)(g[4] - st[4]), (int)(g[5] - st[5]), (int)(g[6] - st[6]), (int)(g[7] - st[7]));
         __syncthreads();
         // the tile grouped by bucket in shared memory ...
 #pragma unroll
