@@ -65,8 +65,8 @@ FP32_NOMINAL_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # headline workload (outputs larger than L2), from one ncu capture of dram__bytes_read.sum
 # and dram__bytes_write.sum; valid only for the kernel source it was taken on (sha256
 # prefix of k_composite.cu followed by gs_internal.cuh). None until captured.
-# DRAM bytes of one compositing launch of 128 cameras (ncu dram__bytes_read.sum /
-# dram__bytes_write.sum, profiles/k_composite_traffic_single_1m_sh3_128cam_640x480.md),
+# DRAM bytes of one compositing launch of 128 cameras (ncu dram__bytes_read.sum and
+# dram__bytes_write.sum, one launch, clocks not locked; the outputs, 629 MB, exceed L2),
 # valid while the kernel source hashes to src_sha
 TRAFFIC_CAPTURE = {"cameras": 128, "read": 12_169_472, "write": 577_390_336,
                    "src_sha": "9d5d65928a3ad056"}

@@ -179,7 +179,7 @@ size_t depth_big_bytes();
 size_t depth_eq_bytes();
 size_t tie_run_bytes();
 constexpr int DEPTH_BUCKETS = 2048;  // per camera
-constexpr int DEPTH_WINDOW = 512;    // window stride (SORT_TILE_KEYS / 4)
+constexpr int DEPTH_WINDOW = 1024;   // window stride (SORT_TILE_KEYS / 2)
 cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
                                const uint32_t *oidx, const SortTile *tiles, const int *tile_start,
                                const long long *seg_start, int m, int grid, uint32_t *count,

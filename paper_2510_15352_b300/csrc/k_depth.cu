@@ -15,7 +15,7 @@
 //                   global atomic per non-empty bucket of the tile;
 //   k_depth_scan    per camera: bucket starts (the scatter's cursors) and the
 //                   windows: window w owns the buckets that start at positions
-//                   [512 w, 512 w + 512) and covers exactly those buckets;
+//                   [1024 w, 1024 w + 1024) and covers exactly those buckets;
 //   k_depth_scatter each tile grouped by bucket in shared memory, its share of
 //                   every bucket reserved with one global atomic on the bucket's
 //                   cursor (after the pass, the cursor is the bucket's end), then
@@ -38,8 +38,9 @@
 //                   each: slots in caller-index order.
 //
 // A bucket is 1/256 of the depth; on the full-size workloads the largest hold
-// about 1,400 keys, so windows average 512 keys and few pass 2,048 (about one
-// per camera goes to k_depth_big). Equal float32 depths are common: about
+// about 1,400 keys, so windows average 1,024 keys and few pass 2,048 (about one
+// per camera goes to k_depth_big; 512-position windows averaged 2.5 keys per
+// thread, and the per-window costs made the window pass 14 % slower). Equal float32 depths are common: about
 // 1,800 runs per camera, nearly all pairs. Nothing after the depth order reads
 // the sorted keys, so only the windows listed for the block sort keep theirs
 // up to date.
@@ -55,8 +56,8 @@ constexpr int NB = DEPTH_BUCKETS;          // buckets per camera (2048)
 constexpr int BSH = 15;                    // a key's bucket: key >> BSH (clamped)
 constexpr int BT = 256;                    // threads of the count / scatter blocks
 constexpr int BPT = SORT_TILE_KEYS / BT;   // keys per thread (8)
-constexpr int WIN = DEPTH_WINDOW;          // window stride (512)
-constexpr int WPS = SORT_TILE_KEYS / WIN;  // windows per sort tile (4)
+constexpr int WIN = DEPTH_WINDOW;          // window stride (1024)
+constexpr int WPS = SORT_TILE_KEYS / WIN;  // windows per sort tile (2)
 constexpr int WT = 256;                    // threads per window block
 constexpr int WPT = 8;                     // keys per thread of a window block
 constexpr int WCAP = WT * WPT;             // largest window sorted in shared memory (2048)
