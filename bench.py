@@ -849,8 +849,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED])
     ap.add_argument("--chunk", type=int, default=512, help="cameras per internal chunk")
     ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
-    ap.add_argument("--group", type=int, default=64,
-                    help="cameras sharing one Gaussian load in the projection (<= 64)")
+    ap.add_argument("--group", type=int, default=128,
+                    help="cameras sharing one Gaussian load in the projection (<= 128)")
     ap.add_argument("--tpb", type=int, default=1,
                     help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
     ap.add_argument("--comp-batch", type=int, default=64,

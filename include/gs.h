@@ -63,7 +63,7 @@ typedef struct gs_config {
     float background[3];   /* added as T * background to rgb (0, 0, 0) */
     int32_t max_chunk_cameras; /* cameras rendered per internal chunk (512) */
     int32_t camera_group;  /* cameras of one scene that share one Gaussian load in the
-                              projection kernels (64, at most 64) */
+                              projection kernels (128, at most 128) */
     int32_t count_pairs;   /* 1: the compositing kernel also counts evaluated pairs
                               (a slower variant of the kernel) */
     int32_t time_stages;   /* 1: record CUDA events around every stage on the render

@@ -38,14 +38,14 @@ DEFAULT_SPACE = {
     "tiles_per_block": (1, 4),
     "comp_batch": (32, 64, 96, 128),
     "persistent": (0, 1),
-    "camera_group": (32, 64),
+    "camera_group": (32, 64, 128),
     "max_chunk_cameras": (128, 256, 512),
 }
 # the stages of the search: compositing knobs first, then the pipeline knobs
 STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch", "persistent"),
           ("camera_group", "max_chunk_cameras"))
 DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 64, "persistent": 0,
-            "camera_group": 64, "max_chunk_cameras": 512}
+            "camera_group": 128, "max_chunk_cameras": 512}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
 

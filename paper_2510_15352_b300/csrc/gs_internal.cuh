@@ -10,7 +10,7 @@
 namespace gsk {
 
 constexpr int TILE = 16;            // tile edge in pixels
-constexpr int MAX_GROUP = 64;       // cameras sharing one Gaussian load (<= 2 x warp size)
+constexpr int MAX_GROUP = 128;      // cameras sharing one Gaussian load
 constexpr int PROJ_THREADS = 256;   // Gaussians per projection block (8 mask words)
 constexpr int BIN_THREADS = 256;    // threads per binning block
 constexpr int BIN_RANKS = 1024;     // depth ranks per binning block (4 per thread) ...

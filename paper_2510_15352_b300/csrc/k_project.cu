@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
     __shared__ CamProj cp[MAX_GROUP];
     __shared__ CamPair cpair[MAX_GROUP / 2];  // cameras (2i, 2i + 1) for prefilter2
     __shared__ long long moff[MAX_GROUP];
-    __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane (camera < 64)
+    __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane
     __shared__ uint32_t smask[NW][MAX_GROUP];
     __shared__ uint8_t cls[NW][MAX_GROUP];            // per warp: BLK_OUT / IN / PART per camera
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -465,8 +465,8 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
         const int c1 = 2 * tid + 1 < gr.ncam ? 2 * tid + 1 : 2 * tid;
         make_pair(cpair[tid], load_cam(camtab[gr.slot0 + 2 * tid]), load_cam(camtab[gr.slot0 + c1]));
     }
-    smask[warp][lane] = 0u;
-    smask[warp][lane + 32] = 0u;
+#pragma unroll
+    for (int c = lane; c < MAX_GROUP; c += 32) smask[warp][c] = 0u;
     const long long g = g0 + tid;
     const bool valid = g < gr.n;
     GaussGeo G;

@@ -47,7 +47,7 @@ def test_host_only_calls(lib):
     assert lib.gs_config_default(None) == lib.GS_ERR_INVALID_ARG
     assert lib.gs_last_error(None) == b"NULL context"
     out = ctypes.c_void_p(123)
-    bad = lib.default_config(camera_group=64)
+    bad = lib.default_config(camera_group=129)  # past the largest camera group (128)
     assert lib.gs_context_create(ctypes.byref(bad), 0, ctypes.byref(out)) == lib.GS_ERR_INVALID_ARG
     assert out.value is None
 

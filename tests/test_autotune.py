@@ -11,7 +11,7 @@ from paper_2510_15352_b300 import autotune, synth
 def test_candidates_cover_the_space():
     c = list(autotune.candidates())
     # layouts (2,1) (4,1) (8,1) x 4 batches x 2 launch forms (8,4) x groups x chunks
-    assert len(c) == 11 * 2 * 3
+    assert len(c) == 11 * 3 * 3
     assert {x["pixels_per_thread"] for x in c} == {2, 4, 8}
     assert {(x["pixels_per_thread"], x["tiles_per_block"]) for x in c} == {(2, 1), (4, 1), (8, 1), (8, 4)}
     assert {x["comp_batch"] for x in c if x["pixels_per_thread"] == 8 and x["tiles_per_block"] == 1} \
@@ -22,12 +22,12 @@ def test_candidates_cover_the_space():
 
 def test_staged_search_space():
     """The search's stages: the compositing knobs with the default pipeline
-    knobs (11 candidates), then the pipeline knobs (6)."""
+    knobs (11 candidates), then the pipeline knobs (9)."""
     best = dict(autotune.DEFAULTS)
     s1 = list(autotune.candidates(None, autotune.STAGES[0], best))
-    assert len(s1) == 11 and all(c["camera_group"] == 64 and c["max_chunk_cameras"] == 512 for c in s1)
+    assert len(s1) == 11 and all(c["camera_group"] == 128 and c["max_chunk_cameras"] == 512 for c in s1)
     s2 = list(autotune.candidates(None, autotune.STAGES[1], s1[0]))
-    assert len(s2) == 6 and all(c["comp_batch"] == s1[0]["comp_batch"] for c in s2)
+    assert len(s2) == 9 and all(c["comp_batch"] == s1[0]["comp_batch"] for c in s2)
 
 
 def test_signature_depends_on_the_batch_not_on_order():
