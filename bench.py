@@ -53,9 +53,10 @@ BATCHED = "batched_32scene_4096cam_mixed"
 # and a lower bound, 22 flops per contributing pair only.
 F_PAIR = 20
 # kernels per render chunk: camera table, mask, mask scan, plan, write; depth
-# order: count, scan, scatter, window, listed windows, listed runs (the last two
-# launch always and exit at once when nothing is listed); bin, composite
-LAUNCHES_PER_CHUNK = 13
+# order: count, scan, scatter, window, listed windows, long runs, listed runs
+# (the last three launch always and exit at once when nothing is listed); bin,
+# composite
+LAUNCHES_PER_CHUNK = 14
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
 # FP32 rate derived from unit counts (148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz),
@@ -68,8 +69,8 @@ FP32_NOMINAL_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes of one compositing launch of 128 cameras (ncu dram__bytes_read.sum and
 # dram__bytes_write.sum, one launch, clocks not locked; the outputs, 629 MB, exceed L2),
 # valid while the kernel source hashes to src_sha
-TRAFFIC_CAPTURE = {"cameras": 128, "read": 12_169_472, "write": 577_390_336,
-                   "src_sha": "9d5d65928a3ad056"}
+TRAFFIC_CAPTURE = {"cameras": 128, "read": 12_302_336, "write": 577_832_448,
+                   "src_sha": "d47ffadf14eeeb09"}
 
 
 def _composite_sha() -> str:
