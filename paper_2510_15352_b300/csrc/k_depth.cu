@@ -202,8 +202,11 @@ __global__ void __launch_bounds__(1024)
 
 // One sort tile per block pass: the tile grouped by bucket in shared memory
 // (ranks from shared-memory atomics), the tile's share of each bucket reserved
-// with one global atomic, then written out run by run (key and slot).
-__global__ void __launch_bounds__(BT)
+// with one global atomic, then written out run by run (key and slot). Six
+// resident blocks per SM (40 registers): a block waits on its reservations'
+// round trip, and more blocks hide more of it (5.0 -> 4.0 ms per 4,096 cameras
+// against four).
+__global__ void __launch_bounds__(BT, 6)
     k_depth_scatter(const uint32_t *__restrict__ keys, uint32_t *__restrict__ dk,
                     uint32_t *__restrict__ dv, const SortTile *__restrict__ tiles,
                     const int *__restrict__ n_tiles_dev, uint32_t *__restrict__ cursor) {
