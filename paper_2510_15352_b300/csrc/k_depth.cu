@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(1024)
 // (ranks from shared-memory atomics), the tile's share of each bucket reserved
 // with one global atomic, then written out run by run (key and slot). Six
 // resident blocks per SM (40 registers): a block waits on its reservations'
-// round trip, and more blocks hide more of it (5.0 -> 4.0 ms per 4,096 cameras
+// round trip, and more blocks hide more of it (4.2 -> 4.0 ms per 4,096 cameras
 // against four).
 __global__ void __launch_bounds__(BT, 6)
     k_depth_scatter(const uint32_t *__restrict__ keys, uint32_t *__restrict__ dk,
