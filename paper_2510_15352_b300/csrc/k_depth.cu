@@ -61,7 +61,7 @@ constexpr int WPS = SORT_TILE_KEYS / WIN;  // windows per sort tile (2)
 constexpr int WT = 256;                    // threads per window block
 constexpr int WPT = 8;                     // keys per thread of a window block
 constexpr int WCAP = WT * WPT;             // largest window sorted in shared memory (2048)
-constexpr int BIN_MAX = 32;                // largest bin the insertion finishes
+constexpr int BIN_MAX = 32;                // largest bin the window pass ranks (else: block sort)
 constexpr int SHORT = 32;                  // runs up to this length are ordered in place
 constexpr int LT = 1024;                   // threads of a listed window's block sort
 constexpr int BCAP = 4096;                 // listed windows up to this size sort in shared memory
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(WT, 4)
         }
         if (lane == 31) wsum[warp] = incl;
         if (__syncthreads_or(cmax > (uint32_t)BIN_MAX)) {
-            // a crowd of (nearly) equal keys: the insertion would be slow
+            // a crowd of (nearly) equal keys: ranking inside the bin would be slow
             if (tid == 0) list_window(big, big_cap, n_big, I.base, I.w.x, n);
             for (int q = 0; q < BW; q += 4)
                 *reinterpret_cast<uint4 *>(&bins[b0 + q]) = make_uint4(0, 0, 0, 0);
