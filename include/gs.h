@@ -338,12 +338,17 @@ gs_status gs_debug_tile_lists(gs_context *ctx, int32_t scene_id, const float *vi
                               int64_t *tile_off, int32_t *gidx, int64_t cap, int64_t *n_out,
                               void *stream);
 
-/* The hot path's segmented sort on caller data: within each segment
+/* A segmented sort on caller data (no counterpart in the paper: the library's
+ * stable radix sort, with which scene set-up orders the Morton codes of the
+ * means; the render's depth order has kernels of its own): within each segment
  * [seg_start[s], seg_start[s] + seg_count[s]) of keys/vals, a stable ascending
  * sort of the uint32 keys, vals moved with their keys, in place.
  * keys, vals: DEVICE [n] uint32; seg_start, seg_count: DEVICE [n_seg] int64,
- * segments must not overlap and lie within [0, n). Scratch (2 n uint32) comes
- * from the context's workspace. */
+ * segments must not overlap and lie within [0, n) (else GS_ERR_INVALID_ARG).
+ * The call reads the segment table to the host (it waits on `stream` for it);
+ * its scratch (2 n uint32 and the tile tables) belongs to the context but not
+ * to the render workspace, so a render still running on another stream is not
+ * disturbed. */
 gs_status gs_sort_segments(gs_context *ctx, uint32_t *keys, uint32_t *vals, int64_t n,
                            const int64_t *seg_start, const int64_t *seg_count, int32_t n_seg,
                            void *stream);
