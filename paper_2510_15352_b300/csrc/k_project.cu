@@ -454,7 +454,6 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
     __shared__ long long moff[MAX_GROUP];
     __shared__ uint16_t queue[NW][MQ];                // camera << 5 | lane
     __shared__ uint32_t smask[NW][MAX_GROUP];
-    __shared__ uint8_t cls[NW][MAX_GROUP];            // per warp: BLK_OUT / IN / PART per camera
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const SceneDev sc = scenes[gr.scene];
     if (tid < gr.ncam) {
@@ -478,7 +477,8 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
         for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
     }
     __syncthreads();
-    // the warp's 32 Gaussians as a group against each camera (lane c: cameras c, c + 32)
+    // the warp's 32 Gaussians as a group against each camera
+    uint32_t in_cams[MAX_GROUP / 32], part_cams[MAX_GROUP / 32];
     {
         const long long wb = (g0 >> 5) + warp;
         const bool live = (wb << 5) < gr.n;
@@ -487,9 +487,15 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
             blo = sc.bounds[2 * wb];
             bhi = sc.bounds[2 * wb + 1];
         }
-        for (int c = lane; c < gr.ncam; c += 32)
-            cls[warp][c] = live ? (uint8_t)classify_block(load_cam(cp[c]), blo, bhi, P) : (uint8_t)BLK_OUT;
-        __syncwarp();
+        // lane l classifies cameras l, l + 32, ...; ballots give the warp the
+        // cameras that keep the whole group (IN) and those that straddle it
+#pragma unroll
+        for (int q = 0; q < MAX_GROUP / 32; ++q) {
+            const int c = lane + 32 * q;
+            const int k = (live && c < gr.ncam) ? classify_block(load_cam(cp[c]), blo, bhi, P) : BLK_OUT;
+            in_cams[q] = __ballot_sync(0xffffffffu, k == BLK_IN);
+            part_cams[q] = __ballot_sync(0xffffffffu, k == BLK_PART);
+        }
     }
     const uint32_t lt = (1u << lane) - 1u;
     int nq = 0;  // queued pairs of this warp (warp-uniform)
@@ -527,17 +533,24 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4)
     };
     // the block's valid Gaussians: the mask word of a camera that keeps them all
     const uint32_t all = __ballot_sync(0xffffffffu, valid);
-    for (int c = 0; c < gr.ncam; c += 2) {  // two cameras per packed prefilter
-        const int k0 = cls[warp][c], k1 = c + 1 < gr.ncam ? cls[warp][c + 1] : BLK_OUT;
-        if (lane == 0) {
-            if (k0 == BLK_IN) smask[warp][c] = all;
-            if (k1 == BLK_IN) smask[warp][c + 1] = all;
+#pragma unroll
+    for (int q = 0; q < MAX_GROUP / 32; ++q)  // cameras that keep the whole group
+        if ((in_cams[q] >> lane) & 1u) smask[warp][lane + 32 * q] = all;
+    // only the camera pairs (2i, 2i + 1) with a straddling camera, in camera
+    // order (most pairs have none: their group test said outside)
+#pragma unroll
+    for (int q = 0; q < MAX_GROUP / 32; ++q) {
+        const uint32_t pm = part_cams[q];
+        uint32_t pairs = (pm | (pm >> 1)) & 0x55555555u;
+        while (pairs) {  // warp-uniform
+            const int b = __ffs(pairs) - 1;
+            pairs &= pairs - 1u;
+            const int c = 32 * q + b;
+            bool in0 = false, in1 = false;
+            if (valid) prefilter2(load_pair(cpair[c >> 1]), G, P, in0, in1);
+            append(c, in0 && ((pm >> b) & 1u));
+            if (c + 1 < gr.ncam) append(c + 1, in1 && ((pm >> (b + 1)) & 1u));
         }
-        if (k0 != BLK_PART && k1 != BLK_PART) continue;  // warp-uniform
-        bool in0 = false, in1 = false;
-        if (valid) prefilter2(load_pair(cpair[c >> 1]), G, P, in0, in1);
-        append(c, in0 && k0 == BLK_PART);
-        if (c + 1 < gr.ncam) append(c + 1, in1 && k1 == BLK_PART);
     }
     if (nq > 0) drain(nq);
     __syncwarp();
