@@ -734,7 +734,18 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
     // half extents sqrt(q Sigma'_00), sqrt(q Sigma'_11), widened so float32
     // rounding of the per-pixel test can never pass a pixel outside it
     const float q = 2.0f * fmaf(log2o, 0.6931471805599453f, -ln_alpha_min);
-    for (int c = 0; c < gr.ncam; ++c) {
+    // the cameras whose mask word for this warp is not zero (most are zero:
+    // the group test found the group outside), visited in camera order
+    uint32_t live_cams[MAX_GROUP / 32];
+#pragma unroll
+    for (int k = 0; k < MAX_GROUP / 32; ++k) {
+        const int c = lane + 32 * k;
+        live_cams[k] = __ballot_sync(0xffffffffu, c < gr.ncam && sword[c][warp] != 0u);
+    }
+#pragma unroll
+    for (int k = 0; k < MAX_GROUP / 32; ++k)
+    for (uint32_t lc = live_cams[k]; lc; lc &= lc - 1u) {  // warp-uniform
+        const int c = 32 * k + __ffs(lc) - 1;
         const uint32_t word = sword[c][warp];
         if (!((word >> lane) & 1u)) continue;
         const CamProj cam = load_cam(cp[c]);
