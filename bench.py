@@ -130,7 +130,7 @@ def measure_alu_peaks(gs, torch, stream, device: int) -> dict:
 
 def step_roofline(scene, n_cams: int, W: int, H: int, cst: dict, ms_step: float,
                   fp32_tflops: float) -> dict:
-    """The whole step against the roofline of the method as the survey states it:
+    """The whole step against the roofline of the common tile-sorted 3DGS design:
     max(algorithmic bytes / HBM peak, FP32 flops / FP32 peak). Bytes: the scene
     once, a 48-byte record written and read per survivor, a 12-byte
     intersection entry written and read per (survivor, tile) pair, 16 bytes of
