@@ -52,11 +52,11 @@ BATCHED = "batched_32scene_4096cam_mixed"
 # 11 per contributing pair (alpha >= alpha_min: 1 - alpha, T', alpha T, four FMAs),
 # and a lower bound, 22 flops per contributing pair only.
 F_PAIR = 20
-# kernels per render chunk: camera table, mask, mask scan, plan, write; depth
-# order: count, scan, scatter, window, listed windows, long runs, listed runs
-# (the last three launch always and exit at once when nothing is listed); bin,
-# composite
-LAUNCHES_PER_CHUNK = 14
+# kernels per render chunk: camera table, mask, mask scan, plan, plan tables,
+# write; depth order: count, scan, scatter, window, listed windows, long runs,
+# listed runs (the last three launch always and exit at once when nothing is
+# listed); bin, composite
+LAUNCHES_PER_CHUNK = 15
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
 # FP32 rate derived from unit counts (148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz),

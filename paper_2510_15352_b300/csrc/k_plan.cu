@@ -44,15 +44,13 @@ __global__ void __launch_bounds__(PT)
            int bin_ranks, long long cap_survivors, int *__restrict__ blkpre,
            int *__restrict__ sorttiles,
            long long *__restrict__ segstart, long long *__restrict__ segcount,
-           SortTile *__restrict__ stiles, int2 *__restrict__ bintab, int *__restrict__ status,
+           int *__restrict__ status,
            long long *__restrict__ need,
            unsigned long long *__restrict__ survivors,
            unsigned long long *__restrict__ sticky) {
     __shared__ long long ws64[PT / 32];
     __shared__ int ws32[PT / 32];
     __shared__ long long carry_s, carry_bm;
-    __shared__ long long b_off[PT], b_cnt[PT];  // per segment of a batch: first survivor, count
-    __shared__ int b_st[PT], b_bb[PT];          // and first sort tile / binning block within the batch
     __shared__ int carry_bb, carry_st, overflow;
     const int tid = threadIdx.x;
     // 1. is the chunk's survivor total within the workspace?
@@ -103,40 +101,6 @@ __global__ void __launch_bounds__(PT)
             segstart[i] = off_s;
             segcount[i] = c;
         }
-        // the SortTile entries of this batch's segments, one tile per thread
-        // (consecutive threads write consecutive entries); a tile's segment is
-        // found by a search over the batch's tile offsets in shared memory
-        b_off[tid] = off_s;
-        b_cnt[tid] = c;
-        b_st[tid] = off_st - carry_st;  // tiles of this batch before segment i
-        b_bb[tid] = off_bb - carry_bb;  // binning blocks of this batch before camera i
-        __syncthreads();
-        // the binning blocks' (camera, first rank), likewise
-        for (int g = tid; g < t_bb; g += PT) {
-            int lo = 0, hi = min(PT, m - b) - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (b_bb[mid] <= g)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            bintab[carry_bb + g] = make_int2(b + lo, (g - b_bb[lo]) * bin_ranks);
-        }
-        for (int g = tid; g < t_st; g += PT) {
-            int lo = 0, hi = min(PT, m - b) - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (b_st[mid] <= g)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            const int t0 = (g - b_st[lo]) * SORT_TILE_KEYS;
-            stiles[carry_st + g] = SortTile{b_off[lo], t0,
-                                            (int)min((long long)SORT_TILE_KEYS, b_cnt[lo] - t0),
-                                            (int)b_cnt[lo], b + lo};
-        }
         __syncthreads();
         if (tid == 0) {
             carry_s += t_s;
@@ -152,6 +116,42 @@ __global__ void __launch_bounds__(PT)
     }
 }
 
+// The binning blocks' (camera, first rank) and the sort tiles' entries of the
+// chunk, one thread per entry over the whole grid (k_plan's single block wrote
+// the per-camera prefixes): an entry's camera is the last whose prefix is at
+// most the entry's index (cameras without blocks share the next one's prefix).
+__device__ __forceinline__ int owner(const int *__restrict__ pre, int m, int g) {
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_plan_tables(int m, int bin_ranks, const int *__restrict__ blkpre,
+                              const int *__restrict__ sorttiles,
+                              const long long *__restrict__ segstart,
+                              const long long *__restrict__ segcount, SortTile *__restrict__ stiles,
+                              int2 *__restrict__ bintab) {
+    const int nbb = blkpre[m], nst = sorttiles[m];
+    const int stride = gridDim.x * blockDim.x;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nbb; g += stride) {
+        const int c = owner(blkpre, m, g);
+        bintab[g] = make_int2(c, (g - blkpre[c]) * bin_ranks);
+    }
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nst; g += stride) {
+        const int c = owner(sorttiles, m, g);
+        const int t0 = (g - sorttiles[c]) * SORT_TILE_KEYS;
+        const long long cnt = segcount[c];
+        stiles[g] = SortTile{segstart[c], t0, (int)min((long long)SORT_TILE_KEYS, cnt - t0),
+                             (int)cnt, c};
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks,
@@ -161,7 +161,9 @@ cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks,
                         unsigned long long *sticky, cudaStream_t s) {
     if (m == 0) return cudaSuccess;
     k_plan<<<1, PT, 0, s>>>(cams, counts, m, bin_ranks, cap_survivors, blkpre, sorttiles, segstart,
-                            segcount, stiles, bintab, status, need, survivors, sticky);
+                            segcount, status, need, survivors, sticky);
+    k_plan_tables<<<4 * 148, 256, 0, s>>>(m, bin_ranks, blkpre, sorttiles, segstart, segcount,
+                                          stiles, bintab);
     return cudaGetLastError();
 }
 
