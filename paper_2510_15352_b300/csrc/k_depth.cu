@@ -412,17 +412,21 @@ __device__ __forceinline__ void stage_item(const WinItem &I, const uint32_t *__r
 struct EqRun {
     uint32_t pos, seg_len;
 };
-constexpr int LOCAL_RUNS = 64;  // runs a window orders itself when the list is full
+constexpr int LOCAL_RUNS = WT;  // runs of a window gathered before they are listed
+static_assert(LOCAL_RUNS <= WT, "one thread per gathered run");
 
 // Each block takes windows blockIdx.x, + gridDim.x, ...; while it sorts one,
 // the next is copied into the other stage. ends[seg][b]: the end of bucket b
 // (the scatter's final cursor). A key of bucket b goes to one of the bucket's
 // c bins by its low bits (one bin per key on average); its place is the bin's
 // start plus the number of the bin's keys below it, equal keys by their staged
-// position. A run of equal keys is listed for k_tie_short, which puts it in
-// caller-index order (about one run per 500 keys on the full-size workloads);
-// when the list is full the window orders the run itself. Only the slots are
-// written back: nothing after the depth order reads the keys.
+// position. A window's runs of equal keys are gathered in shared memory and
+// listed together (one global atomic per window: a listing atomic per run,
+// all on one counter, cost the pass a fifth of its time) for k_tie_short,
+// which puts each in caller-index order (about one run per 100 keys on the
+// full-size workloads); a run past the list's capacity is ordered by the
+// window itself. Only the slots are written back: nothing after the depth
+// order reads the keys.
 __global__ void __launch_bounds__(WT, 4)
     k_depth_window(const uint32_t *__restrict__ K, uint32_t *__restrict__ V,
                    const uint32_t *__restrict__ oidx, const SortTile *__restrict__ tiles,
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__(WT, 4)
     uint32_t *bins = reinterpret_cast<uint32_t *>(wsm_raw + 2 * sizeof(WinStage));
     __shared__ uint32_t wsum[WT / 32];
     __shared__ uint2 local_runs[LOCAL_RUNS];  // (first position in the window, length)
-    __shared__ int n_local;
+    __shared__ int n_local, list_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int items = WPS * *n_tiles_dev;
     const int G = gridDim.x;
@@ -548,14 +552,8 @@ __global__ void __launch_bounds__(WT, 4)
                 }
                 S.v[first + less + eq_before] = vr[r];
                 if (eq_all > 1u && eq_before == 0u) {  // the first of a run of equal keys
-                    const int q = atomicAdd(n_eq, 1);
-                    if (q < eq_cap) {
-                        eq[q] = EqRun{(uint32_t)(I.base + I.w.x + first + less),
-                                      ((uint32_t)I.seg << 6) | eq_all};
-                    } else {
-                        const int l = atomicAdd(&n_local, 1);
-                        if (l < LOCAL_RUNS) local_runs[l] = make_uint2(first + less, eq_all);
-                    }
+                    const int l = atomicAdd(&n_local, 1);
+                    if (l < LOCAL_RUNS) local_runs[l] = make_uint2(first + less, eq_all);
                 }
             }
         }
@@ -563,8 +561,8 @@ __global__ void __launch_bounds__(WT, 4)
         for (int q = 0; q < BW; q += 4)
             *reinterpret_cast<uint4 *>(&bins[b0 + q]) = make_uint4(0, 0, 0, 0);
         const int nl = n_local;
-        if (nl > 0) {  // the list was full: this window orders its runs itself
-            if (nl > LOCAL_RUNS) {  // (or, with too many of them, the global block sort does)
+        if (nl > 0) {  // the window's runs of equal keys
+            if (nl > LOCAL_RUNS) {  // too many to gather: the block sort takes the window
                 __syncthreads();
                 if (tid == 0) {
                     n_local = 0;
@@ -572,7 +570,16 @@ __global__ void __launch_bounds__(WT, 4)
                 }
                 continue;
             }
-            if (tid < nl) order_short_run(S.v + local_runs[tid].x, oidx, I.base, (int)local_runs[tid].y);
+            if (tid == 0) list_base = atomicAdd(n_eq, nl);
+            __syncthreads();
+            if (tid < nl) {  // listed, or ordered here when past the list's end
+                const uint2 R = local_runs[tid];
+                const long long at = (long long)list_base + tid;
+                if (at < eq_cap)
+                    eq[at] = EqRun{(uint32_t)(I.base + I.w.x + R.x), ((uint32_t)I.seg << 6) | R.y};
+                else
+                    order_short_run(S.v + R.x, oidx, I.base, (int)R.y);
+            }
             __syncthreads();
             if (tid == 0) n_local = 0;
         }
