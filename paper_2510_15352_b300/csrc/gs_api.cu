@@ -366,6 +366,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
     const CompParams C{std::log2(cfg.alpha_min),
                        cfg.alpha_max,
                        cfg.T_min,
+                       std::log2(cfg.alpha_max) - 2e-3f,
                        {cfg.background[0], cfg.background[1], cfg.background[2]},
                        a.out_w,
                        a.accumulate};

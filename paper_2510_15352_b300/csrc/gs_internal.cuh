@@ -32,6 +32,8 @@ struct ProjParams {
 struct CompParams {
     float log2_alpha_min;  // log2(alpha_min): alpha test done on log2(o e^power)
     float alpha_max, T_min;
+    float log2_alpha_cap;  // log2(alpha_max) less a slack: for p + its float32 margin
+                           // below it, 2^p < alpha_max (the cap can be left out)
     float bg[3];
     float out_w;           // outputs are out_w * value ...
     int accumulate;        // ... added to the existing outputs when non-zero

@@ -19,6 +19,10 @@
 // and Gaussian:
 //   p = a'dx^2 + b'dx dy + c'dy^2 + log2(o) = log2(o e^power)
 //   p < log2(alpha_min): skip;  alpha = min(alpha_max, 2^p)
+//   (the cap is applied only for records that staging marks as able to reach
+//   it: log2 o plus the float32 margin of p over the live pixels at least
+//   log2(alpha_max); for the others 2^p < alpha_max at every pixel, so the
+//   result is the same without it)
 //   T' = T (1 - alpha); T' < T_min: the pixel stops (this Gaussian not added)
 //   C += alpha T rgb, D += alpha T z, T = T'.
 // Instruction economy (the kernel is issue-bound): when a record is staged,
@@ -35,6 +39,8 @@
 // taken two at a time: both quadratics, then both votes, then the blends, so
 // the two records' latencies overlap. No tensor cores: this is not a dense
 // contraction.
+#include <type_traits>
+
 #include "bin_core.cuh"
 #include "gs_internal.cuh"
 
@@ -115,7 +121,8 @@ __device__ __forceinline__ int block_camera(const int *__restrict__ prefix, int 
 // Shared memory of one compositing block (NT = 256 / PPT threads).
 template <int PPT, int CB>
 struct CompSmem {
-    // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits),
+    // staged records: s0 = (u, v, a', b'), s1 = (c', log2 o, z, warp mask bits
+    // and, in bit 31, "2^p may reach alpha_max"),
     // s2 = (red, green, blue, -)
     float4 s0[CB], s1[CB], s2[CB];
     // candidate ranks of one round in order; compacted in place to the ranks of
@@ -288,6 +295,7 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                 // over the rows' pixel-centre rectangle reaches the threshold (with a
                 // margin past float32 rounding, so no passing pair is skipped)
                 uint32_t m = 0;
+                bool cap = false;
 #pragma unroll
                 for (int k = 0; k < NWARP; ++k) {
                     const float4 L = wl[k];  // live pixel centres of warp k
@@ -300,6 +308,7 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                     const float terms = fmaf(fabsf(b.x), DX * DX,
                                              fmaf(fabsf(b.y), DX * DY, fabsf(b.z) * DY * DY));
                     const float margin = fmaf(1e-6f, terms, 1e-3f);
+                    cap = cap || b.w + margin >= P.log2_alpha_cap;
                     if (max_p_rect(a.x, a.y, b.x, b.y, b.z, b.w, X0, X1, Y0, Y1) >=
                         P.log2_alpha_min - margin)
                         m |= 1u << k;
@@ -315,7 +324,7 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                 }
                 if (put) {
                     s0[at] = make_float4(a.x, a.y, b.x, b.y);
-                    s1[at] = make_float4(b.z, b.w, cc.w, __uint_as_float(m));
+                    s1[at] = make_float4(b.z, b.w, cc.w, __uint_as_float(m | (cap ? 0x80000000u : 0u)));
                     s2[at] = cc;
                 }
             }
@@ -349,7 +358,8 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                     }
                     return any;
                 };
-                auto blend = [&](const float (&p)[PPT], const float4 &g2, float z) {
+                // CAP: std::true_type when the record may reach alpha_max
+                auto blend = [&](const float (&p)[PPT], const float4 &g2, float z, auto CAP) {
                     const float2 R2 = make_float2(g2.x, g2.x), G2 = make_float2(g2.y, g2.y),
                                  B2 = make_float2(g2.z, g2.z), Z2 = make_float2(z, z);
                     const float2 M1 = make_float2(-1.0f, -1.0f);
@@ -363,8 +373,9 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                         const int k = 2 * i;
                         const bool pass0 = p[k] >= thr[k], pass1 = p[k + 1] >= thr[k + 1];
                         if (STATS) al += (pass0 ? 1u : 0u) + (pass1 ? 1u : 0u);
-                        const float2 alpha = make_float2(fminf(P.alpha_max, ex2_approx(p[k])),
-                                                         fminf(P.alpha_max, ex2_approx(p[k + 1])));
+                        float2 alpha = make_float2(ex2_approx(p[k]), ex2_approx(p[k + 1]));
+                        if constexpr (decltype(CAP)::value)
+                            alpha = make_float2(fminf(P.alpha_max, alpha.x), fminf(P.alpha_max, alpha.y));
                         const float2 wgt = __fmul2_rn(alpha, T2[i]);
                         const float2 Tn = __ffma2_rn(wgt, M1, T2[i]);  // T - wgt
                         const bool ok0 = Tn.x >= P.T_min, ok1 = Tn.y >= P.T_min;
@@ -378,6 +389,12 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                         thr[k] = pass0 && !ok0 ? INF : thr[k];
                         thr[k + 1] = pass1 && !ok1 ? INF : thr[k + 1];
                     }
+                };
+                auto blend_rec = [&](const float (&p)[PPT], const float4 &g2, const float4 &g1) {
+                    if (__float_as_uint(g1.w) >> 31)  // warp-uniform
+                        blend(p, g2, g1.z, std::true_type{});
+                    else
+                        blend(p, g2, g1.z, std::false_type{});
                 };
                 if constexpr (COMPACT) {
                     // Records in groups of UNR: their quadratics and votes are
@@ -402,12 +419,12 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                         for (int u = 0; u < UNR; ++u) vu[u] = __any_sync(0xffffffffu, vu[u]);
 #pragma unroll
                         for (int u = 0; u < UNR; ++u)
-                            if (vu[u]) blend(pu[u], s2[j + u], g1u[u].z);
+                            if (vu[u]) blend_rec(pu[u], s2[j + u], g1u[u]);
                     }
                     for (; j < nb; ++j) {
                         const float4 g1 = s1[j];
                         float p[PPT];
-                        if (__any_sync(0xffffffffu, quad_p(s0[j], g1, p))) blend(p, s2[j], g1.z);
+                        if (__any_sync(0xffffffffu, quad_p(s0[j], g1, p))) blend_rec(p, s2[j], g1);
                     }
                 } else {
                     for (int j = 0; j < nb; ++j) {
@@ -422,7 +439,7 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                         float p[PPT];
                         if (!__any_sync(0xffffffffu, quad_p(s0[j], g1, p))) continue;
                         if (STATS) wbl++;
-                        blend(p, s2[j], g1.z);
+                        blend_rec(p, s2[j], g1);
                     }
                 }
             }
