@@ -606,14 +606,20 @@ __global__ void __launch_bounds__(1024)
 
 constexpr float LOG2E = 1.4426950408889634f;
 
+// SH coefficients per channel in groups of four consecutive k (zero past the
+// scene's degree): a Gaussian's column holds 3 * SH_QUADS(DEG) float4.
+__host__ __device__ constexpr int sh_quads(int deg) { return ((deg + 1) * (deg + 1) + 3) / 4; }
+
 // Colour of one Gaussian seen from camera c with its SH coefficients in the
-// lane's own shared-memory column (shc[(3 k + ch) PROJ_THREADS], zero past the
-// scene's degree; consecutive lanes read consecutive words, no bank conflict):
-// per channel the terms add in order of k, as in the definition.
+// lane's own shared-memory column (sh4[(ch Q + j) PROJ_THREADS] = coefficients
+// 4j .. 4j + 3 of channel ch; consecutive lanes read consecutive 16-byte words,
+// no bank conflict). Per channel the even-k and the odd-k terms add in order of
+// k on the two lanes of a packed FP32x2 accumulator, and the two sums are added
+// last (a different association from a single running sum: a few ulp).
 template <int DEG>
-__device__ __forceinline__ void sh_colour_smem(const float *shc, const CamProj &c,
+__device__ __forceinline__ void sh_colour_smem(const float4 *sh4, const CamProj &c,
                                                const GaussGeo &G, float rgb[3]) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int Q = sh_quads(DEG);
     float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
     const float dd = dx * dx + dy * dy + dz * dz;
     if (dd > 0.0f) {
@@ -630,13 +636,17 @@ __device__ __forceinline__ void sh_colour_smem(const float *shc, const CamProj &
 #pragma unroll
     for (int k = 0; k < 16; ++k) Y[k] = 0.0f;
     sh_basis(DEG, dx, dy, dz, Y);
-    float acc[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+    for (int ch = 0; ch < 3; ++ch) {
+        float2 acc = make_float2(0.5f, 0.0f);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(shc[(3 * k + ch) * PROJ_THREADS], Y[k], acc[ch]);
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(acc[ch], 0.0f);
+        for (int j = 0; j < Q; ++j) {
+            const float4 w = sh4[(ch * Q + j) * PROJ_THREADS];
+            acc = __ffma2_rn(make_float2(w.x, w.y), make_float2(Y[4 * j], Y[4 * j + 1]), acc);
+            acc = __ffma2_rn(make_float2(w.z, w.w), make_float2(Y[4 * j + 2], Y[4 * j + 3]), acc);
+        }
+        rgb[ch] = fmaxf(acc.x + acc.y, 0.0f);
+    }
 }
 
 // SH coefficient rows of Gaussian g into registers (zero past the scene's rows).
@@ -704,8 +714,9 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
     const long long g = g0 + tid;
     const bool valid = g < gr.n;
     GaussGeo G;
-    extern __shared__ float shs[];  // [NC][PROJ_THREADS]: this lane's column
-    float *shc = shs + tid;
+    constexpr int SQ = sh_quads(DEG);
+    extern __shared__ float4 shs[];  // [3 SQ][PROJ_THREADS]: this lane's column
+    float4 *shc = shs + tid;
     float log2o = 0.0f;
     uint32_t gidx = 0u;
     if (valid) {
@@ -718,15 +729,23 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
             load_sh<__half, NC>(sc, g, sh);
         else
             load_sh<__nv_bfloat16, NC>(sc, g, sh);
+        // coefficient (k, ch) is row 3 k + ch of the scene
 #pragma unroll
-        for (int i = 0; i < NC; ++i) shc[i * PROJ_THREADS] = sh[i];
+        for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+            for (int j = 0; j < SQ; ++j) {
+                float w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) w[e] = 4 * j + e < NC / 3 ? sh[3 * (4 * j + e) + ch] : 0.0f;
+                shc[(ch * SQ + j) * PROJ_THREADS] = make_float4(w[0], w[1], w[2], w[3]);
+            }
         gidx = (uint32_t)sc.orig[g];
     } else {
         G.mx = G.my = G.mz = G.smax2 = 0.0f;
 #pragma unroll
         for (int k = 0; k < 9; ++k) G.M[k] = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NC; ++i) shc[i * PROJ_THREADS] = 0.0f;
+        for (int i = 0; i < 3 * SQ; ++i) shc[i * PROJ_THREADS] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
@@ -830,8 +849,8 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
     const CamProj *ct = (const CamProj *)camtab;
 #define GS_WRITE(D)                                                                              \
     cudaFuncSetAttribute(k_project_write<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                         3 * (D + 1) * (D + 1) * PROJ_THREADS * 4);                                  \
-    k_project_write<D><<<grid, PROJ_THREADS, 3 * (D + 1) * (D + 1) * PROJ_THREADS * 4, s>>>(      \
+                         3 * sh_quads(D) * PROJ_THREADS * 16);                                       \
+    k_project_write<D><<<grid, PROJ_THREADS, 3 * sh_quads(D) * PROJ_THREADS * 16, s>>>(          \
         groups, scenes, cams, ct, P, masks, woff, rec, with_d, srect, keys, oidx,                 \
         ln_alpha_min, status)
     switch (max_deg) {
