@@ -62,15 +62,12 @@ F_CONTRIB_ONLY = 22
 # FP32 rate derived from unit counts (148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz),
 # reported beside the measured rate for context only
 FP32_NOMINAL_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-# DRAM bytes (read, write) of one compositing launch over CAPTURE_CAMERAS cameras of the
-# headline workload (outputs larger than L2), from one ncu capture of dram__bytes_read.sum
-# and dram__bytes_write.sum; valid only for the kernel source it was taken on (sha256
-# prefix of k_composite.cu followed by gs_internal.cuh). None until captured.
-# DRAM bytes of one compositing launch of 128 cameras (ncu dram__bytes_read.sum and
-# dram__bytes_write.sum, one launch, clocks not locked; the outputs, 629 MB, exceed L2),
-# valid while the kernel source hashes to src_sha
-TRAFFIC_CAPTURE = {"cameras": 128, "read": 12_302_336, "write": 577_832_448,
-                   "src_sha": "d47ffadf14eeeb09"}
+# DRAM bytes of one compositing launch of 128 cameras of the headline workload (ncu
+# dram__bytes_read.sum and dram__bytes_write.sum, one launch, clocks not locked; the
+# outputs, 629 MB, exceed L2), valid only for the kernel source it was taken on: src_sha
+# is the sha256 prefix of k_composite.cu followed by gs_internal.cuh
+TRAFFIC_CAPTURE = {"cameras": 128, "read": 11_521_792, "write": 576_307_712,
+                   "src_sha": "53dcd17a08fe0ac8"}
 
 
 def _composite_sha() -> str:
@@ -854,7 +851,7 @@ def main():
                     help="cameras sharing one Gaussian load in the projection (<= 128)")
     ap.add_argument("--tpb", type=int, default=1,
                     help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
-    ap.add_argument("--comp-batch", type=int, default=64,
+    ap.add_argument("--comp-batch", type=int, default=32,
                     help="records staged per compositing batch (32|64|96|128, with --ppt 8)")
     ap.add_argument("--persistent", type=int, default=0,
                     help="1: binning + compositing as one persistent launch (with --ppt 8)")

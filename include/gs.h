@@ -81,7 +81,7 @@ typedef struct gs_config {
                               gs_render_batch). 1: each render call waits for its
                               status and renders such chunks again at once (0) */
     int32_t comp_batch;    /* records staged per compositing batch with 8 pixels per
-                              thread: 32, 64, 96 or 128 (64; 0 = 64) */
+                              thread: 32, 64, 96 or 128 (32; 0 = 32) */
     int32_t persistent;    /* 1: binning and compositing of a chunk run as one persistent
                               launch pulling (camera, stage) work items from a device
                               queue (8 pixels per thread, one tile per block, no pair

@@ -44,7 +44,7 @@ DEFAULT_SPACE = {
 # the stages of the search: compositing knobs first, then the pipeline knobs
 STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch", "persistent"),
           ("camera_group", "max_chunk_cameras"))
-DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 64, "persistent": 0,
+DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 32, "persistent": 0,
             "camera_group": 128, "max_chunk_cameras": 512}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
@@ -89,7 +89,7 @@ def _distinct(c: dict) -> bool:
     ppt, tpb = c.get("pixels_per_thread", 8), c.get("tiles_per_block", 1)
     if tpb == 4 and ppt != 8:
         return False
-    if (c.get("comp_batch", 64) != 64 or c.get("persistent", 0)) and (ppt != 8 or tpb != 1):
+    if (c.get("comp_batch", 32) != 32 or c.get("persistent", 0)) and (ppt != 8 or tpb != 1):
         return False
     return True
 

@@ -678,7 +678,7 @@ gs_status gs_config_default(gs_config *out) {
     out->time_stages = 0;
     out->pixels_per_thread = 8;
     out->tiles_per_block = 1;
-    out->comp_batch = COMP_BATCH;
+    out->comp_batch = COMP_BATCH_DEFAULT;
     out->sync_errors = 0;
     return GS_OK;
 }
@@ -697,7 +697,7 @@ static bool check_config(gs_config &c) {
         return false;
     // 0 (a zero-initialised config) means 1; quads use 8 pixels per thread
     if (c.tiles_per_block == 0 || c.pixels_per_thread != 8) c.tiles_per_block = 1;
-    if (c.comp_batch == 0) c.comp_batch = COMP_BATCH;
+    if (c.comp_batch == 0) c.comp_batch = COMP_BATCH_DEFAULT;
     return true;
 }
 

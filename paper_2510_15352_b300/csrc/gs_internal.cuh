@@ -18,8 +18,10 @@ constexpr int BIN_RANKS_SMALL = 256;  // ... or 1 per thread when the bitmap wor
                                       // 1,024 ranks of every super-tile exceed
 constexpr int BIN_SMEM_MAX = 200 * 1024;  // this much shared memory
 constexpr int MAX_TILES = 65536;    // tiles per camera (binning smem: 2 B per tile)
-constexpr int COMP_BATCH = 64;      // Gaussian records staged per compositing sub-batch
-                                    // (default; 32 / 96 / 128 selectable for 8 px per thread)
+constexpr int COMP_BATCH = 64;      // Gaussian records staged per compositing sub-batch by
+                                    // the 2- and 4-pixel and quad layouts
+constexpr int COMP_BATCH_DEFAULT = 32;  // the configuration's batch for 8 px per thread
+                                        // (32 / 64 / 96 / 128 selectable)
 
 enum : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 

@@ -12,10 +12,10 @@
 // (block prefix of popcounts), keeps the candidates whose exact tile rect
 // holds this tile (order-preserving ballot compaction), then stages up to
 // a batch of their records at a time in shared memory and composites them
-// (COMP_BATCH = 64 by default; with 8 pixels per thread the batch is a template
-// parameter, 32, 64, 96 or 128, chosen by the configuration / autotuner: a
-// smaller batch refreshes the skip test's live-pixel rectangle more often, a
-// larger one amortises the staging). Per pixel
+// (COMP_BATCH = 64 for 2 and 4 pixels per thread and quads; with 8 pixels per
+// thread the batch is a template parameter, 32 (default), 64, 96 or 128, chosen
+// by the configuration / autotuner: a smaller batch refreshes the skip test's
+// live-pixel rectangle more often, a larger one amortises the staging). Per pixel
 // and Gaussian:
 //   p = a'dx^2 + b'dx dy + c'dy^2 + log2(o) = log2(o e^power)
 //   p < log2(alpha_min): skip;  alpha = min(alpha_max, 2^p)

@@ -16,7 +16,7 @@ def test_candidates_cover_the_space():
     assert {(x["pixels_per_thread"], x["tiles_per_block"]) for x in c} == {(2, 1), (4, 1), (8, 1), (8, 4)}
     assert {x["comp_batch"] for x in c if x["pixels_per_thread"] == 8 and x["tiles_per_block"] == 1} \
         == {32, 64, 96, 128}
-    assert all(x["comp_batch"] == 64 and x["persistent"] == 0
+    assert all(x["comp_batch"] == 32 and x["persistent"] == 0
                for x in c if x["pixels_per_thread"] != 8 or x["tiles_per_block"] != 1)
 
 
