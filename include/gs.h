@@ -88,7 +88,18 @@ typedef struct gs_config {
                               counting, images of at most 128 64x64-pixel super-tiles;
                               other calls use separate launches). Its stage time is
                               reported as compositing. (0) */
-    int32_t reserved[1];
+    int32_t depth_prefix;  /* progressive depth order (8 pixels per thread, one tile per
+                              block, separate launches, no pair counting): compositing
+                              stops reading a tile's list once every pixel has stopped,
+                              almost always within the nearest few per cent of a
+                              camera's survivors, so a first phase orders and bins only
+                              each camera's nearest ranks (at least this many, rounded
+                              up to whole depth buckets; 0: an eighth of the survivors,
+                              at least 4,096), tiles that still have live pixels there
+                              save their state, and a second phase orders and bins the
+                              rest of those tiles' cameras only and resumes them. The
+                              images are the same as with the whole order. -1: the
+                              whole order in one phase. (0) */
 } gs_config;
 
 /* A scene: n Gaussians stored as structure of arrays.
@@ -137,6 +148,9 @@ typedef struct gs_stats {
     int64_t sort_equal_runs;  /* runs of equal depth keys the window pass listed for ordering
                                  by caller index */
     int64_t sort_long_runs;   /* runs of more than 32 equal keys (one block each) */
+    int64_t depth_second_phase_cameras; /* cameras the progressive order's second phase
+                                           ordered further (depth_prefix) */
+    int64_t depth_resumed_tiles; /* tiles it composited past their camera's first phase */
 } gs_stats;
 
 typedef struct gs_context gs_context;
@@ -310,6 +324,13 @@ gs_status gs_sync(gs_context *ctx, void *stream);
 gs_status gs_render_timeout_probe(gs_context *ctx, int32_t scene_id, const float *viewmat,
                                   const float *intrinsics, int32_t width, int32_t height,
                                   float *rgb, float *depth, void *stream);
+
+/* Test hook of the progressive depth order (gs_config.depth_prefix): the list of
+ * saved tile states a chunk's first phase fills holds at most `tiles` entries on
+ * later render calls (0: the default, a sixteenth of the chunk's tiles, at least
+ * 1,024). Tiles past it are rendered again from rank 0 by the second phase, with
+ * the same images. Returns GS_ERR_INVALID_ARG for a NULL context or tiles < 0. */
+gs_status gs_set_resume_capacity(gs_context *ctx, int32_t tiles);
 
 /* ---------------------------------------------------------------------------
  * Inspection entry points (used by the test suite). Each runs the hot-path

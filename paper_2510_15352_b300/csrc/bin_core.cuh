@@ -1,9 +1,10 @@
 // bin_core.cuh -- the body of one binning item (see k_bin.cu): NTH threads
 // take RPT consecutive depth ranks each (NTH * RPT ranks from r0 of camera
-// ci), build the rank column's words of every super-tile row in shared memory
-// (sbm: [NTH * RPT / 32][P] words, P = super-tiles | 1), write the rank-ordered
-// rects and the words out, and add the item's (survivor, tile) pairs to
-// *n_isect. Used by the binning kernel (256 threads per item) and by the
+// ci; ranks at or past lim are left out: their bits are zero), build the rank
+// column's words of every super-tile row in shared memory (sbm: [NTH * RPT /
+// 32][P] words, P = super-tiles | 1), write the rank-ordered rects and the
+// words out, and add the item's (survivor, tile) pairs of ranks at or past
+// from to *n_isect. Used by the binning kernel (256 threads per item) and by the
 // persistent binning + compositing kernel (one warp per item).
 #pragma once
 
@@ -12,7 +13,7 @@
 namespace gsk {
 
 template <int NTH, int RPT>
-__device__ __forceinline__ void bin_item(uint32_t *sbm, const CamInfo &ci, int r0,
+__device__ __forceinline__ void bin_item(uint32_t *sbm, const CamInfo &ci, int r0, int lim, int from,
                                          const uint2 *__restrict__ srect,
                                          const uint32_t *__restrict__ vals,
                                          uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
@@ -28,25 +29,25 @@ __device__ __forceinline__ void bin_item(uint32_t *sbm, const CamInfo &ci, int r
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
         const int r = r0 + j * NTH + tid;
-        slot[j] = r < ci.count ? vals[ci.seg_off + r] : 0u;
+        slot[j] = r < lim ? vals[ci.seg_off + r] : 0u;
     }
     uint2 d[RPT];
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
         const int r = r0 + j * NTH + tid;
-        d[j] = r < ci.count ? srect[ci.seg_off + slot[j]] : make_uint2(1u, 1u);  // empty rect
+        d[j] = r < lim ? srect[ci.seg_off + slot[j]] : make_uint2(1u, 1u);  // empty rect
     }
     __syncthreads();  // sbm cleared
     unsigned long long area = 0;
 #pragma unroll
     for (int j = 0; j < RPT; ++j) {
         const int r = r0 + j * NTH + tid;
-        if (r >= ci.count) continue;
+        if (r >= lim) continue;
         rrect[ci.seg_off + r] = d[j];
         const int x0 = (int)(d[j].x & 0xffffu), x1 = (int)(d[j].x >> 16);
         const int y0 = (int)(d[j].y & 0xffffu), y1 = (int)(d[j].y >> 16);
         if (x1 >= x0 && y1 >= y0) {
-            area += (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
+            if (r >= from) area += (unsigned long long)(x1 - x0 + 1) * (y1 - y0 + 1);
             const uint32_t bit = 1u << lane;
             const int word = j * (NTH / 32) + warp;
             for (int sy = y0 / STILE; sy <= y1 / STILE; ++sy)

@@ -24,6 +24,29 @@ using namespace gsk;
 
 namespace {
 
+// Device statistics words: [0] evaluated pairs, [1] pairs with alpha >=
+// alpha_min, [2] intersections, [3..5] warp iterations (all, box, blend), [6]
+// survivors, [7] cameras of the progressive order's second phase, [8] tiles it
+// resumed.
+constexpr int N_STATS = 9;
+// Stage events per chunk: project | first-phase depth order | binning |
+// compositing | second-phase depth order | binning | compositing.
+constexpr int EV_PER_CHUNK = 8;
+
+// Blocks of the second phase's compositing launch: one resident wave of
+// one-warp blocks (it loops over the resumed tiles).
+int resume_grid() {
+    static int grid[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (grid[dev] == 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+        grid[dev] = std::max(sms, 1) * 18;
+    }
+    return grid[dev];
+}
+
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
@@ -61,7 +84,10 @@ struct gs_context {
     DevBuf seg_tk, seg_tv, seg_tiles, seg_hist;  // gs_sort_segments' own scratch
     DevBuf oidx;  // per survivor slot: the Gaussian's caller index (depth tie-break)
     DevBuf dcount, dwin, dbig, deq;  // depth order: bucket counts, windows, listed windows / runs
-    DevBuf ties, nruns;  // long runs of equal depth keys (list); per chunk 2 list counts
+    DevBuf ties, nruns;  // long runs of equal depth keys (list); per chunk 6 list counts
+    // the progressive depth order: per camera its cut, the two phase maps, the
+    // second phase's counts and camera flags, saved tile states, tiles to render again
+    DevBuf dcut, pmap, prog, rsaved, rstate, ragain;
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
     int workspace_gen = 0;        // bumped when a chunk-workspace buffer is reallocated
@@ -72,7 +98,7 @@ struct gs_context {
     gs_stats last{};
     bool stats_pending = false;
     std::string err;
-    std::vector<cudaEvent_t> ev;  // time_stages: 5 events per chunk of the last call
+    std::vector<cudaEvent_t> ev;  // time_stages: EV_PER_CHUNK events per chunk of the last call
     cudaStream_t copy_stream = nullptr;       // host entry point: device-to-host copies
     std::vector<cudaEvent_t> part_done;       // host / upsampled entry points: one event per part
     cudaStream_t up_stream = nullptr;         // upsampled entry point: the upsampler's stream
@@ -96,6 +122,7 @@ struct gs_context {
     int pgrid[4] = {0, 0, 0, 0};  // its resident grid, per compositing batch (32/64/96/128)
     int probe_extra = 0;          // timeout probe: camera 0 waits for items that never come
     int probe_limit = 0;          // timeout probe: polls before giving up (0: the default)
+    int resume_cap = 0;           // saved tile states a chunk may hold (0: the workspace's)
 };
 
 struct gs_graph {
@@ -210,6 +237,7 @@ struct ChunkPlan {
 
 struct Plan {
     std::vector<ChunkPlan> chunks;
+    int max_tiles = 0;               // compositing blocks of the largest chunk
     std::vector<CamInfo> cams;       // static fields, all chunks (chunk k at chunks[k].c0)
     std::vector<Group> groups;
     std::vector<int> tilepre;        // per chunk m + 1 entries, at c0 + k
@@ -288,6 +316,7 @@ void build_plan(gs_context *ctx, const RenderArgs &a, Plan &P) {
         P.max_gauss = std::max(P.max_gauss, ch.n_gauss);
         P.max_m = std::max(P.max_m, ch.m);
         P.max_sup = std::max(P.max_sup, ch.max_sup);
+        P.max_tiles = std::max(P.max_tiles, ch.tiles_total);
         P.chunks.push_back(ch);
     }
     P.off_groups = align_up(P.cams.size() * sizeof(CamInfo), 256);
@@ -308,7 +337,9 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
                       &ctx->blkpre,
                       &ctx->sorttiles,
                       &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status,
-                      &ctx->oidx,     &ctx->ties,     &ctx->nruns,    &ctx->pq};
+                      &ctx->oidx,     &ctx->ties,     &ctx->nruns,    &ctx->pq,
+                      &ctx->dcut,     &ctx->pmap,     &ctx->prog,     &ctx->rsaved,
+                      &ctx->rstate,   &ctx->ragain};
     // (compared by capacity: a reallocation may return the freed address)
     size_t before[sizeof(held) / sizeof(held[0])];
     for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->cap;
@@ -327,7 +358,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->tvals, (Sx + 4) * 4));
     CKS(grow(ctx, ctx->oidx, Sx * 4));
     CKS(grow(ctx, ctx->ties, (Sx / 33 + 2) * tie_run_bytes()));
-    CKS(grow(ctx, ctx->nruns, 3 * (P.chunks.size() + 1) * sizeof(int)));
+    CKS(grow(ctx, ctx->nruns, 6 * (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->pq, (size_t)(m + 2) * sizeof(int)));
     // bounds implied by S: bitmap words <= max_sup * (S/32 + m), sort tiles <= S/2048 + m
     CKS(grow(ctx, ctx->bitmap, (size_t)P.max_sup * (Sx / 32 + m + 1) * 4));
@@ -345,7 +376,17 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->sorttiles, (size_t)(m + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->segstart, (size_t)m * sizeof(long long)));
     CKS(grow(ctx, ctx->segcount, (size_t)m * sizeof(long long)));
-    CKS(grow(ctx, ctx->stats, 8 * sizeof(unsigned long long)));
+    CKS(grow(ctx, ctx->stats, N_STATS * sizeof(unsigned long long)));
+    CKS(grow(ctx, ctx->dcut, (size_t)m * sizeof(DepthCut)));
+    CKS(grow(ctx, ctx->pmap, 2 * phase_map_ints(m) * sizeof(int)));
+    CKS(grow(ctx, ctx->prog, (size_t)(m + 2) * sizeof(int)));
+    // saved tile states: a sixteenth of the largest chunk's tiles (more tiles than
+    // that reaching their camera's cut are rendered again from rank 0 instead)
+    const size_t tiles = (size_t)std::max(P.max_tiles, 1);
+    const size_t rcap = std::max<size_t>(1024, tiles / 16);
+    CKS(grow(ctx, ctx->rsaved, rcap * sizeof(int2)));
+    CKS(grow(ctx, ctx->rstate, rcap * RESUME_STATE_F4 * sizeof(float4)));
+    CKS(grow(ctx, ctx->ragain, tiles * sizeof(int2)));
     CKS(grow(ctx, ctx->status, (P.chunks.size() + 2) * sizeof(long long)));
     for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i)
         if (held[i]->cap != before[i]) {
@@ -356,8 +397,8 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
 }
 
 // Enqueue the whole render on `st` (no host synchronisation). `tab` holds the
-// uploaded static tables of P. With events != NULL, 5 events per chunk are
-// recorded around the stages.
+// uploaded static tables of P. With events != NULL, EV_PER_CHUNK events per
+// chunk are recorded around the stages.
 gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, char *tab,
                          cudaStream_t st, cudaEvent_t *events,
                          const std::vector<char> *only = nullptr) {
@@ -388,7 +429,21 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         int *status = status_all + k;
         tp += ch.m + 1;
         if (only && !(*only)[k]) continue;
-        cudaEvent_t *E = events ? events + 5 * k : nullptr;
+        cudaEvent_t *E = events ? events + EV_PER_CHUNK * k : nullptr;
+        // the progressive depth order (see DepthCut) with the separate launches of
+        // the 8-pixel, one-tile layout; the whole order otherwise
+        const bool prog = cfg.depth_prefix >= 0 && a.upto == UPTO_ALL && !ch.persistent &&
+                          cfg.pixels_per_thread == 8 && cfg.tiles_per_block == 1 &&
+                          !cfg.count_pairs;
+        DepthCut *cut = (DepthCut *)ctx->dcut.p;
+        int *map1 = (int *)ctx->pmap.p, *map2 = map1 + phase_map_ints(ch.m);
+        int *prog_n = (int *)ctx->prog.p;  // [2] counts, then [m] flags
+        Resume R{prog_n + 2, prog_n, (int2 *)ctx->rsaved.p, (float4 *)ctx->rstate.p,
+                 (int2 *)ctx->ragain.p,
+                 (int)std::min(ctx->rsaved.cap / sizeof(int2),
+                               ctx->rstate.cap / (RESUME_STATE_F4 * sizeof(float4))),
+                 (int)(ctx->ragain.cap / sizeof(int2))};
+        if (ctx->resume_cap > 0) R.cap = std::min(R.cap, ctx->resume_cap);
         if (E) CKC(cudaEventRecord(E[0], st));
         CKC(launch_cam_setup(cams, ch.m, a.vm, a.in, PP, ctx->camtab.p, st));
         CKC(launch_project_mask(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
@@ -418,14 +473,16 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                                ctx->dbig.p, (long long)(ctx->dbig.cap / depth_big_bytes()),
                                ctx->deq.p, (long long)(ctx->deq.cap / depth_eq_bytes()),
                                ctx->ties.p, (long long)(ctx->ties.cap / tie_run_bytes()),
-                               (int *)ctx->nruns.p + 3 * k, st));
+                               (int *)ctx->nruns.p + 6 * k, cut, prog ? cfg.depth_prefix : -1,
+                               (const int *)ctx->blkpre.p, ch.bin_ranks, map1, st));
         if (E) CKC(cudaEventRecord(E[2], st));
         const bool persist = ch.persistent && a.upto == UPTO_ALL;
         if (!persist)
             CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
                            ch.bin_grid, ch.max_sup,
                            ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->tvals.p,
-                           (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, st));
+                           (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, cut,
+                           prog ? 1 : 0, map1, st));
         if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;
         if (persist) {
@@ -447,13 +504,44 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                                      ctx->probe_extra, (unsigned long long *)ctx->sticky.p,
                                      ctx->pgrid[ci], st));
         } else {
+            if (prog) CKC(cudaMemsetAsync(prog_n, 0, (size_t)(ch.m + 2) * sizeof(int), st));
             CKC(launch_composite(cams, tilepre, ch.m, ch.per_cam, ch.tiles_total, recs,
                                  (const uint32_t *)ctx->tvals.p, (const uint2 *)ctx->rrect.p,
                                  (const uint32_t *)ctx->bitmap.p, C, a.rgb, a.depth, a.T, stats,
                                  cfg.count_pairs != 0, cfg.pixels_per_thread, cfg.tiles_per_block,
-                                 cfg.comp_batch, status, st));
+                                 cfg.comp_batch, status, cut, prog ? &R : nullptr, st));
         }
         if (E) CKC(cudaEventRecord(E[4], st));
+        if (prog) {
+            // the second phase: the flagged cameras' remaining ranks, their tiles resumed
+            uint32_t near_bits;
+            memcpy(&near_bits, &cfg.near_plane, 4);
+            CKC(launch_phase_map(2, ch.m, cut, R.flag, (const int *)ctx->sorttiles.p,
+                                 (const int *)ctx->blkpre.p, ch.bin_ranks, map2, R.n, stats + 7, st));
+            CKC(launch_depth_finish(recs, near_bits, (uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
+                                    (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
+                                    (const uint32_t *)ctx->oidx.p, (const SortTile *)ctx->sorttab.p,
+                                    (const long long *)ctx->segstart.p, ch.m, ch.sort_grid,
+                                    (uint32_t *)ctx->dcount.p, ctx->dwin.p, ctx->dbig.p,
+                                    (long long)(ctx->dbig.cap / depth_big_bytes()), ctx->deq.p,
+                                    (long long)(ctx->deq.cap / depth_eq_bytes()), ctx->ties.p,
+                                    (long long)(ctx->ties.cap / tie_run_bytes()),
+                                    (int *)ctx->nruns.p + 6 * k + 3, cut, map2, st));
+            if (E) CKC(cudaEventRecord(E[5], st));
+            CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
+                           ch.bin_grid, ch.max_sup, ch.bin_ranks, (const uint2 *)ctx->srect.p,
+                           (const uint32_t *)ctx->tvals.p, (uint2 *)ctx->rrect.p,
+                           (uint32_t *)ctx->bitmap.p, stats + 2, cut, 2, map2, st));
+            if (E) CKC(cudaEventRecord(E[6], st));
+            CKC(launch_composite_resume(cams, recs, (const uint32_t *)ctx->tvals.p,
+                                        (const uint2 *)ctx->rrect.p, (const uint32_t *)ctx->bitmap.p,
+                                        C, a.rgb, a.depth, a.T, cfg.comp_batch, status, cut, R,
+                                        resume_grid(), st));
+        } else if (E) {
+            CKC(cudaEventRecord(E[5], st));
+            CKC(cudaEventRecord(E[6], st));
+        }
+        if (E) CKC(cudaEventRecord(E[7], st));
     }
     return GS_OK;
 }
@@ -534,7 +622,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
                                  : std::max<long long>(1 << 20, P.max_gauss / 3);
     const bool timing = ctx->cfg.time_stages != 0;
     if (timing)
-        while (ctx->ev.size() < 5 * P.chunks.size()) {
+        while (ctx->ev.size() < EV_PER_CHUNK * P.chunks.size()) {
             cudaEvent_t e;
             CKC(cudaEventCreate(&e));
             ctx->ev.push_back(e);
@@ -558,7 +646,7 @@ gs_status render_impl(gs_context *ctx, const RenderArgs &a) {
     for (int attempt = 0; attempt < 2; ++attempt) {
         CKS(size_workspace(ctx, P));
         CKS(upload_tables_ring(ctx, P, a.st));
-        if (attempt == 0) CKC(cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), a.st));
+        if (attempt == 0) CKC(cudaMemsetAsync(ctx->stats.p, 0, N_STATS * sizeof(unsigned long long), a.st));
         CKC(cudaMemsetAsync(ctx->status.p, 0, status_bytes, a.st));
         // the second pass renders only the chunks that overflowed (the others are
         // final, and may have been accumulated into the outputs)
@@ -647,7 +735,7 @@ gs_status validate(gs_context *ctx, int n, const int32_t *scene_ids, const void 
 
 extern "C" {
 
-int32_t gs_abi_version(void) { return 5; }
+int32_t gs_abi_version(void) { return 6; }
 
 const char *gs_status_string(gs_status s) {
     switch (s) {
@@ -680,6 +768,7 @@ gs_status gs_config_default(gs_config *out) {
     out->tiles_per_block = 1;
     out->comp_batch = COMP_BATCH_DEFAULT;
     out->sync_errors = 0;
+    out->depth_prefix = 0;
     return GS_OK;
 }
 
@@ -693,7 +782,8 @@ static bool check_config(gs_config &c) {
         (c.tiles_per_block != 0 && c.tiles_per_block != 1 && c.tiles_per_block != 4) ||
         (c.comp_batch != 0 && c.comp_batch != 32 && c.comp_batch != 64 && c.comp_batch != 96 &&
          c.comp_batch != 128) ||
-        (c.sync_errors != 0 && c.sync_errors != 1) || (c.persistent != 0 && c.persistent != 1))
+        (c.sync_errors != 0 && c.sync_errors != 1) || (c.persistent != 0 && c.persistent != 1) ||
+        c.depth_prefix < -1)
         return false;
     // 0 (a zero-initialised config) means 1; quads use 8 pixels per thread
     if (c.tiles_per_block == 0 || c.pixels_per_thread != 8) c.tiles_per_block = 1;
@@ -752,6 +842,8 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->oidx,     &ctx->dcount, &ctx->dwin,   &ctx->dbig,    &ctx->deq,
                       &ctx->ties,
                       &ctx->nruns,    &ctx->pq,
+                      &ctx->dcut,     &ctx->pmap,   &ctx->prog,   &ctx->rsaved,  &ctx->rstate,
+                      &ctx->ragain,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -1020,7 +1112,7 @@ gs_status gs_graph_create(gs_context *ctx, int32_t n_cams, const int32_t *scene_
         RenderArgs ac = a;
         ac.st = cs;
         gs_status e1 = GS_OK;
-        if (cudaMemsetAsync(ctx->stats.p, 0, 8 * sizeof(unsigned long long), cs) != cudaSuccess ||
+        if (cudaMemsetAsync(ctx->stats.p, 0, N_STATS * sizeof(unsigned long long), cs) != cudaSuccess ||
             cudaMemsetAsync(ctx->status.p, 0, sizeof(long long) + P.chunks.size() * sizeof(int),
                             cs) != cudaSuccess)
             e1 = GS_ERR_CUDA;
@@ -1251,12 +1343,18 @@ gs_status gs_render_timeout_probe(gs_context *ctx, int32_t scene_id, const float
     return r;
 }
 
+gs_status gs_set_resume_capacity(gs_context *ctx, int32_t tiles) {
+    if (!ctx || tiles < 0) return GS_ERR_INVALID_ARG;
+    ctx->resume_cap = tiles;
+    return GS_OK;
+}
+
 gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
     if (!ctx || !out) return GS_ERR_INVALID_ARG;
     CKC(cudaSetDevice(ctx->device));
     if (ctx->done_valid) CKC(cudaEventSynchronize(ctx->done_ev));  // the last call is complete
     if (ctx->stats_pending && ctx->stats.p) {
-        unsigned long long h[8];
+        unsigned long long h[N_STATS];
         CKC(cudaMemcpy(h, ctx->stats.p, sizeof(h), cudaMemcpyDeviceToHost));
         ctx->last.pairs_evaluated = (int64_t)h[0];
         ctx->last.pairs_alpha = (int64_t)h[1];
@@ -1265,25 +1363,30 @@ gs_status gs_get_stats(gs_context *ctx, gs_stats *out) {
         ctx->last.warp_iters_box = (int64_t)h[4];
         ctx->last.warp_iters_blend = (int64_t)h[5];
         ctx->last.survivors = (int64_t)h[6];
-        // the depth order's lists, per chunk: long runs, listed windows, equal runs
+        ctx->last.depth_second_phase_cameras = (int64_t)h[7];
+        ctx->last.depth_resumed_tiles = (int64_t)h[8];
+        // the depth order's lists, per chunk and phase: long runs, listed windows,
+        // equal runs
         const int nc = ctx->last.n_chunks;
-        if (nc > 0 && ctx->nruns.p && ctx->nruns.cap >= 3 * (size_t)nc * sizeof(int)) {
-            std::vector<int> cnt(3 * (size_t)nc);
+        if (nc > 0 && ctx->nruns.p && ctx->nruns.cap >= 6 * (size_t)nc * sizeof(int)) {
+            std::vector<int> cnt(6 * (size_t)nc);
             CKC(cudaMemcpy(cnt.data(), ctx->nruns.p, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost));
-            for (int c = 0; c < nc; ++c) {
+            for (int c = 0; c < 2 * nc; ++c) {
                 ctx->last.sort_long_runs += cnt[3 * c];
                 ctx->last.sort_windows_listed += cnt[3 * c + 1];
                 ctx->last.sort_equal_runs += cnt[3 * c + 2];
             }
         }
+        // stages: project, depth order (both phases), binning (both), compositing (both)
         float ms[4] = {0, 0, 0, 0};
+        const int stage_of[EV_PER_CHUNK - 1] = {0, 1, 2, 3, 1, 2, 3};
         for (int c = 0; c < ctx->ev_used; ++c) {
-            cudaEvent_t *E = &ctx->ev[5 * c];
-            CKC(cudaEventSynchronize(E[4]));
-            for (int k = 0; k < 4; ++k) {
+            cudaEvent_t *E = &ctx->ev[EV_PER_CHUNK * c];
+            CKC(cudaEventSynchronize(E[EV_PER_CHUNK - 1]));
+            for (int k = 0; k < EV_PER_CHUNK - 1; ++k) {
                 float t = 0;
                 CKC(cudaEventElapsedTime(&t, E[k], E[k + 1]));
-                ms[k] += t;
+                ms[stage_of[k]] += t;
             }
         }
         ctx->last.ms_project = ms[0];

@@ -184,11 +184,88 @@ size_t depth_eq_bytes();
 size_t tie_run_bytes();
 constexpr int DEPTH_BUCKETS = 2048;  // per camera
 constexpr int DEPTH_WINDOW = 1024;   // window stride (SORT_TILE_KEYS / 2)
+
+// Progressive depth order. Compositing reads only the nearest few per cent of
+// a camera's depth ranks before every pixel of a tile has stopped, so the first
+// phase orders (and the binning pass bins) only each camera's ranks [0, pos):
+// the buckets before `bucket`, which are the windows before `win1`. pos is the
+// first bucket start at or past prefix ranks rounded up to whole windows
+// (prefix: at least DEPTH_PREFIX_MIN, else count / DEPTH_PREFIX_DIV, or the
+// configured number; the whole segment when the order is not progressive).
+// A tile that still has live pixels at its camera's cut saves its compositing
+// state and flags the camera; the second phase orders and bins the rest of the
+// flagged cameras only and resumes those tiles.
+struct DepthCut {
+    int pos;     // first rank of the second phase (count when there is none)
+    int bucket;  // its bucket (DEPTH_BUCKETS when there is none)
+    int win1;    // windows of the first phase
+    int count;   // the segment's keys
+};
+constexpr int DEPTH_PREFIX_MIN = 4096;
+constexpr int DEPTH_PREFIX_DIV = 8;
+
+// The work items of one phase per chunk (k_plan.cu, k_phase_map), an int
+// array of phase_map_ints(m): [0] segments listed, [1..3] window items, binning
+// blocks and sort tiles in all; then per kind (windows, binning blocks, sort
+// tiles) the exclusive prefix of the listed segments' items and the first item
+// of each. Item v of a kind is base[k] + v - pre[k] for the last k with
+// pre[k] <= v.
+inline size_t phase_map_ints(int m) { return 4 + 6 * (size_t)(m + 1); }
+__device__ __forceinline__ int phase_item(const int *__restrict__ map, int m, int kind, int v) {
+    const int *pre = map + 4 + 2 * kind * (m + 1), *base = pre + (m + 1);
+    int lo = 0, hi = map[0] - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= v)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return base[lo] + v - pre[lo];
+}
+enum : int { MAP_WINDOWS = 0, MAP_BINS = 1, MAP_TILES = 2 };
+
+// Phase maps: phase 1 lists every segment (its first-phase windows and binning
+// blocks, all its sort tiles); phase 2 the segments whose flag is set (their
+// remaining windows and binning blocks, all their sort tiles) and adds the
+// listed segments and the tiles that reached their cut (rn[0]) to stats[0] /
+// stats[1].
+cudaError_t launch_phase_map(int phase, int m, const DepthCut *cut, const int *flag,
+                             const int *tile_start, const int *blkpre, int bin_ranks, int *map,
+                             const int *rn, unsigned long long *stats, cudaStream_t s);
+
+// The first phase of the depth order: every segment (camera) of keys (z bits
+// minus the near plane's bits, slot order) cut (cut, from prefix: < 0 the whole
+// segment, 0 the default, > 0 that many ranks) and its first-phase ranks
+// sorted by (key, oidx[seg_base + slot]); the slots in that order end in sv.
+// map: the chunk's phase map, written here (phase 1). sk, keys and vals are
+// scratch (sk and sv hold at least 4 elements past the chunk's survivors: the
+// window pass copies 16-byte pieces). tiles / tile_start: the chunk's SortTile
+// table and per-segment tile prefix (tile_start[m] the total, on the device);
+// seg_start: the segments' first positions; blkpre / bin_ranks: the binning
+// blocks (for the map). Work buffers: count (DEPTH_BUCKETS uint32 per segment),
+// win (SORT_TILE_KEYS / DEPTH_WINDOW entries of depth_window_bytes() per sort
+// tile), big (big_cap entries of depth_big_bytes()), eq (eq_cap entries of
+// depth_eq_bytes()), runs (run_cap entries of tie_run_bytes()), counters (3
+// ints, zeroed by the call). grid: blocks of the per-tile kernels. Chunk
+// positions must stay below 2^32.
 cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
                                const uint32_t *oidx, const SortTile *tiles, const int *tile_start,
                                const long long *seg_start, int m, int grid, uint32_t *count,
                                void *win, void *big, long long big_cap, void *eq, long long eq_cap,
-                               void *runs, long long run_cap, int *counters, cudaStream_t s);
+                               void *runs, long long run_cap, int *counters, DepthCut *cut,
+                               int prefix, const int *blkpre, int bin_ranks, int *map,
+                               cudaStream_t s);
+// The second phase: the flagged segments' ranks [pos, count) (map: the phase-2
+// map, written before), their keys taken from the records' depth (rec, the
+// near plane's bits) since the first phase's block sort may have used the key
+// array as scratch. Same buffers as the first phase; counters: 3 more ints.
+cudaError_t launch_depth_finish(const float4 *rec, uint32_t near_bits, uint32_t *keys,
+                                uint32_t *vals, uint32_t *sk, uint32_t *sv, const uint32_t *oidx,
+                                const SortTile *tiles, const long long *seg_start, int m, int grid,
+                                uint32_t *count, void *win, void *big, long long big_cap, void *eq,
+                                long long eq_cap, void *runs, long long run_cap, int *counters,
+                                const DepthCut *cut, const int *map, cudaStream_t s);
 
 // Motion-blur sub-frame poses (see k_blur.cu): out[j * n + i] for j < k.
 // Intrinsics scaled by 1/f (see k_blur.cu).
@@ -210,11 +287,13 @@ cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks, 
 // bin_ranks: ranks per block, BIN_RANKS or BIN_RANKS_SMALL (the plan kernel's
 // blocks must use the same value).
 int bin_ranks_for(int n_super);
+// phase 0: all ranks of every block; 1 / 2: the blocks of the phase map (map),
+// the ranks before each camera's cut / all ranks (pairs counted from the cut).
 cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *bintab, int n_slots,
                        int n_blocks,
                        int n_super, int bin_ranks, const uint2 *srect, const uint32_t *vals,
                        uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
-                       cudaStream_t s);
+                       const DepthCut *cut, int phase, const int *map, cudaStream_t s);
 
 // Binning and compositing of a chunk in one persistent launch (k_composite.cu):
 // 8 pixels per thread, binning items of BIN_RANKS_SMALL ranks (the plan must
@@ -236,12 +315,36 @@ cudaError_t launch_bin_composite(const CamInfo *cams, const int *tile_prefix, in
 // 128, 64 or 32 threads); tiles_per_block 4: one block of 4 warps per 2 x 2 quad
 // of tiles (8 pixels per thread). tile_prefix / n_tiles count the blocks: tiles
 // or quads per camera.
+// The second phase's compositing work of a chunk (see DepthCut): a tile that
+// still has live pixels when it reaches its camera's cut saves its state and
+// flags the camera; when the saved list is full it is listed to be rendered
+// again from rank 0 instead.
+struct Resume {
+    int *flag;       // [m] 1: the camera has tiles past its cut (zero before the first phase)
+    int *n;          // [2] saved tiles, tiles to render again (zero before the first phase)
+    int2 *saved;     // [cap] (camera, tile) of saved states
+    float4 *state;   // [cap][12][32]: per lane its pixels' T, colour and depth sums and
+                     // alpha thresholds
+    int2 *again;     // [again_cap] (camera, tile) rendered again from rank 0
+    int cap, again_cap;
+};
+constexpr int RESUME_STATE_F4 = 12 * 32;  // float4 of one saved tile state
+
+// cut / R: the progressive order's first phase (8 pixels per thread, one tile
+// per block, no counting only; R == nullptr: the whole order).
 cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_slots,
                              int per_cam, int n_tiles, const float4 *rec, const uint32_t *vals,
                              const uint2 *rrect, const uint32_t *bitmap, CompParams C,
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
                              int tiles_per_block, int comp_batch, const int *status,
-                             cudaStream_t s);
+                             const DepthCut *cut, const Resume *R, cudaStream_t s);
+// The second phase's compositing: the saved tiles resumed at their camera's cut,
+// then the listed tiles rendered from rank 0 (8 pixels per thread, grid blocks).
+cudaError_t launch_composite_resume(const CamInfo *cams, const float4 *rec, const uint32_t *vals,
+                                    const uint2 *rrect, const uint32_t *bitmap, CompParams C,
+                                    float *rgb, float *depth, float *final_T, int comp_batch,
+                                    const int *status, const DepthCut *cut, const Resume &R,
+                                    int grid, cudaStream_t s);
 
 }  // namespace gsk

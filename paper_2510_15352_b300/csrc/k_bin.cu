@@ -25,19 +25,26 @@ namespace gsk {
 
 namespace {
 
+// phase 0: every binning block of the chunk, all ranks; phase 1 / 2: the
+// blocks of the phase map, the ranks before the camera's cut / all ranks (the
+// second phase counts pairs from the cut on).
 template <int RPT>  // ranks per thread
 __global__ void __launch_bounds__(BIN_THREADS)
     k_bin(const CamInfo *__restrict__ cams, const int *__restrict__ blk_prefix,
           const int2 *__restrict__ bintab, int n_slots,
           const uint2 *__restrict__ srect, const uint32_t *__restrict__ vals,
           uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
-          unsigned long long *__restrict__ n_isect) {
+          unsigned long long *__restrict__ n_isect, const DepthCut *__restrict__ cut, int phase,
+          const int *__restrict__ map) {
     extern __shared__ uint32_t sbm[];  // [ranks / 32][P]
-    const int nblk = blk_prefix[n_slots];
-    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int nblk = phase == 0 ? blk_prefix[n_slots] : map[2];
+    for (int bv = blockIdx.x; bv < nblk; bv += gridDim.x) {
+        const int blk = phase == 0 ? bv : phase_item(map, n_slots, MAP_BINS, bv);
         const int2 bt = bintab[blk];  // (camera, first rank) of this binning block
         const CamInfo ci = cams[bt.x];
-        bin_item<BIN_THREADS, RPT>(sbm, ci, bt.y, srect, vals, rrect, bitmap, n_isect);
+        const int lim = phase == 1 ? min(ci.count, cut[bt.x].pos) : ci.count;
+        const int from = phase == 2 ? cut[bt.x].pos : 0;
+        bin_item<BIN_THREADS, RPT>(sbm, ci, bt.y, lim, from, srect, vals, rrect, bitmap, n_isect);
     }
 }
 
@@ -53,7 +60,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *b
                        int n_blocks,
                        int n_super, int bin_ranks, const uint2 *srect, const uint32_t *vals,
                        uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
-                       cudaStream_t s) {
+                       const DepthCut *cut, int phase, const int *map, cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
     const size_t smem = (size_t)(n_super | 1) * (bin_ranks / 32) * sizeof(uint32_t);
     auto kern = bin_ranks == BIN_RANKS ? k_bin<BIN_RANKS / BIN_THREADS>
@@ -64,7 +71,7 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *b
         if (e != cudaSuccess) return e;
     }
     kern<<<n_blocks, BIN_THREADS, smem, s>>>(cams, blk_prefix, bintab, n_slots, srect, vals, rrect, bitmap,
-                                             n_isect);
+                                             n_isect, cut, phase, map);
     return cudaGetLastError();
 }
 

@@ -149,12 +149,19 @@ struct CompArgs {
     float *rgb, *depth, *finalT;
     unsigned long long *stats;
     const int *status;
+    const DepthCut *cut;  // the progressive order's cuts (phases 1 and 2)
+    Resume R;
 };
 
 // L2ONLY: the bitmap words and rank-ordered rects are read through L2 only
 // (the persistent kernel writes them during the same launch, on other SMs).
-template <int PPT, bool STATS, int CB, bool L2ONLY = false>
-__device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const CompArgs &A) {
+// PH: 0 the whole list; 1 the ranks before camera cam's cut, the state saved
+// (and the camera flagged) when live pixels remain; 2 the ranks from the cut on,
+// from saved state sidx (sidx < 0: the whole list from rank 0).
+template <int PPT, bool STATS, int CB, bool L2ONLY = false, int PH = 0>
+__device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const CompArgs &A,
+                                               int cam = 0, int sidx = -1) {
+    static_assert(PH == 0 || (PPT == 8 && !STATS), "the progressive order: 8 px, no counting");
     const float4 *__restrict__ rec = A.rec;
     const uint32_t *__restrict__ vals = A.vals;
     const uint2 *__restrict__ rrect = A.rrect;
@@ -195,6 +202,49 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
         T2[i] = make_float2(1.0f, 1.0f);
         cr2[i] = cg2[i] = cb2[i] = cd2[i] = make_float2(0.0f, 0.0f);
     }
+    // the bitmap words this call reads: [w_begin, w_end), the first word's ranks
+    // below the cut left out when resuming
+    int w_begin = 0, w_end = ci.nw;
+    uint32_t first_mask = 0xffffffffu;
+    bool rest = false;  // ranks past the cut remain (the cut can fall inside the last word)
+    if constexpr (PH == 1) {
+        const int pos = A.cut[cam].pos;
+        rest = pos < ci.count;
+        if (rest) w_end = (pos + 31) >> 5;
+    } else if constexpr (PH == 2) {
+        if (sidx >= 0) {
+            const int pos = A.cut[cam].pos;
+            w_begin = pos >> 5;
+            first_mask = ~((1u << (pos & 31)) - 1u);
+            const float4 *st = A.R.state + (long long)sidx * RESUME_STATE_F4 + lane;
+#pragma unroll
+            for (int i = 0; i < NPR / 2; ++i) {
+                float4 v = st[(0 + i) * 32];
+                T2[2 * i] = make_float2(v.x, v.y);
+                T2[2 * i + 1] = make_float2(v.z, v.w);
+                v = st[(2 + i) * 32];
+                cr2[2 * i] = make_float2(v.x, v.y);
+                cr2[2 * i + 1] = make_float2(v.z, v.w);
+                v = st[(4 + i) * 32];
+                cg2[2 * i] = make_float2(v.x, v.y);
+                cg2[2 * i + 1] = make_float2(v.z, v.w);
+                v = st[(6 + i) * 32];
+                cb2[2 * i] = make_float2(v.x, v.y);
+                cb2[2 * i + 1] = make_float2(v.z, v.w);
+                v = st[(8 + i) * 32];
+                cd2[2 * i] = make_float2(v.x, v.y);
+                cd2[2 * i + 1] = make_float2(v.z, v.w);
+            }
+#pragma unroll
+            for (int i = 0; i < PPT / 4; ++i) {
+                const float4 v = st[(10 + i) * 32];
+                thr[4 * i] = v.x;
+                thr[4 * i + 1] = v.y;
+                thr[4 * i + 2] = v.z;
+                thr[4 * i + 3] = v.w;
+            }
+        }
+    }
     const uint32_t warp_bit = 1u << warp;
     unsigned long long ev = 0, al = 0, wi = 0, wbox = 0, wbl = 0;
     auto live_rect = [&]() {
@@ -220,14 +270,15 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
     const long long rec0 = ci.seg_off;
     const uint32_t *cv = vals + ci.seg_off;
     const uint2 *crr = rrect + ci.seg_off;
-    for (int wb = 0; wb < ci.nw; wb += NT) {
+    for (int wb = w_begin; wb < w_end; wb += NT) {
         bool live = false;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
         if (!__syncthreads_or(live)) break;
         // 1. candidates: set bits of NT words of the super-tile row, in rank order
         const int w = wb + tid;
-        uint32_t word = w < ci.nw ? (L2ONLY ? __ldcg(bm + w) : bm[w]) : 0u;
+        uint32_t word = w < w_end ? (L2ONLY ? __ldcg(bm + w) : bm[w]) : 0u;
+        if (PH == 2 && w == w_begin) word &= first_mask;
         uint32_t c = __popc(word);
         uint32_t incl = c;
 #pragma unroll
@@ -450,6 +501,40 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
             if (!__syncthreads_or(live)) goto finished;
         }
     }
+    if constexpr (PH == 1) {
+        // the list ends at the camera's cut: a tile with live pixels left saves
+        // its state for the second phase (which writes its outputs)
+        if (rest) {
+            bool live = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) live = live || thr[k] != INF;
+            if (__any_sync(0xffffffffu, live)) {
+                int slot = 0;
+                if (lane == 0) slot = atomicAdd(A.R.n, 1);
+                slot = __shfl_sync(0xffffffffu, slot, 0);
+                if (slot < A.R.cap) {
+                    float4 *st = A.R.state + (long long)slot * RESUME_STATE_F4 + lane;
+#pragma unroll
+                    for (int i = 0; i < NPR / 2; ++i) {
+                        st[(0 + i) * 32] = make_float4(T2[2 * i].x, T2[2 * i].y, T2[2 * i + 1].x, T2[2 * i + 1].y);
+                        st[(2 + i) * 32] = make_float4(cr2[2 * i].x, cr2[2 * i].y, cr2[2 * i + 1].x, cr2[2 * i + 1].y);
+                        st[(4 + i) * 32] = make_float4(cg2[2 * i].x, cg2[2 * i].y, cg2[2 * i + 1].x, cg2[2 * i + 1].y);
+                        st[(6 + i) * 32] = make_float4(cb2[2 * i].x, cb2[2 * i].y, cb2[2 * i + 1].x, cb2[2 * i + 1].y);
+                        st[(8 + i) * 32] = make_float4(cd2[2 * i].x, cd2[2 * i].y, cd2[2 * i + 1].x, cd2[2 * i + 1].y);
+                    }
+#pragma unroll
+                    for (int i = 0; i < PPT / 4; ++i)
+                        st[(10 + i) * 32] = make_float4(thr[4 * i], thr[4 * i + 1], thr[4 * i + 2], thr[4 * i + 3]);
+                    if (lane == 0) A.R.saved[slot] = make_int2(cam, t);
+                } else if (lane == 0) {
+                    const int r = atomicAdd(A.R.n + 1, 1);
+                    if (r < A.R.again_cap) A.R.again[r] = make_int2(cam, t);
+                }
+                if (lane == 0) A.R.flag[cam] = 1;
+                return;
+            }
+        }
+    }
 finished:
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
@@ -496,12 +581,25 @@ finished:
 }
 
 
-template <int PPT, bool STATS, int CB>
+template <int PPT, bool STATS, int CB, int PH = 0>
 __global__ void __launch_bounds__(256 / PPT, PPT == 8 ? 18 : 1) k_composite(const CompArgs A) {
     if (A.status && *A.status) return;  // the chunk did not fit the workspace: nothing written
     int first;
-    const CamInfo ci = A.cams[block_camera(A.tile_prefix, A.n_slots, A.per_cam, (int)blockIdx.x, first)];
-    composite_tile<PPT, STATS, CB>(ci, (int)blockIdx.x - first, A);
+    const int cam = block_camera(A.tile_prefix, A.n_slots, A.per_cam, (int)blockIdx.x, first);
+    composite_tile<PPT, STATS, CB, false, PH>(A.cams[cam], (int)blockIdx.x - first, A, cam);
+}
+
+// The second phase of the progressive order: saved tiles resumed at their
+// camera's cut, then the tiles listed to be rendered again, grid-stride.
+template <int CB>
+__global__ void __launch_bounds__(32, 18) k_composite_resume(const CompArgs A) {
+    if (A.status && *A.status) return;
+    const int ns = min(A.R.n[0], A.R.cap), na = min(A.R.n[1], A.R.again_cap);
+    for (int e = blockIdx.x; e < ns + na; e += gridDim.x) {
+        const int2 ct = e < ns ? A.R.saved[e] : A.R.again[e - ns];
+        composite_tile<8, false, CB, false, 2>(A.cams[ct.x], ct.y, A, ct.x, e < ns ? e : -1);
+        __syncthreads();  // shared memory is reused by the next tile
+    }
 }
 
 // Binning and compositing of a chunk in one persistent launch (8 pixels per
@@ -562,7 +660,8 @@ __global__ void __launch_bounds__(32, 16) k_bin_composite(const CompArgs A, cons
             const int item = it_now;
             const int2 bt = Q.bintab[item];
             const CamInfo ci = A.cams[bt.x];
-            bin_item<32, PB_RPT>(sbm, ci, bt.y, Q.srect, A.vals, Q.rrect, Q.bitmap, Q.n_isect);
+            bin_item<32, PB_RPT>(sbm, ci, bt.y, ci.count, 0, Q.srect, A.vals, Q.rrect, Q.bitmap,
+                                 Q.n_isect);
             __threadfence();  // this item's rects and words before its count
             if (lane == 0) atomicAdd(Q.bin_done + bt.x, 1);
         } else {
@@ -839,20 +938,31 @@ cudaError_t launch_ppt(const CamInfo *cams, const int *tile_prefix, int n_slots,
                        const float4 *rec, const uint32_t *vals, const uint2 *rrect,
                        const uint32_t *bitmap, CompParams C, float *rgb, float *depth,
                        float *final_T, unsigned long long *stats, bool collect, int comp_batch,
-                       const int *status, cudaStream_t s) {
-    const CompArgs A{cams, tile_prefix, n_slots, per_cam, rec, vals, rrect, bitmap,
-                     C, rgb, depth, final_T, stats, status};
-#define GS_COMP(ST, CBV) k_composite<PPT, ST, CBV><<<n_tiles, 256 / PPT, 0, s>>>(A)
+                       const int *status, const DepthCut *cut, const Resume *R, cudaStream_t s) {
+    CompArgs A{cams, tile_prefix, n_slots, per_cam, rec, vals, rrect, bitmap,
+               C, rgb, depth, final_T, stats, status, cut, {}};
+    if (R) A.R = *R;
+#define GS_COMP(ST, CBV, PHV) k_composite<PPT, ST, CBV, PHV><<<n_tiles, 256 / PPT, 0, s>>>(A)
     if (collect) {
-        GS_COMP(true, COMP_BATCH);
-    } else if (PPT == 8 && comp_batch == 32) {  // the render layout: batch sizes to tune
-        GS_COMP(false, 32);
-    } else if (PPT == 8 && comp_batch == 96) {
-        GS_COMP(false, 96);
-    } else if (PPT == 8 && comp_batch == 128) {
-        GS_COMP(false, 128);
+        GS_COMP(true, COMP_BATCH, 0);
+    } else if constexpr (PPT == 8) {  // the render layout: batch sizes to tune
+        if (R) {  // the progressive order's first phase
+            switch (comp_batch) {
+                case 32: GS_COMP(false, 32, 1); break;
+                case 96: GS_COMP(false, 96, 1); break;
+                case 128: GS_COMP(false, 128, 1); break;
+                default: GS_COMP(false, COMP_BATCH, 1); break;
+            }
+        } else {
+            switch (comp_batch) {
+                case 32: GS_COMP(false, 32, 0); break;
+                case 96: GS_COMP(false, 96, 0); break;
+                case 128: GS_COMP(false, 128, 0); break;
+                default: GS_COMP(false, COMP_BATCH, 0); break;
+            }
+        }
     } else {
-        GS_COMP(false, COMP_BATCH);
+        GS_COMP(false, COMP_BATCH, 0);
     }
 #undef GS_COMP
     return cudaGetLastError();
@@ -905,7 +1015,7 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
                              float *rgb, float *depth, float *final_T,
                              unsigned long long *stats, bool collect, int pixels_per_thread,
                              int tiles_per_block, int comp_batch, const int *status,
-                             cudaStream_t s) {
+                             const DepthCut *cut, const Resume *R, cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
     if (tiles_per_block == 4) {
         if (collect)
@@ -920,12 +1030,30 @@ cudaError_t launch_composite(const CamInfo *cams, const int *tile_prefix, int n_
     }
     if (pixels_per_thread == 8)
         return launch_ppt<8>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C,
-                             rgb, depth, final_T, stats, collect, comp_batch, status, s);
+                             rgb, depth, final_T, stats, collect, comp_batch, status, cut, R, s);
     if (pixels_per_thread == 4)
         return launch_ppt<4>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C,
-                             rgb, depth, final_T, stats, collect, comp_batch, status, s);
+                             rgb, depth, final_T, stats, collect, comp_batch, status, nullptr,
+                             nullptr, s);
     return launch_ppt<2>(cams, tile_prefix, n_slots, per_cam, n_tiles, rec, vals, rrect, bitmap, C, rgb,
-                         depth, final_T, stats, collect, comp_batch, status, s);
+                         depth, final_T, stats, collect, comp_batch, status, nullptr, nullptr, s);
+}
+
+cudaError_t launch_composite_resume(const CamInfo *cams, const float4 *rec, const uint32_t *vals,
+                                    const uint2 *rrect, const uint32_t *bitmap, CompParams C,
+                                    float *rgb, float *depth, float *final_T, int comp_batch,
+                                    const int *status, const DepthCut *cut, const Resume &R,
+                                    int grid, cudaStream_t s) {
+    if (grid < 1) return cudaSuccess;
+    const CompArgs A{cams, nullptr, 0, 0, rec, vals, rrect, bitmap, C, rgb, depth, final_T,
+                     nullptr, status, cut, R};
+    switch (comp_batch) {
+        case 32: k_composite_resume<32><<<grid, 32, 0, s>>>(A); break;
+        case 96: k_composite_resume<96><<<grid, 32, 0, s>>>(A); break;
+        case 128: k_composite_resume<128><<<grid, 32, 0, s>>>(A); break;
+        default: k_composite_resume<COMP_BATCH><<<grid, 32, 0, s>>>(A); break;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace gsk

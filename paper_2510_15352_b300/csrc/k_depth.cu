@@ -121,14 +121,18 @@ __global__ void __launch_bounds__(BT)
 // One block of 1024 threads per camera; thread d owns buckets SPT d .. SPT d +
 // SPT - 1. count becomes the scatter's cursor (the bucket's start in the
 // segment); win[WPS tile_start[s] + w] = (first position, end position, first
-// bucket, last bucket + 1) of window w (empty windows all zero).
+// bucket, last bucket + 1) of window w (empty windows all zero); cut[s] = the
+// segment's cut (see DepthCut): the first non-empty bucket starting at or past
+// the first-phase windows' end, win1 WIN positions each.
 __global__ void __launch_bounds__(1024)
     k_depth_scan(uint32_t *__restrict__ count, int4 *__restrict__ win,
-                 const int *__restrict__ tile_start) {
+                 const int *__restrict__ tile_start, DepthCut *__restrict__ cut, int prefix) {
     constexpr int SPT = NB / 1024;
     __shared__ uint32_t ws[32];
     __shared__ int wm[32];
+    __shared__ int bcut;
     const int s = blockIdx.x, d = threadIdx.x, lane = d & 31, warp = d >> 5;
+    if (d == 0) bcut = NB;
     uint32_t *cs = count + (long long)s * NB + SPT * d;
     uint32_t c[SPT], sum = 0;
 #pragma unroll
@@ -196,6 +200,24 @@ __global__ void __launch_bounds__(1024)
             prev = b0;
         }
     }
+    // the cut: the first-phase windows cover [0, T1), T1 = the prefix rounded up
+    // to whole windows; the second phase starts at the first bucket (with keys)
+    // whose start is at or past T1
+    const int K = prefix < 0 ? total : prefix == 0 ? max(DEPTH_PREFIX_MIN, total / DEPTH_PREFIX_DIV) : prefix;
+    const int win1 = (min(K, total) + WIN - 1) / WIN;
+    const long long T1 = (long long)win1 * WIN;
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+        if (c[q] && (long long)ex[q] >= T1) {
+            atomicMin(&bcut, SPT * d + q);
+            break;
+        }
+    __syncthreads();
+    const int bc = bcut;
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+        if (SPT * d + q == bc) cut[s] = DepthCut{(int)ex[q], bc, win1, total};
+    if (bc == NB && d == 0) cut[s] = DepthCut{total, NB, win1, total};
 }
 
 // ---------------------------------------------------------------- scatter
@@ -205,11 +227,16 @@ __global__ void __launch_bounds__(1024)
 // with one global atomic, then written out run by run (key and slot). Six
 // resident blocks per SM (40 registers): a block waits on its reservations'
 // round trip, and more blocks hide more of it (4.2 -> 4.0 ms per 4,096 cameras
-// against four).
+// against four). Phase 1: every sort tile, the keys of buckets before the
+// segment's cut; phase 2: the sort tiles of the phase map, the keys of the
+// cut's bucket and after, read from the records' depth (rec, near_bits).
+template <int phase>
 __global__ void __launch_bounds__(BT, 6)
     k_depth_scatter(const uint32_t *__restrict__ keys, uint32_t *__restrict__ dk,
                     uint32_t *__restrict__ dv, const SortTile *__restrict__ tiles,
-                    const int *__restrict__ n_tiles_dev, uint32_t *__restrict__ cursor) {
+                    const int *__restrict__ n_tiles_dev, uint32_t *__restrict__ cursor,
+                    const DepthCut *__restrict__ cut, const int *__restrict__ map, int m,
+                    const float4 *__restrict__ rec, uint32_t near_bits) {
     constexpr int DPT = NB / BT;  // buckets per thread (8), read and written as uint4 pairs
     static_assert(DPT == 8, "two uint4 per thread");
     __shared__ __align__(16) uint32_t h[NB];  // counts, then where each bucket starts in the tile
@@ -217,21 +244,39 @@ __global__ void __launch_bounds__(BT, 6)
     __shared__ uint32_t skey[SORT_TILE_KEYS], sval[SORT_TILE_KEYS];
     __shared__ uint32_t ws[BT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nt = *n_tiles_dev;
-    for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int nt = phase == 2 ? map[3] : *n_tiles_dev;
+    for (int tv = blockIdx.x; tv < nt; tv += gridDim.x) {
+        const int tile = phase == 2 ? phase_item(map, m, MAP_TILES, tv) : tv;
         const SortTile T = tiles[tile];
-        const uint32_t *k = keys + T.seg_base + T.t0;
+        const uint32_t bcut = (uint32_t)cut[T.seg].bucket;
+        const uint32_t blo = phase == 2 ? bcut : 0u, bhi = phase == 2 ? (uint32_t)NB : bcut;
         for (int d = tid; d < NB; d += BT) h[d] = 0;
         uint32_t kv[BPT], rk[BPT];
+        uint32_t in = 0;  // bit r: key r of this thread belongs to the phase
+        if constexpr (phase == 2) {
+            const long long s0 = T.seg_base + T.t0;
+#pragma unroll
+            for (int r = 0; r < BPT; ++r) {
+                const int j = r * BT + tid;
+                kv[r] = j < T.nk ? __float_as_uint(rec[rec_c(s0 + j)].w) - near_bits : 0u;
+            }
+        } else {
+            const uint32_t *k = keys + T.seg_base + T.t0;
+#pragma unroll
+            for (int r = 0; r < BPT; ++r) {
+                const int j = r * BT + tid;
+                kv[r] = j < T.nk ? k[j] : 0u;
+            }
+        }
 #pragma unroll
         for (int r = 0; r < BPT; ++r) {
-            const int j = r * BT + tid;
-            kv[r] = j < T.nk ? k[j] : 0u;
+            const uint32_t b = bucket_of(kv[r]);
+            in |= (r * BT + tid < T.nk && b >= blo && b < bhi) ? 1u << r : 0u;
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < BPT; ++r)
-            rk[r] = r * BT + tid < T.nk ? atomicAdd(&h[bucket_of(kv[r])], 1u) : 0u;
+            rk[r] = (in >> r) & 1u ? atomicAdd(&h[bucket_of(kv[r])], 1u) : 0u;
         __syncthreads();
         // thread tid owns buckets DPT tid .. DPT tid + DPT - 1: reserve the
         // tile's share of each, and its start within the tile (16-byte shared
@@ -257,8 +302,11 @@ __global__ void __launch_bounds__(BT, 6)
         }
         if (lane == 31) ws[warp] = incl;
         __syncthreads();
-        uint32_t run = incl - sum;
-        for (int w = 0; w < warp; ++w) run += ws[w];
+        uint32_t run = incl - sum, placed = 0;  // placed: the tile's keys of this phase
+        for (int w = 0; w < BT / 32; ++w) {
+            run += w < warp ? ws[w] : 0u;
+            placed += ws[w];
+        }
         uint32_t st[DPT];
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
@@ -276,7 +324,7 @@ __global__ void __launch_bounds__(BT, 6)
 #pragma unroll
         for (int r = 0; r < BPT; ++r) {
             const int j = r * BT + tid;
-            if (j < T.nk) {
+            if ((in >> r) & 1u) {
                 const uint32_t p = h[bucket_of(kv[r])] + rk[r];
                 skey[p] = kv[r];
                 sval[p] = (uint32_t)(T.t0 + j);  // the survivor's slot
@@ -284,7 +332,7 @@ __global__ void __launch_bounds__(BT, 6)
         }
         __syncthreads();
         // ... and written out: consecutive threads, consecutive addresses of a run
-        for (int p = tid; p < T.nk; p += BT) {
+        for (int p = tid; p < (int)placed; p += BT) {
             const uint32_t key = skey[p];
             const long long at = T.seg_base + move[bucket_of(key)] + p;
             dk[at] = key;
@@ -364,10 +412,13 @@ struct WinItem {
     int seg;
 };
 
+// Item it of the phase map's windows.
 __device__ __forceinline__ WinItem load_item(const int4 *__restrict__ win,
-                                             const SortTile *__restrict__ tiles, int it, int items) {
+                                             const SortTile *__restrict__ tiles,
+                                             const int *__restrict__ map, int m, int it, int items) {
     WinItem I{make_int4(0, 0, 0, 0), 0, 0};
     if (it < items) {
+        it = phase_item(map, m, MAP_WINDOWS, it);
         I.w = win[it];
         const SortTile T = tiles[it / WPS];
         I.base = T.seg_base;
@@ -415,8 +466,8 @@ struct EqRun {
 constexpr int LOCAL_RUNS = WT;  // runs of a window gathered before they are listed
 static_assert(LOCAL_RUNS <= WT, "one thread per gathered run");
 
-// Each block takes windows blockIdx.x, + gridDim.x, ...; while it sorts one,
-// the next is copied into the other stage. ends[seg][b]: the end of bucket b
+// Each block takes windows blockIdx.x, + gridDim.x, ... of the phase map;
+// while it sorts one, the next is copied into the other stage. ends[seg][b]: the end of bucket b
 // (the scatter's final cursor). A key of bucket b goes to one of the bucket's
 // c bins by its low bits (one bin per key on average); its place is the bin's
 // start plus the number of the bin's keys below it, equal keys by their staged
@@ -430,7 +481,7 @@ static_assert(LOCAL_RUNS <= WT, "one thread per gathered run");
 __global__ void __launch_bounds__(WT, 4)
     k_depth_window(const uint32_t *__restrict__ K, uint32_t *__restrict__ V,
                    const uint32_t *__restrict__ oidx, const SortTile *__restrict__ tiles,
-                   const int *__restrict__ n_tiles_dev, const int4 *__restrict__ win,
+                   const int *__restrict__ map, int m, const int4 *__restrict__ win,
                    const uint32_t *__restrict__ ends, BigWin *__restrict__ big, long long big_cap,
                    int *__restrict__ n_big, EqRun *__restrict__ eq, long long eq_cap,
                    int *__restrict__ n_eq) {
@@ -441,21 +492,21 @@ __global__ void __launch_bounds__(WT, 4)
     __shared__ uint2 local_runs[LOCAL_RUNS];  // (first position in the window, length)
     __shared__ int n_local, list_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int items = WPS * *n_tiles_dev;
+    const int items = map[1];
     const int G = gridDim.x;
     for (int b = tid; b < WT * BW_MAX; b += WT) bins[b] = 0;
     if (tid == 0) n_local = 0;
     int it = blockIdx.x;
-    WinItem cur = load_item(win, tiles, it, items);
+    WinItem cur = load_item(win, tiles, map, m, it, items);
     stage_item(cur, K, V, ends, stages);
-    WinItem nxt = load_item(win, tiles, it + G, items);
+    WinItem nxt = load_item(win, tiles, map, m, it + G, items);
     for (int st = 0; it < items; it += G, st ^= 1) {
         cp_async_wait_all();
         __syncthreads();  // this window is staged; the other stage is free
         stage_item(nxt, K, V, ends, stages + (st ^ 1));
         const WinItem I = cur;
         cur = nxt;
-        nxt = load_item(win, tiles, it + 2 * G, items);
+        nxt = load_item(win, tiles, map, m, it + 2 * G, items);
         const int n = I.w.y - I.w.x;
         if (!sorted_here(I.w)) {
             if (n >= 2 && tid == 0) list_window(big, big_cap, n_big, I.base, I.w.x, n);
@@ -801,13 +852,8 @@ size_t depth_big_bytes() { return sizeof(BigWin); }
 size_t depth_eq_bytes() { return sizeof(EqRun); }
 size_t tie_run_bytes() { return sizeof(TieRun); }
 
-cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
-                               const uint32_t *oidx, const SortTile *tiles, const int *tile_start,
-                               const long long *seg_start, int m, int grid, uint32_t *count,
-                               void *win, void *big, long long big_cap, void *eq, long long eq_cap,
-                               void *runs, long long run_cap, int *counters, cudaStream_t s) {
-    if (m <= 0) return cudaSuccess;
-    // per device, once: SM count and resident window blocks per SM
+// Per device, once: SM count and resident window blocks per SM.
+static cudaError_t depth_setup(int &sms, int &win_per) {
     static int sm_count[64] = {0}, win_per_sm[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -828,7 +874,43 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
         win_per_sm[dev] = std::max(per, 1);
         sm_count[dev] = n_sm;
     }
-    const int sms = sm_count[dev];
+    sms = sm_count[dev];
+    win_per = win_per_sm[dev];
+    return cudaSuccess;
+}
+
+// The window pass and what it lists (windows for the one-block sort, runs of
+// equal keys), for the windows of a phase map.
+static void depth_windows(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
+                          const uint32_t *oidx, const SortTile *tiles, const long long *seg_start,
+                          const int *map, int m, int grid, const uint32_t *ends, const int4 *w4,
+                          void *big, long long big_cap, void *eq, long long eq_cap, void *runs,
+                          long long run_cap, int *counters, int sms, int win_per, cudaStream_t s) {
+    k_depth_window<<<std::min(WPS * grid, sms * win_per), WT, WINDOW_SMEM, s>>>(
+        sk, sv, oidx, tiles, map, m, w4, ends, (BigWin *)big, big_cap, counters + 1, (EqRun *)eq,
+        eq_cap, counters + 2);
+    // listed windows: keys and slots sorted through the free keys / vals arrays
+    k_depth_big<<<sms, LT, BIG_SMEM, s>>>(sk, sv, keys, vals, oidx, (const BigWin *)big, big_cap,
+                                          counters + 1, (TieRun *)runs, run_cap, counters);
+    k_tie_long<<<sms, LT, 0, s>>>(sk, sv, keys, vals, oidx, (const TieRun *)runs, run_cap,
+                                  counters);
+    // last: a listed window's runs are already in order when the block sort has
+    // written it, so ordering them again changes nothing
+    k_tie_short<<<sms * 4, 256, 0, s>>>(sv, oidx, seg_start, (const EqRun *)eq, eq_cap,
+                                        counters + 2);
+}
+
+cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
+                               const uint32_t *oidx, const SortTile *tiles, const int *tile_start,
+                               const long long *seg_start, int m, int grid, uint32_t *count,
+                               void *win, void *big, long long big_cap, void *eq, long long eq_cap,
+                               void *runs, long long run_cap, int *counters, DepthCut *cut,
+                               int prefix, const int *blkpre, int bin_ranks, int *map,
+                               cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    int sms = 0, win_per = 0;
+    cudaError_t e = depth_setup(sms, win_per);
+    if (e != cudaSuccess) return e;
     const int *n_tiles_dev = tile_start + m;
     e = cudaMemsetAsync(count, 0, (size_t)m * NB * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
@@ -836,20 +918,33 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
     if (e != cudaSuccess) return e;
     int4 *w4 = (int4 *)win;
     k_depth_count<<<grid, BT, 0, s>>>(keys, tiles, n_tiles_dev, count);
-    k_depth_scan<<<m, 1024, 0, s>>>(count, w4, tile_start);
-    k_depth_scatter<<<grid, BT, 0, s>>>(keys, sk, sv, tiles, n_tiles_dev, count);
-    k_depth_window<<<std::min(WPS * grid, sms * win_per_sm[dev]), WT, WINDOW_SMEM, s>>>(
-        sk, sv, oidx, tiles, n_tiles_dev, w4, count, (BigWin *)big, big_cap, counters + 1,
-        (EqRun *)eq, eq_cap, counters + 2);
-    // listed windows: keys and slots sorted through the free keys / vals arrays
-    k_depth_big<<<sms, LT, BIG_SMEM, s>>>(sk, sv, keys, vals, oidx, (const BigWin *)big, big_cap,
-                                   counters + 1, (TieRun *)runs, run_cap, counters);
-    k_tie_long<<<sms, LT, 0, s>>>(sk, sv, keys, vals, oidx, (const TieRun *)runs, run_cap,
-                                  counters);
-    // last: a listed window's runs are already in order when the block sort has
-    // written it, so ordering them again changes nothing
-    k_tie_short<<<sms * 4, 256, 0, s>>>(sv, oidx, seg_start, (const EqRun *)eq, eq_cap,
-                                        counters + 2);
+    k_depth_scan<<<m, 1024, 0, s>>>(count, w4, tile_start, cut, prefix);
+    e = launch_phase_map(1, m, cut, nullptr, tile_start, blkpre, bin_ranks, map, nullptr, nullptr, s);
+    if (e != cudaSuccess) return e;
+    k_depth_scatter<1><<<grid, BT, 0, s>>>(keys, sk, sv, tiles, n_tiles_dev, count, cut, map, m,
+                                           nullptr, 0u);
+    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, map, m, grid, count, w4, big, big_cap,
+                  eq, eq_cap, runs, run_cap, counters, sms, win_per, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depth_finish(const float4 *rec, uint32_t near_bits, uint32_t *keys,
+                                uint32_t *vals, uint32_t *sk, uint32_t *sv, const uint32_t *oidx,
+                                const SortTile *tiles, const long long *seg_start, int m, int grid,
+                                uint32_t *count, void *win, void *big, long long big_cap, void *eq,
+                                long long eq_cap, void *runs, long long run_cap, int *counters,
+                                const DepthCut *cut, const int *map, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    int sms = 0, win_per = 0;
+    cudaError_t e = depth_setup(sms, win_per);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counters, 0, 3 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_depth_scatter<2><<<grid, BT, 0, s>>>(nullptr, sk, sv, tiles, nullptr, count, cut, map, m,
+                                           rec, near_bits);
+    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, map, m, grid, count,
+                  (const int4 *)win, big, big_cap, eq, eq_cap, runs, run_cap, counters, sms,
+                  win_per, s);
     return cudaGetLastError();
 }
 

@@ -152,7 +152,99 @@ __global__ void k_plan_tables(int m, int bin_ranks, const int *__restrict__ blkp
     }
 }
 
+// The work items of one phase of the progressive depth order (DepthCut): one
+// block, the chunk's segments PT at a time. Phase 1 lists every segment: its
+// first-phase windows (win1), its binning blocks up to the cut (all of them
+// when there is no second phase) and all its sort tiles. Phase 2 lists the
+// segments whose flag is set: their windows from win1 on, their binning blocks
+// from the one holding the cut on (that block bins its ranks below the cut
+// again, with the same result) and all their sort tiles.
+__global__ void __launch_bounds__(PT)
+    k_phase_map(int phase, int m, const DepthCut *__restrict__ cut, const int *__restrict__ flag,
+                const int *__restrict__ tile_start, const int *__restrict__ blkpre, int bin_ranks,
+                int *__restrict__ map, const int *__restrict__ rn,
+                unsigned long long *__restrict__ stats) {
+    constexpr int WPS = SORT_TILE_KEYS / DEPTH_WINDOW;  // window items per sort tile
+    __shared__ int ws32[PT / 32];
+    __shared__ int carry[4];  // listed segments, windows, binning blocks, sort tiles
+    const int tid = threadIdx.x;
+    const int M1 = m + 1;
+    int *pre_w = map + 4, *base_w = pre_w + M1;
+    int *pre_b = base_w + M1, *base_b = pre_b + M1;
+    int *pre_t = base_b + M1, *base_t = pre_t + M1;
+    if (tid < 4) carry[tid] = 0;
+    __syncthreads();
+    for (int b = 0; b < m; b += PT) {
+        const int i = b + tid;
+        int in = 0, nw = 0, nb = 0, nt = 0, bw = 0, bb = 0, bt = 0;
+        if (i < m) {
+            const DepthCut X = cut[i];
+            const int t0 = tile_start[i], t1 = tile_start[i + 1];
+            const int k0 = blkpre[i], k1 = blkpre[i + 1];
+            if (phase == 1) {
+                in = 1;
+                bw = WPS * t0;
+                nw = X.win1;
+                bb = k0;
+                nb = min(k1 - k0, (X.pos + bin_ranks - 1) / bin_ranks);
+                if (X.pos >= X.count) nb = k1 - k0;
+            } else if (flag[i] && X.pos < X.count) {
+                in = 1;
+                bw = WPS * t0 + X.win1;
+                nw = WPS * (t1 - t0) - X.win1;
+                bb = k0 + X.pos / bin_ranks;
+                nb = k1 - bb;
+            }
+            bt = t0;
+            nt = in ? t1 - t0 : 0;
+        }
+        int t_in, t_w, t_b, t_t;
+        const int o_in = block_excl_scan<int>(in, t_in, ws32) + carry[0];
+        const int o_w = block_excl_scan<int>(nw, t_w, ws32) + carry[1];
+        const int o_b = block_excl_scan<int>(nb, t_b, ws32) + carry[2];
+        const int o_t = block_excl_scan<int>(nt, t_t, ws32) + carry[3];
+        if (in) {
+            pre_w[o_in] = o_w;
+            base_w[o_in] = bw;
+            pre_b[o_in] = o_b;
+            base_b[o_in] = bb;
+            pre_t[o_in] = o_t;
+            base_t[o_in] = bt;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            carry[0] += t_in;
+            carry[1] += t_w;
+            carry[2] += t_b;
+            carry[3] += t_t;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int n = carry[0];
+        map[0] = n;
+        map[1] = carry[1];
+        map[2] = carry[2];
+        map[3] = carry[3];
+        pre_w[n] = carry[1];
+        pre_b[n] = carry[2];
+        pre_t[n] = carry[3];
+        if (phase == 2 && stats) {
+            atomicAdd(&stats[0], (unsigned long long)n);
+            atomicAdd(&stats[1], (unsigned long long)rn[0]);  // tiles that reached their cut
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_phase_map(int phase, int m, const DepthCut *cut, const int *flag,
+                             const int *tile_start, const int *blkpre, int bin_ranks, int *map,
+                             const int *rn, unsigned long long *stats, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    k_phase_map<<<1, PT, 0, s>>>(phase, m, cut, flag, tile_start, blkpre, bin_ranks, map, rn, stats);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_plan(CamInfo *cams, const int *counts, int m, int bin_ranks,
                         long long cap_survivors, int *blkpre, int *sorttiles, long long *segstart,

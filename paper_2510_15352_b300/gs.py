@@ -15,7 +15,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgs_b300.so")
-ABI_VERSION = 5
+ABI_VERSION = 6
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_OOM, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, \
     GS_ERR_NOT_FOUND = range(7)
@@ -33,7 +33,7 @@ class gs_config(ctypes.Structure):
                 ("pixels_per_thread", ctypes.c_int32), ("tiles_per_block", ctypes.c_int32),
                 ("workspace_survivors", ctypes.c_int64), ("sync_errors", ctypes.c_int32),
                 ("comp_batch", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("depth_prefix", ctypes.c_int32)]
 
 
 class gs_scene_desc(ctypes.Structure):
@@ -53,7 +53,9 @@ class gs_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("reserved0", ctypes.c_int32),
                 ("warp_iters", ctypes.c_int64), ("warp_iters_box", ctypes.c_int64),
                 ("warp_iters_blend", ctypes.c_int64), ("sort_windows_listed", ctypes.c_int64),
-                ("sort_equal_runs", ctypes.c_int64), ("sort_long_runs", ctypes.c_int64)]
+                ("sort_equal_runs", ctypes.c_int64), ("sort_long_runs", ctypes.c_int64),
+                ("depth_second_phase_cameras", ctypes.c_int64),
+                ("depth_resumed_tiles", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); the same set as include/gs.h declares
@@ -85,6 +87,7 @@ SIGNATURES = {
     "gs_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(gs_stats)]),
     "gs_sync": (ctypes.c_int, [_vp, _vp]),
     "gs_render_timeout_probe": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp]),
+    "gs_set_resume_capacity": (ctypes.c_int, [_vp, _i32]),
     "gs_debug_project": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _i64,
                                         ctypes.POINTER(_i64), _vp]),
     "gs_debug_tile_lists": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp, _i64,
@@ -149,6 +152,7 @@ gs_graph_destroy = lib.gs_graph_destroy
 gs_get_stats = lib.gs_get_stats
 gs_sync = lib.gs_sync
 gs_render_timeout_probe = lib.gs_render_timeout_probe
+gs_set_resume_capacity = lib.gs_set_resume_capacity
 gs_debug_project = lib.gs_debug_project
 gs_debug_tile_lists = lib.gs_debug_tile_lists
 gs_sort_segments = lib.gs_sort_segments
@@ -391,6 +395,10 @@ class Renderer:
         depth = torch.empty((1, H, W), dtype=torch.float32, device=viewmat.device)
         return int(gs_render_timeout_probe(self.ctx, sid, viewmat.data_ptr(), intr.data_ptr(), W, H,
                                            rgb.data_ptr(), depth.data_ptr(), _stream(stream)))
+
+    def set_resume_capacity(self, tiles: int) -> None:
+        """gs_set_resume_capacity: cap the first phase's saved-state list (0: default)."""
+        self._check(gs_set_resume_capacity(self.ctx, tiles))
 
     def sync(self, stream=None) -> None:
         """gs_sync: wait for the stream and the last render call; raise a
