@@ -386,7 +386,7 @@ def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, g
     depth = torch.empty((P,), dtype=torch.float32, device="cuda")
     kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
               tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch,
-              persistent=args.persistent)
+              persistent=args.persistent, depth_prefix=args.depth_prefix)
     counter = gs.Renderer(device=local, count_pairs=1, **kw)
     ids_c = np.array([counter.add_scene(sc) for sc in scenes], dtype=np.int32)[which]
     counter.render_v(ids_c, vm_d, it_d, Ws, Hs, rgb, depth)
@@ -445,7 +445,7 @@ def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, g
                    "frames_640x480_equivalent": eq_frames, "chunk_cameras": args.chunk,
                    "pixels_per_thread": args.ppt, "tiles_per_block": args.tpb,
                    "comp_batch": args.comp_batch, "camera_group": args.group,
-                   "persistent": args.persistent,
+                   "persistent": args.persistent, "depth_prefix": args.depth_prefix,
                    "cuda_graph": bool(graph),
                    "storage": "f32" if "dequantised" not in scenes[0] else "f16/bf16"},
         "roofline": {"kernel": "k_composite", "bound": "alu", "achieved": achieved,
@@ -472,7 +472,7 @@ def half_leg(args, gs, torch, synth, scenes, which, vm, local, stream, fp32_tflo
     R = gs.Renderer(device=local, time_stages=1, max_chunk_cameras=args.chunk,
                     pixels_per_thread=args.ppt, tiles_per_block=args.tpb,
                     camera_group=args.group, comp_batch=args.comp_batch,
-                    persistent=args.persistent)
+                    persistent=args.persistent, depth_prefix=args.depth_prefix)
     try:
         nbytes = 0
         sids = []
@@ -551,7 +551,7 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
                         device="cuda").expand(n, 4).contiguous()
     R = gs.Renderer(device=local, max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
                     tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch,
-                    persistent=args.persistent)
+                    persistent=args.persistent, depth_prefix=args.depth_prefix)
     sids = [R.add_scene(sc) for sc in scenes]
     ids = np.array(sids, dtype=np.int32)[which]
     up = gs.Upsampler(device=local)
@@ -677,7 +677,7 @@ def run_b300(args):
     # algorithmic work of the compositing kernel on these inputs (counting run)
     kw = dict(max_chunk_cameras=args.chunk, pixels_per_thread=args.ppt,
               tiles_per_block=args.tpb, camera_group=args.group, comp_batch=args.comp_batch,
-              persistent=args.persistent)
+              persistent=args.persistent, depth_prefix=args.depth_prefix)
     counter = gs.Renderer(device=local, count_pairs=1, **kw)
     sid_c = counter.add_scene(scene)
     counter.render(sid_c, vm_d, it_d, W, H, rgb, depth)
@@ -755,6 +755,7 @@ def run_b300(args):
                        "gaussians": int(scene["mean"].shape[1]), "sh_degree": 3,
                        "chunk_cameras": args.chunk, "pixels_per_thread": args.ppt,
                        "tiles_per_block": args.tpb, "storage": args.precision,
+                       "depth_prefix": args.depth_prefix,
                        "l2": "inputs larger than L2 (scene 236 MB; 20 GB of outputs per step)"},
             "roofline": {
                 "kernel": "k_composite", "bound": "alu", "achieved": achieved,
@@ -853,6 +854,9 @@ def main():
                     help="compositing tiles per block (1 | 4 = 2x2 quads, with --ppt 8)")
     ap.add_argument("--comp-batch", type=int, default=32,
                     help="records staged per compositing batch (32|64|96|128, with --ppt 8)")
+    ap.add_argument("--depth-prefix", type=int, default=0,
+                    help="progressive depth order: ranks ordered first per camera "
+                         "(0: the library default, -1: the whole order at once)")
     ap.add_argument("--persistent", type=int, default=0,
                     help="1: binning + compositing as one persistent launch (with --ppt 8)")
     ap.add_argument("--precision", choices=["f32", "half"], default="f32",

@@ -412,13 +412,13 @@ struct WinItem {
     int seg;
 };
 
-// Item it of the phase map's windows.
+// Item it of the phase map's windows (map == nullptr: window item it).
 __device__ __forceinline__ WinItem load_item(const int4 *__restrict__ win,
                                              const SortTile *__restrict__ tiles,
                                              const int *__restrict__ map, int m, int it, int items) {
     WinItem I{make_int4(0, 0, 0, 0), 0, 0};
     if (it < items) {
-        it = phase_item(map, m, MAP_WINDOWS, it);
+        if (map) it = phase_item(map, m, MAP_WINDOWS, it);
         I.w = win[it];
         const SortTile T = tiles[it / WPS];
         I.base = T.seg_base;
@@ -481,7 +481,8 @@ static_assert(LOCAL_RUNS <= WT, "one thread per gathered run");
 __global__ void __launch_bounds__(WT, 4)
     k_depth_window(const uint32_t *__restrict__ K, uint32_t *__restrict__ V,
                    const uint32_t *__restrict__ oidx, const SortTile *__restrict__ tiles,
-                   const int *__restrict__ map, int m, const int4 *__restrict__ win,
+                   const int *__restrict__ map, int m, const int *__restrict__ n_tiles_dev,
+                   const int4 *__restrict__ win,
                    const uint32_t *__restrict__ ends, BigWin *__restrict__ big, long long big_cap,
                    int *__restrict__ n_big, EqRun *__restrict__ eq, long long eq_cap,
                    int *__restrict__ n_eq) {
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(WT, 4)
     __shared__ uint2 local_runs[LOCAL_RUNS];  // (first position in the window, length)
     __shared__ int n_local, list_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int items = map[1];
+    const int items = map ? map[1] : WPS * *n_tiles_dev;
     const int G = gridDim.x;
     for (int b = tid; b < WT * BW_MAX; b += WT) bins[b] = 0;
     if (tid == 0) n_local = 0;
@@ -883,12 +884,13 @@ static cudaError_t depth_setup(int &sms, int &win_per) {
 // equal keys), for the windows of a phase map.
 static void depth_windows(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
                           const uint32_t *oidx, const SortTile *tiles, const long long *seg_start,
-                          const int *map, int m, int grid, const uint32_t *ends, const int4 *w4,
+                          const int *map, int m, const int *n_tiles_dev, int grid,
+                          const uint32_t *ends, const int4 *w4,
                           void *big, long long big_cap, void *eq, long long eq_cap, void *runs,
                           long long run_cap, int *counters, int sms, int win_per, cudaStream_t s) {
     k_depth_window<<<std::min(WPS * grid, sms * win_per), WT, WINDOW_SMEM, s>>>(
-        sk, sv, oidx, tiles, map, m, w4, ends, (BigWin *)big, big_cap, counters + 1, (EqRun *)eq,
-        eq_cap, counters + 2);
+        sk, sv, oidx, tiles, map, m, n_tiles_dev, w4, ends, (BigWin *)big, big_cap, counters + 1,
+        (EqRun *)eq, eq_cap, counters + 2);
     // listed windows: keys and slots sorted through the free keys / vals arrays
     k_depth_big<<<sms, LT, BIG_SMEM, s>>>(sk, sv, keys, vals, oidx, (const BigWin *)big, big_cap,
                                           counters + 1, (TieRun *)runs, run_cap, counters);
@@ -923,8 +925,10 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
     if (e != cudaSuccess) return e;
     k_depth_scatter<1><<<grid, BT, 0, s>>>(keys, sk, sv, tiles, n_tiles_dev, count, cut, map, m,
                                            nullptr, 0u);
-    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, map, m, grid, count, w4, big, big_cap,
-                  eq, eq_cap, runs, run_cap, counters, sms, win_per, s);
+    // the whole order (prefix < 0): every window item, no map
+    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, prefix < 0 ? nullptr : map, m,
+                  n_tiles_dev, grid, count, w4, big, big_cap, eq, eq_cap, runs, run_cap, counters,
+                  sms, win_per, s);
     return cudaGetLastError();
 }
 
@@ -942,7 +946,7 @@ cudaError_t launch_depth_finish(const float4 *rec, uint32_t near_bits, uint32_t 
     if (e != cudaSuccess) return e;
     k_depth_scatter<2><<<grid, BT, 0, s>>>(nullptr, sk, sv, tiles, nullptr, count, cut, map, m,
                                            rec, near_bits);
-    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, map, m, grid, count,
+    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, map, m, nullptr, grid, count,
                   (const int4 *)win, big, big_cap, eq, eq_cap, runs, run_cap, counters, sms,
                   win_per, s);
     return cudaGetLastError();
