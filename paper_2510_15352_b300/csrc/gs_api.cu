@@ -88,6 +88,7 @@ struct gs_context {
     // the progressive depth order: per camera its cut, the two phase maps, the
     // second phase's counts and camera flags, saved tile states, tiles to render again
     DevBuf dcut, pmap, prog, rsaved, rstate, ragain;
+    DevBuf gslot;  // per survivor slot: its Gaussian's position in the scene (progressive order)
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
     int workspace_gen = 0;        // bumped when a chunk-workspace buffer is reallocated
@@ -339,7 +340,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
                       &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status,
                       &ctx->oidx,     &ctx->ties,     &ctx->nruns,    &ctx->pq,
                       &ctx->dcut,     &ctx->pmap,     &ctx->prog,     &ctx->rsaved,
-                      &ctx->rstate,   &ctx->ragain};
+                      &ctx->rstate,   &ctx->ragain,   &ctx->gslot};
     // (compared by capacity: a reallocation may return the freed address)
     size_t before[sizeof(held) / sizeof(held[0])];
     for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->cap;
@@ -357,6 +358,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->tkeys, (Sx + 4) * 4));
     CKS(grow(ctx, ctx->tvals, (Sx + 4) * 4));
     CKS(grow(ctx, ctx->oidx, Sx * 4));
+    CKS(grow(ctx, ctx->gslot, Sx * 4));
     CKS(grow(ctx, ctx->ties, (Sx / 33 + 2) * tie_run_bytes()));
     CKS(grow(ctx, ctx->nruns, 6 * (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->pq, (size_t)(m + 2) * sizeof(int)));
@@ -438,6 +440,12 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         DepthCut *cut = (DepthCut *)ctx->dcut.p;
         int *map1 = (int *)ctx->pmap.p, *map2 = map1 + phase_map_ints(ch.m);
         int *prog_n = (int *)ctx->prog.p;  // [2] counts, then [m] flags
+        // the one-block sort's scratch: the slot-order rects' array (unused by the
+        // progressive order), so that the keys stay for its second phase
+        const size_t n_slots_ws = ctx->srect.cap / sizeof(uint2);
+        uint32_t *scr_k = prog ? (uint32_t *)ctx->srect.p : (uint32_t *)ctx->keys.p;
+        uint32_t *scr_v = prog ? (uint32_t *)ctx->srect.p + n_slots_ws : (uint32_t *)ctx->vals.p;
+        const float ln_amin = std::log(cfg.alpha_min);
         Resume R{prog_n + 2, prog_n, (int2 *)ctx->rsaved.p, (float4 *)ctx->rstate.p,
                  (int2 *)ctx->ragain.p,
                  (int)std::min(ctx->rsaved.cap / sizeof(int2),
@@ -456,12 +464,19 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                         (long long *)ctx->segcount.p, (SortTile *)ctx->sorttab.p,
                         (int2 *)ctx->bintab.p, status, need, stats + 6,
                         (unsigned long long *)ctx->sticky.p, st));
-        CKC(launch_project_write(groups, ch.n_groups, ch.max_bx, (const SceneDev *)ctx->d_scenes.p,
-                                 cams, ctx->camtab.p, PP, (const uint32_t *)ctx->masks.p,
-                                 (const uint32_t *)ctx->woff.p, recs, with_d,
-                                 (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p,
-                                 (uint32_t *)ctx->oidx.p, std::log(cfg.alpha_min), status,
-                                 ch.max_deg, st));
+        if (prog)  // keys only: the records of the ranks read come from the binning pass
+            CKC(launch_project_keys(groups, ch.n_groups, ch.max_bx,
+                                    (const SceneDev *)ctx->d_scenes.p, cams, ctx->camtab.p, PP,
+                                    (const uint32_t *)ctx->masks.p, (const uint32_t *)ctx->woff.p,
+                                    (uint32_t *)ctx->keys.p, (uint32_t *)ctx->gslot.p,
+                                    (uint32_t *)ctx->oidx.p, status, st));
+        else
+            CKC(launch_project_write(groups, ch.n_groups, ch.max_bx,
+                                     (const SceneDev *)ctx->d_scenes.p, cams, ctx->camtab.p, PP,
+                                     (const uint32_t *)ctx->masks.p, (const uint32_t *)ctx->woff.p,
+                                     recs, with_d, (uint2 *)ctx->srect.p, (uint32_t *)ctx->keys.p,
+                                     (uint32_t *)ctx->oidx.p, std::log(cfg.alpha_min), status,
+                                     ch.max_deg, st));
         if (E) CKC(cudaEventRecord(E[1], st));
         if (a.upto == UPTO_PROJECT) break;
         // every camera's survivors in (depth, caller index) order, into tkeys / tvals
@@ -474,15 +489,21 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                                ctx->deq.p, (long long)(ctx->deq.cap / depth_eq_bytes()),
                                ctx->ties.p, (long long)(ctx->ties.cap / tie_run_bytes()),
                                (int *)ctx->nruns.p + 6 * k, cut, prog ? cfg.depth_prefix : -1,
-                               (const int *)ctx->blkpre.p, ch.bin_ranks, map1, st));
+                               (const int *)ctx->blkpre.p, ch.bin_ranks, map1, scr_k, scr_v, st));
         if (E) CKC(cudaEventRecord(E[2], st));
         const bool persist = ch.persistent && a.upto == UPTO_ALL;
-        if (!persist)
+        if (prog)
+            CKC(launch_bin_rec(cams, (const int2 *)ctx->bintab.p, ch.m, ch.bin_grid, ch.max_sup,
+                               ch.bin_ranks, (const SceneDev *)ctx->d_scenes.p, ctx->camtab.p, PP,
+                               ln_amin, (const uint32_t *)ctx->gslot.p,
+                               (const uint32_t *)ctx->tvals.p, recs, (uint2 *)ctx->rrect.p,
+                               (uint32_t *)ctx->bitmap.p, stats + 2, cut, 1, map1, st));
+        else if (!persist)
             CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
                            ch.bin_grid, ch.max_sup,
                            ch.bin_ranks, (const uint2 *)ctx->srect.p, (const uint32_t *)ctx->tvals.p,
-                           (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, cut,
-                           prog ? 1 : 0, map1, st));
+                           (uint2 *)ctx->rrect.p, (uint32_t *)ctx->bitmap.p, stats + 2, cut, 0,
+                           map1, st));
         if (E) CKC(cudaEventRecord(E[3], st));
         if (a.upto == UPTO_BIN) break;
         if (persist) {
@@ -514,11 +535,9 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         if (E) CKC(cudaEventRecord(E[4], st));
         if (prog) {
             // the second phase: the flagged cameras' remaining ranks, their tiles resumed
-            uint32_t near_bits;
-            memcpy(&near_bits, &cfg.near_plane, 4);
             CKC(launch_phase_map(2, ch.m, cut, R.flag, (const int *)ctx->sorttiles.p,
                                  (const int *)ctx->blkpre.p, ch.bin_ranks, map2, R.n, stats + 7, st));
-            CKC(launch_depth_finish(recs, near_bits, (uint32_t *)ctx->keys.p, (uint32_t *)ctx->vals.p,
+            CKC(launch_depth_finish((const uint32_t *)ctx->keys.p, scr_k, scr_v,
                                     (uint32_t *)ctx->tkeys.p, (uint32_t *)ctx->tvals.p,
                                     (const uint32_t *)ctx->oidx.p, (const SortTile *)ctx->sorttab.p,
                                     (const long long *)ctx->segstart.p, ch.m, ch.sort_grid,
@@ -528,10 +547,11 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                                     (long long)(ctx->ties.cap / tie_run_bytes()),
                                     (int *)ctx->nruns.p + 6 * k + 3, cut, map2, st));
             if (E) CKC(cudaEventRecord(E[5], st));
-            CKC(launch_bin(cams, (const int *)ctx->blkpre.p, (const int2 *)ctx->bintab.p, ch.m,
-                           ch.bin_grid, ch.max_sup, ch.bin_ranks, (const uint2 *)ctx->srect.p,
-                           (const uint32_t *)ctx->tvals.p, (uint2 *)ctx->rrect.p,
-                           (uint32_t *)ctx->bitmap.p, stats + 2, cut, 2, map2, st));
+            CKC(launch_bin_rec(cams, (const int2 *)ctx->bintab.p, ch.m, ch.bin_grid, ch.max_sup,
+                               ch.bin_ranks, (const SceneDev *)ctx->d_scenes.p, ctx->camtab.p, PP,
+                               ln_amin, (const uint32_t *)ctx->gslot.p,
+                               (const uint32_t *)ctx->tvals.p, recs, (uint2 *)ctx->rrect.p,
+                               (uint32_t *)ctx->bitmap.p, stats + 2, cut, 2, map2, st));
             if (E) CKC(cudaEventRecord(E[6], st));
             CKC(launch_composite_resume(cams, recs, (const uint32_t *)ctx->tvals.p,
                                         (const uint2 *)ctx->rrect.p, (const uint32_t *)ctx->bitmap.p,
@@ -843,7 +863,7 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->ties,
                       &ctx->nruns,    &ctx->pq,
                       &ctx->dcut,     &ctx->pmap,   &ctx->prog,   &ctx->rsaved,  &ctx->rstate,
-                      &ctx->ragain,
+                      &ctx->ragain,   &ctx->gslot,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -900,6 +920,11 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
     total += align_up((size_t)n * 4, 256);
     const size_t off_bounds = total;
     total += align_up((size_t)nblk * 2 * sizeof(float4), 256);
+    // rows per Gaussian for the progressive order's records (see SceneDev)
+    const size_t off_geo_rows = total;
+    total += align_up((size_t)n * 4 * sizeof(float4), 256);
+    const size_t off_sh_rows = total;
+    total += align_up((size_t)n * 48 * as, 256);
     SceneSlot slot;
     slot.live = true;
     if (n > 0) {
@@ -951,6 +976,19 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
         if (e == cudaSuccess)
             e = launch_block_bounds(st + offs[0], st + offs[1], d->geometry_dtype, n,
                                     (float4 *)(st + off_bounds), nullptr);
+        if (e == cudaSuccess) {
+            SceneDev sd{};
+            sd.mean = st + offs[0];
+            sd.log_scale = st + offs[1];
+            sd.quat = st + offs[2];
+            sd.logit = st + offs[3];
+            sd.sh = st + offs[4];
+            sd.n = n;
+            sd.deg = d->sh_degree;
+            sd.geo_dtype = d->geometry_dtype;
+            sd.app_dtype = d->appearance_dtype;
+            e = launch_scene_rows(sd, (float4 *)(st + off_geo_rows), st + off_sh_rows, nullptr);
+        }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(tmp);
         if (e != cudaSuccess) {
@@ -966,6 +1004,8 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
     slot.dev.sh = b + offs[4];
     slot.dev.orig = (const int *)(b + off_orig);
     slot.dev.bounds = (const float4 *)(b + off_bounds);
+    slot.dev.geo_rows = (const float4 *)(b + off_geo_rows);
+    slot.dev.sh_rows = b + off_sh_rows;
     slot.dev.n = n;
     slot.dev.deg = d->sh_degree;
     slot.dev.geo_dtype = d->geometry_dtype;

@@ -50,6 +50,13 @@ struct SceneDev {
     const void *mean, *log_scale, *quat, *logit, *sh;
     const int *orig;
     const float4 *bounds;
+    // one row per Gaussian, for the records of the progressive order (read at
+    // random positions): geo_rows 4 float4 = (mean, log2 o), M = R(q) S by rows
+    // (M0..M3, M4..M7, M8), computed as the projection passes compute them;
+    // sh_rows 48 coefficients of the appearance type, channel-major ([ch][16],
+    // zero past the degree)
+    const float4 *geo_rows;
+    const void *sh_rows;
     long long n;
     int deg, geo_dtype, app_dtype, pad;
 };
@@ -131,6 +138,15 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  uint2 *srect, uint32_t *keys, uint32_t *oidx,
                                  float ln_alpha_min, const int *status, int max_deg,
                                  cudaStream_t s);
+// The progressive order's projection output (instead of launch_project_write):
+// per survivor slot only the depth key, the Gaussian's position in its scene
+// (gslot) and its caller index; the records of the ranks the render reads are
+// computed later by launch_bin_rec.
+cudaError_t launch_project_keys(const Group *groups, int n_groups, int max_blocks_x,
+                                const SceneDev *scenes, const CamInfo *cams, const void *camtab,
+                                ProjParams P, const uint32_t *masks, const uint32_t *woff,
+                                uint32_t *keys, uint32_t *gslot, uint32_t *oidx, const int *status,
+                                cudaStream_t s);
 
 // Scene set-up (k_scene.cu): Morton codes of the means (box: 6 words of
 // scratch) with idx = 0..n-1, to be sorted as (code, idx); a gather of `rows`
@@ -139,6 +155,8 @@ cudaError_t launch_scene_morton(const void *mean, int dtype, long long n, unsign
                                 uint32_t *code, uint32_t *idx, cudaStream_t s);
 cudaError_t launch_gather_rows(const void *src, void *dst, int elem_bytes, const uint32_t *perm,
                                long long n, int rows, cudaStream_t s);
+// A stored scene's geo_rows / sh_rows (see SceneDev) from its attribute arrays.
+cudaError_t launch_scene_rows(const SceneDev &s, float4 *geo_rows, void *sh_rows, cudaStream_t st);
 long long scene_blocks(long long n);
 cudaError_t launch_block_bounds(const void *mean, const void *log_scale, int dtype, long long n,
                                 float4 *bounds, cudaStream_t s);
@@ -241,9 +259,11 @@ cudaError_t launch_phase_map(int phase, int m, const DepthCut *cut, const int *f
 // minus the near plane's bits, slot order) cut (cut, from prefix: < 0 the whole
 // segment, 0 the default, > 0 that many ranks) and its first-phase ranks
 // sorted by (key, oidx[seg_base + slot]); the slots in that order end in sv.
-// map: the chunk's phase map, written here (phase 1). sk, keys and vals are
-// scratch (sk and sv hold at least 4 elements past the chunk's survivors: the
-// window pass copies 16-byte pieces). tiles / tile_start: the chunk's SortTile
+// map: the chunk's phase map, written here (phase 1). keys are read only; sk
+// and the one-block sort's scratch scr_k / scr_v (the chunk's survivors each)
+// are overwritten (sk and sv hold at least 4 elements past the chunk's
+// survivors: the window pass copies 16-byte pieces); scratch other than keys
+// keeps the keys for the second phase. tiles / tile_start: the chunk's SortTile
 // table and per-segment tile prefix (tile_start[m] the total, on the device);
 // seg_start: the segments' first positions; blkpre / bin_ranks: the binning
 // blocks (for the map). Work buffers: count (DEPTH_BUCKETS uint32 per segment),
@@ -258,13 +278,12 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
                                void *win, void *big, long long big_cap, void *eq, long long eq_cap,
                                void *runs, long long run_cap, int *counters, DepthCut *cut,
                                int prefix, const int *blkpre, int bin_ranks, int *map,
-                               cudaStream_t s);
+                               uint32_t *scr_k, uint32_t *scr_v, cudaStream_t s);
 // The second phase: the flagged segments' ranks [pos, count) (map: the phase-2
-// map, written before), their keys taken from the records' depth (rec, the
-// near plane's bits) since the first phase's block sort may have used the key
-// array as scratch. Same buffers as the first phase; counters: 3 more ints.
-cudaError_t launch_depth_finish(const float4 *rec, uint32_t near_bits, uint32_t *keys,
-                                uint32_t *vals, uint32_t *sk, uint32_t *sv, const uint32_t *oidx,
+// map, written before). Same buffers as the first phase (whose scratch must not
+// have been keys); counters: 3 more ints.
+cudaError_t launch_depth_finish(const uint32_t *keys, uint32_t *scr_k, uint32_t *scr_v,
+                                uint32_t *sk, uint32_t *sv, const uint32_t *oidx,
                                 const SortTile *tiles, const long long *seg_start, int m, int grid,
                                 uint32_t *count, void *win, void *big, long long big_cap, void *eq,
                                 long long eq_cap, void *runs, long long run_cap, int *counters,
@@ -297,6 +316,16 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *b
                        int n_super, int bin_ranks, const uint2 *srect, const uint32_t *vals,
                        uint2 *rrect, uint32_t *bitmap, unsigned long long *n_isect,
                        const DepthCut *cut, int phase, const int *map, cudaStream_t s);
+// The binning blocks of a phase map (phase 1 / 2, as launch_bin) that also
+// compute each binned rank's record (the projection passes' arithmetic, from
+// the scene rows of its Gaussian gslot[seg_off + slot]) into rec at the rank's
+// position, and its rect.
+cudaError_t launch_bin_rec(const CamInfo *cams, const int2 *bintab, int n_slots, int n_blocks,
+                           int n_super, int bin_ranks, const SceneDev *scenes, const void *camtab,
+                           ProjParams P, float ln_alpha_min, const uint32_t *gslot,
+                           const uint32_t *vals, float4 *rec, uint2 *rrect, uint32_t *bitmap,
+                           unsigned long long *n_isect, const DepthCut *cut, int phase,
+                           const int *map, cudaStream_t s);
 
 // Binning and compositing of a chunk in one persistent launch (k_composite.cu):
 // 8 pixels per thread, binning items of BIN_RANKS_SMALL ranks (the plan must

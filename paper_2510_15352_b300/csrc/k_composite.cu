@@ -339,7 +339,10 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
             int nstaged = 0;
             for (int q0 = 0; q0 < nb; q0 += NT) {
                 const int q = q0 + tid;
-                const long long sl = rec0 + cv[cand[j0 + min(q, nb - 1)]];
+                // the record of a rank: by its slot, or (the progressive order) at
+                // the rank's own position
+                const uint32_t rk = cand[j0 + min(q, nb - 1)];
+                const long long sl = rec0 + (PH != 0 ? (long long)rk : (long long)cv[rk]);
                 const float4 a = rec[rec_a(sl)], b = rec[rec_b(sl)], cc = rec[rec_c(sl)];
                 // warps some pixel of which can pass the alpha test: the box of the
                 // alpha >= alpha_min region meets the warp's rows and the largest p

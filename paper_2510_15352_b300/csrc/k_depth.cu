@@ -229,14 +229,13 @@ __global__ void __launch_bounds__(1024)
 // round trip, and more blocks hide more of it (4.2 -> 4.0 ms per 4,096 cameras
 // against four). Phase 1: every sort tile, the keys of buckets before the
 // segment's cut; phase 2: the sort tiles of the phase map, the keys of the
-// cut's bucket and after, read from the records' depth (rec, near_bits).
+// cut's bucket and after.
 template <int phase>
 __global__ void __launch_bounds__(BT, 6)
     k_depth_scatter(const uint32_t *__restrict__ keys, uint32_t *__restrict__ dk,
                     uint32_t *__restrict__ dv, const SortTile *__restrict__ tiles,
                     const int *__restrict__ n_tiles_dev, uint32_t *__restrict__ cursor,
-                    const DepthCut *__restrict__ cut, const int *__restrict__ map, int m,
-                    const float4 *__restrict__ rec, uint32_t near_bits) {
+                    const DepthCut *__restrict__ cut, const int *__restrict__ map, int m) {
     constexpr int DPT = NB / BT;  // buckets per thread (8), read and written as uint4 pairs
     static_assert(DPT == 8, "two uint4 per thread");
     __shared__ __align__(16) uint32_t h[NB];  // counts, then where each bucket starts in the tile
@@ -253,14 +252,7 @@ __global__ void __launch_bounds__(BT, 6)
         for (int d = tid; d < NB; d += BT) h[d] = 0;
         uint32_t kv[BPT], rk[BPT];
         uint32_t in = 0;  // bit r: key r of this thread belongs to the phase
-        if constexpr (phase == 2) {
-            const long long s0 = T.seg_base + T.t0;
-#pragma unroll
-            for (int r = 0; r < BPT; ++r) {
-                const int j = r * BT + tid;
-                kv[r] = j < T.nk ? __float_as_uint(rec[rec_c(s0 + j)].w) - near_bits : 0u;
-            }
-        } else {
+        {
             const uint32_t *k = keys + T.seg_base + T.t0;
 #pragma unroll
             for (int r = 0; r < BPT; ++r) {
@@ -882,6 +874,7 @@ static cudaError_t depth_setup(int &sms, int &win_per) {
 
 // The window pass and what it lists (windows for the one-block sort, runs of
 // equal keys), for the windows of a phase map.
+// keys / vals: the one-block sort's and the long ties' scratch.
 static void depth_windows(uint32_t *keys, uint32_t *vals, uint32_t *sk, uint32_t *sv,
                           const uint32_t *oidx, const SortTile *tiles, const long long *seg_start,
                           const int *map, int m, const int *n_tiles_dev, int grid,
@@ -908,7 +901,7 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
                                void *win, void *big, long long big_cap, void *eq, long long eq_cap,
                                void *runs, long long run_cap, int *counters, DepthCut *cut,
                                int prefix, const int *blkpre, int bin_ranks, int *map,
-                               cudaStream_t s) {
+                               uint32_t *scr_k, uint32_t *scr_v, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
     int sms = 0, win_per = 0;
     cudaError_t e = depth_setup(sms, win_per);
@@ -923,17 +916,16 @@ cudaError_t launch_depth_order(uint32_t *keys, uint32_t *vals, uint32_t *sk, uin
     k_depth_scan<<<m, 1024, 0, s>>>(count, w4, tile_start, cut, prefix);
     e = launch_phase_map(1, m, cut, nullptr, tile_start, blkpre, bin_ranks, map, nullptr, nullptr, s);
     if (e != cudaSuccess) return e;
-    k_depth_scatter<1><<<grid, BT, 0, s>>>(keys, sk, sv, tiles, n_tiles_dev, count, cut, map, m,
-                                           nullptr, 0u);
+    k_depth_scatter<1><<<grid, BT, 0, s>>>(keys, sk, sv, tiles, n_tiles_dev, count, cut, map, m);
     // the whole order (prefix < 0): every window item, no map
-    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, prefix < 0 ? nullptr : map, m,
+    depth_windows(scr_k, scr_v, sk, sv, oidx, tiles, seg_start, prefix < 0 ? nullptr : map, m,
                   n_tiles_dev, grid, count, w4, big, big_cap, eq, eq_cap, runs, run_cap, counters,
                   sms, win_per, s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_depth_finish(const float4 *rec, uint32_t near_bits, uint32_t *keys,
-                                uint32_t *vals, uint32_t *sk, uint32_t *sv, const uint32_t *oidx,
+cudaError_t launch_depth_finish(const uint32_t *keys, uint32_t *scr_k, uint32_t *scr_v,
+                                uint32_t *sk, uint32_t *sv, const uint32_t *oidx,
                                 const SortTile *tiles, const long long *seg_start, int m, int grid,
                                 uint32_t *count, void *win, void *big, long long big_cap, void *eq,
                                 long long eq_cap, void *runs, long long run_cap, int *counters,
@@ -944,9 +936,8 @@ cudaError_t launch_depth_finish(const float4 *rec, uint32_t near_bits, uint32_t 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counters, 0, 3 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_depth_scatter<2><<<grid, BT, 0, s>>>(nullptr, sk, sv, tiles, nullptr, count, cut, map, m,
-                                           rec, near_bits);
-    depth_windows(keys, vals, sk, sv, oidx, tiles, seg_start, map, m, nullptr, grid, count,
+    k_depth_scatter<2><<<grid, BT, 0, s>>>(keys, sk, sv, tiles, nullptr, count, cut, map, m);
+    depth_windows(scr_k, scr_v, sk, sv, oidx, tiles, seg_start, map, m, nullptr, grid, count,
                   (const int4 *)win, big, big_cap, eq, eq_cap, runs, run_cap, counters, sms,
                   win_per, s);
     return cudaGetLastError();

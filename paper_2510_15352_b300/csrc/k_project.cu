@@ -30,73 +30,11 @@
 // passes round identically.
 #include <type_traits>
 
-#include "gs_internal.cuh"
+#include "proj_core.cuh"
 
 namespace gsk {
 
 namespace {
-
-// 28 words = 7 float4 (loaded as such from shared memory)
-struct __align__(16) CamProj {
-    float R[9], t[3];
-    float fx, fy, cx, cy;
-    float lxp, lxn, lyp, lyn;  // guard-band limits of x/z and y/z
-    float cpos[3];             // camera centre in world coordinates
-    float kk;                  // bound of z^2 |J|_F^2 over the guard band
-    float W, H;
-    int TX, TY;
-};
-static_assert(sizeof(CamProj) == 7 * 16, "CamProj is seven float4");
-
-__device__ __forceinline__ CamProj load_cam(const CamProj &src) {
-    CamProj c;
-    const float4 *s4 = reinterpret_cast<const float4 *>(&src);
-    float4 *d4 = reinterpret_cast<float4 *>(&c);
-#pragma unroll
-    for (int k = 0; k < 7; ++k) d4[k] = s4[k];
-    return c;
-}
-
-struct GaussGeo {
-    float mx, my, mz;
-    float M[9];   // R(q) diag(exp(log_scale)), row-major
-    float smax2;  // largest scale squared (largest eigenvalue of Sigma)
-};
-
-struct Proj {
-    float u, v, z, A, B, C, r;
-    float sa, sc;  // 2D covariance diagonal (with the dilation)
-    int x0, x1, y0, y1;
-};
-
-// Hardware approximations (PTX rcp/sqrt .approx): a few ulp, far inside the
-// parity tolerances. Both projection passes run these same instructions.
-__device__ __forceinline__ float rcp_a(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float sqrt_a(float x) {
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rsqrt_a(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float lg2_a(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float ldv(const void *p, long long i, int dt) {
-    if (dt == DT_F32) return __ldg(reinterpret_cast<const float *>(p) + i);
-    if (dt == DT_F16) return __half2float(reinterpret_cast<const __half *>(p)[i]);
-    return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i]);
-}
 
 __device__ void cam_setup(CamProj &c, const float *vm, const float *in, int W, int H,
                           float guard) {
@@ -124,154 +62,6 @@ __device__ void cam_setup(CamProj &c, const float *vm, const float *in, int W, i
     c.H = (float)H;
     c.TX = (W + TILE - 1) / TILE;
     c.TY = (H + TILE - 1) / TILE;
-}
-
-template <typename T>
-__device__ __forceinline__ float ldt(const void *p, long long i) {
-    if constexpr (sizeof(T) == 4)
-        return __ldg(reinterpret_cast<const float *>(p) + i);
-    else if constexpr (std::is_same<T, __half>::value)
-        return __half2float(__ldg(reinterpret_cast<const __half *>(p) + i));
-    else
-        return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16 *>(p) + i));
-}
-
-// Mean and M = R(q) S of Gaussian g (quaternion normalised here), attributes of type T.
-template <typename T>
-__device__ __forceinline__ void load_geo_t(const SceneDev &s, long long g, GaussGeo &G) {
-    const long long n = s.n;
-    G.mx = ldt<T>(s.mean, g);
-    G.my = ldt<T>(s.mean, n + g);
-    G.mz = ldt<T>(s.mean, 2 * n + g);
-    const float sx = expf(ldt<T>(s.log_scale, g));
-    const float sy = expf(ldt<T>(s.log_scale, n + g));
-    const float sz = expf(ldt<T>(s.log_scale, 2 * n + g));
-    const float sm = fmaxf(sx, fmaxf(sy, sz));
-    G.smax2 = sm * sm;
-    float w = ldt<T>(s.quat, g), x = ldt<T>(s.quat, n + g);
-    float y = ldt<T>(s.quat, 2 * n + g), z = ldt<T>(s.quat, 3 * n + g);
-    const float qq = w * w + x * x + y * y + z * z;
-    if (qq > 0.0f) {
-        const float inv = 1.0f / sqrtf(qq);
-        w *= inv;
-        x *= inv;
-        y *= inv;
-        z *= inv;
-    } else {
-        w = 1.0f;
-        x = y = z = 0.0f;
-    }
-    G.M[0] = (1.0f - 2.0f * (y * y + z * z)) * sx;
-    G.M[1] = 2.0f * (x * y - w * z) * sy;
-    G.M[2] = 2.0f * (x * z + w * y) * sz;
-    G.M[3] = 2.0f * (x * y + w * z) * sx;
-    G.M[4] = (1.0f - 2.0f * (x * x + z * z)) * sy;
-    G.M[5] = 2.0f * (y * z - w * x) * sz;
-    G.M[6] = 2.0f * (x * z - w * y) * sx;
-    G.M[7] = 2.0f * (y * z + w * x) * sy;
-    G.M[8] = (1.0f - 2.0f * (x * x + y * y)) * sz;
-}
-
-// The storage type is uniform per scene: one branch, then loads of a fixed type.
-__device__ __forceinline__ void load_geo(const SceneDev &s, long long g, GaussGeo &G) {
-    if (s.geo_dtype == DT_F32)
-        load_geo_t<float>(s, g, G);
-    else if (s.geo_dtype == DT_F16)
-        load_geo_t<__half>(s, g, G);
-    else
-        load_geo_t<__nv_bfloat16>(s, g, G);
-}
-
-// The cheap first part of project(): near plane and the cull with a bound of
-// the radius. lambda_max(Sigma') <= |J|_F^2 s_max^2 + dil and |J|_F^2 <= kk / z^2
-// over the guard band; the 1.002 and +0.02 px margins keep rb above the float32
-// radius, so this culls only what the exact test culls. project() calls it, so
-// a pair it rejects is exactly a pair project() rejects here.
-__device__ __forceinline__ bool prefilter(const CamProj &c, const GaussGeo &G, const ProjParams &P,
-                                          float &z, float &iz, float &xz, float &yz, float &u,
-                                          float &v) {
-    const float px = fmaf(c.R[0], G.mx, fmaf(c.R[1], G.my, fmaf(c.R[2], G.mz, c.t[0])));
-    const float py = fmaf(c.R[3], G.mx, fmaf(c.R[4], G.my, fmaf(c.R[5], G.mz, c.t[1])));
-    z = fmaf(c.R[6], G.mx, fmaf(c.R[7], G.my, fmaf(c.R[8], G.mz, c.t[2])));
-    if (!(z > P.near_plane)) return false;
-    iz = rcp_a(z);
-    xz = __fmul_rn(px, iz);
-    yz = __fmul_rn(py, iz);
-    u = fmaf(c.fx, xz, c.cx);
-    v = fmaf(c.fy, yz, c.cy);
-    const float rb = fmaf(1.002f * P.sigma, sqrt_a(fmaf(c.kk * iz * iz, G.smax2, P.dilation)), 0.02f);
-    return !(u + rb < 0.0f || u - rb >= c.W || v + rb < 0.0f || v - rb >= c.H);
-}
-
-// CULL = false: the values of a pair known to survive (the write pass), without
-// the radius bound and the cull tests; every value is computed by the same
-// operations as with CULL = true, so it is the same bit for bit.
-template <bool CULL = true>
-__device__ __forceinline__ bool project(const CamProj &c, const GaussGeo &G,
-                                        const ProjParams &P, Proj &o) {
-    float z, iz, xz, yz, u, v;
-    if (CULL) {
-        const bool pre = prefilter(c, G, P, z, iz, xz, yz, u, v);
-        o.z = z;
-        if (!pre) return false;
-    } else {
-        const float px = fmaf(c.R[0], G.mx, fmaf(c.R[1], G.my, fmaf(c.R[2], G.mz, c.t[0])));
-        const float py = fmaf(c.R[3], G.mx, fmaf(c.R[4], G.my, fmaf(c.R[5], G.mz, c.t[1])));
-        z = fmaf(c.R[6], G.mx, fmaf(c.R[7], G.my, fmaf(c.R[8], G.mz, c.t[2])));
-        iz = rcp_a(z);
-        xz = __fmul_rn(px, iz);
-        yz = __fmul_rn(py, iz);
-        u = fmaf(c.fx, xz, c.cx);
-        v = fmaf(c.fy, yz, c.cy);
-        o.z = z;
-    }
-    const float xc = fminf(fmaxf(xz, -c.lxn), c.lxp);
-    const float yc = fminf(fmaxf(yz, -c.lyn), c.lyp);
-    const float j00 = __fmul_rn(c.fx, iz), j02 = -__fmul_rn(__fmul_rn(c.fx, xc), iz);
-    const float j11 = __fmul_rn(c.fy, iz), j12 = -__fmul_rn(__fmul_rn(c.fy, yc), iz);
-    float T0[3], T1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        T0[k] = fmaf(j00, c.R[k], __fmul_rn(j02, c.R[6 + k]));
-        T1[k] = fmaf(j11, c.R[3 + k], __fmul_rn(j12, c.R[6 + k]));
-    }
-    float g0[3], g1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        g0[k] = fmaf(T0[0], G.M[k], fmaf(T0[1], G.M[3 + k], __fmul_rn(T0[2], G.M[6 + k])));
-        g1[k] = fmaf(T1[0], G.M[k], fmaf(T1[1], G.M[3 + k], __fmul_rn(T1[2], G.M[6 + k])));
-    }
-    const float s00 = fmaf(g0[0], g0[0], fmaf(g0[1], g0[1], __fmul_rn(g0[2], g0[2])));
-    const float s11 = fmaf(g1[0], g1[0], fmaf(g1[1], g1[1], __fmul_rn(g1[2], g1[2])));
-    const float s01 = fmaf(g0[0], g1[0], fmaf(g0[1], g1[1], __fmul_rn(g0[2], g1[2])));
-    const float dil = P.dilation;
-    const float a = __fadd_rn(s00, dil), cc = __fadd_rn(s11, dil), b = s01;
-    const float hd = __fmul_rn(0.5f, __fsub_rn(a, cc));
-    const float lmax = fmaf(0.5f, __fadd_rn(a, cc), sqrt_a(fmaf(hd, hd, __fmul_rn(b, b))));
-    const float r = __fmul_rn(P.sigma, sqrt_a(lmax));
-    if (CULL && (!(__fadd_rn(u, r) >= 0.0f) || !(__fsub_rn(u, r) < c.W) ||
-                 !(__fadd_rn(v, r) >= 0.0f) || !(__fsub_rn(v, r) < c.H)))
-        return false;
-    o.x0 = (int)fmaxf(floorf(__fmul_rn(__fsub_rn(u, r), 0.0625f)), 0.0f);
-    o.x1 = (int)fminf(floorf(__fmul_rn(__fadd_rn(u, r), 0.0625f)), (float)(c.TX - 1));
-    o.y0 = (int)fmaxf(floorf(__fmul_rn(__fsub_rn(v, r), 0.0625f)), 0.0f);
-    o.y1 = (int)fminf(floorf(__fmul_rn(__fadd_rn(v, r), 0.0625f)), (float)(c.TY - 1));
-    // conic: only the write pass uses it
-    const float e0 = fmaf(g0[1], g1[2], -__fmul_rn(g0[2], g1[1]));
-    const float e1 = fmaf(g0[2], g1[0], -__fmul_rn(g0[0], g1[2]));
-    const float e2 = fmaf(g0[0], g1[1], -__fmul_rn(g0[1], g1[0]));
-    const float det = fmaf(dil, __fadd_rn(__fadd_rn(s00, s11), dil),
-                           fmaf(e0, e0, fmaf(e1, e1, __fmul_rn(e2, e2))));
-    const float idet = rcp_a(det);
-    o.A = cc * idet;
-    o.B = -b * idet;
-    o.C = a * idet;
-    o.sa = a;
-    o.sc = cc;
-    o.u = u;
-    o.v = v;
-    o.r = r;
-    return true;
 }
 
 // The prefilter constants of two cameras (c, c + 1), field by field as float2
@@ -333,36 +123,6 @@ __device__ __forceinline__ void prefilter2(const CamPair &c, const GaussGeo &G,
     const float2 va = __fadd2_rn(v, rb), vs = __ffma2_rn(rb, M1, v);
     in0 = z.x > P.near_plane && !(ua.x < 0.0f || us.x >= c.W.x || va.x < 0.0f || vs.x >= c.H.x);
     in1 = z.y > P.near_plane && !(ua.y < 0.0f || us.y >= c.W.y || va.y < 0.0f || vs.y >= c.H.y);
-}
-
-// Real SH basis (Condon-Shortley phase), l-major with m = -l..l, constants
-// written as their closed forms sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the
-// factors of the Cartesian polynomials.
-__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float *Y) {
-    Y[0] = 0.28209479177387814f;  // 1/(2 sqrt(pi))
-    if (deg >= 1) {
-        const float c1 = 0.4886025119029199f;  // sqrt(3/(4 pi))
-        Y[1] = -c1 * y;
-        Y[2] = c1 * z;
-        Y[3] = -c1 * x;
-    }
-    if (deg >= 2) {
-        const float xx = x * x, yy = y * y, zz = z * z;
-        Y[4] = 1.0925484305920792f * x * y;           // sqrt(15/(4 pi))
-        Y[5] = -1.0925484305920792f * y * z;
-        Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);  // sqrt(5/(16 pi))
-        Y[7] = -1.0925484305920792f * x * z;
-        Y[8] = 0.5462742152960396f * (xx - yy);       // sqrt(15/(16 pi))
-        if (deg >= 3) {
-            Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);   // sqrt(35/(32 pi))
-            Y[10] = 2.890611442640554f * x * y * z;              // sqrt(105/(4 pi))
-            Y[11] = -0.4570457994644658f * y * (5.0f * zz - 1.0f);  // sqrt(21/(32 pi))
-            Y[12] = 0.3731763325901154f * z * (5.0f * zz - 3.0f);   // sqrt(7/(16 pi))
-            Y[13] = -0.4570457994644658f * x * (5.0f * zz - 1.0f);
-            Y[14] = 1.445305721320277f * z * (xx - yy);          // sqrt(105/(16 pi))
-            Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
-        }
-    }
 }
 
 // A group of Gaussians (a warp's 32) against one camera, before the Gaussians
@@ -604,7 +364,6 @@ __global__ void __launch_bounds__(1024)
     if (tid == 0) counts[blockIdx.x] = (int)carry;
 }
 
-constexpr float LOG2E = 1.4426950408889634f;
 
 // SH coefficients per channel in groups of four consecutive k (zero past the
 // scene's degree): a Gaussian's column holds 3 * SH_QUADS(DEG) float4.
@@ -620,18 +379,8 @@ template <int DEG>
 __device__ __forceinline__ void sh_colour_smem(const float4 *sh4, const CamProj &c,
                                                const GaussGeo &G, float rgb[3]) {
     constexpr int Q = sh_quads(DEG);
-    float dx = G.mx - c.cpos[0], dy = G.my - c.cpos[1], dz = G.mz - c.cpos[2];
-    const float dd = dx * dx + dy * dy + dz * dz;
-    if (dd > 0.0f) {
-        const float inv = rsqrt_a(dd);
-        dx *= inv;
-        dy *= inv;
-        dz *= inv;
-    } else {
-        dx = 0.0f;
-        dy = 0.0f;
-        dz = 1.0f;
-    }
+    float dx, dy, dz;
+    sh_dir(c.cpos, G.mx, G.my, G.mz, dx, dy, dz);
     float Y[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) Y[k] = 0.0f;
@@ -645,7 +394,7 @@ __device__ __forceinline__ void sh_colour_smem(const float4 *sh4, const CamProj 
             acc = __ffma2_rn(make_float2(w.x, w.y), make_float2(Y[4 * j], Y[4 * j + 1]), acc);
             acc = __ffma2_rn(make_float2(w.z, w.w), make_float2(Y[4 * j + 2], Y[4 * j + 3]), acc);
         }
-        rgb[ch] = fmaxf(acc.x + acc.y, 0.0f);
+        rgb[ch] = fmaxf(__fadd_rn(acc.x, acc.y), 0.0f);
     }
 }
 
@@ -721,7 +470,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
     uint32_t gidx = 0u;
     if (valid) {
         load_geo(sc, g, G);
-        log2o = lg2_a(1.0f / (1.0f + expf(-ldv(sc.logit, g, sc.app_dtype))));
+        log2o = log2_opacity(ldv(sc.logit, g, sc.app_dtype));
         float sh[NC];
         if (sc.app_dtype == DT_F32)
             load_sh<float, NC>(sc, g, sh);
@@ -774,14 +523,15 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
         sh_colour_smem<DEG>(shc, cam, G, rgb);
         float hx = -1e30f, hy = -1e30f;
         if (q >= 0.0f) {
-            hx = fmaf(1.002f, sqrt_a(q * pr.sa), 0.02f);
-            hy = fmaf(1.002f, sqrt_a(q * pr.sc), 0.02f);
+            hx = fmaf(1.002f, sqrt_a(__fmul_rn(q, pr.sa)), 0.02f);
+            hy = fmaf(1.002f, sqrt_a(__fmul_rn(q, pr.sc)), 0.02f);
         }
         const long long at = soff[c] + swoff[c][warp] + __popc(word & lt);
         const uint2 rect = make_uint2((uint32_t)pr.x0 | ((uint32_t)pr.x1 << 16),
                                       (uint32_t)pr.y0 | ((uint32_t)pr.y1 << 16));
         rec[rec_a(at)] = make_float4(pr.u, pr.v, hx, hy);
-        rec[rec_b(at)] = make_float4(-0.5f * LOG2E * pr.A, -LOG2E * pr.B, -0.5f * LOG2E * pr.C, log2o);
+        rec[rec_b(at)] = make_float4(__fmul_rn(-0.5f * LOG2E, pr.A), __fmul_rn(-LOG2E, pr.B),
+                     __fmul_rn(-0.5f * LOG2E, pr.C), log2o);
         rec[rec_c(at)] = make_float4(rgb[0], rgb[1], rgb[2], pr.z);
         if (with_d)
             reinterpret_cast<uint4 *>(rec)[rec_d(at)] =
@@ -793,6 +543,78 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
         const uint32_t kz = __float_as_uint(pr.z) - __float_as_uint(P.near_plane);
         keys[at] = kz;
         oidx[at] = gidx;
+    }
+}
+
+// Key pass of the progressive order: the write pass's walk over the group's
+// cameras whose mask word of this warp is not zero, but a lane with its bit set
+// writes only the depth key (z as the projection computes it, bits minus the
+// near plane's), its Gaussian's position in the scene and its caller index at
+// the pair's stable slot: 12 bytes per survivor instead of the record's 64, and
+// no projection or SH work (the records of the ranks the render reads come
+// from the binning pass).
+__global__ void __launch_bounds__(PROJ_THREADS)
+    k_project_keys(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
+                   const CamInfo *__restrict__ cams, const CamProj *__restrict__ camtab,
+                   ProjParams P, const uint32_t *__restrict__ masks,
+                   const uint32_t *__restrict__ woff, uint32_t *__restrict__ keys,
+                   uint32_t *__restrict__ gslot, uint32_t *__restrict__ oidx,
+                   const int *__restrict__ status) {
+    const Group gr = groups[blockIdx.y];
+    const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
+    if (g0 >= gr.n) return;
+    if (status && *status) return;  // the chunk was planned empty: workspace too small
+    constexpr int NW = PROJ_THREADS / 32;
+    __shared__ float4 zrow[MAX_GROUP];  // R[6], R[7], R[8], t[2]: z of a point
+    __shared__ long long soff[MAX_GROUP];
+    __shared__ uint32_t sword[MAX_GROUP][NW], swoff[MAX_GROUP][NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SceneDev sc = scenes[gr.scene];
+    for (int e = tid; e < gr.ncam * NW; e += PROJ_THREADS) {
+        const int c = e / NW, w = e % NW;
+        const long long wi = (g0 >> 5) + w;
+        uint32_t m = 0u, o = 0u;
+        if ((wi << 5) < gr.n) {
+            const long long at = cams[gr.slot0 + c].mask_off + wi;
+            m = masks[at];
+            o = woff[at];
+        }
+        sword[c][w] = m;
+        swoff[c][w] = o;
+    }
+    if (tid < gr.ncam) {
+        const CamProj &cp = camtab[gr.slot0 + tid];
+        zrow[tid] = make_float4(cp.R[6], cp.R[7], cp.R[8], cp.t[2]);
+        soff[tid] = cams[gr.slot0 + tid].seg_off;
+    }
+    const long long g = g0 + tid;
+    const bool valid = g < gr.n;
+    float mx = 0.0f, my = 0.0f, mz = 0.0f;
+    uint32_t gidx = 0u;
+    if (valid) {
+        mx = ldv(sc.mean, g, sc.geo_dtype);
+        my = ldv(sc.mean, sc.n + g, sc.geo_dtype);
+        mz = ldv(sc.mean, 2 * sc.n + g, sc.geo_dtype);
+        gidx = (uint32_t)sc.orig[g];
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t near_bits = __float_as_uint(P.near_plane);
+#pragma unroll
+    for (int k = 0; k < MAX_GROUP / 32; ++k) {
+        const int cl = lane + 32 * k;
+        uint32_t lc = __ballot_sync(0xffffffffu, cl < gr.ncam && sword[cl][warp] != 0u);
+        for (; lc; lc &= lc - 1u) {  // warp-uniform
+            const int c = 32 * k + __ffs(lc) - 1;
+            const uint32_t word = sword[c][warp];
+            if (!((word >> lane) & 1u)) continue;
+            const float4 zr = zrow[c];
+            const float z = fmaf(zr.x, mx, fmaf(zr.y, my, fmaf(zr.z, mz, zr.w)));
+            const long long at = soff[c] + swoff[c][warp] + __popc(word & lt);
+            keys[at] = __float_as_uint(z) - near_bits;
+            gslot[at] = (uint32_t)g;
+            oidx[at] = gidx;
+        }
     }
 }
 
@@ -860,6 +682,18 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
         default: GS_WRITE(3); break;
     }
 #undef GS_WRITE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_keys(const Group *groups, int n_groups, int max_blocks_x,
+                                const SceneDev *scenes, const CamInfo *cams, const void *camtab,
+                                ProjParams P, const uint32_t *masks, const uint32_t *woff,
+                                uint32_t *keys, uint32_t *gslot, uint32_t *oidx, const int *status,
+                                cudaStream_t s) {
+    if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
+    dim3 grid(max_blocks_x, n_groups);  // PROJ_THREADS Gaussians per block, as the mask pass
+    k_project_keys<<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, (const CamProj *)camtab, P,
+                                                 masks, woff, keys, gslot, oidx, status);
     return cudaGetLastError();
 }
 

@@ -10,10 +10,17 @@
 // 30-bit codes, then a gather of every attribute row. orig[p] keeps the
 // caller's index of the Gaussian stored at position p; the renderer orders
 // equal depths by it and the inspection entry points report it.
+//
+// Rows per Gaussian (k_scene_rows): the progressive depth order computes the
+// records of the ranks it renders after the depth order, at scattered
+// positions, so each Gaussian also gets its geometry as the projection passes
+// derive it (mean, log2 opacity, M = R(q) S: 64 bytes) and its SH coefficients
+// channel-major in one row (load_geo and the opacity expression of
+// proj_core.cuh, so the records are those the projection's write pass makes).
 #include <algorithm>
 #include <type_traits>
 
-#include "gs_internal.cuh"
+#include "proj_core.cuh"
 
 namespace gsk {
 
@@ -162,7 +169,38 @@ void by_dtype(int dt, F &&f) {
         f(__nv_bfloat16{});
 }
 
+// One thread per Gaussian: its geometry row (4 float4) and SH row (48
+// elements of the appearance type, raw bits; zero past the degree).
+template <typename A>
+__global__ void k_scene_rows(const SceneDev s, float4 *__restrict__ geo, A *__restrict__ shr) {
+    const int K = (s.deg + 1) * (s.deg + 1);
+    const A *sh = reinterpret_cast<const A *>(s.sh);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < s.n;
+         g += (long long)gridDim.x * blockDim.x) {
+        GaussGeo G;
+        load_geo(s, g, G);
+        const float log2o = log2_opacity(ldv(s.logit, g, s.app_dtype));
+        geo[4 * g + 0] = make_float4(G.mx, G.my, G.mz, log2o);
+        geo[4 * g + 1] = make_float4(G.M[0], G.M[1], G.M[2], G.M[3]);
+        geo[4 * g + 2] = make_float4(G.M[4], G.M[5], G.M[6], G.M[7]);
+        geo[4 * g + 3] = make_float4(G.M[8], 0.0f, 0.0f, 0.0f);
+        for (int ch = 0; ch < 3; ++ch)
+            for (int k = 0; k < 16; ++k)
+                shr[48 * g + 16 * ch + k] = k < K ? sh[(long long)(3 * k + ch) * s.n + g] : A(0);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_scene_rows(const SceneDev &s, float4 *geo_rows, void *sh_rows, cudaStream_t st) {
+    if (s.n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((s.n + 255) / 256, 148 * 16);
+    if (s.app_dtype == DT_F32)
+        k_scene_rows<uint32_t><<<grid, 256, 0, st>>>(s, geo_rows, (uint32_t *)sh_rows);
+    else
+        k_scene_rows<uint16_t><<<grid, 256, 0, st>>>(s, geo_rows, (uint16_t *)sh_rows);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_scene_morton(const void *mean, int dtype, long long n, unsigned *box,
                                 uint32_t *code, uint32_t *idx, cudaStream_t s) {

@@ -112,3 +112,29 @@ def test_full_size_chunk_equals_whole_order(torch, gsmod):
         assert whole[3]["survivors"] == sd["survivors"] == sf["survivors"]
     finally:
         R.close()
+
+
+def test_batched_scenes_equal_whole_order(torch, gsmod):
+    """Five scenes of SH degree 2 with cameras at two resolutions in chunks of
+    16: the records computed by the binning pass from each scene's rows (the
+    progressive order, cut after the first window or by default) are those of
+    the projection's write pass (the whole order), so the images are the same
+    bit for bit."""
+    scenes, which, vm, it, Ws, Hs = synth.make_batched(
+        n_scenes=5, n_cams=40, seed=7, n_range=(5_000, 40_000), sh_degree=2,
+        sizes=((128, 96, 100.0), (64, 48, 50.0)))
+    vm_d, it_d = torch.from_numpy(vm).cuda(), torch.from_numpy(it).cuda()
+    outs = {}
+    for prefix in (-1, 0, 1):
+        R = gsmod.Renderer(device=0, max_chunk_cameras=16, camera_group=8, depth_prefix=prefix)
+        try:
+            ids = np.array([R.add_scene(s) for s in scenes], dtype=np.int32)[which]
+            rgb, depth, T, _ = R.render_v(ids, vm_d, it_d, Ws, Hs, want_T=True)
+            R.sync()
+            outs[prefix] = ([x.cpu().numpy() for x in (rgb, depth, T)], R.stats())
+        finally:
+            R.close()
+    assert outs[1][1]["depth_second_phase_cameras"] > 0
+    for p in (0, 1):
+        for a, b in zip(outs[-1][0], outs[p][0]):
+            assert np.array_equal(a, b), p
