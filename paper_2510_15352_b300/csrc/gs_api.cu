@@ -88,7 +88,6 @@ struct gs_context {
     // the progressive depth order: per camera its cut, the two phase maps, the
     // second phase's counts and camera flags, saved tile states, tiles to render again
     DevBuf dcut, pmap, prog, rsaved, rstate, ragain;
-    DevBuf gslot;  // per survivor slot: its Gaussian's position in the scene (progressive order)
     long long cap_survivors = 0;  // survivors per chunk the workspace holds
     long long last_chunk_survivors = 0;  // largest chunk of the last render
     int workspace_gen = 0;        // bumped when a chunk-workspace buffer is reallocated
@@ -340,7 +339,7 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
                       &ctx->segstart, &ctx->segcount, &ctx->stats,     &ctx->status,
                       &ctx->oidx,     &ctx->ties,     &ctx->nruns,    &ctx->pq,
                       &ctx->dcut,     &ctx->pmap,     &ctx->prog,     &ctx->rsaved,
-                      &ctx->rstate,   &ctx->ragain,   &ctx->gslot};
+                      &ctx->rstate,   &ctx->ragain};
     // (compared by capacity: a reallocation may return the freed address)
     size_t before[sizeof(held) / sizeof(held[0])];
     for (size_t i = 0; i < sizeof(held) / sizeof(held[0]); ++i) before[i] = held[i]->cap;
@@ -358,7 +357,6 @@ gs_status size_workspace(gs_context *ctx, const Plan &P) {
     CKS(grow(ctx, ctx->tkeys, (Sx + 4) * 4));
     CKS(grow(ctx, ctx->tvals, (Sx + 4) * 4));
     CKS(grow(ctx, ctx->oidx, Sx * 4));
-    CKS(grow(ctx, ctx->gslot, Sx * 4));
     CKS(grow(ctx, ctx->ties, (Sx / 33 + 2) * tie_run_bytes()));
     CKS(grow(ctx, ctx->nruns, 6 * (P.chunks.size() + 1) * sizeof(int)));
     CKS(grow(ctx, ctx->pq, (size_t)(m + 2) * sizeof(int)));
@@ -468,8 +466,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
             CKC(launch_project_keys(groups, ch.n_groups, ch.max_bx,
                                     (const SceneDev *)ctx->d_scenes.p, cams, ctx->camtab.p, PP,
                                     (const uint32_t *)ctx->masks.p, (const uint32_t *)ctx->woff.p,
-                                    (uint32_t *)ctx->keys.p, (uint32_t *)ctx->gslot.p,
-                                    (uint32_t *)ctx->oidx.p, status, st));
+                                    (uint32_t *)ctx->keys.p, (uint32_t *)ctx->oidx.p, status, st));
         else
             CKC(launch_project_write(groups, ch.n_groups, ch.max_bx,
                                      (const SceneDev *)ctx->d_scenes.p, cams, ctx->camtab.p, PP,
@@ -495,7 +492,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
         if (prog)
             CKC(launch_bin_rec(cams, (const int2 *)ctx->bintab.p, ch.m, ch.bin_grid, ch.max_sup,
                                ch.bin_ranks, (const SceneDev *)ctx->d_scenes.p, ctx->camtab.p, PP,
-                               ln_amin, (const uint32_t *)ctx->gslot.p,
+                               ln_amin, (const uint32_t *)ctx->oidx.p,
                                (const uint32_t *)ctx->tvals.p, recs, (uint2 *)ctx->rrect.p,
                                (uint32_t *)ctx->bitmap.p, stats + 2, cut, 1, map1, st));
         else if (!persist)
@@ -549,7 +546,7 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
             if (E) CKC(cudaEventRecord(E[5], st));
             CKC(launch_bin_rec(cams, (const int2 *)ctx->bintab.p, ch.m, ch.bin_grid, ch.max_sup,
                                ch.bin_ranks, (const SceneDev *)ctx->d_scenes.p, ctx->camtab.p, PP,
-                               ln_amin, (const uint32_t *)ctx->gslot.p,
+                               ln_amin, (const uint32_t *)ctx->oidx.p,
                                (const uint32_t *)ctx->tvals.p, recs, (uint2 *)ctx->rrect.p,
                                (uint32_t *)ctx->bitmap.p, stats + 2, cut, 2, map2, st));
             if (E) CKC(cudaEventRecord(E[6], st));
@@ -863,7 +860,7 @@ void gs_context_destroy(gs_context *ctx) {
                       &ctx->ties,
                       &ctx->nruns,    &ctx->pq,
                       &ctx->dcut,     &ctx->pmap,   &ctx->prog,   &ctx->rsaved,  &ctx->rstate,
-                      &ctx->ragain,   &ctx->gslot,
+                      &ctx->ragain,
                       &ctx->h_rgb,    &ctx->h_depth, &ctx->h_T};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -925,6 +922,8 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
     total += align_up((size_t)n * 4 * sizeof(float4), 256);
     const size_t off_sh_rows = total;
     total += align_up((size_t)n * 48 * as, 256);
+    const size_t off_pos_of = total;
+    total += align_up((size_t)n * 4, 256);
     SceneSlot slot;
     slot.live = true;
     if (n > 0) {
@@ -987,7 +986,9 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
             sd.deg = d->sh_degree;
             sd.geo_dtype = d->geometry_dtype;
             sd.app_dtype = d->appearance_dtype;
-            e = launch_scene_rows(sd, (float4 *)(st + off_geo_rows), st + off_sh_rows, nullptr);
+            sd.orig = (const int *)(st + off_orig);
+            e = launch_scene_rows(sd, (float4 *)(st + off_geo_rows), st + off_sh_rows,
+                                  (int *)(st + off_pos_of), nullptr);
         }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(tmp);
@@ -1006,6 +1007,7 @@ gs_status gs_scene_create(gs_context *ctx, const gs_scene_desc *d, int32_t *scen
     slot.dev.bounds = (const float4 *)(b + off_bounds);
     slot.dev.geo_rows = (const float4 *)(b + off_geo_rows);
     slot.dev.sh_rows = b + off_sh_rows;
+    slot.dev.pos_of = (const int *)(b + off_pos_of);
     slot.dev.n = n;
     slot.dev.deg = d->sh_degree;
     slot.dev.geo_dtype = d->geometry_dtype;

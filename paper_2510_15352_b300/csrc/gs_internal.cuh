@@ -57,6 +57,7 @@ struct SceneDev {
     // zero past the degree)
     const float4 *geo_rows;
     const void *sh_rows;
+    const int *pos_of;  // pos_of[i]: the stored position of the caller's Gaussian i
     long long n;
     int deg, geo_dtype, app_dtype, pad;
 };
@@ -139,14 +140,12 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
                                  float ln_alpha_min, const int *status, int max_deg,
                                  cudaStream_t s);
 // The progressive order's projection output (instead of launch_project_write):
-// per survivor slot only the depth key, the Gaussian's position in its scene
-// (gslot) and its caller index; the records of the ranks the render reads are
-// computed later by launch_bin_rec.
+// per survivor slot only the depth key and the Gaussian's caller index; the
+// records of the ranks the render reads are computed later by launch_bin_rec.
 cudaError_t launch_project_keys(const Group *groups, int n_groups, int max_blocks_x,
                                 const SceneDev *scenes, const CamInfo *cams, const void *camtab,
                                 ProjParams P, const uint32_t *masks, const uint32_t *woff,
-                                uint32_t *keys, uint32_t *gslot, uint32_t *oidx, const int *status,
-                                cudaStream_t s);
+                                uint32_t *keys, uint32_t *oidx, const int *status, cudaStream_t s);
 
 // Scene set-up (k_scene.cu): Morton codes of the means (box: 6 words of
 // scratch) with idx = 0..n-1, to be sorted as (code, idx); a gather of `rows`
@@ -155,8 +154,10 @@ cudaError_t launch_scene_morton(const void *mean, int dtype, long long n, unsign
                                 uint32_t *code, uint32_t *idx, cudaStream_t s);
 cudaError_t launch_gather_rows(const void *src, void *dst, int elem_bytes, const uint32_t *perm,
                                long long n, int rows, cudaStream_t s);
-// A stored scene's geo_rows / sh_rows (see SceneDev) from its attribute arrays.
-cudaError_t launch_scene_rows(const SceneDev &s, float4 *geo_rows, void *sh_rows, cudaStream_t st);
+// A stored scene's geo_rows / sh_rows (see SceneDev) from its attribute arrays,
+// and pos_of, the inverse of orig.
+cudaError_t launch_scene_rows(const SceneDev &s, float4 *geo_rows, void *sh_rows, int *pos_of,
+                              cudaStream_t st);
 long long scene_blocks(long long n);
 cudaError_t launch_block_bounds(const void *mean, const void *log_scale, int dtype, long long n,
                                 float4 *bounds, cudaStream_t s);
@@ -318,11 +319,11 @@ cudaError_t launch_bin(const CamInfo *cams, const int *blk_prefix, const int2 *b
                        const DepthCut *cut, int phase, const int *map, cudaStream_t s);
 // The binning blocks of a phase map (phase 1 / 2, as launch_bin) that also
 // compute each binned rank's record (the projection passes' arithmetic, from
-// the scene rows of its Gaussian gslot[seg_off + slot]) into rec at the rank's
-// position, and its rect.
+// the scene rows of its Gaussian pos_of[oidx[seg_off + slot]]) into rec at the
+// rank's position, and its rect.
 cudaError_t launch_bin_rec(const CamInfo *cams, const int2 *bintab, int n_slots, int n_blocks,
                            int n_super, int bin_ranks, const SceneDev *scenes, const void *camtab,
-                           ProjParams P, float ln_alpha_min, const uint32_t *gslot,
+                           ProjParams P, float ln_alpha_min, const uint32_t *oidx,
                            const uint32_t *vals, float4 *rec, uint2 *rrect, uint32_t *bitmap,
                            unsigned long long *n_isect, const DepthCut *cut, int phase,
                            const int *map, cudaStream_t s);

@@ -128,7 +128,7 @@ template <int RPT>
 __global__ void __launch_bounds__(BIN_THREADS)
     k_bin_rec(const CamInfo *__restrict__ cams, const int2 *__restrict__ bintab, int n_slots,
               const SceneDev *__restrict__ scenes, const CamProj *__restrict__ camtab, ProjParams P,
-              float ln_alpha_min, const uint32_t *__restrict__ gslot,
+              float ln_alpha_min, const uint32_t *__restrict__ oidx,
               const uint32_t *__restrict__ vals, float4 *__restrict__ rec,
               uint2 *__restrict__ rrect, uint32_t *__restrict__ bitmap,
               unsigned long long *__restrict__ n_isect, const DepthCut *__restrict__ cut,
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(BIN_THREADS)
         for (int j = 0; j < RPT; ++j) {
             const int r = r0 + j * NTH + tid;
             if (r >= lim) continue;
-            const long long g = gslot[ci.seg_off + slot[j]];
+            const long long g = sc.pos_of[oidx[ci.seg_off + slot[j]]];
             const long long at = ci.seg_off + r;
             const uint2 d =
                 sc.app_dtype == DT_F32 ? rank_record<float>(scam, sc, g, P, ln_alpha_min, rec, at)
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(BIN_THREADS)
 
 cudaError_t launch_bin_rec(const CamInfo *cams, const int2 *bintab, int n_slots, int n_blocks,
                            int n_super, int bin_ranks, const SceneDev *scenes, const void *camtab,
-                           ProjParams P, float ln_alpha_min, const uint32_t *gslot,
+                           ProjParams P, float ln_alpha_min, const uint32_t *oidx,
                            const uint32_t *vals, float4 *rec, uint2 *rrect, uint32_t *bitmap,
                            unsigned long long *n_isect, const DepthCut *cut, int phase,
                            const int *map, cudaStream_t s) {
@@ -214,7 +214,7 @@ cudaError_t launch_bin_rec(const CamInfo *cams, const int2 *bintab, int n_slots,
             if (e != cudaSuccess) return e;                                                      \
         }                                                                                        \
         kern<<<n_blocks, BIN_THREADS, smem, s>>>(cams, bintab, n_slots, scenes, ct, P,           \
-                                                 ln_alpha_min, gslot, vals, rec, rrect, bitmap,  \
+                                                 ln_alpha_min, oidx, vals, rec, rrect, bitmap,   \
                                                  n_isect, cut, phase, map);                      \
     } while (0)
     if (bin_ranks == BIN_RANKS)

@@ -224,14 +224,15 @@ __global__ void __launch_bounds__(1024)
 
 // One sort tile per block pass: the tile grouped by bucket in shared memory
 // (ranks from shared-memory atomics), the tile's share of each bucket reserved
-// with one global atomic, then written out run by run (key and slot). Six
-// resident blocks per SM (40 registers): a block waits on its reservations'
-// round trip, and more blocks hide more of it (4.2 -> 4.0 ms per 4,096 cameras
-// against four). Phase 1: every sort tile, the keys of buckets before the
+// with one global atomic, then written out run by run (key and slot). Five
+// resident blocks per SM: a block waits on its reservations' round trip, and
+// more blocks hide more of it (six against four: 4.2 -> 4.0 ms per 4,096
+// cameras for the whole order; with the early end of tiles without keys of the
+// phase, six spilled). Phase 1: every sort tile, the keys of buckets before the
 // segment's cut; phase 2: the sort tiles of the phase map, the keys of the
 // cut's bucket and after.
 template <int phase>
-__global__ void __launch_bounds__(BT, 6)
+__global__ void __launch_bounds__(BT, 5)
     k_depth_scatter(const uint32_t *__restrict__ keys, uint32_t *__restrict__ dk,
                     uint32_t *__restrict__ dv, const SortTile *__restrict__ tiles,
                     const int *__restrict__ n_tiles_dev, uint32_t *__restrict__ cursor,
@@ -249,7 +250,6 @@ __global__ void __launch_bounds__(BT, 6)
         const SortTile T = tiles[tile];
         const uint32_t bcut = (uint32_t)cut[T.seg].bucket;
         const uint32_t blo = phase == 2 ? bcut : 0u, bhi = phase == 2 ? (uint32_t)NB : bcut;
-        for (int d = tid; d < NB; d += BT) h[d] = 0;
         uint32_t kv[BPT], rk[BPT];
         uint32_t in = 0;  // bit r: key r of this thread belongs to the phase
         {
@@ -265,6 +265,10 @@ __global__ void __launch_bounds__(BT, 6)
             const uint32_t b = bucket_of(kv[r]);
             in |= (r * BT + tid < T.nk && b >= blo && b < bhi) ? 1u << r : 0u;
         }
+        // a tile with no key of this phase (most tiles of the first phase: its
+        // keys are a camera's nearest) ends here
+        if (!__syncthreads_or(in != 0u)) continue;
+        for (int d = tid; d < NB; d += BT) h[d] = 0;
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < BPT; ++r)

@@ -549,17 +549,16 @@ __global__ void __launch_bounds__(PROJ_THREADS, 3)
 // Key pass of the progressive order: the write pass's walk over the group's
 // cameras whose mask word of this warp is not zero, but a lane with its bit set
 // writes only the depth key (z as the projection computes it, bits minus the
-// near plane's), its Gaussian's position in the scene and its caller index at
-// the pair's stable slot: 12 bytes per survivor instead of the record's 64, and
-// no projection or SH work (the records of the ranks the render reads come
-// from the binning pass).
+// near plane's) and its Gaussian's caller index at the pair's stable slot: 8
+// bytes per survivor instead of 64, and no projection or SH work (the records
+// of the ranks the render reads come from the binning pass, which finds the
+// Gaussian through the scene's inverse of orig).
 __global__ void __launch_bounds__(PROJ_THREADS)
     k_project_keys(const Group *__restrict__ groups, const SceneDev *__restrict__ scenes,
                    const CamInfo *__restrict__ cams, const CamProj *__restrict__ camtab,
                    ProjParams P, const uint32_t *__restrict__ masks,
                    const uint32_t *__restrict__ woff, uint32_t *__restrict__ keys,
-                   uint32_t *__restrict__ gslot, uint32_t *__restrict__ oidx,
-                   const int *__restrict__ status) {
+                   uint32_t *__restrict__ oidx, const int *__restrict__ status) {
     const Group gr = groups[blockIdx.y];
     const long long g0 = (long long)blockIdx.x * PROJ_THREADS;
     if (g0 >= gr.n) return;
@@ -612,7 +611,6 @@ __global__ void __launch_bounds__(PROJ_THREADS)
             const float z = fmaf(zr.x, mx, fmaf(zr.y, my, fmaf(zr.z, mz, zr.w)));
             const long long at = soff[c] + swoff[c][warp] + __popc(word & lt);
             keys[at] = __float_as_uint(z) - near_bits;
-            gslot[at] = (uint32_t)g;
             oidx[at] = gidx;
         }
     }
@@ -688,12 +686,11 @@ cudaError_t launch_project_write(const Group *groups, int n_groups, int max_bloc
 cudaError_t launch_project_keys(const Group *groups, int n_groups, int max_blocks_x,
                                 const SceneDev *scenes, const CamInfo *cams, const void *camtab,
                                 ProjParams P, const uint32_t *masks, const uint32_t *woff,
-                                uint32_t *keys, uint32_t *gslot, uint32_t *oidx, const int *status,
-                                cudaStream_t s) {
+                                uint32_t *keys, uint32_t *oidx, const int *status, cudaStream_t s) {
     if (n_groups == 0 || max_blocks_x == 0) return cudaSuccess;
     dim3 grid(max_blocks_x, n_groups);  // PROJ_THREADS Gaussians per block, as the mask pass
     k_project_keys<<<grid, PROJ_THREADS, 0, s>>>(groups, scenes, cams, (const CamProj *)camtab, P,
-                                                 masks, woff, keys, gslot, oidx, status);
+                                                 masks, woff, keys, oidx, status);
     return cudaGetLastError();
 }
 

@@ -172,7 +172,8 @@ void by_dtype(int dt, F &&f) {
 // One thread per Gaussian: its geometry row (4 float4) and SH row (48
 // elements of the appearance type, raw bits; zero past the degree).
 template <typename A>
-__global__ void k_scene_rows(const SceneDev s, float4 *__restrict__ geo, A *__restrict__ shr) {
+__global__ void k_scene_rows(const SceneDev s, float4 *__restrict__ geo, A *__restrict__ shr,
+                             int *__restrict__ pos_of) {
     const int K = (s.deg + 1) * (s.deg + 1);
     const A *sh = reinterpret_cast<const A *>(s.sh);
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < s.n;
@@ -180,6 +181,7 @@ __global__ void k_scene_rows(const SceneDev s, float4 *__restrict__ geo, A *__re
         GaussGeo G;
         load_geo(s, g, G);
         const float log2o = log2_opacity(ldv(s.logit, g, s.app_dtype));
+        pos_of[s.orig[g]] = (int)g;
         geo[4 * g + 0] = make_float4(G.mx, G.my, G.mz, log2o);
         geo[4 * g + 1] = make_float4(G.M[0], G.M[1], G.M[2], G.M[3]);
         geo[4 * g + 2] = make_float4(G.M[4], G.M[5], G.M[6], G.M[7]);
@@ -192,13 +194,14 @@ __global__ void k_scene_rows(const SceneDev s, float4 *__restrict__ geo, A *__re
 
 }  // namespace
 
-cudaError_t launch_scene_rows(const SceneDev &s, float4 *geo_rows, void *sh_rows, cudaStream_t st) {
+cudaError_t launch_scene_rows(const SceneDev &s, float4 *geo_rows, void *sh_rows, int *pos_of,
+                              cudaStream_t st) {
     if (s.n <= 0) return cudaSuccess;
     const int grid = (int)std::min<long long>((s.n + 255) / 256, 148 * 16);
     if (s.app_dtype == DT_F32)
-        k_scene_rows<uint32_t><<<grid, 256, 0, st>>>(s, geo_rows, (uint32_t *)sh_rows);
+        k_scene_rows<uint32_t><<<grid, 256, 0, st>>>(s, geo_rows, (uint32_t *)sh_rows, pos_of);
     else
-        k_scene_rows<uint16_t><<<grid, 256, 0, st>>>(s, geo_rows, (uint16_t *)sh_rows);
+        k_scene_rows<uint16_t><<<grid, 256, 0, st>>>(s, geo_rows, (uint16_t *)sh_rows, pos_of);
     return cudaGetLastError();
 }
 
