@@ -52,11 +52,20 @@ BATCHED = "batched_32scene_4096cam_mixed"
 # 11 per contributing pair (alpha >= alpha_min: 1 - alpha, T', alpha T, four FMAs),
 # and a lower bound, 22 flops per contributing pair only.
 F_PAIR = 20
-# kernels per render chunk: camera table, mask, mask scan, plan, plan tables,
-# write; depth order: count, scan, scatter, window, listed windows, long runs,
-# listed runs (the last three launch always and exit at once when nothing is
-# listed); bin, composite
-LAUNCHES_PER_CHUNK = 15
+def launches_per_chunk(args) -> int:
+    """Kernels the library launches per render chunk with these settings: the
+    camera table, mask, mask scan, plan, plan tables and the key (or write) pass;
+    the depth order's count, scan, phase map, scatter, window, listed windows,
+    long runs and listed runs (those three launch always and exit at once when
+    nothing is listed); binning and compositing (one persistent launch with
+    --persistent 1); and with the progressive order (the default with 8 pixels
+    per thread, one tile per block) its second phase: phase map, scatter, window,
+    the three list kernels, binning and the resumed tiles."""
+    if args.persistent:
+        return 6 + 8 + 1
+    if args.depth_prefix >= 0 and args.ppt == 8 and args.tpb == 1:
+        return 6 + 8 + 2 + 8
+    return 6 + 8 + 2
 F_EVAL_ITEMISED, F_CONTRIB_ITEMISED = 11, 11
 F_CONTRIB_ONLY = 22
 # FP32 rate derived from unit counts (148 SMs x 128 FP32 lanes x 2 flop/FMA x 2.032 GHz),
@@ -66,8 +75,8 @@ FP32_NOMINAL_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # dram__bytes_read.sum and dram__bytes_write.sum, one launch, clocks not locked; the
 # outputs, 629 MB, exceed L2), valid only for the kernel source it was taken on: src_sha
 # is the sha256 prefix of k_composite.cu followed by gs_internal.cuh
-TRAFFIC_CAPTURE = {"cameras": 128, "read": 11_521_792, "write": 576_307_712,
-                   "src_sha": "53dcd17a08fe0ac8"}
+TRAFFIC_CAPTURE = {"cameras": 128, "read": 8_957_952, "write": 575_968_256,
+                   "src_sha": "8e7b4cf597e4fefd"}
 
 
 def _composite_sha() -> str:
@@ -272,11 +281,11 @@ def oracle_time_main(args):
 CNN_FLOPS_PER_LR_PIXEL = 2 * 9 * (6 * 32 + 4 * 32 * 32 + 32 * 48)
 
 
-def upsampled_launches(n_cams, chunk, w, h):
+def upsampled_launches(n_cams, chunk, w, h, per_chunk):
     """Kernel launches of one gs_render_batch_upsampled call: the intrinsics
-    scaling, then per part of at most `chunk` cameras one render chunk and the
-    upsampler (input preparation + 6 convolutions per frame group of at most
-    1 GiB of activations)."""
+    scaling, then per part of at most `chunk` cameras one render chunk
+    (per_chunk kernels) and the upsampler (input preparation + 6 convolutions
+    per frame group of at most 1 GiB of activations)."""
     def a256(b):
         return (b + 255) // 256 * 256
     per_frame = a256(w * h * 16 * 2) + 2 * a256(w * h * 32 * 2)
@@ -284,7 +293,7 @@ def upsampled_launches(n_cams, chunk, w, h):
     for c0 in range(0, n_cams, chunk):
         m = min(chunk, n_cams - c0)
         group = max(1, min(m, (1 << 30) // per_frame))
-        total += LAUNCHES_PER_CHUNK + 7 * -(-m // group)
+        total += per_chunk + 7 * -(-m // group)
     return total
 
 
@@ -453,7 +462,7 @@ def batched_leg(args, gs, torch, scenes, which, vm, it, Ws, Hs, local, stream, g
                      "frac": achieved / fp32_tflops if achieved else None,
                      "peak_source": "measured (gs_microbench)"},
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
-        "gpu_launches": LAUNCHES_PER_CHUNK * n_chunks * args.steps,
+        "gpu_launches": launches_per_chunk(args) * n_chunks * args.steps,
         "clocks": clk,
     }
 
@@ -647,8 +656,9 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
             "frac": cnn_tflops / bf16_peak,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the CNN is timed alone)",
             "flops_per_lr_pixel": CNN_FLOPS_PER_LR_PIXEL},
-        "gpu_launches_per_step": upsampled_launches(len(ids_f), args.chunk, w, h)
-        + (LAUNCHES_PER_CHUNK * -(-len(ids_s) // args.chunk) if len(ids_s) else 0),
+        "gpu_launches_per_step": upsampled_launches(len(ids_f), args.chunk, w, h,
+                                                    launches_per_chunk(args))
+        + (launches_per_chunk(args) * -(-len(ids_s) // args.chunk) if len(ids_s) else 0),
     }
 
 
@@ -696,6 +706,7 @@ def run_b300(args):
 
     ms_comp, n_chunks = 0.0, 0
     stage_ms = {"project": 0.0, "sort": 0.0, "bin": 0.0, "composite": 0.0}
+    second = {"cameras": 0, "tiles": 0}  # the progressive order's second phase
 
     def per_step():
         nonlocal ms_comp, n_chunks
@@ -704,6 +715,8 @@ def run_b300(args):
         n_chunks += st["n_chunks"]
         for k in stage_ms:
             stage_ms[k] += st["ms_" + k]
+        second["cameras"] += st["depth_second_phase_cameras"]
+        second["tiles"] += st["depth_resumed_tiles"]
 
     for _ in range(args.warmup):
         step()
@@ -718,7 +731,7 @@ def run_b300(args):
     clk = clocks.stop()
     t_max = max_over_ranks(ms, dist)
     value = whole_job_rate(n * args.steps, world, t_max / 1e3)
-    launches = LAUNCHES_PER_CHUNK * n_chunks
+    launches = launches_per_chunk(args) * n_chunks
 
     # end to end: host cameras in, host frames out, through the host entry point
     e2e = None
@@ -790,7 +803,8 @@ def run_b300(args):
                       "intersections_per_step": cst["intersections"],
                       "depth_order": {"windows_to_block_sort": cst["sort_windows_listed"],
                                       "equal_key_runs": cst["sort_equal_runs"],
-                                      "runs_over_32": cst["sort_long_runs"]}},
+                                      "runs_over_32": cst["sort_long_runs"]},
+                      "second_phase_per_step": {k: v / args.steps for k, v in second.items()}},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         }
         if world == 1 and not args.no_cpu_baseline:
