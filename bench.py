@@ -831,6 +831,7 @@ def run_b300(args):
         targs.comp_batch, targs.group = cfg["comp_batch"], cfg["camera_group"]
         targs.chunk = cfg["max_chunk_cameras"]
         targs.persistent = cfg["persistent"]
+        targs.depth_prefix = cfg.get("depth_prefix", 0)
         leg = batched_leg(targs, gs, torch, scenes, which, bvm, bit, Ws, Hs, local, stream, True,
                           fp32, clocks=ClockSampler(local))
         default_ms = [t[0] for t in tuned["timings"] if t[1] == {**autotune.DEFAULTS}]

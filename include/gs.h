@@ -94,7 +94,7 @@ typedef struct gs_config {
                               almost always within the nearest few per cent of a
                               camera's survivors, so a first phase orders and bins only
                               each camera's nearest ranks (at least this many, rounded
-                              up to whole depth buckets; 0: 2,048, or 1/128 of the
+                              up to whole depth buckets; 0: 4,096, or 1/128 of the
                               camera's survivors when more), tiles that still have
                               live pixels there
                               save their state, and a second phase orders and bins the

@@ -16,10 +16,15 @@ once), over:
                       queue (8 pixels per thread, one tile per block);
   camera_group        cameras of one scene that share one Gaussian load in the
                       projection kernels (Gaussian batch per projection block);
-  max_chunk_cameras   cameras per chunk of the render pipeline.
+  max_chunk_cameras   cameras per chunk of the render pipeline;
+  depth_prefix        0 (the library's 4,096), 2,048 or 8,192 -- ranks per camera
+                      the progressive depth order takes first (8 pixels per
+                      thread, one tile per block, separate launches): sparser
+                      scenes need deeper lists, denser ones fewer.
 The search is staged: first the compositing knobs (layout and batch) with the
 default pipeline knobs, then the pipeline knobs (camera group and chunk) with
-the best compositing knobs; the fastest candidate is kept. Results are cached
+the best compositing knobs, then the depth order's first-phase depth; the
+fastest candidate is kept. Results are cached
 in a JSON file keyed by the GPU and a signature of the batch (camera count,
 resolutions, scene sizes, SH degrees), so a later run with the same kind of
 batch skips the search.
@@ -40,12 +45,14 @@ DEFAULT_SPACE = {
     "persistent": (0, 1),
     "camera_group": (32, 64, 128),
     "max_chunk_cameras": (128, 256, 512),
+    "depth_prefix": (0, 2048, 8192),
 }
-# the stages of the search: compositing knobs first, then the pipeline knobs
+# the stages of the search: compositing knobs first, then the pipeline knobs,
+# then the depth order's first phase
 STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch", "persistent"),
-          ("camera_group", "max_chunk_cameras"))
+          ("camera_group", "max_chunk_cameras"), ("depth_prefix",))
 DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 32, "persistent": 0,
-            "camera_group": 128, "max_chunk_cameras": 512}
+            "camera_group": 128, "max_chunk_cameras": 512, "depth_prefix": 0}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
 
@@ -84,12 +91,16 @@ def store_cache(entry_key: str, entry: dict, path: str = DEFAULT_CACHE) -> None:
 
 def _distinct(c: dict) -> bool:
     """False for combinations the library runs as another one: quads need 8
-    pixels per thread, and the batch and the persistent launch are knobs of the
-    8-pixel, one-tile layout only (others stage 64 in separate launches)."""
+    pixels per thread, the batch and the persistent launch are knobs of the
+    8-pixel, one-tile layout only (others stage 64 in separate launches), and
+    the depth prefix matters only for that layout's separate launches (the
+    others order the whole list at once)."""
     ppt, tpb = c.get("pixels_per_thread", 8), c.get("tiles_per_block", 1)
     if tpb == 4 and ppt != 8:
         return False
     if (c.get("comp_batch", 32) != 32 or c.get("persistent", 0)) and (ppt != 8 or tpb != 1):
+        return False
+    if c.get("depth_prefix", 0) != 0 and (ppt != 8 or tpb != 1 or c.get("persistent", 0)):
         return False
     return True
 

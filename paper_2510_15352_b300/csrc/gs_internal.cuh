@@ -210,10 +210,12 @@ constexpr int DEPTH_WINDOW = 1024;   // window stride (SORT_TILE_KEYS / 2)
 // the buckets before `bucket`, which are the windows before `win1`. pos is the
 // first bucket start at or past prefix ranks rounded up to whole windows
 // (prefix: DEPTH_PREFIX_MIN, or count / DEPTH_PREFIX_DIV when larger, or the
-// configured number; the whole segment when the order is not progressive). On
-// the 640x480, 1M-Gaussian workload a cut at 2,048 ranks measured best (1,024:
-// more cameras need the second phase; 8,192 and an eighth of the survivors:
-// more of the first phase's work is never read).
+// configured number; the whole segment when the order is not progressive).
+// Measured: on the 640x480, 1M-Gaussian workload cuts at 2,048 and 4,096 ranks
+// are as fast (1,024: more cameras need the second phase; 8,192 and an eighth
+// of the survivors: more first-phase work is never read); on the 32-scene
+// mixed batch, whose sparser scenes need deeper lists, 4,096 is 5 % faster than
+// 2,048 (788 instead of 1,806 of 4,096 cameras need the second phase).
 // A tile that still has live pixels at its camera's cut saves its compositing
 // state and flags the camera; the second phase orders and bins the rest of the
 // flagged cameras only and resumes those tiles.
@@ -223,7 +225,7 @@ struct DepthCut {
     int win1;    // windows of the first phase
     int count;   // the segment's keys
 };
-constexpr int DEPTH_PREFIX_MIN = 2048;
+constexpr int DEPTH_PREFIX_MIN = 4096;
 constexpr int DEPTH_PREFIX_DIV = 128;
 
 // The work items of one phase per chunk (k_plan.cu, k_phase_map), an int

@@ -149,11 +149,23 @@ __global__ void __launch_bounds__(BIN_THREADS)
         const int nsup = SX * SY, Pp = nsup | 1;
         if (tid < 7) reinterpret_cast<float4 *>(&scam)[tid] = reinterpret_cast<const float4 *>(&camtab[bt.x])[tid];
         for (int i = tid; i < Pp * WORDS; i += NTH) sbm[i] = 0u;
-        uint32_t slot[RPT];
+        // the Gaussians of the thread's ranks, each step's loads issued together
+        // (slot, caller index, position: three dependent gathers, not twelve)
+        uint32_t gi[RPT];
 #pragma unroll
         for (int j = 0; j < RPT; ++j) {
             const int r = r0 + j * NTH + tid;
-            slot[j] = r < lim ? vals[ci.seg_off + r] : 0u;
+            gi[j] = r < lim ? vals[ci.seg_off + r] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int r = r0 + j * NTH + tid;
+            gi[j] = r < lim ? oidx[ci.seg_off + gi[j]] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int r = r0 + j * NTH + tid;
+            gi[j] = r < lim ? (uint32_t)sc.pos_of[gi[j]] : 0u;
         }
         __syncthreads();  // sbm cleared, scam loaded
         unsigned long long area = 0;
@@ -161,7 +173,7 @@ __global__ void __launch_bounds__(BIN_THREADS)
         for (int j = 0; j < RPT; ++j) {
             const int r = r0 + j * NTH + tid;
             if (r >= lim) continue;
-            const long long g = sc.pos_of[oidx[ci.seg_off + slot[j]]];
+            const long long g = gi[j];
             const long long at = ci.seg_off + r;
             const uint2 d =
                 sc.app_dtype == DT_F32 ? rank_record<float>(scam, sc, g, P, ln_alpha_min, rec, at)

@@ -10,8 +10,12 @@ from paper_2510_15352_b300 import autotune, synth
 
 def test_candidates_cover_the_space():
     c = list(autotune.candidates())
-    # layouts (2,1) (4,1) (8,1) x 4 batches x 2 launch forms (8,4) x groups x chunks
-    assert len(c) == 11 * 3 * 3
+    # layouts (2,1) (4,1) (8,1) x 4 batches x 2 launch forms (8,4) x groups x chunks, the
+    # 4 progressive ones (8,1, separate launches) with 3 depth prefixes: 19 x 3 x 3
+    assert len(c) == (4 * 3 + 7) * 3 * 3
+    assert {x["depth_prefix"] for x in c} == {0, 2048, 8192}
+    assert all(x["depth_prefix"] == 0 for x in c
+               if x["pixels_per_thread"] != 8 or x["tiles_per_block"] != 1 or x["persistent"])
     assert {x["pixels_per_thread"] for x in c} == {2, 4, 8}
     assert {(x["pixels_per_thread"], x["tiles_per_block"]) for x in c} == {(2, 1), (4, 1), (8, 1), (8, 4)}
     assert {x["comp_batch"] for x in c if x["pixels_per_thread"] == 8 and x["tiles_per_block"] == 1} \
@@ -22,12 +26,16 @@ def test_candidates_cover_the_space():
 
 def test_staged_search_space():
     """The search's stages: the compositing knobs with the default pipeline
-    knobs (11 candidates), then the pipeline knobs (9)."""
+    knobs (11 candidates), then the pipeline knobs (9), then the depth prefix
+    (3 for the progressive layout, 1 otherwise)."""
     best = dict(autotune.DEFAULTS)
     s1 = list(autotune.candidates(None, autotune.STAGES[0], best))
     assert len(s1) == 11 and all(c["camera_group"] == 128 and c["max_chunk_cameras"] == 512 for c in s1)
     s2 = list(autotune.candidates(None, autotune.STAGES[1], s1[0]))
     assert len(s2) == 9 and all(c["comp_batch"] == s1[0]["comp_batch"] for c in s2)
+    prog = dict(best, pixels_per_thread=8, tiles_per_block=1, persistent=0)
+    assert len(list(autotune.candidates(None, autotune.STAGES[2], prog))) == 3
+    assert len(list(autotune.candidates(None, autotune.STAGES[2], dict(prog, persistent=1)))) == 1
 
 
 def test_signature_depends_on_the_batch_not_on_order():
