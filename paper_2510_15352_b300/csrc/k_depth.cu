@@ -940,7 +940,9 @@ cudaError_t launch_depth_finish(const uint32_t *keys, uint32_t *scr_k, uint32_t 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counters, 0, 3 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_depth_scatter<2><<<grid, BT, 0, s>>>(keys, sk, sv, tiles, nullptr, count, cut, map, m);
+    // (usually little or no work: a small grid, looping over the map's tiles)
+    k_depth_scatter<2><<<std::min(grid, 4 * sms), BT, 0, s>>>(keys, sk, sv, tiles, nullptr, count,
+                                                               cut, map, m);
     depth_windows(scr_k, scr_v, sk, sv, oidx, tiles, seg_start, map, m, nullptr, grid, count,
                   (const int4 *)win, big, big_cap, eq, eq_cap, runs, run_cap, counters, sms,
                   win_per, s);
