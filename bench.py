@@ -75,8 +75,8 @@ FP32_NOMINAL_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # dram__bytes_read.sum and dram__bytes_write.sum, one launch, clocks not locked; the
 # outputs, 629 MB, exceed L2), valid only for the kernel source it was taken on: src_sha
 # is the sha256 prefix of k_composite.cu followed by gs_internal.cuh
-TRAFFIC_CAPTURE = {"cameras": 128, "read": 8_957_952, "write": 575_968_256,
-                   "src_sha": "8e7b4cf597e4fefd"}
+TRAFFIC_CAPTURE = {"cameras": 128, "read": 8_915_712, "write": 574_920_960,
+                   "src_sha": "5aeb00024d3ea24f"}
 
 
 def _composite_sha() -> str:
@@ -861,7 +861,7 @@ def main():
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
     ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 4096)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED])
-    ap.add_argument("--chunk", type=int, default=512, help="cameras per internal chunk")
+    ap.add_argument("--chunk", type=int, default=1024, help="cameras per internal chunk")
     ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
     ap.add_argument("--group", type=int, default=128,
                     help="cameras sharing one Gaussian load in the projection (<= 128)")

@@ -44,7 +44,7 @@ DEFAULT_SPACE = {
     "comp_batch": (32, 64, 96, 128),
     "persistent": (0, 1),
     "camera_group": (32, 64, 128),
-    "max_chunk_cameras": (128, 256, 512),
+    "max_chunk_cameras": (256, 512, 1024),
     "depth_prefix": (0, 2048, 8192),
 }
 # the stages of the search: compositing knobs first, then the pipeline knobs,
@@ -52,7 +52,7 @@ DEFAULT_SPACE = {
 STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch", "persistent"),
           ("camera_group", "max_chunk_cameras"), ("depth_prefix",))
 DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 32, "persistent": 0,
-            "camera_group": 128, "max_chunk_cameras": 512, "depth_prefix": 0}
+            "camera_group": 128, "max_chunk_cameras": 1024, "depth_prefix": 0}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
 
@@ -110,6 +110,8 @@ def candidates(space: dict | None = None, keys=None, base: dict | None = None):
     the other knobs taken from `base`."""
     space = space or DEFAULT_SPACE
     keys = sorted(k for k in (keys or space) if k in space)
+    if not keys:  # a stage none of whose knobs the space holds
+        return
     for vals in itertools.product(*(space[k] for k in keys)):
         c = dict(base or {})
         c.update(zip(keys, vals))
@@ -144,6 +146,9 @@ def tune(scenes, scene_of_camera, viewmats, intrinsics, widths, heights, device:
         ids = np.array([r.add_scene(s) for s in scenes], dtype=np.int32)[scene_of_camera]
 
         def measure(cand):
+            for ms, c in timings:  # the previous stage's choice, already timed
+                if c == cand:
+                    return ms
             r.set_config(**cand)
             r.render_v(ids, vm, it, widths, heights, rgb, depth, stream=stream)  # warm-up
             e0 = torch.cuda.Event(enable_timing=True)

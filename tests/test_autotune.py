@@ -27,15 +27,18 @@ def test_candidates_cover_the_space():
 def test_staged_search_space():
     """The search's stages: the compositing knobs with the default pipeline
     knobs (11 candidates), then the pipeline knobs (9), then the depth prefix
-    (3 for the progressive layout, 1 otherwise)."""
+    (3 for the progressive layout, 1 otherwise; none when the space lacks it)."""
     best = dict(autotune.DEFAULTS)
     s1 = list(autotune.candidates(None, autotune.STAGES[0], best))
-    assert len(s1) == 11 and all(c["camera_group"] == 128 and c["max_chunk_cameras"] == 512 for c in s1)
+    assert len(s1) == 11 and all(c["camera_group"] == 128 and c["max_chunk_cameras"] == 1024 for c in s1)
     s2 = list(autotune.candidates(None, autotune.STAGES[1], s1[0]))
     assert len(s2) == 9 and all(c["comp_batch"] == s1[0]["comp_batch"] for c in s2)
     prog = dict(best, pixels_per_thread=8, tiles_per_block=1, persistent=0)
     assert len(list(autotune.candidates(None, autotune.STAGES[2], prog))) == 3
     assert len(list(autotune.candidates(None, autotune.STAGES[2], dict(prog, persistent=1)))) == 1
+    # a space without the depth prefix has no third stage (nothing is timed twice)
+    small = {"pixels_per_thread": (4, 8), "max_chunk_cameras": (8, 24)}
+    assert list(autotune.candidates(small, autotune.STAGES[2], prog)) == []
 
 
 def test_signature_depends_on_the_batch_not_on_order():
