@@ -544,10 +544,9 @@ gs_status enqueue_render(gs_context *ctx, const RenderArgs &a, const Plan &P, ch
                                     (long long)(ctx->ties.cap / tie_run_bytes()),
                                     (int *)ctx->nruns.p + 6 * k + 3, cut, map2, st));
             if (E) CKC(cudaEventRecord(E[5], st));
-            // (the flagged cameras only: usually little or no work, a small grid)
-            CKC(launch_bin_rec(cams, (const int2 *)ctx->bintab.p, ch.m,
-                               std::min(ch.bin_grid, std::max(4 * resume_grid() / 18, 1)),
-                               ch.max_sup,
+            // (the flagged cameras only: usually little or no work, one wave of
+            // resident blocks looping over the phase map)
+            CKC(launch_bin_rec(cams, (const int2 *)ctx->bintab.p, ch.m, ch.bin_grid, ch.max_sup,
                                ch.bin_ranks, (const SceneDev *)ctx->d_scenes.p, ctx->camtab.p, PP,
                                ln_amin, (const uint32_t *)ctx->oidx.p,
                                (const uint32_t *)ctx->tvals.p, recs, (uint2 *)ctx->rrect.p,

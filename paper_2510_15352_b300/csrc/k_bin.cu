@@ -225,6 +225,16 @@ cudaError_t launch_bin_rec(const CamInfo *cams, const int2 *bintab, int n_slots,
                                                  (int)smem);                                     \
             if (e != cudaSuccess) return e;                                                      \
         }                                                                                        \
+        if (phase == 2) { /* one wave of resident blocks: a second wave would double the time */ \
+            int occ = 0, dev = 0, sms = 0;                                                       \
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BIN_THREADS, \
+                                                                          smem);                 \
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);                                       \
+            if (e == cudaSuccess)                                                                \
+                e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);           \
+            if (e != cudaSuccess) return e;                                                      \
+            n_blocks = std::min(n_blocks, std::max(occ * sms, 1));                               \
+        }                                                                                        \
         kern<<<n_blocks, BIN_THREADS, smem, s>>>(cams, bintab, n_slots, scenes, ct, P,           \
                                                  ln_alpha_min, oidx, vals, rec, rrect, bitmap,   \
                                                  n_isect, cut, phase, map);                      \
