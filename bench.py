@@ -861,7 +861,7 @@ def main():
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
     ap.add_argument("--cams", type=int, default=None, help="cameras per GPU (default 4096)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, BATCHED])
-    ap.add_argument("--chunk", type=int, default=1024, help="cameras per internal chunk")
+    ap.add_argument("--chunk", type=int, default=2048, help="cameras per internal chunk")
     ap.add_argument("--ppt", type=int, default=8, help="compositing pixels per thread (2|4|8)")
     ap.add_argument("--group", type=int, default=128,
                     help="cameras sharing one Gaussian load in the projection (<= 128)")

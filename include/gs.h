@@ -61,7 +61,7 @@ typedef struct gs_config {
     float alpha_max;       /* alpha is clamped to this (0.99) */
     float T_min;           /* a pixel stops before T would fall below this (1e-4) */
     float background[3];   /* added as T * background to rgb (0, 0, 0) */
-    int32_t max_chunk_cameras; /* cameras rendered per internal chunk (1024) */
+    int32_t max_chunk_cameras; /* cameras rendered per internal chunk (2048) */
     int32_t camera_group;  /* cameras of one scene that share one Gaussian load in the
                               projection kernels (128, at most 128) */
     int32_t count_pairs;   /* 1: the compositing kernel also counts evaluated pairs

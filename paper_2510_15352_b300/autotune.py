@@ -44,7 +44,7 @@ DEFAULT_SPACE = {
     "comp_batch": (32, 64, 96, 128),
     "persistent": (0, 1),
     "camera_group": (32, 64, 128),
-    "max_chunk_cameras": (256, 512, 1024),
+    "max_chunk_cameras": (512, 1024, 2048),
     "depth_prefix": (0, 2048, 8192),
 }
 # the stages of the search: compositing knobs first, then the pipeline knobs,
@@ -52,7 +52,7 @@ DEFAULT_SPACE = {
 STAGES = (("pixels_per_thread", "tiles_per_block", "comp_batch", "persistent"),
           ("camera_group", "max_chunk_cameras"), ("depth_prefix",))
 DEFAULTS = {"pixels_per_thread": 8, "tiles_per_block": 1, "comp_batch": 32, "persistent": 0,
-            "camera_group": 128, "max_chunk_cameras": 1024, "depth_prefix": 0}
+            "camera_group": 128, "max_chunk_cameras": 2048, "depth_prefix": 0}
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
 

@@ -779,7 +779,7 @@ gs_status gs_config_default(gs_config *out) {
     out->alpha_min = 1.0f / 255.0f;
     out->alpha_max = 0.99f;
     out->T_min = 1e-4f;
-    out->max_chunk_cameras = 1024;
+    out->max_chunk_cameras = 2048;
     out->camera_group = 128;
     out->count_pairs = 0;
     out->time_stages = 0;

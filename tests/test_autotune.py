@@ -30,7 +30,7 @@ def test_staged_search_space():
     (3 for the progressive layout, 1 otherwise; none when the space lacks it)."""
     best = dict(autotune.DEFAULTS)
     s1 = list(autotune.candidates(None, autotune.STAGES[0], best))
-    assert len(s1) == 11 and all(c["camera_group"] == 128 and c["max_chunk_cameras"] == 1024 for c in s1)
+    assert len(s1) == 11 and all(c["camera_group"] == 128 and c["max_chunk_cameras"] == 2048 for c in s1)
     s2 = list(autotune.candidates(None, autotune.STAGES[1], s1[0]))
     assert len(s2) == 9 and all(c["comp_batch"] == s1[0]["comp_batch"] for c in s2)
     prog = dict(best, pixels_per_thread=8, tiles_per_block=1, persistent=0)
