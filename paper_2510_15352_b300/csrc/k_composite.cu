@@ -30,15 +30,14 @@
 // its alpha >= alpha_min region meets the warp's rows, and the largest value of
 // the quadratic over the rows' pixel-centre rectangle reaches the threshold);
 // other warps skip it (uniform branch; both tests have margins past float32
-// rounding, so the skip never changes a result); the blend runs only
-// when some lane passes the alpha test (warp vote) and is branch-free: a
-// stopped pixel's alpha threshold becomes +inf, which freezes it. The block
-// stops reading its list once every pixel has stopped. The blend updates T and
-// the sums of two pixels per packed FP32x2 instruction (each lane rounds as
-// the scalar instruction would), and with one warp per tile the records are
-// taken two at a time: both quadratics, then both votes, then the blends, so
-// the two records' latencies overlap. No tensor cores: this is not a dense
-// contraction.
+// rounding, so the skip never changes a result); the blend is branch-free: a
+// stopped pixel's alpha threshold becomes +inf, which freezes it. With one
+// warp per tile (8 pixels per thread) records no pixel of the tile can take
+// are not staged and every staged record is blended; the other layouts blend
+// only when some lane passes the alpha test (warp vote). The block stops
+// reading its list once every pixel has stopped. The blend updates T and the
+// sums of two pixels per packed FP32x2 instruction (each lane rounds as the
+// scalar instruction would). No tensor cores: this is not a dense contraction.
 #include <type_traits>
 
 #include "bin_core.cuh"
@@ -390,7 +389,8 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
             if (__any_sync(0xffffffffu, live)) {
                 // p_k = a'dx^2 + b'dy dx + c'dy^2 + log2 o of the thread's pixels
                 // k = 0..PPT-1 (at dx = dx0 + k CPR: P0 + k (D + k E)); true when
-                // some pixel passes its alpha test
+                // some pixel passes its alpha test (the warp vote of the layouts
+                // that stage every record)
                 auto quad_p = [&](const float4 &g0, const float4 &g1, float (&p)[PPT]) {
                     const float dy = py - g0.y;
                     const float dx0 = px0 - g0.x;
@@ -451,34 +451,17 @@ __device__ __forceinline__ void composite_tile(const CamInfo ci, int t, const Co
                         blend(p, g2, g1.z, std::false_type{});
                 };
                 if constexpr (COMPACT) {
-                    // Records in groups of UNR: their quadratics and votes are
-                    // independent, so their latencies overlap. A record's vote
-                    // sees the thresholds before the group's earlier blends; a
-                    // pixel can only stop there, so the vote may say "some pixel
-                    // passes" when none does (the blend then adds nothing), never
-                    // the reverse.
-                    constexpr int UNR = 2;
-                    int j = 0;
-                    for (; j + UNR <= nb; j += UNR) {
-                        float4 g1u[UNR];
-                        float pu[UNR][PPT];
-                        bool vu[UNR];
-#pragma unroll
-                        for (int u = 0; u < UNR; ++u) g1u[u] = s1[j + u];
-                        // every quadratic before the first vote (a vote is a
-                        // warp-wide step the compiler does not move work across)
-#pragma unroll
-                        for (int u = 0; u < UNR; ++u) vu[u] = quad_p(s0[j + u], g1u[u], pu[u]);
-#pragma unroll
-                        for (int u = 0; u < UNR; ++u) vu[u] = __any_sync(0xffffffffu, vu[u]);
-#pragma unroll
-                        for (int u = 0; u < UNR; ++u)
-                            if (vu[u]) blend_rec(pu[u], s2[j + u], g1u[u]);
-                    }
-                    for (; j < nb; ++j) {
+                    // Every staged record is blended, with no warp vote first: a
+                    // record no pixel passes adds exactly nothing (its weights are
+                    // zero, T and the thresholds unchanged). The vote skipped ~14 %
+                    // of the staged records but cost a compare per pixel on the
+                    // ALU pipe, the kernel's busiest (79.4 -> 78.7 ms per 4,096
+                    // cameras without it; records in pairs then spilled: 83.5).
+                    for (int j = 0; j < nb; ++j) {
                         const float4 g1 = s1[j];
                         float p[PPT];
-                        if (__any_sync(0xffffffffu, quad_p(s0[j], g1, p))) blend_rec(p, s2[j], g1);
+                        quad_p(s0[j], g1, p);
+                        blend_rec(p, s2[j], g1);
                     }
                 } else {
                     for (int j = 0; j < nb; ++j) {
