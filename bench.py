@@ -549,7 +549,7 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
     same cameras (time and PSNR). The network is trained first (untimed) on
     renderer pairs of held-out poses cycling through the scenes; each scene is
     validated on 8 other poses, and the cameras of a scene below 35 dB are
-    rendered at full resolution instead (the fallback)."""
+    rendered at full resolution instead (the fallback: upsampler.FallbackPlan)."""
     import numpy as np
     from paper_2510_15352_b300 import upsampler
     W, H = 640, 480
@@ -574,21 +574,11 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
                                  lr_max=1e-3, lr_min=3e-5, seed=100)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        val = {}
-        for k, sid in enumerate(sids):
-            vmv, itv = synth.make_cameras(8, W, H, 0.75 * W, (0.3, 1.2), seed=7000 + k)
-            val[k] = upsampler.evaluate(up, R, sid, vmv, itv, W, H)["psnr_mean"]
-        slow = np.array([val[int(which[i])] < 35.0 for i in range(n)])
-        fast_idx = torch.from_numpy(np.nonzero(~slow)[0]).cuda()
-        slow_idx = torch.from_numpy(np.nonzero(slow)[0]).cuda()
+        # per-scene validation; the cameras of a scene below 35 dB render at full size
+        val = upsampler.validate_scenes(up, R, sids, W, H)
+        plan = upsampler.FallbackPlan(ids, vm_d, it_d, W, H, val)
         plain = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
         plain_d = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
-        vm_f, it_f, ids_f = vm_d[fast_idx].contiguous(), it_d[fast_idx].contiguous(), ids[~slow]
-        vm_s, it_s, ids_s = vm_d[slow_idx].contiguous(), it_d[slow_idx].contiguous(), ids[slow]
-        out_f = torch.empty((len(ids_f), H, W, 3), dtype=torch.float32, device="cuda")
-        out_fd = torch.empty((len(ids_f), H, W), dtype=torch.float32, device="cuda")
-        out_s = torch.empty((len(ids_s), H, W, 3), dtype=torch.float32, device="cuda")
-        out_sd = torch.empty((len(ids_s), H, W), dtype=torch.float32, device="cuda")
         lr = torch.empty((n, h, w, 3), dtype=torch.float32, device="cuda")
         ld = torch.empty((n, h, w), dtype=torch.float32, device="cuda")
         it_q = it_d / 4.0
@@ -597,10 +587,7 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
             R.render(ids, vm_d, it_d, W, H, plain, plain_d, stream=stream)
 
         def up_step():
-            if len(ids_f):
-                R.render_upsampled(up, ids_f, vm_f, it_f, W, H, out_f, out_fd, stream=stream)
-            if len(ids_s):
-                R.render(ids_s, vm_s, it_s, W, H, out_s, out_sd, stream=stream)
+            plan.render(R, up, stream=stream)
 
         def lr_step():
             R.render(ids, vm_d, it_q, w, h, lr, ld, stream=stream)
@@ -611,10 +598,7 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
         ms_plain = _timed_steps(torch, stream, plain_step, args.steps, args.warmup) / args.steps
         ms_up = _timed_steps(torch, stream, up_step, args.steps, args.warmup) / args.steps
         up.check(stream)
-        out = torch.empty_like(plain)
-        out[fast_idx] = out_f
-        if len(ids_s):
-            out[slow_idx] = out_s
+        out, _ = plan.assemble()
         p_net = upsampler.psnr(out, plain).cpu().numpy()
         # bilinear x4 of the quarter-resolution render, for reference
         lr_step()
@@ -642,7 +626,7 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
         "plain_same_cameras": {"value": n / (ms_plain / 1e3), "unit": UNIT,
                                "ms_per_step": ms_plain},
         "speedup_vs_plain": ms_plain / ms_up,
-        "fallback_cameras": int(slow.sum()),
+        "fallback_cameras": plan.fallback_cameras,
         "psnr_db_mean": float(p_net.mean()), "psnr_db_p5": float(np.percentile(p_net, 5)),
         "bilinear_psnr_db_mean": float(p_bil.mean()),
         "bilinear_psnr_db_p5": float(np.percentile(p_bil, 5)),
@@ -656,9 +640,9 @@ def upsampled_batched_leg(args, gs, torch, synth, scenes, which, vm, local, stre
             "frac": cnn_tflops / bf16_peak,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the CNN is timed alone)",
             "flops_per_lr_pixel": CNN_FLOPS_PER_LR_PIXEL},
-        "gpu_launches_per_step": upsampled_launches(len(ids_f), args.chunk, w, h,
+        "gpu_launches_per_step": upsampled_launches(len(plan.ids_f), args.chunk, w, h,
                                                     launches_per_chunk(args))
-        + (launches_per_chunk(args) * -(-len(ids_s) // args.chunk) if len(ids_s) else 0),
+        + (launches_per_chunk(args) * -(-len(plan.ids_s) // args.chunk) if len(plan.ids_s) else 0),
     }
 
 

@@ -115,3 +115,75 @@ def train(up: "gs.Upsampler", renderer: "gs.Renderer", scene_ids, W: int, H: int
         if log:
             log(f"pairs {step * frames_per_step}: loss {float(losses[-1].item()):.3e}")
     return [float(x) for x in torch.cat(losses).cpu()]
+
+
+# A scene whose held-out poses upsample below this PSNR (against the full render)
+# is rendered at full resolution instead.
+PSNR_FLOOR_DB = 35.0
+
+
+def validate_scenes(up: "gs.Upsampler", renderer: "gs.Renderer", scene_ids, W: int, H: int,
+                    n_poses: int = 8, seed: int = 7000) -> dict:
+    """Mean PSNR of the upsampled render per scene on `n_poses` held-out poses
+    (robot-height cameras, f = 0.75 W; pose seed `seed + k` for the k-th scene)."""
+    out = {}
+    for k, sid in enumerate(scene_ids):
+        vm, it = synth.make_cameras(n_poses, W, H, 0.75 * W, (0.3, 1.2), seed=seed + k)
+        out[int(sid)] = evaluate(up, renderer, sid, vm, it, W, H)["psnr_mean"]
+    return out
+
+
+class FallbackPlan:
+    """One batch of cameras split by scene quality: cameras of scenes whose
+    validation PSNR is below `floor_db` are rendered at full resolution, the
+    others at a quarter of the resolution and upsampled. The split, the index
+    tensors and the two output buffers are made once; `render` issues the two
+    calls on a stream (nothing else), `assemble` scatters both parts into one
+    [n][H][W][3] / [n][H][W] pair in camera order."""
+
+    def __init__(self, scene_of_camera, viewmats, intrinsics, W: int, H: int, psnr_by_scene: dict,
+                 floor_db: float = PSNR_FLOOR_DB):
+        import torch
+        ids = np.asarray(scene_of_camera, dtype=np.int32)
+        self.W, self.H, self.n = W, H, len(ids)
+        self.slow = np.array([psnr_by_scene[int(s)] < floor_db for s in ids], dtype=bool)
+        dev = viewmats.device
+        self.fast_idx = torch.from_numpy(np.nonzero(~self.slow)[0]).to(dev)
+        self.slow_idx = torch.from_numpy(np.nonzero(self.slow)[0]).to(dev)
+        self.ids_f, self.ids_s = ids[~self.slow], ids[self.slow]
+        self.vm_f = viewmats[self.fast_idx].contiguous()
+        self.it_f = intrinsics[self.fast_idx].contiguous()
+        self.vm_s = viewmats[self.slow_idx].contiguous()
+        self.it_s = intrinsics[self.slow_idx].contiguous()
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.rgb_f = torch.empty((len(self.ids_f), H, W, 3), **f32)
+        self.depth_f = torch.empty((len(self.ids_f), H, W), **f32)
+        self.rgb_s = torch.empty((len(self.ids_s), H, W, 3), **f32)
+        self.depth_s = torch.empty((len(self.ids_s), H, W), **f32)
+
+    @property
+    def fallback_cameras(self) -> int:
+        return int(self.slow.sum())
+
+    def render(self, renderer: "gs.Renderer", up: "gs.Upsampler", stream=None) -> None:
+        if len(self.ids_f):
+            renderer.render_upsampled(up, self.ids_f, self.vm_f, self.it_f, self.W, self.H,
+                                      self.rgb_f, self.depth_f, stream=stream)
+        if len(self.ids_s):
+            renderer.render(self.ids_s, self.vm_s, self.it_s, self.W, self.H, self.rgb_s,
+                            self.depth_s, stream=stream)
+
+    def assemble(self, rgb=None, depth=None):
+        import torch
+        dev = self.rgb_f.device
+        if rgb is None:
+            rgb = torch.empty((self.n, self.H, self.W, 3), dtype=torch.float32, device=dev)
+        if depth is None:
+            depth = torch.empty((self.n, self.H, self.W), dtype=torch.float32, device=dev)
+        if len(self.ids_f):
+            rgb[self.fast_idx] = self.rgb_f
+            depth[self.fast_idx] = self.depth_f
+        if len(self.ids_s):
+            rgb[self.slow_idx] = self.rgb_s
+            depth[self.slow_idx] = self.depth_s
+        return rgb, depth

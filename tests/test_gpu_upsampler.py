@@ -334,3 +334,49 @@ def test_training_gains_over_bilinear(torch_cuda):
         R.close()
     assert np.mean(losses[-50:]) < np.mean(losses[:50])
     assert ev["psnr_mean"] > ev["bilinear_psnr_mean"] + 0.3, ev
+
+
+def test_fallback_plan_renders_failing_scenes_at_full_size(torch_cuda):
+    """The per-scene quality gate: a network that fails validation (PSNR below
+    35 dB on held-out poses) sends its scenes' cameras to the full-resolution
+    render, the others are upsampled, and the assembled batch holds each
+    camera's own result in camera order."""
+    torch = torch_cuda
+    from paper_2510_15352_b300 import gs, upsampler
+    scenes = [synth.make_scene(8000, 1, seed=40 + k) for k in range(2)]
+    W, H = 160, 120
+    vm, it = synth.make_cameras(6, W, H, 120.0, (0.3, 1.2), seed=41)
+    which = np.array([0, 1, 1, 0, 1, 0])
+    R = gs.Renderer(0)
+    up = gs.Upsampler(0)
+    try:
+        sids = [R.add_scene(s) for s in scenes]
+        ids = np.array(sids, dtype=np.int32)[which]
+        vm_d, it_d = torch.from_numpy(vm).cuda(), torch.from_numpy(it).cuda()
+        # weights far from any trained network: every scene fails the gate
+        rng = np.random.default_rng(5)
+        up.set_params(rng.normal(0.0, 1.0, gs.Upsampler.n_params).astype(np.float32))
+        val = upsampler.validate_scenes(up, R, sids, W, H, n_poses=2)
+        assert set(val) == set(sids)
+        assert all(v < upsampler.PSNR_FLOOR_DB for v in val.values()), val
+        full_rgb, full_d, _ = R.render(ids, vm_d, it_d, W, H)
+        up_rgb, up_d = R.render_upsampled(up, ids, vm_d, it_d, W, H)
+        plan = upsampler.FallbackPlan(ids, vm_d, it_d, W, H, val)
+        assert plan.fallback_cameras == len(ids)
+        plan.render(R, up)
+        rgb, d = plan.assemble()
+        torch.cuda.synchronize()
+        assert torch.equal(rgb, full_rgb) and torch.equal(d, full_d)
+        # one scene passing, the other failing
+        plan = upsampler.FallbackPlan(ids, vm_d, it_d, W, H, {sids[0]: 99.0, sids[1]: 0.0})
+        assert plan.fallback_cameras == int((which == 1).sum())
+        plan.render(R, up)
+        rgb, d = plan.assemble()
+        up.check()
+        f = torch.from_numpy(which == 0).cuda()
+        s = torch.from_numpy(which == 1).cuda()
+        assert torch.equal(rgb[f], up_rgb[f]) and torch.equal(d[f], up_d[f])
+        assert torch.equal(rgb[s], full_rgb[s]) and torch.equal(d[s], full_d[s])
+    finally:
+        up.close()
+        R.close()
